@@ -1,0 +1,200 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module only draws and lays out inputs: quadrature nodes and weights of
+the cells, source densities, target points and the sparsity pattern (and, for
+parity-only runs, seeded values) of the correction matrix. It holds none of the
+volume-potential arithmetic, so both the CUDA path and the CPU oracle can take
+their inputs from here.
+
+Layout conventions (the ones the C ABI uses):
+  * points are float64 arrays of shape [n, 2] holding (x, y);
+  * densities are float64 arrays of shape [ndens, n_src];
+  * the correction matrix is CSR (rowptr int64 [n_tgt + 1], col int32, val
+    float64), rows indexed by targets, columns by source nodes.
+
+Workloads mirror the cells of the paper: regular boxes carrying tensor
+Gauss-Legendre nodes (the box cells of Sec. 4.2, here with Gauss-Legendre in
+place of Chebyshev roots), and seeded point clouds for ragged cases.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2203_05933
+
+
+@dataclass
+class Problem:
+    """One volume-potential evaluation problem in caller order."""
+
+    name: str
+    src_xy: np.ndarray  # [n_src, 2]
+    w: np.ndarray  # [n_src]
+    tgt_xy: np.ndarray  # [n_tgt, 2]
+    f: np.ndarray  # [ndens, n_src]
+    csr: tuple | None = None  # (rowptr, col, val)
+    root: tuple | None = None  # (x0, y0, side) of the enclosing square, when known
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_src(self) -> int:
+        return int(self.src_xy.shape[0])
+
+    @property
+    def n_tgt(self) -> int:
+        return int(self.tgt_xy.shape[0])
+
+    @property
+    def ndens(self) -> int:
+        return int(self.f.shape[0])
+
+    @property
+    def nnz(self) -> int:
+        return 0 if self.csr is None else int(self.csr[0][-1])
+
+
+def gauss_legendre(order: int):
+    """Gauss-Legendre nodes and weights on [-1, 1] (numpy's routine)."""
+    return np.polynomial.legendre.leggauss(order)
+
+
+def box_grid_nodes(nbox: int, order: int, lo: float = -1.0, hi: float = 1.0):
+    """Nodes and weights of an nbox x nbox grid of boxes, order x order tensor GL.
+
+    Ordered cell by cell (cell index = by * nbox + bx), then node (iy, ix) inside
+    the cell. Weights are w_GL(ix) w_GL(iy) (side / 2)^2, i.e. the reference
+    weights times the constant Jacobian of the box map.
+    Returns (xy [n, 2], w [n], cell [n]).
+    """
+    t, wt = gauss_legendre(order)
+    side = (hi - lo) / nbox
+    half = side / 2.0
+    cx = lo + half + side * np.arange(nbox)
+    by, bx, iy, ix = np.meshgrid(np.arange(nbox), np.arange(nbox), np.arange(order),
+                                 np.arange(order), indexing="ij")
+    x = cx[bx] + half * t[ix]
+    y = cx[by] + half * t[iy]
+    w = wt[ix] * wt[iy] * half * half
+    cell = by * nbox + bx
+    xy = np.stack([x.ravel(), y.ravel()], axis=1)
+    return np.ascontiguousarray(xy), w.ravel().copy(), cell.ravel().copy()
+
+
+def f_config1(x, y):
+    """Source density of the 16x16-box workload: a Gaussian bump plus a smooth wave."""
+    return np.exp(-25.0 * ((x - 0.1) ** 2 + (y + 0.2) ** 2)) + np.sin(3.0 * x) * np.cos(2.0 * y)
+
+
+def neighbour_csr_pattern(nbox: int, order: int):
+    """CSR pattern of the box-grid correction: each target node couples to every
+    node of its own box and of the (up to) 8 boxes around it.
+    Returns (rowptr int64, col int32)."""
+    npc = order * order
+    ncell = nbox * nbox
+    cell_cols = []
+    for by in range(nbox):
+        for bx in range(nbox):
+            cols = []
+            for ny in range(max(0, by - 1), min(nbox, by + 2)):
+                for nx in range(max(0, bx - 1), min(nbox, bx + 2)):
+                    c = ny * nbox + nx
+                    cols.append(np.arange(c * npc, (c + 1) * npc))
+            cell_cols.append(np.concatenate(cols).astype(np.int32))
+    lens = np.repeat(np.array([c.size for c in cell_cols], np.int64), npc)
+    rowptr = np.zeros(ncell * npc + 1, np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    col = np.concatenate([np.tile(cell_cols[c], npc) for c in range(ncell)])
+    return rowptr, col
+
+
+def synthetic_csr_values(rowptr, col, w, seed: int, scale: float = 1.0):
+    """Seeded stand-in values for a correction pattern, sized like real ones
+    (a few times the node weight of the column). For parity and timing only."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal(col.size) * np.asarray(w)[col]
+
+
+def box_grid_problem(nbox: int = 16, order: int = 8, ndens: int = 1, seed: int = SEED_BASE + 1,
+                     csr: str = "synthetic", name: str | None = None) -> Problem:
+    """The uniform box-grid workload on [-1, 1]^2: sources = targets = the GL nodes.
+
+    csr: "synthetic" (seeded values on the own + 8 neighbour pattern), "none",
+    or a (rowptr, col, val) tuple supplied by the caller (e.g. the box
+    correction tables of the host set-up).
+    """
+    xy, w, _ = box_grid_nodes(nbox, order)
+    rng = np.random.default_rng(seed)
+    f0 = f_config1(xy[:, 0], xy[:, 1])
+    if ndens == 1:
+        f = f0[None, :]
+    else:
+        f = np.vstack([f0[None, :], rng.standard_normal((ndens - 1, xy.shape[0]))])
+    if isinstance(csr, tuple):
+        mat = csr
+    elif csr == "synthetic":
+        rowptr, col = neighbour_csr_pattern(nbox, order)
+        mat = (rowptr, col, synthetic_csr_values(rowptr, col, w, seed + 17))
+    else:
+        mat = None
+    return Problem(name=name or f"boxgrid{nbox}x{nbox}_gl{order}", src_xy=xy, w=w, tgt_xy=xy.copy(),
+                   f=np.ascontiguousarray(f), csr=mat, root=(-1.0, -1.0, 2.0),
+                   meta={"nbox": nbox, "order": order})
+
+
+def random_csr(n_tgt: int, n_src: int, per_row_max: int, seed: int, empty_frac: float = 0.1):
+    """Seeded random CSR with ragged rows (some empty), sorted columns."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, per_row_max + 1, size=n_tgt)
+    lens[rng.random(n_tgt) < empty_frac] = 0
+    lens = np.minimum(lens, n_src)
+    rowptr = np.zeros(n_tgt + 1, np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    col = np.empty(int(rowptr[-1]), np.int32)
+    for i in range(n_tgt):
+        if lens[i]:
+            col[rowptr[i]:rowptr[i + 1]] = np.sort(rng.choice(n_src, size=lens[i], replace=False))
+    val = rng.standard_normal(col.size) * 1e-3
+    return rowptr, col, val
+
+
+def cloud_problem(n_src: int, n_tgt: int, ndens: int = 1, seed: int = SEED_BASE + 100,
+                  shared: int = 0, clustered: bool = True, csr_per_row: int = 32,
+                  name: str | None = None) -> Problem:
+    """Seeded ragged point cloud: a mix of uniform points and Gaussian clusters in
+    [-1, 1]^2, positive weights, Gaussian-mixture densities. The first `shared`
+    targets coincide exactly with sources (the node-target case)."""
+    rng = np.random.default_rng(seed)
+
+    def pts(n):
+        if not clustered:
+            return rng.uniform(-1.0, 1.0, size=(n, 2))
+        k = n // 2
+        centres = rng.uniform(-0.7, 0.7, size=(5, 2))
+        lab = rng.integers(0, 5, size=n - k)
+        cl = centres[lab] + 0.03 * rng.standard_normal((n - k, 2))
+        return np.clip(np.vstack([rng.uniform(-1.0, 1.0, size=(k, 2)), cl]), -0.999, 0.999)
+
+    src = pts(n_src)
+    tgt = pts(n_tgt)
+    shared = min(shared, n_src, n_tgt)
+    if shared:
+        tgt[:shared] = src[rng.choice(n_src, size=shared, replace=False)]
+    w = rng.uniform(0.5, 1.5, size=n_src) * 4.0 / n_src
+    f = np.empty((ndens, n_src))
+    for d in range(ndens):
+        c = rng.uniform(-0.8, 0.8, size=(3, 2))
+        a = rng.standard_normal(3)
+        s = rng.uniform(0.05, 0.4, size=3)
+        f[d] = sum(a[m] * np.exp(-((src[:, 0] - c[m, 0]) ** 2 + (src[:, 1] - c[m, 1]) ** 2) / s[m] ** 2)
+                   for m in range(3)) + 0.1
+    mat = random_csr(n_tgt, n_src, csr_per_row, seed + 1) if csr_per_row > 0 else None
+    return Problem(name=name or f"cloud{n_src}x{n_tgt}", src_xy=np.ascontiguousarray(src), w=w,
+                   tgt_xy=np.ascontiguousarray(tgt), f=f, csr=mat)
+
+
+def normaliser(problem: Problem) -> np.ndarray:
+    """sum_j |w_j f_j^d| per density: the scale of the relative l-infinity error."""
+    return np.abs(problem.w[None, :] * problem.f).sum(axis=1)
