@@ -1,0 +1,214 @@
+/*
+ * vp.h — C ABI of libvp, the GB300 (sm_103a) evaluator of the FMM-accelerated
+ * volume potential with sparse singular/near-singular corrections of
+ * Anderson, Zhu and Veerapaneni, "A fast, high-order scheme for evaluating
+ * volume potentials on complex 2D geometries via area-to-line integral
+ * conversion and domain mappings" (arXiv 2203.05933).
+ *
+ * What one evaluation computes, for every target t_i and density d:
+ *
+ *   out[d][i] = sum_{j : r_j != t_i} w_j f[d][j] G(r_j, t_i)  +  sum_k Pi_ik f[d][k]
+ *
+ *   G(r, r0) = -(1/2pi) log|r - r0|                       (Sec. 2.1)
+ *   first sum: the target-independent smooth quadrature rule over all cells,
+ *              Jacobians folded into the weights w_j       (Eq. Tk_smooth_quad
+ *              and the remark after it; Eq. vio_rokh_quad_rule; Sec. 4.2)
+ *   second sum: the sparse correction matrix Pi that collects the per-cell
+ *              maps Pi_k(r0), "accurate minus smooth"      (Sec. 4, paragraph
+ *              after Eq. nsrcs)
+ *
+ * The first sum is evaluated by a fast multipole method (the paper's "point
+ * FMM", Sec. 1 synopsis and Sec. 4); the second by a CSR sparse product. A
+ * source/target pair with bitwise equal coordinates contributes no smooth term.
+ *
+ * Conventions shared by every entry point
+ *   - Points are interleaved float64 pairs: xy[2*i] = x_i, xy[2*i+1] = y_i.
+ *   - Densities are row-major float64 [ndens][ld] with ld >= n (leading
+ *     dimension in elements); results likewise.
+ *   - The correction matrix is CSR with rows = targets, columns = sources:
+ *     rowptr int64 [n_tgt+1] (rowptr[0] = 0, non-decreasing), col int32 [nnz]
+ *     in [0, n_src), val float64 [nnz]. Column order inside a row is free.
+ *   - "device" pointers are CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary or pinned host memory.
+ *   - The caller keeps ownership of every pointer it passes. A plan copies what
+ *     it needs (in tree order) into memory it owns and frees in
+ *     vp_plan_destroy.
+ *   - stream is a cudaStream_t cast to void* (NULL = legacy default stream).
+ *     vp_eval and vp_eval_adjoint only enqueue work on it and never synchronize
+ *     the device; vp_plan_create and the *_host entry points synchronize it.
+ *   - Every entry point returns a vp_status. No exception crosses the ABI. On
+ *     error the output buffers hold unspecified values and the plan stays
+ *     usable unless the status is VP_ERR_CUDA (sticky CUDA errors).
+ *   - Arithmetic is IEEE float64 throughout.
+ */
+#ifndef VP_H
+#define VP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VP_OK = 0,
+    VP_ERR_ARG = 1,         /* null pointer, negative size, malformed CSR, non-finite input,
+                               point outside a caller-given root box, ld < n            */
+    VP_ERR_CUDA = 2,        /* a CUDA runtime call failed (message: vp_last_error)        */
+    VP_ERR_OOM = 3,         /* device or host allocation failed                           */
+    VP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                         */
+    VP_ERR_UNSUPPORTED = 5, /* option outside the compiled set (e.g. p_fmm not built)     */
+    VP_ERR_STATE = 6        /* plan used after destroy, or on another device              */
+} vp_status;
+
+typedef struct vp_plan_s* vp_plan;
+
+/* Plan options. Zero-initialise and set what you need; zeros pick defaults. */
+typedef struct {
+    int32_t p_fmm;      /* expansion order P: coefficients 0..P; one of 16, 24, 30 (0 -> 30) */
+    int32_t leaf;       /* split a box while it holds more than `leaf` sources or targets
+                           (0 -> 64; 1..4096)                                                */
+    int32_t max_level;  /* deepest tree level (0 -> 24; at most 27)                          */
+    int32_t max_dens;   /* densities processed per pass; workspace is sized for it (0 -> 1)  */
+    int32_t flags;      /* VP_FLAG_* bits                                                    */
+    int32_t reserved;
+    double root[3];     /* enclosing square (x0, y0, side); side <= 0 -> smallest square
+                           around all points. Every point must satisfy
+                           x0 <= x < x0 + side and y0 <= y < y0 + side.                      */
+} vp_options;
+
+/* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
+#define VP_FLAG_TIMING 1u
+
+/*
+ * vp_plan_create — "vp_plan(nodes, weights, targets, corr_csr)".
+ * Builds the adaptive quadtree over sources and targets (Morton order, leaves of
+ * at most opt->leaf points, interaction lists U/V/W/X of the adaptive FMM) and
+ * copies geometry, weights and the correction matrix, permuted into tree
+ * order, into plan-owned device memory. Geometry is static after this call
+ * (the paper's setting: static geometry, Sec. 1 "Limitations").
+ *   src_xy [n_src][2], w [n_src]     device; quadrature nodes and weights (w includes J)
+ *   tgt_xy [n_tgt][2]                device; evaluation points (may coincide with nodes)
+ *   corr_rowptr/col/val, nnz         device; Pi in CSR (all NULL with nnz = 0: no correction)
+ *   opt                              host; may be NULL (all defaults)
+ * n_src >= 0, n_tgt >= 0. Synchronizes `stream`. Errors: VP_ERR_ARG, VP_ERR_OOM,
+ * VP_ERR_CUDA, VP_ERR_UNSUPPORTED. *out is NULL on error.
+ */
+vp_status vp_plan_create(vp_plan* out,
+                         int64_t n_src, const double* src_xy, const double* w,
+                         int64_t n_tgt, const double* tgt_xy,
+                         const int64_t* corr_rowptr, const int32_t* corr_col,
+                         const double* corr_val, int64_t nnz,
+                         const vp_options* opt, void* stream);
+
+/*
+ * vp_eval — "vp_eval(plan, f, out)": out[d][i] for d < ndens (formula above).
+ *   f   [ndens][ld_f]   device, ld_f >= n_src, caller (input) order
+ *   out [ndens][ld_out] device, ld_out >= n_tgt, caller (input) order; overwritten
+ * ndens >= 0; densities beyond max_dens are processed in successive passes.
+ * Enqueues on `stream` only; f and out must stay valid until the work completes.
+ * Not reentrant on one plan: calls on different streams with the same plan race
+ * on the plan's workspace.
+ */
+vp_status vp_eval(vp_plan plan, int32_t ndens, const double* f, int64_t ld_f,
+                  double* out, int64_t ld_out, void* stream);
+
+/*
+ * vp_eval_adjoint — transpose of vp_eval and target-position gradient.
+ * For upstream gradients g[d][i] = dL/dout[d][i]:
+ *   grad_f[d][j]  = w_j sum_{i: t_i != r_j} G(r_j, t_i) g[d][i] + sum_i Pi_ij g[d][i]
+ *                   (transposed FMM, charges at the targets, plus Pi^T g)
+ *   grad_tgt[i]   = sum_d g[d][i] sum_{j: r_j != t_i} w_j f[d][j] grad_{t_i} G(r_j, t_i)
+ *                   (Pi held fixed: correction weights are set-up data)
+ *   g        [ndens][ld_g]    device, ld_g >= n_tgt
+ *   grad_f   [ndens][ld_gf]   device or NULL (skip), ld_gf >= n_src; overwritten
+ *   f        [ndens][ld_f]    device; required when grad_tgt != NULL, else may be NULL
+ *   grad_tgt [n_tgt][2]       device or NULL (skip); overwritten
+ * Expansions are recomputed from g (and f) on every call, never stored per
+ * right-hand side. Enqueues on `stream` only.
+ */
+vp_status vp_eval_adjoint(vp_plan plan, int32_t ndens,
+                          const double* g, int64_t ld_g,
+                          double* grad_f, int64_t ld_gf,
+                          const double* f, int64_t ld_f,
+                          double* grad_tgt, void* stream);
+
+/*
+ * vp_eval_host — vp_eval on host buffers: copies f (host, [ndens][n_src] dense)
+ * to plan-owned device staging, evaluates, copies out back (host,
+ * [ndens][n_tgt] dense), and synchronizes `stream` before returning. Pinned host
+ * memory gives asynchronous copies; pageable memory works but is staged by the
+ * driver. The staging buffers grow on demand (VP_ERR_OOM if that fails).
+ */
+vp_status vp_eval_host(vp_plan plan, int32_t ndens, const double* f_host,
+                       double* out_host, void* stream);
+
+/* Plan summary (host struct filled by vp_plan_info). */
+typedef struct {
+    int64_t n_src, n_tgt, nnz;
+    int32_t p_fmm, leaf, max_dens, n_levels;
+    int64_t n_boxes, n_leaves;
+    int64_t n_u_pairs;      /* sum over target leaves of |U| (leaf-leaf P2P blocks)     */
+    int64_t n_v_pairs;      /* sum over boxes of |V| (M2L translations)                 */
+    int64_t n_w_pairs;      /* sum over leaves of |W| (multipole-to-target blocks)      */
+    int64_t n_x_pairs;      /* sum over boxes of |X| (source-to-local blocks)           */
+    int64_t p2p_pairs;      /* source-target pairs summed directly (one density)        */
+    double root[3];
+} vp_plan_stats;
+
+vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);
+
+/*
+ * Per-phase device times of the last vp_eval on this plan, in milliseconds,
+ * measured with CUDA events recorded on the evaluation stream (only with
+ * VP_FLAG_TIMING). Synchronizes on the last recorded event. names/ms are host
+ * arrays of capacity `cap`; *n receives the number of phases.
+ */
+vp_status vp_plan_phase_times(vp_plan plan, int32_t cap, const char** names,
+                              double* ms, int32_t* n);
+
+vp_status vp_plan_destroy(vp_plan plan);
+
+/* Static description of a status code; never NULL. */
+const char* vp_status_string(int32_t status);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* vp_last_error(void);
+
+/* Library version string, e.g. "libvp 0.1 sm_103a". */
+const char* vp_version(void);
+
+/*
+ * Host-side inspection of the tree and interaction lists (no GPU needed).
+ * vp_tree_build builds exactly the tree vp_plan_create would build for the same
+ * points and options, on the host, from host arrays.
+ * vp_tree_get copies one array out (which = VP_TREE_*); pass dst = NULL to get
+ * the element count in *count first. Arrays:
+ *   VP_TREE_BOX_LEVEL   int32 [n_boxes]
+ *   VP_TREE_BOX_IXY     int32 [n_boxes][2]   integer box coordinates at its level
+ *   VP_TREE_BOX_PARENT  int32 [n_boxes]      -1 for the root
+ *   VP_TREE_BOX_LEAF    int32 [n_boxes]      1 if leaf
+ *   VP_TREE_BOX_SRC     int32 [n_boxes][2]   [begin, end) in sorted source order
+ *   VP_TREE_BOX_TGT     int32 [n_boxes][2]   [begin, end) in sorted target order
+ *   VP_TREE_SRC_PERM    int32 [n_src]        sorted position -> caller index
+ *   VP_TREE_TGT_PERM    int32 [n_tgt]
+ *   VP_TREE_{U,V,W,X}_PTR int32 [n_boxes+1]  CSR offsets of each list
+ *   VP_TREE_{U,V,W,X}_IDX int32 [...]        box indices
+ */
+typedef struct vp_tree_s* vp_tree;
+enum {
+    VP_TREE_BOX_LEVEL = 0, VP_TREE_BOX_IXY, VP_TREE_BOX_PARENT, VP_TREE_BOX_LEAF,
+    VP_TREE_BOX_SRC, VP_TREE_BOX_TGT, VP_TREE_SRC_PERM, VP_TREE_TGT_PERM,
+    VP_TREE_U_PTR, VP_TREE_U_IDX, VP_TREE_V_PTR, VP_TREE_V_IDX,
+    VP_TREE_W_PTR, VP_TREE_W_IDX, VP_TREE_X_PTR, VP_TREE_X_IDX
+};
+vp_status vp_tree_build(vp_tree* out, int64_t n_src, const double* src_xy_host,
+                        int64_t n_tgt, const double* tgt_xy_host, const vp_options* opt);
+vp_status vp_tree_get(vp_tree tree, int32_t which, int32_t* dst, int64_t* count);
+vp_status vp_tree_destroy(vp_tree tree);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VP_H */

@@ -1,0 +1,763 @@
+// C ABI of libvp (declared in include/vp.h): plan construction, evaluation,
+// adjoint, inspection. Host code only; kernels live in vp_fmm.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vp_internal.h"
+
+using namespace vp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+vp_status fail(vp_status st, const std::string& msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+vp_status cuda_fail(cudaError_t e, const char* where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA;
+}
+
+#define VP_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+uint64_t binom_u64(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;  // exact at every step
+    return r;
+}
+
+// Operator tables for order P, laid out as in DevTables (all offsets multiples of 2 doubles).
+std::vector<double> make_tables(int P, size_t off[7])
+{
+    const int P1 = P + 1;
+    std::vector<double> v;
+    auto reserve_even = [&]() {
+        if (v.size() & 1) v.push_back(0.0);
+    };
+    off[0] = v.size();  // H
+    for (int l = 0; l <= P; ++l)
+        for (int k = 0; k <= P; ++k) v.push_back(k >= 1 ? (double)binom_u64(l + k - 1, k - 1) : 0.0);
+    off[1] = v.size();  // Bm
+    for (int l = 0; l <= P; ++l)
+        for (int k = 0; k <= P; ++k)
+            v.push_back((k >= 1 && k <= l) ? std::ldexp((double)binom_u64(l - 1, k - 1), -k) : 0.0);
+    off[2] = v.size();  // Bl
+    for (int l = 0; l <= P; ++l)
+        for (int k = 0; k <= P; ++k) v.push_back(k >= l ? std::ldexp((double)binom_u64(k, l), -l) : 0.0);
+    reserve_even();
+    off[3] = v.size();  // tpow [49][P1] complex
+    std::vector<double> mt;
+    for (int oy = -3; oy <= 3; ++oy)
+        for (int ox = -3; ox <= 3; ++ox) {
+            const bool far = std::max(std::abs(ox), std::abs(oy)) >= 2;
+            const long double den = 2.0L * (long double)(ox * ox + oy * oy);
+            const long double tr = far ? (long double)ox / den : 0.0L;
+            const long double ti = far ? -(long double)oy / den : 0.0L;
+            long double pr = 1.0L, pi = 0.0L;  // t^l
+            long double mr = 1.0L, mi = 0.0L;  // (-t)^l
+            for (int l = 0; l <= P; ++l) {
+                v.push_back(far ? (double)pr : 0.0);
+                v.push_back(far ? (double)pi : 0.0);
+                mt.push_back(far ? (double)mr : 0.0);
+                mt.push_back(far ? (double)mi : 0.0);
+                const long double nr = pr * tr - pi * ti, ni = pr * ti + pi * tr;
+                pr = nr;
+                pi = ni;
+                const long double qr = -(mr * tr - mi * ti), qi = -(mr * ti + mi * tr);
+                mr = qr;
+                mi = qi;
+            }
+        }
+    off[4] = v.size();  // mtpow
+    v.insert(v.end(), mt.begin(), mt.end());
+    off[5] = v.size();  // log2o [49]
+    for (int oy = -3; oy <= 3; ++oy)
+        for (int ox = -3; ox <= 3; ++ox) {
+            const int r2 = ox * ox + oy * oy;
+            v.push_back(r2 > 0 ? std::log(2.0) + 0.5 * std::log((double)r2) : 0.0);
+        }
+    reserve_even();
+    off[6] = v.size();  // zpow [4][P1] complex
+    for (int c = 0; c < 4; ++c) {
+        const double zr = (c & 1) ? 0.5 : -0.5, zi = (c & 2) ? 0.5 : -0.5;
+        double pr = 1.0, pi = 0.0;
+        for (int m = 0; m <= P; ++m) {
+            v.push_back(pr);
+            v.push_back(pi);
+            const double nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;  // exact: dyadic values
+            pr = nr;
+            pi = ni;
+        }
+    }
+    (void)P1;
+    return v;
+}
+
+bool finite_all(const std::vector<double>& a)
+{
+    for (double x : a)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int PhaseTimer::begin(const char* name)
+{
+    if (!on) return -1;
+    int ph = -1;
+    for (size_t i = 0; i < names.size(); ++i)
+        if (names[i] == name) ph = (int)i;
+    if (ph < 0) {
+        names.emplace_back(name);
+        ph = (int)names.size() - 1;
+    }
+    if ((size_t)(2 * used + 2) > pool.size()) {
+        for (int k = 0; k < 16; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            pool.push_back(e);
+        }
+    }
+    const int id = used++;
+    if ((size_t)id >= phase_of.size()) phase_of.resize(id + 1);
+    phase_of[id] = ph;
+    cudaEventRecord(pool[2 * id], stream);
+    return id;
+}
+
+void PhaseTimer::end(int id)
+{
+    if (id < 0) return;
+    cudaEventRecord(pool[2 * id + 1], stream);
+}
+
+struct vp_plan_s {
+    int device = 0;
+    int P = 30;
+    int leaf = 64;
+    int max_dens = 1;
+    int nd_cap = 1;
+    uint32_t flags = 0;
+    int64_t n_src = 0, n_tgt = 0, nnz = 0;
+    Tree host;
+    DevTree dt;
+    DevTables tab;
+    std::vector<void*> allocs;
+    // points and weights in tree order
+    double2* src_xy = nullptr;
+    double2* tgt_xy = nullptr;
+    double* w_sorted = nullptr;
+    int32_t *src_perm = nullptr, *tgt_perm = nullptr, *src_inv = nullptr, *tgt_inv = nullptr;
+    int32_t *box_src = nullptr, *box_tgt = nullptr;
+    // correction in caller order, and its transpose
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    int64_t* cptr = nullptr;
+    int32_t* crow = nullptr;
+    double* cval = nullptr;
+    Workspace ws;
+    PhaseTimer timer;
+    // staging for vp_eval_host
+    double* stage = nullptr;
+    size_t stage_cap = 0;
+    int64_t p2p_pairs = 0;
+    bool alive = true;
+
+    template <typename T>
+    cudaError_t alloc(T** p, size_t n)
+    {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        *p = (T*)q;
+        return cudaSuccess;
+    }
+    template <typename T>
+    cudaError_t upload(T** p, const std::vector<T>& h, cudaStream_t s)
+    {
+        cudaError_t e = alloc(p, h.size());
+        if (e != cudaSuccess) return e;
+        if (h.empty()) return cudaSuccess;
+        return cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+    ~vp_plan_s()
+    {
+        for (void* p : allocs) cudaFree(p);
+        if (stage) cudaFree(stage);
+        for (auto e : timer.pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+vp_status check_plan(vp_plan p)
+{
+    if (!p || !p->alive) return fail(VP_ERR_STATE, "invalid plan");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device)
+        return fail(VP_ERR_STATE, "plan used on a different device than it was created on");
+    return VP_OK;
+}
+
+int chunk_for(int remaining, int cap)
+{
+    int nd = 1;
+    while (nd * 2 <= remaining && nd * 2 <= cap) nd *= 2;
+    return nd;
+}
+
+PassGeom forward_geom(vp_plan p)
+{
+    PassGeom g;
+    g.cxy = p->src_xy;
+    g.crng = p->box_src;
+    g.n_charge = (int32_t)p->n_src;
+    g.exy = p->tgt_xy;
+    g.erng = p->box_tgt;
+    g.n_eval = (int32_t)p->n_tgt;
+    return g;
+}
+
+PassGeom adjoint_geom(vp_plan p)
+{
+    PassGeom g;
+    g.cxy = p->tgt_xy;
+    g.crng = p->box_tgt;
+    g.n_charge = (int32_t)p->n_tgt;
+    g.exy = p->src_xy;
+    g.erng = p->box_src;
+    g.n_eval = (int32_t)p->n_src;
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vp_status_string(int32_t status)
+{
+    switch (status) {
+        case VP_OK: return "ok";
+        case VP_ERR_ARG: return "invalid argument";
+        case VP_ERR_CUDA: return "CUDA error";
+        case VP_ERR_OOM: return "out of memory";
+        case VP_ERR_TIMEOUT: return "device wait timed out";
+        case VP_ERR_UNSUPPORTED: return "unsupported option";
+        case VP_ERR_STATE: return "invalid plan state";
+        default: return "unknown status";
+    }
+}
+
+const char* vp_last_error(void) { return g_last_error.c_str(); }
+
+const char* vp_version(void) { return "libvp 0.1 sm_103a fp64"; }
+
+vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, const double* w, int64_t n_tgt,
+                         const double* tgt_xy, const int64_t* corr_rowptr, const int32_t* corr_col,
+                         const double* corr_val, int64_t nnz, const vp_options* opt_in, void* stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(VP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_src < 0 || n_tgt < 0 || nnz < 0) return fail(VP_ERR_ARG, "negative size");
+    if (n_src > (1LL << 30) || n_tgt > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 points");
+    if ((n_src > 0 && (!src_xy || !w)) || (n_tgt > 0 && !tgt_xy)) return fail(VP_ERR_ARG, "NULL point array");
+    const bool has_corr = corr_rowptr != nullptr;
+    if (has_corr && nnz > 0 && (!corr_col || !corr_val)) return fail(VP_ERR_ARG, "NULL CSR array");
+    if (!has_corr && nnz != 0) return fail(VP_ERR_ARG, "nnz > 0 without a CSR");
+    vp_options opt;
+    std::memset(&opt, 0, sizeof(opt));
+    if (opt_in) opt = *opt_in;
+    const int P = opt.p_fmm == 0 ? 30 : opt.p_fmm;
+    if (!p_supported(P)) return fail(VP_ERR_UNSUPPORTED, "p_fmm must be 16, 24 or 30");
+    const int leaf = opt.leaf == 0 ? 64 : opt.leaf;
+    const int max_level = opt.max_level == 0 ? 24 : opt.max_level;
+    const int max_dens = opt.max_dens <= 0 ? 1 : opt.max_dens;
+    if (leaf < 1 || leaf > 4096) return fail(VP_ERR_ARG, "leaf outside [1, 4096]");
+    if (max_level < 1 || max_level >= kCoordBits) return fail(VP_ERR_ARG, "max_level outside [1, 27]");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // pull geometry and correction to the host (plan time only)
+    std::vector<double> hs((size_t)n_src * 2), hw((size_t)n_src), ht((size_t)n_tgt * 2);
+    std::vector<int64_t> hrow;
+    std::vector<int32_t> hcol;
+    std::vector<double> hval;
+    if (n_src) {
+        VP_CUDA(cudaMemcpyAsync(hs.data(), src_xy, hs.size() * sizeof(double), cudaMemcpyDefault, s));
+        VP_CUDA(cudaMemcpyAsync(hw.data(), w, hw.size() * sizeof(double), cudaMemcpyDefault, s));
+    }
+    if (n_tgt) VP_CUDA(cudaMemcpyAsync(ht.data(), tgt_xy, ht.size() * sizeof(double), cudaMemcpyDefault, s));
+    if (has_corr) {
+        hrow.resize((size_t)n_tgt + 1);
+        VP_CUDA(cudaMemcpyAsync(hrow.data(), corr_rowptr, hrow.size() * sizeof(int64_t), cudaMemcpyDefault, s));
+        hcol.resize((size_t)nnz);
+        hval.resize((size_t)nnz);
+        if (nnz) {
+            VP_CUDA(cudaMemcpyAsync(hcol.data(), corr_col, hcol.size() * sizeof(int32_t), cudaMemcpyDefault, s));
+            VP_CUDA(cudaMemcpyAsync(hval.data(), corr_val, hval.size() * sizeof(double), cudaMemcpyDefault, s));
+        }
+    }
+    VP_CUDA(cudaStreamSynchronize(s));
+    if (!finite_all(hw)) return fail(VP_ERR_ARG, "non-finite weight");
+    if (has_corr) {
+        if (hrow[0] != 0 || hrow[(size_t)n_tgt] != nnz) return fail(VP_ERR_ARG, "CSR rowptr does not span [0, nnz]");
+        for (int64_t i = 0; i < n_tgt; ++i)
+            if (hrow[(size_t)i + 1] < hrow[(size_t)i]) return fail(VP_ERR_ARG, "CSR rowptr not monotone");
+        for (int64_t k = 0; k < nnz; ++k)
+            if (hcol[(size_t)k] < 0 || hcol[(size_t)k] >= n_src) return fail(VP_ERR_ARG, "CSR column out of range");
+        if (!finite_all(hval)) return fail(VP_ERR_ARG, "non-finite CSR value");
+    }
+
+    vp_plan p = new (std::nothrow) vp_plan_s();
+    if (!p) return fail(VP_ERR_OOM, "host allocation");
+    cudaGetDevice(&p->device);
+    p->P = P;
+    p->leaf = leaf;
+    p->max_dens = max_dens;
+    p->nd_cap = chunk_for(max_dens, 8);
+    p->flags = (uint32_t)opt.flags;
+    p->n_src = n_src;
+    p->n_tgt = n_tgt;
+    p->nnz = has_corr ? nnz : 0;
+    p->timer.on = (p->flags & VP_FLAG_TIMING) != 0;
+
+    TreeOptions to;
+    to.leaf = leaf;
+    to.max_level = max_level;
+    to.root[0] = opt.root[0];
+    to.root[1] = opt.root[1];
+    to.root[2] = opt.root[2];
+    std::string err = build_tree(n_src, hs.data(), n_tgt, ht.data(), to, p->host);
+    if (!err.empty()) {
+        delete p;
+        return fail(VP_ERR_ARG, err);
+    }
+    const Tree& T = p->host;
+    const int32_t nb = (int32_t)T.n_boxes();
+
+    // host arrays in tree order
+    std::vector<double> sxy((size_t)n_src * 2), txy((size_t)n_tgt * 2), ws((size_t)n_src);
+    std::vector<int32_t> sinv((size_t)n_src), tinv((size_t)n_tgt);
+    for (int64_t i = 0; i < n_src; ++i) {
+        const int32_t c = T.src_perm[(size_t)i];
+        sxy[2 * i] = hs[2 * (size_t)c];
+        sxy[2 * i + 1] = hs[2 * (size_t)c + 1];
+        ws[(size_t)i] = hw[(size_t)c];
+        sinv[(size_t)c] = (int32_t)i;
+    }
+    for (int64_t i = 0; i < n_tgt; ++i) {
+        const int32_t c = T.tgt_perm[(size_t)i];
+        txy[2 * i] = ht[2 * (size_t)c];
+        txy[2 * i + 1] = ht[2 * (size_t)c + 1];
+        tinv[(size_t)c] = (int32_t)i;
+    }
+    std::vector<double> center((size_t)nb * 2), radius((size_t)nb), logr((size_t)nb);
+    std::vector<int32_t> ixy((size_t)nb * 2), brs((size_t)nb * 2), brt((size_t)nb * 2), leaves;
+    for (int32_t b = 0; b < nb; ++b) {
+        center[2 * (size_t)b] = T.box_cx(b);
+        center[2 * (size_t)b + 1] = T.box_cy(b);
+        radius[(size_t)b] = 0.5 * T.box_side(b);
+        logr[(size_t)b] = std::log(radius[(size_t)b]);
+        ixy[2 * (size_t)b] = T.ix[(size_t)b];
+        ixy[2 * (size_t)b + 1] = T.iy[(size_t)b];
+        brs[2 * (size_t)b] = T.src_begin[(size_t)b];
+        brs[2 * (size_t)b + 1] = T.src_end[(size_t)b];
+        brt[2 * (size_t)b] = T.tgt_begin[(size_t)b];
+        brt[2 * (size_t)b + 1] = T.tgt_end[(size_t)b];
+        if (T.is_leaf[(size_t)b]) leaves.push_back(b);
+    }
+    int64_t pairs = 0;
+    for (int32_t b : leaves)
+        for (int32_t e = T.u_ptr[(size_t)b]; e < T.u_ptr[(size_t)b + 1]; ++e) {
+            const int32_t a = T.u_idx[(size_t)e];
+            pairs += (int64_t)(T.tgt_end[(size_t)b] - T.tgt_begin[(size_t)b]) * (T.src_end[(size_t)a] - T.src_begin[(size_t)a]);
+        }
+    p->p2p_pairs = pairs;
+
+    // transposed correction (columns = sources), for the adjoint
+    std::vector<int64_t> hcptr;
+    std::vector<int32_t> hcrow;
+    std::vector<double> hcval;
+    if (has_corr) {
+        hcptr.assign((size_t)n_src + 1, 0);
+        for (int64_t k = 0; k < nnz; ++k) hcptr[(size_t)hcol[(size_t)k] + 1]++;
+        for (int64_t j = 0; j < n_src; ++j) hcptr[(size_t)j + 1] += hcptr[(size_t)j];
+        std::vector<int64_t> fill(hcptr.begin(), hcptr.end() - 1);
+        hcrow.resize((size_t)nnz);
+        hcval.resize((size_t)nnz);
+        for (int64_t i = 0; i < n_tgt; ++i)
+            for (int64_t k = hrow[(size_t)i]; k < hrow[(size_t)i + 1]; ++k) {
+                const int64_t pos = fill[(size_t)hcol[(size_t)k]]++;
+                hcrow[(size_t)pos] = (int32_t)i;
+                hcval[(size_t)pos] = hval[(size_t)k];
+            }
+    }
+    size_t off[7];
+    std::vector<double> tables = make_tables(P, off);
+
+    cudaError_t e = cudaSuccess;
+    auto up = [&](auto** dst, const auto& h) {
+        if (e == cudaSuccess) e = p->upload(dst, h, s);
+    };
+    double* d_xy_s = nullptr;
+    double* d_xy_t = nullptr;
+    up(&d_xy_s, sxy);
+    up(&d_xy_t, txy);
+    p->src_xy = (double2*)d_xy_s;
+    p->tgt_xy = (double2*)d_xy_t;
+    up(&p->w_sorted, ws);
+    up(&p->src_perm, T.src_perm);
+    up(&p->tgt_perm, T.tgt_perm);
+    up(&p->src_inv, sinv);
+    up(&p->tgt_inv, tinv);
+    up(&p->box_src, brs);
+    up(&p->box_tgt, brt);
+    double *d_center = nullptr, *d_radius = nullptr, *d_logr = nullptr, *d_tab = nullptr;
+    int32_t *d_ixy = nullptr, *d_parent = nullptr, *d_child = nullptr, *d_leaf = nullptr, *d_leaves = nullptr;
+    int32_t *d_up, *d_ui, *d_vp, *d_vi, *d_wp, *d_wi, *d_xp, *d_xi;
+    up(&d_center, center);
+    up(&d_radius, radius);
+    up(&d_logr, logr);
+    up(&d_ixy, ixy);
+    up(&d_parent, T.parent);
+    up(&d_child, T.child);
+    up(&d_leaf, T.is_leaf);
+    up(&d_leaves, leaves);
+    up(&d_up, T.u_ptr);
+    up(&d_ui, T.u_idx);
+    up(&d_vp, T.v_ptr);
+    up(&d_vi, T.v_idx);
+    up(&d_wp, T.w_ptr);
+    up(&d_wi, T.w_idx);
+    up(&d_xp, T.x_ptr);
+    up(&d_xi, T.x_idx);
+    up(&d_tab, tables);
+    if (has_corr) {
+        up(&p->rowptr, hrow);
+        up(&p->col, hcol);
+        up(&p->val, hval);
+        up(&p->cptr, hcptr);
+        up(&p->crow, hcrow);
+        up(&p->cval, hcval);
+    }
+    const int P1 = P + 1;
+    const int64_t npts = std::max<int64_t>(std::max<int64_t>(n_src, n_tgt), 1);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.q, (size_t)npts * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.psi, (size_t)npts * 2 * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.M, (size_t)nb * P1 * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "vp_plan_create upload");
+    }
+    p->ws.nd_cap = p->nd_cap;
+
+    DevTree& dt = p->dt;
+    dt.nbox = nb;
+    dt.nlevels = T.n_levels;
+    dt.nleaf = (int32_t)leaves.size();
+    dt.center = (const double2*)d_center;
+    dt.radius = d_radius;
+    dt.log_radius = d_logr;
+    dt.ixy = d_ixy;
+    dt.parent = d_parent;
+    dt.child = d_child;
+    dt.is_leaf = d_leaf;
+    dt.src_rng = p->box_src;
+    dt.tgt_rng = p->box_tgt;
+    dt.leaves = d_leaves;
+    dt.u_ptr = d_up;
+    dt.u_idx = d_ui;
+    dt.v_ptr = d_vp;
+    dt.v_idx = d_vi;
+    dt.w_ptr = d_wp;
+    dt.w_idx = d_wi;
+    dt.x_ptr = d_xp;
+    dt.x_idx = d_xi;
+    dt.level_start = T.level_start;
+    DevTables& tb = p->tab;
+    tb.H = d_tab + off[0];
+    tb.Bm = d_tab + off[1];
+    tb.Bl = d_tab + off[2];
+    tb.tpow = (const double2*)(d_tab + off[3]);
+    tb.mtpow = (const double2*)(d_tab + off[4]);
+    tb.log2o = d_tab + off[5];
+    tb.zpow = (const double2*)(d_tab + off[6]);
+    *out = p;
+    return VP_OK;
+}
+
+vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, double* out, int64_t ld_out,
+                  void* stream)
+{
+    vp_status st = check_plan(p);
+    if (st != VP_OK) return st;
+    if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
+    if (ndens == 0 || p->n_tgt == 0) return VP_OK;
+    if (!out || (p->n_src > 0 && !f)) return fail(VP_ERR_ARG, "NULL density or output");
+    if (ld_f < p->n_src || ld_out < p->n_tgt) return fail(VP_ERR_ARG, "leading dimension too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->timer.stream = s;
+    p->timer.used = 0;
+    PassGeom g = forward_geom(p);
+    for (int d0 = 0; d0 < ndens;) {
+        const int nd = chunk_for(ndens - d0, p->nd_cap);
+        const double* fc = f + (int64_t)d0 * ld_f;
+        int id = p->timer.begin("charges");
+        VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, s));
+        p->timer.end(id);
+        VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, p->timer.on ? &p->timer : nullptr, s));
+        id = p->timer.begin("out");
+        VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc, ld_f,
+                                   out + (int64_t)d0 * ld_out, ld_out, s));
+        p->timer.end(id);
+        d0 += nd;
+    }
+    return VP_OK;
+}
+
+vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_g, double* grad_f, int64_t ld_gf,
+                          const double* f, int64_t ld_f, double* grad_tgt, void* stream)
+{
+    vp_status st = check_plan(p);
+    if (st != VP_OK) return st;
+    if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (grad_tgt && p->n_tgt > 0) {
+        if (ndens == 0) {
+            VP_CUDA(cudaMemsetAsync(grad_tgt, 0, sizeof(double) * 2 * p->n_tgt, s));
+        } else if (!g || (p->n_src > 0 && !f) || ld_g < p->n_tgt || ld_f < p->n_src) {
+            return fail(VP_ERR_ARG, "target gradient needs g and f with valid leading dimensions");
+        }
+    }
+    if (grad_f && p->n_src > 0) {
+        if (ndens == 0) return VP_OK;
+        if ((p->n_tgt > 0 && !g) || ld_g < p->n_tgt || ld_gf < p->n_src)
+            return fail(VP_ERR_ARG, "grad_f needs g with valid leading dimensions");
+    }
+    if (ndens == 0) return VP_OK;
+    p->timer.stream = s;
+    p->timer.used = 0;
+    if (grad_f && p->n_src > 0) {
+        PassGeom gg = adjoint_geom(p);
+        for (int d0 = 0; d0 < ndens;) {
+            const int nd = chunk_for(ndens - d0, p->nd_cap);
+            const double* gc = g + (int64_t)d0 * ld_g;
+            VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, s));
+            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, nullptr, s));
+            VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr, p->crow,
+                                       p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
+            d0 += nd;
+        }
+    }
+    if (grad_tgt && p->n_tgt > 0) {
+        PassGeom gf = forward_geom(p);
+        for (int d0 = 0; d0 < ndens;) {
+            const int nd = chunk_for(ndens - d0, p->nd_cap);
+            const double* fc = f + (int64_t)d0 * ld_f;
+            VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, s));
+            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, nullptr, s));
+            VP_CUDA(launch_grad_out(nd, d0 > 0, (int32_t)p->n_tgt, p->tgt_perm, p->ws.psi, g + (int64_t)d0 * ld_g,
+                                    ld_g, grad_tgt, s));
+            d0 += nd;
+        }
+    }
+    return VP_OK;
+}
+
+vp_status vp_eval_host(vp_plan p, int32_t ndens, const double* f_host, double* out_host, void* stream)
+{
+    vp_status st = check_plan(p);
+    if (st != VP_OK) return st;
+    if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
+    if (ndens == 0) return VP_OK;
+    if ((p->n_src > 0 && !f_host) || (p->n_tgt > 0 && !out_host)) return fail(VP_ERR_ARG, "NULL host buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nf = (size_t)ndens * (size_t)p->n_src, no = (size_t)ndens * (size_t)p->n_tgt;
+    if (nf + no > p->stage_cap) {
+        if (p->stage) cudaFree(p->stage);
+        p->stage = nullptr;
+        p->stage_cap = 0;
+        void* q = nullptr;
+        VP_CUDA(cudaMalloc(&q, (nf + no) * sizeof(double)));
+        p->stage = (double*)q;
+        p->stage_cap = nf + no;
+    }
+    double* df = p->stage;
+    double* dout = p->stage + nf;
+    if (nf) VP_CUDA(cudaMemcpyAsync(df, f_host, nf * sizeof(double), cudaMemcpyHostToDevice, s));
+    st = vp_eval(p, ndens, df, p->n_src, dout, p->n_tgt, stream);
+    if (st != VP_OK) return st;
+    if (no) VP_CUDA(cudaMemcpyAsync(out_host, dout, no * sizeof(double), cudaMemcpyDeviceToHost, s));
+    VP_CUDA(cudaStreamSynchronize(s));
+    return VP_OK;
+}
+
+vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
+{
+    if (!p || !p->alive) return fail(VP_ERR_STATE, "invalid plan");
+    if (!o) return fail(VP_ERR_ARG, "NULL stats");
+    std::memset(o, 0, sizeof(*o));
+    const Tree& T = p->host;
+    o->n_src = p->n_src;
+    o->n_tgt = p->n_tgt;
+    o->nnz = p->nnz;
+    o->p_fmm = p->P;
+    o->leaf = p->leaf;
+    o->max_dens = p->max_dens;
+    o->n_levels = T.n_levels;
+    o->n_boxes = T.n_boxes();
+    int64_t nl = 0, nu = 0, nw = 0;
+    for (int64_t b = 0; b < T.n_boxes(); ++b)
+        if (T.is_leaf[(size_t)b]) {
+            ++nl;
+            nu += T.u_ptr[(size_t)b + 1] - T.u_ptr[(size_t)b];
+            nw += T.w_ptr[(size_t)b + 1] - T.w_ptr[(size_t)b];
+        }
+    o->n_leaves = nl;
+    o->n_u_pairs = nu;
+    o->n_v_pairs = (int64_t)T.v_idx.size();
+    o->n_w_pairs = nw;
+    o->n_x_pairs = (int64_t)T.x_idx.size();
+    o->p2p_pairs = p->p2p_pairs;
+    o->root[0] = T.x0;
+    o->root[1] = T.y0;
+    o->root[2] = T.side;
+    return VP_OK;
+}
+
+vp_status vp_plan_phase_times(vp_plan p, int32_t cap, const char** names, double* ms, int32_t* n)
+{
+    if (!p || !p->alive) return fail(VP_ERR_STATE, "invalid plan");
+    if (!n) return fail(VP_ERR_ARG, "NULL count");
+    const PhaseTimer& t = p->timer;
+    *n = (int32_t)t.names.size();
+    if (!t.on) {
+        *n = 0;
+        return VP_OK;
+    }
+    std::vector<double> sum(t.names.size(), 0.0);
+    for (int i = 0; i < t.used; ++i) {
+        VP_CUDA(cudaEventSynchronize(t.pool[2 * i + 1]));
+        float x = 0.f;
+        VP_CUDA(cudaEventElapsedTime(&x, t.pool[2 * i], t.pool[2 * i + 1]));
+        sum[(size_t)t.phase_of[(size_t)i]] += x;
+    }
+    for (int32_t i = 0; i < *n && i < cap; ++i) {
+        if (names) names[i] = t.names[(size_t)i].c_str();
+        if (ms) ms[i] = sum[(size_t)i];
+    }
+    return VP_OK;
+}
+
+vp_status vp_plan_destroy(vp_plan p)
+{
+    if (!p) return VP_OK;
+    if (!p->alive) return fail(VP_ERR_STATE, "plan destroyed twice");
+    p->alive = false;
+    delete p;
+    return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+struct vp_tree_s {
+    Tree t;
+};
+
+vp_status vp_tree_build(vp_tree* out, int64_t n_src, const double* src_xy, int64_t n_tgt, const double* tgt_xy,
+                        const vp_options* opt_in)
+{
+    if (!out) return fail(VP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_src < 0 || n_tgt < 0) return fail(VP_ERR_ARG, "negative size");
+    if ((n_src > 0 && !src_xy) || (n_tgt > 0 && !tgt_xy)) return fail(VP_ERR_ARG, "NULL point array");
+    vp_options opt;
+    std::memset(&opt, 0, sizeof(opt));
+    if (opt_in) opt = *opt_in;
+    TreeOptions to;
+    to.leaf = opt.leaf == 0 ? 64 : opt.leaf;
+    to.max_level = opt.max_level == 0 ? 24 : opt.max_level;
+    to.root[0] = opt.root[0];
+    to.root[1] = opt.root[1];
+    to.root[2] = opt.root[2];
+    vp_tree t = new (std::nothrow) vp_tree_s();
+    if (!t) return fail(VP_ERR_OOM, "host allocation");
+    std::string err = build_tree(n_src, src_xy, n_tgt, tgt_xy, to, t->t);
+    if (!err.empty()) {
+        delete t;
+        return fail(VP_ERR_ARG, err);
+    }
+    *out = t;
+    return VP_OK;
+}
+
+vp_status vp_tree_get(vp_tree tree, int32_t which, int32_t* dst, int64_t* count)
+{
+    if (!tree || !count) return fail(VP_ERR_ARG, "NULL tree or count");
+    const Tree& T = tree->t;
+    std::vector<int32_t> tmp;
+    const std::vector<int32_t>* src = nullptr;
+    auto pairs = [&](const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+        tmp.resize(a.size() * 2);
+        for (size_t i = 0; i < a.size(); ++i) {
+            tmp[2 * i] = a[i];
+            tmp[2 * i + 1] = b[i];
+        }
+        src = &tmp;
+    };
+    switch (which) {
+        case VP_TREE_BOX_LEVEL: src = &T.level; break;
+        case VP_TREE_BOX_IXY: pairs(T.ix, T.iy); break;
+        case VP_TREE_BOX_PARENT: src = &T.parent; break;
+        case VP_TREE_BOX_LEAF: src = &T.is_leaf; break;
+        case VP_TREE_BOX_SRC: pairs(T.src_begin, T.src_end); break;
+        case VP_TREE_BOX_TGT: pairs(T.tgt_begin, T.tgt_end); break;
+        case VP_TREE_SRC_PERM: src = &T.src_perm; break;
+        case VP_TREE_TGT_PERM: src = &T.tgt_perm; break;
+        case VP_TREE_U_PTR: src = &T.u_ptr; break;
+        case VP_TREE_U_IDX: src = &T.u_idx; break;
+        case VP_TREE_V_PTR: src = &T.v_ptr; break;
+        case VP_TREE_V_IDX: src = &T.v_idx; break;
+        case VP_TREE_W_PTR: src = &T.w_ptr; break;
+        case VP_TREE_W_IDX: src = &T.w_idx; break;
+        case VP_TREE_X_PTR: src = &T.x_ptr; break;
+        case VP_TREE_X_IDX: src = &T.x_idx; break;
+        default: return fail(VP_ERR_ARG, "unknown tree array");
+    }
+    *count = (int64_t)src->size();
+    if (dst && !src->empty()) std::memcpy(dst, src->data(), src->size() * sizeof(int32_t));
+    return VP_OK;
+}
+
+vp_status vp_tree_destroy(vp_tree tree)
+{
+    delete tree;
+    return VP_OK;
+}
+
+}  // extern "C"

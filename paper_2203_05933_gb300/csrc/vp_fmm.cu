@@ -1,0 +1,714 @@
+// FMM kernels for the smooth-quadrature point sum of the volume potential and
+// the correction apply (arXiv 2203.05933, Eq. Tk_smooth_quad and the sparse
+// correction matrix of Sec. 4), all in IEEE float64 on sm_103a.
+//
+// Potential convention inside this file: psi(z) = Re sum_j q_j log(z - z_j),
+// so that V = -(1/2pi) psi with G = -(1/2pi) log|r - r0| (Sec. 2.1). The
+// complex-variable Laplace expansions are the classical ones (multipole
+// a_0 log(z - c) + sum_k a_k / (z - c)^k, local sum_l b_l (z - c)^l), stored
+// scaled by the box half-side R so that every coefficient stays O(1):
+//   M_k = a_k / R^k,  L_l = b_l R^l.
+// Translation operators in scaled form (z0 = source centre - target centre):
+//   P2M  M_0 = sum q,  M_k = -(1/k) sum q u^k,              u = (z - c)/R
+//   M2M  B_l = -M_0 zeta^l / l + sum_{k<=l} C(l-1,k-1) 2^-k M_k zeta^(l-k)
+//   M2L  A_k = M_k (-t)^k, t = R/z0;  L_0 = M_0 log|z0| + sum_k A_k,
+//        L_l = t^l (-M_0/l + sum_k C(l+k-1,k-1) A_k)
+//   L2L  L'_l = 2^-l sum_{k>=l} C(k,l) zeta^(k-l) L_k
+//   P2L  L_0 = q log|z - c|, L_l = -(q/l) v^l,               v = R/(z - c)
+//   M2P  M_0 log|z - c| + Re sum_k M_k v^k
+//   L2P  Re sum_l L_l u^l
+// zeta is the child-centre offset over the parent half-side, (+-1 +- i)/2.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+constexpr double kInv2Pi = 0.159154943091895335768883763372514362;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kLeafThreads = 64;
+constexpr int kChunk = 16;  // charges staged per step in P2M / P2L
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// a * b + c
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__device__ __forceinline__ int global_warp() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int num_warps() { return (int)((gridDim.x * blockDim.x) >> 5); }
+
+int warp_blocks(int64_t nwork)
+{
+    int64_t b = (nwork + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+// ----------------------------------------------------------------------------
+// a1: charges q_j = w_j f_j gathered into tree order, density-fastest layout.
+template <int ND>
+__global__ void k_charges(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ w,
+                          const double* __restrict__ f, int64_t ld_f, double* __restrict__ q)
+{
+    const int64_t total = (int64_t)n * ND;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = (int32_t)(i / ND);
+        const int d = (int)(i % ND);
+        const double wv = w ? w[s] : 1.0;
+        q[i] = wv * f[d * ld_f + perm[s]];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a3: P2M, one warp per leaf; lane k accumulates coefficient k.
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_p2m(DevTree t, PassGeom g, const double* __restrict__ q, double2* __restrict__ M)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 pw[kWarpsPerBlock][kChunk][P1];
+    __shared__ double qs[kWarpsPerBlock][kChunk][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int li = global_warp(); li < t.nleaf; li += num_warps()) {
+        const int b = t.leaves[li];
+        const int s0 = g.crng[2 * b], s1 = g.crng[2 * b + 1];
+        double2 acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+        const double2 c = t.center[b];
+        const double invR = 1.0 / t.radius[b];
+        for (int base = s0; base < s1; base += kChunk) {
+            const int n = min(kChunk, s1 - base);
+            if (lane < n) {
+                const double2 z = g.cxy[base + lane];
+                const double2 u = make_double2((z.x - c.x) * invR, (z.y - c.y) * invR);
+                double2 p = make_double2(1.0, 0.0);
+                pw[wb][lane][0] = p;
+#pragma unroll 4
+                for (int k = 1; k <= P; ++k) {
+                    p = cmul(p, u);
+                    pw[wb][lane][k] = p;
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) qs[wb][lane][d] = q[(int64_t)(base + lane) * ND + d];
+            }
+            __syncwarp();
+            if (lane <= P) {
+                for (int j = 0; j < n; ++j) {
+                    const double2 pv = pw[wb][j][lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        acc[d].x = fma(qs[wb][j][d], pv.x, acc[d].x);
+                        acc[d].y = fma(qs[wb][j][d], pv.y, acc[d].y);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (lane <= P) {
+            const double s = lane == 0 ? 1.0 : -1.0 / (double)lane;
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                M[((int64_t)b * P1 + lane) * ND + d] = make_double2(acc[d].x * s, acc[d].y * s);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a3: M2M for the non-leaf boxes of one level, one warp per parent.
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_m2m(DevTree t, DevTables tab, int b0, int b1, double2* __restrict__ M)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 Ms[kWarpsPerBlock][P1][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const double inv_l = lane == 0 ? 0.0 : -1.0 / (double)lane;
+    for (int b = b0 + global_warp(); b < b1; b += num_warps()) {
+        if (t.is_leaf[b]) continue;
+        double2 acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+        for (int c = 0; c < 4; ++c) {
+            const int ch = t.child[4 * b + c];
+            if (ch < 0) continue;
+            if (lane <= P) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) Ms[wb][lane][d] = M[((int64_t)ch * P1 + lane) * ND + d];
+            }
+            __syncwarp();
+            if (lane <= P) {
+                const double2* zp = tab.zpow + c * P1;
+                if (lane == 0) {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d] = cadd(acc[d], Ms[wb][0][d]);
+                } else {
+                    const double2 zl = zp[lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const double m0 = Ms[wb][0][d].x * inv_l;
+                        acc[d].x = fma(m0, zl.x, acc[d].x);
+                        acc[d].y = fma(m0, zl.y, acc[d].y);
+                    }
+                    for (int k = 1; k <= lane; ++k) {
+                        const double bm = tab.Bm[lane * P1 + k];
+                        const double2 z = zp[lane - k];
+                        const double2 zb = make_double2(z.x * bm, z.y * bm);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) acc[d] = cfma(zb, Ms[wb][k][d], acc[d]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) M[((int64_t)b * P1 + lane) * ND + d] = acc[d];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a4: M2L over the V list plus P2L over the X list, one warp per target box;
+// lane l owns local coefficient l. Writes every box's L (zeros if no lists).
+template <int P, int ND>
+struct M2LSmem {
+    static constexpr int P1 = P + 1;
+    static constexpr int kA = P1 * ND;                    // double2 per warp, M2L staging
+    static constexpr int kPw = kChunk * P1;               // double2 per warp, P2L powers
+    static constexpr int kUnion = (kA > kPw + (kChunk * (ND + 1) + 1) / 2) ? kA
+                                                                           : kPw + (kChunk * (ND + 1) + 1) / 2;
+};
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_m2l(DevTree t, DevTables tab, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
+          const double* __restrict__ q)
+{
+    constexpr int P1 = P + 1;
+    using S = M2LSmem<P, ND>;
+    __shared__ double Hs[P1 * P1];
+    __shared__ double2 buf[kWarpsPerBlock][S::kUnion];
+    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) Hs[i] = tab.H[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    double2(*As)[ND] = reinterpret_cast<double2(*)[ND]>(&buf[wb][0]);
+    double2(*pw)[P1] = reinterpret_cast<double2(*)[P1]>(&buf[wb][0]);
+    double* qs = reinterpret_cast<double*>(&buf[wb][S::kPw]);  // [kChunk][ND]
+    double* lgs = qs + kChunk * ND;                            // [kChunk]
+    const double inv_l = lane == 0 ? 0.0 : 1.0 / (double)lane;
+
+    for (int b = global_warp(); b < t.nbox; b += num_warps()) {
+        double2 lacc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) lacc[d] = make_double2(0.0, 0.0);
+        const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
+        const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
+        const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
+        const double logR = t.log_radius[b];
+        for (int e = v0; e < v1; ++e) {
+            const int C = t.v_idx[e];
+            const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+            if (lane <= P) {
+                const double2 mt = tab.mtpow[o * P1 + lane];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double2 m = M[((int64_t)C * P1 + lane) * ND + d];
+                    As[lane][d] = lane == 0 ? m : cmul(m, mt);
+                }
+            }
+            __syncwarp();
+            if (lane <= P) {
+                double2 acc[ND];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+                for (int k = 1; k <= P; ++k) {
+                    const double h = Hs[lane * P1 + k];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        acc[d].x = fma(h, As[k][d].x, acc[d].x);
+                        acc[d].y = fma(h, As[k][d].y, acc[d].y);
+                    }
+                }
+                if (lane == 0) {
+                    const double lz = logR + tab.log2o[o];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        lacc[d].x += fma(As[0][d].x, lz, acc[d].x);
+                        lacc[d].y += acc[d].y;
+                    }
+                } else {
+                    const double2 tl = tab.tpow[o * P1 + lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const double2 a = make_double2(fma(-As[0][d].x, inv_l, acc[d].x),
+                                                       fma(-As[0][d].y, inv_l, acc[d].y));
+                        lacc[d] = cfma(tl, a, lacc[d]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (x1 > x0) {
+            const double2 c = t.center[b];
+            const double R = t.radius[b];
+            for (int e = x0; e < x1; ++e) {
+                const int C = t.x_idx[e];
+                const int s0 = g.crng[2 * C], s1 = g.crng[2 * C + 1];
+                for (int base = s0; base < s1; base += kChunk) {
+                    const int n = min(kChunk, s1 - base);
+                    if (lane < n) {
+                        const double2 z = g.cxy[base + lane];
+                        const double dx = z.x - c.x, dy = z.y - c.y;
+                        const double r2 = dx * dx + dy * dy;
+                        const double s = R / r2;
+                        const double2 v = make_double2(dx * s, -dy * s);
+                        double2 p = make_double2(1.0, 0.0);
+                        pw[lane][0] = p;
+#pragma unroll 4
+                        for (int k = 1; k <= P; ++k) {
+                            p = cmul(p, v);
+                            pw[lane][k] = p;
+                        }
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) qs[lane * ND + d] = q[(int64_t)(base + lane) * ND + d];
+                        lgs[lane] = 0.5 * log(r2);
+                    }
+                    __syncwarp();
+                    if (lane <= P) {
+                        for (int j = 0; j < n; ++j) {
+                            if (lane == 0) {
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) lacc[d].x = fma(qs[j * ND + d], lgs[j], lacc[d].x);
+                            } else {
+                                const double2 pv = pw[j][lane];
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) {
+                                    const double cq = -qs[j * ND + d] * inv_l;
+                                    lacc[d].x = fma(cq, pv.x, lacc[d].x);
+                                    lacc[d].y = fma(cq, pv.y, lacc[d].y);
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) L[((int64_t)b * P1 + lane) * ND + d] = lacc[d];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a5: L2L from parents into the boxes of one level, one warp per child.
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_l2l(DevTree t, DevTables tab, int b0, int b1, double2* __restrict__ L)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 Ls[kWarpsPerBlock][P1][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int b = b0 + global_warp(); b < b1; b += num_warps()) {
+        const int p = t.parent[b];
+        const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) Ls[wb][lane][d] = L[((int64_t)p * P1 + lane) * ND + d];
+        }
+        __syncwarp();
+        if (lane <= P) {
+            const double2* zp = tab.zpow + cq * P1;
+            double2 acc[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+            for (int k = lane; k <= P; ++k) {
+                const double bl = tab.Bl[lane * P1 + k];
+                const double2 z = zp[k - lane];
+                const double2 zb = make_double2(z.x * bl, z.y * bl);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = cfma(zb, Ls[wb][k][d], acc[d]);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const int64_t i = ((int64_t)b * P1 + lane) * ND + d;
+                L[i] = cadd(L[i], acc[d]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a5 + a6: per leaf, L2P + M2P over the W list + direct P2P over the U list.
+// GRAD = false: psi[e][d] = Re phi(z_e). GRAD = true: psi[e][0..1][d] = grad Re phi.
+template <int P, int ND, bool GRAD>
+__global__ void __launch_bounds__(kLeafThreads)
+    k_leaf(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
+           const double2* __restrict__ L, double* __restrict__ psi)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 Cs[P1][ND];
+    __shared__ double2 sxy[kLeafThreads];
+    __shared__ double sq[kLeafThreads][ND];
+    const int tid = threadIdx.x;
+    for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
+        const int b = t.leaves[li];
+        const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
+        if (e0 == e1) continue;
+        const double2 cb = t.center[b];
+        const double Rb = t.radius[b];
+        const double invRb = 1.0 / Rb;
+        const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
+        const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
+        for (int tb = e0; tb < e1; tb += kLeafThreads) {
+            const int ti = tb + tid;
+            const bool valid = ti < e1;
+            const double2 z = valid ? g.exy[ti] : cb;
+            double acc[ND], acy[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = acy[d] = 0.0;
+
+            // L2P
+            __syncthreads();
+            for (int i = tid; i < P1 * ND; i += kLeafThreads) (&Cs[0][0])[i] = L[(int64_t)b * P1 * ND + i];
+            __syncthreads();
+            if (valid) {
+                const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (!GRAD) {
+                        double2 s = Cs[P][d];
+                        for (int l = P - 1; l >= 0; --l) s = cfma(s, u, Cs[l][d]);
+                        acc[d] += s.x;
+                    } else {
+                        double2 s = make_double2(Cs[P][d].x * P, Cs[P][d].y * P);
+                        for (int l = P - 1; l >= 1; --l)
+                            s = cfma(s, u, make_double2(Cs[l][d].x * l, Cs[l][d].y * l));
+                        acc[d] += s.x * invRb;
+                        acy[d] -= s.y * invRb;
+                    }
+                }
+            }
+            // M2P over W
+            for (int e = w0; e < w1; ++e) {
+                const int D = t.w_idx[e];
+                __syncthreads();
+                for (int i = tid; i < P1 * ND; i += kLeafThreads) (&Cs[0][0])[i] = M[(int64_t)D * P1 * ND + i];
+                __syncthreads();
+                if (valid) {
+                    const double2 cD = t.center[D];
+                    const double RD = t.radius[D];
+                    const double dx = z.x - cD.x, dy = z.y - cD.y;
+                    const double r2 = dx * dx + dy * dy;
+                    const double2 inv = make_double2(dx / r2, -dy / r2);
+                    const double2 v = make_double2(inv.x * RD, inv.y * RD);
+                    if (!GRAD) {
+                        const double lg = 0.5 * log(r2);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            double2 s = make_double2(0.0, 0.0);
+                            for (int k = P; k >= 1; --k) s = cmul(cadd(s, Cs[k][d]), v);
+                            acc[d] += fma(Cs[0][d].x, lg, s.x);
+                        }
+                    } else {
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            double2 s = make_double2(0.0, 0.0);
+                            for (int k = P; k >= 1; --k)
+                                s = cmul(cadd(s, make_double2(Cs[k][d].x * k, Cs[k][d].y * k)), v);
+                            const double2 dphi = cmul(inv, make_double2(Cs[0][d].x - s.x, Cs[0][d].y - s.y));
+                            acc[d] += dphi.x;
+                            acy[d] -= dphi.y;
+                        }
+                    }
+                }
+            }
+            // P2P over U
+            for (int e = u0; e < u1; ++e) {
+                const int A = t.u_idx[e];
+                const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                for (int sb = a0; sb < a1; sb += kLeafThreads) {
+                    const int n = min(kLeafThreads, a1 - sb);
+                    __syncthreads();
+                    if (tid < n) {
+                        sxy[tid] = g.cxy[sb + tid];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) sq[tid][d] = q[(int64_t)(sb + tid) * ND + d];
+                    }
+                    __syncthreads();
+                    if (valid) {
+                        for (int j = 0; j < n; ++j) {
+                            const double dx = z.x - sxy[j].x, dy = z.y - sxy[j].y;
+                            if (dx == 0.0 && dy == 0.0) continue;  // coincident pair: no smooth term
+                            const double r2 = dx * dx + dy * dy;
+                            if (!GRAD) {
+                                const double lg = 0.5 * log(r2);
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) acc[d] = fma(sq[j][d], lg, acc[d]);
+                            } else {
+                                const double ir = 1.0 / r2;
+                                const double gx = dx * ir, gy = dy * ir;
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) {
+                                    acc[d] = fma(sq[j][d], gx, acc[d]);
+                                    acy[d] = fma(sq[j][d], gy, acy[d]);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (!GRAD) {
+                        psi[(int64_t)ti * ND + d] = acc[d];
+                    } else {
+                        psi[((int64_t)ti * 2 + 0) * ND + d] = acc[d];
+                        psi[((int64_t)ti * 2 + 1) * ND + d] = acy[d];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a7: out = -(1/2pi) psi (back to caller order) + Pi f, one warp per target row.
+template <int ND>
+__global__ void k_out_forward(int32_t n_tgt, const int32_t* __restrict__ inv, const double* __restrict__ psi,
+                              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const double* __restrict__ f, int64_t ld_f,
+                              double* __restrict__ out, int64_t ld_out)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = global_warp(); i < n_tgt; i += num_warps()) {
+        double s[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) s[d] = 0.0;
+        if (rowptr) {
+            const int64_t k1 = rowptr[i + 1];
+            for (int64_t k = rowptr[i] + lane; k < k1; k += 32) {
+                const double v = val[k];
+                const int32_t c = col[k];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) s[d] = fma(v, f[d * ld_f + c], s[d]);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                for (int o = 16; o > 0; o >>= 1) s[d] += __shfl_xor_sync(0xffffffffu, s[d], o);
+        }
+        if (lane == 0) {
+            const int32_t ts = inv[i];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) out[d * ld_out + i] = fma(-kInv2Pi, psi[(int64_t)ts * ND + d], s[d]);
+        }
+    }
+}
+
+// transposed output: grad_f = -(1/2pi) w psi (caller order) + Pi^T g, one warp per source
+template <int ND>
+__global__ void k_out_adjoint(int32_t n_src, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
+                              const double* __restrict__ psi, const int64_t* __restrict__ cptr,
+                              const int32_t* __restrict__ crow, const double* __restrict__ cval,
+                              const double* __restrict__ g, int64_t ld_g, double* __restrict__ out,
+                              int64_t ld_out)
+{
+    const int lane = threadIdx.x & 31;
+    for (int j = global_warp(); j < n_src; j += num_warps()) {
+        double s[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) s[d] = 0.0;
+        if (cptr) {
+            const int64_t k1 = cptr[j + 1];
+            for (int64_t k = cptr[j] + lane; k < k1; k += 32) {
+                const double v = cval[k];
+                const int32_t r = crow[k];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) s[d] = fma(v, g[d * ld_g + r], s[d]);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                for (int o = 16; o > 0; o >>= 1) s[d] += __shfl_xor_sync(0xffffffffu, s[d], o);
+        }
+        if (lane == 0) {
+            const int32_t js = inv[j];
+            const double wj = -kInv2Pi * w_sorted[js];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) out[d * ld_out + j] = fma(wj, psi[(int64_t)js * ND + d], s[d]);
+        }
+    }
+}
+
+// grad_tgt[i] (+)= -(1/2pi) sum_d g[d][i] grad psi_d(t_i), one thread per sorted target
+template <int ND>
+__global__ void k_grad_out(int32_t n_tgt, int accumulate, const int32_t* __restrict__ perm,
+                           const double* __restrict__ gpsi, const double* __restrict__ g, int64_t ld_g,
+                           double* __restrict__ grad)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tgt; t += gridDim.x * blockDim.x) {
+        const int32_t i = perm[t];
+        double gx = 0.0, gy = 0.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const double gv = g[d * ld_g + i];
+            gx = fma(gv, gpsi[((int64_t)t * 2 + 0) * ND + d], gx);
+            gy = fma(gv, gpsi[((int64_t)t * 2 + 1) * ND + d], gy);
+        }
+        gx *= -kInv2Pi;
+        gy *= -kInv2Pi;
+        if (accumulate) {
+            grad[2 * (int64_t)i] += gx;
+            grad[2 * (int64_t)i + 1] += gy;
+        } else {
+            grad[2 * (int64_t)i] = gx;
+            grad[2 * (int64_t)i + 1] = gy;
+        }
+    }
+}
+
+template <int P, int ND>
+cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool gradient,
+                     PhaseTimer* tm, cudaStream_t s)
+{
+    const int threads = kWarpsPerBlock * 32;
+    int id = tm ? tm->begin("p2m") : -1;
+    k_p2m<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.q, ws.M);
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("m2m") : -1;
+    for (int l = t.nlevels - 2; l >= 0; --l) {
+        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
+        k_m2m<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.M);
+    }
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("m2l") : -1;
+    k_m2l<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q);
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("l2l") : -1;
+    for (int l = 1; l < t.nlevels; ++l) {
+        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
+        k_l2l<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.L);
+    }
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("leaf") : -1;
+    const int blocks = t.nleaf < 1 ? 1 : (t.nleaf > 152 * 64 ? 152 * 64 : t.nleaf);
+    if (gradient)
+        k_leaf<P, ND, true><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
+    else
+        k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
+    if (tm) tm->end(id);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t fmm_p(int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool grad,
+                  PhaseTimer* tm, cudaStream_t s)
+{
+    switch (nd) {
+        case 1: return fmm_impl<P, 1>(t, tab, g, ws, grad, tm, s);
+        case 2: return fmm_impl<P, 2>(t, tab, g, ws, grad, tm, s);
+        case 4: return fmm_impl<P, 4>(t, tab, g, ws, grad, tm, s);
+        case 8: return fmm_impl<P, 8>(t, tab, g, ws, grad, tm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int grid_1d(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+}  // namespace
+
+bool p_supported(int P) { return P == 16 || P == 24 || P == 30; }
+
+cudaError_t launch_charges(int nd, int32_t n, const int32_t* perm, const double* w_sorted, const double* f,
+                           int64_t ld_f, double* q, cudaStream_t s)
+{
+    const int blocks = grid_1d((int64_t)n * nd, 256);
+    switch (nd) {
+        case 1: k_charges<1><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
+        case 2: k_charges<2><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
+        case 4: k_charges<4><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
+        case 8: k_charges<8><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fmm_potential(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g,
+                                 Workspace& ws, bool gradient, PhaseTimer* timer, cudaStream_t s)
+{
+    switch (P) {
+        case 16: return fmm_p<16>(nd, t, tab, g, ws, gradient, timer, s);
+        case 24: return fmm_p<24>(nd, t, tab, g, ws, gradient, timer, s);
+        case 30: return fmm_p<30>(nd, t, tab, g, ws, gradient, timer, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_out_forward(int nd, int32_t n_tgt, const int32_t* tgt_inv, const double* psi,
+                               const int64_t* rowptr, const int32_t* col, const double* val, const double* f,
+                               int64_t ld_f, double* out, int64_t ld_out, cudaStream_t s)
+{
+    const int blocks = warp_blocks(n_tgt), threads = kWarpsPerBlock * 32;
+    switch (nd) {
+        case 1: k_out_forward<1><<<blocks, threads, 0, s>>>(n_tgt, tgt_inv, psi, rowptr, col, val, f, ld_f, out, ld_out); break;
+        case 2: k_out_forward<2><<<blocks, threads, 0, s>>>(n_tgt, tgt_inv, psi, rowptr, col, val, f, ld_f, out, ld_out); break;
+        case 4: k_out_forward<4><<<blocks, threads, 0, s>>>(n_tgt, tgt_inv, psi, rowptr, col, val, f, ld_f, out, ld_out); break;
+        case 8: k_out_forward<8><<<blocks, threads, 0, s>>>(n_tgt, tgt_inv, psi, rowptr, col, val, f, ld_f, out, ld_out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_out_adjoint(int nd, int32_t n_src, const int32_t* src_inv, const double* w_sorted,
+                               const double* psi, const int64_t* cptr, const int32_t* crow, const double* cval,
+                               const double* g, int64_t ld_g, double* out, int64_t ld_out, cudaStream_t s)
+{
+    const int blocks = warp_blocks(n_src), threads = kWarpsPerBlock * 32;
+    switch (nd) {
+        case 1: k_out_adjoint<1><<<blocks, threads, 0, s>>>(n_src, src_inv, w_sorted, psi, cptr, crow, cval, g, ld_g, out, ld_out); break;
+        case 2: k_out_adjoint<2><<<blocks, threads, 0, s>>>(n_src, src_inv, w_sorted, psi, cptr, crow, cval, g, ld_g, out, ld_out); break;
+        case 4: k_out_adjoint<4><<<blocks, threads, 0, s>>>(n_src, src_inv, w_sorted, psi, cptr, crow, cval, g, ld_g, out, ld_out); break;
+        case 8: k_out_adjoint<8><<<blocks, threads, 0, s>>>(n_src, src_inv, w_sorted, psi, cptr, crow, cval, g, ld_g, out, ld_out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_out(int nd, bool accumulate, int32_t n_tgt, const int32_t* tgt_perm, const double* gpsi,
+                            const double* g, int64_t ld_g, double* grad, cudaStream_t s)
+{
+    const int blocks = grid_1d(n_tgt, 256);
+    const int acc = accumulate ? 1 : 0;
+    switch (nd) {
+        case 1: k_grad_out<1><<<blocks, 256, 0, s>>>(n_tgt, acc, tgt_perm, gpsi, g, ld_g, grad); break;
+        case 2: k_grad_out<2><<<blocks, 256, 0, s>>>(n_tgt, acc, tgt_perm, gpsi, g, ld_g, grad); break;
+        case 4: k_grad_out<4><<<blocks, 256, 0, s>>>(n_tgt, acc, tgt_perm, gpsi, g, ld_g, grad); break;
+        case 8: k_grad_out<8><<<blocks, 256, 0, s>>>(n_tgt, acc, tgt_perm, gpsi, g, ld_g, grad); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vp

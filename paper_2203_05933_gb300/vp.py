@@ -1,0 +1,312 @@
+"""Thin ctypes binding of libvp's C ABI (include/vp.h).
+
+Each function carries the name of the C entry point it wraps and only marshals
+arguments: torch tensors become device pointers, the current torch CUDA stream
+becomes the stream argument, statuses become exceptions. Every step of the
+computation runs in libvp's CUDA kernels. If libvp.so is missing the import of
+this module's functions raises; there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+VP_OK = 0
+VP_FLAG_TIMING = 1
+
+TREE_ARRAYS = {
+    "box_level": 0, "box_ixy": 1, "box_parent": 2, "box_leaf": 3, "box_src": 4, "box_tgt": 5,
+    "src_perm": 6, "tgt_perm": 7, "u_ptr": 8, "u_idx": 9, "v_ptr": 10, "v_idx": 11,
+    "w_ptr": 12, "w_idx": 13, "x_ptr": 14, "x_idx": 15,
+}
+
+EXPORTED = [
+    "vp_plan_create", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_plan_info",
+    "vp_plan_phase_times", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
+    "vp_tree_build", "vp_tree_get", "vp_tree_destroy",
+]
+
+
+class VPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _load()
+        msg = lib.vp_status_string(status).decode()
+        detail = lib.vp_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+class vp_options(ctypes.Structure):
+    _fields_ = [("p_fmm", ctypes.c_int32), ("leaf", ctypes.c_int32), ("max_level", ctypes.c_int32),
+                ("max_dens", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("root", ctypes.c_double * 3)]
+
+
+class vp_plan_stats(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("n_tgt", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("p_fmm", ctypes.c_int32), ("leaf", ctypes.c_int32), ("max_dens", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_u_pairs", ctypes.c_int64), ("n_v_pairs", ctypes.c_int64), ("n_w_pairs", ctypes.c_int64),
+                ("n_x_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("root", ctypes.c_double * 3)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libvp.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "vp_plan_create": [ctypes.POINTER(P), I64, P, P, I64, P, P, P, P, I64, ctypes.POINTER(vp_options), P],
+        "vp_eval": [P, I32, P, I64, P, I64, P],
+        "vp_eval_adjoint": [P, I32, P, I64, P, I64, P, I64, P, P],
+        "vp_eval_host": [P, I32, P, P, P],
+        "vp_plan_info": [P, ctypes.POINTER(vp_plan_stats)],
+        "vp_plan_phase_times": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(I32)],
+        "vp_plan_destroy": [P],
+        "vp_status_string": [I32],
+        "vp_last_error": [],
+        "vp_version": [],
+        "vp_tree_build": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options)],
+        "vp_tree_get": [P, I32, P, ctypes.POINTER(I64)],
+        "vp_tree_destroy": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name in ("vp_status_string", "vp_last_error", "vp_version") else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != VP_OK:
+        raise VPError(status, where)
+
+
+def make_options(p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0, root=None) -> vp_options:
+    o = vp_options()
+    o.p_fmm, o.leaf, o.max_level, o.max_dens, o.flags = p_fmm, leaf, max_level, max_dens, flags
+    if root is not None:
+        o.root[0], o.root[1], o.root[2] = root
+    return o
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t, shape_last=None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.float64))
+    t = t.to(device="cuda", dtype=torch.float64)
+    return t.contiguous()
+
+
+def vp_version() -> str:
+    return _load().vp_version().decode()
+
+
+def vp_status_string(status: int) -> str:
+    return _load().vp_status_string(status).decode()
+
+
+def vp_plan_create(src_xy, w, tgt_xy, csr=None, options: vp_options | None = None, stream=None):
+    """Returns (plan handle, keep-alive tuple). Inputs may be numpy or torch."""
+    import torch
+    lib = _load()
+    src = _dev_f64(src_xy).reshape(-1, 2)
+    tgt = _dev_f64(tgt_xy).reshape(-1, 2)
+    wt = _dev_f64(w).reshape(-1)
+    if wt.numel() != src.shape[0]:
+        raise ValueError("weights and sources differ in length")
+    rowptr = col = val = None
+    nnz = 0
+    if csr is not None:
+        r, c, v = csr
+        rowptr = torch.as_tensor(np.asarray(r, dtype=np.int64) if not isinstance(r, torch.Tensor) else r)
+        rowptr = rowptr.to(device="cuda", dtype=torch.int64).contiguous()
+        col = torch.as_tensor(np.asarray(c, dtype=np.int32) if not isinstance(c, torch.Tensor) else c)
+        col = col.to(device="cuda", dtype=torch.int32).contiguous()
+        val = _dev_f64(v).reshape(-1)
+        nnz = int(col.numel())
+    h = ctypes.c_void_p()
+    st = lib.vp_plan_create(ctypes.byref(h), src.shape[0], _ptr(src), _ptr(wt), tgt.shape[0], _ptr(tgt),
+                            _ptr(rowptr), _ptr(col), _ptr(val), nnz,
+                            ctypes.byref(options) if options is not None else None, _stream(stream))
+    _check(st, "vp_plan_create")
+    return h
+
+
+def vp_eval(plan, f, out=None, stream=None):
+    """f: CUDA float64 tensor [ndens, n_src] (or [n_src]); returns out [ndens, n_tgt]."""
+    import torch
+    lib = _load()
+    squeeze = f.dim() == 1
+    f2 = f.reshape(1, -1) if squeeze else f
+    if f2.stride(1) != 1:
+        f2 = f2.contiguous()
+    info = vp_plan_info(plan)
+    if out is None:
+        out = torch.empty((f2.shape[0], info.n_tgt), dtype=torch.float64, device=f2.device)
+    ld_f = max(f2.stride(0), f2.shape[1], 1)
+    ld_out = max(out.stride(0), out.shape[1], 1)
+    st = lib.vp_eval(plan, f2.shape[0], _ptr(f2), ld_f, _ptr(out), ld_out, _stream(stream))
+    _check(st, "vp_eval")
+    return out[0] if squeeze else out
+
+
+def vp_eval_adjoint(plan, g, grad_f=True, f=None, grad_tgt=False, stream=None):
+    """Returns (grad_f [ndens, n_src] or None, grad_tgt [n_tgt, 2] or None)."""
+    import torch
+    lib = _load()
+    g2 = g.reshape(1, -1) if g.dim() == 1 else g
+    g2 = g2.contiguous()
+    info = vp_plan_info(plan)
+    nd = g2.shape[0]
+    gf = torch.empty((nd, info.n_src), dtype=torch.float64, device=g2.device) if grad_f else None
+    gt = torch.empty((info.n_tgt, 2), dtype=torch.float64, device=g2.device) if grad_tgt else None
+    f2 = None
+    if grad_tgt:
+        if f is None:
+            raise ValueError("the target gradient needs f")
+        f2 = (f.reshape(1, -1) if f.dim() == 1 else f).contiguous()
+    st = lib.vp_eval_adjoint(plan, nd, _ptr(g2), max(info.n_tgt, 1), _ptr(gf), max(info.n_src, 1),
+                             _ptr(f2), max(info.n_src, 1), _ptr(gt), _stream(stream))
+    _check(st, "vp_eval_adjoint")
+    if gf is not None and g.dim() == 1:
+        gf = gf[0]
+    return gf, gt
+
+
+def vp_eval_host(plan, f_host: np.ndarray, out_host: np.ndarray | None = None, stream=None) -> np.ndarray:
+    """Host-buffer evaluation: f_host [ndens, n_src] float64 (pinned or pageable)."""
+    lib = _load()
+    info = vp_plan_info(plan)
+    f_host = np.ascontiguousarray(f_host, dtype=np.float64).reshape(-1, info.n_src) if info.n_src else \
+        np.zeros((np.asarray(f_host).reshape(-1, 0).shape[0], 0))
+    nd = f_host.shape[0]
+    if out_host is None:
+        out_host = np.empty((nd, info.n_tgt), np.float64)
+    st = lib.vp_eval_host(plan, nd, f_host.ctypes.data_as(ctypes.c_void_p),
+                          out_host.ctypes.data_as(ctypes.c_void_p), _stream(stream))
+    _check(st, "vp_eval_host")
+    return out_host
+
+
+def vp_eval_host_ptr(plan, ndens: int, f_ptr: int, out_ptr: int, stream=None):
+    """vp_eval_host on raw host addresses (e.g. pinned torch tensors)."""
+    st = _load().vp_eval_host(plan, ndens, ctypes.c_void_p(f_ptr), ctypes.c_void_p(out_ptr), _stream(stream))
+    _check(st, "vp_eval_host")
+
+
+def vp_plan_info(plan) -> vp_plan_stats:
+    s = vp_plan_stats()
+    _check(_load().vp_plan_info(plan, ctypes.byref(s)), "vp_plan_info")
+    return s
+
+
+def vp_plan_phase_times(plan) -> dict:
+    lib = _load()
+    cap = 32
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = ctypes.c_int32()
+    _check(lib.vp_plan_phase_times(plan, cap, names, ms, ctypes.byref(n)), "vp_plan_phase_times")
+    return {names[i].decode(): ms[i] for i in range(min(n.value, cap))}
+
+
+def vp_plan_destroy(plan):
+    if plan:
+        _check(_load().vp_plan_destroy(plan), "vp_plan_destroy")
+
+
+def vp_tree_build(src_xy: np.ndarray, tgt_xy: np.ndarray, options: vp_options | None = None) -> dict:
+    """Host tree + interaction lists for inspection; returns a dict of int32 arrays."""
+    lib = _load()
+    src = np.ascontiguousarray(src_xy, np.float64).reshape(-1, 2)
+    tgt = np.ascontiguousarray(tgt_xy, np.float64).reshape(-1, 2)
+    h = ctypes.c_void_p()
+    st = lib.vp_tree_build(ctypes.byref(h), src.shape[0], src.ctypes.data_as(ctypes.c_void_p), tgt.shape[0],
+                           tgt.ctypes.data_as(ctypes.c_void_p),
+                           ctypes.byref(options) if options is not None else None)
+    _check(st, "vp_tree_build")
+    out = {}
+    try:
+        for name, which in TREE_ARRAYS.items():
+            n = ctypes.c_int64()
+            _check(lib.vp_tree_get(h, which, None, ctypes.byref(n)), "vp_tree_get")
+            a = np.empty(n.value, np.int32)
+            _check(lib.vp_tree_get(h, which, a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)), "vp_tree_get")
+            if name in ("box_ixy", "box_src", "box_tgt"):
+                a = a.reshape(-1, 2)
+            out[name] = a
+    finally:
+        lib.vp_tree_destroy(h)
+    return out
+
+
+@dataclass
+class Plan:
+    """Owning wrapper: creates the plan, destroys it when closed or collected."""
+
+    handle: ctypes.c_void_p
+    n_src: int
+    n_tgt: int
+
+    @classmethod
+    def create(cls, src_xy, w, tgt_xy, csr=None, p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0,
+               root=None, stream=None) -> "Plan":
+        opts = make_options(p_fmm, leaf, max_level, max_dens, flags, root)
+        h = vp_plan_create(src_xy, w, tgt_xy, csr, opts, stream)
+        info = vp_plan_info(h)
+        return cls(h, int(info.n_src), int(info.n_tgt))
+
+    def eval(self, f, out=None, stream=None):
+        return vp_eval(self.handle, f, out, stream)
+
+    def adjoint(self, g, grad_f=True, f=None, grad_tgt=False, stream=None):
+        return vp_eval_adjoint(self.handle, g, grad_f, f, grad_tgt, stream)
+
+    def eval_host(self, f_host, out_host=None, stream=None):
+        return vp_eval_host(self.handle, f_host, out_host, stream)
+
+    def info(self) -> vp_plan_stats:
+        return vp_plan_info(self.handle)
+
+    def phase_times(self) -> dict:
+        return vp_plan_phase_times(self.handle)
+
+    def close(self):
+        if self.handle:
+            vp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Error metric (forward): max over targets and densities of |V_gpu - V_oracle|
+divided by sum_j |w_j f_j| of that density; the bar is 1e-10.
+Adjoint: |grad_f_gpu - grad_f_oracle| / (max_j w_j * sum_i |g_i|) <= 1e-10, the
+forward metric of the transposed sum (charges g) scaled by the output weight.
+Target gradient: |err| / (sum_d sum_j |w_j f_j g_i^d| / min distance) style
+bound replaced by a plain relative bar of 1e-8 against the oracle's direct-sum
+gradient (the gradient kernel is 1/r, so its far field converges one order
+slower in P).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2203_05933_gb300 import inputs, vp  # noqa: E402
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_05933_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def rel_err(prob, out, ref):
+    return float(np.max(np.abs(np.asarray(out) - ref) / inputs.normaliser(prob)[:, None]))
+
+
+def run_forward(prob, **opts):
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, root=prob.root, **opts)
+    f = torch.as_tensor(prob.f, device="cuda")
+    out = plan.eval(f).cpu().numpy()
+    return plan, out
+
+
+@pytest.mark.parametrize("P", [30])
+def test_box_grid_small(P):
+    prob = inputs.box_grid_problem(nbox=6, order=8)
+    plan, out = run_forward(prob, p_fmm=P, leaf=64)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    assert rel_err(prob, out, ref) <= TOL
+    plan.close()
+
+
+def test_box_grid_full_16x16():
+    prob = inputs.box_grid_problem(nbox=16, order=8)
+    plan, out = run_forward(prob, p_fmm=30, leaf=64)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    err = rel_err(prob, out, ref)
+    print(f"16x16 box grid rel err {err:.3e}")
+    assert err <= TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("leaf", [8, 32, 64])
+def test_ragged_cloud_p30(leaf):
+    prob = inputs.cloud_problem(3000, 2500, ndens=1, shared=600, seed=21)
+    plan, out = run_forward(prob, p_fmm=30, leaf=leaf)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    err = rel_err(prob, out, ref)
+    print(f"cloud leaf={leaf} rel err {err:.3e}")
+    assert err <= TOL
+    plan.close()
+
+
+def test_error_decreases_with_p():
+    prob = inputs.cloud_problem(2000, 2000, seed=22, csr_per_row=0)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy)
+    errs = []
+    for P in (16, 24, 30):
+        plan, out = run_forward(prob, p_fmm=P, leaf=16)
+        errs.append(rel_err(prob, out, ref))
+        plan.close()
+    print("errors by P", errs)
+    assert errs[0] > errs[2] and errs[2] <= TOL and errs[0] < 1e-5
+
+
+@pytest.mark.parametrize("ndens,max_dens", [(5, 8), (11, 4), (3, 1)])
+def test_multi_density_chunks(ndens, max_dens):
+    prob = inputs.cloud_problem(1500, 1200, ndens=ndens, shared=300, seed=23)
+    plan, out = run_forward(prob, p_fmm=30, leaf=32, max_dens=max_dens)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    assert rel_err(prob, out, ref) <= TOL
+    plan.close()
+
+
+def test_leading_dimensions_and_views():
+    prob = inputs.cloud_problem(800, 700, ndens=3, seed=24)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=32, max_dens=4)
+    big = torch.zeros((3, prob.n_src + 13), dtype=torch.float64, device="cuda")
+    big[:, :prob.n_src] = torch.as_tensor(prob.f, device="cuda")
+    out_big = torch.full((3, prob.n_tgt + 7), 7.0, dtype=torch.float64, device="cuda")
+    plan.eval(big[:, :prob.n_src], out=out_big[:, :prob.n_tgt])
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    assert rel_err(prob, out_big[:, :prob.n_tgt].cpu().numpy(), ref) <= TOL
+    assert torch.all(out_big[:, prob.n_tgt:] == 7.0)
+    plan.close()
+
+
+def test_eval_host_matches_device():
+    prob = inputs.cloud_problem(900, 600, ndens=2, seed=25)
+    plan, out = run_forward(prob, p_fmm=24, leaf=32, max_dens=2)
+    host = plan.eval_host(prob.f)
+    assert np.array_equal(host, out)
+    plan.close()
+
+
+def test_adjoint_matches_oracle():
+    prob = inputs.cloud_problem(1800, 1500, ndens=3, shared=400, seed=26)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=32, max_dens=4)
+    g = np.random.default_rng(1).standard_normal((3, prob.n_tgt))
+    gf, _ = plan.adjoint(torch.as_tensor(g, device="cuda"))
+    ref = oracle.adjoint(prob.src_xy, prob.w, g, prob.tgt_xy, prob.csr)
+    scale = np.abs(g).sum(axis=1)[:, None] * prob.w.max()
+    err = float(np.max(np.abs(gf.cpu().numpy() - ref) / scale))
+    print(f"adjoint rel err {err:.3e}")
+    assert err <= TOL
+    plan.close()
+
+
+def test_adjoint_dot_product_identity():
+    prob = inputs.cloud_problem(1200, 1000, ndens=2, shared=200, seed=27)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=16, max_dens=2)
+    f = torch.as_tensor(prob.f, device="cuda")
+    g = torch.as_tensor(np.random.default_rng(2).standard_normal((2, prob.n_tgt)), device="cuda")
+    Af = plan.eval(f)
+    Atg, _ = plan.adjoint(g)
+    lhs = (Af * g).sum(dim=1).cpu().numpy()
+    rhs = (f * Atg).sum(dim=1).cpu().numpy()
+    scale = (np.abs(prob.w[None, :] * prob.f).sum(axis=1) * np.abs(g.cpu().numpy()).sum(axis=1))
+    assert np.all(np.abs(lhs - rhs) / scale <= TOL)
+    plan.close()
+
+
+def test_target_gradient_matches_oracle():
+    prob = inputs.cloud_problem(1500, 1000, ndens=2, shared=300, seed=28)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=32, max_dens=2)
+    g = np.random.default_rng(3).standard_normal((2, prob.n_tgt))
+    f = torch.as_tensor(prob.f, device="cuda")
+    _, gt = plan.adjoint(torch.as_tensor(g, device="cuda"), grad_f=False, f=f, grad_tgt=True)
+    ref = oracle.grad_targets(prob.src_xy, prob.w, prob.f, g, prob.tgt_xy)
+    err = float(np.max(np.abs(gt.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    print(f"target gradient rel err {err:.3e}")
+    assert err <= 1e-8
+    plan.close()
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(4)
+    # no targets
+    src = rng.uniform(-1, 1, (50, 2))
+    plan = vp.Plan.create(src, np.ones(50), np.zeros((0, 2)))
+    out = plan.eval(torch.ones(50, dtype=torch.float64, device="cuda"))
+    assert out.numel() == 0
+    plan.close()
+    # no sources
+    tgt = rng.uniform(-1, 1, (40, 2))
+    plan = vp.Plan.create(np.zeros((0, 2)), np.zeros(0), tgt)
+    out = plan.eval(torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert torch.all(out == 0)
+    plan.close()
+    # one source on one coincident target, one far target
+    plan = vp.Plan.create(np.array([[0.1, 0.2]]), np.array([2.0]), np.array([[0.1, 0.2], [0.6, 0.2]]))
+    out = plan.eval(torch.tensor([3.0], dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert out[0] == 0.0 and abs(out[1] - (-6.0 * np.log(0.5) / (2 * np.pi))) < 1e-14
+    plan.close()
+    # all points coincident beyond the deepest level
+    xy = np.full((300, 2), 0.25)
+    xy[150:] = -0.5
+    prob = inputs.Problem("coincident", xy, np.full(300, 0.01), xy.copy(), np.ones((1, 300)))
+    plan, out = run_forward(prob, leaf=16, max_level=5)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy)
+    assert rel_err(prob, out, ref) <= TOL
+    plan.close()
+
+
+def test_bad_arguments_raise():
+    with pytest.raises(vp.VPError):
+        vp.Plan.create(np.zeros((4, 2)), np.ones(4), np.zeros((4, 2)), p_fmm=17)
+    rowptr = np.array([0, 2, 1, 3, 3], np.int64)  # not monotone
+    with pytest.raises(vp.VPError):
+        vp.Plan.create(np.zeros((4, 2)), np.ones(4), np.zeros((4, 2)),
+                       (rowptr, np.array([0, 1, 2], np.int32), np.ones(3)))
+    with pytest.raises(vp.VPError):
+        vp.Plan.create(np.zeros((4, 2)), np.ones(4), np.zeros((4, 2)),
+                       (np.array([0, 1, 1, 1, 1]), np.array([9], np.int32), np.ones(1)))
+    w = np.ones(4)
+    w[2] = np.nan
+    with pytest.raises(vp.VPError):
+        vp.Plan.create(np.zeros((4, 2)), w, np.zeros((4, 2)))
+
+
+def test_phase_timing_flag():
+    prob = inputs.box_grid_problem(nbox=6, order=8)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, flags=vp.VP_FLAG_TIMING, root=prob.root)
+    plan.eval(torch.as_tensor(prob.f, device="cuda"))
+    t = plan.phase_times()
+    assert {"charges", "p2m", "m2m", "m2l", "l2l", "leaf", "out"} <= set(t)
+    assert all(v >= 0 for v in t.values())
+    plan.close()
