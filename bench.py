@@ -1,0 +1,348 @@
+"""Benchmark of the volume-potential hot path on GB300.
+
+One step = one vp_eval of the unit-disk workload (about 1.1 M quadrature nodes of
+adaptive boxes and curved triangles, targets = nodes, self + near-cell
+correction matrix of about 6e8 nonzeros): charges, the whole FMM (P2M, M2M,
+M2L, L2L, L2P, M2P, P2L, P2P) and the correction apply.
+
+Metric: volume-potential Mpoints/s = n_targets * ndens / t_eval, FP64, with the
+relative l-infinity error against the CPU oracle (sampled targets) reported
+beside it (the gate is 1e-10, normalised by sum_j |w_j f_j|).
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch under torch.distributed.run; every rank evaluates its own
+independent disk problem (different seeded refinement), no data-path
+collective (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "volume-potential Mpoints/s (FP64, rel err <=1e-10), batched/adjoint vs plain FMM"
+UNIT = "Mpoints/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM (measured), 152 SMs, 2070 MHz
+P2P_FLOP_PER_PAIR = 27.0  # 7 flops + 20 flop-equivalents for one FP64 log (stated convention)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=30)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--batched", type=int, default=64, help="densities of the batched leg (0: skip)")
+    ap.add_argument("--small", action="store_true", help="small disk (for profiling runs)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(args, rank):
+    from paper_2203_05933_gb300 import inputs
+
+    seed = inputs.SEED_BASE + 2 + 1000 * rank
+    if args.small:
+        return inputs.disk_problem(base_level=5, fine_level=7, seed=seed, name="disk_small")
+    return inputs.disk_problem(seed=seed, name="disk_1M")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)  # writes 256 MB, twice the 129 MB L2
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain C, OpenMP) on the host cores: each step evaluates a
+    bounded seeded sample of targets of the same workload, exactly."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2203_05933_gb300 import inputs
+
+    oracle.build()
+    prob = make_problem(args, 0)
+    rng = np.random.default_rng(7)
+    cores = oracle.max_threads()
+    sample = 256
+    rows = rng.choice(prob.n_tgt, size=sample, replace=False)
+    csr = oracle.csr_rows(prob.csr, rows)
+    tgt = prob.tgt_xy[rows]
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.evaluate(prob.src_xy, prob.w, prob.f, tgt, csr)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = sample * prob.ndens / t / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
+                   "ndens": prob.ndens, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} seeded targets of {prob.n_tgt} per step, full direct sum over "
+                                   f"{prob.n_src} sources + their correction rows"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(prob, budget_s=15.0):
+    import oracle
+
+    oracle.build()
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(11)
+    probe = 32
+    rows = rng.choice(prob.n_tgt, size=probe, replace=False)
+    t0 = time.perf_counter()
+    oracle.evaluate(prob.src_xy, prob.w, prob.f[:1], prob.tgt_xy[rows], oracle.csr_rows(prob.csr, rows))
+    per_tgt = (time.perf_counter() - t0) / probe
+    n = int(min(max(budget_s / max(per_tgt, 1e-9), 64), 16384))
+    rows = rng.choice(prob.n_tgt, size=n, replace=False)
+    t0 = time.perf_counter()
+    oracle.evaluate(prob.src_xy, prob.w, prob.f[:1], prob.tgt_xy[rows], oracle.csr_rows(prob.csr, rows))
+    dt = time.perf_counter() - t0
+    return {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded targets of {prob.n_tgt}, full direct sum over {prob.n_src} sources + "
+                      f"correction rows, one density ({dt:.1f} s)"}
+
+
+def sampled_error(prob, out, k=256, seed=5):
+    import oracle
+    from paper_2203_05933_gb300 import inputs
+
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(prob.n_tgt, size=min(k, prob.n_tgt), replace=False)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy[rows], oracle.csr_rows(prob.csr, rows))
+    return float(np.max(np.abs(out[:, rows] - ref) / inputs.normaliser(prob)[:, None]))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2203_05933_gb300 import build, vp
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    vp._load()
+    prob = make_problem(args, rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=args.p, leaf=args.leaf,
+                          max_dens=8, flags=vp.VP_FLAG_TIMING, root=prob.root)
+    info = plan.info()
+    f = torch.as_tensor(prob.f, device=dev)
+    out = torch.empty((prob.ndens, prob.n_tgt), dtype=torch.float64, device=dev)
+    flush = torch.empty(32 * 1024 * 1024, dtype=torch.float64, device=dev)
+
+    # accuracy gate on sampled targets
+    plan.eval(f, out=out)
+    torch.cuda.synchronize()
+    rel_err = sampled_error(prob, out.cpu().numpy()) if rank == 0 else None
+
+    for _ in range(args.warmup):
+        flush_l2(flush)
+        plan.eval(f, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    phase_sum = {}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush_l2(flush)
+        ev[k][0].record(stream)
+        plan.eval(f, out=out)
+        ev[k][1].record(stream)
+        for name, ms in plan.phase_times().items():
+            phase_sum[name] = phase_sum.get(name, 0.0) + ms
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_dev = float(t.item())
+        total_pts = torch.tensor([prob.n_tgt * prob.ndens * args.steps], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(total_pts)
+        pts = float(total_pts.item())
+    else:
+        pts = float(prob.n_tgt * prob.ndens * args.steps)
+    value = pts / t_dev / 1e6
+    phase_ms = {k: v / args.steps for k, v in phase_sum.items()}
+
+    # e2e: the C-ABI host-buffer entry point, pinned buffers, copies inside the timed region
+    f_pin = torch.empty((prob.ndens, prob.n_src), dtype=torch.float64, pin_memory=True)
+    f_pin.copy_(torch.as_tensor(prob.f))
+    o_pin = torch.empty((prob.ndens, prob.n_tgt), dtype=torch.float64, pin_memory=True)
+    vp.vp_eval_host_ptr(plan.handle, prob.ndens, f_pin.data_ptr(), o_pin.data_ptr())
+    e2e_t = []
+    for k in range(max(3, args.steps // 2)):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vp.vp_eval_host_ptr(plan.handle, prob.ndens, f_pin.data_ptr(), o_pin.data_ptr())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = prob.n_tgt * prob.ndens / float(np.mean(e2e_t)) / 1e6
+
+    # batched leg: many densities through one plan (max_dens chunks of 8)
+    batched = None
+    if args.batched > 0:
+        from paper_2203_05933_gb300 import inputs
+
+        rng = np.random.default_rng(3)
+        fb = torch.as_tensor(rng.standard_normal((args.batched, prob.n_src)), device=dev)
+        ob = torch.empty((args.batched, prob.n_tgt), dtype=torch.float64, device=dev)
+        plan.eval(fb, out=ob)
+        torch.cuda.synchronize()
+        bt = []
+        for k in range(max(2, args.steps // 3)):
+            flush_l2(flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.eval(fb, out=ob)
+            b.record(stream)
+            torch.cuda.synchronize()
+            bt.append(a.elapsed_time(b) / 1e3)
+        batched = {"ndens": args.batched, "value": prob.n_tgt * args.batched / float(np.mean(bt)) / 1e6,
+                   "unit": UNIT, "speedup_vs_single": (prob.n_tgt * args.batched / float(np.mean(bt)) / 1e6) / value}
+
+    if rank != 0:
+        plan.close()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    # roofline of the dominant kernel (leaf: P2P + L2P + M2P), FP64 ALU bound
+    P = info.p_fmm
+    leaf_flops = info.p2p_pairs * P2P_FLOP_PER_PAIR + info.n_tgt * 8.0 * P + info.n_w_pairs * 64 * 8.0 * P
+    dom = max(phase_ms, key=phase_ms.get)
+    leaf_ms = phase_ms.get("leaf", float("nan"))
+    achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_leaf (P2P+L2P+M2P)", "dominant_phase": dom,
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "FP64 FMA units: 2/clk/SM (measured) x 152 SMs x 2070 MHz",
+                "algorithmic_flop_per_launch": leaf_flops}
+    cpu = None if args.no_cpu else cpu_baseline(prob)
+    launches_per_chunk = 5 + 2 * (info.n_levels - 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
+                   "ndens": prob.ndens, "p_fmm": P, "leaf": info.leaf, "levels": info.n_levels,
+                   "boxes": info.n_boxes, "p2p_pairs": info.p2p_pairs, "m2l_pairs": info.n_v_pairs,
+                   "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
+        "rel_err": rel_err,
+        "phase_ms": phase_ms,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(prob.ndens * prob.n_src * 8),
+                "d2h_bytes_per_step": int(prob.ndens * prob.n_tgt * 8)},
+        "batched": batched,
+        "clocks": clk,
+        "gpu_launches": launches_per_chunk * args.steps,
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

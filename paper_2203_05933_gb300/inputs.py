@@ -198,3 +198,53 @@ def cloud_problem(n_src: int, n_tgt: int, ndens: int = 1, seed: int = SEED_BASE 
 def normaliser(problem: Problem) -> np.ndarray:
     """sum_j |w_j f_j^d| per density: the scale of the relative l-infinity error."""
     return np.abs(problem.w[None, :] * problem.f).sum(axis=1)
+
+
+def disk_centres(seed: int, k: int = 5, rmax: float = 0.8):
+    """k seeded bump centres, uniform in the disk r < rmax."""
+    rng = np.random.default_rng(seed)
+    r = rmax * np.sqrt(rng.random(k))
+    th = 2 * np.pi * rng.random(k)
+    return np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+
+
+def f_disk(x, y, sigma: float = 0.1):
+    """Radial density 1 + exp(-r^2 / sigma^2) on the unit disk."""
+    return 1.0 + np.exp(-(x * x + y * y) / sigma**2)
+
+
+def disk_problem(base_level: int = 7, fine_level: int = 9, refine_radius=None, ndens: int = 1,
+                 seed: int = SEED_BASE + 2, csr: str = "synthetic", name: str | None = None) -> Problem:
+    """The unit-disk workload: quadtree boxes (8x8 Gauss-Legendre) refined around
+    5 seeded bump centres, plus a band of curved and straight degree-7 triangles
+    (36 nodes each); sources = targets = the nodes. With the defaults (levels
+    7..9) it has about 1.1 M nodes. The correction pattern is self + near cells;
+    its values are seeded stand-ins (parity and timing only)."""
+    from .setup import meshes
+
+    if refine_radius is None:
+        refine_radius = {base_level + 1: 0.11, base_level + 2: 0.04}
+    mesh = meshes.disk_mesh(base_level=base_level, fine_level=fine_level, centres=disk_centres(seed),
+                            refine_radius=refine_radius)
+    xy, w = mesh.xy, mesh.w
+    f0 = f_disk(xy[:, 0], xy[:, 1])
+    if ndens == 1:
+        f = f0[None, :]
+    else:
+        rng = np.random.default_rng(seed + 3)
+        f = np.empty((ndens, xy.shape[0]))
+        f[0] = f0
+        for d in range(1, ndens):  # random Gaussian mixtures
+            c = rng.uniform(-0.7, 0.7, size=(4, 2))
+            a = rng.standard_normal(4)
+            s = rng.uniform(0.05, 0.5, size=4)
+            f[d] = sum(a[m] * np.exp(-((xy[:, 0] - c[m, 0]) ** 2 + (xy[:, 1] - c[m, 1]) ** 2) / s[m] ** 2)
+                       for m in range(4))
+    mat = None
+    if csr == "synthetic":
+        rowptr, col = meshes.near_cell_pattern(mesh)
+        mat = (rowptr, col, synthetic_csr_values(rowptr, col, w, seed + 17))
+    return Problem(name=name or f"disk_L{base_level}-{fine_level}", src_xy=xy, w=w, tgt_xy=xy.copy(),
+                   f=np.ascontiguousarray(f), csr=mat, root=(-1.0, -1.0, 2.0),
+                   meta={"n_cells": mesh.ncell, "n_triangles": int((mesh.cell_kind > 0).sum()),
+                         "base_level": base_level, "fine_level": fine_level})

@@ -207,3 +207,26 @@ def test_phase_timing_flag():
     assert {"charges", "p2m", "m2m", "m2l", "l2l", "leaf", "out"} <= set(t)
     assert all(v >= 0 for v in t.values())
     plan.close()
+
+
+def test_disk_small_adaptive_with_triangles():
+    prob = inputs.disk_problem(base_level=4, fine_level=6, ndens=2)
+    plan, out = run_forward(prob, p_fmm=30, leaf=64, max_dens=8)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    err = rel_err(prob, out, ref)
+    print(f"small disk rel err {err:.3e}")
+    assert err <= TOL
+    plan.close()
+
+
+@pytest.mark.parametrize("P", [24, 30])
+def test_disk_1M_sampled_targets(P):
+    # the benchmark's workload and launch configuration, checked on sampled targets
+    prob = inputs.disk_problem()
+    plan, out = run_forward(prob, p_fmm=P, leaf=64, max_dens=8)
+    rows = np.random.default_rng(9).choice(prob.n_tgt, size=192, replace=False)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy[rows], oracle.csr_rows(prob.csr, rows))
+    err = rel_err(prob, out[:, rows], ref)
+    print(f"disk 1M P={P} sampled rel err {err:.3e}")
+    assert err <= TOL
+    plan.close()
