@@ -207,6 +207,45 @@ vp_status vp_tree_build(vp_tree* out, int64_t n_src, const double* src_xy_host,
 vp_status vp_tree_get(vp_tree tree, int32_t which, int32_t* dst, int64_t* count);
 vp_status vp_tree_destroy(vp_tree tree);
 
+/*
+ * vp_eval_direct_static — evaluation that allocates nothing.
+ *
+ * For callers that cannot allocate device memory when they need the volume
+ * potential: a host application that owns every device allocation and hands
+ * out only buffers it made itself, a plug-in running inside someone else's
+ * stream capture where an allocation would break the capture, or an embedded
+ * user whose device footprint must not grow after start-up. vp_plan_create
+ * allocates (tree, workspace), so such callers use this entry point instead.
+ * The paper has no counterpart: this is a convenience variant of the direct
+ * (P2P) kernel without a tree, summing over every source, so its cost is
+ * O(n_src * n_tgt) and it suits small problems.
+ *
+ * It computes the same quantity as vp_eval:
+ *   out[d][i] = sum_{j: r_j != t_i} w_j f[d][j] G(r_j, t_i) + sum_k Pi_ik f[d][k]
+ * with the same argument conventions (device pointers, caller order, CSR
+ * optional: corr_rowptr = NULL means no correction). It calls no cudaMalloc,
+ * cudaFree or other allocating routine. Its intermediate charges and partial
+ * sums live in one file-scope device array of VP_STATIC_SCRATCH_DOUBLES
+ * doubles (16 MiB) that every GPU which loads libvp holds until the process
+ * exits. Limits: n_src + n_tgt <= VP_STATIC_SCRATCH_DOUBLES, else VP_ERR_ARG
+ * ("problem too large for the static scratch"; see vp_last_error).
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture that should contain later calls. All calls share
+ * the one array and it keeps the last call's contents; every element a call
+ * reads is written earlier in the same call, so nothing needs clearing. Calls
+ * whose work overlaps on the GPU (different streams, or different host threads
+ * on one device) race on the array: serialize them.
+ */
+#define VP_STATIC_SCRATCH_DOUBLES (1 << 21)
+vp_status vp_eval_direct_static(int64_t n_src, const double* src_xy, const double* w,
+                                int32_t ndens, const double* f, int64_t ld_f,
+                                int64_t n_tgt, const double* tgt_xy,
+                                const int64_t* corr_rowptr, const int32_t* corr_col,
+                                const double* corr_val, double* out, int64_t ld_out,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

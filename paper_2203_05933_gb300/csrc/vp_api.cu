@@ -120,6 +120,10 @@ bool finite_all(const std::vector<double>& a)
 
 }  // namespace
 
+namespace vp {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace vp
+
 // ---------------------------------------------------------------------------
 int PhaseTimer::begin(const char* name)
 {

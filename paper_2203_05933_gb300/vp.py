@@ -310,3 +310,23 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def vp_eval_direct_static(src_xy, w, f, tgt_xy, out, csr=None, stream=None):
+    """Binding of the allocation-free entry point (direct sum, scratch in a fixed
+    device array). Every argument must already be a CUDA float64 tensor (CSR:
+    int64 rowptr, int32 col, float64 val) because the call itself allocates
+    nothing; `out` [ndens, n_tgt] receives the result."""
+    lib = _load()
+    fn = lib.vp_eval_direct_static
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    fn.argtypes = [I64, P, P, I32, P, I64, I64, P, P, P, P, P, I64, P]
+    fn.restype = ctypes.c_int
+    f2 = f.reshape(1, -1) if f.dim() == 1 else f
+    out2 = out.reshape(1, -1) if out.dim() == 1 else out
+    n_src, n_tgt = src_xy.shape[0], tgt_xy.shape[0]
+    rowptr, col, val = csr if csr is not None else (None, None, None)
+    st = fn(n_src, _ptr(src_xy), _ptr(w), f2.shape[0], _ptr(f2), max(f2.stride(0), n_src, 1), n_tgt, _ptr(tgt_xy),
+            _ptr(rowptr), _ptr(col), _ptr(val), _ptr(out2), max(out2.stride(0), n_tgt, 1), _stream(stream))
+    _check(st, "vp_eval_direct_static")
+    return out
