@@ -79,6 +79,9 @@ typedef struct {
 
 /* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
 #define VP_FLAG_TIMING 1u
+/* Near field (direct sums over adjacent leaves) with FP64 log instead of the default
+ * float-float evaluation (same result to about 1e-12 absolute per pair; slower). */
+#define VP_FLAG_P2P_FP64 2u
 
 /*
  * vp_plan_create — "vp_plan(nodes, weights, targets, corr_csr)".

@@ -111,6 +111,50 @@ std::vector<double> make_tables(int P, size_t off[7])
     return v;
 }
 
+// 128-entry table for the float-float log of the near-field kernel: for
+// c_k = 1 + (k + 1/2)/128, rc_k = fl(1/c_k) and T_k = -log(rc_k) split as
+// T_hi (rounded to 19 fractional bits, so that e*ln2_hi + T_hi is exact in one
+// float for |e| <= 15) plus T_lo.
+std::vector<float> make_log_table()
+{
+    std::vector<float> t(128 * 4);
+    for (int k = 0; k < 128; ++k) {
+        const long double c = 1.0L + ((long double)k + 0.5L) / 128.0L;
+        const float rc = (float)(1.0L / c);
+        const long double T = -logl((long double)rc);
+        const long double Th = roundl(T * 524288.0L) / 524288.0L;
+        t[4 * k + 0] = rc;
+        t[4 * k + 1] = (float)Th;
+        t[4 * k + 2] = (float)(T - Th);
+        t[4 * k + 3] = 0.0f;
+    }
+    return t;
+}
+
+// Leaf-relative coordinates of every point of each leaf: ((x, y) - centre)/side,
+// each component split into hi + lo floats.
+std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted, bool sources)
+{
+    const size_t n = xy_sorted.size() / 2;
+    std::vector<float> r(n * 4, 0.0f);
+    for (int64_t b = 0; b < T.n_boxes(); ++b) {
+        if (!T.is_leaf[(size_t)b]) continue;
+        const int32_t p0 = sources ? T.src_begin[(size_t)b] : T.tgt_begin[(size_t)b];
+        const int32_t p1 = sources ? T.src_end[(size_t)b] : T.tgt_end[(size_t)b];
+        const double side = T.box_side((int)b), cx = T.box_cx((int)b), cy = T.box_cy((int)b);
+        for (int32_t i = p0; i < p1; ++i) {
+            const double rx = (xy_sorted[2 * (size_t)i] - cx) / side;
+            const double ry = (xy_sorted[2 * (size_t)i + 1] - cy) / side;
+            const float xh = (float)rx, yh = (float)ry;
+            r[4 * (size_t)i + 0] = xh;
+            r[4 * (size_t)i + 1] = (float)(rx - (double)xh);
+            r[4 * (size_t)i + 2] = yh;
+            r[4 * (size_t)i + 3] = (float)(ry - (double)yh);
+        }
+    }
+    return r;
+}
+
 bool finite_all(const std::vector<double>& a)
 {
     for (double x : a)
@@ -170,6 +214,8 @@ struct vp_plan_s {
     // points and weights in tree order
     double2* src_xy = nullptr;
     double2* tgt_xy = nullptr;
+    float4* src_rho = nullptr;
+    float4* tgt_rho = nullptr;
     double* w_sorted = nullptr;
     int32_t *src_perm = nullptr, *tgt_perm = nullptr, *src_inv = nullptr, *tgt_inv = nullptr;
     int32_t *box_src = nullptr, *box_tgt = nullptr;
@@ -239,9 +285,11 @@ PassGeom forward_geom(vp_plan p)
     PassGeom g;
     g.cxy = p->src_xy;
     g.crng = p->box_src;
+    g.crho = p->src_rho;
     g.n_charge = (int32_t)p->n_src;
     g.exy = p->tgt_xy;
     g.erng = p->box_tgt;
+    g.erho = p->tgt_rho;
     g.n_eval = (int32_t)p->n_tgt;
     return g;
 }
@@ -251,12 +299,16 @@ PassGeom adjoint_geom(vp_plan p)
     PassGeom g;
     g.cxy = p->tgt_xy;
     g.crng = p->box_tgt;
+    g.crho = p->tgt_rho;
     g.n_charge = (int32_t)p->n_tgt;
     g.exy = p->src_xy;
     g.erng = p->box_src;
+    g.erho = p->src_rho;
     g.n_eval = (int32_t)p->n_src;
     return g;
 }
+
+bool p2p_fp64(vp_plan p) { return (p->flags & VP_FLAG_P2P_FP64) != 0; }
 
 }  // namespace
 
@@ -422,6 +474,8 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     }
     size_t off[7];
     std::vector<double> tables = make_tables(P, off);
+    std::vector<float> logtab = make_log_table();
+    std::vector<float> srho = make_rho(T, sxy, true), trho = make_rho(T, txy, false);
 
     cudaError_t e = cudaSuccess;
     auto up = [&](auto** dst, const auto& h) {
@@ -460,6 +514,14 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     up(&d_xp, T.x_ptr);
     up(&d_xi, T.x_idx);
     up(&d_tab, tables);
+    float *d_logtab = nullptr, *d_srho = nullptr, *d_trho = nullptr;
+    int32_t* d_level = nullptr;
+    up(&d_logtab, logtab);
+    up(&d_srho, srho);
+    up(&d_trho, trho);
+    up(&d_level, T.level);
+    p->src_rho = (float4*)d_srho;
+    p->tgt_rho = (float4*)d_trho;
     if (has_corr) {
         up(&p->rowptr, hrow);
         up(&p->col, hcol);
@@ -471,6 +533,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     const int P1 = P + 1;
     const int64_t npts = std::max<int64_t>(std::max<int64_t>(n_src, n_tgt), 1);
     if (e == cudaSuccess) e = p->alloc(&p->ws.q, (size_t)npts * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.qf, (size_t)npts * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.psi, (size_t)npts * 2 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.M, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
@@ -489,6 +552,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     dt.radius = d_radius;
     dt.log_radius = d_logr;
     dt.ixy = d_ixy;
+    dt.level = d_level;
     dt.parent = d_parent;
     dt.child = d_child;
     dt.is_leaf = d_leaf;
@@ -512,6 +576,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     tb.mtpow = (const double2*)(d_tab + off[4]);
     tb.log2o = d_tab + off[5];
     tb.zpow = (const double2*)(d_tab + off[6]);
+    tb.logtab = (const float4*)d_logtab;
     *out = p;
     return VP_OK;
 }
@@ -533,9 +598,10 @@ vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, doubl
         const int nd = chunk_for(ndens - d0, p->nd_cap);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
-        VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, s));
+        VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
         p->timer.end(id);
-        VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, p->timer.on ? &p->timer : nullptr, s));
+        VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, p2p_fp64(p),
+                                     p->timer.on ? &p->timer : nullptr, s));
         id = p->timer.begin("out");
         VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc, ld_f,
                                    out + (int64_t)d0 * ld_out, ld_out, s));
@@ -572,8 +638,8 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
         for (int d0 = 0; d0 < ndens;) {
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* gc = g + (int64_t)d0 * ld_g;
-            VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, s));
-            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, nullptr, s));
+            VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
+            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, p2p_fp64(p), nullptr, s));
             VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr, p->crow,
                                        p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
             d0 += nd;
@@ -584,8 +650,8 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
         for (int d0 = 0; d0 < ndens;) {
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* fc = f + (int64_t)d0 * ld_f;
-            VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, s));
-            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, nullptr, s));
+            VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
+            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, true, nullptr, s));
             VP_CUDA(launch_grad_out(nd, d0 > 0, (int32_t)p->n_tgt, p->tgt_perm, p->ws.psi, g + (int64_t)d0 * ld_g,
                                     ld_g, grad_tgt, s));
             d0 += nd;

@@ -58,9 +58,12 @@ int warp_blocks(int64_t nwork)
 
 // ----------------------------------------------------------------------------
 // a1: charges q_j = w_j f_j gathered into tree order, density-fastest layout.
+// Also writes each charge as an unevaluated sum of two floats (hi + lo) for the
+// float-float near-field kernel.
 template <int ND>
 __global__ void k_charges(int32_t n, const int32_t* __restrict__ perm, const double* __restrict__ w,
-                          const double* __restrict__ f, int64_t ld_f, double* __restrict__ q)
+                          const double* __restrict__ f, int64_t ld_f, double* __restrict__ q,
+                          float2* __restrict__ qf)
 {
     const int64_t total = (int64_t)n * ND;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -68,7 +71,10 @@ __global__ void k_charges(int32_t n, const int32_t* __restrict__ perm, const dou
         const int32_t s = (int32_t)(i / ND);
         const int d = (int)(i % ND);
         const double wv = w ? w[s] : 1.0;
-        q[i] = wv * f[d * ld_f + perm[s]];
+        const double v = wv * f[d * ld_f + perm[s]];
+        q[i] = v;
+        const float hi = __double2float_rn(v);
+        qf[i] = make_float2(hi, __double2float_rn(v - (double)hi));
     }
 }
 
@@ -490,6 +496,249 @@ __global__ void __launch_bounds__(kLeafThreads)
 }
 
 // ----------------------------------------------------------------------------
+// a5 + a6, float-float near field. Same result as k_leaf<.., false>, but the
+// direct sum over the U list runs on the FP32 pipes (64x the FP64 rate on this
+// part) in float-float arithmetic: every quantity is an unevaluated sum hi + lo
+// of two floats, carried with error-free transformations (TwoSum, FMA-based
+// TwoProd), which keeps about 48 significant bits.
+//
+// Per pair, in units of the target leaf's side (so r2 stays within a few
+// binades of 1):
+//   dx, dy   from leaf-relative coordinates (exact leaf-centre offsets)
+//   r2       = dx^2 + dy^2 (hi, lo)
+//   log r2   = e ln2 + T_k + log1p(u),  r2 = 2^e m, m in [1, 2),
+//              k = top 7 bits of m, u = m / c_k - 1 (|u| <= 2^-8),
+//              T_k = log c_k from a 128-entry table, log1p by its series to u^6.
+//            The exponent is limited to |e| <= 15 so that e * ln2_hi + T_hi is
+//            exact in one float (ln2_hi and T_hi have 19 fractional bits);
+//            other pairs (and only those) take an FP64 log.
+//   psi     += q * log r2 (hi, lo), accumulated with TwoSum.
+// Absolute error of one log r2 is below about 3e-12; the result is converted
+// to FP64 once per target and combined with the leaf-size term
+// log(side) * (sum of the U-list charges minus coincident ones).
+namespace ff {
+
+constexpr float kLn2Hi = 363409.0f / 524288.0f;  // ln 2 rounded to 19 fractional bits
+constexpr float kLn2Lo = 1.0f * (float)(0.693147180559945309417232121458176568 - 363409.0 / 524288.0);
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+}  // namespace ff
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kLeafThreads)
+    k_leaf_ff(DevTree t, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
+              const double2* __restrict__ M, const double2* __restrict__ L, const float4* __restrict__ logtab,
+              double* __restrict__ psi)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 Cs[P1][ND];
+    __shared__ float4 s_rho[kLeafThreads];
+    __shared__ float2 s_q[kLeafThreads][ND];
+    __shared__ double s_qd[kLeafThreads][ND];
+    __shared__ float4 s_tab[128];
+    __shared__ double s_red[kLeafThreads / 32][ND];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 128; i += kLeafThreads) s_tab[i] = logtab[i];
+    for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
+        const int b = t.leaves[li];
+        const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
+        if (e0 == e1) continue;
+        const double2 cb = t.center[b];
+        const double Rb = t.radius[b];
+        const double invRb = 1.0 / Rb;
+        const double log_side = t.log_radius[b] + 0.693147180559945309417232121458176568;
+        const int lb = t.level[b];
+        const int ixb = t.ixy[2 * b], iyb = t.ixy[2 * b + 1];
+        const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
+        const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
+        for (int tb = e0; tb < e1; tb += kLeafThreads) {
+            const int ti = tb + tid;
+            const bool valid = ti < e1;
+            const double2 z = valid ? g.exy[ti] : cb;
+            double acc[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+
+            // L2P (FP64)
+            __syncthreads();
+            for (int i = tid; i < P1 * ND; i += kLeafThreads) (&Cs[0][0])[i] = L[(int64_t)b * P1 * ND + i];
+            __syncthreads();
+            if (valid) {
+                const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double2 s = Cs[P][d];
+                    for (int l = P - 1; l >= 0; --l) s = cfma(s, u, Cs[l][d]);
+                    acc[d] += s.x;
+                }
+            }
+            // M2P over W (FP64)
+            for (int e = w0; e < w1; ++e) {
+                const int D = t.w_idx[e];
+                __syncthreads();
+                for (int i = tid; i < P1 * ND; i += kLeafThreads) (&Cs[0][0])[i] = M[(int64_t)D * P1 * ND + i];
+                __syncthreads();
+                if (valid) {
+                    const double2 cD = t.center[D];
+                    const double RD = t.radius[D];
+                    const double dx = z.x - cD.x, dy = z.y - cD.y;
+                    const double r2 = dx * dx + dy * dy;
+                    const double2 v = make_double2(dx / r2 * RD, -dy / r2 * RD);
+                    const double lg = 0.5 * log(r2);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        double2 s = make_double2(0.0, 0.0);
+                        for (int k = P; k >= 1; --k) s = cmul(cadd(s, Cs[k][d]), v);
+                        acc[d] += fma(Cs[0][d].x, lg, s.x);
+                    }
+                }
+            }
+
+            // P2P over U (float-float)
+            const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float ah[ND], al[ND];
+            double qsum[ND], qco[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                ah[d] = al[d] = 0.f;
+                qsum[d] = qco[d] = 0.0;
+            }
+            for (int e = u0; e < u1; ++e) {
+                const int A = t.u_idx[e];
+                const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                if (a0 == a1) continue;
+                // leaf A's centre and scale in units of leaf b (exact dyadic numbers)
+                const int dl = lb - t.level[A];
+                const double sc = ldexp(1.0, dl);
+                const float offx = (float)((2.0 * t.ixy[2 * A] + 1.0) * 0.5 * sc - ((double)ixb + 0.5));
+                const float offy = (float)((2.0 * t.ixy[2 * A + 1] + 1.0) * 0.5 * sc - ((double)iyb + 0.5));
+                const float scf = (float)sc;
+                for (int sb = a0; sb < a1; sb += kLeafThreads) {
+                    const int n = min(kLeafThreads, a1 - sb);
+                    __syncthreads();
+                    if (tid < n) {
+                        const int j = sb + tid;
+                        const float4 r = g.crho[j];
+                        float xh, xl, yh, yl;
+                        ff::two_sum(offx, __fmul_rn(scf, r.x), xh, xl);
+                        xl = __fadd_rn(xl, __fmul_rn(scf, r.y));
+                        ff::two_sum(offy, __fmul_rn(scf, r.z), yh, yl);
+                        yl = __fadd_rn(yl, __fmul_rn(scf, r.w));
+                        s_rho[tid] = make_float4(xh, xl, yh, yl);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            s_q[tid][d] = qf[(int64_t)j * ND + d];
+                            const double qv = q[(int64_t)j * ND + d];
+                            s_qd[tid][d] = qv;
+                            qsum[d] += qv;
+                        }
+                    }
+                    __syncthreads();
+                    if (valid) {
+#pragma unroll 2
+                        for (int k = 0; k < n; ++k) {
+                            const float4 sr = s_rho[k];
+                            float dxs, dxe, dys, dye;
+                            ff::two_sum(rt.x, -sr.x, dxs, dxe);
+                            dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
+                            ff::two_sum(rt.z, -sr.z, dys, dye);
+                            dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
+                            const float px = __fmul_rn(dxs, dxs);
+                            float pxe = fmaf(dxs, dxs, -px);
+                            pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
+                            pxe = fmaf(dxe, dxe, pxe);
+                            const float py = __fmul_rn(dys, dys);
+                            float pye = fmaf(dys, dys, -py);
+                            pye = fmaf(__fadd_rn(dys, dys), dye, pye);
+                            pye = fmaf(dye, dye, pye);
+                            float rs, re;
+                            ff::two_sum(px, py, rs, re);
+                            re = __fadd_rn(re, __fadd_rn(pxe, pye));
+                            const float r2h = __fadd_rn(rs, re);
+                            const float r2l = __fsub_rn(re, __fsub_rn(r2h, rs));
+                            if (r2h == 0.0f) {  // bitwise-coincident pair: no smooth term
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) qco[d] += s_qd[k][d];
+                                continue;
+                            }
+                            const int bits = __float_as_int(r2h);
+                            const int ex = (bits >> 23) - 127;
+                            float S, lo;
+                            if ((unsigned)(ex + 15) <= 30u) {
+                                const float4 tk = s_tab[(bits >> 16) & 127];
+                                const float mh = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+                                const float ml = __fmul_rn(r2l, __int_as_float((127 - ex) << 23));
+                                const float Pm = __fmul_rn(mh, tk.x);
+                                const float Pe = fmaf(mh, tk.x, -Pm);
+                                const float uh = __fsub_rn(Pm, 1.0f);
+                                const float ul = fmaf(ml, tk.x, Pe);
+                                const float ef = __fsub_rn(__int_as_float(0x4B400000 + ex), 12582912.0f);
+                                const float hi = fmaf(ef, ff::kLn2Hi, tk.y);
+                                const float uhh = __fsub_rn(__fadd_rn(uh, 24.0f), 24.0f);
+                                const float uhl = __fsub_rn(uh, uhh);
+                                S = __fadd_rn(hi, uhh);
+                                const float s2 = __fmul_rn(uh, uh);
+                                const float s2e = fmaf(uh, uh, -s2);
+                                const float poly = fmaf(uh, fmaf(uh, fmaf(uh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f);
+                                float tt = __fmul_rn(__fmul_rn(s2, uh), poly);
+                                tt = fmaf(-uh, ul, tt);
+                                tt = fmaf(-0.5f, s2e, tt);
+                                tt = __fadd_rn(tt, ul);
+                                tt = __fadd_rn(tt, tk.z);
+                                tt = __fadd_rn(tt, uhl);
+                                tt = fmaf(-0.5f, s2, tt);
+                                lo = fmaf(ef, ff::kLn2Lo, tt);
+                            } else {
+                                const double ld = log((double)r2h + (double)r2l);
+                                S = __double2float_rn(ld);
+                                lo = __double2float_rn(ld - (double)S);
+                            }
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) {
+                                const float2 qq = s_q[k][d];
+                                const float p = __fmul_rn(qq.x, S);
+                                float pe = fmaf(qq.x, S, -p);
+                                pe = fmaf(qq.x, lo, pe);
+                                pe = fmaf(qq.y, S, pe);
+                                float sh, se;
+                                ff::two_sum(ah[d], p, sh, se);
+                                ah[d] = sh;
+                                al[d] = __fadd_rn(al[d], __fadd_rn(se, pe));
+                            }
+                        }
+                    }
+                }
+            }
+            // sum of the U-list charges over the block (each thread summed the ones it loaded)
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                for (int o = 16; o > 0; o >>= 1) qsum[d] += __shfl_xor_sync(0xffffffffu, qsum[d], o);
+            __syncthreads();
+            if ((tid & 31) == 0) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) s_red[tid >> 5][d] = qsum[d];
+            }
+            __syncthreads();
+            if (valid) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double qu = 0.0;
+                    for (int w = 0; w < kLeafThreads / 32; ++w) qu += s_red[w][d];
+                    const double near = 0.5 * ((double)ah[d] + (double)al[d]) + log_side * (qu - qco[d]);
+                    psi[(int64_t)ti * ND + d] = acc[d] + near;
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
 // a7: out = -(1/2pi) psi (back to caller order) + Pi f, one warp per target row.
 template <int ND>
 __global__ void k_out_forward(int32_t n_tgt, const int32_t* __restrict__ inv, const double* __restrict__ psi,
@@ -585,7 +834,7 @@ __global__ void k_grad_out(int32_t n_tgt, int accumulate, const int32_t* __restr
 
 template <int P, int ND>
 cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool gradient,
-                     PhaseTimer* tm, cudaStream_t s)
+                     bool p2p_fp64, PhaseTimer* tm, cudaStream_t s)
 {
     const int threads = kWarpsPerBlock * 32;
     int id = tm ? tm->begin("p2m") : -1;
@@ -610,21 +859,23 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
     const int blocks = t.nleaf < 1 ? 1 : (t.nleaf > 152 * 64 ? 152 * 64 : t.nleaf);
     if (gradient)
         k_leaf<P, ND, true><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
-    else
+    else if (p2p_fp64)
         k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
+    else
+        k_leaf_ff<P, ND><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.qf, ws.M, ws.L, tab.logtab, ws.psi);
     if (tm) tm->end(id);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t fmm_p(int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool grad,
-                  PhaseTimer* tm, cudaStream_t s)
+                  bool p2p_fp64, PhaseTimer* tm, cudaStream_t s)
 {
     switch (nd) {
-        case 1: return fmm_impl<P, 1>(t, tab, g, ws, grad, tm, s);
-        case 2: return fmm_impl<P, 2>(t, tab, g, ws, grad, tm, s);
-        case 4: return fmm_impl<P, 4>(t, tab, g, ws, grad, tm, s);
-        case 8: return fmm_impl<P, 8>(t, tab, g, ws, grad, tm, s);
+        case 1: return fmm_impl<P, 1>(t, tab, g, ws, grad, p2p_fp64, tm, s);
+        case 2: return fmm_impl<P, 2>(t, tab, g, ws, grad, p2p_fp64, tm, s);
+        case 4: return fmm_impl<P, 4>(t, tab, g, ws, grad, p2p_fp64, tm, s);
+        case 8: return fmm_impl<P, 8>(t, tab, g, ws, grad, p2p_fp64, tm, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -642,26 +893,26 @@ int grid_1d(int64_t n, int threads)
 bool p_supported(int P) { return P == 16 || P == 24 || P == 30; }
 
 cudaError_t launch_charges(int nd, int32_t n, const int32_t* perm, const double* w_sorted, const double* f,
-                           int64_t ld_f, double* q, cudaStream_t s)
+                           int64_t ld_f, double* q, float2* qf, cudaStream_t s)
 {
     const int blocks = grid_1d((int64_t)n * nd, 256);
     switch (nd) {
-        case 1: k_charges<1><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
-        case 2: k_charges<2><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
-        case 4: k_charges<4><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
-        case 8: k_charges<8><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q); break;
+        case 1: k_charges<1><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q, qf); break;
+        case 2: k_charges<2><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q, qf); break;
+        case 4: k_charges<4><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q, qf); break;
+        case 8: k_charges<8><<<blocks, 256, 0, s>>>(n, perm, w_sorted, f, ld_f, q, qf); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_fmm_potential(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g,
-                                 Workspace& ws, bool gradient, PhaseTimer* timer, cudaStream_t s)
+                                 Workspace& ws, bool gradient, bool p2p_fp64, PhaseTimer* timer, cudaStream_t s)
 {
     switch (P) {
-        case 16: return fmm_p<16>(nd, t, tab, g, ws, gradient, timer, s);
-        case 24: return fmm_p<24>(nd, t, tab, g, ws, gradient, timer, s);
-        case 30: return fmm_p<30>(nd, t, tab, g, ws, gradient, timer, s);
+        case 16: return fmm_p<16>(nd, t, tab, g, ws, gradient, p2p_fp64, timer, s);
+        case 24: return fmm_p<24>(nd, t, tab, g, ws, gradient, p2p_fp64, timer, s);
+        case 30: return fmm_p<30>(nd, t, tab, g, ws, gradient, p2p_fp64, timer, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -26,6 +26,7 @@ struct DevTree {
     const double* radius = nullptr;     // [nbox] half side R
     const double* log_radius = nullptr; // [nbox] log R
     const int32_t* ixy = nullptr;       // [nbox][2]
+    const int32_t* level = nullptr;     // [nbox]
     const int32_t* parent = nullptr;    // [nbox]
     const int32_t* child = nullptr;     // [nbox][4]
     const int32_t* is_leaf = nullptr;   // [nbox]
@@ -48,20 +49,24 @@ struct DevTables {
     const double2* mtpow = nullptr; // [49][P1] (-t_o)^k                           (M2L)
     const double* log2o = nullptr;  // [49] log(2 |o|)                             (M2L)
     const double2* zpow = nullptr;  // [4][P1] zeta_c^m, zeta_c = child offset / R_parent
+    const float4* logtab = nullptr; // [128] {1/c_k, T_hi, T_lo, 0}, T = -log(1/c_k)  (P2P log)
 };
 
 // One direction of the FMM: where charges sit and where the potential is taken.
 struct PassGeom {
     const double2* cxy = nullptr;   // charge points, tree order
     const int32_t* crng = nullptr;  // per box [begin, end) into cxy
+    const float4* crho = nullptr;   // charge points relative to their leaf: (x - c)/side as hi/lo floats
     int32_t n_charge = 0;
     const double2* exy = nullptr;   // evaluation points, tree order
     const int32_t* erng = nullptr;
+    const float4* erho = nullptr;
     int32_t n_eval = 0;
 };
 
 struct Workspace {
     double* q = nullptr;      // [max(n_src, n_tgt)][ND] charges, tree order
+    float2* qf = nullptr;     // [max(n_src, n_tgt)][ND] the same charges as hi/lo float pairs
     double2* M = nullptr;     // [nbox][P1][ND] multipole coefficients (scaled)
     double2* L = nullptr;     // [nbox][P1][ND] local coefficients (scaled)
     double* psi = nullptr;    // [max(n_src, n_tgt)][2][ND] potential (or gradient) in tree order
@@ -81,9 +86,10 @@ struct PhaseTimer {
 
 // Launchers (vp_fmm.cu). All enqueue on `s`; nd is the density chunk (1, 2, 4 or 8).
 cudaError_t launch_charges(int nd, int32_t n, const int32_t* perm, const double* w_sorted,
-                           const double* f, int64_t ld_f, double* q, cudaStream_t s);
+                           const double* f, int64_t ld_f, double* q, float2* qf, cudaStream_t s);
+// p2p_fp64: evaluate the near field with FP64 log instead of the float-float path
 cudaError_t launch_fmm_potential(int P, int nd, const DevTree& t, const DevTables& tab,
-                                 const PassGeom& g, Workspace& ws, bool gradient,
+                                 const PassGeom& g, Workspace& ws, bool gradient, bool p2p_fp64,
                                  PhaseTimer* timer, cudaStream_t s);
 cudaError_t launch_out_forward(int nd, int32_t n_tgt, const int32_t* tgt_inv, const double* psi,
                                const int64_t* rowptr, const int32_t* col, const double* val,

@@ -21,6 +21,7 @@ _lib = None
 
 VP_OK = 0
 VP_FLAG_TIMING = 1
+VP_FLAG_P2P_FP64 = 2
 
 TREE_ARRAYS = {
     "box_level": 0, "box_ixy": 1, "box_parent": 2, "box_leaf": 3, "box_src": 4, "box_tgt": 5,
