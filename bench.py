@@ -33,19 +33,52 @@ sys.path.insert(0, ROOT)
 METRIC = "volume-potential Mpoints/s (FP64, rel err <=1e-10), batched/adjoint vs plain FMM"
 UNIT = "Mpoints/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM (measured), 152 SMs, 2070 MHz
+FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12     # FP32/INT32 lane-operations per second (T ops/s)
 P2P_FLOP_PER_PAIR = 27.0  # 7 flops + 20 flop-equivalents for one FP64 log (stated convention)
+P2P_FF_OPS_PER_PAIR = 90.0  # FP32 operations of the float-float pair evaluation (k_leaf_ff)
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "profiling-recipe fallback 6.8 TB/s"
+
+
+def roofline_models(info, prob, ndens=1):
+    """Per-phase roofline models: algorithmic work per launch of each phase."""
+    P = info.p_fmm
+    hbm, hbm_src = hbm_peak()
+    return {
+        "leaf": {"bound": "alu", "kernel": "k_leaf_ff (float-float P2P + FP64 L2P/M2P)",
+                 "work": info.p2p_pairs * P2P_FF_OPS_PER_PAIR * ndens, "unit": "T FP32-ops/s",
+                 "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",
+                 "fp64_equiv_flop": info.p2p_pairs * P2P_FLOP_PER_PAIR * ndens,
+                 "per_unit": f"{P2P_FF_OPS_PER_PAIR:.0f} FP32 ops per source-target pair"},
+        "m2l": {"bound": "alu", "kernel": "k_m2l_ff (float-float scaled-Hankel M2L)",
+                "work": info.n_v_pairs * (P + 1) * (24.0 * P + 100.0) * ndens, "unit": "T FP32-ops/s",
+                "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",
+                "fp64_equiv_flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens,
+                "per_unit": f"(P+1)(24P+100) FP32 ops per V-list pair, P={P}"},
+        "out": {"bound": "hbm", "kernel": "k_out_forward (CSR correction apply)",
+                "work": info.nnz * 12.0 + info.n_tgt * 8.0 * (2 * ndens + 1), "unit": "GB/s",
+                "peak": hbm, "peak_source": hbm_src,
+                "per_unit": "12 B per nonzero (int32 col + fp64 val) + 8 B per row per density in and out"},
+    }
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--p", type=int, default=30)
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--batched", type=int, default=64, help="densities of the batched leg (0: skip)")
-    ap.add_argument("--small", action="store_true", help="small disk (for profiling runs)")
+    ap.add_argument("--size", default="full", choices=["full", "medium", "small"],
+                    help="disk levels 7-9 (1.1 M nodes), 6-8 (profiling) or 5-7")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     return ap.parse_args()
 
@@ -61,8 +94,10 @@ def make_problem(args, rank):
     from paper_2203_05933_gb300 import inputs
 
     seed = inputs.SEED_BASE + 2 + 1000 * rank
-    if args.small:
+    if args.size == "small":
         return inputs.disk_problem(base_level=5, fine_level=7, seed=seed, name="disk_small")
+    if args.size == "medium":
+        return inputs.disk_problem(base_level=6, fine_level=8, seed=seed, name="disk_medium")
     return inputs.disk_problem(seed=seed, name="disk_1M")
 
 
@@ -263,6 +298,7 @@ def main():
         pts = float(prob.n_tgt * prob.ndens * args.steps)
     value = pts / t_dev / 1e6
     phase_ms = {k: v / args.steps for k, v in phase_sum.items()}
+    launches_per_eval = plan.info().last_launches
 
     # e2e: the C-ABI host-buffer entry point, pinned buffers, copies inside the timed region
     f_pin = torch.empty((prob.ndens, prob.n_src), dtype=torch.float64, pin_memory=True)
@@ -306,35 +342,44 @@ def main():
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()
         return
-    # roofline of the dominant kernel (leaf: P2P + L2P + M2P), FP64 ALU bound
-    P = info.p_fmm
-    leaf_flops = info.p2p_pairs * P2P_FLOP_PER_PAIR + info.n_tgt * 8.0 * P + info.n_w_pairs * 64 * 8.0 * P
+    # roofline of the dominant phase, from live CUDA-event phase times on the evaluation stream
+    models = roofline_models(info, prob)
     dom = max(phase_ms, key=phase_ms.get)
-    leaf_ms = phase_ms.get("leaf", float("nan"))
-    achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_leaf (P2P+L2P+M2P)", "dominant_phase": dom,
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "FP64 FMA units: 2/clk/SM (measured) x 152 SMs x 2070 MHz",
-                "algorithmic_flop_per_launch": leaf_flops}
+    rl_all = {}
+    for name, m in models.items():
+        ms = phase_ms.get(name)
+        if not ms:
+            continue
+        scale = 1e9 if m["bound"] == "hbm" else 1e12
+        achieved = m["work"] / (ms * 1e-3) / scale
+        r = {"bound": m["bound"], "kernel": m["kernel"], "achieved": achieved, "peak": m["peak"],
+             "unit": m["unit"], "frac": achieved / m["peak"], "traffic": None, "ms": ms,
+             "peak_source": m["peak_source"], "per_unit": m["per_unit"]}
+        if "fp64_equiv_flop" in m:
+            fe = m["fp64_equiv_flop"] / (ms * 1e-3) / 1e12
+            r["fp64_equiv"] = {"achieved_tflops": fe, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                               "frac": fe / FP64_PEAK_TFLOPS}
+        rl_all[name] = r
+    roofline = dict(rl_all.get(dom, {}), phase=dom)
     cpu = None if args.no_cpu else cpu_baseline(prob)
-    launches_per_chunk = 5 + 2 * (info.n_levels - 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
-                   "ndens": prob.ndens, "p_fmm": P, "leaf": info.leaf, "levels": info.n_levels,
+                   "ndens": prob.ndens, "p_fmm": info.p_fmm, "leaf": info.leaf, "levels": info.n_levels,
                    "boxes": info.n_boxes, "p2p_pairs": info.p2p_pairs, "m2l_pairs": info.n_v_pairs,
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": f"replicas x{world}"},
         "rel_err": rel_err,
         "phase_ms": phase_ms,
         "roofline": roofline,
+        "roofline_phases": rl_all,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(prob.ndens * prob.n_src * 8),
                 "d2h_bytes_per_step": int(prob.ndens * prob.n_tgt * 8)},
         "batched": batched,
         "clocks": clk,
-        "gpu_launches": launches_per_chunk * args.steps,
+        "gpu_launches": int(launches_per_eval * args.steps),
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)

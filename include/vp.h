@@ -79,9 +79,10 @@ typedef struct {
 
 /* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
 #define VP_FLAG_TIMING 1u
-/* Near field (direct sums over adjacent leaves) with FP64 log instead of the default
- * float-float evaluation (same result to about 1e-12 absolute per pair; slower). */
-#define VP_FLAG_P2P_FP64 2u
+/* Run the near field (direct sums over adjacent leaves) and M2L in FP64 instead of the
+ * default float-float evaluation on the FP32 pipes (same result to about 1e-12 relative
+ * to the total charge; several times slower on GB300). */
+#define VP_FLAG_FP64 2u
 
 /*
  * vp_plan_create — "vp_plan(nodes, weights, targets, corr_csr)".
@@ -156,6 +157,7 @@ typedef struct {
     int64_t n_w_pairs;      /* sum over leaves of |W| (multipole-to-target blocks)      */
     int64_t n_x_pairs;      /* sum over boxes of |X| (source-to-local blocks)           */
     int64_t p2p_pairs;      /* source-target pairs summed directly (one density)        */
+    int64_t last_launches;  /* kernel launches made by the last vp_eval on this plan      */
     double root[3];
 } vp_plan_stats;
 

@@ -131,6 +131,90 @@ std::vector<float> make_log_table()
     return t;
 }
 
+// Float-float copies of the M2L tables (each value split as hi + lo floats):
+// H [P1][P1] (float2), t^l and (-t)^k [49][P1] (float4 complex), log(2|o|) [49],
+// 1/l [P1] (float2), the M2M and L2L binomials [P1][P1] (float2) and the child
+// offset powers zeta^m [4][P1] (float2, exact). Offsets in floats in off[8].
+std::vector<float> make_ff_tables(int P, size_t off[8])
+{
+    const int P1 = P + 1;
+    std::vector<float> v;
+    auto split = [&](long double x) {
+        const float h = (float)x;
+        v.push_back(h);
+        v.push_back((float)(x - (long double)h));
+    };
+    auto align16 = [&]() {  // every table starts on a 16-byte boundary (float4 loads)
+        while (v.size() % 4) v.push_back(0.0f);
+    };
+    off[0] = v.size();
+    for (int l = 0; l <= P; ++l)
+        for (int k = 0; k <= P; ++k) {
+            if (k == 0) {
+                split(0.0L);
+                continue;
+            }
+            const uint64_t hb = binom_u64(l + k - 1, k - 1);
+            const float h = (float)hb;
+            v.push_back(h);
+            v.push_back((float)((long double)hb - (long double)h));
+        }
+    for (int pass = 0; pass < 2; ++pass) {
+        align16();
+        off[1 + pass] = v.size();
+        for (int oy = -3; oy <= 3; ++oy)
+            for (int ox = -3; ox <= 3; ++ox) {
+                const bool far = std::max(std::abs(ox), std::abs(oy)) >= 2;
+                const long double den = 2.0L * (long double)(ox * ox + oy * oy);
+                const long double sgn = pass == 0 ? 1.0L : -1.0L;
+                const long double tr = far ? sgn * (long double)ox / den : 0.0L;
+                const long double ti = far ? -sgn * (long double)oy / den : 0.0L;
+                long double pr = 1.0L, pi = 0.0L;
+                for (int l = 0; l <= P; ++l) {
+                    split(far ? pr : 0.0L);
+                    split(far ? pi : 0.0L);
+                    const long double nr = pr * tr - pi * ti, ni = pr * ti + pi * tr;
+                    pr = nr;
+                    pi = ni;
+                }
+            }
+    }
+    align16();
+    off[3] = v.size();
+    for (int oy = -3; oy <= 3; ++oy)
+        for (int ox = -3; ox <= 3; ++ox) {
+            const int r2 = ox * ox + oy * oy;
+            split(r2 > 0 ? logl(2.0L) + 0.5L * logl((long double)r2) : 0.0L);
+        }
+    align16();
+    off[4] = v.size();
+    for (int l = 0; l <= P; ++l) split(l == 0 ? 0.0L : 1.0L / (long double)l);
+    align16();
+    off[5] = v.size();
+    for (int l = 0; l <= P; ++l)
+        for (int k = 0; k <= P; ++k)
+            split((k >= 1 && k <= l) ? ldexpl((long double)binom_u64(l - 1, k - 1), -k) : 0.0L);
+    align16();
+    off[6] = v.size();
+    for (int l = 0; l <= P; ++l)
+        for (int k = 0; k <= P; ++k) split(k >= l ? ldexpl((long double)binom_u64(k, l), -l) : 0.0L);
+    align16();
+    off[7] = v.size();
+    for (int c = 0; c < 4; ++c) {
+        const double zr = (c & 1) ? 0.5 : -0.5, zi = (c & 2) ? 0.5 : -0.5;
+        double pr = 1.0, pi = 0.0;
+        for (int m = 0; m <= P; ++m) {
+            v.push_back((float)pr);  // exact: dyadic values
+            v.push_back((float)pi);
+            const double nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
+            pr = nr;
+            pi = ni;
+        }
+    }
+    (void)P1;
+    return v;
+}
+
 // Leaf-relative coordinates of every point of each leaf: ((x, y) - centre)/side,
 // each component split into hi + lo floats.
 std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted, bool sources)
@@ -153,6 +237,46 @@ std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted,
         }
     }
     return r;
+}
+
+// Groups of consecutive rows with identical column lists, and the values as
+// hi/lo float pairs, for the grouped correction apply.
+struct HostGroups {
+    std::vector<int32_t> g_r0;
+    std::vector<int64_t> g_c0;
+    std::vector<int32_t> cols;
+    std::vector<float> vf;
+    int32_t max_m = 0;
+};
+
+void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
+                  const std::vector<double>& val, HostGroups& G)
+{
+    int64_t start = -1;
+    for (int64_t i = 0; i < nrows; ++i) {
+        const int64_t a = rowptr[(size_t)i], b = rowptr[(size_t)i + 1];
+        bool same = start >= 0;
+        if (same) {
+            const int64_t sa = rowptr[(size_t)start], sb = rowptr[(size_t)start + 1];
+            same = (b - a) == (sb - sa) &&
+                   std::memcmp(col.data() + a, col.data() + sa, (size_t)(b - a) * sizeof(int32_t)) == 0;
+        }
+        if (!same) {
+            G.g_r0.push_back((int32_t)i);
+            G.g_c0.push_back((int64_t)G.cols.size());
+            G.cols.insert(G.cols.end(), col.begin() + a, col.begin() + b);
+            G.max_m = std::max<int32_t>(G.max_m, (int32_t)(b - a));
+            start = i;
+        }
+    }
+    G.g_r0.push_back((int32_t)nrows);
+    G.g_c0.push_back((int64_t)G.cols.size());
+    G.vf.resize(val.size() * 2);
+    for (size_t k = 0; k < val.size(); ++k) {
+        const float h = (float)val[k];
+        G.vf[2 * k] = h;
+        G.vf[2 * k + 1] = (float)(val[k] - (double)h);
+    }
 }
 
 bool finite_all(const std::vector<double>& a)
@@ -226,12 +350,15 @@ struct vp_plan_s {
     int64_t* cptr = nullptr;
     int32_t* crow = nullptr;
     double* cval = nullptr;
+    bool grouped = false;       // correction applied by the grouped float-float kernel
+    DevGroupedCSR gfwd, gadj;   // Pi and Pi^T, rows grouped by shared column lists
     Workspace ws;
     PhaseTimer timer;
     // staging for vp_eval_host
     double* stage = nullptr;
     size_t stage_cap = 0;
     int64_t p2p_pairs = 0;
+    int64_t last_launches = 0;
     bool alive = true;
 
     template <typename T>
@@ -308,7 +435,7 @@ PassGeom adjoint_geom(vp_plan p)
     return g;
 }
 
-bool p2p_fp64(vp_plan p) { return (p->flags & VP_FLAG_P2P_FP64) != 0; }
+bool use_fp64(vp_plan p) { return (p->flags & VP_FLAG_FP64) != 0; }
 
 }  // namespace
 
@@ -475,6 +602,8 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     size_t off[7];
     std::vector<double> tables = make_tables(P, off);
     std::vector<float> logtab = make_log_table();
+    size_t offf[8];
+    std::vector<float> fftab = make_ff_tables(P, offf);
     std::vector<float> srho = make_rho(T, sxy, true), trho = make_rho(T, txy, false);
 
     cudaError_t e = cudaSuccess;
@@ -517,12 +646,15 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     float *d_logtab = nullptr, *d_srho = nullptr, *d_trho = nullptr;
     int32_t* d_level = nullptr;
     up(&d_logtab, logtab);
+    float* d_fftab = nullptr;
+    up(&d_fftab, fftab);
     up(&d_srho, srho);
     up(&d_trho, trho);
     up(&d_level, T.level);
     p->src_rho = (float4*)d_srho;
     p->tgt_rho = (float4*)d_trho;
-    if (has_corr) {
+    p->grouped = has_corr && !(p->flags & VP_FLAG_FP64);
+    if (has_corr && !p->grouped) {
         up(&p->rowptr, hrow);
         up(&p->col, hcol);
         up(&p->val, hval);
@@ -530,12 +662,40 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
         up(&p->crow, hcrow);
         up(&p->cval, hcval);
     }
+    if (p->grouped) {
+        for (int pass = 0; pass < 2; ++pass) {
+            HostGroups G;
+            const bool fwd = pass == 0;
+            const int64_t nrows = fwd ? n_tgt : n_src;
+            build_groups(nrows, fwd ? hrow : hcptr, fwd ? hcol : hcrow, fwd ? hval : hcval, G);
+            DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
+            int32_t *d_r0 = nullptr, *d_cols = nullptr;
+            int64_t *d_c0 = nullptr, *d_rp = nullptr;
+            float* d_vf = nullptr;
+            up(&d_r0, G.g_r0);
+            up(&d_c0, G.g_c0);
+            up(&d_cols, G.cols);
+            up(&d_rp, fwd ? hrow : hcptr);
+            up(&d_vf, G.vf);
+            A.nrows = (int32_t)nrows;
+            A.ngroups = (int32_t)G.g_r0.size() - 1;
+            A.max_m = G.max_m;
+            A.g_r0 = d_r0;
+            A.g_c0 = d_c0;
+            A.cols = d_cols;
+            A.rowptr = d_rp;
+            A.vf = (const float2*)d_vf;
+        }
+    }
     const int P1 = P + 1;
     const int64_t npts = std::max<int64_t>(std::max<int64_t>(n_src, n_tgt), 1);
     if (e == cudaSuccess) e = p->alloc(&p->ws.q, (size_t)npts * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.qf, (size_t)npts * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.psi, (size_t)npts * 2 * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.xf, (size_t)npts * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.M, (size_t)nb * P1 * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.Mf, (size_t)nb * P1 * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -577,6 +737,28 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     tb.log2o = d_tab + off[5];
     tb.zpow = (const double2*)(d_tab + off[6]);
     tb.logtab = (const float4*)d_logtab;
+    tb.Hf = (const float2*)(d_fftab + offf[0]);
+    tb.tpowf = (const float4*)(d_fftab + offf[1]);
+    tb.mtpowf = (const float4*)(d_fftab + offf[2]);
+    tb.log2of = (const float2*)(d_fftab + offf[3]);
+    tb.invlf = (const float2*)(d_fftab + offf[4]);
+    tb.Bmf = (const float2*)(d_fftab + offf[5]);
+    tb.Blf = (const float2*)(d_fftab + offf[6]);
+    tb.zpowf = (const float2*)(d_fftab + offf[7]);
+    {
+        const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
+                               p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf};
+        const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
+                              p->gfwd.vf, p->gadj.vf};
+        bool ok = true;
+        for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);
+        for (const void* q : vec8) ok = ok && ((uintptr_t)q % 8 == 0);
+        if (!ok) {
+            delete p;
+            *out = nullptr;
+            return fail(VP_ERR_CUDA, "internal error: misaligned device table");
+        }
+    }
     *out = p;
     return VP_OK;
 }
@@ -594,17 +776,27 @@ vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, doubl
     p->timer.stream = s;
     p->timer.used = 0;
     PassGeom g = forward_geom(p);
+    p->last_launches = 0;
     for (int d0 = 0; d0 < ndens;) {
         const int nd = chunk_for(ndens - d0, p->nd_cap);
+        // charges, P2M, M2M per level, (conversion +) M2L, L2L per level, leaf, output
+        p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
         VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
         p->timer.end(id);
-        VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, p2p_fp64(p),
+        VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, use_fp64(p),
                                      p->timer.on ? &p->timer : nullptr, s));
         id = p->timer.begin("out");
-        VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc, ld_f,
-                                   out + (int64_t)d0 * ld_out, ld_out, s));
+        if (p->grouped) {
+            VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_src, fc, ld_f, p->ws.xf, s));
+            VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_src,
+                                       out + (int64_t)d0 * ld_out, ld_out, s));
+            p->last_launches += 1;
+        } else {
+            VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc,
+                                       ld_f, out + (int64_t)d0 * ld_out, ld_out, s));
+        }
         p->timer.end(id);
         d0 += nd;
     }
@@ -639,9 +831,15 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* gc = g + (int64_t)d0 * ld_g;
             VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
-            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, p2p_fp64(p), nullptr, s));
-            VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr, p->crow,
-                                       p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
+            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, use_fp64(p), nullptr, s));
+            if (p->grouped) {
+                VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
+                VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
+                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
+            } else {
+                VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr,
+                                           p->crow, p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
+            }
             d0 += nd;
         }
     }
@@ -651,7 +849,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* fc = f + (int64_t)d0 * ld_f;
             VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
-            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, true, nullptr, s));
+            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, use_fp64(p), nullptr, s));
             VP_CUDA(launch_grad_out(nd, d0 > 0, (int32_t)p->n_tgt, p->tgt_perm, p->ws.psi, g + (int64_t)d0 * ld_g,
                                     ld_g, grad_tgt, s));
             d0 += nd;
@@ -715,6 +913,7 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->n_w_pairs = nw;
     o->n_x_pairs = (int64_t)T.x_idx.size();
     o->p2p_pairs = p->p2p_pairs;
+    o->last_launches = p->last_launches;
     o->root[0] = T.x0;
     o->root[1] = T.y0;
     o->root[2] = T.side;

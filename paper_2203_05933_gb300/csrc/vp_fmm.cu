@@ -20,8 +20,10 @@
 // zeta is the child-centre offset over the parent half-side, (+-1 +- i)/2.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
+#include "vp_ff.cuh"
 #include "vp_internal.h"
 
 namespace vp {
@@ -322,6 +324,317 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // ----------------------------------------------------------------------------
+// a3/a5 on the FP32 pipes: P2M, M2M and L2L with float-float expansions (same
+// operators as the FP64 kernels above; zeta powers are exact in float).
+//
+// P2M: u = (z - c)/R = 2 rho, rho the leaf-relative coordinate (hi/lo floats).
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_p2m_ff(DevTree t, DevTables tab, PassGeom g, const float2* __restrict__ qf, float4* __restrict__ Mf)
+{
+    constexpr int P1 = P + 1;
+    __shared__ float4 pw[kWarpsPerBlock][kChunk][P1];
+    __shared__ float2 qs[kWarpsPerBlock][kChunk][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int ll = lane <= P ? lane : P;
+    const ff::F minvl = ff::neg(ff::F{tab.invlf[ll].x, tab.invlf[ll].y});
+    for (int li = global_warp(); li < t.nleaf; li += num_warps()) {
+        const int b = t.leaves[li];
+        const int s0 = g.crng[2 * b], s1 = g.crng[2 * b + 1];
+        ff::C acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+        for (int base = s0; base < s1; base += kChunk) {
+            const int n = min(kChunk, s1 - base);
+            if (lane < n) {
+                const float4 r = g.crho[base + lane];
+                const ff::C u{{2.f * r.x, 2.f * r.y}, {2.f * r.z, 2.f * r.w}};
+                ff::C p{{1.f, 0.f}, {0.f, 0.f}};
+                pw[wb][lane][0] = ff::to_float4(p);
+                for (int k = 1; k <= P; ++k) {
+                    p = ff::cnorm(ff::cmul(p, u));
+                    pw[wb][lane][k] = ff::to_float4(p);
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) qs[wb][lane][d] = qf[(int64_t)(base + lane) * ND + d];
+            }
+            __syncwarp();
+            if (lane <= P) {
+                for (int j = 0; j < n; ++j) {
+                    const float4 pv = pw[wb][j][lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const ff::F qq{qs[wb][j][d].x, qs[wb][j][d].y};
+                        acc[d].re = ff::add(acc[d].re, ff::mul(qq, ff::F{pv.x, pv.y}));
+                        acc[d].im = ff::add(acc[d].im, ff::mul(qq, ff::F{pv.z, pv.w}));
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = ff::cnorm(acc[d]);
+            }
+            __syncwarp();
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                ff::C m = acc[d];
+                if (lane > 0) m = ff::cnorm(ff::C{ff::mul(m.re, minvl), ff::mul(m.im, minvl)});
+                Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(m);
+            }
+        }
+    }
+}
+
+// complex float-float times an exact float complex (a power of zeta: every
+// component is 0 or a power of two, so each product below is exact)
+__device__ __forceinline__ ff::C cmul_exact(ff::C a, float zx, float zy)
+{
+    const ff::F ax{__fmul_rn(a.re.h, zx), __fmul_rn(a.re.l, zx)}, ay{__fmul_rn(a.re.h, zy), __fmul_rn(a.re.l, zy)};
+    const ff::F bx{__fmul_rn(a.im.h, zx), __fmul_rn(a.im.l, zx)}, by{__fmul_rn(a.im.h, zy), __fmul_rn(a.im.l, zy)};
+    return ff::C{ff::add(ax, ff::neg(by)), ff::add(ay, bx)};
+}
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_m2m_ff(DevTree t, DevTables tab, int b0, int b1, float4* __restrict__ Mf)
+{
+    constexpr int P1 = P + 1;
+    __shared__ float4 Ms[kWarpsPerBlock][P1][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int ll = lane <= P ? lane : P;
+    const ff::F minvl = ff::neg(ff::F{tab.invlf[ll].x, tab.invlf[ll].y});
+    for (int b = b0 + global_warp(); b < b1; b += num_warps()) {
+        if (t.is_leaf[b]) continue;
+        ff::C acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+        for (int c = 0; c < 4; ++c) {
+            const int ch = t.child[4 * b + c];
+            if (ch < 0) continue;
+            if (lane <= P) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) Ms[wb][lane][d] = Mf[((int64_t)ch * P1 + lane) * ND + d];
+            }
+            __syncwarp();
+            if (lane <= P) {
+                const float2* zp = tab.zpowf + c * P1;
+                if (lane == 0) {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d] = ff::cadd(acc[d], ff::from_float4(Ms[wb][0][d]));
+                } else {
+                    const float2 zl = zp[lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 m0 = Ms[wb][0][d];
+                        const ff::F a = ff::mul(ff::F{m0.x, m0.y}, minvl);  // -M_0 / l (M_0 is real)
+                        acc[d] = ff::cadd(acc[d], cmul_exact(ff::C{a, {0.f, 0.f}}, zl.x, zl.y));
+                    }
+                    for (int k = 1; k <= lane; ++k) {
+                        const float2 bv = tab.Bmf[lane * P1 + k];
+                        const float2 z = zp[lane - k];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const ff::C mk = ff::from_float4(Ms[wb][k][d]);
+                            const ff::C bm{ff::mul(mk.re, ff::F{bv.x, bv.y}), ff::mul(mk.im, ff::F{bv.x, bv.y})};
+                            acc[d] = ff::cadd(acc[d], cmul_exact(bm, z.x, z.y));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = ff::cnorm(acc[d]);
+            }
+            __syncwarp();
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(acc[d]);
+        }
+    }
+}
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_l2l_ff(DevTree t, DevTables tab, int b0, int b1, float4* __restrict__ Lf)
+{
+    constexpr int P1 = P + 1;
+    __shared__ float4 Ls[kWarpsPerBlock][P1][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int b = b0 + global_warp(); b < b1; b += num_warps()) {
+        const int p = t.parent[b];
+        const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) Ls[wb][lane][d] = Lf[((int64_t)p * P1 + lane) * ND + d];
+        }
+        __syncwarp();
+        if (lane <= P) {
+            const float2* zp = tab.zpowf + cq * P1;
+            ff::C acc[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+            for (int k = lane; k <= P; ++k) {
+                const float2 bv = tab.Blf[lane * P1 + k];
+                const float2 z = zp[k - lane];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const ff::C lk = ff::from_float4(Ls[wb][k][d]);
+                    const ff::C bl{ff::mul(lk.re, ff::F{bv.x, bv.y}), ff::mul(lk.im, ff::F{bv.x, bv.y})};
+                    acc[d] = ff::cadd(acc[d], cmul_exact(bl, z.x, z.y));
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const int64_t i = ((int64_t)b * P1 + lane) * ND + d;
+                Lf[i] = ff::to_float4(ff::cnorm(ff::cadd(ff::from_float4(Lf[i]), acc[d])));
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// a4 on the FP32 pipes: the same M2L as k_m2l (scaled Hankel form), with the
+// multipoles, operator tables and the per-box accumulators in float-float
+// (about 48 significant bits). One warp per target box, lane l owns L_l; the
+// X-list P2L stays in FP64 (it is rare: adaptive refinement boundaries only).
+template <int P, int ND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_m2l_ff(DevTree t, DevTables tab, PassGeom g, const float4* __restrict__ Mf, float4* __restrict__ Lf,
+             const double* __restrict__ q)
+{
+    constexpr int P1 = P + 1;
+    using S = M2LSmem<P, ND>;
+    __shared__ float2 Hs[P1 * P1];
+    __shared__ double2 buf[kWarpsPerBlock][S::kUnion];  // V-list staging or P2L powers (not both at once)
+    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) Hs[i] = tab.Hf[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    float4(*As)[ND] = reinterpret_cast<float4(*)[ND]>(&buf[wb][0]);
+    double2(*pw)[P1] = reinterpret_cast<double2(*)[P1]>(&buf[wb][0]);
+    double* qs = reinterpret_cast<double*>(&buf[wb][S::kPw]);
+    double* lgs = qs + kChunk * ND;
+    const double inv_l = lane == 0 ? 0.0 : 1.0 / (double)lane;
+    const int ll = lane <= P ? lane : P;
+    const ff::F invlf = ff::F{tab.invlf[ll].x, tab.invlf[ll].y};
+
+    for (int b = global_warp(); b < t.nbox; b += num_warps()) {
+        ff::C lacc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) lacc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+        const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
+        const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
+        const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
+        const ff::F logR = ff::from_double(t.log_radius[b]);
+        for (int e = v0; e < v1; ++e) {
+            const int C = t.v_idx[e];
+            const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+            if (lane <= P) {
+                const ff::C mt = ff::from_float4(tab.mtpowf[o * P1 + lane]);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const ff::C m = ff::from_float4(Mf[((int64_t)C * P1 + lane) * ND + d]);
+                    As[lane][d] = ff::to_float4(lane == 0 ? m : ff::cnorm(ff::cmul(m, mt)));
+                }
+            }
+            __syncwarp();
+            if (lane <= P) {
+                ff::C acc[ND];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+                for (int k = 1; k <= P; ++k) {
+                    const float2 hv = Hs[lane * P1 + k];
+                    const ff::F h{hv.x, hv.y};
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 a = As[k][d];
+                        acc[d].re = ff::add(acc[d].re, ff::mul(h, ff::F{a.x, a.y}));
+                        acc[d].im = ff::add(acc[d].im, ff::mul(h, ff::F{a.z, a.w}));
+                    }
+                }
+                if (lane == 0) {
+                    const float2 lo = tab.log2of[o];
+                    const ff::F lz = ff::add(logR, ff::F{lo.x, lo.y});
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 a0 = As[0][d];
+                        lacc[d].re = ff::add(lacc[d].re, ff::add(acc[d].re, ff::mul(ff::F{a0.x, a0.y}, lz)));
+                        lacc[d].im = ff::add(lacc[d].im, acc[d].im);
+                    }
+                } else {
+                    const ff::C tl = ff::from_float4(tab.tpowf[o * P1 + lane]);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 a0 = As[0][d];
+                        const ff::C a{ff::add(acc[d].re, ff::neg(ff::mul(ff::F{a0.x, a0.y}, invlf))),
+                                      ff::add(acc[d].im, ff::neg(ff::mul(ff::F{a0.z, a0.w}, invlf)))};
+                        lacc[d] = ff::cadd(lacc[d], ff::cmul(tl, ff::cnorm(a)));
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) lacc[d] = ff::cnorm(lacc[d]);
+            }
+            __syncwarp();
+        }
+        double2 l64[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) l64[d] = make_double2(0.0, 0.0);
+        if (x1 > x0) {
+            const double2 c = t.center[b];
+            const double R = t.radius[b];
+            for (int e = x0; e < x1; ++e) {
+                const int C = t.x_idx[e];
+                const int s0 = g.crng[2 * C], s1 = g.crng[2 * C + 1];
+                for (int base = s0; base < s1; base += kChunk) {
+                    const int n = min(kChunk, s1 - base);
+                    if (lane < n) {
+                        const double2 z = g.cxy[base + lane];
+                        const double dx = z.x - c.x, dy = z.y - c.y;
+                        const double r2 = dx * dx + dy * dy;
+                        const double sr = R / r2;
+                        const double2 v = make_double2(dx * sr, -dy * sr);
+                        double2 p = make_double2(1.0, 0.0);
+                        pw[lane][0] = p;
+#pragma unroll 4
+                        for (int k = 1; k <= P; ++k) {
+                            p = cmul(p, v);
+                            pw[lane][k] = p;
+                        }
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) qs[lane * ND + d] = q[(int64_t)(base + lane) * ND + d];
+                        lgs[lane] = 0.5 * log(r2);
+                    }
+                    __syncwarp();
+                    if (lane <= P) {
+                        for (int j = 0; j < n; ++j) {
+                            if (lane == 0) {
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) l64[d].x = fma(qs[j * ND + d], lgs[j], l64[d].x);
+                            } else {
+                                const double2 pv = pw[j][lane];
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) {
+                                    const double cq = -qs[j * ND + d] * inv_l;
+                                    l64[d].x = fma(cq, pv.x, l64[d].x);
+                                    l64[d].y = fma(cq, pv.y, l64[d].y);
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                ff::C v = lacc[d];
+                if (x1 > x0) v = ff::cnorm(ff::cadd(v, ff::from_double2(l64[d])));
+                Lf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(v);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
 // a5: L2L from parents into the boxes of one level, one warp per child.
 template <int P, int ND>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
@@ -516,28 +829,22 @@ __global__ void __launch_bounds__(kLeafThreads)
 // Absolute error of one log r2 is below about 3e-12; the result is converted
 // to FP64 once per target and combined with the leaf-size term
 // log(side) * (sum of the U-list charges minus coincident ones).
-namespace ff {
+namespace fflog {
 
 constexpr float kLn2Hi = 363409.0f / 524288.0f;  // ln 2 rounded to 19 fractional bits
 constexpr float kLn2Lo = 1.0f * (float)(0.693147180559945309417232121458176568 - 363409.0 / 524288.0);
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-}  // namespace ff
+}  // namespace fflog
 
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafThreads)
     k_leaf_ff(DevTree t, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
-              const double2* __restrict__ M, const double2* __restrict__ L, const float4* __restrict__ logtab,
+              const float4* __restrict__ Mf, const float4* __restrict__ Lf, const float4* __restrict__ logtab,
               double* __restrict__ psi)
 {
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1][ND];
+    __shared__ float4 s_L[P1 * ND];
     __shared__ float4 s_rho[kLeafThreads];
     __shared__ float2 s_q[kLeafThreads][ND];
     __shared__ double s_qd[kLeafThreads][ND];
@@ -565,24 +872,27 @@ __global__ void __launch_bounds__(kLeafThreads)
 #pragma unroll
             for (int d = 0; d < ND; ++d) acc[d] = 0.0;
 
-            // L2P (FP64)
+            // L2P (float-float, u = 2 rho_t)
+            const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncthreads();
-            for (int i = tid; i < P1 * ND; i += kLeafThreads) (&Cs[0][0])[i] = L[(int64_t)b * P1 * ND + i];
+            for (int i = tid; i < P1 * ND; i += kLeafThreads) s_L[i] = Lf[(int64_t)b * P1 * ND + i];
             __syncthreads();
             if (valid) {
-                const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
+                const ff::C u{{2.f * rt.x, 2.f * rt.y}, {2.f * rt.z, 2.f * rt.w}};
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    double2 s = Cs[P][d];
-                    for (int l = P - 1; l >= 0; --l) s = cfma(s, u, Cs[l][d]);
-                    acc[d] += s.x;
+                    ff::C sacc = ff::from_float4(s_L[P * ND + d]);
+                    for (int l = P - 1; l >= 0; --l)
+                        sacc = ff::cnorm(ff::cadd(ff::cmul(sacc, u), ff::from_float4(s_L[l * ND + d])));
+                    acc[d] += ff::to_double(sacc.re);
                 }
             }
-            // M2P over W (FP64)
+            // M2P over W (FP64; the multipole is converted once per block)
             for (int e = w0; e < w1; ++e) {
                 const int D = t.w_idx[e];
                 __syncthreads();
-                for (int i = tid; i < P1 * ND; i += kLeafThreads) (&Cs[0][0])[i] = M[(int64_t)D * P1 * ND + i];
+                for (int i = tid; i < P1 * ND; i += kLeafThreads)
+                    (&Cs[0][0])[i] = ff::to_double2(ff::from_float4(Mf[(int64_t)D * P1 * ND + i]));
                 __syncthreads();
                 if (valid) {
                     const double2 cD = t.center[D];
@@ -601,7 +911,6 @@ __global__ void __launch_bounds__(kLeafThreads)
             }
 
             // P2P over U (float-float)
-            const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
             float ah[ND], al[ND];
             double qsum[ND], qco[ND];
 #pragma unroll
@@ -679,7 +988,7 @@ __global__ void __launch_bounds__(kLeafThreads)
                                 const float uh = __fsub_rn(Pm, 1.0f);
                                 const float ul = fmaf(ml, tk.x, Pe);
                                 const float ef = __fsub_rn(__int_as_float(0x4B400000 + ex), 12582912.0f);
-                                const float hi = fmaf(ef, ff::kLn2Hi, tk.y);
+                                const float hi = fmaf(ef, fflog::kLn2Hi, tk.y);
                                 const float uhh = __fsub_rn(__fadd_rn(uh, 24.0f), 24.0f);
                                 const float uhl = __fsub_rn(uh, uhh);
                                 S = __fadd_rn(hi, uhh);
@@ -693,7 +1002,7 @@ __global__ void __launch_bounds__(kLeafThreads)
                                 tt = __fadd_rn(tt, tk.z);
                                 tt = __fadd_rn(tt, uhl);
                                 tt = fmaf(-0.5f, s2, tt);
-                                lo = fmaf(ef, ff::kLn2Lo, tt);
+                                lo = fmaf(ef, fflog::kLn2Lo, tt);
                             } else {
                                 const double ld = log((double)r2h + (double)r2l);
                                 S = __double2float_rn(ld);
@@ -834,48 +1143,61 @@ __global__ void k_grad_out(int32_t n_tgt, int accumulate, const int32_t* __restr
 
 template <int P, int ND>
 cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool gradient,
-                     bool p2p_fp64, PhaseTimer* tm, cudaStream_t s)
+                     bool fp64, PhaseTimer* tm, cudaStream_t s)
 {
     const int threads = kWarpsPerBlock * 32;
+    const bool ffp = !fp64 && !gradient;  // float-float pipeline (potential only)
     int id = tm ? tm->begin("p2m") : -1;
-    k_p2m<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.q, ws.M);
+    if (ffp)
+        k_p2m_ff<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, tab, g, ws.qf, ws.Mf);
+    else
+        k_p2m<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.q, ws.M);
     if (tm) tm->end(id);
     id = tm ? tm->begin("m2m") : -1;
     for (int l = t.nlevels - 2; l >= 0; --l) {
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
-        k_m2m<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.M);
+        if (ffp)
+            k_m2m_ff<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.Mf);
+        else
+            k_m2m<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.M);
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("m2l") : -1;
-    k_m2l<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q);
+    if (ffp)
+        k_m2l_ff<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.Mf, ws.Lf, ws.q);
+    else
+        k_m2l<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q);
     if (tm) tm->end(id);
     id = tm ? tm->begin("l2l") : -1;
     for (int l = 1; l < t.nlevels; ++l) {
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
-        k_l2l<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.L);
+        if (ffp)
+            k_l2l_ff<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.Lf);
+        else
+            k_l2l<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.L);
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
     const int blocks = t.nleaf < 1 ? 1 : (t.nleaf > 152 * 64 ? 152 * 64 : t.nleaf);
     if (gradient)
         k_leaf<P, ND, true><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
-    else if (p2p_fp64)
+    else if (fp64)
         k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
     else
-        k_leaf_ff<P, ND><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.qf, ws.M, ws.L, tab.logtab, ws.psi);
+        k_leaf_ff<P, ND><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi);
     if (tm) tm->end(id);
     return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t fmm_p(int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool grad,
-                  bool p2p_fp64, PhaseTimer* tm, cudaStream_t s)
+                  bool fp64, PhaseTimer* tm, cudaStream_t s)
 {
     switch (nd) {
-        case 1: return fmm_impl<P, 1>(t, tab, g, ws, grad, p2p_fp64, tm, s);
-        case 2: return fmm_impl<P, 2>(t, tab, g, ws, grad, p2p_fp64, tm, s);
-        case 4: return fmm_impl<P, 4>(t, tab, g, ws, grad, p2p_fp64, tm, s);
-        case 8: return fmm_impl<P, 8>(t, tab, g, ws, grad, p2p_fp64, tm, s);
+        case 1: return fmm_impl<P, 1>(t, tab, g, ws, grad, fp64, tm, s);
+        case 2: return fmm_impl<P, 2>(t, tab, g, ws, grad, fp64, tm, s);
+        case 4: return fmm_impl<P, 4>(t, tab, g, ws, grad, fp64, tm, s);
+        case 8: return fmm_impl<P, 8>(t, tab, g, ws, grad, fp64, tm, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -907,12 +1229,12 @@ cudaError_t launch_charges(int nd, int32_t n, const int32_t* perm, const double*
 }
 
 cudaError_t launch_fmm_potential(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g,
-                                 Workspace& ws, bool gradient, bool p2p_fp64, PhaseTimer* timer, cudaStream_t s)
+                                 Workspace& ws, bool gradient, bool fp64, PhaseTimer* timer, cudaStream_t s)
 {
     switch (P) {
-        case 16: return fmm_p<16>(nd, t, tab, g, ws, gradient, p2p_fp64, timer, s);
-        case 24: return fmm_p<24>(nd, t, tab, g, ws, gradient, p2p_fp64, timer, s);
-        case 30: return fmm_p<30>(nd, t, tab, g, ws, gradient, p2p_fp64, timer, s);
+        case 16: return fmm_p<16>(nd, t, tab, g, ws, gradient, fp64, timer, s);
+        case 24: return fmm_p<24>(nd, t, tab, g, ws, gradient, fp64, timer, s);
+        case 30: return fmm_p<30>(nd, t, tab, g, ws, gradient, fp64, timer, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -50,6 +50,15 @@ struct DevTables {
     const double* log2o = nullptr;  // [49] log(2 |o|)                             (M2L)
     const double2* zpow = nullptr;  // [4][P1] zeta_c^m, zeta_c = child offset / R_parent
     const float4* logtab = nullptr; // [128] {1/c_k, T_hi, T_lo, 0}, T = -log(1/c_k)  (P2P log)
+    // float-float copies for the FP32-pipe M2L
+    const float2* Hf = nullptr;     // [P1][P1]
+    const float4* tpowf = nullptr;  // [49][P1] complex (re_h, re_l, im_h, im_l)
+    const float4* mtpowf = nullptr; // [49][P1]
+    const float2* log2of = nullptr; // [49]
+    const float2* invlf = nullptr;  // [P1] 1/l (0 for l = 0)
+    const float2* Bmf = nullptr;    // [P1][P1] C(l-1, k-1) 2^-k as hi/lo
+    const float2* Blf = nullptr;    // [P1][P1] C(k, l) 2^-l as hi/lo
+    const float2* zpowf = nullptr;  // [4][P1] zeta_c^m (exact in float)
 };
 
 // One direction of the FMM: where charges sit and where the potential is taken.
@@ -64,12 +73,29 @@ struct PassGeom {
     int32_t n_eval = 0;
 };
 
+// Correction matrix with consecutive rows that share one column list grouped
+// together (the rows of one cell couple to the same near cells), and values
+// as hi/lo float pairs. Rows are in caller order.
+struct DevGroupedCSR {
+    int32_t nrows = 0;
+    int32_t ngroups = 0;
+    int32_t max_m = 0;                 // longest column list
+    const int32_t* g_r0 = nullptr;     // [ngroups + 1] first row of each group
+    const int64_t* g_c0 = nullptr;     // [ngroups + 1] offsets into cols
+    const int32_t* cols = nullptr;     // column list of each group
+    const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf
+    const float2* vf = nullptr;        // [nnz] values as hi/lo floats
+};
+
 struct Workspace {
     double* q = nullptr;      // [max(n_src, n_tgt)][ND] charges, tree order
     float2* qf = nullptr;     // [max(n_src, n_tgt)][ND] the same charges as hi/lo float pairs
     double2* M = nullptr;     // [nbox][P1][ND] multipole coefficients (scaled)
+    float4* Mf = nullptr;     // [nbox][P1][ND] multipoles as float-float complex (re_h, re_l, im_h, im_l)
+    float4* Lf = nullptr;     // [nbox][P1][ND] locals as float-float complex
     double2* L = nullptr;     // [nbox][P1][ND] local coefficients (scaled)
     double* psi = nullptr;    // [max(n_src, n_tgt)][2][ND] potential (or gradient) in tree order
+    float2* xf = nullptr;     // [ND][max(n_src, n_tgt)] correction input (f or g) as hi/lo floats
     int32_t nd_cap = 0;
 };
 
@@ -87,9 +113,9 @@ struct PhaseTimer {
 // Launchers (vp_fmm.cu). All enqueue on `s`; nd is the density chunk (1, 2, 4 or 8).
 cudaError_t launch_charges(int nd, int32_t n, const int32_t* perm, const double* w_sorted,
                            const double* f, int64_t ld_f, double* q, float2* qf, cudaStream_t s);
-// p2p_fp64: evaluate the near field with FP64 log instead of the float-float path
+// fp64: run the near field and M2L in FP64 instead of on the float-float paths
 cudaError_t launch_fmm_potential(int P, int nd, const DevTree& t, const DevTables& tab,
-                                 const PassGeom& g, Workspace& ws, bool gradient, bool p2p_fp64,
+                                 const PassGeom& g, Workspace& ws, bool gradient, bool fp64,
                                  PhaseTimer* timer, cudaStream_t s);
 cudaError_t launch_out_forward(int nd, int32_t n_tgt, const int32_t* tgt_inv, const double* psi,
                                const int64_t* rowptr, const int32_t* col, const double* val,
@@ -102,6 +128,13 @@ cudaError_t launch_out_adjoint(int nd, int32_t n_src, const int32_t* src_inv, co
 cudaError_t launch_grad_out(int nd, bool accumulate, int32_t n_tgt, const int32_t* tgt_perm,
                             const double* gpsi, const double* g, int64_t ld_g, double* grad,
                             cudaStream_t s);
+
+// Correction apply on the FP32 pipes (vp_spmv.cu): out[d][r] = -(1/2pi) w psi[inv[r]][d] + (A x)[d][r]
+// for every row r of A, w = w_sorted[inv[r]] or 1 when w_sorted is NULL.
+cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, float2* xf, cudaStream_t s);
+cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
+                               const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
+                               cudaStream_t s);
 
 bool p_supported(int P);
 

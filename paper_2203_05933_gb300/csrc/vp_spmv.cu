@@ -1,0 +1,130 @@
+// Correction apply (a7): out = -(1/2pi) psi + Pi f, the sparse map of the
+// per-cell corrections "accurate minus smooth" (arXiv 2203.05933, Sec. 4,
+// paragraph after Eq. nsrcs), on the FP32 pipes in float-float arithmetic.
+//
+// The rows of one cell share their column list (every node of a cell couples
+// to the nodes of the same near cells), so the plan stores each distinct
+// column list once per group of consecutive rows. One block per group gathers
+// x[:, cols] once into shared memory as hi/lo floats; each warp then streams
+// its rows' values (8 bytes per nonzero, coalesced) and accumulates with
+// TwoProd/TwoSum. HBM traffic is one read of the values plus the outputs.
+#include <cuda_runtime.h>
+
+#include "vp_ff.cuh"
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+constexpr double kInv2PiG = 0.159154943091895335768883763372514362;
+constexpr int kGroupThreads = 256;
+constexpr int kGroupSmemBytes = 96 * 1024;
+
+__global__ void k_to_ff_rows(int64_t total, int32_t n, const double* __restrict__ x, int64_t ld_x,
+                             float2* __restrict__ xf)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = i / n, j = i % n;
+        const ff::F v = ff::from_double(x[d * ld_x + j]);
+        xf[i] = make_float2(v.h, v.l);
+    }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(kGroupThreads)
+    k_out_grouped(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
+                  const double* __restrict__ psi, const float2* __restrict__ xf, int64_t ld_xf,
+                  double* __restrict__ out, int64_t ld_out)
+{
+    extern __shared__ float2 F[];  // [smem_m][ND]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int gi = blockIdx.x; gi < A.ngroups; gi += gridDim.x) {
+        const int r0 = A.g_r0[gi], r1 = A.g_r0[gi + 1];
+        const int64_t c0 = A.g_c0[gi];
+        const int m = (int)(A.g_c0[gi + 1] - c0);
+        const bool staged = m <= smem_m;
+        __syncthreads();
+        if (staged) {
+            for (int i = threadIdx.x; i < m * ND; i += blockDim.x) {
+                const int k = i / ND, d = i % ND;
+                F[i] = xf[d * ld_xf + A.cols[c0 + k]];
+            }
+        }
+        __syncthreads();
+        for (int r = r0 + warp; r < r1; r += nw) {
+            const int64_t v0 = A.rowptr[r];
+            ff::F acc[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = ff::F{0.f, 0.f};
+            for (int k = lane; k < m; k += 32) {
+                const float2 v = A.vf[v0 + k];
+                const ff::F vv{v.x, v.y};
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const float2 x = staged ? F[k * ND + d] : xf[d * ld_xf + A.cols[c0 + k]];
+                    acc[d] = ff::add(acc[d], ff::mul(vv, ff::F{x.x, x.y}));
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float h = __shfl_xor_sync(0xffffffffu, acc[d].h, o);
+                    const float l = __shfl_xor_sync(0xffffffffu, acc[d].l, o);
+                    acc[d] = ff::add(acc[d], ff::F{h, l});
+                }
+            }
+            if (lane == 0) {
+                const int32_t ri = inv[r];
+                const double wv = w_sorted ? w_sorted[ri] : 1.0;
+#pragma unroll
+                for (int d = 0; d < ND; ++d)
+                    out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[d]));
+            }
+        }
+    }
+}
+
+template <int ND>
+cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
+                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_out_grouped<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGroupSmemBytes);
+    if (e != cudaSuccess) return e;
+    int smem_m = kGroupSmemBytes / (ND * (int)sizeof(float2));
+    if (A.max_m < smem_m) smem_m = A.max_m;
+    if (smem_m < 1) smem_m = 1;
+    const size_t bytes = (size_t)smem_m * ND * sizeof(float2);
+    int blocks = A.ngroups < 152 * 16 ? A.ngroups : 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_out_grouped<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, xf, ld_xf, out, ld_out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, float2* xf, cudaStream_t s)
+{
+    const int64_t total = (int64_t)nd * n;
+    if (total == 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_to_ff_rows<<<(int)blocks, 256, 0, s>>>(total, n, x, ld_x, xf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
+                               const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
+                               cudaStream_t s)
+{
+    switch (nd) {
+        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vp

@@ -21,7 +21,7 @@ _lib = None
 
 VP_OK = 0
 VP_FLAG_TIMING = 1
-VP_FLAG_P2P_FP64 = 2
+VP_FLAG_FP64 = 2
 
 TREE_ARRAYS = {
     "box_level": 0, "box_ixy": 1, "box_parent": 2, "box_leaf": 3, "box_src": 4, "box_tgt": 5,
@@ -56,7 +56,8 @@ class vp_plan_stats(ctypes.Structure):
                 ("p_fmm", ctypes.c_int32), ("leaf", ctypes.c_int32), ("max_dens", ctypes.c_int32),
                 ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("n_u_pairs", ctypes.c_int64), ("n_v_pairs", ctypes.c_int64), ("n_w_pairs", ctypes.c_int64),
-                ("n_x_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("root", ctypes.c_double * 3)]
+                ("n_x_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("last_launches", ctypes.c_int64),
+                ("root", ctypes.c_double * 3)]
 
 
 def library_path() -> str:

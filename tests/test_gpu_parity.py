@@ -233,18 +233,18 @@ def test_disk_1M_sampled_targets(P):
 
 
 @pytest.mark.parametrize("leaf,seed", [(8, 41), (32, 42), (64, 43)])
-def test_float_float_near_field_matches_fp64(leaf, seed):
-    # the default near field (float-float log) against the FP64-log near field on
-    # the same plan: agreement far below the 1e-10 gate shows the float-float
+def test_float_float_paths_match_fp64(leaf, seed):
+    # the default float-float near field and M2L against the all-FP64 kernels on
+    # the same tree: agreement far below the 1e-10 gate shows the float-float
     # evaluation keeps FP64-level accuracy
     prob = inputs.cloud_problem(4000, 3000, ndens=3, shared=800, seed=seed)
     f = torch.as_tensor(prob.f, device="cuda")
     outs = []
-    for flags in (0, vp.VP_FLAG_P2P_FP64):
+    for flags in (0, vp.VP_FLAG_FP64):
         plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=leaf, max_dens=4,
                               flags=flags)
         outs.append(plan.eval(f).cpu().numpy())
         plan.close()
     diff = rel_err(prob, outs[0], outs[1])
-    print(f"float-float vs FP64 near field, leaf={leaf}: {diff:.3e}")
+    print(f"float-float vs FP64 kernels, leaf={leaf}: {diff:.3e}")
     assert diff <= 1e-12
