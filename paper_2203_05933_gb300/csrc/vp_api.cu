@@ -215,6 +215,27 @@ std::vector<float> make_ff_tables(int P, size_t off[8])
     return v;
 }
 
+// For each entry (b, A) of an interaction list: the centre of box A relative to
+// the centre of box b in units of b's side, and side_A / side_b. Both are exact
+// dyadic numbers: with dl = level_b - level_A,
+// (c_A - c_b)/side_b = K 2^(min(dl,0) - 1), K = (2 ix_A + 1) 2^max(dl,0) - (2 ix_b + 1) 2^max(-dl,0).
+std::vector<float> make_list_offsets(const Tree& T, const std::vector<int32_t>& ptr, const std::vector<int32_t>& idx)
+{
+    std::vector<float> o(idx.size() * 4, 0.0f);
+    for (int64_t b = 0; b + 1 < (int64_t)ptr.size(); ++b)
+        for (int32_t e = ptr[(size_t)b]; e < ptr[(size_t)b + 1]; ++e) {
+            const int32_t a = idx[(size_t)e];
+            const int dl = T.level[(size_t)b] - T.level[(size_t)a];
+            const int up = dl > 0 ? dl : 0, dn = dl < 0 ? -dl : 0;
+            const int64_t kx = (2LL * T.ix[(size_t)a] + 1) * (1LL << up) - (2LL * T.ix[(size_t)b] + 1) * (1LL << dn);
+            const int64_t ky = (2LL * T.iy[(size_t)a] + 1) * (1LL << up) - (2LL * T.iy[(size_t)b] + 1) * (1LL << dn);
+            o[4 * (size_t)e + 0] = (float)std::ldexp((double)kx, (dl < 0 ? dl : 0) - 1);
+            o[4 * (size_t)e + 1] = (float)std::ldexp((double)ky, (dl < 0 ? dl : 0) - 1);
+            o[4 * (size_t)e + 2] = (float)std::ldexp(1.0, dl);
+        }
+    return o;
+}
+
 // Leaf-relative coordinates of every point of each leaf: ((x, y) - centre)/side,
 // each component split into hi + lo floats.
 std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted, bool sources)
@@ -605,6 +626,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     size_t offf[8];
     std::vector<float> fftab = make_ff_tables(P, offf);
     std::vector<float> srho = make_rho(T, sxy, true), trho = make_rho(T, txy, false);
+    std::vector<float> uoff = make_list_offsets(T, T.u_ptr, T.u_idx), xoff = make_list_offsets(T, T.x_ptr, T.x_idx);
 
     cudaError_t e = cudaSuccess;
     auto up = [&](auto** dst, const auto& h) {
@@ -651,6 +673,9 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     up(&d_srho, srho);
     up(&d_trho, trho);
     up(&d_level, T.level);
+    float *d_uoff = nullptr, *d_xoff = nullptr;
+    up(&d_uoff, uoff);
+    up(&d_xoff, xoff);
     p->src_rho = (float4*)d_srho;
     p->tgt_rho = (float4*)d_trho;
     p->grouped = has_corr && !(p->flags & VP_FLAG_FP64);
@@ -721,6 +746,8 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     dt.leaves = d_leaves;
     dt.u_ptr = d_up;
     dt.u_idx = d_ui;
+    dt.u_off = (const float4*)d_uoff;
+    dt.x_off = (const float4*)d_xoff;
     dt.v_ptr = d_vp;
     dt.v_idx = d_vi;
     dt.w_ptr = d_wp;
@@ -747,7 +774,8 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     {
         const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
-                               p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf};
+                               p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf,
+                               p->dt.u_off, p->dt.x_off};
         const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
                               p->gfwd.vf, p->gadj.vf};
         bool ok = true;

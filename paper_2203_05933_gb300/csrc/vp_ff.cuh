@@ -83,3 +83,73 @@ __device__ __forceinline__ double2 to_double2(C a) { return make_double2(to_doub
 
 }  // namespace ff
 }  // namespace vp
+
+namespace vp {
+namespace ff {
+
+// ln 2 split for the exponent term of the table log: kLn2Hi has 19 fractional
+// bits, so e * kLn2Hi + T_hi is exact in one float for |e| <= 15.
+constexpr float kLn2Hi = 363409.0f / 524288.0f;
+constexpr float kLn2Lo = (float)(0.693147180559945309417232121458176568 - 363409.0 / 524288.0);
+
+// log(x) for x = xh + xl > 0 given as a float pair, as (S, lo) with S + lo
+// accurate to about 1.3e-12 absolute: x = 2^e m (m in [1, 2)), k = top 7 bits of
+// m, u = m / c_k - 1 (|u| <= 2^-8), log x = e ln2 + T_k + log1p(u) with the
+// series to u^6. tab[k] = {fl(1/c_k), T_hi, T_lo, 0}, c_k = 1 + (k + 1/2)/128,
+// T = -log(fl(1/c_k)) (T_hi rounded to 19 fractional bits). Values with |e| > 15
+// (or xh = 0) take an FP64 log.
+__device__ __forceinline__ void log_pair(float xh, float xl, const float4* tab, float& S, float& lo)
+{
+    const int bits = __float_as_int(xh);
+    const int ex = (bits >> 23) - 127;
+    if (xh > 0.0f && (unsigned)(ex + 15) <= 30u) {
+        const float4 tk = tab[(bits >> 16) & 127];
+        const float mh = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+        const float ml = __fmul_rn(xl, __int_as_float((127 - ex) << 23));
+        const float Pm = __fmul_rn(mh, tk.x);
+        const float Pe = fmaf(mh, tk.x, -Pm);
+        const float uh = __fsub_rn(Pm, 1.0f);
+        const float ul = fmaf(ml, tk.x, Pe);
+        const float ef = __fsub_rn(__int_as_float(0x4B400000 + ex), 12582912.0f);
+        const float hi = fmaf(ef, kLn2Hi, tk.y);
+        const float uhh = __fsub_rn(__fadd_rn(uh, 24.0f), 24.0f);
+        const float uhl = __fsub_rn(uh, uhh);
+        S = __fadd_rn(hi, uhh);
+        const float s2 = __fmul_rn(uh, uh);
+        const float s2e = fmaf(uh, uh, -s2);
+        const float poly = fmaf(uh, fmaf(uh, fmaf(uh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f);
+        float tt = __fmul_rn(__fmul_rn(s2, uh), poly);
+        tt = fmaf(-uh, ul, tt);
+        tt = fmaf(-0.5f, s2e, tt);
+        tt = __fadd_rn(tt, ul);
+        tt = __fadd_rn(tt, tk.z);
+        tt = __fadd_rn(tt, uhl);
+        tt = fmaf(-0.5f, s2, tt);
+        lo = fmaf(ef, kLn2Lo, tt);
+    } else {
+        const double ld = log((double)xh + (double)xl);
+        S = __double2float_rn(ld);
+        lo = __double2float_rn(ld - (double)S);
+    }
+}
+
+// 1 / x for x = (xh, xl) > 0: float reciprocal refined by one Newton step in
+// float-float (relative error about 2^-46).
+__device__ __forceinline__ F recip(F x)
+{
+    const float r0 = __frcp_rn(x.h);
+    float e = fmaf(-x.h, r0, 1.0f);  // exact residual of the hi part
+    e = fmaf(-x.l, r0, e);
+    return F{r0, __fmul_rn(r0, e)};
+}
+
+// (offset + scale * (rh + rl)) for an exact float offset and a power-of-two scale
+__device__ __forceinline__ F shift_scale(float off, float scale, float rh, float rl)
+{
+    float s, e;
+    two_sum(off, __fmul_rn(scale, rh), s, e);
+    return F{s, __fadd_rn(e, __fmul_rn(scale, rl))};
+}
+
+}  // namespace ff
+}  // namespace vp

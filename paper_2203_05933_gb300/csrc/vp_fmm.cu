@@ -492,27 +492,38 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
 }
 
-// a4 on the FP32 pipes: the same M2L as k_m2l (scaled Hankel form), with the
-// multipoles, operator tables and the per-box accumulators in float-float
-// (about 48 significant bits). One warp per target box, lane l owns L_l; the
-// X-list P2L stays in FP64 (it is rare: adaptive refinement boundaries only).
+// a4 on the FP32 pipes: the same M2L as k_m2l (scaled Hankel form) and the same
+// X-list P2L, with multipoles, operator tables and accumulators in float-float
+// (about 48 significant bits). One warp per target box, lane l owns L_l.
+constexpr int kChunkF = 8;  // charges staged per step in the float-float P2L
+
+template <int P, int ND>
+struct M2LffSmem {
+    static constexpr int P1 = P + 1;
+    static constexpr int kA = P1 * ND;                                   // V-list staging (float4)
+    static constexpr int kPw = kChunkF * P1;                             // P2L powers (float4)
+    static constexpr int kX = kPw + (kChunkF * (ND + 1) * 2 + 3) / 4;    // + charges and logs (float2)
+    static constexpr int kUnion = kA > kX ? kA : kX;
+};
+
 template <int P, int ND>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_m2l_ff(DevTree t, DevTables tab, PassGeom g, const float4* __restrict__ Mf, float4* __restrict__ Lf,
-             const double* __restrict__ q)
+             const float2* __restrict__ qf)
 {
     constexpr int P1 = P + 1;
-    using S = M2LSmem<P, ND>;
+    using S = M2LffSmem<P, ND>;
     __shared__ float2 Hs[P1 * P1];
-    __shared__ double2 buf[kWarpsPerBlock][S::kUnion];  // V-list staging or P2L powers (not both at once)
+    __shared__ float4 buf[kWarpsPerBlock][S::kUnion];  // V-list staging or P2L powers (never both at once)
+    __shared__ float4 s_tab[128];
     for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) Hs[i] = tab.Hf[i];
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) s_tab[i] = tab.logtab[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     float4(*As)[ND] = reinterpret_cast<float4(*)[ND]>(&buf[wb][0]);
-    double2(*pw)[P1] = reinterpret_cast<double2(*)[P1]>(&buf[wb][0]);
-    double* qs = reinterpret_cast<double*>(&buf[wb][S::kPw]);
-    double* lgs = qs + kChunk * ND;
-    const double inv_l = lane == 0 ? 0.0 : 1.0 / (double)lane;
+    float4(*pw)[P1] = reinterpret_cast<float4(*)[P1]>(&buf[wb][0]);
+    float2* qs = reinterpret_cast<float2*>(&buf[wb][S::kPw]);  // [kChunkF][ND]
+    float2* lgs = qs + kChunkF * ND;                            // [kChunkF]
     const int ll = lane <= P ? lane : P;
     const ff::F invlf = ff::F{tab.invlf[ll].x, tab.invlf[ll].y};
 
@@ -574,50 +585,58 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             }
             __syncwarp();
         }
-        double2 l64[ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) l64[d] = make_double2(0.0, 0.0);
+        // P2L over X: w = (z - c_b)/side_b (exact leaf offset + scaled leaf-relative
+        // coordinate), v = R_b/(z - c_b) = 1/(2w), L_l += -(q/l) v^l,
+        // L_0 += q log|z - c_b| = q (1/2 log|w|^2 + log side_b)
         if (x1 > x0) {
-            const double2 c = t.center[b];
-            const double R = t.radius[b];
+            const ff::F logside = ff::from_double(t.log_radius[b] + 0.693147180559945309417232121458176568);
             for (int e = x0; e < x1; ++e) {
                 const int C = t.x_idx[e];
                 const int s0 = g.crng[2 * C], s1 = g.crng[2 * C + 1];
-                for (int base = s0; base < s1; base += kChunk) {
-                    const int n = min(kChunk, s1 - base);
+                const float4 xo = t.x_off[e];
+                for (int base = s0; base < s1; base += kChunkF) {
+                    const int n = min(kChunkF, s1 - base);
                     if (lane < n) {
-                        const double2 z = g.cxy[base + lane];
-                        const double dx = z.x - c.x, dy = z.y - c.y;
-                        const double r2 = dx * dx + dy * dy;
-                        const double sr = R / r2;
-                        const double2 v = make_double2(dx * sr, -dy * sr);
-                        double2 p = make_double2(1.0, 0.0);
-                        pw[lane][0] = p;
-#pragma unroll 4
+                        const float4 r = g.crho[base + lane];
+                        const ff::F wx = ff::shift_scale(xo.x, xo.z, r.x, r.y);
+                        const ff::F wy = ff::shift_scale(xo.y, xo.z, r.z, r.w);
+                        const ff::F n2 = ff::norm(ff::add(ff::mul(wx, wx), ff::mul(wy, wy)));
+                        const ff::F rn = ff::recip(n2);
+                        const ff::F hr = ff::F{0.5f * rn.h, 0.5f * rn.l};
+                        const ff::C v{ff::norm(ff::mul(wx, hr)), ff::norm(ff::neg(ff::mul(wy, hr)))};
+                        ff::C pwr{{1.f, 0.f}, {0.f, 0.f}};
+                        pw[lane][0] = ff::to_float4(pwr);
                         for (int k = 1; k <= P; ++k) {
-                            p = cmul(p, v);
-                            pw[lane][k] = p;
+                            pwr = ff::cnorm(ff::cmul(pwr, v));
+                            pw[lane][k] = ff::to_float4(pwr);
                         }
+                        float Sl, lol;
+                        ff::log_pair(n2.h, n2.l, s_tab, Sl, lol);
+                        const ff::F lg = ff::norm(ff::add(ff::F{0.5f * Sl, 0.5f * lol}, logside));
+                        lgs[lane] = make_float2(lg.h, lg.l);
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) qs[lane * ND + d] = q[(int64_t)(base + lane) * ND + d];
-                        lgs[lane] = 0.5 * log(r2);
+                        for (int d = 0; d < ND; ++d) qs[lane * ND + d] = qf[(int64_t)(base + lane) * ND + d];
                     }
                     __syncwarp();
                     if (lane <= P) {
                         for (int j = 0; j < n; ++j) {
                             if (lane == 0) {
+                                const ff::F lg{lgs[j].x, lgs[j].y};
 #pragma unroll
-                                for (int d = 0; d < ND; ++d) l64[d].x = fma(qs[j * ND + d], lgs[j], l64[d].x);
+                                for (int d = 0; d < ND; ++d)
+                                    lacc[d].re = ff::add(lacc[d].re, ff::mul(ff::F{qs[j * ND + d].x, qs[j * ND + d].y}, lg));
                             } else {
-                                const double2 pv = pw[j][lane];
+                                const float4 pv = pw[j][lane];
 #pragma unroll
                                 for (int d = 0; d < ND; ++d) {
-                                    const double cq = -qs[j * ND + d] * inv_l;
-                                    l64[d].x = fma(cq, pv.x, l64[d].x);
-                                    l64[d].y = fma(cq, pv.y, l64[d].y);
+                                    const ff::F cq = ff::neg(ff::mul(ff::F{qs[j * ND + d].x, qs[j * ND + d].y}, invlf));
+                                    lacc[d].re = ff::add(lacc[d].re, ff::mul(cq, ff::F{pv.x, pv.y}));
+                                    lacc[d].im = ff::add(lacc[d].im, ff::mul(cq, ff::F{pv.z, pv.w}));
                                 }
                             }
                         }
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) lacc[d] = ff::cnorm(lacc[d]);
                     }
                     __syncwarp();
                 }
@@ -625,11 +644,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
         if (lane <= P) {
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                ff::C v = lacc[d];
-                if (x1 > x0) v = ff::cnorm(ff::cadd(v, ff::from_double2(l64[d])));
-                Lf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(v);
-            }
+            for (int d = 0; d < ND; ++d) Lf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(lacc[d]);
         }
     }
 }
@@ -838,42 +853,33 @@ constexpr float kLn2Lo = 1.0f * (float)(0.693147180559945309417232121458176568 -
 
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafThreads)
-    k_leaf_ff(DevTree t, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
-              const float4* __restrict__ Mf, const float4* __restrict__ Lf, const float4* __restrict__ logtab,
-              double* __restrict__ psi)
+    k_leaf_ff(DevTree t, PassGeom g, const float2* __restrict__ qf, const float4* __restrict__ Mf,
+              const float4* __restrict__ Lf, const float4* __restrict__ logtab, double* __restrict__ psi)
 {
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1][ND];
     __shared__ float4 s_L[P1 * ND];
     __shared__ float4 s_rho[kLeafThreads];
     __shared__ float2 s_q[kLeafThreads][ND];
-    __shared__ double s_qd[kLeafThreads][ND];
     __shared__ float4 s_tab[128];
-    __shared__ double s_red[kLeafThreads / 32][ND];
     const int tid = threadIdx.x;
     for (int i = tid; i < 128; i += kLeafThreads) s_tab[i] = logtab[i];
     for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
         const int b = t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
-        const double2 cb = t.center[b];
-        const double Rb = t.radius[b];
-        const double invRb = 1.0 / Rb;
         const double log_side = t.log_radius[b] + 0.693147180559945309417232121458176568;
-        const int lb = t.level[b];
-        const int ixb = t.ixy[2 * b], iyb = t.ixy[2 * b + 1];
         const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
         for (int tb = e0; tb < e1; tb += kLeafThreads) {
             const int ti = tb + tid;
             const bool valid = ti < e1;
-            const double2 z = valid ? g.exy[ti] : cb;
+            const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
             double acc[ND];
 #pragma unroll
             for (int d = 0; d < ND; ++d) acc[d] = 0.0;
 
-            // L2P (float-float, u = 2 rho_t)
-            const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+            // L2P (float-float, u = (z - c)/R = 2 rho_t)
             __syncthreads();
             for (int i = tid; i < P1 * ND; i += kLeafThreads) s_L[i] = Lf[(int64_t)b * P1 * ND + i];
             __syncthreads();
@@ -887,66 +893,63 @@ __global__ void __launch_bounds__(kLeafThreads)
                     acc[d] += ff::to_double(sacc.re);
                 }
             }
-            // M2P over W (FP64; the multipole is converted once per block)
-            for (int e = w0; e < w1; ++e) {
-                const int D = t.w_idx[e];
-                __syncthreads();
-                for (int i = tid; i < P1 * ND; i += kLeafThreads)
-                    (&Cs[0][0])[i] = ff::to_double2(ff::from_float4(Mf[(int64_t)D * P1 * ND + i]));
-                __syncthreads();
-                if (valid) {
-                    const double2 cD = t.center[D];
-                    const double RD = t.radius[D];
-                    const double dx = z.x - cD.x, dy = z.y - cD.y;
-                    const double r2 = dx * dx + dy * dy;
-                    const double2 v = make_double2(dx / r2 * RD, -dy / r2 * RD);
-                    const double lg = 0.5 * log(r2);
+            // M2P over W (FP64; adaptive refinement boundaries only)
+            if (w1 > w0) {
+                const double2 z = valid ? g.exy[ti] : t.center[b];
+                for (int e = w0; e < w1; ++e) {
+                    const int D = t.w_idx[e];
+                    __syncthreads();
+                    for (int i = tid; i < P1 * ND; i += kLeafThreads)
+                        (&Cs[0][0])[i] = ff::to_double2(ff::from_float4(Mf[(int64_t)D * P1 * ND + i]));
+                    __syncthreads();
+                    if (valid) {
+                        const double2 cD = t.center[D];
+                        const double RD = t.radius[D];
+                        const double dx = z.x - cD.x, dy = z.y - cD.y;
+                        const double r2 = dx * dx + dy * dy;
+                        const double2 v = make_double2(dx / r2 * RD, -dy / r2 * RD);
+                        const double lg = 0.5 * log(r2);
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        double2 s = make_double2(0.0, 0.0);
-                        for (int k = P; k >= 1; --k) s = cmul(cadd(s, Cs[k][d]), v);
-                        acc[d] += fma(Cs[0][d].x, lg, s.x);
+                        for (int d = 0; d < ND; ++d) {
+                            double2 sv = make_double2(0.0, 0.0);
+                            for (int k = P; k >= 1; --k) sv = cmul(cadd(sv, Cs[k][d]), v);
+                            acc[d] += fma(Cs[0][d].x, lg, sv.x);
+                        }
                     }
                 }
             }
 
-            // P2P over U (float-float)
+            // P2P over U (float-float). Coordinates in units of leaf b's side, so
+            // sum q log r = 1/2 sum q log r'^2 + log(side_b) (sum_U q - coincident q);
+            // sum_U q is read from the leaves' monopoles M_0.
             float ah[ND], al[ND];
-            double qsum[ND], qco[ND];
+            ff::F qu[ND], qco[ND];
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 ah[d] = al[d] = 0.f;
-                qsum[d] = qco[d] = 0.0;
+                qu[d] = qco[d] = ff::F{0.f, 0.f};
             }
             for (int e = u0; e < u1; ++e) {
                 const int A = t.u_idx[e];
                 const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
                 if (a0 == a1) continue;
-                // leaf A's centre and scale in units of leaf b (exact dyadic numbers)
-                const int dl = lb - t.level[A];
-                const double sc = ldexp(1.0, dl);
-                const float offx = (float)((2.0 * t.ixy[2 * A] + 1.0) * 0.5 * sc - ((double)ixb + 0.5));
-                const float offy = (float)((2.0 * t.ixy[2 * A + 1] + 1.0) * 0.5 * sc - ((double)iyb + 0.5));
-                const float scf = (float)sc;
+                const float4 uo = t.u_off[e];  // exact offset of leaf A's centre and its scale, in b units
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const float4 m0 = Mf[(int64_t)A * P1 * ND + d];
+                    qu[d] = ff::add(qu[d], ff::F{m0.x, m0.y});
+                }
                 for (int sb = a0; sb < a1; sb += kLeafThreads) {
                     const int n = min(kLeafThreads, a1 - sb);
                     __syncthreads();
                     if (tid < n) {
                         const int j = sb + tid;
                         const float4 r = g.crho[j];
-                        float xh, xl, yh, yl;
-                        ff::two_sum(offx, __fmul_rn(scf, r.x), xh, xl);
-                        xl = __fadd_rn(xl, __fmul_rn(scf, r.y));
-                        ff::two_sum(offy, __fmul_rn(scf, r.z), yh, yl);
-                        yl = __fadd_rn(yl, __fmul_rn(scf, r.w));
-                        s_rho[tid] = make_float4(xh, xl, yh, yl);
+                        const ff::F sx = ff::shift_scale(uo.x, uo.z, r.x, r.y);
+                        const ff::F sy = ff::shift_scale(uo.y, uo.z, r.z, r.w);
+                        s_rho[tid] = make_float4(sx.h, sx.l, sy.h, sy.l);
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) {
-                            s_q[tid][d] = qf[(int64_t)j * ND + d];
-                            const double qv = q[(int64_t)j * ND + d];
-                            s_qd[tid][d] = qv;
-                            qsum[d] += qv;
-                        }
+                        for (int d = 0; d < ND; ++d) s_q[tid][d] = qf[(int64_t)j * ND + d];
                     }
                     __syncthreads();
                     if (valid) {
@@ -973,41 +976,12 @@ __global__ void __launch_bounds__(kLeafThreads)
                             const float r2l = __fsub_rn(re, __fsub_rn(r2h, rs));
                             if (r2h == 0.0f) {  // bitwise-coincident pair: no smooth term
 #pragma unroll
-                                for (int d = 0; d < ND; ++d) qco[d] += s_qd[k][d];
+                                for (int d = 0; d < ND; ++d)
+                                    qco[d] = ff::add(qco[d], ff::F{s_q[k][d].x, s_q[k][d].y});
                                 continue;
                             }
-                            const int bits = __float_as_int(r2h);
-                            const int ex = (bits >> 23) - 127;
                             float S, lo;
-                            if ((unsigned)(ex + 15) <= 30u) {
-                                const float4 tk = s_tab[(bits >> 16) & 127];
-                                const float mh = __int_as_float((bits & 0x007fffff) | 0x3f800000);
-                                const float ml = __fmul_rn(r2l, __int_as_float((127 - ex) << 23));
-                                const float Pm = __fmul_rn(mh, tk.x);
-                                const float Pe = fmaf(mh, tk.x, -Pm);
-                                const float uh = __fsub_rn(Pm, 1.0f);
-                                const float ul = fmaf(ml, tk.x, Pe);
-                                const float ef = __fsub_rn(__int_as_float(0x4B400000 + ex), 12582912.0f);
-                                const float hi = fmaf(ef, fflog::kLn2Hi, tk.y);
-                                const float uhh = __fsub_rn(__fadd_rn(uh, 24.0f), 24.0f);
-                                const float uhl = __fsub_rn(uh, uhh);
-                                S = __fadd_rn(hi, uhh);
-                                const float s2 = __fmul_rn(uh, uh);
-                                const float s2e = fmaf(uh, uh, -s2);
-                                const float poly = fmaf(uh, fmaf(uh, fmaf(uh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f);
-                                float tt = __fmul_rn(__fmul_rn(s2, uh), poly);
-                                tt = fmaf(-uh, ul, tt);
-                                tt = fmaf(-0.5f, s2e, tt);
-                                tt = __fadd_rn(tt, ul);
-                                tt = __fadd_rn(tt, tk.z);
-                                tt = __fadd_rn(tt, uhl);
-                                tt = fmaf(-0.5f, s2, tt);
-                                lo = fmaf(ef, fflog::kLn2Lo, tt);
-                            } else {
-                                const double ld = log((double)r2h + (double)r2l);
-                                S = __double2float_rn(ld);
-                                lo = __double2float_rn(ld - (double)S);
-                            }
+                            ff::log_pair(r2h, r2l, s_tab, S, lo);
 #pragma unroll
                             for (int d = 0; d < ND; ++d) {
                                 const float2 qq = s_q[k][d];
@@ -1024,22 +998,11 @@ __global__ void __launch_bounds__(kLeafThreads)
                     }
                 }
             }
-            // sum of the U-list charges over the block (each thread summed the ones it loaded)
-#pragma unroll
-            for (int d = 0; d < ND; ++d)
-                for (int o = 16; o > 0; o >>= 1) qsum[d] += __shfl_xor_sync(0xffffffffu, qsum[d], o);
-            __syncthreads();
-            if ((tid & 31) == 0) {
-#pragma unroll
-                for (int d = 0; d < ND; ++d) s_red[tid >> 5][d] = qsum[d];
-            }
-            __syncthreads();
             if (valid) {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    double qu = 0.0;
-                    for (int w = 0; w < kLeafThreads / 32; ++w) qu += s_red[w][d];
-                    const double near = 0.5 * ((double)ah[d] + (double)al[d]) + log_side * (qu - qco[d]);
+                    const double near = 0.5 * ((double)ah[d] + (double)al[d]) +
+                                        log_side * (ff::to_double(qu[d]) - ff::to_double(qco[d]));
                     psi[(int64_t)ti * ND + d] = acc[d] + near;
                 }
             }
@@ -1164,7 +1127,7 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
     if (tm) tm->end(id);
     id = tm ? tm->begin("m2l") : -1;
     if (ffp)
-        k_m2l_ff<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.Mf, ws.Lf, ws.q);
+        k_m2l_ff<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.Mf, ws.Lf, ws.qf);
     else
         k_m2l<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q);
     if (tm) tm->end(id);
@@ -1184,7 +1147,7 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
     else if (fp64)
         k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
     else
-        k_leaf_ff<P, ND><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi);
+        k_leaf_ff<P, ND><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi);
     if (tm) tm->end(id);
     return cudaGetLastError();
 }

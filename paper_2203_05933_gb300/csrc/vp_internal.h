@@ -34,9 +34,11 @@ struct DevTree {
     const int32_t* tgt_rng = nullptr;   // [nbox][2]
     const int32_t* leaves = nullptr;    // [nleaf]
     const int32_t *u_ptr = nullptr, *u_idx = nullptr;
+    const float4* u_off = nullptr;      // per U entry (b, A): ((c_A - c_b)/side_b as x, y, side_A/side_b, 0)
     const int32_t *v_ptr = nullptr, *v_idx = nullptr;
     const int32_t *w_ptr = nullptr, *w_idx = nullptr;
     const int32_t *x_ptr = nullptr, *x_idx = nullptr;
+    const float4* x_off = nullptr;      // per X entry (b, C): the same offsets as u_off
     std::vector<int32_t> level_start;   // host copy, [nlevels + 1]
 };
 

@@ -54,24 +54,40 @@ __global__ void __launch_bounds__(kGroupThreads)
         __syncthreads();
         for (int r = r0 + warp; r < r1; r += nw) {
             const int64_t v0 = A.rowptr[r];
-            ff::F acc[ND];
+            // four independent accumulators per density keep four loads in flight per lane
+            ff::F acc[4][ND];
 #pragma unroll
-            for (int d = 0; d < ND; ++d) acc[d] = ff::F{0.f, 0.f};
-            for (int k = lane; k < m; k += 32) {
-                const float2 v = A.vf[v0 + k];
-                const ff::F vv{v.x, v.y};
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    const float2 x = staged ? F[k * ND + d] : xf[d * ld_xf + A.cols[c0 + k]];
-                    acc[d] = ff::add(acc[d], ff::mul(vv, ff::F{x.x, x.y}));
+                for (int d = 0; d < ND; ++d) acc[u][d] = ff::F{0.f, 0.f};
+            for (int k0 = lane; k0 < m; k0 += 128) {
+                float2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k0 + 32 * u;
+                    v[u] = k < m ? A.vf[v0 + k] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k0 + 32 * u;
+                    if (k < m) {
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const float2 x = staged ? F[k * ND + d] : xf[d * ld_xf + A.cols[c0 + k]];
+                            acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].x, v[u].y}, ff::F{x.x, x.y}));
+                        }
+                    }
                 }
             }
 #pragma unroll
+            for (int d = 0; d < ND; ++d)
+                acc[0][d] = ff::add(ff::add(acc[0][d], acc[1][d]), ff::add(acc[2][d], acc[3][d]));
+#pragma unroll
             for (int d = 0; d < ND; ++d) {
                 for (int o = 16; o > 0; o >>= 1) {
-                    const float h = __shfl_xor_sync(0xffffffffu, acc[d].h, o);
-                    const float l = __shfl_xor_sync(0xffffffffu, acc[d].l, o);
-                    acc[d] = ff::add(acc[d], ff::F{h, l});
+                    const float h = __shfl_xor_sync(0xffffffffu, acc[0][d].h, o);
+                    const float l = __shfl_xor_sync(0xffffffffu, acc[0][d].l, o);
+                    acc[0][d] = ff::add(acc[0][d], ff::F{h, l});
                 }
             }
             if (lane == 0) {
@@ -79,7 +95,7 @@ __global__ void __launch_bounds__(kGroupThreads)
                 const double wv = w_sorted ? w_sorted[ri] : 1.0;
 #pragma unroll
                 for (int d = 0; d < ND; ++d)
-                    out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[d]));
+                    out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
             }
         }
     }

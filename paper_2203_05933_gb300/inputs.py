@@ -248,3 +248,55 @@ def disk_problem(base_level: int = 7, fine_level: int = 9, refine_radius=None, n
                    f=np.ascontiguousarray(f), csr=mat, root=(-1.0, -1.0, 2.0),
                    meta={"n_cells": mesh.ncell, "n_triangles": int((mesh.cell_kind > 0).sum()),
                          "base_level": base_level, "fine_level": fine_level})
+
+
+def own_cell_csr(cell_start, w, seed: int):
+    """Correction pattern that couples every node to the nodes of its own cell
+    (block diagonal), with seeded stand-in values."""
+    cell_start = np.asarray(cell_start, np.int64)
+    sizes = np.diff(cell_start)
+    rowptr = np.zeros(cell_start[-1] + 1, np.int64)
+    np.cumsum(np.repeat(sizes, sizes), out=rowptr[1:])
+    col = np.concatenate([np.tile(np.arange(a, b, dtype=np.int32), b - a)
+                          for a, b in zip(cell_start[:-1], cell_start[1:])])
+    return rowptr, col, synthetic_csr_values(rowptr, col, w, seed)
+
+
+def many_problems(count: int = 256, n_min: int = 2048, n_max: int = 65536, seed: int = SEED_BASE + 4) -> list[Problem]:
+    """Independent problems of uneven size for the many-problem batch: half box
+    grids on squares (nbox x nbox boxes, 8x8 GL), half unit-disk meshes (boxes +
+    curved triangle band), sizes log-uniform in [n_min, n_max] (box grids
+    exactly, disks from three mesh levels); each problem scaled and shifted at
+    random. Disk meshes are built once per level and reused (a similarity
+    transform of a quadrature rule is a rule, with weights scaled by the square
+    of the scale). The correction couples each node to its own cell (block
+    diagonal, seeded values), which keeps the batch's host inputs small."""
+    from .setup import meshes
+
+    rng = np.random.default_rng(seed)
+    disk_cache = {}
+    out = []
+    for i in range(count):
+        target_n = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        scale = float(np.exp(rng.uniform(np.log(0.5), np.log(4.0))))
+        shift = rng.uniform(-5.0, 5.0, size=2)
+        if i % 2 == 0:
+            nbox = int(np.clip(round(np.sqrt(target_n / 64.0)), 6, 32))
+            xy, w, cell = box_grid_nodes(nbox, 8)
+            cs = np.arange(0, xy.shape[0] + 1, 64, dtype=np.int64)
+            kind = "square"
+        else:
+            base = int(np.clip(round(np.log(target_n / 3000.0) / np.log(4.0)) + 3, 3, 5))
+            if base not in disk_cache:
+                disk_cache[base] = meshes.disk_mesh(base_level=base, fine_level=base)
+            m = disk_cache[base]
+            xy, w, cs = m.xy, m.w, m.cell_start
+            kind = "disk"
+        xy = xy * scale + shift
+        w = w * scale * scale
+        f = np.exp(-((xy[:, 0] - shift[0]) ** 2 + (xy[:, 1] - shift[1]) ** 2) / (0.3 * scale) ** 2)[None, :] + 0.5
+        root = (float(shift[0] - scale), float(shift[1] - scale), float(2.0 * scale))
+        out.append(Problem(name=f"{kind}{i}", src_xy=np.ascontiguousarray(xy), w=w, tgt_xy=np.ascontiguousarray(xy),
+                           f=np.ascontiguousarray(f), csr=own_cell_csr(cs, w, seed + 1000 + i), root=root,
+                           meta={"kind": kind}))
+    return out
