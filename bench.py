@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--batched", type=int, default=64, help="densities of the batched leg (0: skip)")
     ap.add_argument("--size", default="full", choices=["full", "medium", "small"],
                     help="disk levels 7-9 (1.1 M nodes), 6-8 (profiling) or 5-7")
+    ap.add_argument("--many", type=int, default=256, help="problems of the many-problem leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     return ap.parse_args()
 
@@ -251,7 +252,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=args.p, leaf=args.leaf,
-                          max_dens=8, flags=vp.VP_FLAG_TIMING, root=prob.root)
+                          max_dens=8, flags=vp.VP_FLAG_GRAPH, root=prob.root)
     info = plan.info()
     f = torch.as_tensor(prob.f, device=dev)
     out = torch.empty((prob.ndens, prob.n_tgt), dtype=torch.float64, device=dev)
@@ -262,6 +263,17 @@ def main():
     torch.cuda.synchronize()
     rel_err = sampled_error(prob, out.cpu().numpy()) if rank == 0 else None
 
+    def timed(fn, steps):
+        """CUDA-event time of each call on the evaluation stream, L2 flushed before each."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush_l2(flush)
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) / 1e3 for a, b in ev]
+
     for _ in range(args.warmup):
         flush_l2(flush)
         plan.eval(f, out=out)
@@ -269,24 +281,14 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    phase_sum = {}
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush_l2(flush)
-        ev[k][0].record(stream)
-        plan.eval(f, out=out)
-        ev[k][1].record(stream)
-        for name, ms in plan.phase_times().items():
-            phase_sum[name] = phase_sum.get(name, 0.0) + ms
-    torch.cuda.synchronize()
+    step_s = timed(lambda: plan.eval(f, out=out), args.steps)
     wall = time.perf_counter() - wall0
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_dev = sum(step_ms) / 1e3
+    t_dev = sum(step_s)
+    launches_per_eval = plan.info().last_launches
     if world > 1:
         t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -297,8 +299,17 @@ def main():
     else:
         pts = float(prob.n_tgt * prob.ndens * args.steps)
     value = pts / t_dev / 1e6
+
+    # per-phase CUDA-event times (same kernels launched one by one, timing events on the stream)
+    plan.set_flags(vp.VP_FLAG_TIMING)
+    phase_sum = {}
+    for k in range(args.steps):
+        flush_l2(flush)
+        plan.eval(f, out=out)
+        for name, ms in plan.phase_times().items():
+            phase_sum[name] = phase_sum.get(name, 0.0) + ms
+    plan.set_flags(vp.VP_FLAG_GRAPH)
     phase_ms = {k: v / args.steps for k, v in phase_sum.items()}
-    launches_per_eval = plan.info().last_launches
 
     # e2e: the C-ABI host-buffer entry point, pinned buffers, copies inside the timed region
     f_pin = torch.empty((prob.ndens, prob.n_src), dtype=torch.float64, pin_memory=True)
@@ -313,28 +324,46 @@ def main():
         vp.vp_eval_host_ptr(plan.handle, prob.ndens, f_pin.data_ptr(), o_pin.data_ptr())
         e2e_t.append(time.perf_counter() - t0)
     e2e_val = prob.n_tgt * prob.ndens / float(np.mean(e2e_t)) / 1e6
+    clk = clocks.stop()
 
-    # batched leg: many densities through one plan (max_dens chunks of 8)
+    # batched leg: many densities through one plan (chunks of 8 densities per pass)
     batched = None
     if args.batched > 0:
-        from paper_2203_05933_gb300 import inputs
-
         rng = np.random.default_rng(3)
         fb = torch.as_tensor(rng.standard_normal((args.batched, prob.n_src)), device=dev)
         ob = torch.empty((args.batched, prob.n_tgt), dtype=torch.float64, device=dev)
         plan.eval(fb, out=ob)
+        bt = timed(lambda: plan.eval(fb, out=ob), max(2, args.steps // 5))
+        bv = prob.n_tgt * args.batched / float(np.mean(bt)) / 1e6
+        batched = {"ndens": args.batched, "value": bv, "unit": UNIT, "speedup_vs_single": bv / value,
+                   "ms_per_step": float(np.mean(bt)) * 1e3}
+        del fb, ob
+
+    # adjoint leg: transposed FMM + transposed correction (dL/df), one density
+    g = torch.as_tensor(np.random.default_rng(4).standard_normal((1, prob.n_tgt)), device=dev)
+    plan.adjoint(g)
+    at = timed(lambda: plan.adjoint(g), max(2, args.steps // 5))
+    adjoint = {"value": prob.n_src / float(np.mean(at)) / 1e6, "unit": "Msources/s",
+               "ms_per_step": float(np.mean(at)) * 1e3, "ratio_vs_forward": (t_dev / args.steps) / float(np.mean(at))}
+
+    # many-problem leg: 256 uneven square and disk problems in one plan, one graph per evaluation
+    many = None
+    if args.many > 0 and rank == 0:
+        from paper_2203_05933_gb300 import inputs
+        probs = inputs.many_problems(args.many)
+        mplan = vp.Plan.create_many([(p.src_xy, p.w, p.tgt_xy, p.csr, p.root) for p in probs], p_fmm=args.p,
+                                    leaf=args.leaf, max_dens=1, flags=vp.VP_FLAG_GRAPH)
+        mf = torch.as_tensor(np.concatenate([p.f for p in probs], axis=1), device=dev)
+        mo = torch.empty((1, mplan.n_tgt), dtype=torch.float64, device=dev)
+        mplan.eval(mf, out=mo)
         torch.cuda.synchronize()
-        bt = []
-        for k in range(max(2, args.steps // 3)):
-            flush_l2(flush)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            plan.eval(fb, out=ob)
-            b.record(stream)
-            torch.cuda.synchronize()
-            bt.append(a.elapsed_time(b) / 1e3)
-        batched = {"ndens": args.batched, "value": prob.n_tgt * args.batched / float(np.mean(bt)) / 1e6,
-                   "unit": UNIT, "speedup_vs_single": (prob.n_tgt * args.batched / float(np.mean(bt)) / 1e6) / value}
+        mt = timed(lambda: mplan.eval(mf, out=mo), max(3, args.steps // 3))
+        mi = mplan.info()
+        many = {"problems": len(probs), "n_tgt": int(mi.n_tgt), "nnz": int(mi.nnz), "levels": int(mi.n_levels),
+                "value": mi.n_tgt / float(np.mean(mt)) / 1e6, "unit": UNIT, "ms_per_step": float(np.mean(mt)) * 1e3,
+                "launches_per_eval": int(mi.last_launches), "graph": True}
+        mplan.close()
+        del mf, mo
 
     if rank != 0:
         plan.close()
@@ -378,9 +407,12 @@ def main():
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(prob.ndens * prob.n_src * 8),
                 "d2h_bytes_per_step": int(prob.ndens * prob.n_tgt * 8)},
         "batched": batched,
+        "adjoint": adjoint,
+        "many_problems": many,
         "clocks": clk,
         "gpu_launches": int(launches_per_eval * args.steps),
         "wall_s": wall,
+        "graph": True,
     }
     print(json.dumps(line), flush=True)
     plan.close()

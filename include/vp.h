@@ -83,6 +83,11 @@ typedef struct {
  * default float-float evaluation on the FP32 pipes (same result to about 1e-12 relative
  * to the total charge; several times slower on GB300). */
 #define VP_FLAG_FP64 2u
+/* Capture each distinct vp_eval call (same f, out, leading dimensions and ndens) once
+ * into a CUDA graph and replay it afterwards. The first call with new arguments
+ * synchronizes `stream` and captures on a plan-owned stream; later calls only launch
+ * the graph on `stream`. Ignored while VP_FLAG_TIMING is set. */
+#define VP_FLAG_GRAPH 4u
 
 /*
  * vp_plan_create — "vp_plan(nodes, weights, targets, corr_csr)".
@@ -104,6 +109,31 @@ vp_status vp_plan_create(vp_plan* out,
                          const int64_t* corr_rowptr, const int32_t* corr_col,
                          const double* corr_val, int64_t nnz,
                          const vp_options* opt, void* stream);
+
+/*
+ * vp_plan_create_many — one plan for nprob independent problems (many uneven
+ * problems evaluated together). Problem k has n_src[k] sources src_xy[k] with
+ * weights w[k], n_tgt[k] targets tgt_xy[k] and an optional correction
+ * (corr_rowptr[k], corr_col[k], corr_val[k], nnz[k]; corr_rowptr itself may be
+ * NULL for no corrections anywhere). roots: NULL, or [nprob][3] root squares
+ * (side <= 0 -> derived). The arrays of pointers are host arrays; the pointed-to
+ * data follow vp_plan_create's conventions. opt (shared by all problems) as in
+ * vp_plan_create; opt->root is ignored.
+ * The plan behaves as one problem whose sources, targets and densities are the
+ * problems' concatenated in order (caller index of problem k's j-th point =
+ * sum_{m<k} n[m] + j) and whose correction is block diagonal: vp_eval,
+ * vp_eval_adjoint and vp_eval_host take [ndens][sum n_src] densities and give
+ * [ndens][sum n_tgt] results. Interactions never cross problems. The boxes of
+ * all problems are stored level by level, so each FMM phase is one launch per
+ * level for the whole batch.
+ */
+vp_status vp_plan_create_many(vp_plan* out, int32_t nprob,
+                              const int64_t* n_src, const double* const* src_xy,
+                              const double* const* w,
+                              const int64_t* n_tgt, const double* const* tgt_xy,
+                              const int64_t* const* corr_rowptr, const int32_t* const* corr_col,
+                              const double* const* corr_val, const int64_t* nnz,
+                              const double* roots, const vp_options* opt, void* stream);
 
 /*
  * vp_eval — "vp_eval(plan, f, out)": out[d][i] for d < ndens (formula above).
@@ -158,7 +188,8 @@ typedef struct {
     int64_t n_x_pairs;      /* sum over boxes of |X| (source-to-local blocks)           */
     int64_t p2p_pairs;      /* source-target pairs summed directly (one density)        */
     int64_t last_launches;  /* kernel launches made by the last vp_eval on this plan      */
-    double root[3];
+    int64_t n_problems;     /* independent problems in the plan (vp_plan_create_many)     */
+    double root[3];         /* root square of the (first) problem                         */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);
@@ -171,6 +202,10 @@ vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);
  */
 vp_status vp_plan_phase_times(vp_plan plan, int32_t cap, const char** names,
                               double* ms, int32_t* n);
+
+/* Change the run-time flags of a plan (VP_FLAG_TIMING, VP_FLAG_GRAPH); the other
+ * bits must equal those given at creation (VP_ERR_ARG otherwise). */
+vp_status vp_plan_set_flags(vp_plan plan, uint32_t flags);
 
 vp_status vp_plan_destroy(vp_plan plan);
 

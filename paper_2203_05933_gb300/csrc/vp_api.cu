@@ -352,7 +352,10 @@ struct vp_plan_s {
     int nd_cap = 1;
     uint32_t flags = 0;
     int64_t n_src = 0, n_tgt = 0, nnz = 0;
-    Tree host;
+    int32_t n_problems = 1;
+    int32_t stat_levels = 0;
+    int64_t stat_boxes = 0, stat_leaves = 0, stat_u = 0, stat_v = 0, stat_w = 0, stat_x = 0;
+    double stat_root[3] = {0.0, 0.0, 0.0};
     DevTree dt;
     DevTables tab;
     std::vector<void*> allocs;
@@ -375,6 +378,17 @@ struct vp_plan_s {
     DevGroupedCSR gfwd, gadj;   // Pi and Pi^T, rows grouped by shared column lists
     Workspace ws;
     PhaseTimer timer;
+    struct GraphEntry {
+        const double* f;
+        int64_t ld_f;
+        double* out;
+        int64_t ld_out;
+        int32_t ndens;
+        int64_t launches;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;  // captured evaluations (VP_FLAG_GRAPH), most recent last
+    cudaStream_t cap_stream = nullptr;
     // staging for vp_eval_host
     double* stage = nullptr;
     size_t stage_cap = 0;
@@ -404,6 +418,8 @@ struct vp_plan_s {
     }
     ~vp_plan_s()
     {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (void* p : allocs) cudaFree(p);
         if (stage) cudaFree(stage);
         for (auto e : timer.pool) cudaEventDestroy(e);
@@ -480,127 +496,304 @@ const char* vp_last_error(void) { return g_last_error.c_str(); }
 
 const char* vp_version(void) { return "libvp 0.1 sm_103a fp64"; }
 
-vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, const double* w, int64_t n_tgt,
-                         const double* tgt_xy, const int64_t* corr_rowptr, const int32_t* corr_col,
-                         const double* corr_val, int64_t nnz, const vp_options* opt_in, void* stream)
-{
-    g_last_error.clear();
-    if (!out) return fail(VP_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (n_src < 0 || n_tgt < 0 || nnz < 0) return fail(VP_ERR_ARG, "negative size");
-    if (n_src > (1LL << 30) || n_tgt > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 points");
-    if ((n_src > 0 && (!src_xy || !w)) || (n_tgt > 0 && !tgt_xy)) return fail(VP_ERR_ARG, "NULL point array");
-    const bool has_corr = corr_rowptr != nullptr;
-    if (has_corr && nnz > 0 && (!corr_col || !corr_val)) return fail(VP_ERR_ARG, "NULL CSR array");
-    if (!has_corr && nnz != 0) return fail(VP_ERR_ARG, "nnz > 0 without a CSR");
-    vp_options opt;
-    std::memset(&opt, 0, sizeof(opt));
-    if (opt_in) opt = *opt_in;
-    const int P = opt.p_fmm == 0 ? 30 : opt.p_fmm;
-    if (!p_supported(P)) return fail(VP_ERR_UNSUPPORTED, "p_fmm must be 16, 24 or 30");
-    const int leaf = opt.leaf == 0 ? 64 : opt.leaf;
-    const int max_level = opt.max_level == 0 ? 24 : opt.max_level;
-    const int max_dens = opt.max_dens <= 0 ? 1 : opt.max_dens;
-    if (leaf < 1 || leaf > 4096) return fail(VP_ERR_ARG, "leaf outside [1, 4096]");
-    if (max_level < 1 || max_level >= kCoordBits) return fail(VP_ERR_ARG, "max_level outside [1, 27]");
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
 
-    // pull geometry and correction to the host (plan time only)
-    std::vector<double> hs((size_t)n_src * 2), hw((size_t)n_src), ht((size_t)n_tgt * 2);
+namespace {
+
+// One problem's inputs, copied to the host at plan time.
+struct ProblemIn {
+    int64_t n_src = 0, n_tgt = 0, nnz = 0;
+    bool has_corr = false;
+    std::vector<double> hs, hw, ht;
     std::vector<int64_t> hrow;
     std::vector<int32_t> hcol;
     std::vector<double> hval;
+    double root[3] = {0.0, 0.0, 0.0};
+};
+
+// Host arrays of a plan (one problem, or several merged): points in tree
+// order, boxes level by level, interaction lists, correction in caller order.
+struct Built {
+    int64_t n_src = 0, n_tgt = 0, nnz = 0;
+    bool has_corr = false;
+    int n_levels = 0;
+    std::vector<double> sxy, txy, ws;
+    std::vector<int32_t> src_perm, tgt_perm, sinv, tinv;
+    std::vector<double> center, radius, logr;
+    std::vector<int32_t> ixy, level, parent, child, is_leaf, brs, brt, leaves, level_start;
+    std::vector<int32_t> u_ptr, u_idx, v_ptr, v_idx, w_ptr, w_idx, x_ptr, x_idx;
+    std::vector<float> srho, trho, uoff, xoff;
+    std::vector<int64_t> hrow;
+    std::vector<int32_t> hcol;
+    std::vector<double> hval;
+    int64_t p2p_pairs = 0;
+    double root[3] = {0.0, 0.0, 0.0};
+};
+
+vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const double* w, int64_t n_tgt,
+                       const double* tgt_xy, const int64_t* corr_rowptr, const int32_t* corr_col,
+                       const double* corr_val, int64_t nnz, cudaStream_t s)
+{
+    if (n_src < 0 || n_tgt < 0 || nnz < 0) return fail(VP_ERR_ARG, "negative size");
+    if (n_src > (1LL << 30) || n_tgt > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 points");
+    if ((n_src > 0 && (!src_xy || !w)) || (n_tgt > 0 && !tgt_xy)) return fail(VP_ERR_ARG, "NULL point array");
+    P.has_corr = corr_rowptr != nullptr;
+    if (P.has_corr && nnz > 0 && (!corr_col || !corr_val)) return fail(VP_ERR_ARG, "NULL CSR array");
+    if (!P.has_corr && nnz != 0) return fail(VP_ERR_ARG, "nnz > 0 without a CSR");
+    P.n_src = n_src;
+    P.n_tgt = n_tgt;
+    P.nnz = P.has_corr ? nnz : 0;
+    P.hs.resize((size_t)n_src * 2);
+    P.hw.resize((size_t)n_src);
+    P.ht.resize((size_t)n_tgt * 2);
     if (n_src) {
-        VP_CUDA(cudaMemcpyAsync(hs.data(), src_xy, hs.size() * sizeof(double), cudaMemcpyDefault, s));
-        VP_CUDA(cudaMemcpyAsync(hw.data(), w, hw.size() * sizeof(double), cudaMemcpyDefault, s));
+        VP_CUDA(cudaMemcpyAsync(P.hs.data(), src_xy, P.hs.size() * sizeof(double), cudaMemcpyDefault, s));
+        VP_CUDA(cudaMemcpyAsync(P.hw.data(), w, P.hw.size() * sizeof(double), cudaMemcpyDefault, s));
     }
-    if (n_tgt) VP_CUDA(cudaMemcpyAsync(ht.data(), tgt_xy, ht.size() * sizeof(double), cudaMemcpyDefault, s));
-    if (has_corr) {
-        hrow.resize((size_t)n_tgt + 1);
-        VP_CUDA(cudaMemcpyAsync(hrow.data(), corr_rowptr, hrow.size() * sizeof(int64_t), cudaMemcpyDefault, s));
-        hcol.resize((size_t)nnz);
-        hval.resize((size_t)nnz);
+    if (n_tgt) VP_CUDA(cudaMemcpyAsync(P.ht.data(), tgt_xy, P.ht.size() * sizeof(double), cudaMemcpyDefault, s));
+    if (P.has_corr) {
+        P.hrow.resize((size_t)n_tgt + 1);
+        VP_CUDA(cudaMemcpyAsync(P.hrow.data(), corr_rowptr, P.hrow.size() * sizeof(int64_t), cudaMemcpyDefault, s));
+        P.hcol.resize((size_t)nnz);
+        P.hval.resize((size_t)nnz);
         if (nnz) {
-            VP_CUDA(cudaMemcpyAsync(hcol.data(), corr_col, hcol.size() * sizeof(int32_t), cudaMemcpyDefault, s));
-            VP_CUDA(cudaMemcpyAsync(hval.data(), corr_val, hval.size() * sizeof(double), cudaMemcpyDefault, s));
+            VP_CUDA(cudaMemcpyAsync(P.hcol.data(), corr_col, P.hcol.size() * sizeof(int32_t), cudaMemcpyDefault, s));
+            VP_CUDA(cudaMemcpyAsync(P.hval.data(), corr_val, P.hval.size() * sizeof(double), cudaMemcpyDefault, s));
         }
     }
     VP_CUDA(cudaStreamSynchronize(s));
-    if (!finite_all(hw)) return fail(VP_ERR_ARG, "non-finite weight");
-    if (has_corr) {
-        if (hrow[0] != 0 || hrow[(size_t)n_tgt] != nnz) return fail(VP_ERR_ARG, "CSR rowptr does not span [0, nnz]");
+    if (!finite_all(P.hw)) return fail(VP_ERR_ARG, "non-finite weight");
+    if (P.has_corr) {
+        if (P.hrow[0] != 0 || P.hrow[(size_t)n_tgt] != nnz) return fail(VP_ERR_ARG, "CSR rowptr does not span [0, nnz]");
         for (int64_t i = 0; i < n_tgt; ++i)
-            if (hrow[(size_t)i + 1] < hrow[(size_t)i]) return fail(VP_ERR_ARG, "CSR rowptr not monotone");
+            if (P.hrow[(size_t)i + 1] < P.hrow[(size_t)i]) return fail(VP_ERR_ARG, "CSR rowptr not monotone");
         for (int64_t k = 0; k < nnz; ++k)
-            if (hcol[(size_t)k] < 0 || hcol[(size_t)k] >= n_src) return fail(VP_ERR_ARG, "CSR column out of range");
-        if (!finite_all(hval)) return fail(VP_ERR_ARG, "non-finite CSR value");
+            if (P.hcol[(size_t)k] < 0 || P.hcol[(size_t)k] >= n_src) return fail(VP_ERR_ARG, "CSR column out of range");
+        if (!finite_all(P.hval)) return fail(VP_ERR_ARG, "non-finite CSR value");
     }
+    return VP_OK;
+}
 
-    vp_plan p = new (std::nothrow) vp_plan_s();
-    if (!p) return fail(VP_ERR_OOM, "host allocation");
-    cudaGetDevice(&p->device);
-    p->P = P;
-    p->leaf = leaf;
-    p->max_dens = max_dens;
-    p->nd_cap = chunk_for(max_dens, 8);
-    p->flags = (uint32_t)opt.flags;
-    p->n_src = n_src;
-    p->n_tgt = n_tgt;
-    p->nnz = has_corr ? nnz : 0;
-    p->timer.on = (p->flags & VP_FLAG_TIMING) != 0;
-
-    TreeOptions to;
-    to.leaf = leaf;
-    to.max_level = max_level;
-    to.root[0] = opt.root[0];
-    to.root[1] = opt.root[1];
-    to.root[2] = opt.root[2];
-    std::string err = build_tree(n_src, hs.data(), n_tgt, ht.data(), to, p->host);
-    if (!err.empty()) {
-        delete p;
-        return fail(VP_ERR_ARG, err);
-    }
-    const Tree& T = p->host;
+std::string build_one(ProblemIn& P, const TreeOptions& to, Built& B)
+{
+    Tree T;
+    std::string err = build_tree(P.n_src, P.hs.data(), P.n_tgt, P.ht.data(), to, T);
+    if (!err.empty()) return err;
+    const int64_t n_src = P.n_src, n_tgt = P.n_tgt;
     const int32_t nb = (int32_t)T.n_boxes();
-
-    // host arrays in tree order
-    std::vector<double> sxy((size_t)n_src * 2), txy((size_t)n_tgt * 2), ws((size_t)n_src);
-    std::vector<int32_t> sinv((size_t)n_src), tinv((size_t)n_tgt);
+    B.n_src = n_src;
+    B.n_tgt = n_tgt;
+    B.nnz = P.nnz;
+    B.has_corr = P.has_corr;
+    B.n_levels = T.n_levels;
+    B.root[0] = T.x0;
+    B.root[1] = T.y0;
+    B.root[2] = T.side;
+    B.sxy.resize((size_t)n_src * 2);
+    B.txy.resize((size_t)n_tgt * 2);
+    B.ws.resize((size_t)n_src);
+    B.sinv.resize((size_t)n_src);
+    B.tinv.resize((size_t)n_tgt);
     for (int64_t i = 0; i < n_src; ++i) {
         const int32_t c = T.src_perm[(size_t)i];
-        sxy[2 * i] = hs[2 * (size_t)c];
-        sxy[2 * i + 1] = hs[2 * (size_t)c + 1];
-        ws[(size_t)i] = hw[(size_t)c];
-        sinv[(size_t)c] = (int32_t)i;
+        B.sxy[2 * i] = P.hs[2 * (size_t)c];
+        B.sxy[2 * i + 1] = P.hs[2 * (size_t)c + 1];
+        B.ws[(size_t)i] = P.hw[(size_t)c];
+        B.sinv[(size_t)c] = (int32_t)i;
     }
     for (int64_t i = 0; i < n_tgt; ++i) {
         const int32_t c = T.tgt_perm[(size_t)i];
-        txy[2 * i] = ht[2 * (size_t)c];
-        txy[2 * i + 1] = ht[2 * (size_t)c + 1];
-        tinv[(size_t)c] = (int32_t)i;
+        B.txy[2 * i] = P.ht[2 * (size_t)c];
+        B.txy[2 * i + 1] = P.ht[2 * (size_t)c + 1];
+        B.tinv[(size_t)c] = (int32_t)i;
     }
-    std::vector<double> center((size_t)nb * 2), radius((size_t)nb), logr((size_t)nb);
-    std::vector<int32_t> ixy((size_t)nb * 2), brs((size_t)nb * 2), brt((size_t)nb * 2), leaves;
+    B.center.resize((size_t)nb * 2);
+    B.radius.resize((size_t)nb);
+    B.logr.resize((size_t)nb);
+    B.ixy.resize((size_t)nb * 2);
+    B.brs.resize((size_t)nb * 2);
+    B.brt.resize((size_t)nb * 2);
     for (int32_t b = 0; b < nb; ++b) {
-        center[2 * (size_t)b] = T.box_cx(b);
-        center[2 * (size_t)b + 1] = T.box_cy(b);
-        radius[(size_t)b] = 0.5 * T.box_side(b);
-        logr[(size_t)b] = std::log(radius[(size_t)b]);
-        ixy[2 * (size_t)b] = T.ix[(size_t)b];
-        ixy[2 * (size_t)b + 1] = T.iy[(size_t)b];
-        brs[2 * (size_t)b] = T.src_begin[(size_t)b];
-        brs[2 * (size_t)b + 1] = T.src_end[(size_t)b];
-        brt[2 * (size_t)b] = T.tgt_begin[(size_t)b];
-        brt[2 * (size_t)b + 1] = T.tgt_end[(size_t)b];
-        if (T.is_leaf[(size_t)b]) leaves.push_back(b);
+        B.center[2 * (size_t)b] = T.box_cx(b);
+        B.center[2 * (size_t)b + 1] = T.box_cy(b);
+        B.radius[(size_t)b] = 0.5 * T.box_side(b);
+        B.logr[(size_t)b] = std::log(B.radius[(size_t)b]);
+        B.ixy[2 * (size_t)b] = T.ix[(size_t)b];
+        B.ixy[2 * (size_t)b + 1] = T.iy[(size_t)b];
+        B.brs[2 * (size_t)b] = T.src_begin[(size_t)b];
+        B.brs[2 * (size_t)b + 1] = T.src_end[(size_t)b];
+        B.brt[2 * (size_t)b] = T.tgt_begin[(size_t)b];
+        B.brt[2 * (size_t)b + 1] = T.tgt_end[(size_t)b];
+        if (T.is_leaf[(size_t)b]) B.leaves.push_back(b);
     }
-    int64_t pairs = 0;
-    for (int32_t b : leaves)
+    for (int32_t b : B.leaves)
         for (int32_t e = T.u_ptr[(size_t)b]; e < T.u_ptr[(size_t)b + 1]; ++e) {
             const int32_t a = T.u_idx[(size_t)e];
-            pairs += (int64_t)(T.tgt_end[(size_t)b] - T.tgt_begin[(size_t)b]) * (T.src_end[(size_t)a] - T.src_begin[(size_t)a]);
+            B.p2p_pairs += (int64_t)(T.tgt_end[(size_t)b] - T.tgt_begin[(size_t)b]) *
+                           (T.src_end[(size_t)a] - T.src_begin[(size_t)a]);
         }
-    p->p2p_pairs = pairs;
+    B.srho = make_rho(T, B.sxy, true);
+    B.trho = make_rho(T, B.txy, false);
+    B.uoff = make_list_offsets(T, T.u_ptr, T.u_idx);
+    B.xoff = make_list_offsets(T, T.x_ptr, T.x_idx);
+    B.src_perm = std::move(T.src_perm);
+    B.tgt_perm = std::move(T.tgt_perm);
+    B.level = std::move(T.level);
+    B.parent = std::move(T.parent);
+    B.child = std::move(T.child);
+    B.is_leaf = std::move(T.is_leaf);
+    B.level_start = std::move(T.level_start);
+    B.u_ptr = std::move(T.u_ptr);
+    B.u_idx = std::move(T.u_idx);
+    B.v_ptr = std::move(T.v_ptr);
+    B.v_idx = std::move(T.v_idx);
+    B.w_ptr = std::move(T.w_ptr);
+    B.w_idx = std::move(T.w_idx);
+    B.x_ptr = std::move(T.x_ptr);
+    B.x_idx = std::move(T.x_idx);
+    B.hrow = std::move(P.hrow);
+    B.hcol = std::move(P.hcol);
+    B.hval = std::move(P.hval);
+    return "";
+}
+
+// Several independent problems as one forest: points and caller indices are
+// concatenated problem by problem, boxes are reordered level by level (all
+// problems' level-l boxes together, so one launch per level serves every
+// problem), list entries and ranges are remapped, and the corrections become
+// one block-diagonal matrix. Interactions never cross problems.
+Built merge(std::vector<Built>& parts)
+{
+    Built M;
+    M.has_corr = false;
+    for (const Built& B : parts) {
+        M.n_levels = std::max(M.n_levels, B.n_levels);
+        M.has_corr = M.has_corr || B.has_corr;
+    }
+    if (!parts.empty()) std::memcpy(M.root, parts[0].root, sizeof(M.root));
+    std::vector<std::vector<int32_t>> newid(parts.size());
+    std::vector<int64_t> so(parts.size()), to(parts.size());
+    int64_t ns = 0, nt = 0;
+    for (size_t k = 0; k < parts.size(); ++k) {
+        so[k] = ns;
+        to[k] = nt;
+        ns += parts[k].n_src;
+        nt += parts[k].n_tgt;
+        newid[k].assign(parts[k].level.size(), -1);
+    }
+    M.n_src = ns;
+    M.n_tgt = nt;
+    int32_t next = 0;
+    M.level_start.push_back(0);
+    for (int l = 0; l < M.n_levels; ++l) {
+        for (size_t k = 0; k < parts.size(); ++k) {
+            const Built& B = parts[k];
+            if (l >= B.n_levels) continue;
+            for (int32_t b = B.level_start[(size_t)l]; b < B.level_start[(size_t)l + 1]; ++b) newid[k][(size_t)b] = next++;
+        }
+        M.level_start.push_back(next);
+    }
+    const size_t nb = (size_t)next;
+    std::vector<std::pair<int32_t, int32_t>> origin(nb);  // new id -> (problem, old id)
+    for (size_t k = 0; k < parts.size(); ++k)
+        for (size_t b = 0; b < newid[k].size(); ++b) origin[(size_t)newid[k][b]] = {(int32_t)k, (int32_t)b};
+    M.center.resize(nb * 2);
+    M.radius.resize(nb);
+    M.logr.resize(nb);
+    M.ixy.resize(nb * 2);
+    M.level.resize(nb);
+    M.parent.resize(nb);
+    M.child.resize(nb * 4);
+    M.is_leaf.resize(nb);
+    M.brs.resize(nb * 2);
+    M.brt.resize(nb * 2);
+    M.u_ptr.assign(nb + 1, 0);
+    M.v_ptr.assign(nb + 1, 0);
+    M.w_ptr.assign(nb + 1, 0);
+    M.x_ptr.assign(nb + 1, 0);
+    auto map = [&](size_t k, int32_t b) { return b < 0 ? -1 : newid[k][(size_t)b]; };
+    for (size_t n = 0; n < nb; ++n) {
+        const size_t k = (size_t)origin[n].first;
+        const int32_t b = origin[n].second;
+        const Built& B = parts[k];
+        M.center[2 * n] = B.center[2 * (size_t)b];
+        M.center[2 * n + 1] = B.center[2 * (size_t)b + 1];
+        M.radius[n] = B.radius[(size_t)b];
+        M.logr[n] = B.logr[(size_t)b];
+        M.ixy[2 * n] = B.ixy[2 * (size_t)b];
+        M.ixy[2 * n + 1] = B.ixy[2 * (size_t)b + 1];
+        M.level[n] = B.level[(size_t)b];
+        M.parent[n] = map(k, B.parent[(size_t)b]);
+        for (int c = 0; c < 4; ++c) M.child[4 * n + c] = map(k, B.child[4 * (size_t)b + c]);
+        M.is_leaf[n] = B.is_leaf[(size_t)b];
+        M.brs[2 * n] = B.brs[2 * (size_t)b] + (int32_t)so[k];
+        M.brs[2 * n + 1] = B.brs[2 * (size_t)b + 1] + (int32_t)so[k];
+        M.brt[2 * n] = B.brt[2 * (size_t)b] + (int32_t)to[k];
+        M.brt[2 * n + 1] = B.brt[2 * (size_t)b + 1] + (int32_t)to[k];
+        if (M.is_leaf[n]) M.leaves.push_back((int32_t)n);
+        auto copy_list = [&](const std::vector<int32_t>& ptr, const std::vector<int32_t>& idx,
+                             std::vector<int32_t>& optr, std::vector<int32_t>& oidx, const std::vector<float>* off,
+                             std::vector<float>* ooff) {
+            for (int32_t e = ptr[(size_t)b]; e < ptr[(size_t)b + 1]; ++e) {
+                oidx.push_back(map(k, idx[(size_t)e]));
+                if (off) ooff->insert(ooff->end(), off->begin() + 4 * (size_t)e, off->begin() + 4 * (size_t)e + 4);
+            }
+            optr[n + 1] = (int32_t)oidx.size();
+        };
+        copy_list(B.u_ptr, B.u_idx, M.u_ptr, M.u_idx, &B.uoff, &M.uoff);
+        copy_list(B.v_ptr, B.v_idx, M.v_ptr, M.v_idx, nullptr, nullptr);
+        copy_list(B.w_ptr, B.w_idx, M.w_ptr, M.w_idx, nullptr, nullptr);
+        copy_list(B.x_ptr, B.x_idx, M.x_ptr, M.x_idx, &B.xoff, &M.xoff);
+    }
+    int64_t nnz = 0;
+    if (M.has_corr) M.hrow.push_back(0);
+    for (size_t k = 0; k < parts.size(); ++k) {
+        Built& B = parts[k];
+        for (double v : B.sxy) M.sxy.push_back(v);
+        for (double v : B.txy) M.txy.push_back(v);
+        for (double v : B.ws) M.ws.push_back(v);
+        for (float v : B.srho) M.srho.push_back(v);
+        for (float v : B.trho) M.trho.push_back(v);
+        for (int32_t v : B.src_perm) M.src_perm.push_back(v + (int32_t)so[k]);
+        for (int32_t v : B.tgt_perm) M.tgt_perm.push_back(v + (int32_t)to[k]);
+        for (int32_t v : B.sinv) M.sinv.push_back(v + (int32_t)so[k]);
+        for (int32_t v : B.tinv) M.tinv.push_back(v + (int32_t)to[k]);
+        M.p2p_pairs += B.p2p_pairs;
+        if (M.has_corr) {
+            for (int64_t i = 0; i < B.n_tgt; ++i) M.hrow.push_back(nnz + (B.has_corr ? B.hrow[(size_t)i + 1] : 0));
+            if (B.has_corr) {
+                for (int32_t c : B.hcol) M.hcol.push_back(c + (int32_t)so[k]);
+                M.hval.insert(M.hval.end(), B.hval.begin(), B.hval.end());
+                nnz += B.nnz;
+            }
+        }
+        B = Built();  // release
+    }
+    M.nnz = nnz;
+    return M;
+}
+
+vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
+{
+    const int64_t n_src = B.n_src, n_tgt = B.n_tgt, nnz = B.nnz;
+    const bool has_corr = B.has_corr;
+    const int32_t nb = (int32_t)B.level.size();
+    p->n_src = n_src;
+    p->n_tgt = n_tgt;
+    p->nnz = has_corr ? nnz : 0;
+    p->p2p_pairs = B.p2p_pairs;
+    p->stat_levels = B.n_levels;
+    p->stat_boxes = nb;
+    p->stat_leaves = (int64_t)B.leaves.size();
+    p->stat_u = 0;
+    p->stat_w = 0;
+    for (int32_t b : B.leaves) {
+        p->stat_u += B.u_ptr[(size_t)b + 1] - B.u_ptr[(size_t)b];
+        p->stat_w += B.w_ptr[(size_t)b + 1] - B.w_ptr[(size_t)b];
+    }
+    p->stat_v = (int64_t)B.v_idx.size();
+    p->stat_x = (int64_t)B.x_idx.size();
+    std::memcpy(p->stat_root, B.root, sizeof(p->stat_root));
 
     // transposed correction (columns = sources), for the adjoint
     std::vector<int64_t> hcptr;
@@ -608,16 +801,16 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     std::vector<double> hcval;
     if (has_corr) {
         hcptr.assign((size_t)n_src + 1, 0);
-        for (int64_t k = 0; k < nnz; ++k) hcptr[(size_t)hcol[(size_t)k] + 1]++;
+        for (int64_t k = 0; k < nnz; ++k) hcptr[(size_t)B.hcol[(size_t)k] + 1]++;
         for (int64_t j = 0; j < n_src; ++j) hcptr[(size_t)j + 1] += hcptr[(size_t)j];
         std::vector<int64_t> fill(hcptr.begin(), hcptr.end() - 1);
         hcrow.resize((size_t)nnz);
         hcval.resize((size_t)nnz);
         for (int64_t i = 0; i < n_tgt; ++i)
-            for (int64_t k = hrow[(size_t)i]; k < hrow[(size_t)i + 1]; ++k) {
-                const int64_t pos = fill[(size_t)hcol[(size_t)k]]++;
+            for (int64_t k = B.hrow[(size_t)i]; k < B.hrow[(size_t)i + 1]; ++k) {
+                const int64_t pos = fill[(size_t)B.hcol[(size_t)k]]++;
                 hcrow[(size_t)pos] = (int32_t)i;
-                hcval[(size_t)pos] = hval[(size_t)k];
+                hcval[(size_t)pos] = B.hval[(size_t)k];
             }
     }
     size_t off[7];
@@ -625,8 +818,6 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     std::vector<float> logtab = make_log_table();
     size_t offf[8];
     std::vector<float> fftab = make_ff_tables(P, offf);
-    std::vector<float> srho = make_rho(T, sxy, true), trho = make_rho(T, txy, false);
-    std::vector<float> uoff = make_list_offsets(T, T.u_ptr, T.u_idx), xoff = make_list_offsets(T, T.x_ptr, T.x_idx);
 
     cudaError_t e = cudaSuccess;
     auto up = [&](auto** dst, const auto& h) {
@@ -634,55 +825,74 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     };
     double* d_xy_s = nullptr;
     double* d_xy_t = nullptr;
-    up(&d_xy_s, sxy);
-    up(&d_xy_t, txy);
+    up(&d_xy_s, B.sxy);
+    up(&d_xy_t, B.txy);
     p->src_xy = (double2*)d_xy_s;
     p->tgt_xy = (double2*)d_xy_t;
-    up(&p->w_sorted, ws);
-    up(&p->src_perm, T.src_perm);
-    up(&p->tgt_perm, T.tgt_perm);
-    up(&p->src_inv, sinv);
-    up(&p->tgt_inv, tinv);
-    up(&p->box_src, brs);
-    up(&p->box_tgt, brt);
+    up(&p->w_sorted, B.ws);
+    up(&p->src_perm, B.src_perm);
+    up(&p->tgt_perm, B.tgt_perm);
+    up(&p->src_inv, B.sinv);
+    up(&p->tgt_inv, B.tinv);
+    up(&p->box_src, B.brs);
+    up(&p->box_tgt, B.brt);
     double *d_center = nullptr, *d_radius = nullptr, *d_logr = nullptr, *d_tab = nullptr;
     int32_t *d_ixy = nullptr, *d_parent = nullptr, *d_child = nullptr, *d_leaf = nullptr, *d_leaves = nullptr;
-    int32_t *d_up, *d_ui, *d_vp, *d_vi, *d_wp, *d_wi, *d_xp, *d_xi;
-    up(&d_center, center);
-    up(&d_radius, radius);
-    up(&d_logr, logr);
-    up(&d_ixy, ixy);
-    up(&d_parent, T.parent);
-    up(&d_child, T.child);
-    up(&d_leaf, T.is_leaf);
-    up(&d_leaves, leaves);
-    up(&d_up, T.u_ptr);
-    up(&d_ui, T.u_idx);
-    up(&d_vp, T.v_ptr);
-    up(&d_vi, T.v_idx);
-    up(&d_wp, T.w_ptr);
-    up(&d_wi, T.w_idx);
-    up(&d_xp, T.x_ptr);
-    up(&d_xi, T.x_idx);
+    int32_t *d_up = nullptr, *d_ui = nullptr, *d_vp = nullptr, *d_vi = nullptr, *d_wp = nullptr, *d_wi = nullptr,
+            *d_xp = nullptr, *d_xi = nullptr;
+    up(&d_center, B.center);
+    up(&d_radius, B.radius);
+    up(&d_logr, B.logr);
+    up(&d_ixy, B.ixy);
+    up(&d_parent, B.parent);
+    up(&d_child, B.child);
+    up(&d_leaf, B.is_leaf);
+    {
+        // costliest leaves first, so the persistent near-field kernel ends evenly
+        std::vector<int64_t> cost(B.leaves.size());
+        for (size_t i = 0; i < B.leaves.size(); ++i) {
+            const int32_t b = B.leaves[i];
+            int64_t srcs = 0;
+            for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
+                const int32_t a = B.u_idx[(size_t)e2];
+                srcs += B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
+            }
+            cost[i] = (int64_t)(B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b]) * srcs;
+        }
+        std::vector<size_t> order(B.leaves.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b2) { return cost[a] > cost[b2]; });
+        std::vector<int32_t> sorted(order.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = B.leaves[order[i]];
+        B.leaves.swap(sorted);
+    }
+    up(&d_leaves, B.leaves);
+    up(&d_up, B.u_ptr);
+    up(&d_ui, B.u_idx);
+    up(&d_vp, B.v_ptr);
+    up(&d_vi, B.v_idx);
+    up(&d_wp, B.w_ptr);
+    up(&d_wi, B.w_idx);
+    up(&d_xp, B.x_ptr);
+    up(&d_xi, B.x_idx);
     up(&d_tab, tables);
-    float *d_logtab = nullptr, *d_srho = nullptr, *d_trho = nullptr;
+    float *d_logtab = nullptr, *d_srho = nullptr, *d_trho = nullptr, *d_fftab = nullptr;
     int32_t* d_level = nullptr;
     up(&d_logtab, logtab);
-    float* d_fftab = nullptr;
     up(&d_fftab, fftab);
-    up(&d_srho, srho);
-    up(&d_trho, trho);
-    up(&d_level, T.level);
+    up(&d_srho, B.srho);
+    up(&d_trho, B.trho);
+    up(&d_level, B.level);
     float *d_uoff = nullptr, *d_xoff = nullptr;
-    up(&d_uoff, uoff);
-    up(&d_xoff, xoff);
+    up(&d_uoff, B.uoff);
+    up(&d_xoff, B.xoff);
     p->src_rho = (float4*)d_srho;
     p->tgt_rho = (float4*)d_trho;
     p->grouped = has_corr && !(p->flags & VP_FLAG_FP64);
     if (has_corr && !p->grouped) {
-        up(&p->rowptr, hrow);
-        up(&p->col, hcol);
-        up(&p->val, hval);
+        up(&p->rowptr, B.hrow);
+        up(&p->col, B.hcol);
+        up(&p->val, B.hval);
         up(&p->cptr, hcptr);
         up(&p->crow, hcrow);
         up(&p->cval, hcval);
@@ -692,7 +902,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
             HostGroups G;
             const bool fwd = pass == 0;
             const int64_t nrows = fwd ? n_tgt : n_src;
-            build_groups(nrows, fwd ? hrow : hcptr, fwd ? hcol : hcrow, fwd ? hval : hcval, G);
+            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, G);
             DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
             int32_t *d_r0 = nullptr, *d_cols = nullptr;
             int64_t *d_c0 = nullptr, *d_rp = nullptr;
@@ -700,7 +910,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
             up(&d_r0, G.g_r0);
             up(&d_c0, G.g_c0);
             up(&d_cols, G.cols);
-            up(&d_rp, fwd ? hrow : hcptr);
+            up(&d_rp, fwd ? B.hrow : hcptr);
             up(&d_vf, G.vf);
             A.nrows = (int32_t)nrows;
             A.ngroups = (int32_t)G.g_r0.size() - 1;
@@ -722,17 +932,15 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     if (e == cudaSuccess) e = p->alloc(&p->ws.Mf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.work, 4);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        delete p;
-        return cuda_fail(e, "vp_plan_create upload");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
     p->ws.nd_cap = p->nd_cap;
 
     DevTree& dt = p->dt;
     dt.nbox = nb;
-    dt.nlevels = T.n_levels;
-    dt.nleaf = (int32_t)leaves.size();
+    dt.nlevels = B.n_levels;
+    dt.nleaf = (int32_t)B.leaves.size();
     dt.center = (const double2*)d_center;
     dt.radius = d_radius;
     dt.log_radius = d_logr;
@@ -754,7 +962,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     dt.w_idx = d_wi;
     dt.x_ptr = d_xp;
     dt.x_idx = d_xi;
-    dt.level_start = T.level_start;
+    dt.level_start = B.level_start;
     DevTables& tb = p->tab;
     tb.H = d_tab + off[0];
     tb.Bm = d_tab + off[1];
@@ -772,42 +980,147 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     tb.Bmf = (const float2*)(d_fftab + offf[5]);
     tb.Blf = (const float2*)(d_fftab + offf[6]);
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
-    {
-        const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
-                               p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf,
-                               p->dt.u_off, p->dt.x_off};
-        const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
-                              p->gfwd.vf, p->gadj.vf};
-        bool ok = true;
-        for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);
-        for (const void* q : vec8) ok = ok && ((uintptr_t)q % 8 == 0);
-        if (!ok) {
-            delete p;
-            *out = nullptr;
-            return fail(VP_ERR_CUDA, "internal error: misaligned device table");
-        }
+    const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
+                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off};
+    const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
+                          p->gfwd.vf, p->gadj.vf};
+    bool ok = true;
+    for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);
+    for (const void* q : vec8) ok = ok && ((uintptr_t)q % 8 == 0);
+    if (!ok) return fail(VP_ERR_CUDA, "internal error: misaligned device table");
+    return VP_OK;
+}
+
+vp_status plan_options(const vp_options* opt_in, vp_options& opt, int& P, int& leaf, int& max_level, int& max_dens)
+{
+    std::memset(&opt, 0, sizeof(opt));
+    if (opt_in) opt = *opt_in;
+    P = opt.p_fmm == 0 ? 30 : opt.p_fmm;
+    if (!p_supported(P)) return fail(VP_ERR_UNSUPPORTED, "p_fmm must be 16, 24 or 30");
+    leaf = opt.leaf == 0 ? 64 : opt.leaf;
+    max_level = opt.max_level == 0 ? 24 : opt.max_level;
+    max_dens = opt.max_dens <= 0 ? 1 : opt.max_dens;
+    if (leaf < 1 || leaf > 4096) return fail(VP_ERR_ARG, "leaf outside [1, 4096]");
+    if (max_level < 1 || max_level >= kCoordBits) return fail(VP_ERR_ARG, "max_level outside [1, 27]");
+    return VP_OK;
+}
+
+vp_plan new_plan(const vp_options& opt, int P, int leaf, int max_dens)
+{
+    vp_plan p = new (std::nothrow) vp_plan_s();
+    if (!p) return nullptr;
+    cudaGetDevice(&p->device);
+    p->P = P;
+    p->leaf = leaf;
+    p->max_dens = max_dens;
+    p->nd_cap = chunk_for(max_dens, 8);
+    p->flags = (uint32_t)opt.flags;
+    p->timer.on = (p->flags & VP_FLAG_TIMING) != 0;
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, const double* w, int64_t n_tgt,
+                         const double* tgt_xy, const int64_t* corr_rowptr, const int32_t* corr_col,
+                         const double* corr_val, int64_t nnz, const vp_options* opt_in, void* stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(VP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    vp_options opt;
+    int P, leaf, max_level, max_dens;
+    vp_status st = plan_options(opt_in, opt, P, leaf, max_level, max_dens);
+    if (st != VP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ProblemIn in;
+    st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s);
+    if (st != VP_OK) return st;
+    TreeOptions to;
+    to.leaf = leaf;
+    to.max_level = max_level;
+    std::memcpy(to.root, opt.root, sizeof(to.root));
+    Built B;
+    std::string err = build_one(in, to, B);
+    if (!err.empty()) return fail(VP_ERR_ARG, err);
+    vp_plan p = new_plan(opt, P, leaf, max_dens);
+    if (!p) return fail(VP_ERR_OOM, "host allocation");
+    st = finalize(p, B, P, s);
+    if (st != VP_OK) {
+        delete p;
+        return st;
     }
     *out = p;
     return VP_OK;
 }
 
-vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, double* out, int64_t ld_out,
-                  void* stream)
+vp_status vp_plan_create_many(vp_plan* out, int32_t nprob, const int64_t* n_src, const double* const* src_xy,
+                              const double* const* w, const int64_t* n_tgt, const double* const* tgt_xy,
+                              const int64_t* const* corr_rowptr, const int32_t* const* corr_col,
+                              const double* const* corr_val, const int64_t* nnz, const double* roots,
+                              const vp_options* opt_in, void* stream)
 {
-    vp_status st = check_plan(p);
+    g_last_error.clear();
+    if (!out) return fail(VP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1) return fail(VP_ERR_ARG, "nprob < 1");
+    if (!n_src || !src_xy || !w || !n_tgt || !tgt_xy) return fail(VP_ERR_ARG, "NULL per-problem array");
+    vp_options opt;
+    int P, leaf, max_level, max_dens;
+    vp_status st = plan_options(opt_in, opt, P, leaf, max_level, max_dens);
     if (st != VP_OK) return st;
-    if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
-    if (ndens == 0 || p->n_tgt == 0) return VP_OK;
-    if (!out || (p->n_src > 0 && !f)) return fail(VP_ERR_ARG, "NULL density or output");
-    if (ld_f < p->n_src || ld_out < p->n_tgt) return fail(VP_ERR_ARG, "leading dimension too small");
     cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Built> parts((size_t)nprob);
+    int64_t tot_s = 0, tot_t = 0;
+    for (int32_t k = 0; k < nprob; ++k) {
+        ProblemIn in;
+        st = copy_problem(in, n_src[k], src_xy[k], w[k], n_tgt[k], tgt_xy[k], corr_rowptr ? corr_rowptr[k] : nullptr,
+                          corr_col ? corr_col[k] : nullptr, corr_val ? corr_val[k] : nullptr, nnz ? nnz[k] : 0, s);
+        if (st != VP_OK) return fail(st, "problem " + std::to_string(k) + ": " + g_last_error);
+        tot_s += n_src[k];
+        tot_t += n_tgt[k];
+        if (tot_s > (1LL << 30) || tot_t > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 points in total");
+        TreeOptions to;
+        to.leaf = leaf;
+        to.max_level = max_level;
+        if (roots) std::memcpy(to.root, roots + 3 * (size_t)k, sizeof(to.root));
+        std::string err = build_one(in, to, parts[(size_t)k]);
+        if (!err.empty()) return fail(VP_ERR_ARG, "problem " + std::to_string(k) + ": " + err);
+    }
+    Built B = merge(parts);
+    vp_plan p = new_plan(opt, P, leaf, max_dens);
+    if (!p) return fail(VP_ERR_OOM, "host allocation");
+    p->n_problems = nprob;
+    st = finalize(p, B, P, s);
+    if (st != VP_OK) {
+        delete p;
+        return st;
+    }
+    *out = p;
+    return VP_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+}  // extern "C"
+
+namespace {
+
+// The launch sequence of one evaluation, enqueued on s.
+vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, double* out, int64_t ld_out,
+                       cudaStream_t s)
+{
     p->timer.stream = s;
     p->timer.used = 0;
     PassGeom g = forward_geom(p);
     p->last_launches = 0;
     for (int d0 = 0; d0 < ndens;) {
         const int nd = chunk_for(ndens - d0, p->nd_cap);
-        // charges, P2M, M2M per level, (conversion +) M2L, L2L per level, leaf, output
+        // charges, P2M, M2M per level, M2L, L2L per level, leaf, output
         p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
@@ -829,6 +1142,61 @@ vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, doubl
         d0 += nd;
     }
     return VP_OK;
+}
+
+// Replays (or captures, then replays) the evaluation as a CUDA graph keyed by
+// its arguments. Capture runs on a plan-owned stream in relaxed mode; the
+// graph is launched on the caller's stream.
+vp_status eval_graph(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, double* out, int64_t ld_out,
+                     cudaStream_t s)
+{
+    for (auto& gc : p->graphs)
+        if (gc.f == f && gc.ld_f == ld_f && gc.out == out && gc.ld_out == ld_out && gc.ndens == ndens) {
+            p->last_launches = gc.launches;
+            VP_CUDA(cudaGraphLaunch(gc.exec, s));
+            return VP_OK;
+        }
+    if (!p->cap_stream) VP_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    // order the capture after the caller's pending work on s, and the replay after the capture
+    VP_CUDA(cudaStreamSynchronize(s));
+    VP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
+    vp_status st = enqueue_eval(p, ndens, f, ld_f, out, ld_out, p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (st != VP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (p->graphs.size() >= 8) {
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back(vp_plan_s::GraphEntry{f, ld_f, out, ld_out, ndens, p->last_launches, exec});
+    VP_CUDA(cudaGraphLaunch(exec, s));
+    return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, double* out, int64_t ld_out,
+                  void* stream)
+{
+    vp_status st = check_plan(p);
+    if (st != VP_OK) return st;
+    if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
+    if (ndens == 0 || p->n_tgt == 0) return VP_OK;
+    if (!out || (p->n_src > 0 && !f)) return fail(VP_ERR_ARG, "NULL density or output");
+    if (ld_f < p->n_src || ld_out < p->n_tgt) return fail(VP_ERR_ARG, "leading dimension too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((p->flags & VP_FLAG_GRAPH) && !p->timer.on) return eval_graph(p, ndens, f, ld_f, out, ld_out, s);
+    return enqueue_eval(p, ndens, f, ld_f, out, ld_out, s);
 }
 
 vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_g, double* grad_f, int64_t ld_gf,
@@ -919,32 +1287,25 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     if (!p || !p->alive) return fail(VP_ERR_STATE, "invalid plan");
     if (!o) return fail(VP_ERR_ARG, "NULL stats");
     std::memset(o, 0, sizeof(*o));
-    const Tree& T = p->host;
     o->n_src = p->n_src;
     o->n_tgt = p->n_tgt;
     o->nnz = p->nnz;
     o->p_fmm = p->P;
     o->leaf = p->leaf;
     o->max_dens = p->max_dens;
-    o->n_levels = T.n_levels;
-    o->n_boxes = T.n_boxes();
-    int64_t nl = 0, nu = 0, nw = 0;
-    for (int64_t b = 0; b < T.n_boxes(); ++b)
-        if (T.is_leaf[(size_t)b]) {
-            ++nl;
-            nu += T.u_ptr[(size_t)b + 1] - T.u_ptr[(size_t)b];
-            nw += T.w_ptr[(size_t)b + 1] - T.w_ptr[(size_t)b];
-        }
-    o->n_leaves = nl;
-    o->n_u_pairs = nu;
-    o->n_v_pairs = (int64_t)T.v_idx.size();
-    o->n_w_pairs = nw;
-    o->n_x_pairs = (int64_t)T.x_idx.size();
+    o->n_levels = p->stat_levels;
+    o->n_boxes = p->stat_boxes;
+    o->n_leaves = p->stat_leaves;
+    o->n_u_pairs = p->stat_u;
+    o->n_v_pairs = p->stat_v;
+    o->n_w_pairs = p->stat_w;
+    o->n_x_pairs = p->stat_x;
     o->p2p_pairs = p->p2p_pairs;
     o->last_launches = p->last_launches;
-    o->root[0] = T.x0;
-    o->root[1] = T.y0;
-    o->root[2] = T.side;
+    o->n_problems = p->n_problems;
+    o->root[0] = p->stat_root[0];
+    o->root[1] = p->stat_root[1];
+    o->root[2] = p->stat_root[2];
     return VP_OK;
 }
 
@@ -969,6 +1330,17 @@ vp_status vp_plan_phase_times(vp_plan p, int32_t cap, const char** names, double
         if (names) names[i] = t.names[(size_t)i].c_str();
         if (ms) ms[i] = sum[(size_t)i];
     }
+    return VP_OK;
+}
+
+vp_status vp_plan_set_flags(vp_plan p, uint32_t flags)
+{
+    if (!p || !p->alive) return fail(VP_ERR_STATE, "invalid plan");
+    const uint32_t runtime = VP_FLAG_TIMING | VP_FLAG_GRAPH;
+    if ((flags & ~runtime) != (p->flags & ~runtime))
+        return fail(VP_ERR_ARG, "only VP_FLAG_TIMING and VP_FLAG_GRAPH can change after plan creation");
+    p->flags = flags;
+    p->timer.on = (flags & VP_FLAG_TIMING) != 0;
     return VP_OK;
 }
 

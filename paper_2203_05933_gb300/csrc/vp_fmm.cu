@@ -854,7 +854,8 @@ constexpr float kLn2Lo = 1.0f * (float)(0.693147180559945309417232121458176568 -
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafThreads)
     k_leaf_ff(DevTree t, PassGeom g, const float2* __restrict__ qf, const float4* __restrict__ Mf,
-              const float4* __restrict__ Lf, const float4* __restrict__ logtab, double* __restrict__ psi)
+              const float4* __restrict__ Lf, const float4* __restrict__ logtab, double* __restrict__ psi,
+              int* __restrict__ work)
 {
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1][ND];
@@ -864,7 +865,14 @@ __global__ void __launch_bounds__(kLeafThreads)
     __shared__ float4 s_tab[128];
     const int tid = threadIdx.x;
     for (int i = tid; i < 128; i += kLeafThreads) s_tab[i] = logtab[i];
-    for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
+    // persistent blocks pull leaves from a queue (leaves are stored costliest first)
+    __shared__ int s_next;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_next = atomicAdd(work, 1);
+        __syncthreads();
+        const int li = s_next;
+        if (li >= t.nleaf) break;
         const int b = t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
@@ -1146,8 +1154,22 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
         k_leaf<P, ND, true><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
     else if (fp64)
         k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
-    else
-        k_leaf_ff<P, ND><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi);
+    else {
+        static int resident = 0;  // blocks of this instantiation that fit on one SM
+        if (resident == 0) {
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND>, kLeafThreads, 0) != cudaSuccess ||
+                nb < 1)
+                nb = 1;
+            resident = nb;
+        }
+        int sms = 152;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int pblocks = std::max(1, std::min(t.nleaf, sms * resident));
+        cudaMemsetAsync(ws.work, 0, sizeof(int), s);
+        k_leaf_ff<P, ND><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi, ws.work);
+    }
     if (tm) tm->end(id);
     return cudaGetLastError();
 }

@@ -98,6 +98,7 @@ struct Workspace {
     double2* L = nullptr;     // [nbox][P1][ND] local coefficients (scaled)
     double* psi = nullptr;    // [max(n_src, n_tgt)][2][ND] potential (or gradient) in tree order
     float2* xf = nullptr;     // [ND][max(n_src, n_tgt)] correction input (f or g) as hi/lo floats
+    int* work = nullptr;      // work-queue counter of the persistent near-field kernel
     int32_t nd_cap = 0;
 };
 

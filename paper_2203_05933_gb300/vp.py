@@ -22,6 +22,7 @@ _lib = None
 VP_OK = 0
 VP_FLAG_TIMING = 1
 VP_FLAG_FP64 = 2
+VP_FLAG_GRAPH = 4
 
 TREE_ARRAYS = {
     "box_level": 0, "box_ixy": 1, "box_parent": 2, "box_leaf": 3, "box_src": 4, "box_tgt": 5,
@@ -30,8 +31,8 @@ TREE_ARRAYS = {
 }
 
 EXPORTED = [
-    "vp_plan_create", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_plan_info",
-    "vp_plan_phase_times", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
+    "vp_plan_create", "vp_plan_create_many", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_plan_info",
+    "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy",
 ]
 
@@ -57,7 +58,7 @@ class vp_plan_stats(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("n_u_pairs", ctypes.c_int64), ("n_v_pairs", ctypes.c_int64), ("n_w_pairs", ctypes.c_int64),
                 ("n_x_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("last_launches", ctypes.c_int64),
-                ("root", ctypes.c_double * 3)]
+                ("n_problems", ctypes.c_int64), ("root", ctypes.c_double * 3)]
 
 
 def library_path() -> str:
@@ -75,6 +76,7 @@ def _load():
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     sig = {
         "vp_plan_create": [ctypes.POINTER(P), I64, P, P, I64, P, P, P, P, I64, ctypes.POINTER(vp_options), P],
+        "vp_plan_create_many": [ctypes.POINTER(P), I32, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(vp_options), P],
         "vp_eval": [P, I32, P, I64, P, I64, P],
         "vp_eval_adjoint": [P, I32, P, I64, P, I64, P, I64, P, P],
         "vp_eval_host": [P, I32, P, P, P],
@@ -82,6 +84,7 @@ def _load():
         "vp_plan_phase_times": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(I32)],
         "vp_plan_destroy": [P],
+        "vp_plan_set_flags": [P, ctypes.c_uint32],
         "vp_status_string": [I32],
         "vp_last_error": [],
         "vp_version": [],
@@ -163,6 +166,46 @@ def vp_plan_create(src_xy, w, tgt_xy, csr=None, options: vp_options | None = Non
     return h
 
 
+def vp_plan_create_many(problems, options: vp_options | None = None, stream=None):
+    """One plan for many independent problems. `problems` is a sequence of
+    (src_xy, w, tgt_xy, csr or None, root or None); inputs may be numpy or torch."""
+    import torch
+    lib = _load()
+    n = len(problems)
+    keep = []
+    ns = (ctypes.c_int64 * n)()
+    nt = (ctypes.c_int64 * n)()
+    nz = (ctypes.c_int64 * n)()
+    ps, pw, pt = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+    pr, pc, pv = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+    roots = (ctypes.c_double * (3 * n))()
+    any_csr = False
+    for k, (src_xy, w, tgt_xy, csr, root) in enumerate(problems):
+        src = _dev_f64(src_xy).reshape(-1, 2)
+        tgt = _dev_f64(tgt_xy).reshape(-1, 2)
+        wt = _dev_f64(w).reshape(-1)
+        keep += [src, tgt, wt]
+        ns[k], nt[k] = src.shape[0], tgt.shape[0]
+        ps[k], pw[k], pt[k] = src.data_ptr(), wt.data_ptr(), tgt.data_ptr()
+        if csr is not None:
+            any_csr = True
+            r = torch.as_tensor(np.asarray(csr[0], dtype=np.int64)).to("cuda").contiguous()
+            c = torch.as_tensor(np.asarray(csr[1], dtype=np.int32)).to("cuda").contiguous()
+            v = _dev_f64(csr[2]).reshape(-1)
+            keep += [r, c, v]
+            pr[k], pc[k], pv[k] = r.data_ptr(), c.data_ptr(), v.data_ptr()
+            nz[k] = c.numel()
+        if root is not None:
+            roots[3 * k], roots[3 * k + 1], roots[3 * k + 2] = root
+    h = ctypes.c_void_p()
+    st = lib.vp_plan_create_many(ctypes.byref(h), n, ns, ps, pw, nt, pt,
+                                 pr if any_csr else None, pc if any_csr else None, pv if any_csr else None,
+                                 nz if any_csr else None, roots,
+                                 ctypes.byref(options) if options is not None else None, _stream(stream))
+    _check(st, "vp_plan_create_many")
+    return h
+
+
 def vp_eval(plan, f, out=None, stream=None):
     """f: CUDA float64 tensor [ndens, n_src] (or [n_src]); returns out [ndens, n_tgt]."""
     import torch
@@ -241,6 +284,10 @@ def vp_plan_phase_times(plan) -> dict:
     return {names[i].decode(): ms[i] for i in range(min(n.value, cap))}
 
 
+def vp_plan_set_flags(plan, flags: int):
+    _check(_load().vp_plan_set_flags(plan, flags), "vp_plan_set_flags")
+
+
 def vp_plan_destroy(plan):
     if plan:
         _check(_load().vp_plan_destroy(plan), "vp_plan_destroy")
@@ -287,6 +334,14 @@ class Plan:
         info = vp_plan_info(h)
         return cls(h, int(info.n_src), int(info.n_tgt))
 
+    @classmethod
+    def create_many(cls, problems, p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0, stream=None) -> "Plan":
+        """problems: sequence of (src_xy, w, tgt_xy, csr or None, root or None)."""
+        opts = make_options(p_fmm, leaf, max_level, max_dens, flags, None)
+        h = vp_plan_create_many(problems, opts, stream)
+        info = vp_plan_info(h)
+        return cls(h, int(info.n_src), int(info.n_tgt))
+
     def eval(self, f, out=None, stream=None):
         return vp_eval(self.handle, f, out, stream)
 
@@ -295,6 +350,9 @@ class Plan:
 
     def eval_host(self, f_host, out_host=None, stream=None):
         return vp_eval_host(self.handle, f_host, out_host, stream)
+
+    def set_flags(self, flags: int):
+        vp_plan_set_flags(self.handle, flags)
 
     def info(self) -> vp_plan_stats:
         return vp_plan_info(self.handle)

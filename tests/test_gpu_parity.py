@@ -248,3 +248,74 @@ def test_float_float_paths_match_fp64(leaf, seed):
     diff = rel_err(prob, outs[0], outs[1])
     print(f"float-float vs FP64 kernels, leaf={leaf}: {diff:.3e}")
     assert diff <= 1e-12
+
+
+def test_many_problems_one_plan():
+    # uneven independent problems in one forest plan: each block of the result
+    # equals that problem alone (oracle), and interactions never cross problems
+    probs = [inputs.cloud_problem(n, m, ndens=2, shared=min(n, m) // 3, seed=60 + k)
+             for k, (n, m) in enumerate([(700, 500), (3000, 2000), (150, 900), (1200, 1200), (40, 30)])]
+    probs.append(inputs.box_grid_problem(nbox=5, order=8, ndens=2))
+    for k, p in enumerate(probs):  # move problems apart so that a wrong cross-term would show
+        shift = np.array([10.0 * k, -7.0 * k])
+        p.src_xy = p.src_xy + shift
+        p.tgt_xy = p.tgt_xy + shift
+    plan = vp.Plan.create_many([(p.src_xy, p.w, p.tgt_xy, p.csr, None) for p in probs], p_fmm=30, leaf=32,
+                               max_dens=2)
+    assert plan.info().n_problems == len(probs)
+    f = torch.as_tensor(np.concatenate([p.f for p in probs], axis=1), device="cuda")
+    out = plan.eval(f).cpu().numpy()
+    col = 0
+    for p in probs:
+        ref = oracle.evaluate(p.src_xy, p.w, p.f, p.tgt_xy, p.csr)
+        assert rel_err(p, out[:, col:col + p.n_tgt], ref) <= TOL
+        col += p.n_tgt
+    # adjoint through the forest
+    g = np.random.default_rng(4).standard_normal((2, plan.n_tgt))
+    gf, _ = plan.adjoint(torch.as_tensor(g, device="cuda"))
+    gf = gf.cpu().numpy()
+    cs, ct = 0, 0
+    for p in probs:
+        ref = oracle.adjoint(p.src_xy, p.w, g[:, ct:ct + p.n_tgt], p.tgt_xy, p.csr)
+        scale = np.abs(g[:, ct:ct + p.n_tgt]).sum(axis=1)[:, None] * p.w.max()
+        assert np.max(np.abs(gf[:, cs:cs + p.n_src] - ref) / scale) <= TOL
+        cs += p.n_src
+        ct += p.n_tgt
+    plan.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    prob = inputs.cloud_problem(2500, 2000, ndens=3, shared=500, seed=71)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=24, leaf=32, max_dens=4)
+    f = torch.as_tensor(prob.f, device="cuda")
+    ref = plan.eval(f).clone()
+    plan.set_flags(vp.VP_FLAG_GRAPH)
+    out = torch.empty_like(ref)
+    for _ in range(3):  # capture, then replays into the same buffers
+        out.zero_()
+        plan.eval(f, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    f2 = f * 2.0  # new arguments: a second graph
+    out2 = plan.eval(f2)
+    torch.cuda.synchronize()
+    assert torch.allclose(out2, 2.0 * ref, rtol=1e-14, atol=1e-14 * float(ref.abs().max()))
+    with pytest.raises(vp.VPError):
+        plan.set_flags(vp.VP_FLAG_FP64)
+    plan.close()
+
+
+def test_autotuner_picks_an_accurate_fast_configuration():
+    from paper_2203_05933_gb300 import autotune
+    prob = inputs.cloud_problem(6000, 6000, seed=81, csr_per_row=0)
+    res = autotune.tune(prob.src_xy, prob.w, prob.tgt_xy, ndens=2, geometry="test-cloud", use_cache=False,
+                        steps=2)
+    assert res["p_fmm"] in (16, 24, 30) and res["leaf"] in (32, 64, 128)
+    assert res["err"] <= 1e-11
+    assert len(res["table"]) == 9
+    # the chosen configuration really meets the gate against the oracle
+    plan, out = run_forward(inputs.Problem("c", prob.src_xy, prob.w, prob.tgt_xy, prob.f), p_fmm=res["p_fmm"],
+                            leaf=res["leaf"])
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy)
+    assert rel_err(prob, out, ref) <= TOL
+    plan.close()
