@@ -35,7 +35,7 @@ UNIT = "Mpoints/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM (measured), 152 SMs, 2070 MHz
 FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12     # FP32/INT32 lane-operations per second (T ops/s)
 P2P_FLOP_PER_PAIR = 27.0  # 7 flops + 20 flop-equivalents for one FP64 log (stated convention)
-P2P_FF_OPS_PER_PAIR = 90.0  # FP32 operations of the float-float pair evaluation (k_leaf_ff)
+P2P_FF_OPS_PER_PAIR = 77.0  # FP32 operations of the float-float pair evaluation (k_leaf_ff, exact-hi pairs)
 
 
 def hbm_peak():
@@ -74,8 +74,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--p", type=int, default=30)
-    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--p", type=int, default=0, help="expansion order (0: autotuned with the leaf size)")
+    ap.add_argument("--leaf", type=int, default=0, help="leaf size (0: autotuned with the expansion order)")
     ap.add_argument("--batched", type=int, default=64, help="densities of the batched leg (0: skip)")
     ap.add_argument("--size", default="full", choices=["full", "medium", "small"],
                     help="disk levels 7-9 (1.1 M nodes), 6-8 (profiling) or 5-7")
@@ -251,6 +251,13 @@ def main():
     prob = make_problem(args, rank)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.p == 0 or args.leaf == 0:
+        from paper_2203_05933_gb300 import autotune
+        tuned = autotune.tune(prob.src_xy, prob.w, prob.tgt_xy, ndens=1, geometry=prob.name, root=prob.root,
+                              use_cache=False, steps=3)
+        args.p = args.p or tuned["p_fmm"]
+        args.leaf = args.leaf or tuned["leaf"]
     plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=args.p, leaf=args.leaf,
                           max_dens=8, flags=vp.VP_FLAG_GRAPH, root=prob.root)
     info = plan.info()
@@ -413,6 +420,10 @@ def main():
         "gpu_launches": int(launches_per_eval * args.steps),
         "wall_s": wall,
         "graph": True,
+        "autotune": None if tuned is None else {
+            "chosen": {"p_fmm": tuned["p_fmm"], "leaf": tuned["leaf"]}, "tol": tuned["tol"], "safety": tuned["safety"],
+            "table": [{k: r[k] for k in ("p_fmm", "leaf", "err", "ms")} for r in tuned["table"]],
+            "tuning_s": tuned["tuning_s"]},
     }
     print(json.dumps(line), flush=True)
     plan.close()

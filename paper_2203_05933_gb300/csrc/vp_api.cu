@@ -237,7 +237,7 @@ std::vector<float> make_list_offsets(const Tree& T, const std::vector<int32_t>& 
 }
 
 // Leaf-relative coordinates of every point of each leaf: ((x, y) - centre)/side,
-// each component split into hi + lo floats.
+// each component split into hi + lo floats, hi on the grid 2^-21.
 std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted, bool sources)
 {
     const size_t n = xy_sorted.size() / 2;
@@ -250,7 +250,11 @@ std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted,
         for (int32_t i = p0; i < p1; ++i) {
             const double rx = (xy_sorted[2 * (size_t)i] - cx) / side;
             const double ry = (xy_sorted[2 * (size_t)i + 1] - cy) / side;
-            const float xh = (float)rx, yh = (float)ry;
+            // hi parts on the grid 2^-21: |rho| <= 1/2 needs 20 bits, and after the
+            // exact shift/scale to a neighbouring leaf one level apart (factor 1/2
+            // or 2) the difference of two hi parts still fits 24 bits
+            const float xh = (float)(std::nearbyint(rx * 2097152.0) / 2097152.0);
+            const float yh = (float)(std::nearbyint(ry * 2097152.0) / 2097152.0);
             r[4 * (size_t)i + 0] = xh;
             r[4 * (size_t)i + 1] = (float)(rx - (double)xh);
             r[4 * (size_t)i + 2] = yh;

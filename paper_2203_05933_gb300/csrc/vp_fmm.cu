@@ -851,6 +851,62 @@ constexpr float kLn2Lo = 1.0f * (float)(0.693147180559945309417232121458176568 -
 
 }  // namespace fflog
 
+// Float-float direct sum of one target over a staged tile of charges:
+// ah + al += sum_k q_k log r_k'^2, coincident charges collected in qco.
+// EXACT: the hi parts of target and source differ exactly in float.
+template <int ND, bool EXACT>
+__device__ __forceinline__ void p2p_tile(const float4 rt, const float4* __restrict__ s_rho,
+                                         const float2 (*__restrict__ s_q)[ND], int n,
+                                         const float4* __restrict__ s_tab, float* ah, float* al, ff::F* qco)
+{
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+        const float4 sr = s_rho[k];
+        float dxs, dxe, dys, dye;
+        if (EXACT) {
+            dxs = __fsub_rn(rt.x, sr.x);
+            dxe = __fsub_rn(rt.y, sr.y);
+            dys = __fsub_rn(rt.z, sr.z);
+            dye = __fsub_rn(rt.w, sr.w);
+        } else {
+            ff::two_sum(rt.x, -sr.x, dxs, dxe);
+            dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
+            ff::two_sum(rt.z, -sr.z, dys, dye);
+            dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
+        }
+        const float px = __fmul_rn(dxs, dxs);
+        float pxe = fmaf(dxs, dxs, -px);
+        pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
+        pxe = fmaf(dxe, dxe, pxe);
+        const float py = __fmul_rn(dys, dys);
+        float pye = fmaf(dys, dys, -py);
+        pye = fmaf(__fadd_rn(dys, dys), dye, pye);
+        pye = fmaf(dye, dye, pye);
+        float rs, re;
+        ff::two_sum(px, py, rs, re);
+        re = __fadd_rn(re, __fadd_rn(pxe, pye));
+        if (rs == 0.0f && re == 0.0f) {  // bitwise-coincident pair: no smooth term
+#pragma unroll
+            for (int d = 0; d < ND; ++d) qco[d] = ff::add(qco[d], ff::F{s_q[k][d].x, s_q[k][d].y});
+            continue;
+        }
+        float S, lo;
+        ff::log_pair(rs, re, s_tab, S, lo);  // (rs, re) need not be renormalised
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const float2 qq = s_q[k][d];
+            const float p = __fmul_rn(qq.x, S);
+            float pe = fmaf(qq.x, S, -p);
+            pe = fmaf(qq.x, lo, pe);
+            pe = fmaf(qq.y, S, pe);
+            float sh, se;
+            ff::two_sum(ah[d], p, sh, se);
+            ah[d] = sh;
+            al[d] = __fadd_rn(al[d], __fadd_rn(se, pe));
+        }
+    }
+}
+
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafThreads)
     k_leaf_ff(DevTree t, PassGeom g, const float2* __restrict__ qf, const float4* __restrict__ Mf,
@@ -947,62 +1003,33 @@ __global__ void __launch_bounds__(kLeafThreads)
                     const float4 m0 = Mf[(int64_t)A * P1 * ND + d];
                     qu[d] = ff::add(qu[d], ff::F{m0.x, m0.y});
                 }
+                // same level or one level apart: hi parts differ exactly (both on
+                // the 2^-22 grid after the exact shift/scale), so dx = (th - sh) + (tl - sl)
+                const bool exact_hi = uo.z >= 0.5f && uo.z <= 2.0f;
                 for (int sb = a0; sb < a1; sb += kLeafThreads) {
                     const int n = min(kLeafThreads, a1 - sb);
                     __syncthreads();
                     if (tid < n) {
                         const int j = sb + tid;
                         const float4 r = g.crho[j];
-                        const ff::F sx = ff::shift_scale(uo.x, uo.z, r.x, r.y);
-                        const ff::F sy = ff::shift_scale(uo.y, uo.z, r.z, r.w);
+                        ff::F sx, sy;
+                        if (exact_hi) {
+                            sx = ff::F{__fadd_rn(uo.x, __fmul_rn(uo.z, r.x)), __fmul_rn(uo.z, r.y)};
+                            sy = ff::F{__fadd_rn(uo.y, __fmul_rn(uo.z, r.z)), __fmul_rn(uo.z, r.w)};
+                        } else {
+                            sx = ff::shift_scale(uo.x, uo.z, r.x, r.y);
+                            sy = ff::shift_scale(uo.y, uo.z, r.z, r.w);
+                        }
                         s_rho[tid] = make_float4(sx.h, sx.l, sy.h, sy.l);
 #pragma unroll
                         for (int d = 0; d < ND; ++d) s_q[tid][d] = qf[(int64_t)j * ND + d];
                     }
                     __syncthreads();
                     if (valid) {
-#pragma unroll 2
-                        for (int k = 0; k < n; ++k) {
-                            const float4 sr = s_rho[k];
-                            float dxs, dxe, dys, dye;
-                            ff::two_sum(rt.x, -sr.x, dxs, dxe);
-                            dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
-                            ff::two_sum(rt.z, -sr.z, dys, dye);
-                            dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
-                            const float px = __fmul_rn(dxs, dxs);
-                            float pxe = fmaf(dxs, dxs, -px);
-                            pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
-                            pxe = fmaf(dxe, dxe, pxe);
-                            const float py = __fmul_rn(dys, dys);
-                            float pye = fmaf(dys, dys, -py);
-                            pye = fmaf(__fadd_rn(dys, dys), dye, pye);
-                            pye = fmaf(dye, dye, pye);
-                            float rs, re;
-                            ff::two_sum(px, py, rs, re);
-                            re = __fadd_rn(re, __fadd_rn(pxe, pye));
-                            const float r2h = __fadd_rn(rs, re);
-                            const float r2l = __fsub_rn(re, __fsub_rn(r2h, rs));
-                            if (r2h == 0.0f) {  // bitwise-coincident pair: no smooth term
-#pragma unroll
-                                for (int d = 0; d < ND; ++d)
-                                    qco[d] = ff::add(qco[d], ff::F{s_q[k][d].x, s_q[k][d].y});
-                                continue;
-                            }
-                            float S, lo;
-                            ff::log_pair(r2h, r2l, s_tab, S, lo);
-#pragma unroll
-                            for (int d = 0; d < ND; ++d) {
-                                const float2 qq = s_q[k][d];
-                                const float p = __fmul_rn(qq.x, S);
-                                float pe = fmaf(qq.x, S, -p);
-                                pe = fmaf(qq.x, lo, pe);
-                                pe = fmaf(qq.y, S, pe);
-                                float sh, se;
-                                ff::two_sum(ah[d], p, sh, se);
-                                ah[d] = sh;
-                                al[d] = __fadd_rn(al[d], __fadd_rn(se, pe));
-                            }
-                        }
+                        if (exact_hi)
+                            p2p_tile<ND, true>(rt, s_rho, s_q, n, s_tab, ah, al, qco);
+                        else
+                            p2p_tile<ND, false>(rt, s_rho, s_q, n, s_tab, ah, al, qco);
                     }
                 }
             }

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kGroupThreads)
                   const double* __restrict__ psi, const float2* __restrict__ xf, int64_t ld_xf,
                   double* __restrict__ out, int64_t ld_out)
 {
-    extern __shared__ float2 F[];  // [smem_m][ND]
+    extern __shared__ float2 F[];  // [ND][smem_m]: lanes read consecutive columns of one density
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int gi = blockIdx.x; gi < A.ngroups; gi += gridDim.x) {
         const int r0 = A.g_r0[gi], r1 = A.g_r0[gi + 1];
@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(kGroupThreads)
         __syncthreads();
         if (staged) {
             for (int i = threadIdx.x; i < m * ND; i += blockDim.x) {
-                const int k = i / ND, d = i % ND;
-                F[i] = xf[d * ld_xf + A.cols[c0 + k]];
+                const int k = i % m, d = i / m;
+                F[d * smem_m + k] = xf[d * ld_xf + A.cols[c0 + k]];
             }
         }
         __syncthreads();
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kGroupThreads)
                     if (k < m) {
 #pragma unroll
                         for (int d = 0; d < ND; ++d) {
-                            const float2 x = staged ? F[k * ND + d] : xf[d * ld_xf + A.cols[c0 + k]];
+                            const float2 x = staged ? F[d * smem_m + k] : xf[d * ld_xf + A.cols[c0 + k]];
                             acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].x, v[u].y}, ff::F{x.x, x.y}));
                         }
                     }

@@ -121,9 +121,10 @@ def box_grid_problem(nbox: int = 16, order: int = 8, ndens: int = 1, seed: int =
                      csr: str = "synthetic", name: str | None = None) -> Problem:
     """The uniform box-grid workload on [-1, 1]^2: sources = targets = the GL nodes.
 
-    csr: "synthetic" (seeded values on the own + 8 neighbour pattern), "none",
-    or a (rowptr, col, val) tuple supplied by the caller (e.g. the box
-    correction tables of the host set-up).
+    csr: "synthetic" (seeded values on the own + 8 neighbour pattern),
+    "corrections" (the singular/near-singular corrections computed by the host
+    set-up, setup.corrections.box_grid_csr), "none", or a (rowptr, col, val)
+    tuple supplied by the caller.
     """
     xy, w, _ = box_grid_nodes(nbox, order)
     rng = np.random.default_rng(seed)
@@ -137,6 +138,9 @@ def box_grid_problem(nbox: int = 16, order: int = 8, ndens: int = 1, seed: int =
     elif csr == "synthetic":
         rowptr, col = neighbour_csr_pattern(nbox, order)
         mat = (rowptr, col, synthetic_csr_values(rowptr, col, w, seed + 17))
+    elif csr == "corrections":
+        from .setup import corrections
+        mat = corrections.box_grid_csr(nbox, order)
     else:
         mat = None
     return Problem(name=name or f"boxgrid{nbox}x{nbox}_gl{order}", src_xy=xy, w=w, tgt_xy=xy.copy(),

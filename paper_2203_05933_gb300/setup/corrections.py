@@ -235,3 +235,33 @@ def box_grid_csr(nbox: int, order: int = 8, lo: float = -1.0, hi: float = 1.0, t
                     vals.append(T[by - ny + 1, bx - nx + 1, i])
                 rows_ptr.append(rows_ptr[-1] + npc * len(nb))
     return np.array(rows_ptr, np.int64), np.concatenate(cols), np.concatenate(vals)
+
+
+def box_grid_corrections_at(targets, nbox: int, order: int = 8, lo: float = -1.0, hi: float = 1.0):
+    """Correction rows for arbitrary targets inside the box grid (the generic,
+    target-dependent pre-computation of Sec. 4): each target couples to the
+    nodes of the box containing it and of the (up to) 8 boxes around it.
+    Returns CSR (rowptr, col, val) with columns in the grid's node order."""
+    targets = np.asarray(targets, float).reshape(-1, 2)
+    side = (hi - lo) / nbox
+    a = side / 2.0
+    x, y, _, _ = gl_box(order)
+    npc = order * order
+    lens, cols, vals = [], [], []
+    for t in targets:
+        bx = min(max(int((t[0] - lo) // side), 0), nbox - 1)
+        by = min(max(int((t[1] - lo) // side), 0), nbox - 1)
+        n_blocks = 0
+        for ny in range(max(0, by - 1), min(nbox, by + 2)):
+            for nx in range(max(0, bx - 1), min(nbox, bx + 2)):
+                c = ny * nbox + nx
+                cx, cy = lo + (nx + 0.5) * side, lo + (ny + 0.5) * side
+                z0 = np.array([(t[0] - cx) / a, (t[1] - cy) / a])
+                coinc = np.nonzero((cx + a * x == t[0]) & (cy + a * y == t[1]))[0]
+                cols.append(np.arange(c * npc, (c + 1) * npc, dtype=np.int32))
+                vals.append(box_node_corrections(z0, a, order, coincident=int(coinc[0]) if coinc.size else None))
+                n_blocks += 1
+        lens.append(n_blocks * npc)
+    rp = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    return rp, np.concatenate(cols), np.concatenate(vals)

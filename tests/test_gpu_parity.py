@@ -319,3 +319,20 @@ def test_autotuner_picks_an_accurate_fast_configuration():
     ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy)
     assert rel_err(prob, out, ref) <= TOL
     plan.close()
+
+
+def test_box_grid_with_area_to_line_corrections():
+    # the 16x16 box grid with the corrections of the host set-up: GPU against the
+    # oracle, and for f = 1 against the exact potential of the square
+    from test_oracle_pins import rect_potential
+    prob = inputs.box_grid_problem(nbox=16, order=8, ndens=1, csr="corrections")
+    plan, out = run_forward(prob, p_fmm=30, leaf=64)
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    assert rel_err(prob, out, ref) <= TOL
+    ones = torch.ones((1, prob.n_src), dtype=torch.float64, device="cuda")
+    v1 = plan.eval(ones).cpu().numpy()[0]
+    exact = np.array([rect_potential(x, y, -1, 1, -1, 1) for x, y in prob.tgt_xy])
+    err = float(np.max(np.abs(v1 - exact)))
+    print(f"16x16 grid, f = 1: max |V - exact| = {err:.3e}")
+    assert err < 1e-12
+    plan.close()
