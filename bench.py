@@ -36,6 +36,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM (measured),
 FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12     # FP32/INT32 lane-operations per second (T ops/s)
 P2P_FLOP_PER_PAIR = 27.0  # 7 flops + 20 flop-equivalents for one FP64 log (stated convention)
 P2P_FF_OPS_PER_PAIR = 77.0  # FP32 operations of the float-float pair evaluation (k_leaf_ff, exact-hi pairs)
+# DRAM bytes (read + write) per work unit from one ncu capture of the current
+# kernels on the medium disk case (profiles/*_disk_medium.md), scaled to a
+# launch by the units it processes; None once a kernel changes until re-profiled.
+PROFILED_TRAFFIC = {
+    "leaf": (14.818e6 / 159450440, "pairs", "profiles/k_leaf_ff_disk_medium.md"),
+    "m2l": (3.034e6 / 145118, "V-list pairs", "profiles/k_m2l_ff_disk_medium.md"),
+    "out": ((1298.684e6 + 5.309e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
+}
 
 
 def hbm_peak():
@@ -54,17 +62,17 @@ def roofline_models(info, prob, ndens=1):
         "leaf": {"bound": "alu", "kernel": "k_leaf_ff (float-float P2P + FP64 L2P/M2P)",
                  "work": info.p2p_pairs * P2P_FF_OPS_PER_PAIR * ndens, "unit": "T FP32-ops/s",
                  "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",
-                 "fp64_equiv_flop": info.p2p_pairs * P2P_FLOP_PER_PAIR * ndens,
+                 "fp64_equiv_flop": info.p2p_pairs * P2P_FLOP_PER_PAIR * ndens, "units": info.p2p_pairs,
                  "per_unit": f"{P2P_FF_OPS_PER_PAIR:.0f} FP32 ops per source-target pair"},
         "m2l": {"bound": "alu", "kernel": "k_m2l_ff (float-float scaled-Hankel M2L)",
                 "work": info.n_v_pairs * (P + 1) * (24.0 * P + 100.0) * ndens, "unit": "T FP32-ops/s",
                 "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",
-                "fp64_equiv_flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens,
+                "fp64_equiv_flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens, "units": info.n_v_pairs,
                 "per_unit": f"(P+1)(24P+100) FP32 ops per V-list pair, P={P}"},
-        "out": {"bound": "hbm", "kernel": "k_out_forward (CSR correction apply)",
-                "work": info.nnz * 12.0 + info.n_tgt * 8.0 * (2 * ndens + 1), "unit": "GB/s",
-                "peak": hbm, "peak_source": hbm_src,
-                "per_unit": "12 B per nonzero (int32 col + fp64 val) + 8 B per row per density in and out"},
+        "out": {"bound": "hbm", "kernel": "k_out_grouped (correction apply, rows grouped by shared column lists)",
+                "work": info.nnz * 8.0 + info.n_tgt * 8.0 * (2 * ndens + 1), "unit": "GB/s",
+                "peak": hbm, "peak_source": hbm_src, "units": info.nnz,
+                "per_unit": "8 B per nonzero (one 64-bit value) + 8 B per row per density in and out"},
     }
 
 
@@ -391,6 +399,10 @@ def main():
         r = {"bound": m["bound"], "kernel": m["kernel"], "achieved": achieved, "peak": m["peak"],
              "unit": m["unit"], "frac": achieved / m["peak"], "traffic": None, "ms": ms,
              "peak_source": m["peak_source"], "per_unit": m["per_unit"]}
+        if PROFILED_TRAFFIC.get(name) and m.get("units"):
+            per, what, src = PROFILED_TRAFFIC[name]
+            r["traffic"] = per * m["units"]
+            r["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum per {what}, {src}, scaled"
         if "fp64_equiv_flop" in m:
             fe = m["fp64_equiv_flop"] / (ms * 1e-3) / 1e12
             r["fp64_equiv"] = {"achieved_tflops": fe, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
