@@ -304,3 +304,151 @@ def many_problems(count: int = 256, n_min: int = 2048, n_max: int = 65536, seed:
                            f=np.ascontiguousarray(f), csr=own_cell_csr(cs, w, seed + 1000 + i), root=root,
                            meta={"kind": kind}))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Star domain with holes: r(theta) = 1 + 0.3 cos(5 theta), 12 circular holes
+# ---------------------------------------------------------------------------
+
+STAR_SIZES = {
+    # name: (base box level, refinement radius in Gaussian widths, total targets)
+    "4M": (8, 41.0, 1 << 22),
+    "1M": (7, 14.0, 1 << 20),
+    "small": (7, 0.0, 1 << 14),
+}
+
+
+def star_geometry(seed: int = SEED_BASE + 3, count: int = 50):
+    """Holes (rows cx, cy, R; radii uniform in [0.02, 0.08], gaps >= 0.12) and the
+    Gaussians of the density (centres uniform in the domain, widths log-uniform
+    in [1e-3, 1e-1], amplitudes N(0, 1))."""
+    from .setup import meshes
+
+    holes = meshes.star_holes(seed, gap=0.12)
+    rng = np.random.default_rng(seed + 1)
+    cen = []
+    while len(cen) < count:
+        p = rng.uniform(-1.3, 1.3, size=2)
+        if meshes.inside_star(np.array([p[0]]), np.array([p[1]]), holes)[0]:
+            cen.append(p)
+    width = np.exp(rng.uniform(np.log(1e-3), np.log(1e-1), size=count))
+    amp = rng.standard_normal(count)
+    return holes, np.array(cen), width, amp
+
+
+def f_star(x, y, centres, width, amp):
+    """Sum of Gaussians a_i exp(-|r - c_i|^2 / s_i^2)."""
+    out = np.zeros_like(x)
+    for (cx, cy), s, a in zip(centres, width, amp):
+        out += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (s * s))
+    return out
+
+
+def star_random_points(n: int, holes, seed: int):
+    """n seeded points uniform in the star minus its holes (rejection sampling)."""
+    from .setup import meshes
+
+    rng = np.random.default_rng(seed)
+    out = [np.zeros((0, 2))]
+    have = 0
+    while have < n:
+        p = rng.uniform(-1.3, 1.3, size=(max(2 * (n - have), 1024), 2))
+        p = p[meshes.inside_star(p[:, 0], p[:, 1], holes)]
+        out.append(p)
+        have += p.shape[0]
+    return np.ascontiguousarray(np.vstack(out)[:n])
+
+
+def cell_rows_csr(cell_start, tgt_cell, cell_cols=None):
+    """CSR whose row i holds the columns of cell tgt_cell[i]: the nodes of that
+    cell itself (cell_cols None), or cell_cols[c], the column list of cell c.
+    Returns (rowptr int64, col int32)."""
+    cell_start = np.asarray(cell_start, np.int64)
+    tgt_cell = np.asarray(tgt_cell, np.int64)
+    if cell_cols is None:
+        lens = np.diff(cell_start)[tgt_cell]
+        rowptr = np.zeros(tgt_cell.size + 1, np.int64)
+        np.cumsum(lens, out=rowptr[1:])
+        col = (np.repeat(cell_start[tgt_cell] - rowptr[:-1], lens) + np.arange(rowptr[-1])).astype(np.int32)
+        return rowptr, col
+    lens = np.array([cell_cols[c].size for c in tgt_cell], np.int64)
+    rowptr = np.zeros(tgt_cell.size + 1, np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    col = np.empty(int(rowptr[-1]), np.int32)
+    for i, c in enumerate(tgt_cell):
+        col[rowptr[i]:rowptr[i + 1]] = cell_cols[c]
+    return rowptr, col
+
+
+def star_problem(size: str = "4M", ndens: int = 1, seed: int = SEED_BASE + 3, targets: str = "mixed",
+                 csr: str = "own", extra_targets=None, name: str | None = None) -> Problem:
+    """The star-with-holes workload: quadtree boxes (8x8 Gauss-Legendre) of a
+    base level, refined towards the narrow Gaussians of the density (a box of
+    side b is split while b > 2 s_i and it lies within rho s_i of centre c_i),
+    plus bands of curved and straight degree-7 triangles (36 nodes) along the
+    star boundary and around the holes.
+
+    size: "4M" (about 4.1 M nodes, 2^22 targets), "1M" (about 1 M nodes, 2^20
+    targets) or "small" (unrefined level-7 boxes, 2^14 targets).
+    targets: "mixed" (a seeded subsample of the nodes, at most half of them and
+    of the total, plus uniform random interior points up to the total) or "nodes" (targets = sources).
+    csr: "own" (each target couples to the nodes of its cell; a random target
+    to those of the cell whose centre is nearest), "near" (the cells touching
+    that cell as well), or "none"; values are seeded stand-ins.
+    extra_targets: optional [k, 2] points appended to the targets (no
+    correction rows)."""
+    from .setup import meshes
+
+    base, rho, total = STAR_SIZES[size]
+    holes, cen, width, amp = star_geometry(seed)
+
+    def refine(level, x0, y0, b):
+        d = meshes._box_point_dist(x0, y0, b, cen[:, 0], cen[:, 1])
+        return bool(np.any((b > 2.0 * width) & (d < rho * width)))
+
+    mesh = meshes.star_mesh(holes, base_level=base, fine_level=11, refine=refine if rho > 0 else None)
+    xy, w = mesh.xy, mesh.w
+    f0 = f_star(xy[:, 0], xy[:, 1], cen, width, amp)
+    if ndens == 1:
+        f = f0[None, :]
+    else:
+        rng = np.random.default_rng(seed + 3)
+        f = np.empty((ndens, xy.shape[0]))
+        f[0] = f0
+        for d in range(1, ndens):
+            c = rng.uniform(-0.9, 0.9, size=(4, 2))
+            a = rng.standard_normal(4)
+            s = rng.uniform(0.05, 0.5, size=4)
+            f[d] = f_star(xy[:, 0], xy[:, 1], c, s, a)
+    node_cell = np.repeat(np.arange(mesh.ncell), np.diff(mesh.cell_start))
+    if targets == "nodes":
+        tgt = xy.copy()
+        tgt_cell = node_cell
+    else:
+        rng = np.random.default_rng(seed + 5)
+        n_sub = min(xy.shape[0] // 2, total // 2)
+        sub = np.sort(rng.choice(xy.shape[0], size=n_sub, replace=False))
+        rnd = star_random_points(total - n_sub, holes, seed + 6)
+        from scipy.spatial import cKDTree
+
+        bb = mesh.cell_bbox
+        cc = np.stack([(bb[:, 0] + bb[:, 1]) / 2, (bb[:, 2] + bb[:, 3]) / 2], axis=1)
+        _, near = cKDTree(cc).query(rnd)
+        tgt = np.ascontiguousarray(np.vstack([xy[sub], rnd]))
+        tgt_cell = np.concatenate([node_cell[sub], near])
+    mat = None
+    if csr in ("own", "near"):
+        cols = None
+        if csr == "near":
+            cols = meshes.near_cell_columns(mesh)
+        rowptr, col = cell_rows_csr(mesh.cell_start, tgt_cell, cols)
+        mat = (rowptr, col, synthetic_csr_values(rowptr, col, w, seed + 17))
+    if extra_targets is not None:
+        tgt = np.ascontiguousarray(np.vstack([tgt, np.asarray(extra_targets, float).reshape(-1, 2)]))
+        if mat is not None:
+            k = tgt.shape[0] - (mat[0].size - 1)
+            mat = (np.concatenate([mat[0], np.full(k, mat[0][-1], np.int64)]), mat[1], mat[2])
+    return Problem(name=name or f"star_{size}", src_xy=xy, w=w, tgt_xy=tgt, f=np.ascontiguousarray(f), csr=mat,
+                   root=(-1.3, -1.3, 2.6),
+                   meta={"n_cells": mesh.ncell, "n_triangles": int((mesh.cell_kind > 0).sum()), "holes": holes,
+                         "area": mesh.area, "base_level": base})

@@ -101,10 +101,11 @@ def affine_map(v, xi, eta):
     return x, np.full(xi.shape, J)
 
 
-def blended_map(v, curve, xi, eta):
+def blended_map(v, curve, xi, eta, signed: bool = False):
     """Curved triangle (Eq. deformed_triangle_maps): vertices v [3, 2], the edge
     from v[0] to v[1] follows curve(s) -> (lam, mu, dlam, dmu) for s in [0, 1]
-    with curve(0) = v[0], curve(1) = v[1]. Returns points [n, 2] and |det DR|."""
+    with curve(0) = v[0], curve(1) = v[1]. Returns points [n, 2] and |det DR|
+    (det DR itself with signed=True)."""
     v = np.asarray(v, float)
     lam, mu, dlam, dmu = curve(xi)
     g = (1 - xi - eta) / (1 - xi)
@@ -117,8 +118,8 @@ def blended_map(v, curve, xi, eta):
     y_xi = v[1, 1] - v[0, 1] + dg_dxi * phy + g * (dmu + v[0, 1] - v[1, 1])
     x_eta = v[2, 0] - v[0, 0] - phx / (1 - xi)
     y_eta = v[2, 1] - v[0, 1] - phy / (1 - xi)
-    J = np.abs(x_xi * y_eta - x_eta * y_xi)
-    return np.stack([x, y], axis=1), J
+    J = x_xi * y_eta - x_eta * y_xi
+    return np.stack([x, y], axis=1), (J if signed else np.abs(J))
 
 
 def circle_arc(cx, cy, r, th0, th1):
