@@ -89,6 +89,7 @@ def parse():
                     help="disk levels 7-9 (1.1 M nodes), 6-8 (profiling) or 5-7")
     ap.add_argument("--many", type=int, default=256, help="problems of the many-problem leg (0: skip)")
     ap.add_argument("--star", type=int, default=1, help="run the 4 M star-with-holes leg (0: skip)")
+    ap.add_argument("--upsampled", type=int, default=1, help="run the oversampled (q = 2p) disk leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     return ap.parse_args()
 
@@ -379,6 +380,32 @@ def main():
         mplan.close()
         del mf, mo
 
+    # oversampled leg: the same disk, densities at the p-nodes, FMM over the q = 2p nodes
+    # (16 x 16 per box, 81 per triangle), same correction matrix
+    upsampled = None
+    if args.upsampled > 0 and rank == 0:
+        from paper_2203_05933_gb300 import inputs
+        t0 = time.perf_counter()
+        uxy, uw, ups = inputs.disk_upsampling(seed=inputs.SEED_BASE + 2) if args.size == "full" else \
+            inputs.disk_upsampling(base_level=5 if args.size == "small" else 6,
+                                   fine_level=7 if args.size == "small" else 8, seed=inputs.SEED_BASE + 2)
+        gen_s = time.perf_counter() - t0
+        uplan = vp.Plan.create_upsampled(uxy, uw, prob.tgt_xy, prob.csr, ups, p_fmm=args.p, leaf=args.leaf,
+                                         max_dens=1, flags=vp.VP_FLAG_GRAPH, root=prob.root)
+        uo = torch.empty((1, prob.n_tgt), dtype=torch.float64, device=dev)
+        for _ in range(max(3, args.warmup)):
+            uplan.eval(f[:1], out=uo)
+        torch.cuda.synchronize()
+        ut = timed(lambda: uplan.eval(f[:1], out=uo), max(3, args.steps // 3))
+        ui = uplan.info()
+        upsampled = {"workload": prob.name + "_q2p", "n_q_nodes": int(ui.n_src), "n_f": int(ui.n_f),
+                     "n_tgt": int(ui.n_tgt), "cells": int(ui.n_cells), "p2p_pairs": int(ui.p2p_pairs),
+                     "value": prob.n_tgt / float(np.mean(ut)) / 1e6, "unit": UNIT,
+                     "ms_per_step": float(np.mean(ut)) * 1e3, "input_gen_s": gen_s,
+                     "launches_per_eval": int(ui.last_launches), "graph": True}
+        uplan.close()
+        del uo
+
     # star leg: star with 12 holes, about 4.2 M sources and 2^22 targets (half nodes,
     # half random interior points), own-cell correction rows; same P and leaf
     star = None
@@ -387,8 +414,15 @@ def main():
         t0 = time.perf_counter()
         sprob = inputs.star_problem("4M", csr="own")
         gen_s = time.perf_counter() - t0
+        sp_, sl_, stune = args.p, args.leaf, None
+        if tuned is not None:  # tune P and the leaf size on this geometry as well
+            from paper_2203_05933_gb300 import autotune
+            stune = autotune.tune(sprob.src_xy, sprob.w, sprob.tgt_xy, ndens=1, geometry=sprob.name,
+                                  root=sprob.root, use_cache=False, steps=3, p_choices=(16, 24),
+                                  leaf_choices=(64, 128))
+            sp_, sl_ = stune["p_fmm"], stune["leaf"]
         t0 = time.perf_counter()
-        splan = vp.Plan.create(sprob.src_xy, sprob.w, sprob.tgt_xy, sprob.csr, p_fmm=args.p, leaf=args.leaf,
+        splan = vp.Plan.create(sprob.src_xy, sprob.w, sprob.tgt_xy, sprob.csr, p_fmm=sp_, leaf=sl_,
                                max_dens=1, flags=vp.VP_FLAG_GRAPH, root=sprob.root)
         torch.cuda.synchronize()
         plan_s = time.perf_counter() - t0
@@ -403,7 +437,10 @@ def main():
                 "triangles": sprob.meta["n_triangles"], "p_fmm": int(si.p_fmm), "leaf": int(si.leaf),
                 "p2p_pairs": int(si.p2p_pairs), "value": sprob.n_tgt / float(np.mean(st)) / 1e6, "unit": UNIT,
                 "ms_per_step": float(np.mean(st)) * 1e3, "input_gen_s": gen_s, "plan_s": plan_s,
-                "launches_per_eval": int(si.last_launches), "graph": True}
+                "launches_per_eval": int(si.last_launches), "graph": True,
+                "autotune": None if stune is None else {
+                    "table": [{k: r[k] for k in ("p_fmm", "leaf", "err", "ms")} for r in stune["table"]],
+                    "tuning_s": stune["tuning_s"]}}
         splan.close()
         del sf, so, sprob
 
@@ -456,6 +493,7 @@ def main():
         "adjoint": adjoint,
         "many_problems": many,
         "star": star,
+        "upsampled": upsampled,
         "clocks": clk,
         "gpu_launches": int(launches_per_eval * args.steps),
         "wall_s": wall,

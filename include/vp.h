@@ -136,6 +136,56 @@ vp_status vp_plan_create_many(vp_plan* out, int32_t nprob,
                               const double* roots, const vp_options* opt, void* stream);
 
 /*
+ * vp_plan_create_upsampled — plan of the oversampled smooth quadrature
+ * (Sec. 2, "Oversampled smooth quadratures", Eq. Tk_smooth_quad; Sec. 4.2 for
+ * boxes; the twofold q = 2p of the Remark after Eq. nsrcs). The density is
+ * given at the p-nodes of each cell; the FMM sources are the cells' q-nodes,
+ * whose values are interpolated per cell by a fixed matrix of the cell's type,
+ *     f_q^k = O_{p,q} f_p^k,
+ * fused into the charge load. One evaluation computes
+ *     out[d][i] = sum_{j: r_j != t_i} w_j (O f[d])_j G(r_j, t_i) + sum_k Pi_ik f[d][k]
+ * where j runs over the q-nodes (src_xy, w: their positions and weights with
+ * Jacobians, device, as in vp_plan_create) and the correction's columns index
+ * the p-nodes (0 <= col < n_f, n_f = ups->f_start[ups->n_cells]).
+ *   ups: host description. Cell k owns q-nodes [src_start[k], src_start[k+1])
+ *   and p-nodes [f_start[k], f_start[k+1]) (both starting at 0, non-decreasing,
+ *   src_start[n_cells] = n_src; the counts equal the type's n_q and n_p).
+ *   A VP_UPS_DENSE type gives O [n_q][n_p] row-major in `mat`; a VP_UPS_TENSOR
+ *   type gives O = A (x) B (Kronecker product: row ra*qb + rb, column
+ *   ia*pb + ib) with A [qa][pa] in `a` and B [qb][pb] in `b`, row-major, as for
+ *   tensor-product nodes of boxes. 1 <= n_q, n_p <= 1024.
+ * On such a plan vp_eval, vp_eval_host and the f of vp_eval_adjoint take
+ * densities [ndens][ld_f] with ld_f >= n_f, and vp_eval_adjoint's grad_f is
+ * [ndens][ld_gf] with ld_gf >= n_f: grad_f = O^T (w * transposed sum) + Pi^T g.
+ * Other conventions and errors as in vp_plan_create.
+ */
+#define VP_UPS_DENSE 0
+#define VP_UPS_TENSOR 1
+typedef struct {
+    int32_t kind;               /* VP_UPS_DENSE or VP_UPS_TENSOR                         */
+    int32_t n_q, n_p;           /* rows (q-nodes) and columns (p-nodes) of O             */
+    int32_t qa, pa, qb, pb;     /* VP_UPS_TENSOR: n_q = qa * qb, n_p = pa * pb            */
+    int32_t reserved;
+    const double* mat;          /* VP_UPS_DENSE: [n_q][n_p], host                         */
+    const double* a;            /* VP_UPS_TENSOR: [qa][pa], host                          */
+    const double* b;            /* VP_UPS_TENSOR: [qb][pb], host                          */
+} vp_upsample_type;
+typedef struct {
+    int32_t n_types;
+    int32_t reserved;
+    const vp_upsample_type* types;  /* host [n_types]                                     */
+    int64_t n_cells;
+    const int32_t* cell_type;       /* host [n_cells], each in [0, n_types)               */
+    const int64_t* f_start;         /* host [n_cells + 1]                                 */
+    const int64_t* src_start;       /* host [n_cells + 1]                                 */
+} vp_upsample;
+vp_status vp_plan_create_upsampled(vp_plan* out,
+                                   int64_t n_src, const double* src_xy, const double* w,
+                                   int64_t n_tgt, const double* tgt_xy,
+                                   const int64_t* corr_rowptr, const int32_t* corr_col,
+                                   const double* corr_val, int64_t nnz,
+                                   const vp_upsample* ups, const vp_options* opt, void* stream);
+/*
  * vp_eval — "vp_eval(plan, f, out)": out[d][i] for d < ndens (formula above).
  *   f   [ndens][ld_f]   device, ld_f >= n_src, caller (input) order
  *   out [ndens][ld_out] device, ld_out >= n_tgt, caller (input) order; overwritten
@@ -190,6 +240,8 @@ typedef struct {
     int64_t last_launches;  /* kernel launches made by the last vp_eval on this plan      */
     int64_t n_problems;     /* independent problems in the plan (vp_plan_create_many)     */
     double root[3];         /* root square of the (first) problem                         */
+    int64_t n_f;            /* length of a density: n_src, or the p-nodes of an upsampled plan */
+    int64_t n_cells;        /* cells of an upsampled plan (0 otherwise)                    */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);

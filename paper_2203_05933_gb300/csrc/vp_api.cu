@@ -356,6 +356,9 @@ struct vp_plan_s {
     int nd_cap = 1;
     uint32_t flags = 0;
     int64_t n_src = 0, n_tgt = 0, nnz = 0;
+    int64_t n_f = 0;            // density length: n_src, or the p-nodes of an upsampled plan
+    bool ups = false;           // charges interpolated per cell from the p-nodes (oversampling)
+    DevUpsample dups;
     int32_t n_problems = 1;
     int32_t stat_levels = 0;
     int64_t stat_boxes = 0, stat_leaves = 0, stat_u = 0, stat_v = 0, stat_w = 0, stat_x = 0;
@@ -507,6 +510,7 @@ namespace {
 // One problem's inputs, copied to the host at plan time.
 struct ProblemIn {
     int64_t n_src = 0, n_tgt = 0, nnz = 0;
+    int64_t n_cols = 0;  // correction columns = density length (n_src, or the p-nodes of an upsampled plan)
     bool has_corr = false;
     std::vector<double> hs, hw, ht;
     std::vector<int64_t> hrow;
@@ -519,6 +523,7 @@ struct ProblemIn {
 // order, boxes level by level, interaction lists, correction in caller order.
 struct Built {
     int64_t n_src = 0, n_tgt = 0, nnz = 0;
+    int64_t n_cols = 0;
     bool has_corr = false;
     int n_levels = 0;
     std::vector<double> sxy, txy, ws;
@@ -536,8 +541,10 @@ struct Built {
 
 vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const double* w, int64_t n_tgt,
                        const double* tgt_xy, const int64_t* corr_rowptr, const int32_t* corr_col,
-                       const double* corr_val, int64_t nnz, cudaStream_t s)
+                       const double* corr_val, int64_t nnz, cudaStream_t s, int64_t n_cols = -1)
 {
+    if (n_cols < 0) n_cols = n_src;
+    P.n_cols = n_cols;
     if (n_src < 0 || n_tgt < 0 || nnz < 0) return fail(VP_ERR_ARG, "negative size");
     if (n_src > (1LL << 30) || n_tgt > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 points");
     if ((n_src > 0 && (!src_xy || !w)) || (n_tgt > 0 && !tgt_xy)) return fail(VP_ERR_ARG, "NULL point array");
@@ -572,7 +579,7 @@ vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const 
         for (int64_t i = 0; i < n_tgt; ++i)
             if (P.hrow[(size_t)i + 1] < P.hrow[(size_t)i]) return fail(VP_ERR_ARG, "CSR rowptr not monotone");
         for (int64_t k = 0; k < nnz; ++k)
-            if (P.hcol[(size_t)k] < 0 || P.hcol[(size_t)k] >= n_src) return fail(VP_ERR_ARG, "CSR column out of range");
+            if (P.hcol[(size_t)k] < 0 || P.hcol[(size_t)k] >= n_cols) return fail(VP_ERR_ARG, "CSR column out of range");
         if (!finite_all(P.hval)) return fail(VP_ERR_ARG, "non-finite CSR value");
     }
     return VP_OK;
@@ -587,6 +594,7 @@ std::string build_one(ProblemIn& P, const TreeOptions& to, Built& B)
     const int32_t nb = (int32_t)T.n_boxes();
     B.n_src = n_src;
     B.n_tgt = n_tgt;
+    B.n_cols = P.n_cols;
     B.nnz = P.nnz;
     B.has_corr = P.has_corr;
     B.n_levels = T.n_levels;
@@ -686,6 +694,7 @@ Built merge(std::vector<Built>& parts)
         newid[k].assign(parts[k].level.size(), -1);
     }
     M.n_src = ns;
+    M.n_cols = ns;
     M.n_tgt = nt;
     int32_t next = 0;
     M.level_start.push_back(0);
@@ -779,10 +788,11 @@ Built merge(std::vector<Built>& parts)
 
 vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
 {
-    const int64_t n_src = B.n_src, n_tgt = B.n_tgt, nnz = B.nnz;
+    const int64_t n_src = B.n_src, n_tgt = B.n_tgt, nnz = B.nnz, n_cols = B.n_cols;
     const bool has_corr = B.has_corr;
     const int32_t nb = (int32_t)B.level.size();
     p->n_src = n_src;
+    p->n_f = n_cols;
     p->n_tgt = n_tgt;
     p->nnz = has_corr ? nnz : 0;
     p->p2p_pairs = B.p2p_pairs;
@@ -804,9 +814,9 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     std::vector<int32_t> hcrow;
     std::vector<double> hcval;
     if (has_corr) {
-        hcptr.assign((size_t)n_src + 1, 0);
+        hcptr.assign((size_t)n_cols + 1, 0);
         for (int64_t k = 0; k < nnz; ++k) hcptr[(size_t)B.hcol[(size_t)k] + 1]++;
-        for (int64_t j = 0; j < n_src; ++j) hcptr[(size_t)j + 1] += hcptr[(size_t)j];
+        for (int64_t j = 0; j < n_cols; ++j) hcptr[(size_t)j + 1] += hcptr[(size_t)j];
         std::vector<int64_t> fill(hcptr.begin(), hcptr.end() - 1);
         hcrow.resize((size_t)nnz);
         hcval.resize((size_t)nnz);
@@ -905,7 +915,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         for (int pass = 0; pass < 2; ++pass) {
             HostGroups G;
             const bool fwd = pass == 0;
-            const int64_t nrows = fwd ? n_tgt : n_src;
+            const int64_t nrows = fwd ? n_tgt : n_cols;
             build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, G);
             DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
             int32_t *d_r0 = nullptr, *d_cols = nullptr;
@@ -927,7 +937,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         }
     }
     const int P1 = P + 1;
-    const int64_t npts = std::max<int64_t>(std::max<int64_t>(n_src, n_tgt), 1);
+    const int64_t npts = std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(n_src, n_tgt), n_cols), 1);
     if (e == cudaSuccess) e = p->alloc(&p->ws.q, (size_t)npts * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.qf, (size_t)npts * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.psi, (size_t)npts * 2 * p->nd_cap);
@@ -1106,6 +1116,126 @@ vp_status vp_plan_create_many(vp_plan* out, int32_t nprob, const int64_t* n_src,
     return VP_OK;
 }
 
+vp_status vp_plan_create_upsampled(vp_plan* out, int64_t n_src, const double* src_xy, const double* w,
+                                   int64_t n_tgt, const double* tgt_xy, const int64_t* corr_rowptr,
+                                   const int32_t* corr_col, const double* corr_val, int64_t nnz,
+                                   const vp_upsample* ups, const vp_options* opt_in, void* stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(VP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ups || ups->n_types < 1 || !ups->types || ups->n_cells < 0 || (ups->n_cells > 0 && !ups->cell_type) ||
+        !ups->f_start || !ups->src_start)
+        return fail(VP_ERR_ARG, "incomplete upsampling description");
+    if (ups->n_cells > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 cells");
+    // types: host tables of [kind, n_q, n_p, qa, pa, qb, pb, 0] and concatenated matrices
+    std::vector<int32_t> tinfo((size_t)ups->n_types * 8, 0);
+    std::vector<int64_t> toff((size_t)ups->n_types * 2, 0);
+    std::vector<double> mats;
+    int32_t max_q = 1, max_p = 1, max_tmp = 1;
+    for (int32_t t = 0; t < ups->n_types; ++t) {
+        const vp_upsample_type& ty = ups->types[t];
+        const std::string where = "upsampling type " + std::to_string(t) + ": ";
+        if (ty.n_q < 1 || ty.n_p < 1 || ty.n_q > 1024 || ty.n_p > 1024)
+            return fail(VP_ERR_ARG, where + "n_q and n_p must lie in [1, 1024]");
+        int32_t* ti = tinfo.data() + 8 * (size_t)t;
+        ti[1] = ty.n_q;
+        ti[2] = ty.n_p;
+        if (ty.kind == VP_UPS_TENSOR) {
+            if (ty.qa < 1 || ty.pa < 1 || ty.qb < 1 || ty.pb < 1 || (int64_t)ty.qa * ty.qb != ty.n_q ||
+                (int64_t)ty.pa * ty.pb != ty.n_p || (int64_t)ty.pa * ty.qb > 1024 || !ty.a || !ty.b)
+                return fail(VP_ERR_ARG, where + "tensor factors do not match n_q, n_p (or pa*qb > 1024)");
+            ti[0] = 1;
+            ti[3] = ty.qa;
+            ti[4] = ty.pa;
+            ti[5] = ty.qb;
+            ti[6] = ty.pb;
+            toff[2 * (size_t)t] = (int64_t)mats.size();
+            mats.insert(mats.end(), ty.a, ty.a + (size_t)ty.qa * ty.pa);
+            toff[2 * (size_t)t + 1] = (int64_t)mats.size();
+            mats.insert(mats.end(), ty.b, ty.b + (size_t)ty.qb * ty.pb);
+            max_tmp = std::max(max_tmp, ty.pa * ty.qb);
+        } else if (ty.kind == VP_UPS_DENSE) {
+            if (!ty.mat) return fail(VP_ERR_ARG, where + "NULL matrix");
+            toff[2 * (size_t)t] = (int64_t)mats.size();
+            toff[2 * (size_t)t + 1] = (int64_t)mats.size();
+            mats.insert(mats.end(), ty.mat, ty.mat + (size_t)ty.n_q * ty.n_p);
+        } else {
+            return fail(VP_ERR_ARG, where + "unknown kind");
+        }
+        max_q = std::max(max_q, ty.n_q);
+        max_p = std::max(max_p, ty.n_p);
+    }
+    if (!finite_all(mats)) return fail(VP_ERR_ARG, "non-finite upsampling matrix");
+    const int64_t nc = ups->n_cells;
+    if (ups->f_start[0] != 0 || ups->src_start[0] != 0) return fail(VP_ERR_ARG, "cell ranges must start at 0");
+    for (int64_t k = 0; k < nc; ++k) {
+        const int32_t t = ups->cell_type[k];
+        if (t < 0 || t >= ups->n_types) return fail(VP_ERR_ARG, "cell type out of range");
+        if (ups->src_start[k + 1] - ups->src_start[k] != ups->types[t].n_q ||
+            ups->f_start[k + 1] - ups->f_start[k] != ups->types[t].n_p)
+            return fail(VP_ERR_ARG, "cell " + std::to_string(k) + ": node counts differ from its type");
+    }
+    if (ups->src_start[nc] != n_src) return fail(VP_ERR_ARG, "cells do not cover the n_src q-nodes");
+    const int64_t n_f = ups->f_start[nc];
+    if (n_f > (1LL << 30)) return fail(VP_ERR_ARG, "more than 2^30 density nodes");
+    vp_options opt;
+    int P, leaf, max_level, max_dens;
+    vp_status st = plan_options(opt_in, opt, P, leaf, max_level, max_dens);
+    if (st != VP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ProblemIn in;
+    st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s, n_f);
+    if (st != VP_OK) return st;
+    TreeOptions to;
+    to.leaf = leaf;
+    to.max_level = max_level;
+    std::memcpy(to.root, opt.root, sizeof(to.root));
+    Built B;
+    std::string err = build_one(in, to, B);
+    if (!err.empty()) return fail(VP_ERR_ARG, err);
+    vp_plan p = new_plan(opt, P, leaf, max_dens);
+    if (!p) return fail(VP_ERR_OOM, "host allocation");
+    st = finalize(p, B, P, s);
+    if (st == VP_OK) {
+        std::vector<int32_t> ctype(ups->cell_type, ups->cell_type + nc);
+        std::vector<int64_t> fst(ups->f_start, ups->f_start + nc + 1), sst(ups->src_start, ups->src_start + nc + 1);
+        int32_t *d_ct = nullptr, *d_ti = nullptr;
+        int64_t *d_fs = nullptr, *d_ss = nullptr, *d_to = nullptr;
+        double* d_m = nullptr;
+        cudaError_t e = p->upload(&d_ct, ctype, s);
+        if (e == cudaSuccess) e = p->upload(&d_fs, fst, s);
+        if (e == cudaSuccess) e = p->upload(&d_ss, sst, s);
+        if (e == cudaSuccess) e = p->upload(&d_ti, tinfo, s);
+        if (e == cudaSuccess) e = p->upload(&d_to, toff, s);
+        if (e == cudaSuccess) e = p->upload(&d_m, mats, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "vp_plan_create_upsampled upload");
+        } else {
+            p->ups = true;
+            DevUpsample& u = p->dups;
+            u.n_cells = (int32_t)nc;
+            u.n_types = ups->n_types;
+            u.max_q = max_q;
+            u.max_p = max_p;
+            u.max_tmp = max_tmp;
+            u.cell_type = d_ct;
+            u.f_start = d_fs;
+            u.src_start = d_ss;
+            u.tinfo = d_ti;
+            u.toff = d_to;
+            u.mats = d_m;
+        }
+    }
+    if (st != VP_OK) {
+        delete p;
+        return st;
+    }
+    *out = p;
+    return VP_OK;
+}
+
 }  // extern "C"
 
 extern "C" {
@@ -1128,14 +1258,17 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
-        VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
+        if (p->ups)
+            VP_CUDA(launch_ups_charges(nd, p->dups, p->src_inv, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
+        else
+            VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
         p->timer.end(id);
         VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, use_fp64(p),
                                      p->timer.on ? &p->timer : nullptr, s));
         id = p->timer.begin("out");
         if (p->grouped) {
-            VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_src, fc, ld_f, p->ws.xf, s));
-            VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_src,
+            VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, s));
+            VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f,
                                        out + (int64_t)d0 * ld_out, ld_out, s));
             p->last_launches += 1;
         } else {
@@ -1196,8 +1329,8 @@ vp_status vp_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, doubl
     if (st != VP_OK) return st;
     if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
     if (ndens == 0 || p->n_tgt == 0) return VP_OK;
-    if (!out || (p->n_src > 0 && !f)) return fail(VP_ERR_ARG, "NULL density or output");
-    if (ld_f < p->n_src || ld_out < p->n_tgt) return fail(VP_ERR_ARG, "leading dimension too small");
+    if (!out || (p->n_f > 0 && !f)) return fail(VP_ERR_ARG, "NULL density or output");
+    if (ld_f < p->n_f || ld_out < p->n_tgt) return fail(VP_ERR_ARG, "leading dimension too small");
     cudaStream_t s = (cudaStream_t)stream;
     if ((p->flags & VP_FLAG_GRAPH) && !p->timer.on) return eval_graph(p, ndens, f, ld_f, out, ld_out, s);
     return enqueue_eval(p, ndens, f, ld_f, out, ld_out, s);
@@ -1213,26 +1346,38 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
     if (grad_tgt && p->n_tgt > 0) {
         if (ndens == 0) {
             VP_CUDA(cudaMemsetAsync(grad_tgt, 0, sizeof(double) * 2 * p->n_tgt, s));
-        } else if (!g || (p->n_src > 0 && !f) || ld_g < p->n_tgt || ld_f < p->n_src) {
+        } else if (!g || (p->n_f > 0 && !f) || ld_g < p->n_tgt || ld_f < p->n_f) {
             return fail(VP_ERR_ARG, "target gradient needs g and f with valid leading dimensions");
         }
     }
-    if (grad_f && p->n_src > 0) {
+    if (grad_f && p->n_f > 0) {
         if (ndens == 0) return VP_OK;
-        if ((p->n_tgt > 0 && !g) || ld_g < p->n_tgt || ld_gf < p->n_src)
+        if ((p->n_tgt > 0 && !g) || ld_g < p->n_tgt || ld_gf < p->n_f)
             return fail(VP_ERR_ARG, "grad_f needs g with valid leading dimensions");
     }
     if (ndens == 0) return VP_OK;
     p->timer.stream = s;
     p->timer.used = 0;
-    if (grad_f && p->n_src > 0) {
+    if (grad_f && p->n_f > 0) {
         PassGeom gg = adjoint_geom(p);
         for (int d0 = 0; d0 < ndens;) {
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* gc = g + (int64_t)d0 * ld_g;
             VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
             VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, use_fp64(p), nullptr, s));
-            if (p->grouped) {
+            if (p->ups) {
+                // grad_f = O^T (w * transposed sum at the q-nodes), then += Pi^T g
+                double* gfc = grad_f + (int64_t)d0 * ld_gf;
+                VP_CUDA(launch_ups_adjoint(nd, p->dups, p->src_inv, p->w_sorted, p->ws.psi, gfc, ld_gf, s));
+                if (p->grouped) {
+                    VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
+                    VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc, ld_gf,
+                                               s));
+                } else if (p->cptr) {
+                    VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_f, nullptr, nullptr, nullptr, p->cptr, p->crow,
+                                               p->cval, gc, ld_g, gfc, ld_gf, s));
+                }
+            } else if (p->grouped) {
                 VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                 VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
                                            grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
@@ -1248,7 +1393,11 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
         for (int d0 = 0; d0 < ndens;) {
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* fc = f + (int64_t)d0 * ld_f;
-            VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
+            if (p->ups)
+                VP_CUDA(launch_ups_charges(nd, p->dups, p->src_inv, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
+            else
+                VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf,
+                                       s));
             VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, use_fp64(p), nullptr, s));
             VP_CUDA(launch_grad_out(nd, d0 > 0, (int32_t)p->n_tgt, p->tgt_perm, p->ws.psi, g + (int64_t)d0 * ld_g,
                                     ld_g, grad_tgt, s));
@@ -1264,9 +1413,9 @@ vp_status vp_eval_host(vp_plan p, int32_t ndens, const double* f_host, double* o
     if (st != VP_OK) return st;
     if (ndens < 0) return fail(VP_ERR_ARG, "ndens < 0");
     if (ndens == 0) return VP_OK;
-    if ((p->n_src > 0 && !f_host) || (p->n_tgt > 0 && !out_host)) return fail(VP_ERR_ARG, "NULL host buffer");
+    if ((p->n_f > 0 && !f_host) || (p->n_tgt > 0 && !out_host)) return fail(VP_ERR_ARG, "NULL host buffer");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t nf = (size_t)ndens * (size_t)p->n_src, no = (size_t)ndens * (size_t)p->n_tgt;
+    const size_t nf = (size_t)ndens * (size_t)p->n_f, no = (size_t)ndens * (size_t)p->n_tgt;
     if (nf + no > p->stage_cap) {
         if (p->stage) cudaFree(p->stage);
         p->stage = nullptr;
@@ -1279,7 +1428,7 @@ vp_status vp_eval_host(vp_plan p, int32_t ndens, const double* f_host, double* o
     double* df = p->stage;
     double* dout = p->stage + nf;
     if (nf) VP_CUDA(cudaMemcpyAsync(df, f_host, nf * sizeof(double), cudaMemcpyHostToDevice, s));
-    st = vp_eval(p, ndens, df, p->n_src, dout, p->n_tgt, stream);
+    st = vp_eval(p, ndens, df, p->n_f, dout, p->n_tgt, stream);
     if (st != VP_OK) return st;
     if (no) VP_CUDA(cudaMemcpyAsync(out_host, dout, no * sizeof(double), cudaMemcpyDeviceToHost, s));
     VP_CUDA(cudaStreamSynchronize(s));
@@ -1310,6 +1459,8 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->root[0] = p->stat_root[0];
     o->root[1] = p->stat_root[1];
     o->root[2] = p->stat_root[2];
+    o->n_f = p->n_f;
+    o->n_cells = p->ups ? p->dups.n_cells : 0;
     return VP_OK;
 }
 

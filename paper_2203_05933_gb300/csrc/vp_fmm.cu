@@ -1104,10 +1104,15 @@ __global__ void k_out_adjoint(int32_t n_src, const int32_t* __restrict__ inv, co
                 for (int o = 16; o > 0; o >>= 1) s[d] += __shfl_xor_sync(0xffffffffu, s[d], o);
         }
         if (lane == 0) {
-            const int32_t js = inv[j];
-            const double wj = -kInv2Pi * w_sorted[js];
+            if (psi) {
+                const int32_t js = inv[j];
+                const double wj = -kInv2Pi * w_sorted[js];
 #pragma unroll
-            for (int d = 0; d < ND; ++d) out[d * ld_out + j] = fma(wj, psi[(int64_t)js * ND + d], s[d]);
+                for (int d = 0; d < ND; ++d) out[d * ld_out + j] = fma(wj, psi[(int64_t)js * ND + d], s[d]);
+            } else {  // accumulate onto out
+#pragma unroll
+                for (int d = 0; d < ND; ++d) out[d * ld_out + j] += s[d];
+            }
         }
     }
 }

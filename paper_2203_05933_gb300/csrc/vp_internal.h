@@ -89,6 +89,22 @@ struct DevGroupedCSR {
     const float2* vf = nullptr;        // [nnz] values as hi/lo floats
 };
 
+// Per-cell interpolation from the density's p-nodes to the FMM's q-nodes
+// (oversampled smooth quadrature). Type t: tinfo[8 t ..] = kind, n_q, n_p, qa,
+// pa, qb, pb, 0; its matrices start at mats + toff[2 t] (dense O, or A) and
+// mats + toff[2 t + 1] (B).
+struct DevUpsample {
+    int32_t n_cells = 0;
+    int32_t n_types = 0;
+    int32_t max_q = 0, max_p = 0, max_tmp = 0;  // largest n_q, n_p, pa * qb over the types
+    const int32_t* cell_type = nullptr;
+    const int64_t* f_start = nullptr;
+    const int64_t* src_start = nullptr;
+    const int32_t* tinfo = nullptr;
+    const int64_t* toff = nullptr;
+    const double* mats = nullptr;
+};
+
 struct Workspace {
     double* q = nullptr;      // [max(n_src, n_tgt)][ND] charges, tree order
     float2* qf = nullptr;     // [max(n_src, n_tgt)][ND] the same charges as hi/lo float pairs
@@ -133,11 +149,20 @@ cudaError_t launch_grad_out(int nd, bool accumulate, int32_t n_tgt, const int32_
                             cudaStream_t s);
 
 // Correction apply on the FP32 pipes (vp_spmv.cu): out[d][r] = -(1/2pi) w psi[inv[r]][d] + (A x)[d][r]
-// for every row r of A, w = w_sorted[inv[r]] or 1 when w_sorted is NULL.
+// for every row r of A, w = w_sorted[inv[r]] or 1 when w_sorted is NULL; with psi NULL,
+// out[d][r] += (A x)[d][r] instead (launch_out_adjoint likewise).
 cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, float2* xf, cudaStream_t s);
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
                                cudaStream_t s);
+
+// Oversampling (vp_upsample.cu). Charges q[pos][d] = w_pos (O f)[d][j], pos = inv[j]
+// the tree position of q-node j, fused with the interpolation; and the transposed
+// interpolation out[d][i] = sum_j O_ji (-(1/2pi) w_pos psi[pos][d]) over each cell.
+cudaError_t launch_ups_charges(int nd, const DevUpsample& u, const int32_t* inv, const double* w_sorted,
+                               const double* f, int64_t ld_f, double* q, float2* qf, cudaStream_t s);
+cudaError_t launch_ups_adjoint(int nd, const DevUpsample& u, const int32_t* inv, const double* w_sorted,
+                               const double* psi, double* out, int64_t ld_out, cudaStream_t s);
 
 bool p_supported(int P);
 

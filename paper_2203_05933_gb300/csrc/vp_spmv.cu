@@ -91,11 +91,16 @@ __global__ void __launch_bounds__(kGroupThreads)
                 }
             }
             if (lane == 0) {
-                const int32_t ri = inv[r];
-                const double wv = w_sorted ? w_sorted[ri] : 1.0;
+                if (psi) {
+                    const int32_t ri = inv[r];
+                    const double wv = w_sorted ? w_sorted[ri] : 1.0;
 #pragma unroll
-                for (int d = 0; d < ND; ++d)
-                    out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
+                    for (int d = 0; d < ND; ++d)
+                        out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
+                } else {  // accumulate onto out
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) out[d * ld_out + r] += ff::to_double(acc[0][d]);
+                }
             }
         }
     }

@@ -254,6 +254,24 @@ def disk_problem(base_level: int = 7, fine_level: int = 9, refine_radius=None, n
                          "base_level": base_level, "fine_level": fine_level})
 
 
+def disk_upsampling(base_level: int = 7, fine_level: int = 9, refine_radius=None, seed: int = SEED_BASE + 2,
+                    q_box: int = 16, m_tri: int = 9):
+    """q-nodes of the disk workload's cells for the oversampled smooth rule
+    (q = 2p: 16 x 16 Gauss-Legendre per box; collapsed Gauss rule with
+    m_tri^2 nodes per triangle) and the per-cell interpolation from the p-nodes
+    of disk_problem with the same arguments. Returns (xy_q, w_q, Upsampling)."""
+    from .setup import meshes, upsample
+
+    if refine_radius is None:
+        refine_radius = {base_level + 1: 0.11, base_level + 2: 0.04}
+    cen = disk_centres(seed)
+    mp = meshes.disk_mesh(base_level=base_level, fine_level=fine_level, centres=cen, refine_radius=refine_radius)
+    rule = upsample.collapsed_triangle_rule(m_tri)
+    mq = meshes.disk_mesh(base_level=base_level, fine_level=fine_level, centres=cen, refine_radius=refine_radius,
+                          box_order=q_box, tri_rule=rule)
+    return mq.xy, mq.w, upsample.mesh_upsampling(mp, mq, 8, q_box, 8, rule)
+
+
 def own_cell_csr(cell_start, w, seed: int):
     """Correction pattern that couples every node to the nodes of its own cell
     (block diagonal), with seeded stand-in values."""

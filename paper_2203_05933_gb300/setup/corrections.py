@@ -182,12 +182,28 @@ def box_basis_potentials(z0, order: int = 8, n_t: int = 16, n_s: int = 16) -> np
     return total
 
 
-def box_node_corrections(z0, a: float = 1.0, order: int = 8, coincident: int | None = None) -> np.ndarray:
+def box_node_corrections(z0, a: float = 1.0, order: int = 8, coincident: int | None = None,
+                         q: int | None = None) -> np.ndarray:
     """Correction weights (accurate minus smooth) of the order^2 GL nodes of the
     box c + a[-1,1]^2 for the target c + a z0. `coincident` is the index of the
-    node equal to the target, if any (its smooth term is omitted)."""
+    node equal to the target, if any (its smooth term is omitted).
+    q: the smooth rule is the oversampled one (Sec. 2, "Oversampled smooth
+    quadratures"; Sec. 4.2): q x q GL nodes carrying the values interpolated
+    from the order x order nodes, so the smooth weight of node i is
+    sum_j W^q_j G(z^q_j, z0) O_ji. The q-nodes never coincide with a p-node
+    target (disjoint Gauss-Legendre sets)."""
     x, y, W, Vinv = gl_box(order)
     pot = box_basis_potentials(z0, order) @ Vinv  # nodal potentials at unit scale
+    if q is not None:
+        from .upsample import box_upsample_1d
+
+        xq, yq, Wq, _ = gl_box(q)
+        L = box_upsample_1d(order, q)
+        rq = np.hypot(xq - z0[0], yq - z0[1])
+        if np.any(rq == 0.0):
+            raise ValueError("target on an oversampled node")
+        smooth = (Wq * (-INV_2PI) * np.log(rq)) @ np.kron(L, L)
+        return a * a * (pot - smooth)  # log a terms cancel: both rules integrate the nodal basis exactly
     r = np.hypot(x - z0[0], y - z0[1])
     corr = np.empty(order * order)
     with np.errstate(divide="ignore"):
@@ -198,10 +214,11 @@ def box_node_corrections(z0, a: float = 1.0, order: int = 8, coincident: int | N
     return a * a * corr
 
 
-def box_grid_correction_tables(order: int = 8, a: float = 1.0) -> np.ndarray:
+def box_grid_correction_tables(order: int = 8, a: float = 1.0, q: int | None = None) -> np.ndarray:
     """T[oy+1, ox+1, i, j]: correction of source node j of a box for target
     node i of the box at offset (ox, oy) in {-1, 0, 1}^2 (uniform grid, half
-    side a). One table per offset serves every box (Eq. Vkhat_box)."""
+    side a). One table per offset serves every box (Eq. Vkhat_box).
+    q: oversampled smooth rule (see box_node_corrections)."""
     x, y, W, _ = gl_box(order)
     n = order * order
     T = np.empty((3, 3, n, n))
@@ -210,16 +227,18 @@ def box_grid_correction_tables(order: int = 8, a: float = 1.0) -> np.ndarray:
             for i in range(n):
                 z0 = np.array([x[i] + 2.0 * ox, y[i] + 2.0 * oy])
                 T[oy + 1, ox + 1, i] = box_node_corrections(z0, a, order,
-                                                            coincident=i if (ox == 0 and oy == 0) else None)
+                                                            coincident=i if (ox == 0 and oy == 0) else None, q=q)
     return T
 
 
-def box_grid_csr(nbox: int, order: int = 8, lo: float = -1.0, hi: float = 1.0, tables=None):
+def box_grid_csr(nbox: int, order: int = 8, lo: float = -1.0, hi: float = 1.0, tables=None, q: int | None = None):
     """Correction matrix of the nbox x nbox box grid on [lo, hi]^2 with order^2
     GL nodes per box, in the node order of the box-grid generator (cell by
-    cell, x fastest) and the own + 8 neighbour pattern."""
+    cell, x fastest) and the own + 8 neighbour pattern. Rows are the p-node
+    targets, columns the p-nodes (the density samples), also with an
+    oversampled smooth rule (q)."""
     a = (hi - lo) / nbox / 2.0
-    T = box_grid_correction_tables(order, a) if tables is None else tables
+    T = box_grid_correction_tables(order, a, q) if tables is None else tables
     npc = order * order
     rows_ptr = [0]
     cols, vals = [], []

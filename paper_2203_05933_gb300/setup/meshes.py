@@ -83,12 +83,13 @@ def _staircase_loop(adm: np.ndarray):
 
 
 def disk_mesh(base_level: int = 7, fine_level: int = 9, centres=None, refine_radius=None,
-              delta: float = 0.8, box_order: int = 8, tri_p: int = 8) -> Mesh:
+              delta: float = 0.8, box_order: int = 8, tri_p: int = 8, tri_rule=None) -> Mesh:
     """Unit disk: quadtree boxes over [-1, 1]^2 at `base_level` inside
     r <= 1 - delta*h, refined towards `fine_level` near the given centres
     (refine a level-l box into level l+1 while it lies within refine_radius[l+1]
     of a centre), plus the triangle band. Box nodes: box_order^2 tensor
-    Gauss-Legendre; triangle nodes: tri_p (tri_p+1)/2 simplex nodes."""
+    Gauss-Legendre; triangle nodes: tri_p (tri_p+1)/2 simplex nodes, or the
+    given rule tri_rule = (xi, eta, w) on the reference triangle."""
     centres = np.zeros((0, 2)) if centres is None else np.asarray(centres, float)
     refine_radius = refine_radius or {}
     n = 1 << base_level
@@ -154,7 +155,7 @@ def disk_mesh(base_level: int = 7, fine_level: int = 9, centres=None, refine_rad
         tris.append((2, np.array(best[1]), (th0, th1)))
         tris.append((1, np.array(best[2]), None))
 
-    txi, teta, tw = simplex.simplex_rule(tri_p)
+    txi, teta, tw = simplex.simplex_rule(tri_p) if tri_rule is None else tri_rule
     bx, by, bw = simplex.gauss_legendre_box(box_order)
     xs, ws, start, bbox, kind, level = [], [], [0], [], [], []
     for k, v, th in tris:
@@ -456,7 +457,7 @@ def inside_star(x, y, holes, a: float = 0.3, k: int = 5):
 
 def star_mesh(holes, base_level: int = 8, fine_level: int = 11, refine=None, delta: float = 0.8,
               box_order: int = 8, tri_p: int = 8, a: float = 0.3, k: int = 5, lo: float = -1.3,
-              side: float = 2.6) -> Mesh:
+              side: float = 2.6, tri_rule=None) -> Mesh:
     """Star r(theta) = 1 + a cos(k theta) with circular holes (rows cx, cy, R):
     uniform boxes of level `base_level` over [lo, lo + side]^2 kept where they
     lie inside the star at distance >= delta*h from its boundary and at distance
@@ -538,7 +539,7 @@ def star_mesh(holes, base_level: int = 8, fine_level: int = 11, refine=None, del
         tris.extend(ht)
         arcs.extend([("circle", (hx, hy, hr)) if tk == 2 else None for tk, _, _ in ht])
 
-    txi, teta, tw = simplex.simplex_rule(tri_p)
+    txi, teta, tw = simplex.simplex_rule(tri_p) if tri_rule is None else tri_rule
     bx, by, bw = simplex.gauss_legendre_box(box_order)
     xs, ws, start, bbox, kind, level = [], [], [0], [], [], []
     for (tk, v, thr), arc in zip(tris, arcs):

@@ -31,7 +31,7 @@ TREE_ARRAYS = {
 }
 
 EXPORTED = [
-    "vp_plan_create", "vp_plan_create_many", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_plan_info",
+    "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_plan_info",
     "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy",
 ]
@@ -58,7 +58,24 @@ class vp_plan_stats(ctypes.Structure):
                 ("n_levels", ctypes.c_int32), ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("n_u_pairs", ctypes.c_int64), ("n_v_pairs", ctypes.c_int64), ("n_w_pairs", ctypes.c_int64),
                 ("n_x_pairs", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64), ("last_launches", ctypes.c_int64),
-                ("n_problems", ctypes.c_int64), ("root", ctypes.c_double * 3)]
+                ("n_problems", ctypes.c_int64), ("root", ctypes.c_double * 3), ("n_f", ctypes.c_int64),
+                ("n_cells", ctypes.c_int64)]
+
+
+VP_UPS_DENSE = 0
+VP_UPS_TENSOR = 1
+
+
+class vp_upsample_type(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_q", ctypes.c_int32), ("n_p", ctypes.c_int32), ("qa", ctypes.c_int32),
+                ("pa", ctypes.c_int32), ("qb", ctypes.c_int32), ("pb", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mat", ctypes.c_void_p), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
+class vp_upsample(ctypes.Structure):
+    _fields_ = [("n_types", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("types", ctypes.POINTER(vp_upsample_type)), ("n_cells", ctypes.c_int64),
+                ("cell_type", ctypes.c_void_p), ("f_start", ctypes.c_void_p), ("src_start", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -77,6 +94,8 @@ def _load():
     sig = {
         "vp_plan_create": [ctypes.POINTER(P), I64, P, P, I64, P, P, P, P, I64, ctypes.POINTER(vp_options), P],
         "vp_plan_create_many": [ctypes.POINTER(P), I32, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(vp_options), P],
+        "vp_plan_create_upsampled": [ctypes.POINTER(P), I64, P, P, I64, P, P, P, P, I64, ctypes.POINTER(vp_upsample),
+                                     ctypes.POINTER(vp_options), P],
         "vp_eval": [P, I32, P, I64, P, I64, P],
         "vp_eval_adjoint": [P, I32, P, I64, P, I64, P, I64, P, P],
         "vp_eval_host": [P, I32, P, P, P],
@@ -166,6 +185,66 @@ def vp_plan_create(src_xy, w, tgt_xy, csr=None, options: vp_options | None = Non
     return h
 
 
+def _csr_dev(csr):
+    import torch
+    if csr is None:
+        return None, None, None, 0
+    r, c, v = csr
+    rowptr = torch.as_tensor(np.asarray(r, dtype=np.int64) if not isinstance(r, torch.Tensor) else r)
+    rowptr = rowptr.to(device="cuda", dtype=torch.int64).contiguous()
+    col = torch.as_tensor(np.asarray(c, dtype=np.int32) if not isinstance(c, torch.Tensor) else c)
+    col = col.to(device="cuda", dtype=torch.int32).contiguous()
+    val = _dev_f64(v).reshape(-1)
+    return rowptr, col, val, int(col.numel())
+
+
+def vp_plan_create_upsampled(src_xy, w, tgt_xy, csr, ups, options: vp_options | None = None, stream=None):
+    """Plan of the oversampled smooth rule. src_xy, w: the q-nodes and their
+    weights; csr columns index the p-nodes; ups: an object with `types` (dicts
+    {"kind": "tensor", "a", "b"} or {"kind": "dense", "mat"}), `cell_type`,
+    `f_start`, `src_start` (see setup.upsample.Upsampling)."""
+    lib = _load()
+    src = _dev_f64(src_xy).reshape(-1, 2)
+    tgt = _dev_f64(tgt_xy).reshape(-1, 2)
+    wt = _dev_f64(w).reshape(-1)
+    if wt.numel() != src.shape[0]:
+        raise ValueError("weights and sources differ in length")
+    rowptr, col, val, nnz = _csr_dev(csr)
+    keep = []
+    nt = len(ups.types)
+    tys = (vp_upsample_type * nt)()
+    for k, ty in enumerate(ups.types):
+        if ty["kind"] == "tensor":
+            a = np.ascontiguousarray(ty["a"], np.float64)
+            b = np.ascontiguousarray(ty["b"], np.float64)
+            keep += [a, b]
+            tys[k].kind = VP_UPS_TENSOR
+            tys[k].qa, tys[k].pa = a.shape
+            tys[k].qb, tys[k].pb = b.shape
+            tys[k].n_q, tys[k].n_p = a.shape[0] * b.shape[0], a.shape[1] * b.shape[1]
+            tys[k].a, tys[k].b = a.ctypes.data, b.ctypes.data
+        else:
+            m = np.ascontiguousarray(ty["mat"], np.float64)
+            keep.append(m)
+            tys[k].kind = VP_UPS_DENSE
+            tys[k].n_q, tys[k].n_p = m.shape
+            tys[k].mat = m.ctypes.data
+    ct = np.ascontiguousarray(ups.cell_type, np.int32)
+    fs = np.ascontiguousarray(ups.f_start, np.int64)
+    ss = np.ascontiguousarray(ups.src_start, np.int64)
+    u = vp_upsample()
+    u.n_types = nt
+    u.types = tys
+    u.n_cells = ct.size
+    u.cell_type, u.f_start, u.src_start = ct.ctypes.data, fs.ctypes.data, ss.ctypes.data
+    h = ctypes.c_void_p()
+    st = lib.vp_plan_create_upsampled(ctypes.byref(h), src.shape[0], _ptr(src), _ptr(wt), tgt.shape[0], _ptr(tgt),
+                                      _ptr(rowptr), _ptr(col), _ptr(val), nnz, ctypes.byref(u),
+                                      ctypes.byref(options) if options is not None else None, _stream(stream))
+    _check(st, "vp_plan_create_upsampled")
+    return h
+
+
 def vp_plan_create_many(problems, options: vp_options | None = None, stream=None):
     """One plan for many independent problems. `problems` is a sequence of
     (src_xy, w, tgt_xy, csr or None, root or None); inputs may be numpy or torch."""
@@ -232,15 +311,15 @@ def vp_eval_adjoint(plan, g, grad_f=True, f=None, grad_tgt=False, stream=None):
     g2 = g2.contiguous()
     info = vp_plan_info(plan)
     nd = g2.shape[0]
-    gf = torch.empty((nd, info.n_src), dtype=torch.float64, device=g2.device) if grad_f else None
+    gf = torch.empty((nd, info.n_f), dtype=torch.float64, device=g2.device) if grad_f else None
     gt = torch.empty((info.n_tgt, 2), dtype=torch.float64, device=g2.device) if grad_tgt else None
     f2 = None
     if grad_tgt:
         if f is None:
             raise ValueError("the target gradient needs f")
         f2 = (f.reshape(1, -1) if f.dim() == 1 else f).contiguous()
-    st = lib.vp_eval_adjoint(plan, nd, _ptr(g2), max(info.n_tgt, 1), _ptr(gf), max(info.n_src, 1),
-                             _ptr(f2), max(info.n_src, 1), _ptr(gt), _stream(stream))
+    st = lib.vp_eval_adjoint(plan, nd, _ptr(g2), max(info.n_tgt, 1), _ptr(gf), max(info.n_f, 1),
+                             _ptr(f2), max(info.n_f, 1), _ptr(gt), _stream(stream))
     _check(st, "vp_eval_adjoint")
     if gf is not None and g.dim() == 1:
         gf = gf[0]
@@ -251,7 +330,7 @@ def vp_eval_host(plan, f_host: np.ndarray, out_host: np.ndarray | None = None, s
     """Host-buffer evaluation: f_host [ndens, n_src] float64 (pinned or pageable)."""
     lib = _load()
     info = vp_plan_info(plan)
-    f_host = np.ascontiguousarray(f_host, dtype=np.float64).reshape(-1, info.n_src) if info.n_src else \
+    f_host = np.ascontiguousarray(f_host, dtype=np.float64).reshape(-1, info.n_f) if info.n_f else \
         np.zeros((np.asarray(f_host).reshape(-1, 0).shape[0], 0))
     nd = f_host.shape[0]
     if out_host is None:
@@ -325,6 +404,11 @@ class Plan:
     handle: ctypes.c_void_p
     n_src: int
     n_tgt: int
+    n_f: int = -1  # density length (n_src unless upsampled)
+
+    def __post_init__(self):
+        if self.n_f < 0:
+            self.n_f = self.n_src
 
     @classmethod
     def create(cls, src_xy, w, tgt_xy, csr=None, p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0,
@@ -341,6 +425,16 @@ class Plan:
         h = vp_plan_create_many(problems, opts, stream)
         info = vp_plan_info(h)
         return cls(h, int(info.n_src), int(info.n_tgt))
+
+    @classmethod
+    def create_upsampled(cls, src_xy, w, tgt_xy, csr, ups, p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0,
+                         root=None, stream=None) -> "Plan":
+        """Oversampled smooth rule: src_xy, w are the q-nodes; densities live on the
+        p-nodes described by ups (setup.upsample.Upsampling)."""
+        opts = make_options(p_fmm, leaf, max_level, max_dens, flags, root)
+        h = vp_plan_create_upsampled(src_xy, w, tgt_xy, csr, ups, opts, stream)
+        info = vp_plan_info(h)
+        return cls(h, int(info.n_src), int(info.n_tgt), int(info.n_f))
 
     def eval(self, f, out=None, stream=None):
         return vp_eval(self.handle, f, out, stream)
