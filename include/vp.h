@@ -300,6 +300,53 @@ vp_status vp_tree_get(vp_tree tree, int32_t which, int32_t* dst, int64_t* count)
 vp_status vp_tree_destroy(vp_tree tree);
 
 /*
+ * Interpolation of nodal values to arbitrary points (Sec. 3.2.1, Eq.
+ * vals_to_coeffs and the Koornwinder expansion above it; Sec. 4.2 for boxes):
+ * inside each cell the values at the cell's nodes determine a polynomial
+ * expansion, coefficients a = C v (C the values-to-coefficients map of the
+ * cell's type), which is then summed at the reference coordinates of every
+ * point located in that cell:
+ *     out[d][k] = sum_b a_b phi_b(xi_k, eta_k).
+ * Typical use: V at off-node points from V at the nodes (vp_eval's output).
+ * Bases (n_basis = n_nodes of the type):
+ *   VP_BASIS_LEGENDRE2: P_i(xi) P_j(eta) on [-1, 1]^2, 0 <= i, j < order,
+ *     index b = j * order + i (eta-major, xi fastest, like the box nodes).
+ *   VP_BASIS_SIMPLEX: on {xi, eta >= 0, xi + eta <= 1}, total degree < order,
+ *     phi_(m,k) = P_m(s / t) t^m P_k^(2m+1,0)(2 eta - 1), s = 2 xi - 1 + eta,
+ *     t = 1 - eta, index running over m = 0..order-1 and k = 0..order-1-m
+ *     (m-major); P_k^(a,b) the Jacobi polynomials.
+ * Point location and the inverse cell maps are set-up work (static geometry):
+ * the caller gives each point's cell and reference coordinates.
+ */
+#define VP_BASIS_LEGENDRE2 0
+#define VP_BASIS_SIMPLEX 1
+typedef struct vp_interp_s* vp_interp;
+typedef struct {
+    int32_t basis;        /* VP_BASIS_*                                                  */
+    int32_t order;        /* 1..32                                                       */
+    int32_t n_nodes;      /* order^2 (LEGENDRE2) or order (order + 1) / 2 (SIMPLEX)       */
+    int32_t reserved;
+    const double* coef;   /* C [n_nodes][n_nodes] row-major, a_b = sum_i C[b][i] v_i, host */
+} vp_interp_type;
+/*
+ * vp_interp_create — copies the description into device memory.
+ *   types [n_types], cell_type [n_cells], node_start [n_cells + 1] (node range
+ *   of each cell in the value vector, starting at 0, counts = the type's
+ *   n_nodes): host. pt_cell [n_pts] int32 in [0, n_cells) and pt_ref
+ *   [n_pts][2] (xi, eta): device. Synchronizes `stream`.
+ */
+vp_status vp_interp_create(vp_interp* out, int32_t n_types, const vp_interp_type* types,
+                           int64_t n_cells, const int32_t* cell_type, const int64_t* node_start,
+                           int64_t n_pts, const int32_t* pt_cell, const double* pt_ref, void* stream);
+/*
+ * vp_interp_eval — v [ndens][ld_v] (device, ld_v >= node_start[n_cells]) to
+ * out [ndens][ld_out] (device, ld_out >= n_pts). Enqueues on `stream` only.
+ */
+vp_status vp_interp_eval(vp_interp ip, int32_t ndens, const double* v, int64_t ld_v,
+                         double* out, int64_t ld_out, void* stream);
+vp_status vp_interp_destroy(vp_interp ip);
+
+/*
  * vp_eval_direct_static — evaluation that allocates nothing.
  *
  * For callers that cannot allocate device memory when they need the volume

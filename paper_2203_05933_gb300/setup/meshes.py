@@ -34,6 +34,7 @@ class Mesh:
     cell_kind: np.ndarray   # [ncell] 0 box, 1 straight triangle, 2 curved triangle
     cell_level: np.ndarray  # [ncell] quadtree level for boxes, -1 for triangles
     area: float             # exact area of the domain
+    geom: list | None = None  # per cell: ("box", x0, y0, side) or ("tri", vertices [3, 2], curve or None)
 
     @property
     def n(self) -> int:
@@ -158,7 +159,9 @@ def disk_mesh(base_level: int = 7, fine_level: int = 9, centres=None, refine_rad
     txi, teta, tw = simplex.simplex_rule(tri_p) if tri_rule is None else tri_rule
     bx, by, bw = simplex.gauss_legendre_box(box_order)
     xs, ws, start, bbox, kind, level = [], [], [0], [], [], []
+    geom = []
     for k, v, th in tris:
+        geom.append(("tri", v, simplex.circle_arc(0.0, 0.0, 1.0, th[0], th[1]) if k == 2 else None))
         if k == 2:
             pts, J = simplex.blended_map(v, simplex.circle_arc(0.0, 0.0, 1.0, th[0], th[1]), txi, teta)
             lo_th, hi_th = th
@@ -185,9 +188,10 @@ def disk_mesh(base_level: int = 7, fine_level: int = 9, centres=None, refine_rad
         bbox.append([x0, x0 + side, y0, y0 + side])
         kind.append(0)
         level.append(lvl)
+        geom.append(("box", x0, y0, side))
     return Mesh(xy=np.ascontiguousarray(np.vstack(xs)), w=np.concatenate(ws),
                 cell_start=np.array(start, np.int64), cell_bbox=np.array(bbox), cell_kind=np.array(kind, np.int8),
-                cell_level=np.array(level, np.int32), area=math.pi)
+                cell_level=np.array(level, np.int32), area=math.pi, geom=geom)
 
 
 def near_cell_columns(mesh: Mesh, tol: float = 1e-9):
@@ -542,12 +546,16 @@ def star_mesh(holes, base_level: int = 8, fine_level: int = 11, refine=None, del
     txi, teta, tw = simplex.simplex_rule(tri_p) if tri_rule is None else tri_rule
     bx, by, bw = simplex.gauss_legendre_box(box_order)
     xs, ws, start, bbox, kind, level = [], [], [0], [], [], []
+    geom = []
     for (tk, v, thr), arc in zip(tris, arcs):
+        curve = None
         if tk == 2:
             if arc[0] == "star":
                 curve = star_curve(thr[0], thr[1], a, k)
             else:
                 curve = simplex.circle_arc(arc[1][0], arc[1][1], arc[1][2], thr[0], thr[1])
+        geom.append(("tri", v, curve))
+        if tk == 2:
             pts, J = simplex.blended_map(v, curve, txi, teta, signed=True)
             # the map must not fold: det DR keeps the sign of the counter-clockwise vertices
             if np.any(J <= 0) or np.any(simplex.blended_map(v, curve, *_edge_samples(), signed=True)[1] <= 0):
@@ -574,7 +582,8 @@ def star_mesh(holes, base_level: int = 8, fine_level: int = 11, refine=None, del
         bbox.append([x0, x0 + s, y0, y0 + s])
         kind.append(0)
         level.append(lvl)
+        geom.append(("box", x0, y0, s))
     area = math.pi * (1.0 + a * a / 2.0) - float(np.sum(math.pi * holes[:, 2] ** 2))
     return Mesh(xy=np.ascontiguousarray(np.vstack(xs)), w=np.concatenate(ws),
                 cell_start=np.array(start, np.int64), cell_bbox=np.array(bbox), cell_kind=np.array(kind, np.int8),
-                cell_level=np.array(level, np.int32), area=area)
+                cell_level=np.array(level, np.int32), area=area, geom=geom)

@@ -101,6 +101,24 @@ def affine_map(v, xi, eta):
     return x, np.full(xi.shape, J)
 
 
+def blended_map_jacobian(v, curve, xi, eta):
+    """The blending map of a curved triangle (as blended_map) and its partial
+    derivatives: returns (x, y, x_xi, y_xi, x_eta, y_eta)."""
+    v = np.asarray(v, float)
+    lam, mu, dlam, dmu = curve(xi)
+    g = (1 - xi - eta) / (1 - xi)
+    phx = lam - (1 - xi) * v[0, 0] - xi * v[1, 0]
+    phy = mu - (1 - xi) * v[0, 1] - xi * v[1, 1]
+    x = (1 - xi - eta) * v[0, 0] + xi * v[1, 0] + eta * v[2, 0] + g * phx
+    y = (1 - xi - eta) * v[0, 1] + xi * v[1, 1] + eta * v[2, 1] + g * phy
+    dg_dxi = -eta / (1 - xi) ** 2
+    x_xi = v[1, 0] - v[0, 0] + dg_dxi * phx + g * (dlam + v[0, 0] - v[1, 0])
+    y_xi = v[1, 1] - v[0, 1] + dg_dxi * phy + g * (dmu + v[0, 1] - v[1, 1])
+    x_eta = v[2, 0] - v[0, 0] - phx / (1 - xi)
+    y_eta = v[2, 1] - v[0, 1] - phy / (1 - xi)
+    return x, y, x_xi, y_xi, x_eta, y_eta
+
+
 def blended_map(v, curve, xi, eta, signed: bool = False):
     """Curved triangle (Eq. deformed_triangle_maps): vertices v [3, 2], the edge
     from v[0] to v[1] follows curve(s) -> (lam, mu, dlam, dmu) for s in [0, 1]

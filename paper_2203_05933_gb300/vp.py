@@ -33,7 +33,7 @@ TREE_ARRAYS = {
 EXPORTED = [
     "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_plan_info",
     "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
-    "vp_tree_build", "vp_tree_get", "vp_tree_destroy",
+    "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
 ]
 
 
@@ -70,6 +70,11 @@ class vp_upsample_type(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n_q", ctypes.c_int32), ("n_p", ctypes.c_int32), ("qa", ctypes.c_int32),
                 ("pa", ctypes.c_int32), ("qb", ctypes.c_int32), ("pb", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("mat", ctypes.c_void_p), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
+class vp_interp_type(ctypes.Structure):
+    _fields_ = [("basis", ctypes.c_int32), ("order", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("coef", ctypes.c_void_p)]
 
 
 class vp_upsample(ctypes.Structure):
@@ -110,6 +115,9 @@ def _load():
         "vp_tree_build": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options)],
         "vp_tree_get": [P, I32, P, ctypes.POINTER(I64)],
         "vp_tree_destroy": [P],
+        "vp_interp_create": [ctypes.POINTER(P), I32, ctypes.POINTER(vp_interp_type), I64, P, P, I64, P, P, P],
+        "vp_interp_eval": [P, I32, P, I64, P, I64, P],
+        "vp_interp_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -484,3 +492,55 @@ def vp_eval_direct_static(src_xy, w, f, tgt_xy, out, csr=None, stream=None):
             _ptr(rowptr), _ptr(col), _ptr(val), _ptr(out2), max(out2.stride(0), n_tgt, 1), _stream(stream))
     _check(st, "vp_eval_direct_static")
     return out
+
+
+class Interp:
+    """Interpolation of nodal values to points inside cells (vp_interp_*).
+    types: [(basis, order, C)] with basis 0 (tensor Legendre, boxes) or 1
+    (simplex); cell_type [n_cells]; node_start [n_cells + 1]; pt_cell [n_pts];
+    pt_ref [n_pts, 2] reference coordinates."""
+
+    def __init__(self, types, cell_type, node_start, pt_cell, pt_ref, stream=None):
+        import torch
+        lib = _load()
+        keep = []
+        tys = (vp_interp_type * len(types))()
+        for k, (basis, order, C) in enumerate(types):
+            c = np.ascontiguousarray(C, np.float64)
+            keep.append(c)
+            tys[k].basis, tys[k].order, tys[k].n_nodes = basis, order, c.shape[0]
+            tys[k].coef = c.ctypes.data
+        ct = np.ascontiguousarray(cell_type, np.int32)
+        ns = np.ascontiguousarray(node_start, np.int64)
+        pc = torch.as_tensor(np.ascontiguousarray(pt_cell, np.int32)).to("cuda")
+        pr = _dev_f64(pt_ref).reshape(-1, 2)
+        h = ctypes.c_void_p()
+        st = lib.vp_interp_create(ctypes.byref(h), len(types), tys, ct.size, ct.ctypes.data_as(ctypes.c_void_p),
+                                  ns.ctypes.data_as(ctypes.c_void_p), pc.numel(), _ptr(pc), _ptr(pr), _stream(stream))
+        _check(st, "vp_interp_create")
+        self.handle = h
+        self.n_pts = int(pc.numel())
+        self.n_vals = int(ns[-1])
+
+    def eval(self, v, out=None, stream=None):
+        """v: CUDA float64 [ndens, n_vals] (or [n_vals]); returns [ndens, n_pts]."""
+        import torch
+        squeeze = v.dim() == 1
+        v2 = (v.reshape(1, -1) if squeeze else v).contiguous()
+        if out is None:
+            out = torch.empty((v2.shape[0], self.n_pts), dtype=torch.float64, device=v2.device)
+        st = _load().vp_interp_eval(self.handle, v2.shape[0], _ptr(v2), max(v2.shape[1], 1), _ptr(out),
+                                    max(out.stride(0), self.n_pts, 1), _stream(stream))
+        _check(st, "vp_interp_eval")
+        return out[0] if squeeze else out
+
+    def close(self):
+        if self.handle:
+            _check(_load().vp_interp_destroy(self.handle), "vp_interp_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
