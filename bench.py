@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--many", type=int, default=256, help="problems of the many-problem leg (0: skip)")
     ap.add_argument("--star", type=int, default=1, help="run the 4 M star-with-holes leg (0: skip)")
     ap.add_argument("--upsampled", type=int, default=1, help="run the oversampled (q = 2p) disk leg (0: skip)")
+    ap.add_argument("--interp", type=int, default=1 << 20,
+                    help="random points of the interpolation leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     return ap.parse_args()
 
@@ -406,6 +408,37 @@ def main():
         uplan.close()
         del uo
 
+    # interpolation leg: V from the disk's nodes to uniform random points of the disk
+    interp_leg = None
+    if args.interp > 0 and rank == 0:
+        from paper_2203_05933_gb300 import inputs
+        from paper_2203_05933_gb300.setup import interp as sinterp
+        from paper_2203_05933_gb300.setup import meshes as smeshes
+        base, fine = {"full": (7, 9), "medium": (6, 8), "small": (5, 7)}[args.size]
+        t0 = time.perf_counter()
+        mesh = smeshes.disk_mesh(base_level=base, fine_level=fine, centres=inputs.disk_centres(inputs.SEED_BASE + 2),
+                                 refine_radius={base + 1: 0.11, base + 2: 0.04})
+        rng = np.random.default_rng(21)
+        rr = np.sqrt(rng.random(args.interp)) * (1.0 - 1e-9)
+        th = rng.random(args.interp) * 2 * np.pi
+        ipts = np.stack([rr * np.cos(th), rr * np.sin(th)], axis=1)
+        icell, iref = sinterp.locate_mesh(mesh, ipts)
+        gen_s = time.perf_counter() - t0
+        ip = vp.Interp(sinterp.mesh_types(), np.where(mesh.cell_kind == 0, 0, 1).astype(np.int32), mesh.cell_start,
+                       icell, iref)
+        io = torch.empty((1, args.interp), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            ip.eval(out[:1], out=io)
+        torch.cuda.synchronize()
+        it = timed(lambda: ip.eval(out[:1], out=io), max(3, args.steps // 3))
+        interp_leg = {"points": args.interp, "node_values": prob.n_tgt, "cells": mesh.ncell,
+                      "value": args.interp / float(np.mean(it)) / 1e6, "unit": "Mpoints/s",
+                      "ms_per_step": float(np.mean(it)) * 1e3, "setup_s": gen_s,
+                      "what": "V at uniform random points of the disk from V at the nodes "
+                              "(per-cell coefficients + basis recurrences), launched on the evaluation stream"}
+        ip.close()
+        del io
+
     # star leg: star with 12 holes, about 4.2 M sources and 2^22 targets (half nodes,
     # half random interior points), own-cell correction rows; same P and leaf
     star = None
@@ -494,6 +527,7 @@ def main():
         "many_problems": many,
         "star": star,
         "upsampled": upsampled,
+        "interp": interp_leg,
         "clocks": clk,
         "gpu_launches": int(launches_per_eval * args.steps),
         "wall_s": wall,

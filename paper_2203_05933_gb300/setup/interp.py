@@ -48,26 +48,29 @@ def mesh_types(box_order: int = 8, tri_p: int = 8):
     return [(BASIS_LEGENDRE2, box_order, box_coef(box_order)), (BASIS_SIMPLEX, tri_p, simplex_coef(tri_p))]
 
 
-def _invert_triangle(v, curve, p, iters: int = 30):
-    """Reference coordinates of point p in the triangle (affine, or blended when
-    curve is given); Newton from the affine guess for curved triangles."""
+def _invert_triangle(v, curve, p, iters: int = 40):
+    """Reference coordinates of the points p [k, 2] in one triangle (affine, or
+    blended when curve is given: Newton from the affine guess). Returns
+    (ref [k, 2], converged [k])."""
+    p = np.atleast_2d(p)
     A = np.array([[v[1, 0] - v[0, 0], v[2, 0] - v[0, 0]], [v[1, 1] - v[0, 1], v[2, 1] - v[0, 1]]])
-    r = np.linalg.solve(A, p - v[0])
+    r = np.linalg.solve(A, (p - v[0]).T).T
     if curve is None:
-        return r, True
-    xi, eta = float(r[0]), float(r[1])
+        return r, np.ones(p.shape[0], bool)
+    xi, eta = r[:, 0].copy(), r[:, 1].copy()
     for _ in range(iters):
-        xi_c = min(max(xi, 0.0), 1.0 - 1e-12)
-        x, y, xx, yx, xe, ye = simplex.blended_map_jacobian(v, curve, np.array([xi_c]), np.array([eta]))
-        res = np.array([x[0] - p[0], y[0] - p[1]])
-        J = np.array([[xx[0], xe[0]], [yx[0], ye[0]]])
-        step = np.linalg.solve(J, res)
-        xi, eta = xi_c - step[0], eta - step[1]
-        if np.max(np.abs(step)) < 1e-15:
+        xi = np.clip(xi, 0.0, 1.0 - 1e-12)
+        x, y, xx, yx, xe, ye = simplex.blended_map_jacobian(v, curve, xi, eta)
+        rx, ry = x - p[:, 0], y - p[:, 1]
+        det = xx * ye - xe * yx
+        dxi = (ye * rx - xe * ry) / det
+        deta = (-yx * rx + xx * ry) / det
+        xi, eta = xi - dxi, eta - deta
+        if np.max(np.abs(dxi) + np.abs(deta)) < 1e-15:
             break
-    x, y, *_ = simplex.blended_map_jacobian(v, curve, np.array([min(max(xi, 0.0), 1.0 - 1e-12)]), np.array([eta]))
-    ok = abs(x[0] - p[0]) + abs(y[0] - p[1]) < 1e-12
-    return np.array([xi, eta]), ok
+    x, y, *_ = simplex.blended_map_jacobian(v, curve, np.clip(xi, 0.0, 1.0 - 1e-12), eta)
+    ok = np.abs(x - p[:, 0]) + np.abs(y - p[:, 1]) < 1e-12
+    return np.stack([xi, eta], axis=1), ok
 
 
 def locate_mesh(mesh, pts, tol: float = 1e-12):
@@ -105,22 +108,29 @@ def locate_mesh(mesh, pts, tol: float = 1e-12):
             cy = np.array([gg[2] + gg[3] / 2 for gg in g]) if g else np.zeros(0)
             ref[hp, 0] = (pts[hp, 0] - cx) / (s / 2)
             ref[hp, 1] = (pts[hp, 1] - cy) / (s / 2)
-    tris = [k for k, g in enumerate(mesh.geom) if g[0] == "tri"]
+    tris = np.array([k for k, g in enumerate(mesh.geom) if g[0] == "tri"], np.int64)
     todo = np.nonzero(cell < 0)[0]
-    if todo.size and tris:
-        bb = mesh.cell_bbox[tris]
-        for i in todo:
-            p = pts[i]
-            cand = np.nonzero((bb[:, 0] - tol <= p[0]) & (p[0] <= bb[:, 1] + tol) & (bb[:, 2] - tol <= p[1])
-                              & (p[1] <= bb[:, 3] + tol))[0]
-            for c in cand:
-                k = tris[c]
+    if todo.size and tris.size:
+        from scipy.spatial import cKDTree
+
+        cen = np.array([mesh.geom[k][1].mean(axis=0) for k in tris])
+        kk = min(8, tris.size)
+        _, cand = cKDTree(cen).query(pts[todo], k=kk)
+        cand = cand.reshape(todo.size, kk)
+        for j in range(kk):
+            left = cell[todo] < 0
+            if not left.any():
+                break
+            idx = todo[left]
+            cj = cand[left, j]
+            for c in np.unique(cj):
+                sel = idx[cj == c]
+                k = int(tris[c])
                 _, v, curve = mesh.geom[k]
-                r, ok = _invert_triangle(v, curve, p)
-                if ok and r[0] >= -1e-10 and r[1] >= -1e-10 and r[0] + r[1] <= 1 + 1e-10:
-                    cell[i] = k
-                    ref[i] = r
-                    break
+                r, ok = _invert_triangle(v, curve, pts[sel])
+                inside = ok & (r[:, 0] >= -1e-10) & (r[:, 1] >= -1e-10) & (r[:, 0] + r[:, 1] <= 1 + 1e-10)
+                cell[sel[inside]] = k
+                ref[sel[inside]] = r[inside]
     if np.any(cell < 0):
         raise ValueError(f"{int(np.sum(cell < 0))} points lie in no cell")
     return cell.astype(np.int32), ref
