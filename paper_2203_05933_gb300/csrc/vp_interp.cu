@@ -8,7 +8,8 @@
 //                  sum_b a_b phi_b(xi, eta) with the basis generated by its
 //                  three-term recurrences (Legendre; scaled Legendre
 //                  Q_m = P_m(s/t) t^m; Jacobi P_k^(2m+1,0)), written back in
-//                  caller order.
+//                  caller order. The recurrence coefficients come from a
+//                  table built once on the host, so the kernel only multiplies.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +37,7 @@ struct vp_interp_s {
     double2* pref = nullptr;       // reference coordinates, sorted
     int32_t* pperm = nullptr;      // sorted position -> caller index
     double* coef = nullptr;        // [8][n_vals]
+    double* rec = nullptr;         // recurrence coefficients (kRecLeg + kRecJac doubles)
     std::vector<void*> allocs;
     bool alive = true;
 
@@ -60,6 +62,34 @@ namespace {
 
 constexpr int kInterpThreads = 128;
 constexpr int kMaxChunk = 8;
+constexpr int kMaxOrder = 32;
+// rec[2 n], rec[2 n + 1]: Legendre P_n = rec[2n] x P_{n-1} - rec[2n+1] P_{n-2} (n >= 2)
+// rec[kRecLeg + 3 (m kMaxOrder + n) + {0,1,2}]: Jacobi P_n^(2m+1,0)(b) = (c0 + c1 b) P_{n-1} - c2 P_{n-2}
+constexpr int kRecLeg = 2 * kMaxOrder;
+constexpr int kRecJac = 3 * kMaxOrder * kMaxOrder;
+
+std::vector<double> recurrence_table()
+{
+    std::vector<double> r((size_t)(kRecLeg + kRecJac), 0.0);
+    for (int n = 2; n < kMaxOrder; ++n) {
+        r[2 * (size_t)n] = (2.0 * n - 1.0) / n;
+        r[2 * (size_t)n + 1] = (n - 1.0) / n;
+    }
+    for (int m = 0; m < kMaxOrder; ++m) {
+        const double al = 2.0 * m + 1.0;
+        for (int n = 2; n < kMaxOrder; ++n) {
+            const double a1 = 2.0 * n * (n + al) * (2.0 * n + al - 2.0);
+            const double a2 = (2.0 * n + al - 1.0) * al * al;
+            const double a3 = (2.0 * n + al - 2.0) * (2.0 * n + al - 1.0) * (2.0 * n + al);
+            const double a4 = 2.0 * (n + al - 1.0) * (n - 1.0) * (2.0 * n + al);
+            double* c = r.data() + kRecLeg + 3 * ((size_t)m * kMaxOrder + n);
+            c[0] = a2 / a1;
+            c[1] = a3 / a1;
+            c[2] = a4 / a1;
+        }
+    }
+    return r;
+}
 
 vp_status ifail(vp_status st, const std::string& m)
 {
@@ -106,7 +136,8 @@ __global__ void __launch_bounds__(kInterpThreads)
     k_interp_eval(int64_t n_pts, const int32_t* __restrict__ pcell, const double2* __restrict__ pref,
                   const int32_t* __restrict__ pperm, const int32_t* __restrict__ cell_type,
                   const int64_t* __restrict__ node_start, const int32_t* __restrict__ tinfo,
-                  const double* __restrict__ coef, int64_t ld_c, double* __restrict__ out, int64_t ld_out)
+                  const double* __restrict__ rec, const double* __restrict__ coef, int64_t ld_c,
+                  double* __restrict__ out, int64_t ld_out)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_pts;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -119,31 +150,30 @@ __global__ void __launch_bounds__(kInterpThreads)
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc[d] = 0.0;
         if (basis == VP_BASIS_LEGENDRE2) {
-            // P_j(eta) outer, P_i(xi) inner; index j * order + i
+            // sum_j P_j(eta) sum_i a[j order + i] P_i(xi), the P_i(xi) generated once
+            double px[kMaxOrder];
+            px[0] = 1.0;
+            if (order > 1) px[1] = r.x;
+            for (int i = 2; i < order; ++i) px[i] = fma(rec[2 * i] * r.x, px[i - 1], -rec[2 * i + 1] * px[i - 2]);
             double py = 1.0, pym = 0.0;
             for (int j = 0; j < order; ++j) {
                 if (j == 1) {
                     pym = 1.0;
                     py = r.y;
                 } else if (j > 1) {
-                    const double nx = ((2 * j - 1) * r.y * py - (j - 1) * pym) / j;
+                    const double nx = fma(rec[2 * j] * r.y, py, -rec[2 * j + 1] * pym);
                     pym = py;
                     py = nx;
                 }
-                double px = 1.0, pxm = 0.0;
-                for (int i = 0; i < order; ++i) {
-                    if (i == 1) {
-                        pxm = 1.0;
-                        px = r.x;
-                    } else if (i > 1) {
-                        const double nx = ((2 * i - 1) * r.x * px - (i - 1) * pxm) / i;
-                        pxm = px;
-                        px = nx;
-                    }
-                    const double phi = px * py;
+                double inner[ND];
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) acc[d] = fma(a[d * ld_c + j * order + i], phi, acc[d]);
+                for (int d = 0; d < ND; ++d) inner[d] = 0.0;
+                for (int i = 0; i < order; ++i) {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) inner[d] = fma(a[d * ld_c + j * order + i], px[i], inner[d]);
                 }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = fma(inner[d], py, acc[d]);
             }
         } else {
             const double s = 2.0 * r.x - 1.0 + r.y, tt = 1.0 - r.y, b = 2.0 * r.y - 1.0, t2 = tt * tt;
@@ -154,23 +184,20 @@ __global__ void __launch_bounds__(kInterpThreads)
                     qm = 1.0;
                     q = s;
                 } else if (m > 1) {
-                    const double nq = ((2 * m - 1) * s * q - (m - 1) * t2 * qm) / m;
+                    const double nq = fma(rec[2 * m] * s, q, -rec[2 * m + 1] * t2 * qm);
                     qm = q;
                     q = nq;
                 }
-                const double al = 2.0 * m + 1.0;
+                const double al = 2.0 * m + 1.0;  // Jacobi alpha of this m
+                const double* jc = rec + kRecLeg + 3 * m * kMaxOrder;
                 double pj = 1.0, pjm = 0.0;
                 for (int kk = 0; kk < order - m; ++kk) {
                     if (kk == 1) {
                         pjm = 1.0;
                         pj = (al + 1.0) + (al + 2.0) * (b - 1.0) * 0.5;
                     } else if (kk > 1) {
-                        const double n = kk;
-                        const double a1 = 2.0 * n * (n + al) * (2.0 * n + al - 2.0);
-                        const double a2 = (2.0 * n + al - 1.0) * al * al;
-                        const double a3 = (2.0 * n + al - 2.0) * (2.0 * n + al - 1.0) * (2.0 * n + al);
-                        const double a4 = 2.0 * (n + al - 1.0) * (n - 1.0) * (2.0 * n + al);
-                        const double nj = ((a2 + a3 * b) * pj - a4 * pjm) / a1;
+                        const double* c = jc + 3 * kk;
+                        const double nj = fma(fma(c[1], b, c[0]), pj, -c[2] * pjm);
                         pjm = pj;
                         pj = nj;
                     }
@@ -204,8 +231,8 @@ cudaError_t interp_chunk(vp_interp ip, const double* v, int64_t ld_v, double* ou
     if (ip->n_pts > 0) {
         const int blocks = (int)std::min<int64_t>((ip->n_pts + kInterpThreads - 1) / kInterpThreads, 152 * 32);
         k_interp_eval<ND><<<blocks, kInterpThreads, 0, s>>>(ip->n_pts, ip->pcell, ip->pref, ip->pperm,
-                                                           ip->cell_type, ip->node_start, ip->tinfo, ip->coef,
-                                                           ip->n_vals, out, ld_out);
+                                                           ip->cell_type, ip->node_start, ip->tinfo, ip->rec,
+                                                           ip->coef, ip->n_vals, out, ld_out);
         e = cudaGetLastError();
     }
     return e;
@@ -233,7 +260,7 @@ vp_status vp_interp_create(vp_interp* out, int32_t n_types, const vp_interp_type
     for (int32_t t = 0; t < n_types; ++t) {
         const vp_interp_type& ty = types[t];
         const int o = ty.order;
-        if (o < 1 || o > 32 || !ty.coef) return ifail(VP_ERR_ARG, "interpolation type: order outside 1..32 or NULL C");
+        if (o < 1 || o > kMaxOrder || !ty.coef) return ifail(VP_ERR_ARG, "interpolation type: order outside 1..32 or NULL C");
         const int n = ty.basis == VP_BASIS_LEGENDRE2 ? o * o : ty.basis == VP_BASIS_SIMPLEX ? o * (o + 1) / 2 : -1;
         if (n < 0) return ifail(VP_ERR_ARG, "interpolation type: unknown basis");
         if (ty.n_nodes != n) return ifail(VP_ERR_ARG, "interpolation type: n_nodes does not match the basis");
@@ -306,6 +333,7 @@ vp_status vp_interp_create(vp_interp* out, int32_t n_types, const vp_interp_type
     up(&dref, sref);
     ip->pref = (double2*)dref;
     up(&ip->pperm, perm);
+    up(&ip->rec, recurrence_table());
     if (e == cudaSuccess) e = ip->alloc(&ip->coef, (size_t)kMaxChunk * std::max<int64_t>(ip->n_vals, 1));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
