@@ -92,40 +92,48 @@ namespace ff {
 constexpr float kLn2Hi = 363409.0f / 524288.0f;
 constexpr float kLn2Lo = (float)(0.693147180559945309417232121458176568 - 363409.0 / 524288.0);
 
-// log(x) for x = xh + xl > 0 given as a float pair, as (S, lo) with S + lo
-// accurate to about 1.3e-12 absolute: x = 2^e m (m in [1, 2)), k = top 7 bits of
-// m, u = m / c_k - 1 (|u| <= 2^-8), log x = e ln2 + T_k + log1p(u) with the
-// series to u^6. tab[k] = {fl(1/c_k), T_hi, T_lo, 0}, c_k = 1 + (k + 1/2)/128,
-// T = -log(fl(1/c_k)) (T_hi rounded to 19 fractional bits). Values with |e| > 15
-// (or xh = 0) take an FP64 log.
-__device__ __forceinline__ void log_pair(float xh, float xl, const float4* tab, float& S, float& lo)
+// log(x) for x = xh + xl with 2^-15 <= xh < 2^16 (the caller checks), as
+// (S, lo) with S + lo accurate to about 1.3e-12 absolute: x = 2^e m (m in
+// [1, 2)), k = top 7 bits of m, u = m / c_k - 1 (|u| <= 2^-8),
+// log x = e ln2 + T_k + log1p(u) with the series to u^5 (the u^6 term is below
+// 6e-16). tab[k] = {fl(1/c_k), T_hi, T_lo, 0}, c_k = 1 + (k + 1/2)/128,
+// T = -log(fl(1/c_k)) (T_hi rounded to 19 fractional bits, so that
+// e ln2_hi + T_hi is exact for |e| <= 15). Integer work is kept to bit
+// masks: the table offset, the mantissa, 2^-e and e come straight from the bits.
+__device__ __forceinline__ void log_pair_fast(float xh, float xl, const float4* tab, float& S, float& lo)
 {
     const int bits = __float_as_int(xh);
-    const int ex = (bits >> 23) - 127;
-    if (xh > 0.0f && (unsigned)(ex + 15) <= 30u) {
-        const float4 tk = tab[(bits >> 16) & 127];
-        const float mh = __int_as_float((bits & 0x007fffff) | 0x3f800000);
-        const float ml = __fmul_rn(xl, __int_as_float((127 - ex) << 23));
-        const float Pm = __fmul_rn(mh, tk.x);
-        const float Pe = fmaf(mh, tk.x, -Pm);
-        const float uh = __fsub_rn(Pm, 1.0f);
-        const float ul = fmaf(ml, tk.x, Pe);
-        const float ef = __fsub_rn(__int_as_float(0x4B400000 + ex), 12582912.0f);
-        const float hi = fmaf(ef, kLn2Hi, tk.y);
-        const float uhh = __fsub_rn(__fadd_rn(uh, 24.0f), 24.0f);
-        const float uhl = __fsub_rn(uh, uhh);
-        S = __fadd_rn(hi, uhh);
-        const float s2 = __fmul_rn(uh, uh);
-        const float s2e = fmaf(uh, uh, -s2);
-        const float poly = fmaf(uh, fmaf(uh, fmaf(uh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f);
-        float tt = __fmul_rn(__fmul_rn(s2, uh), poly);
-        tt = fmaf(-uh, ul, tt);
-        tt = fmaf(-0.5f, s2e, tt);
-        tt = __fadd_rn(tt, ul);
-        tt = __fadd_rn(tt, tk.z);
-        tt = __fadd_rn(tt, uhl);
-        tt = fmaf(-0.5f, s2, tt);
-        lo = fmaf(ef, kLn2Lo, tt);
+    const float4 tk = *(const float4*)((const char*)tab + ((bits >> 12) & 0x7F0));
+    const float mh = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+    const float ml = __fmul_rn(xl, __int_as_float(0x7F000000 - (bits & 0x7F800000)));  // xl 2^-e
+    const float Pm = __fmul_rn(mh, tk.x);
+    const float Pe = fmaf(mh, tk.x, -Pm);
+    const float uh = __fsub_rn(Pm, 1.0f);
+    const float ul = fmaf(ml, tk.x, Pe);
+    const float ef = __fsub_rn(__int_as_float((bits >> 23) + (0x4B400000 - 127)), 12582912.0f);  // e
+    const float hi = fmaf(ef, kLn2Hi, tk.y);
+    const float uhh = __fsub_rn(__fadd_rn(uh, 24.0f), 24.0f);
+    const float uhl = __fsub_rn(uh, uhh);
+    S = __fadd_rn(hi, uhh);
+    const float s2 = __fmul_rn(uh, uh);
+    const float s2e = fmaf(uh, uh, -s2);
+    const float poly = fmaf(uh, fmaf(uh, 0.2f, -0.25f), 1.0f / 3.0f);
+    float tt = __fmul_rn(__fmul_rn(s2, uh), poly);
+    tt = fmaf(-uh, ul, tt);
+    tt = fmaf(-0.5f, s2e, tt);
+    tt = __fadd_rn(tt, ul);
+    tt = __fadd_rn(tt, tk.z);
+    tt = __fadd_rn(tt, uhl);
+    tt = fmaf(-0.5f, s2, tt);
+    lo = fmaf(ef, kLn2Lo, tt);
+}
+
+// log(x) for any x = xh + xl > 0: the table path for 2^-15 <= xh < 2^16, an
+// FP64 log otherwise.
+__device__ __forceinline__ void log_pair(float xh, float xl, const float4* tab, float& S, float& lo)
+{
+    if (xh >= 0x1p-15f && xh < 0x1p16f) {
+        log_pair_fast(xh, xl, tab, S, lo);
     } else {
         const double ld = log((double)xh + (double)xl);
         S = __double2float_rn(ld);

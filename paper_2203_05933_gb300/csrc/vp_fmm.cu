@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(kLeafThreads)
 //   r2       = dx^2 + dy^2 (hi, lo)
 //   log r2   = e ln2 + T_k + log1p(u),  r2 = 2^e m, m in [1, 2),
 //              k = top 7 bits of m, u = m / c_k - 1 (|u| <= 2^-8),
-//              T_k = log c_k from a 128-entry table, log1p by its series to u^6.
+//              T_k = log c_k from a 128-entry table, log1p by its series to u^5.
 //            The exponent is limited to |e| <= 15 so that e * ln2_hi + T_hi is
 //            exact in one float (ln2_hi and T_hi have 19 fractional bits);
 //            other pairs (and only those) take an FP64 log.
@@ -859,7 +859,7 @@ __device__ __forceinline__ void p2p_tile(const float4 rt, const float4* __restri
                                          const float2 (*__restrict__ s_q)[ND], int n,
                                          const float4* __restrict__ s_tab, float* ah, float* al, ff::F* qco)
 {
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < n; ++k) {
         const float4 sr = s_rho[k];
         float dxs, dxe, dys, dye;
@@ -882,16 +882,23 @@ __device__ __forceinline__ void p2p_tile(const float4 rt, const float4* __restri
         float pye = fmaf(dys, dys, -py);
         pye = fmaf(__fadd_rn(dys, dys), dye, pye);
         pye = fmaf(dye, dye, pye);
-        float rs, re;
-        ff::two_sum(px, py, rs, re);
+        // r2 = px + py by Fast2Sum (both are >= 0, so the larger one goes first)
+        const float rs = __fadd_rn(px, py);
+        float re = __fsub_rn(fminf(px, py), __fsub_rn(rs, fmaxf(px, py)));
         re = __fadd_rn(re, __fadd_rn(pxe, pye));
-        if (rs == 0.0f && re == 0.0f) {  // bitwise-coincident pair: no smooth term
-#pragma unroll
-            for (int d = 0; d < ND; ++d) qco[d] = ff::add(qco[d], ff::F{s_q[k][d].x, s_q[k][d].y});
-            continue;
-        }
         float S, lo;
-        ff::log_pair(rs, re, s_tab, S, lo);  // (rs, re) need not be renormalised
+        if (rs >= 0x1p-15f && rs < 0x1p16f) {
+            ff::log_pair_fast(rs, re, s_tab, S, lo);  // (rs, re) need not be renormalised
+        } else {
+            if (rs == 0.0f && re == 0.0f) {  // bitwise-coincident pair: no smooth term
+#pragma unroll
+                for (int d = 0; d < ND; ++d) qco[d] = ff::add(qco[d], ff::F{s_q[k][d].x, s_q[k][d].y});
+                continue;
+            }
+            const double ld = log((double)rs + (double)re);
+            S = __double2float_rn(ld);
+            lo = __double2float_rn(ld - (double)S);
+        }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
             const float2 qq = s_q[k][d];
