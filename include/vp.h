@@ -242,6 +242,9 @@ typedef struct {
     double root[3];         /* root square of the (first) problem                         */
     int64_t n_f;            /* length of a density: n_src, or the p-nodes of an upsampled plan */
     int64_t n_cells;        /* cells of an upsampled plan (0 otherwise)                    */
+    int64_t sym_slots;      /* > 0: the near field is summed once per pair of adjacent leaves
+                               (evaluation points = quadrature nodes); the partial sums
+                               handed between leaves                                        */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);

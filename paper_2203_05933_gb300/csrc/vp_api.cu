@@ -881,6 +881,72 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         B.leaves.swap(sorted);
     }
     up(&d_leaves, B.leaves);
+    // symmetric near field when the charge points of both passes are the evaluation
+    // points (same coordinates, same tree order) and the U lists are symmetric
+    bool sym = !(p->flags & VP_FLAG_FP64) && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
+    if (sym) {
+        for (int32_t b : B.leaves) {
+            for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1] && sym; ++e2) {
+                const int32_t a = B.u_idx[(size_t)e2];
+                if (a == b) continue;
+                bool found = false;
+                for (int32_t f = B.u_ptr[(size_t)a]; f < B.u_ptr[(size_t)a + 1]; ++f)
+                    if (B.u_idx[(size_t)f] == b) found = true;
+                sym = found;
+            }
+            if (!sym) break;
+        }
+    }
+    std::vector<int32_t> sym_leaves, in_ptr, in_pptr, in_pbox;
+    std::vector<int64_t> sym_off, in_slot;
+    int64_t nslots = 0;
+    if (sym) {
+        sym_off.assign(B.u_idx.size(), -1);
+        std::vector<std::vector<int64_t>> rin((size_t)nb);
+        std::vector<std::vector<int32_t>> rbox((size_t)nb);
+        std::vector<int32_t> asc(B.leaves);
+        std::sort(asc.begin(), asc.end());
+        std::vector<int64_t> cost((size_t)nb, 0);
+        for (int32_t b : asc) {
+            const int64_t nt_b = B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b];
+            if (nt_b == 0) continue;
+            const int64_t ng = (nt_b + 31) / 32;
+            int64_t work = 0;
+            for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
+                const int32_t a = B.u_idx[(size_t)e2];
+                const int64_t na = B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
+                if (a < b || na == 0) continue;
+                work += na;
+                if (a == b) continue;
+                sym_off[(size_t)e2] = nslots;
+                for (int64_t gi = 0; gi < ng; ++gi) rin[(size_t)a].push_back(nslots + gi * na);
+                rbox[(size_t)a].push_back(b);
+                nslots += ng * na;
+            }
+            cost[(size_t)b] = nt_b * work;
+        }
+        sym_leaves = B.leaves;
+        std::stable_sort(sym_leaves.begin(), sym_leaves.end(),
+                         [&](int32_t a, int32_t b2) { return cost[(size_t)a] > cost[(size_t)b2]; });
+        in_ptr.assign((size_t)nb + 1, 0);
+        in_pptr.assign((size_t)nb + 1, 0);
+        for (int32_t a = 0; a < nb; ++a) {
+            in_ptr[(size_t)a + 1] = in_ptr[(size_t)a] + (int32_t)rin[(size_t)a].size();
+            in_pptr[(size_t)a + 1] = in_pptr[(size_t)a] + (int32_t)rbox[(size_t)a].size();
+            in_slot.insert(in_slot.end(), rin[(size_t)a].begin(), rin[(size_t)a].end());
+            in_pbox.insert(in_pbox.end(), rbox[(size_t)a].begin(), rbox[(size_t)a].end());
+        }
+    }
+    int32_t *d_sym_leaves = nullptr, *d_in_ptr = nullptr, *d_in_pptr = nullptr, *d_in_pbox = nullptr;
+    int64_t *d_sym_off = nullptr, *d_in_slot = nullptr;
+    if (sym) {
+        up(&d_sym_leaves, sym_leaves);
+        up(&d_sym_off, sym_off);
+        up(&d_in_ptr, in_ptr);
+        up(&d_in_slot, in_slot);
+        up(&d_in_pptr, in_pptr);
+        up(&d_in_pbox, in_pbox);
+    }
     up(&d_up, B.u_ptr);
     up(&d_ui, B.u_idx);
     up(&d_vp, B.v_ptr);
@@ -947,6 +1013,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.work, 4);
+    if (e == cudaSuccess && sym) e = p->alloc(&p->ws.slots, (size_t)std::max<int64_t>(nslots, 1) * p->nd_cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
     p->ws.nd_cap = p->nd_cap;
@@ -977,6 +1044,14 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     dt.x_ptr = d_xp;
     dt.x_idx = d_xi;
     dt.level_start = B.level_start;
+    dt.sym = sym;
+    dt.sym_leaves = d_sym_leaves;
+    dt.sym_off = d_sym_off;
+    dt.sym_in_ptr = d_in_ptr;
+    dt.sym_in_slot = d_in_slot;
+    dt.sym_in_pptr = d_in_pptr;
+    dt.sym_in_pbox = d_in_pbox;
+    dt.sym_slots = nslots;
     DevTables& tb = p->tab;
     tb.H = d_tab + off[0];
     tb.Bm = d_tab + off[1];
@@ -1254,8 +1329,8 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
     p->last_launches = 0;
     for (int d0 = 0; d0 < ndens;) {
         const int nd = chunk_for(ndens - d0, p->nd_cap);
-        // charges, P2M, M2M per level, M2L, L2L per level, leaf, output
-        p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1);
+        // charges, P2M, M2M per level, M2L, L2L per level, leaf (+ slot reduction), output
+        p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1) + (p->dt.sym ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
         if (p->ups)
@@ -1461,6 +1536,7 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->root[2] = p->stat_root[2];
     o->n_f = p->n_f;
     o->n_cells = p->ups ? p->dups.n_cells : 0;
+    o->sym_slots = p->dt.sym ? p->dt.sym_slots : 0;
     return VP_OK;
 }
 

@@ -914,11 +914,92 @@ __device__ __forceinline__ void p2p_tile(const float4 rt, const float4* __restri
     }
 }
 
-template <int P, int ND>
+// Symmetric pass over one chunk of at most 32 sources of a leaf A for the 32
+// targets of one warp (targets are the charge points of the warp's own leaf b,
+// A != b, so no pair coincides). At step t lane l takes source (l + t) mod 32:
+// it adds q_j log r^2 to its own target and q_i log r^2 (q_i the charge at its
+// target) to a float-float accumulator for that source, and the accumulators
+// move one lane down after each step; after 32 steps lane l holds the sum over
+// the warp's targets for source l. rh, rl must be zero on entry.
+template <int ND, bool EXACT>
+__device__ __forceinline__ void p2p_chunk_sym(const float4 rt, const float2* qi, bool valid_i,
+                                              const float4* __restrict__ s_rho,
+                                              const float2 (*__restrict__ s_q)[ND], int n, int lane,
+                                              const float4* __restrict__ s_tab, float* ah, float* al, float* rh,
+                                              float* rl)
+{
+#pragma unroll 2
+    for (int t = 0; t < 32; ++t) {
+        const int j = (lane + t) & 31;
+        if (valid_i && j < n) {
+            const float4 sr = s_rho[j];
+            float dxs, dxe, dys, dye;
+            if (EXACT) {
+                dxs = __fsub_rn(rt.x, sr.x);
+                dxe = __fsub_rn(rt.y, sr.y);
+                dys = __fsub_rn(rt.z, sr.z);
+                dye = __fsub_rn(rt.w, sr.w);
+            } else {
+                ff::two_sum(rt.x, -sr.x, dxs, dxe);
+                dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
+                ff::two_sum(rt.z, -sr.z, dys, dye);
+                dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
+            }
+            const float px = __fmul_rn(dxs, dxs);
+            float pxe = fmaf(dxs, dxs, -px);
+            pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
+            pxe = fmaf(dxe, dxe, pxe);
+            const float py = __fmul_rn(dys, dys);
+            float pye = fmaf(dys, dys, -py);
+            pye = fmaf(__fadd_rn(dys, dys), dye, pye);
+            pye = fmaf(dye, dye, pye);
+            const float rs = __fadd_rn(px, py);
+            float re = __fsub_rn(fminf(px, py), __fsub_rn(rs, fmaxf(px, py)));
+            re = __fadd_rn(re, __fadd_rn(pxe, pye));
+            float S, lo;
+            if (rs >= 0x1p-15f && rs < 0x1p16f) {
+                ff::log_pair_fast(rs, re, s_tab, S, lo);
+            } else if (rs == 0.0f && re == 0.0f) {
+                S = lo = 0.0f;  // not reached for distinct leaves
+            } else {
+                const double ld = log((double)rs + (double)re);
+                S = __double2float_rn(ld);
+                lo = __double2float_rn(ld - (double)S);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const float2 qq = s_q[j][d];
+                const float p = __fmul_rn(qq.x, S);
+                float pe = fmaf(qq.x, S, -p);
+                pe = fmaf(qq.x, lo, pe);
+                pe = fmaf(qq.y, S, pe);
+                float sh, se;
+                ff::two_sum(ah[d], p, sh, se);
+                ah[d] = sh;
+                al[d] = __fadd_rn(al[d], __fadd_rn(se, pe));
+                const float r = __fmul_rn(qi[d].x, S);
+                float re2 = fmaf(qi[d].x, S, -r);
+                re2 = fmaf(qi[d].x, lo, re2);
+                re2 = fmaf(qi[d].y, S, re2);
+                ff::two_sum(rh[d], r, sh, se);
+                rh[d] = sh;
+                rl[d] = __fadd_rn(rl[d], __fadd_rn(se, re2));
+            }
+        }
+        const int from = (lane + 1) & 31;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            rh[d] = __shfl_sync(0xffffffffu, rh[d], from);
+            rl[d] = __shfl_sync(0xffffffffu, rl[d], from);
+        }
+    }
+}
+
+template <int P, int ND, bool SYM>
 __global__ void __launch_bounds__(kLeafThreads)
     k_leaf_ff(DevTree t, PassGeom g, const float2* __restrict__ qf, const float4* __restrict__ Mf,
               const float4* __restrict__ Lf, const float4* __restrict__ logtab, double* __restrict__ psi,
-              int* __restrict__ work)
+              int* __restrict__ work, float2* __restrict__ slots)
 {
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1][ND];
@@ -936,7 +1017,7 @@ __global__ void __launch_bounds__(kLeafThreads)
         __syncthreads();
         const int li = s_next;
         if (li >= t.nleaf) break;
-        const int b = t.leaves[li];
+        const int b = SYM ? t.sym_leaves[li] : t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
         const double log_side = t.log_radius[b] + 0.693147180559945309417232121458176568;
@@ -992,7 +1073,16 @@ __global__ void __launch_bounds__(kLeafThreads)
 
             // P2P over U (float-float). Coordinates in units of leaf b's side, so
             // sum q log r = 1/2 sum q log r'^2 + log(side_b) (sum_U q - coincident q);
-            // sum_U q is read from the leaves' monopoles M_0.
+            // sum_U q is read from the leaves' monopoles M_0. With SYM, leaves A < b
+            // are skipped (A's block sends their part through the slots) and leaves
+            // A > b are summed in both directions.
+            const int warp = tid >> 5, lane = tid & 31;
+            const int grp = (tb - e0) / 32 + warp;  // this warp's group of 32 targets of b
+            const bool grp_live = tb + 32 * warp < e1;
+            float2 qi[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                qi[d] = (SYM && valid) ? qf[(int64_t)ti * ND + d] : make_float2(0.f, 0.f);
             float ah[ND], al[ND];
             ff::F qu[ND], qco[ND];
 #pragma unroll
@@ -1010,6 +1100,9 @@ __global__ void __launch_bounds__(kLeafThreads)
                     const float4 m0 = Mf[(int64_t)A * P1 * ND + d];
                     qu[d] = ff::add(qu[d], ff::F{m0.x, m0.y});
                 }
+                if (SYM && A < b) continue;
+                const bool rev = SYM && A > b;
+                const int64_t sbase = rev ? t.sym_off[e] + (int64_t)grp * (a1 - a0) : 0;
                 // same level or one level apart: hi parts differ exactly (both on
                 // the 2^-22 grid after the exact shift/scale), so dx = (th - sh) + (tl - sl)
                 const bool exact_hi = uo.z >= 0.5f && uo.z <= 2.0f;
@@ -1032,7 +1125,27 @@ __global__ void __launch_bounds__(kLeafThreads)
                         for (int d = 0; d < ND; ++d) s_q[tid][d] = qf[(int64_t)j * ND + d];
                     }
                     __syncthreads();
-                    if (valid) {
+                    if (rev) {
+                        if (grp_live) {  // warp-uniform
+                            for (int c = 0; c < n; c += 32) {
+                                const int nc = min(32, n - c);
+                                float rh[ND], rl[ND];
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) rh[d] = rl[d] = 0.f;
+                                if (exact_hi)
+                                    p2p_chunk_sym<ND, true>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab, ah,
+                                                            al, rh, rl);
+                                else
+                                    p2p_chunk_sym<ND, false>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab, ah,
+                                                             al, rh, rl);
+                                if (lane < nc) {
+                                    const int64_t o = (sbase + (sb - a0) + c + lane) * ND;
+#pragma unroll
+                                    for (int d = 0; d < ND; ++d) slots[o + d] = make_float2(rh[d], rl[d]);
+                                }
+                            }
+                        }
+                    } else if (valid) {
                         if (exact_hi)
                             p2p_tile<ND, true>(rt, s_rho, s_q, n, s_tab, ah, al, qco);
                         else
@@ -1151,6 +1264,52 @@ __global__ void k_grad_out(int32_t n_tgt, int accumulate, const int32_t* __restr
     }
 }
 
+// Adds the slots of the symmetric near field to the receiving leaves'
+// potentials, one warp per leaf, slots in a fixed order (deterministic). The
+// sender b summed q_i log r'^2 in b's units: the physical sum is half of it plus
+// log(side_b) sum_b q, of which log(side_A) sum_b q is already in A's own
+// near-field term; the rest is (log R_b - log R_A) M_0(b).
+template <int P, int ND>
+__global__ void k_sym_reduce(DevTree t, PassGeom g, const float2* __restrict__ slots, const float4* __restrict__ Mf,
+                             double* __restrict__ psi)
+{
+    constexpr int P1 = P + 1;
+    const int lane = threadIdx.x & 31;
+    for (int li = global_warp(); li < t.nleaf; li += num_warps()) {
+        const int A = t.leaves[li];
+        const int s0 = t.sym_in_ptr[A], s1 = t.sym_in_ptr[A + 1];
+        if (s0 == s1) continue;
+        const int e0 = g.erng[2 * A], e1 = g.erng[2 * A + 1];
+        double cst[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) cst[d] = 0.0;
+        for (int k = t.sym_in_pptr[A]; k < t.sym_in_pptr[A + 1]; ++k) {
+            const int b = t.sym_in_pbox[k];
+            const double dl = t.log_radius[b] - t.log_radius[A];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const float4 m0 = Mf[(int64_t)b * P1 * ND + d];
+                cst[d] = fma(dl, (double)m0.x + (double)m0.y, cst[d]);
+            }
+        }
+        for (int j = lane; j < e1 - e0; j += 32) {
+            double acc[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+            for (int k = s0; k < s1; ++k) {
+                const int64_t o = (t.sym_in_slot[k] + j) * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const float2 v = slots[o + d];
+                    acc[d] += (double)v.x + (double)v.y;
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) psi[(int64_t)(e0 + j) * ND + d] += fma(0.5, acc[d], cst[d]);
+        }
+    }
+}
+
 template <int P, int ND>
 cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool gradient,
                      bool fp64, PhaseTimer* tm, cudaStream_t s)
@@ -1194,20 +1353,29 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
     else if (fp64)
         k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
     else {
-        static int resident = 0;  // blocks of this instantiation that fit on one SM
-        if (resident == 0) {
+        static int resident[2] = {0, 0};  // blocks of each instantiation that fit on one SM
+        const int si = t.sym ? 1 : 0;
+        if (resident[si] == 0) {
             int nb = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND>, kLeafThreads, 0) != cudaSuccess ||
-                nb < 1)
-                nb = 1;
-            resident = nb;
+            const cudaError_t oe =
+                t.sym ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND, true>, kLeafThreads, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND, false>, kLeafThreads, 0);
+            if (oe != cudaSuccess || nb < 1) nb = 1;
+            resident[si] = nb;
         }
         int sms = 152;
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int pblocks = std::max(1, std::min(t.nleaf, sms * resident));
+        const int pblocks = std::max(1, std::min(t.nleaf, sms * resident[si]));
         cudaMemsetAsync(ws.work, 0, sizeof(int), s);
-        k_leaf_ff<P, ND><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi, ws.work);
+        if (t.sym) {
+            k_leaf_ff<P, ND, true><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi,
+                                                                   ws.work, ws.slots);
+            k_sym_reduce<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.slots, ws.Mf, ws.psi);
+        } else {
+            k_leaf_ff<P, ND, false><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi,
+                                                                    ws.work, nullptr);
+        }
     }
     if (tm) tm->end(id);
     return cudaGetLastError();

@@ -40,6 +40,19 @@ struct DevTree {
     const int32_t *x_ptr = nullptr, *x_idx = nullptr;
     const float4* x_off = nullptr;      // per X entry (b, C): the same offsets as u_off
     std::vector<int32_t> level_start;   // host copy, [nlevels + 1]
+    // Symmetric near field (charge points identical to evaluation points, same
+    // tree order): each pair of distinct adjacent leaves (b, A), A > b, is summed
+    // once by the block of b, which also produces q_b-weighted sums for A's
+    // points in "slots" (one run of |A| float-float values per group of 32 of
+    // b's points), added to A's potentials afterwards in a fixed order.
+    bool sym = false;
+    const int32_t* sym_leaves = nullptr;  // [nleaf] leaf order for the symmetric kernel (costliest first)
+    const int64_t* sym_off = nullptr;     // per U entry (b, A): first slot when A > b, else -1
+    const int32_t* sym_in_ptr = nullptr;  // per box: range of sym_in_slot (groups received)
+    const int64_t* sym_in_slot = nullptr; // slot bases received by a leaf
+    const int32_t* sym_in_pptr = nullptr; // per box: range of sym_in_pbox
+    const int32_t* sym_in_pbox = nullptr; // leaves b that sent slots to a leaf
+    int64_t sym_slots = 0;
 };
 
 // Translation-operator tables for one expansion order P (P1 = P + 1 entries).
@@ -115,6 +128,7 @@ struct Workspace {
     double* psi = nullptr;    // [max(n_src, n_tgt)][2][ND] potential (or gradient) in tree order
     float2* xf = nullptr;     // [ND][max(n_src, n_tgt)] correction input (f or g) as hi/lo floats
     int* work = nullptr;      // work-queue counter of the persistent near-field kernel
+    float2* slots = nullptr;  // [sym_slots][ND] symmetric near-field partial sums
     int32_t nd_cap = 0;
 };
 

@@ -336,3 +336,30 @@ def test_box_grid_with_area_to_line_corrections():
     print(f"16x16 grid, f = 1: max |V - exact| = {err:.3e}")
     assert err < 1e-12
     plan.close()
+
+
+@pytest.mark.parametrize("which", ["boxgrid", "disk"])
+def test_symmetric_near_field_matches_fp64(which):
+    # targets = nodes: the near field is summed once per pair of adjacent leaves
+    # (partial sums handed between leaves); the all-FP64 kernels sum every
+    # directed pair. Forward (three densities: chunks of 2 and 1) and adjoint.
+    if which == "boxgrid":
+        prob = inputs.box_grid_problem(nbox=8, order=8, ndens=3)
+    else:
+        prob = inputs.disk_problem(base_level=4, fine_level=6, ndens=3)
+    f = torch.as_tensor(prob.f, device="cuda")
+    g = torch.as_tensor(np.random.default_rng(6).standard_normal((3, prob.n_tgt)), device="cuda")
+    res = {}
+    for flags in (0, vp.VP_FLAG_FP64):
+        plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=32, max_dens=2, flags=flags,
+                              root=prob.root)
+        info = plan.info()
+        assert (info.sym_slots > 0) == (flags == 0)
+        res[flags] = (plan.eval(f).cpu().numpy(), plan.adjoint(g)[0].cpu().numpy())
+        plan.close()
+    norm = inputs.normaliser(prob)[:, None]
+    err = float(np.max(np.abs(res[0][0] - res[vp.VP_FLAG_FP64][0]) / norm))
+    scale = np.abs(g.cpu().numpy()).sum(axis=1)[:, None] * prob.w.max()
+    err_a = float(np.max(np.abs(res[0][1] - res[vp.VP_FLAG_FP64][1]) / scale))
+    print(f"{which}: symmetric float-float vs FP64 forward {err:.2e} adjoint {err_a:.2e}")
+    assert err <= 1e-12 and err_a <= 1e-12
