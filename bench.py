@@ -36,11 +36,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 2 FP64 FMA/clk/SM (measured),
 FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12     # FP32/INT32 lane-operations per second (T ops/s)
 P2P_FLOP_PER_PAIR = 27.0  # 7 flops + 20 flop-equivalents for one FP64 log (stated convention)
 P2P_FF_OPS_PER_PAIR = 77.0  # FP32 operations of the float-float pair evaluation (k_leaf_ff, exact-hi pairs)
+P2P_FF_OPS_REVERSE = 14.0   # extra FP32 operations when one evaluation serves both directions (symmetric near field)
 # DRAM bytes (read + write) per work unit from one ncu capture of the current
 # kernels on the medium disk case (profiles/*_disk_medium.md), scaled to a
 # launch by the units it processes; None once a kernel changes until re-profiled.
 PROFILED_TRAFFIC = {
-    "leaf": (14.818e6 / 159450440, "pairs", "profiles/k_leaf_ff_disk_medium.md"),
+    "leaf": None,  # k_leaf_ff changed since its capture (symmetric near field): re-profile before filling
     "m2l": (3.034e6 / 145118, "V-list pairs", "profiles/k_m2l_ff_disk_medium.md"),
     "out": ((1298.684e6 + 5.309e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
 }
@@ -58,12 +59,16 @@ def roofline_models(info, prob, ndens=1):
     """Per-phase roofline models: algorithmic work per launch of each phase."""
     P = info.p_fmm
     hbm, hbm_src = hbm_peak()
+    evals = int(info.p2p_evals)
+    two_way = int(info.p2p_pairs) - evals  # evaluations that serve both directions
     return {
         "leaf": {"bound": "alu", "kernel": "k_leaf_ff (float-float P2P + FP64 L2P/M2P)",
-                 "work": info.p2p_pairs * P2P_FF_OPS_PER_PAIR * ndens, "unit": "T FP32-ops/s",
+                 "work": (evals * P2P_FF_OPS_PER_PAIR + two_way * P2P_FF_OPS_REVERSE) * ndens, "unit": "T FP32-ops/s",
                  "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",
-                 "fp64_equiv_flop": info.p2p_pairs * P2P_FLOP_PER_PAIR * ndens, "units": info.p2p_pairs,
-                 "per_unit": f"{P2P_FF_OPS_PER_PAIR:.0f} FP32 ops per source-target pair"},
+                 "fp64_equiv_flop": (evals * P2P_FLOP_PER_PAIR + two_way * 7.0) * ndens, "units": info.p2p_pairs,
+                 "per_unit": f"{P2P_FF_OPS_PER_PAIR:.0f} FP32 ops per evaluated source-target distance, "
+                             f"+{P2P_FF_OPS_REVERSE:.0f} when it serves both directions "
+                             f"({evals} evaluations for {info.p2p_pairs} directed pairs)"},
         "m2l": {"bound": "alu", "kernel": "k_m2l_ff (float-float scaled-Hankel M2L)",
                 "work": info.n_v_pairs * (P + 1) * (24.0 * P + 100.0) * ndens, "unit": "T FP32-ops/s",
                 "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",

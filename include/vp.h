@@ -245,6 +245,9 @@ typedef struct {
     int64_t sym_slots;      /* > 0: the near field is summed once per pair of adjacent leaves
                                (evaluation points = quadrature nodes); the partial sums
                                handed between leaves                                        */
+    int64_t p2p_evals;      /* source-target distances the near field evaluates (one density):
+                               p2p_pairs, or with sym_slots > 0 the pairs inside leaves plus
+                               one per pair of points in distinct adjacent leaves            */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);

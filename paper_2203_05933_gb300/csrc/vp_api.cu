@@ -400,6 +400,7 @@ struct vp_plan_s {
     double* stage = nullptr;
     size_t stage_cap = 0;
     int64_t p2p_pairs = 0;
+    int64_t p2p_evals = 0;      // distances evaluated by the symmetric near field
     int64_t last_launches = 0;
     bool alive = true;
 
@@ -924,6 +925,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
                 nslots += ng * na;
             }
             cost[(size_t)b] = nt_b * work;
+            p->p2p_evals += nt_b * work;
         }
         sym_leaves = B.leaves;
         std::stable_sort(sym_leaves.begin(), sym_leaves.end(),
@@ -1537,6 +1539,7 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->n_f = p->n_f;
     o->n_cells = p->ups ? p->dups.n_cells : 0;
     o->sym_slots = p->dt.sym ? p->dt.sym_slots : 0;
+    o->p2p_evals = p->dt.sym ? p->p2p_evals : p->p2p_pairs;
     return VP_OK;
 }
 
