@@ -242,15 +242,23 @@ typedef struct {
     double root[3];         /* root square of the (first) problem                         */
     int64_t n_f;            /* length of a density: n_src, or the p-nodes of an upsampled plan */
     int64_t n_cells;        /* cells of an upsampled plan (0 otherwise)                    */
-    int64_t sym_slots;      /* > 0: the near field is summed once per pair of adjacent leaves
-                               (evaluation points = quadrature nodes); the partial sums
-                               handed between leaves                                        */
-    int64_t p2p_evals;      /* source-target distances the near field evaluates (one density):
-                               p2p_pairs, or with sym_slots > 0 the pairs inside leaves plus
-                               one per pair of points in distinct adjacent leaves            */
+    int64_t sym_slots;      /* > 0: passes of one or two densities sum the near field once per
+                               pair of adjacent leaves (evaluation points = quadrature nodes)
+                               and hand the partial sums between leaves through this many
+                               slots; more densities per pass sum every directed pair        */
+    int64_t p2p_evals;      /* source-target distances such a symmetric pass evaluates (one
+                               density): the pairs inside leaves plus one per pair of points
+                               in distinct adjacent leaves; p2p_pairs without symmetry       */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);
+/*
+ * vp_plan_check — synchronizes `stream` and reports whether a bounded
+ * device-side wait (the bulk-copy pipeline of the correction apply) gave up in
+ * an evaluation since the last check: VP_ERR_TIMEOUT (and the results of that
+ * evaluation are unspecified), else VP_OK. Clears the condition.
+ */
+vp_status vp_plan_check(vp_plan plan, void* stream);
 
 /*
  * Per-phase device times of the last vp_eval on this plan, in milliseconds,

@@ -270,6 +270,7 @@ struct HostGroups {
     std::vector<int32_t> g_r0;
     std::vector<int64_t> g_c0;
     std::vector<int32_t> cols;
+    std::vector<int64_t> rowptr;  // row starts in vf (rows padded to even lengths)
     std::vector<float> vf;
     int32_t max_m = 0;
 };
@@ -296,12 +297,22 @@ void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::
     }
     G.g_r0.push_back((int32_t)nrows);
     G.g_c0.push_back((int64_t)G.cols.size());
-    G.vf.resize(val.size() * 2);
-    for (size_t k = 0; k < val.size(); ++k) {
-        const float h = (float)val[k];
-        G.vf[2 * k] = h;
-        G.vf[2 * k + 1] = (float)(val[k] - (double)h);
+    // values as hi/lo floats, every row padded to an even length (zeros), so that
+    // each row starts on a 16-byte boundary and any run of rows can be moved by a
+    // bulk copy
+    G.rowptr.assign((size_t)nrows + 1, 0);
+    for (int64_t i = 0; i < nrows; ++i) {
+        const int64_t len = rowptr[(size_t)i + 1] - rowptr[(size_t)i];
+        G.rowptr[(size_t)i + 1] = G.rowptr[(size_t)i] + len + (len & 1);
     }
+    G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
+    for (int64_t i = 0; i < nrows; ++i)
+        for (int64_t k = rowptr[(size_t)i]; k < rowptr[(size_t)i + 1]; ++k) {
+            const size_t o = (size_t)(G.rowptr[(size_t)i] + (k - rowptr[(size_t)i]));
+            const float h = (float)val[(size_t)k];
+            G.vf[2 * o] = h;
+            G.vf[2 * o + 1] = (float)(val[(size_t)k] - (double)h);
+        }
 }
 
 bool finite_all(const std::vector<double>& a)
@@ -992,7 +1003,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             up(&d_r0, G.g_r0);
             up(&d_c0, G.g_c0);
             up(&d_cols, G.cols);
-            up(&d_rp, fwd ? B.hrow : hcptr);
+            up(&d_rp, G.rowptr);
             up(&d_vf, G.vf);
             A.nrows = (int32_t)nrows;
             A.ngroups = (int32_t)G.g_r0.size() - 1;
@@ -1015,6 +1026,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.work, 4);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.err, 0, sizeof(int), s);
     if (e == cudaSuccess && sym) e = p->alloc(&p->ws.slots, (size_t)std::max<int64_t>(nslots, 1) * p->nd_cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
@@ -1332,7 +1345,7 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
     for (int d0 = 0; d0 < ndens;) {
         const int nd = chunk_for(ndens - d0, p->nd_cap);
         // charges, P2M, M2M per level, M2L, L2L per level, leaf (+ slot reduction), output
-        p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1) + (p->dt.sym ? 1 : 0);
+        p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1) + (p->dt.sym && nd <= 2 ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
         if (p->ups)
@@ -1346,7 +1359,7 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         if (p->grouped) {
             VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, s));
             VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f,
-                                       out + (int64_t)d0 * ld_out, ld_out, s));
+                                       out + (int64_t)d0 * ld_out, ld_out, p->ws.err, s));
             p->last_launches += 1;
         } else {
             VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc,
@@ -1449,7 +1462,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                 if (p->grouped) {
                     VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                     VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc, ld_gf,
-                                               s));
+                                               p->ws.err, s));
                 } else if (p->cptr) {
                     VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_f, nullptr, nullptr, nullptr, p->cptr, p->crow,
                                                p->cval, gc, ld_g, gfc, ld_gf, s));
@@ -1457,7 +1470,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             } else if (p->grouped) {
                 VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                 VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
-                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
+                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, p->ws.err, s));
             } else {
                 VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr,
                                            p->crow, p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
@@ -1540,6 +1553,22 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->n_cells = p->ups ? p->dups.n_cells : 0;
     o->sym_slots = p->dt.sym ? p->dt.sym_slots : 0;
     o->p2p_evals = p->dt.sym ? p->p2p_evals : p->p2p_pairs;
+    return VP_OK;
+}
+
+vp_status vp_plan_check(vp_plan p, void* stream)
+{
+    vp_status st = check_plan(p);
+    if (st != VP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    VP_CUDA(cudaMemcpyAsync(&h, p->ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    VP_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        VP_CUDA(cudaMemsetAsync(p->ws.err, 0, sizeof(int), s));
+        VP_CUDA(cudaStreamSynchronize(s));
+        return fail(VP_ERR_TIMEOUT, "a bounded device wait gave up in an earlier evaluation");
+    }
     return VP_OK;
 }
 

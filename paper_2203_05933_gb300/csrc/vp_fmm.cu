@@ -1354,11 +1354,15 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
         k_leaf<P, ND, false><<<blocks, kLeafThreads, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi);
     else {
         static int resident[2] = {0, 0};  // blocks of each instantiation that fit on one SM
-        const int si = t.sym ? 1 : 0;
+        // the symmetric near field pays off while the shared log dominates the
+        // per-pair work (one or two densities); beyond that the second
+        // accumulation costs about as much as it saves
+        const bool sym = t.sym && ND <= 2;
+        const int si = sym ? 1 : 0;
         if (resident[si] == 0) {
             int nb = 0;
             const cudaError_t oe =
-                t.sym ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND, true>, kLeafThreads, 0)
+                sym ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND, true>, kLeafThreads, 0)
                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf_ff<P, ND, false>, kLeafThreads, 0);
             if (oe != cudaSuccess || nb < 1) nb = 1;
             resident[si] = nb;
@@ -1368,7 +1372,7 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int pblocks = std::max(1, std::min(t.nleaf, sms * resident[si]));
         cudaMemsetAsync(ws.work, 0, sizeof(int), s);
-        if (t.sym) {
+        if (sym) {
             k_leaf_ff<P, ND, true><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi,
                                                                    ws.work, ws.slots);
             k_sym_reduce<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.slots, ws.Mf, ws.psi);
