@@ -95,6 +95,7 @@ def parse():
     ap.add_argument("--many", type=int, default=256, help="problems of the many-problem leg (0: skip)")
     ap.add_argument("--star", type=int, default=1, help="run the 4 M star-with-holes leg (0: skip)")
     ap.add_argument("--upsampled", type=int, default=1, help="run the oversampled (q = 2p) disk leg (0: skip)")
+    ap.add_argument("--tricorr", type=int, default=1, help="run the triangle self-correction leg (0: skip)")
     ap.add_argument("--interp", type=int, default=1 << 20,
                     help="random points of the interpolation leg (0: skip)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -444,6 +445,38 @@ def main():
         ip.close()
         del io
 
+    # triangle self-correction leg: the self blocks of every band triangle of the
+    # disk generated on the GPU from the fixed reference-space rules
+    tricorr_leg = None
+    if args.tricorr > 0 and rank == 0:
+        from paper_2203_05933_gb300 import inputs
+        from paper_2203_05933_gb300.setup import meshes as smeshes
+        from paper_2203_05933_gb300.setup import tricorr as stricorr
+        base, fine = {"full": (7, 9), "medium": (6, 8), "small": (5, 7)}[args.size]
+        t0 = time.perf_counter()
+        rules = stricorr.self_rules(8)
+        mesh = smeshes.disk_mesh(base_level=base, fine_level=fine, centres=inputs.disk_centres(inputs.SEED_BASE + 2),
+                                 refine_radius={base + 1: 0.11, base + 2: 0.04})
+        geom = np.array([stricorr.geom_params(g) for g in mesh.geom if g[0] == "tri"])
+        setup_s = time.perf_counter() - t0
+        tc = vp.TriCorr(rules)
+        gdev = torch.as_tensor(geom, device=dev)
+        tout = torch.empty((geom.shape[0], 36, 36), dtype=torch.float64, device=dev)
+        tc.eval(gdev, out=tout)
+        torch.cuda.synchronize()
+        tt = timed(lambda: tc.eval(gdev, out=tout), 3)
+        t0 = time.perf_counter()
+        stricorr.self_corrections_reference([g for g in mesh.geom if g[0] == "tri"][0], rules)
+        host_cell_s = time.perf_counter() - t0
+        n_rule = int(rules["N"])
+        flops = geom.shape[0] * 36 * (36 * n_rule * 2.0 + 36 * 36 * 2.0)
+        ms = float(np.mean(tt)) * 1e3
+        tricorr_leg = {"cells": int(geom.shape[0]), "targets_per_cell": 36, "rule_nodes_per_target": n_rule,
+                       "ms": ms, "value": geom.shape[0] / (ms * 1e-3), "unit": "cells/s",
+                       "contraction_tflops": flops / (ms * 1e-3) / 1e12, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+                       "host_numpy_s_per_cell": host_cell_s, "setup_s": setup_s}
+        tc.close()
+
     # star leg: star with 12 holes, about 4.2 M sources and 2^22 targets (half nodes,
     # half random interior points), own-cell correction rows; same P and leaf
     star = None
@@ -533,6 +566,7 @@ def main():
         "star": star,
         "upsampled": upsampled,
         "interp": interp_leg,
+        "tricorr": tricorr_leg,
         "clocks": clk,
         "gpu_launches": int(launches_per_eval * args.steps),
         "wall_s": wall,

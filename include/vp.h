@@ -361,6 +361,38 @@ vp_status vp_interp_eval(vp_interp ip, int32_t ndens, const double* v, int64_t l
 vp_status vp_interp_destroy(vp_interp ip);
 
 /*
+ * Singular (self) corrections of mapped triangles, generated on the GPU
+ * (Sec. 3.3; efficient pre-computation of Sec. 3.4, Eq. singcorr_inner_prod).
+ * For the target at reference node a of a cell with map R and Jacobian J:
+ *   Vhat_b = sum_i g_i B[a][b][i],
+ *   g_i = J(chi_i) / (2 pi)                                   if tau[a][i] < 0,
+ *   g_i = -(log|R(chi_i) - R(zeta_a)| - log tau[a][i]) J(chi_i) / (2 pi)   otherwise,
+ *   corr[c][a][j] = sum_b Vhat_b coef[b][j] - w_j J(zeta_j) G(R(zeta_j), R(zeta_a))
+ *                   (the smooth term only for j != a),
+ * the "accurate minus smooth" self block of cell c (Sec. 4). chi, tau and B are
+ * the same for every cell (the kind of node, tau < 0, marks the nodes whose
+ * -log t factor is folded into B; |tau| is the node's ray parameter t). The
+ * set-up (host) builds them once; the GPU evaluates the mapped Green function
+ * and Jacobian and the contraction for all cells.
+ * vp_tricorr_create: host tables node_ref [n_nodes][2] (reference nodes
+ * zeta_j), node_w [n_nodes] (reference weights w_j), coef [n_basis][n_nodes]
+ * (values-to-coefficients map), chi [n_nodes][n_rule][2], tau
+ * [n_nodes][n_rule] (0 < |tau| <= 1), B [n_nodes][n_basis][n_rule];
+ * n_basis <= 36. Synchronizes `stream`.
+ * vp_tricorr_eval: geom [n_cells][12] device: v0, v1, v2 (x, y), kind (0
+ * straight, 1 circle arc cx, cy, r, th0, th1; 2 polar arc r = 1 + a cos(k th)
+ * with a, k, th0, th1), the curved edge running from v0 (th0) to v1 (th1);
+ * out [n_cells][n_nodes][n_nodes] device. Enqueues on `stream` only.
+ */
+typedef struct vp_tricorr_s* vp_tricorr;
+vp_status vp_tricorr_create(vp_tricorr* out, int32_t n_nodes, int32_t n_basis, int32_t n_rule,
+                            const double* node_ref, const double* node_w, const double* coef,
+                            const double* chi, const double* tau, const double* B, void* stream);
+vp_status vp_tricorr_eval(vp_tricorr tc, int64_t n_cells, const double* geom, double* out,
+                          void* stream);
+vp_status vp_tricorr_destroy(vp_tricorr tc);
+
+/*
  * vp_eval_direct_static — evaluation that allocates nothing.
  *
  * For callers that cannot allocate device memory when they need the volume

@@ -253,6 +253,7 @@ def star_curve(th0, th1, a: float = 0.3, k: int = 5):
         c, sn = np.cos(th), np.sin(th)
         return r * c, r * sn, dth * (dr * c - r * sn), dth * (dr * sn + r * c)
 
+    curve.spec = (2.0, a, float(k), th0, th1)
     return curve
 
 

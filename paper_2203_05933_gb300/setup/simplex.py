@@ -148,6 +148,7 @@ def circle_arc(cx, cy, r, th0, th1):
         th = th0 + s * dth
         return (cx + r * np.cos(th), cy + r * np.sin(th), -r * dth * np.sin(th), r * dth * np.cos(th))
 
+    curve.spec = (1.0, cx, cy, r, th0, th1)
     return curve
 
 

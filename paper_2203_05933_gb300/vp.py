@@ -34,6 +34,7 @@ EXPORTED = [
     "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host",
     "vp_plan_info", "vp_plan_check", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
+    "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
 ]
 
 
@@ -120,6 +121,9 @@ def _load():
         "vp_interp_create": [ctypes.POINTER(P), I32, ctypes.POINTER(vp_interp_type), I64, P, P, I64, P, P, P],
         "vp_interp_eval": [P, I32, P, I64, P, I64, P],
         "vp_interp_destroy": [P],
+        "vp_tricorr_create": [ctypes.POINTER(P), I32, I32, I32, P, P, P, P, P, P, P],
+        "vp_tricorr_eval": [P, I64, P, P, P],
+        "vp_tricorr_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -547,6 +551,45 @@ class Interp:
     def close(self):
         if self.handle:
             _check(_load().vp_interp_destroy(self.handle), "vp_interp_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TriCorr:
+    """Self-correction blocks of mapped triangles on the GPU (vp_tricorr_*).
+    rules: dict of setup.tricorr.self_rules (xi, eta, tw, C, chi, tau, B)."""
+
+    def __init__(self, rules, stream=None):
+        lib = _load()
+        ref = np.ascontiguousarray(np.stack([rules["xi"], rules["eta"]], axis=1), np.float64)
+        arrs = [ref, np.ascontiguousarray(rules["tw"], np.float64), np.ascontiguousarray(rules["C"], np.float64),
+                np.ascontiguousarray(rules["chi"], np.float64), np.ascontiguousarray(rules["tau"], np.float64),
+                np.ascontiguousarray(rules["B"], np.float64)]
+        n_nodes, n_basis, n_rule = ref.shape[0], arrs[2].shape[0], arrs[3].shape[1]
+        h = ctypes.c_void_p()
+        st = lib.vp_tricorr_create(ctypes.byref(h), n_nodes, n_basis, n_rule,
+                                   *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs], _stream(stream))
+        _check(st, "vp_tricorr_create")
+        self.handle = h
+        self.n_nodes = n_nodes
+
+    def eval(self, geom, out=None, stream=None):
+        """geom: [n_cells, 12] (numpy or CUDA tensor); returns [n_cells, n_nodes, n_nodes]."""
+        import torch
+        g = _dev_f64(geom).reshape(-1, 12)
+        if out is None:
+            out = torch.empty((g.shape[0], self.n_nodes, self.n_nodes), dtype=torch.float64, device=g.device)
+        _check(_load().vp_tricorr_eval(self.handle, g.shape[0], _ptr(g), _ptr(out), _stream(stream)), "vp_tricorr_eval")
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(_load().vp_tricorr_destroy(self.handle), "vp_tricorr_destroy")
             self.handle = None
 
     def __del__(self):
