@@ -40,44 +40,56 @@ __global__ void __launch_bounds__(kGroupThreads)
                   const double* __restrict__ psi, const float2* __restrict__ xf, int64_t ld_xf,
                   double* __restrict__ out, int64_t ld_out)
 {
-    extern __shared__ float2 F[];  // [ND][smem_m]: lanes read consecutive columns of one density
+    // [ND][smem_m] (smem_m even): lanes read consecutive pairs of columns of one density
+    extern __shared__ __align__(16) float2 F[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int gi = blockIdx.x; gi < A.ngroups; gi += gridDim.x) {
         const int r0 = A.g_r0[gi], r1 = A.g_r0[gi + 1];
         const int64_t c0 = A.g_c0[gi];
         const int m = (int)(A.g_c0[gi + 1] - c0);
-        const bool staged = m <= smem_m;
+        const bool staged = m + (m & 1) <= smem_m;
         __syncthreads();
         if (staged) {
             for (int i = threadIdx.x; i < m * ND; i += blockDim.x) {
                 const int k = i % m, d = i / m;
                 F[d * smem_m + k] = xf[d * ld_xf + A.cols[c0 + k]];
             }
+            if ((m & 1) && threadIdx.x < ND) F[threadIdx.x * smem_m + m] = make_float2(0.f, 0.f);
         }
         __syncthreads();
+        const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
         for (int r = r0 + warp; r < r1; r += nw) {
-            const int64_t v0 = A.rowptr[r];
-            // four independent accumulators per density keep four loads in flight per lane
+            const float4* vrow = reinterpret_cast<const float4*>(A.vf + A.rowptr[r]);  // rows start on 16 bytes
+            // four independent accumulators per density keep four 16-byte loads in flight per lane
             ff::F acc[4][ND];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) acc[u][d] = ff::F{0.f, 0.f};
-            for (int k0 = lane; k0 < m; k0 += 128) {
-                float2 v[4];
+            for (int q0 = lane; q0 < np; q0 += 128) {
+                float4 v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int k = k0 + 32 * u;
-                    v[u] = k < m ? A.vf[v0 + k] : make_float2(0.f, 0.f);
+                    const int q = q0 + 32 * u;
+                    v[u] = q < np ? vrow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int k = k0 + 32 * u;
-                    if (k < m) {
+                    const int q = q0 + 32 * u;
+                    if (q < np) {
+                        const int k = 2 * q;
 #pragma unroll
                         for (int d = 0; d < ND; ++d) {
-                            const float2 x = staged ? F[d * smem_m + k] : xf[d * ld_xf + A.cols[c0 + k]];
+                            float4 x;
+                            if (staged) {
+                                x = *reinterpret_cast<const float4*>(F + d * smem_m + k);
+                            } else {
+                                const float2 x0 = xf[d * ld_xf + A.cols[c0 + k]];
+                                const float2 x1 = k + 1 < m ? xf[d * ld_xf + A.cols[c0 + k + 1]] : make_float2(0.f, 0.f);
+                                x = make_float4(x0.x, x0.y, x1.x, x1.y);
+                            }
                             acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].x, v[u].y}, ff::F{x.x, x.y}));
+                            acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].z, v[u].w}, ff::F{x.z, x.w}));
                         }
                     }
                 }
@@ -289,8 +301,9 @@ template <int ND>
 cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
                               const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, int* err, cudaStream_t s)
 {
-    // bulk-copy path: every row fits in one stage and the value array starts on 16 bytes
-    if (err && A.ngroups > 0 && (int64_t)(A.max_m + 1) * 8 <= kTmaStageBytes && ((uintptr_t)A.vf % 16) == 0) {
+    // bulk-copy path (kept for matrices whose rows are long enough to fill its stages;
+    // with rows of a few hundred values the register-streaming kernel below is faster)
+    if (err && A.ngroups > 0 && A.max_m >= kTmaStageElems / 2 && (int64_t)(A.max_m + 1) * 8 <= kTmaStageBytes && ((uintptr_t)A.vf % 16) == 0) {
         const int smem_m = A.max_m < 1 ? 1 : A.max_m;
         const size_t bytes = (size_t)kTmaStages * kTmaStageBytes + (size_t)smem_m * ND * sizeof(float2);
         if (bytes <= 200 * 1024) {
