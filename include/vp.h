@@ -253,14 +253,6 @@ typedef struct {
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);
 /*
- * vp_plan_check — synchronizes `stream` and reports whether a bounded
- * device-side wait (the bulk-copy pipeline of the correction apply) gave up in
- * an evaluation since the last check: VP_ERR_TIMEOUT (and the results of that
- * evaluation are unspecified), else VP_OK. Clears the condition.
- */
-vp_status vp_plan_check(vp_plan plan, void* stream);
-
-/*
  * Per-phase device times of the last vp_eval on this plan, in milliseconds,
  * measured with CUDA events recorded on the evaluation stream (only with
  * VP_FLAG_TIMING). Synchronizes on the last recorded event. names/ms are host

@@ -298,8 +298,7 @@ void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::
     G.g_r0.push_back((int32_t)nrows);
     G.g_c0.push_back((int64_t)G.cols.size());
     // values as hi/lo floats, every row padded to an even length (zeros), so that
-    // each row starts on a 16-byte boundary and any run of rows can be moved by a
-    // bulk copy
+    // each row starts on a 16-byte boundary and is read as pairs of values
     G.rowptr.assign((size_t)nrows + 1, 0);
     for (int64_t i = 0; i < nrows; ++i) {
         const int64_t len = rowptr[(size_t)i + 1] - rowptr[(size_t)i];
@@ -1026,8 +1025,6 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.work, 4);
-    if (e == cudaSuccess) e = p->alloc(&p->ws.err, 1);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.err, 0, sizeof(int), s);
     if (e == cudaSuccess && sym) e = p->alloc(&p->ws.slots, (size_t)std::max<int64_t>(nslots, 1) * p->nd_cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
@@ -1359,7 +1356,7 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         if (p->grouped) {
             VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, s));
             VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f,
-                                       out + (int64_t)d0 * ld_out, ld_out, p->ws.err, s));
+                                       out + (int64_t)d0 * ld_out, ld_out, s));
             p->last_launches += 1;
         } else {
             VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc,
@@ -1462,7 +1459,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                 if (p->grouped) {
                     VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                     VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc, ld_gf,
-                                               p->ws.err, s));
+                                               s));
                 } else if (p->cptr) {
                     VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_f, nullptr, nullptr, nullptr, p->cptr, p->crow,
                                                p->cval, gc, ld_g, gfc, ld_gf, s));
@@ -1470,7 +1467,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             } else if (p->grouped) {
                 VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                 VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
-                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, p->ws.err, s));
+                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
             } else {
                 VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr,
                                            p->crow, p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
@@ -1553,22 +1550,6 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->n_cells = p->ups ? p->dups.n_cells : 0;
     o->sym_slots = p->dt.sym ? p->dt.sym_slots : 0;
     o->p2p_evals = p->dt.sym ? p->p2p_evals : p->p2p_pairs;
-    return VP_OK;
-}
-
-vp_status vp_plan_check(vp_plan p, void* stream)
-{
-    vp_status st = check_plan(p);
-    if (st != VP_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    int h = 0;
-    VP_CUDA(cudaMemcpyAsync(&h, p->ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    VP_CUDA(cudaStreamSynchronize(s));
-    if (h != 0) {
-        VP_CUDA(cudaMemsetAsync(p->ws.err, 0, sizeof(int), s));
-        VP_CUDA(cudaStreamSynchronize(s));
-        return fail(VP_ERR_TIMEOUT, "a bounded device wait gave up in an earlier evaluation");
-    }
     return VP_OK;
 }
 

@@ -1296,6 +1296,7 @@ __global__ void k_sym_reduce(DevTree t, PassGeom g, const float2* __restrict__ s
             double acc[ND];
 #pragma unroll
             for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+#pragma unroll 4
             for (int k = s0; k < s1; ++k) {
                 const int64_t o = (t.sym_in_slot[k] + j) * ND;
 #pragma unroll

@@ -129,7 +129,6 @@ struct Workspace {
     float2* xf = nullptr;     // [ND][max(n_src, n_tgt)] correction input (f or g) as hi/lo floats
     int* work = nullptr;      // work-queue counter of the persistent near-field kernel
     float2* slots = nullptr;  // [sym_slots][ND] symmetric near-field partial sums
-    int* err = nullptr;       // device word: 1 after a bounded device wait gave up
     int32_t nd_cap = 0;
 };
 
@@ -167,10 +166,9 @@ cudaError_t launch_grad_out(int nd, bool accumulate, int32_t n_tgt, const int32_
 // for every row r of A, w = w_sorted[inv[r]] or 1 when w_sorted is NULL; with psi NULL,
 // out[d][r] += (A x)[d][r] instead (launch_out_adjoint likewise).
 cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, float2* xf, cudaStream_t s);
-// err: device word set to 1 if a bounded wait of the bulk-copy path gives up.
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
-                               int* err, cudaStream_t s);
+                               cudaStream_t s);
 
 // Oversampling (vp_upsample.cu). Charges q[pos][d] = w_pos (O f)[d][j], pos = inv[j]
 // the tree position of q-node j, fused with the interpolation; and the transposed

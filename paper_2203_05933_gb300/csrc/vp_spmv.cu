@@ -10,9 +10,6 @@
 // TwoProd/TwoSum. HBM traffic is one read of the values plus the outputs.
 #include <cuda_runtime.h>
 
-#include <algorithm>
-#include <cstdint>
-
 #include "vp_ff.cuh"
 #include "vp_internal.h"
 
@@ -121,208 +118,10 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
 }
 
-// ---------------------------------------------------------------------------
-// The same product with the values streamed into shared memory by the Tensor
-// Memory Accelerator (cp.async.bulk, completion counted on an mbarrier), in
-// runs of whole rows of one group, kTmaStages runs in flight per block: the
-// copies of the next runs proceed while the warps reduce the current one from
-// shared memory. Rows are padded to even lengths, so every run starts on a
-// 16-byte boundary and has a multiple of 16 bytes. A wait that does not
-// complete within its bound sets *err and ends the block.
-constexpr int kTmaStages = 3;
-constexpr int kTmaStageBytes = 32 * 1024;
-constexpr int kTmaStageElems = kTmaStageBytes / 8;
-constexpr long long kTmaWaitBound = 1LL << 22;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// rows of group g that fit in one stage
-__device__ __forceinline__ int tma_rows(const DevGroupedCSR& A, int g, int r)
-{
-    const int m = (int)(A.g_c0[g + 1] - A.g_c0[g]);
-    const int mp = m + (m & 1);
-    const int rpc = mp > 0 ? max(1, kTmaStageElems / mp) : 1 << 30;
-    return min(rpc, A.g_r0[g + 1] - r);
-}
-
-template <int ND>
-__global__ void __launch_bounds__(kGroupThreads)
-    k_out_grouped_tma(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv,
-                      const double* __restrict__ w_sorted, const double* __restrict__ psi,
-                      const float2* __restrict__ xf, int64_t ld_xf, double* __restrict__ out, int64_t ld_out,
-                      int* __restrict__ err)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2* stage = (float2*)smem_raw;                                        // [kTmaStages][kTmaStageElems]
-    float2* F = (float2*)(smem_raw + (size_t)kTmaStages * kTmaStageBytes);   // [ND][smem_m]
-    __shared__ __align__(8) uint64_t full[kTmaStages];
-    __shared__ int s_fail;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int G = A.ngroups;
-    if (tid == 0) {
-        for (int s = 0; s < kTmaStages; ++s) mbar_init(&full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_fail = 0;
-    }
-    __syncthreads();
-    // producer cursor (thread 0): next run to load
-    int pg = blockIdx.x, pr = pg < G ? A.g_r0[pg] : 0;
-    auto produce = [&](int s) {
-        while (pg < G && pr >= A.g_r0[pg + 1]) {
-            pg += gridDim.x;
-            if (pg < G) pr = A.g_r0[pg];
-        }
-        if (pg >= G) return;
-        const int nr = tma_rows(A, pg, pr);
-        const int64_t v0 = A.rowptr[pr], v1 = A.rowptr[pr + nr];
-        const uint32_t bytes = (uint32_t)((v1 - v0) * 8);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&full[s], bytes);
-        if (bytes > 0) bulk_copy_g2s(stage + (size_t)s * kTmaStageElems, A.vf + v0, bytes, &full[s]);
-        pr += nr;
-    };
-    if (tid == 0)
-        for (int s = 0; s < kTmaStages; ++s) produce(s);
-    int cg = blockIdx.x, cr = cg < G ? A.g_r0[cg] : 0, last_g = -1;
-    for (int c = 0;; ++c) {
-        while (cg < G && cr >= A.g_r0[cg + 1]) {
-            cg += gridDim.x;
-            if (cg < G) cr = A.g_r0[cg];
-        }
-        if (cg >= G) break;
-        const int s = c % kTmaStages;
-        const uint32_t parity = (uint32_t)((c / kTmaStages) & 1);
-        const int m = (int)(A.g_c0[cg + 1] - A.g_c0[cg]);
-        const int mp = m + (m & 1);
-        const int nr = tma_rows(A, cg, cr);
-        if (cg != last_g) {  // block-uniform: gather x[:, cols] of the new group
-            const int64_t c0 = A.g_c0[cg];
-            for (int i = tid; i < m * ND; i += blockDim.x) {
-                const int k = i % m, d = i / m;
-                F[d * smem_m + k] = xf[d * ld_xf + A.cols[c0 + k]];
-            }
-            last_g = cg;
-        }
-        bool ok = false;
-        for (long long it = 0; it < kTmaWaitBound && !ok; ++it) ok = mbar_try_wait(&full[s], parity);
-        if (!ok) s_fail = 1;
-        __syncthreads();  // F complete; every thread saw the run arrive (or a wait gave up)
-        if (s_fail) {
-            if (tid == 0) atomicExch(err, 1);
-            return;
-        }
-        const float2* V = stage + (size_t)s * kTmaStageElems;
-        for (int i = warp; i < nr; i += nw) {
-            const float2* vr = V + (size_t)i * mp;
-            ff::F acc[4][ND];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[u][d] = ff::F{0.f, 0.f};
-            for (int k0 = lane; k0 < m; k0 += 128) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int k = k0 + 32 * u;
-                    if (k < m) {
-                        const float2 v = vr[k];
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) {
-                            const float2 x = F[d * smem_m + k];
-                            acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v.x, v.y}, ff::F{x.x, x.y}));
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int d = 0; d < ND; ++d)
-                acc[0][d] = ff::add(ff::add(acc[0][d], acc[1][d]), ff::add(acc[2][d], acc[3][d]));
-#pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float h = __shfl_xor_sync(0xffffffffu, acc[0][d].h, o);
-                    const float l = __shfl_xor_sync(0xffffffffu, acc[0][d].l, o);
-                    acc[0][d] = ff::add(acc[0][d], ff::F{h, l});
-                }
-            }
-            if (lane == 0) {
-                const int r = cr + i;
-                if (psi) {
-                    const int32_t ri = inv[r];
-                    const double wv = w_sorted ? w_sorted[ri] : 1.0;
-#pragma unroll
-                    for (int d = 0; d < ND; ++d)
-                        out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
-                } else {
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) out[d * ld_out + r] += ff::to_double(acc[0][d]);
-                }
-            }
-        }
-        __syncthreads();  // stage s and F are free
-        if (tid == 0) produce(s);
-        cr += nr;
-    }
-}
-
 template <int ND>
 cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
-                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, int* err, cudaStream_t s)
+                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, cudaStream_t s)
 {
-    // bulk-copy path (kept for matrices whose rows are long enough to fill its stages;
-    // with rows of a few hundred values the register-streaming kernel below is faster)
-    if (err && A.ngroups > 0 && A.max_m >= kTmaStageElems / 2 && (int64_t)(A.max_m + 1) * 8 <= kTmaStageBytes && ((uintptr_t)A.vf % 16) == 0) {
-        const int smem_m = A.max_m < 1 ? 1 : A.max_m;
-        const size_t bytes = (size_t)kTmaStages * kTmaStageBytes + (size_t)smem_m * ND * sizeof(float2);
-        if (bytes <= 200 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_out_grouped_tma<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)bytes);
-            if (e != cudaSuccess) return e;
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_out_grouped_tma<ND>, kGroupThreads, bytes) !=
-                    cudaSuccess ||
-                per_sm < 1)
-                per_sm = 1;
-            int sms = 152, dev = 0;
-            if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int blocks = std::min(A.ngroups, sms * per_sm);
-            k_out_grouped_tma<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, xf, ld_xf, out,
-                                                                      ld_out, err);
-            return cudaGetLastError();
-        }
-    }
     cudaError_t e = cudaFuncSetAttribute(k_out_grouped<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kGroupSmemBytes);
     if (e != cudaSuccess) return e;
@@ -350,13 +149,13 @@ cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, 
 
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
-                               int* err, cudaStream_t s)
+                               cudaStream_t s)
 {
     switch (nd) {
-        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, err, s);
-        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, err, s);
-        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, err, s);
-        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, err, s);
+        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -32,7 +32,7 @@ TREE_ARRAYS = {
 
 EXPORTED = [
     "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host",
-    "vp_plan_info", "vp_plan_check", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
+    "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
     "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
 ]
@@ -107,7 +107,6 @@ def _load():
         "vp_eval_adjoint": [P, I32, P, I64, P, I64, P, I64, P, P],
         "vp_eval_host": [P, I32, P, P, P],
         "vp_plan_info": [P, ctypes.POINTER(vp_plan_stats)],
-        "vp_plan_check": [P, P],
         "vp_plan_phase_times": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(I32)],
         "vp_plan_destroy": [P],
@@ -367,11 +366,6 @@ def vp_plan_info(plan) -> vp_plan_stats:
     return s
 
 
-def vp_plan_check(plan, stream=None):
-    """Raises VPError (VP_ERR_TIMEOUT) if a bounded device wait gave up since the last check."""
-    _check(_load().vp_plan_check(plan, _stream(stream)), "vp_plan_check")
-
-
 def vp_plan_phase_times(plan) -> dict:
     lib = _load()
     cap = 32
@@ -472,9 +466,6 @@ class Plan:
 
     def phase_times(self) -> dict:
         return vp_plan_phase_times(self.handle)
-
-    def check(self, stream=None):
-        vp_plan_check(self.handle, stream)
 
     def close(self):
         if self.handle:
