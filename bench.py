@@ -358,8 +358,14 @@ def main():
         plan.eval(fb, out=ob)
         bt = timed(lambda: plan.eval(fb, out=ob), max(2, args.steps // 5))
         bv = prob.n_tgt * args.batched / float(np.mean(bt)) / 1e6
+        # per-phase times of one pass of 8 densities
+        plan.set_flags(vp.VP_FLAG_TIMING)
+        flush_l2(flush)
+        plan.eval(fb[:8], out=ob[:8])
+        bphase = plan.phase_times()
+        plan.set_flags(vp.VP_FLAG_GRAPH)
         batched = {"ndens": args.batched, "value": bv, "unit": UNIT, "speedup_vs_single": bv / value,
-                   "ms_per_step": float(np.mean(bt)) * 1e3}
+                   "ms_per_step": float(np.mean(bt)) * 1e3, "phase_ms_8_densities": bphase}
         del fb, ob
 
     # adjoint leg: transposed FMM + transposed correction (dL/df), one density
