@@ -1025,6 +1025,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.work, 4);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.m2m_count, (size_t)std::max<int32_t>(nb, 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.m2m_count, 0, sizeof(int) * (size_t)std::max<int32_t>(nb, 1), s);
     if (e == cudaSuccess && sym) e = p->alloc(&p->ws.slots, (size_t)std::max<int64_t>(nslots, 1) * p->nd_cap);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
@@ -1341,8 +1343,11 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
     p->last_launches = 0;
     for (int d0 = 0; d0 < ndens;) {
         const int nd = chunk_for(ndens - d0, p->nd_cap);
-        // charges, P2M, M2M per level, M2L, L2L per level, leaf (+ slot reduction), output
-        p->last_launches += 5 + 2 * (int64_t)(p->dt.nlevels - 1) + (p->dt.sym && nd <= 2 ? 1 : 0);
+        // charges, P2M (+ M2M in the same launch on the float-float path, else per
+        // level), M2L, L2L per level, leaf (+ slot reduction), output
+        const bool ffp = !use_fp64(p);
+        p->last_launches += 5 + (ffp ? 0 : (int64_t)(p->dt.nlevels - 1)) + (int64_t)(p->dt.nlevels - 1) +
+                            (p->dt.sym && nd <= 2 ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
         if (p->ups)

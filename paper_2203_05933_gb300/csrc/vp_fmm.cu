@@ -324,17 +324,103 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }
 
 // ----------------------------------------------------------------------------
+// complex float-float times an exact float complex (a power of zeta: every
+// component is 0 or a power of two, so each product below is exact)
+__device__ __forceinline__ ff::C cmul_exact(ff::C a, float zx, float zy)
+{
+    const ff::F ax{__fmul_rn(a.re.h, zx), __fmul_rn(a.re.l, zx)}, ay{__fmul_rn(a.re.h, zy), __fmul_rn(a.re.l, zy)};
+    const ff::F bx{__fmul_rn(a.im.h, zx), __fmul_rn(a.im.l, zx)}, by{__fmul_rn(a.im.h, zy), __fmul_rn(a.im.l, zy)};
+    return ff::C{ff::add(ax, ff::neg(by)), ff::add(ay, bx)};
+}
+
+// M2M of one box by one warp: M(b) = sum over children of the shifted child
+// multipoles (scaled form: the operator depends only on the child quadrant).
+// The children are staged CB at a time (Ms [CB][P1][ND]) so that their loads
+// overlap. CG: read the children with L1 bypassed (written by other blocks in
+// the same launch).
+template <int P, int ND, int CB, bool CG>
+__device__ __forceinline__ void m2m_box_ff(const DevTree& t, const DevTables& tab, int b, float4* __restrict__ Mf,
+                                           float4 (*Ms)[P + 1][ND], int lane, const ff::F minvl)
+{
+    constexpr int P1 = P + 1;
+    ff::C acc[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+    for (int c0 = 0; c0 < 4; c0 += CB) {
+        int chs[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+            chs[c] = t.child[4 * b + c0 + c];
+            if (chs[c] >= 0 && lane <= P) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const float4* src = Mf + ((int64_t)chs[c] * P1 + lane) * ND + d;
+                    Ms[c][lane][d] = CG ? __ldcg(src) : *src;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane <= P) {
+            for (int c = 0; c < CB; ++c) {
+                if (chs[c] < 0) continue;
+                const float2* zp = tab.zpowf + (c0 + c) * P1;
+                if (lane == 0) {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d] = ff::cadd(acc[d], ff::from_float4(Ms[c][0][d]));
+                } else {
+                    const float2 zl = zp[lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 m0 = Ms[c][0][d];
+                        const ff::F a = ff::mul(ff::F{m0.x, m0.y}, minvl);  // -M_0 / l (M_0 is real)
+                        acc[d] = ff::cadd(acc[d], cmul_exact(ff::C{a, {0.f, 0.f}}, zl.x, zl.y));
+                    }
+                    for (int k = 1; k <= lane; ++k) {
+                        const float2 bv = tab.Bmf[lane * P1 + k];
+                        const float2 z = zp[lane - k];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const ff::C mk = ff::from_float4(Ms[c][k][d]);
+                            const ff::C bm{ff::mul(mk.re, ff::F{bv.x, bv.y}), ff::mul(mk.im, ff::F{bv.x, bv.y})};
+                            acc[d] = ff::cadd(acc[d], cmul_exact(bm, z.x, z.y));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = ff::cnorm(acc[d]);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane <= P) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(acc[d]);
+    }
+    __syncwarp();
+}
+
 // a3/a5 on the FP32 pipes: P2M, M2M and L2L with float-float expansions (same
 // operators as the FP64 kernels above; zeta powers are exact in float).
 //
 // P2M: u = (z - c)/R = 2 rho, rho the leaf-relative coordinate (hi/lo floats).
+// With counters (one per box, zero on entry and left zero), the upward pass
+// follows in the same launch: a warp that has finished a box counts itself in
+// at the parent (after a fence), and the warp that completes the count computes
+// the parent's M2M and carries on upwards; nothing waits.
 template <int P, int ND>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_p2m_ff(DevTree t, DevTables tab, PassGeom g, const float2* __restrict__ qf, float4* __restrict__ Mf)
+    k_p2m_ff(DevTree t, DevTables tab, PassGeom g, const float2* __restrict__ qf, float4* __restrict__ Mf,
+             int* __restrict__ counters)
 {
     constexpr int P1 = P + 1;
-    __shared__ float4 pw[kWarpsPerBlock][kChunk][P1];
+    // per warp: the powers of the staged charges, later the children staged by M2M
+    // (CB children at a time in the same space)
+    constexpr int kBuf = kChunk * P1;
+    constexpr int CB = kChunk / ND >= 4 ? 4 : kChunk / ND;
+    static_assert(CB >= 1 && CB * ND <= kChunk, "M2M staging");
+    __shared__ float4 sbuf[kWarpsPerBlock][kBuf];
     __shared__ float2 qs[kWarpsPerBlock][kChunk][ND];
+    auto pwf = [&](int w, int j, int k) -> float4& { return sbuf[w][j * P1 + k]; };
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     const int ll = lane <= P ? lane : P;
     const ff::F minvl = ff::neg(ff::F{tab.invlf[ll].x, tab.invlf[ll].y});
@@ -350,10 +436,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 const float4 r = g.crho[base + lane];
                 const ff::C u{{2.f * r.x, 2.f * r.y}, {2.f * r.z, 2.f * r.w}};
                 ff::C p{{1.f, 0.f}, {0.f, 0.f}};
-                pw[wb][lane][0] = ff::to_float4(p);
+                pwf(wb, lane, 0) = ff::to_float4(p);
                 for (int k = 1; k <= P; ++k) {
                     p = ff::cnorm(ff::cmul(p, u));
-                    pw[wb][lane][k] = ff::to_float4(p);
+                    pwf(wb, lane, k) = ff::to_float4(p);
                 }
 #pragma unroll
                 for (int d = 0; d < ND; ++d) qs[wb][lane][d] = qf[(int64_t)(base + lane) * ND + d];
@@ -361,7 +447,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             __syncwarp();
             if (lane <= P) {
                 for (int j = 0; j < n; ++j) {
-                    const float4 pv = pw[wb][j][lane];
+                    const float4 pv = pwf(wb, j, lane);
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
                         const ff::F qq{qs[wb][j][d].x, qs[wb][j][d].y};
@@ -382,72 +468,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(m);
             }
         }
-    }
-}
-
-// complex float-float times an exact float complex (a power of zeta: every
-// component is 0 or a power of two, so each product below is exact)
-__device__ __forceinline__ ff::C cmul_exact(ff::C a, float zx, float zy)
-{
-    const ff::F ax{__fmul_rn(a.re.h, zx), __fmul_rn(a.re.l, zx)}, ay{__fmul_rn(a.re.h, zy), __fmul_rn(a.re.l, zy)};
-    const ff::F bx{__fmul_rn(a.im.h, zx), __fmul_rn(a.im.l, zx)}, by{__fmul_rn(a.im.h, zy), __fmul_rn(a.im.l, zy)};
-    return ff::C{ff::add(ax, ff::neg(by)), ff::add(ay, bx)};
-}
-
-template <int P, int ND>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_m2m_ff(DevTree t, DevTables tab, int b0, int b1, float4* __restrict__ Mf)
-{
-    constexpr int P1 = P + 1;
-    __shared__ float4 Ms[kWarpsPerBlock][P1][ND];
-    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    const int ll = lane <= P ? lane : P;
-    const ff::F minvl = ff::neg(ff::F{tab.invlf[ll].x, tab.invlf[ll].y});
-    for (int b = b0 + global_warp(); b < b1; b += num_warps()) {
-        if (t.is_leaf[b]) continue;
-        ff::C acc[ND];
+        if (counters) {
+            for (int cur = b;;) {
+                const int par = t.parent[cur];
+                if (par < 0) break;
+                __threadfence();  // this warp's M(cur) before its arrival at the parent
+                __syncwarp();
+                int old = 0;
+                if (lane == 0) old = atomicAdd(&counters[par], 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                int nch = 0;
 #pragma unroll
-        for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
-        for (int c = 0; c < 4; ++c) {
-            const int ch = t.child[4 * b + c];
-            if (ch < 0) continue;
-            if (lane <= P) {
-#pragma unroll
-                for (int d = 0; d < ND; ++d) Ms[wb][lane][d] = Mf[((int64_t)ch * P1 + lane) * ND + d];
+                for (int c = 0; c < 4; ++c) nch += t.child[4 * par + c] >= 0 ? 1 : 0;
+                if (old != nch - 1) break;  // a sibling is still running; it will carry on
+                __threadfence();            // the siblings' M before reading them
+                if (lane == 0) counters[par] = 0;
+                m2m_box_ff<P, ND, CB, true>(t, tab, par, Mf, reinterpret_cast<float4(*)[P1][ND]>(&sbuf[wb][0]), lane, minvl);
+                cur = par;
             }
-            __syncwarp();
-            if (lane <= P) {
-                const float2* zp = tab.zpowf + c * P1;
-                if (lane == 0) {
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) acc[d] = ff::cadd(acc[d], ff::from_float4(Ms[wb][0][d]));
-                } else {
-                    const float2 zl = zp[lane];
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        const float4 m0 = Ms[wb][0][d];
-                        const ff::F a = ff::mul(ff::F{m0.x, m0.y}, minvl);  // -M_0 / l (M_0 is real)
-                        acc[d] = ff::cadd(acc[d], cmul_exact(ff::C{a, {0.f, 0.f}}, zl.x, zl.y));
-                    }
-                    for (int k = 1; k <= lane; ++k) {
-                        const float2 bv = tab.Bmf[lane * P1 + k];
-                        const float2 z = zp[lane - k];
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) {
-                            const ff::C mk = ff::from_float4(Ms[wb][k][d]);
-                            const ff::C bm{ff::mul(mk.re, ff::F{bv.x, bv.y}), ff::mul(mk.im, ff::F{bv.x, bv.y})};
-                            acc[d] = ff::cadd(acc[d], cmul_exact(bm, z.x, z.y));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[d] = ff::cnorm(acc[d]);
-            }
-            __syncwarp();
-        }
-        if (lane <= P) {
-#pragma unroll
-            for (int d = 0; d < ND; ++d) Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(acc[d]);
         }
     }
 }
@@ -1318,20 +1356,20 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
     const int threads = kWarpsPerBlock * 32;
     const bool ffp = !fp64 && !gradient;  // float-float pipeline (potential only)
     int id = tm ? tm->begin("p2m") : -1;
-    if (ffp)
-        k_p2m_ff<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, tab, g, ws.qf, ws.Mf);
-    else
+    if (ffp) {
+        // P2M and the whole M2M pass in one launch (see k_p2m_ff)
+        k_p2m_ff<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, tab, g, ws.qf, ws.Mf, ws.m2m_count);
+        if (tm) tm->end(id);
+    } else {
         k_p2m<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.q, ws.M);
-    if (tm) tm->end(id);
-    id = tm ? tm->begin("m2m") : -1;
-    for (int l = t.nlevels - 2; l >= 0; --l) {
-        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
-        if (ffp)
-            k_m2m_ff<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.Mf);
-        else
+        if (tm) tm->end(id);
+        id = tm ? tm->begin("m2m") : -1;
+        for (int l = t.nlevels - 2; l >= 0; --l) {
+            const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
             k_m2m<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.M);
+        }
+        if (tm) tm->end(id);
     }
-    if (tm) tm->end(id);
     id = tm ? tm->begin("m2l") : -1;
     if (ffp)
         k_m2l_ff<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.Mf, ws.Lf, ws.qf);

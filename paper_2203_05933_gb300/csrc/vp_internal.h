@@ -129,6 +129,7 @@ struct Workspace {
     float2* xf = nullptr;     // [ND][max(n_src, n_tgt)] correction input (f or g) as hi/lo floats
     int* work = nullptr;      // work-queue counter of the persistent near-field kernel
     float2* slots = nullptr;  // [sym_slots][ND] symmetric near-field partial sums
+    int* m2m_count = nullptr; // [nbox] arrivals of finished children (zero between launches)
     int32_t nd_cap = 0;
 };
 
