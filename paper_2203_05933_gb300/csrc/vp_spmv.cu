@@ -19,6 +19,7 @@ namespace {
 constexpr double kInv2PiG = 0.159154943091895335768883763372514362;
 constexpr int kGroupThreads = 256;
 constexpr int kGroupSmemBytes = 96 * 1024;
+static_assert((kGroupSmemBytes / (8 * (int)sizeof(float2))) % 2 == 0, "even staging capacity for 8 densities");
 
 __global__ void k_to_ff_rows(int64_t total, int32_t n, const double* __restrict__ x, int64_t ld_x,
                              float2* __restrict__ xf)
@@ -125,9 +126,12 @@ cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const 
     cudaError_t e = cudaFuncSetAttribute(k_out_grouped<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kGroupSmemBytes);
     if (e != cudaSuccess) return e;
+    // the staged columns of density d start at F + d * smem_m and are read as 16-byte
+    // pairs: smem_m must be even (the capacity below is)
     int smem_m = kGroupSmemBytes / (ND * (int)sizeof(float2));
-    if (A.max_m < smem_m) smem_m = A.max_m;
-    if (smem_m < 1) smem_m = 1;
+    const int want = A.max_m + (A.max_m & 1);
+    if (want < smem_m) smem_m = want;
+    if (smem_m < 2) smem_m = 2;
     const size_t bytes = (size_t)smem_m * ND * sizeof(float2);
     int blocks = A.ngroups < 152 * 16 ? A.ngroups : 152 * 16;
     if (blocks < 1) blocks = 1;
