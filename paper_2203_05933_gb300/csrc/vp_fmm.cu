@@ -1355,7 +1355,7 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
 {
     const int threads = kWarpsPerBlock * 32;
     const bool ffp = !fp64 && !gradient;  // float-float pipeline (potential only)
-    int id = tm ? tm->begin("p2m") : -1;
+    int id = tm ? tm->begin(ffp ? "upward" : "p2m") : -1;
     if (ffp) {
         // P2M and the whole M2M pass in one launch (see k_p2m_ff)
         k_p2m_ff<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, tab, g, ws.qf, ws.Mf, ws.m2m_count);
