@@ -336,16 +336,18 @@ __device__ __forceinline__ ff::C cmul_exact(ff::C a, float zx, float zy)
 // M2M of one box by one warp: M(b) = sum over children of the shifted child
 // multipoles (scaled form: the operator depends only on the child quadrant).
 // The children are staged CB at a time (Ms [CB][P1][ND]) so that their loads
-// overlap. CG: read the children with L1 bypassed (written by other blocks in
+// overlap, and each staged child has its own accumulator, so the CB sums
+// advance side by side (the box's M2M is on the critical path of the upward
+// pass). CG: read the children with L1 bypassed (written by other blocks in
 // the same launch).
 template <int P, int ND, int CB, bool CG>
 __device__ __forceinline__ void m2m_box_ff(const DevTree& t, const DevTables& tab, int b, float4* __restrict__ Mf,
                                            float4 (*Ms)[P + 1][ND], int lane, const ff::F minvl)
 {
     constexpr int P1 = P + 1;
-    ff::C acc[ND];
+    ff::C tot[ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+    for (int d = 0; d < ND; ++d) tot[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
     for (int c0 = 0; c0 < 4; c0 += CB) {
         int chs[CB];
 #pragma unroll
@@ -361,40 +363,47 @@ __device__ __forceinline__ void m2m_box_ff(const DevTree& t, const DevTables& ta
         }
         __syncwarp();
         if (lane <= P) {
+            ff::C acc[CB][ND];
+#pragma unroll
             for (int c = 0; c < CB; ++c) {
-                if (chs[c] < 0) continue;
-                const float2* zp = tab.zpowf + (c0 + c) * P1;
-                if (lane == 0) {
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) acc[d] = ff::cadd(acc[d], ff::from_float4(Ms[c][0][d]));
-                } else {
-                    const float2 zl = zp[lane];
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        const float4 m0 = Ms[c][0][d];
+                for (int d = 0; d < ND; ++d) {
+                    acc[c][d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+                    if (chs[c] < 0) continue;
+                    const float4 m0 = Ms[c][0][d];
+                    if (lane == 0) {
+                        acc[c][d] = ff::from_float4(m0);
+                    } else {
+                        const float2 zl = tab.zpowf[(c0 + c) * P1 + lane];
                         const ff::F a = ff::mul(ff::F{m0.x, m0.y}, minvl);  // -M_0 / l (M_0 is real)
-                        acc[d] = ff::cadd(acc[d], cmul_exact(ff::C{a, {0.f, 0.f}}, zl.x, zl.y));
-                    }
-                    for (int k = 1; k <= lane; ++k) {
-                        const float2 bv = tab.Bmf[lane * P1 + k];
-                        const float2 z = zp[lane - k];
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) {
-                            const ff::C mk = ff::from_float4(Ms[c][k][d]);
-                            const ff::C bm{ff::mul(mk.re, ff::F{bv.x, bv.y}), ff::mul(mk.im, ff::F{bv.x, bv.y})};
-                            acc[d] = ff::cadd(acc[d], cmul_exact(bm, z.x, z.y));
-                        }
+                        acc[c][d] = cmul_exact(ff::C{a, {0.f, 0.f}}, zl.x, zl.y);
                     }
                 }
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[d] = ff::cnorm(acc[d]);
             }
+            for (int k = 1; k <= lane; ++k) {
+                const float2 bv = tab.Bmf[lane * P1 + k];
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    if (chs[c] < 0) continue;
+                    const float2 z = tab.zpowf[(c0 + c) * P1 + lane - k];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const ff::C mk = ff::from_float4(Ms[c][k][d]);
+                        const ff::C bm{ff::mul(mk.re, ff::F{bv.x, bv.y}), ff::mul(mk.im, ff::F{bv.x, bv.y})};
+                        acc[c][d] = ff::cadd(acc[c][d], cmul_exact(bm, z.x, z.y));
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) tot[d] = ff::cnorm(ff::cadd(tot[d], acc[c][d]));
         }
         __syncwarp();
     }
     if (lane <= P) {
 #pragma unroll
-        for (int d = 0; d < ND; ++d) Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(acc[d]);
+        for (int d = 0; d < ND; ++d) Mf[((int64_t)b * P1 + lane) * ND + d] = ff::to_float4(tot[d]);
     }
     __syncwarp();
 }
