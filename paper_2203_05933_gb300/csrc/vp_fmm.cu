@@ -547,7 +547,7 @@ constexpr int kChunkF = 8;  // charges staged per step in the float-float P2L
 template <int P, int ND>
 struct M2LffSmem {
     static constexpr int P1 = P + 1;
-    static constexpr int kA = P1 * ND;                                   // V-list staging (float4)
+    static constexpr int kA = 2 * P1 * ND;                               // V-list staging (float4), two halves
     static constexpr int kPw = kChunkF * P1;                             // P2L powers (float4)
     static constexpr int kX = kPw + (kChunkF * (ND + 1) * 2 + 3) / 4;    // + charges and logs (float2)
     static constexpr int kUnion = kA > kX ? kA : kX;
@@ -582,6 +582,124 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
         const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
         const ff::F logR = ff::from_double(t.log_radius[b]);
+        if constexpr (P == 16) {
+            // 17 coefficients: each half-warp takes every other V-list entry, lane
+            // hl of a half computes L_hl, and L_16 is summed across the half
+            // (one term per lane, then a 4-step exchange); the halves are added
+            // at the end, with L_16 placed in lane 16.
+            const int h = lane >> 4, hl = lane & 15;
+            float4(*Ah)[ND] = reinterpret_cast<float4(*)[ND]>(&buf[wb][h * P1 * ND]);
+            const ff::F invh{tab.invlf[hl].x, tab.invlf[hl].y};
+            const ff::F inv16{tab.invlf[16].x, tab.invlf[16].y};
+            ff::C l16[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) l16[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+            for (int it = v0; it < v1; it += 2) {
+                const int e = it + h;
+                const bool ok = e < v1;
+                int o = 0;
+                if (ok) {
+                    const int C = t.v_idx[e];
+                    o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+                    const ff::C mt = ff::from_float4(tab.mtpowf[o * P1 + hl]);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const ff::C m = ff::from_float4(Mf[((int64_t)C * P1 + hl) * ND + d]);
+                        Ah[hl][d] = ff::to_float4(hl == 0 ? m : ff::cnorm(ff::cmul(m, mt)));
+                    }
+                    if (hl == 0) {
+                        const ff::C mt16 = ff::from_float4(tab.mtpowf[o * P1 + 16]);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d)
+                            Ah[16][d] = ff::to_float4(
+                                ff::cnorm(ff::cmul(ff::from_float4(Mf[((int64_t)C * P1 + 16) * ND + d]), mt16)));
+                    }
+                }
+                __syncwarp();
+                ff::C part[ND];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) part[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+                if (ok) {
+                    ff::C acc[ND];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d] = ff::C{{0.f, 0.f}, {0.f, 0.f}};
+                    for (int k = 1; k <= 16; ++k) {
+                        const float2 hv = Hs[hl * P1 + k];
+                        const ff::F hh{hv.x, hv.y};
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const float4 a = Ah[k][d];
+                            acc[d].re = ff::add(acc[d].re, ff::mul(hh, ff::F{a.x, a.y}));
+                            acc[d].im = ff::add(acc[d].im, ff::mul(hh, ff::F{a.z, a.w}));
+                        }
+                    }
+                    if (hl == 0) {
+                        const float2 lo = tab.log2of[o];
+                        const ff::F lz = ff::add(logR, ff::F{lo.x, lo.y});
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const float4 a0 = Ah[0][d];
+                            lacc[d].re = ff::add(lacc[d].re, ff::add(acc[d].re, ff::mul(ff::F{a0.x, a0.y}, lz)));
+                            lacc[d].im = ff::add(lacc[d].im, acc[d].im);
+                        }
+                    } else {
+                        const ff::C tl = ff::from_float4(tab.tpowf[o * P1 + hl]);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const float4 a0 = Ah[0][d];
+                            const ff::C a{ff::add(acc[d].re, ff::neg(ff::mul(ff::F{a0.x, a0.y}, invh))),
+                                          ff::add(acc[d].im, ff::neg(ff::mul(ff::F{a0.z, a0.w}, invh)))};
+                            lacc[d] = ff::cadd(lacc[d], ff::cmul(tl, ff::cnorm(a)));
+                        }
+                    }
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) lacc[d] = ff::cnorm(lacc[d]);
+                    // this lane's term of L_16: H[16][hl + 1] A_(hl + 1)
+                    const float2 hv = Hs[16 * P1 + hl + 1];
+                    const ff::F hh{hv.x, hv.y};
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 a = Ah[hl + 1][d];
+                        part[d] = ff::C{ff::mul(hh, ff::F{a.x, a.y}), ff::mul(hh, ff::F{a.z, a.w})};
+                    }
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    for (int sh = 8; sh > 0; sh >>= 1) {
+                        const ff::C other{{__shfl_xor_sync(0xffffffffu, part[d].re.h, sh, 16),
+                                           __shfl_xor_sync(0xffffffffu, part[d].re.l, sh, 16)},
+                                          {__shfl_xor_sync(0xffffffffu, part[d].im.h, sh, 16),
+                                           __shfl_xor_sync(0xffffffffu, part[d].im.l, sh, 16)}};
+                        part[d] = ff::cadd(part[d], other);
+                    }
+                }
+                if (ok) {
+                    const ff::C t16 = ff::from_float4(tab.tpowf[o * P1 + 16]);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const float4 a0 = Ah[0][d];
+                        const ff::C a{ff::add(part[d].re, ff::neg(ff::mul(ff::F{a0.x, a0.y}, inv16))),
+                                      ff::add(part[d].im, ff::neg(ff::mul(ff::F{a0.z, a0.w}, inv16)))};
+                        l16[d] = ff::cnorm(ff::cadd(l16[d], ff::cmul(t16, ff::cnorm(a))));
+                    }
+                }
+                __syncwarp();
+            }
+            // add the halves: lanes 0..15 hold L_0..L_15, lane 16 takes L_16
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const ff::C ol{{__shfl_xor_sync(0xffffffffu, lacc[d].re.h, 16),
+                                __shfl_xor_sync(0xffffffffu, lacc[d].re.l, 16)},
+                               {__shfl_xor_sync(0xffffffffu, lacc[d].im.h, 16),
+                                __shfl_xor_sync(0xffffffffu, lacc[d].im.l, 16)}};
+                const ff::C o16{{__shfl_xor_sync(0xffffffffu, l16[d].re.h, 16),
+                                 __shfl_xor_sync(0xffffffffu, l16[d].re.l, 16)},
+                                {__shfl_xor_sync(0xffffffffu, l16[d].im.h, 16),
+                                 __shfl_xor_sync(0xffffffffu, l16[d].im.l, 16)}};
+                if (lane < 16) lacc[d] = ff::cnorm(ff::cadd(lacc[d], ol));
+                else if (lane == 16) lacc[d] = ff::cnorm(ff::cadd(l16[d], o16));
+            }
+        } else
         for (int e = v0; e < v1; ++e) {
             const int C = t.v_idx[e];
             const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);

@@ -364,3 +364,23 @@ def test_symmetric_near_field_matches_fp64(which):
     err_a = float(np.max(np.abs(res[0][1] - res[vp.VP_FLAG_FP64][1]) / scale))
     print(f"{which}: symmetric float-float vs FP64 forward {err:.2e} adjoint {err_a:.2e}")
     assert err <= 1e-12 and err_a <= 1e-12
+
+
+@pytest.mark.parametrize("ndens", [1, 3, 8])
+def test_p16_float_float_matches_fp64(ndens):
+    # P = 16 has its own M2L schedule (half-warps over alternate V-list entries);
+    # check it, with every density chunk width, against the all-FP64 kernels on
+    # an adaptive cloud (V, W and X lists all present)
+    prob = inputs.cloud_problem(6000, 5000, ndens=ndens, shared=1500, seed=61)
+    f = torch.as_tensor(prob.f, device="cuda")
+    res = {}
+    for flags in (0, vp.VP_FLAG_FP64):
+        plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=16, leaf=32, max_dens=8,
+                              flags=flags)
+        info = plan.info()
+        assert info.n_x_pairs > 0 and info.n_w_pairs > 0
+        res[flags] = plan.eval(f).cpu().numpy()
+        plan.close()
+    err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / inputs.normaliser(prob)[:, None]))
+    print(f"P=16 float-float vs FP64, {ndens} densities: {err:.2e}")
+    assert err <= 1e-12
