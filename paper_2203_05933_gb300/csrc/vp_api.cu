@@ -1344,10 +1344,11 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
     for (int d0 = 0; d0 < ndens;) {
         const int nd = chunk_for(ndens - d0, p->nd_cap);
         // charges, P2M (+ M2M in the same launch on the float-float path, else per
-        // level), M2L, L2L per level, leaf (+ slot reduction), output
+        // level from level 2 up), M2L, L2L per level from level 3 down, leaf (+ slot
+        // reduction), output
         const bool ffp = !use_fp64(p);
-        p->last_launches += 5 + (ffp ? 0 : (int64_t)(p->dt.nlevels - 1)) + (int64_t)(p->dt.nlevels - 1) +
-                            (p->dt.sym && nd <= 2 ? 1 : 0);
+        p->last_launches += 5 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
+                            (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
         int id = p->timer.begin("charges");
         if (p->ups)

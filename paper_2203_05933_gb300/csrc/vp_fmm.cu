@@ -480,7 +480,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         if (counters) {
             for (int cur = b;;) {
                 const int par = t.parent[cur];
-                if (par < 0) break;
+                // multipoles of levels 0 and 1 are never read (V, W and X lists start at level 2)
+                if (par < 0 || t.level[par] < 2) break;
                 __threadfence();  // this warp's M(cur) before its arrival at the parent
                 __syncwarp();
                 int old = 0;
@@ -1491,7 +1492,7 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
         k_p2m<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.q, ws.M);
         if (tm) tm->end(id);
         id = tm ? tm->begin("m2m") : -1;
-        for (int l = t.nlevels - 2; l >= 0; --l) {
+        for (int l = t.nlevels - 2; l >= 2; --l) {  // levels 0 and 1 are never read
             const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
             k_m2m<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.M);
         }
@@ -1504,7 +1505,9 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
         k_m2l<P, ND><<<warp_blocks(t.nbox), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q);
     if (tm) tm->end(id);
     id = tm ? tm->begin("l2l") : -1;
-    for (int l = 1; l < t.nlevels; ++l) {
+    // boxes of levels 0 and 1 have empty V and X lists, so their locals are zero
+    // and the first L2L that adds anything goes into level 3
+    for (int l = 3; l < t.nlevels; ++l) {
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
         if (ffp)
             k_l2l_ff<P, ND><<<warp_blocks(b1 - b0), threads, 0, s>>>(t, tab, b0, b1, ws.Lf);
