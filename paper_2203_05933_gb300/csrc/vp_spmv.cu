@@ -58,21 +58,24 @@ __global__ void __launch_bounds__(kGroupThreads)
         const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
         for (int r = r0 + warp; r < r1; r += nw) {
             const float4* vrow = reinterpret_cast<const float4*>(A.vf + A.rowptr[r]);  // rows start on 16 bytes
-            // four independent accumulators per density keep four 16-byte loads in flight per lane
-            ff::F acc[4][ND];
+            // U independent accumulators per density keep U 16-byte loads in flight per
+            // lane (four for one or two densities; two beyond, where each value is
+            // reused ND times and registers are the scarcer resource)
+            constexpr int U = ND >= 4 ? 2 : 4;
+            ff::F acc[U][ND];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int d = 0; d < ND; ++d) acc[u][d] = ff::F{0.f, 0.f};
-            for (int q0 = lane; q0 < np; q0 += 128) {
-                float4 v[4];
+            for (int q0 = lane; q0 < np; q0 += 32 * U) {
+                float4 v[U];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const int q = q0 + 32 * u;
                     v[u] = q < np ? vrow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const int q = q0 + 32 * u;
                     if (q < np) {
                         const int k = 2 * q;
@@ -93,8 +96,9 @@ __global__ void __launch_bounds__(kGroupThreads)
                 }
             }
 #pragma unroll
-            for (int d = 0; d < ND; ++d)
-                acc[0][d] = ff::add(ff::add(acc[0][d], acc[1][d]), ff::add(acc[2][d], acc[3][d]));
+            for (int u = 1; u < U; ++u)
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[0][d] = ff::add(acc[0][d], acc[u][d]);
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 for (int o = 16; o > 0; o >>= 1) {
