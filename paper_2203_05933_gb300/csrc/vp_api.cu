@@ -406,6 +406,9 @@ struct vp_plan_s {
     };
     std::vector<GraphEntry> graphs;  // captured evaluations (VP_FLAG_GRAPH), most recent last
     cudaStream_t cap_stream = nullptr;
+    // the correction product runs beside the FMM on a low-priority stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // staging for vp_eval_host
     double* stage = nullptr;
     size_t stage_cap = 0;
@@ -438,6 +441,9 @@ struct vp_plan_s {
     {
         for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         for (void* p : allocs) cudaFree(p);
         if (stage) cudaFree(stage);
         for (auto e : timer.pool) cudaEventDestroy(e);
@@ -1025,6 +1031,13 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     if (e == cudaSuccess) e = p->alloc(&p->ws.Lf, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.L, (size_t)nb * P1 * p->nd_cap);
     if (e == cudaSuccess) e = p->alloc(&p->ws.work, 4);
+    if (e == cudaSuccess && p->grouped) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = p->alloc(&p->ws.m2m_count, (size_t)std::max<int32_t>(nb, 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(p->ws.m2m_count, 0, sizeof(int) * (size_t)std::max<int32_t>(nb, 1), s);
     if (e == cudaSuccess && sym) e = p->alloc(&p->ws.slots, (size_t)std::max<int64_t>(nslots, 1) * p->nd_cap);
@@ -1350,6 +1363,19 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         p->last_launches += 5 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
                             (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
+        double* oc = out + (int64_t)d0 * ld_out;
+        // Pi f does not depend on the FMM: outside phase timing it runs beside the
+        // FMM on the plan's low-priority stream, and the smooth part is added after
+        const bool overlap = p->grouped && !p->timer.on;
+        if (overlap) {
+            VP_CUDA(cudaEventRecord(p->ev_fork, s));
+            VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+            VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, p->side));
+            VP_CUDA(launch_out_grouped(nd, p->gfwd, nullptr, nullptr, nullptr, p->ws.xf, p->n_f, oc, ld_out,
+                                       kOutOverwrite, p->side));
+            VP_CUDA(cudaEventRecord(p->ev_join, p->side));
+            p->last_launches += 2;
+        }
         int id = p->timer.begin("charges");
         if (p->ups)
             VP_CUDA(launch_ups_charges(nd, p->dups, p->src_inv, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
@@ -1359,10 +1385,13 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, use_fp64(p),
                                      p->timer.on ? &p->timer : nullptr, s));
         id = p->timer.begin("out");
-        if (p->grouped) {
+        if (overlap) {
+            VP_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+            VP_CUDA(launch_add_psi(nd, (int32_t)p->n_tgt, p->tgt_inv, nullptr, p->ws.psi, oc, ld_out, s));
+        } else if (p->grouped) {
             VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, s));
-            VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f,
-                                       out + (int64_t)d0 * ld_out, ld_out, s));
+            VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f, oc, ld_out,
+                                       kOutWithPsi, s));
             p->last_launches += 1;
         } else {
             VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc,
@@ -1386,7 +1415,12 @@ vp_status eval_graph(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, do
             VP_CUDA(cudaGraphLaunch(gc.exec, s));
             return VP_OK;
         }
-    if (!p->cap_stream) VP_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    if (!p->cap_stream) {
+        // captured FMM kernels take precedence over the correction product beside them
+        int least = 0, greatest = 0;
+        VP_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        VP_CUDA(cudaStreamCreateWithPriority(&p->cap_stream, cudaStreamNonBlocking, greatest));
+    }
     // order the capture after the caller's pending work on s, and the replay after the capture
     VP_CUDA(cudaStreamSynchronize(s));
     VP_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -1456,16 +1490,30 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
         for (int d0 = 0; d0 < ndens;) {
             const int nd = chunk_for(ndens - d0, p->nd_cap);
             const double* gc = g + (int64_t)d0 * ld_g;
+            double* gfc0 = grad_f + (int64_t)d0 * ld_gf;
+            // Pi^T g beside the transposed FMM (as in the forward evaluation)
+            const bool overlap = p->grouped && !p->ups;
+            if (overlap) {
+                VP_CUDA(cudaEventRecord(p->ev_fork, s));
+                VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+                VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, p->side));
+                VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc0, ld_gf,
+                                           kOutOverwrite, p->side));
+                VP_CUDA(cudaEventRecord(p->ev_join, p->side));
+            }
             VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
             VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, use_fp64(p), nullptr, s));
-            if (p->ups) {
+            if (overlap) {
+                VP_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+                VP_CUDA(launch_add_psi(nd, (int32_t)p->n_f, p->src_inv, p->w_sorted, p->ws.psi, gfc0, ld_gf, s));
+            } else if (p->ups) {
                 // grad_f = O^T (w * transposed sum at the q-nodes), then += Pi^T g
                 double* gfc = grad_f + (int64_t)d0 * ld_gf;
                 VP_CUDA(launch_ups_adjoint(nd, p->dups, p->src_inv, p->w_sorted, p->ws.psi, gfc, ld_gf, s));
                 if (p->grouped) {
                     VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                     VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc, ld_gf,
-                                               s));
+                                               kOutAccumulate, s));
                 } else if (p->cptr) {
                     VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_f, nullptr, nullptr, nullptr, p->cptr, p->crow,
                                                p->cval, gc, ld_g, gfc, ld_gf, s));
@@ -1473,7 +1521,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             } else if (p->grouped) {
                 VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                 VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
-                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
+                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, kOutWithPsi, s));
             } else {
                 VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr,
                                            p->crow, p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));

@@ -164,12 +164,18 @@ cudaError_t launch_grad_out(int nd, bool accumulate, int32_t n_tgt, const int32_
                             cudaStream_t s);
 
 // Correction apply on the FP32 pipes (vp_spmv.cu): out[d][r] = -(1/2pi) w psi[inv[r]][d] + (A x)[d][r]
-// for every row r of A, w = w_sorted[inv[r]] or 1 when w_sorted is NULL; with psi NULL,
-// out[d][r] += (A x)[d][r] instead (launch_out_adjoint likewise).
+// for every row r of A, w = w_sorted[inv[r]] or 1 when w_sorted is NULL (see mode below;
+// launch_out_adjoint accumulates when psi is NULL).
 cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, float2* xf, cudaStream_t s);
+// mode: kOutWithPsi (out = -(1/2pi) w psi + A x), kOutAccumulate (out += A x),
+// kOutOverwrite (out = A x).
+constexpr int kOutWithPsi = 0, kOutAccumulate = 1, kOutOverwrite = 2;
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
-                               cudaStream_t s);
+                               int mode, cudaStream_t s);
+// out[d][r] += -(1/2pi) w psi[inv[r]][d] for r < n (w = w_sorted[inv[r]] or 1)
+cudaError_t launch_add_psi(int nd, int32_t n, const int32_t* inv, const double* w_sorted, const double* psi,
+                           double* out, int64_t ld_out, cudaStream_t s);
 
 // Oversampling (vp_upsample.cu). Charges q[pos][d] = w_pos (O f)[d][j], pos = inv[j]
 // the tree position of q-node j, fused with the interpolation; and the transposed

@@ -10,6 +10,8 @@
 // TwoProd/TwoSum. HBM traffic is one read of the values plus the outputs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "vp_ff.cuh"
 #include "vp_internal.h"
 
@@ -36,7 +38,7 @@ template <int ND>
 __global__ void __launch_bounds__(kGroupThreads)
     k_out_grouped(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
                   const double* __restrict__ psi, const float2* __restrict__ xf, int64_t ld_xf,
-                  double* __restrict__ out, int64_t ld_out)
+                  double* __restrict__ out, int64_t ld_out, int mode)
 {
     // [ND][smem_m] (smem_m even): lanes read consecutive pairs of columns of one density
     extern __shared__ __align__(16) float2 F[];
@@ -108,24 +110,43 @@ __global__ void __launch_bounds__(kGroupThreads)
                 }
             }
             if (lane == 0) {
-                if (psi) {
+                if (mode == kOutWithPsi) {
                     const int32_t ri = inv[r];
                     const double wv = w_sorted ? w_sorted[ri] : 1.0;
 #pragma unroll
                     for (int d = 0; d < ND; ++d)
                         out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
-                } else {  // accumulate onto out
+                } else if (mode == kOutAccumulate) {
 #pragma unroll
                     for (int d = 0; d < ND; ++d) out[d * ld_out + r] += ff::to_double(acc[0][d]);
+                } else {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) out[d * ld_out + r] = ff::to_double(acc[0][d]);
                 }
             }
         }
     }
 }
 
+// out[d][r] += -(1/2pi) w psi[inv[r]][d], w = w_sorted[inv[r]] or 1 (the smooth part added
+// to a correction computed on its own)
+template <int ND>
+__global__ void k_add_psi(int32_t n, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
+                          const double* __restrict__ psi, double* __restrict__ out, int64_t ld_out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * ND;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = (int32_t)(i / ND);
+        const int d = (int)(i - (int64_t)r * ND);
+        const int32_t ri = inv[r];
+        const double wv = w_sorted ? w_sorted[ri] : 1.0;
+        out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], out[d * ld_out + r]);
+    }
+}
+
 template <int ND>
 cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
-                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, cudaStream_t s)
+                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, int mode, cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_out_grouped<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kGroupSmemBytes);
@@ -139,7 +160,8 @@ cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const 
     const size_t bytes = (size_t)smem_m * ND * sizeof(float2);
     int blocks = A.ngroups < 152 * 16 ? A.ngroups : 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_out_grouped<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, xf, ld_xf, out, ld_out);
+    k_out_grouped<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, xf, ld_xf, out, ld_out,
+                                                          mode);
     return cudaGetLastError();
 }
 
@@ -157,15 +179,31 @@ cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, 
 
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
-                               cudaStream_t s)
+                               int mode, cudaStream_t s)
 {
     switch (nd) {
-        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
-        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
-        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
-        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, s);
+        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
+        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
+        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
+        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_add_psi(int nd, int32_t n, const int32_t* inv, const double* w_sorted, const double* psi,
+                           double* out, int64_t ld_out, cudaStream_t s)
+{
+    const int64_t total = (int64_t)nd * n;
+    if (total == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    switch (nd) {
+        case 1: k_add_psi<1><<<blocks, 256, 0, s>>>(n, inv, w_sorted, psi, out, ld_out); break;
+        case 2: k_add_psi<2><<<blocks, 256, 0, s>>>(n, inv, w_sorted, psi, out, ld_out); break;
+        case 4: k_add_psi<4><<<blocks, 256, 0, s>>>(n, inv, w_sorted, psi, out, ld_out); break;
+        case 8: k_add_psi<8><<<blocks, 256, 0, s>>>(n, inv, w_sorted, psi, out, ld_out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace vp
