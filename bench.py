@@ -41,9 +41,9 @@ P2P_FF_OPS_REVERSE = 14.0   # extra FP32 operations when one evaluation serves b
 # kernels on the medium disk case (profiles/*_disk_medium.md), scaled to a
 # launch by the units it processes; None once a kernel changes until re-profiled.
 PROFILED_TRAFFIC = {
-    "leaf": None,  # k_leaf_ff changed since its capture (symmetric near field): re-profile before filling
-    "m2l": (3.034e6 / 145118, "V-list pairs", "profiles/k_m2l_ff_disk_medium.md"),
-    "out": ((1298.684e6 + 5.309e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
+    "leaf": (15.155e6 / 88772380, "evaluated distances", "profiles/k_leaf_ff_sym_disk_medium.md"),
+    "m2l": (3.043e6 / 145118, "V-list pairs", "profiles/k_m2l_ff_disk_medium.md"),
+    "out": ((1298.547e6 + 5.140e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
 }
 
 
@@ -65,7 +65,7 @@ def roofline_models(info, prob, ndens=1):
         "leaf": {"bound": "alu", "kernel": "k_leaf_ff (float-float P2P + FP64 L2P/M2P)",
                  "work": (evals * P2P_FF_OPS_PER_PAIR + two_way * P2P_FF_OPS_REVERSE) * ndens, "unit": "T FP32-ops/s",
                  "peak": FP32_OPS_PEAK, "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz",
-                 "fp64_equiv_flop": (evals * P2P_FLOP_PER_PAIR + two_way * 7.0) * ndens, "units": info.p2p_pairs,
+                 "fp64_equiv_flop": (evals * P2P_FLOP_PER_PAIR + two_way * 7.0) * ndens, "units": evals,
                  "per_unit": f"{P2P_FF_OPS_PER_PAIR:.0f} FP32 ops per evaluated source-target distance, "
                              f"+{P2P_FF_OPS_REVERSE:.0f} when it serves both directions "
                              f"({evals} evaluations for {info.p2p_pairs} directed pairs)"},
