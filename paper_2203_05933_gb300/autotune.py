@@ -11,6 +11,9 @@ parameters and is left out of the tuning runs.
 
 Results are cached in a JSON file keyed by (geometry class, log2 of the point
 count, number of densities).
+
+tune_overlap picks, on a plan that carries its correction matrix, how much of
+each SM the correction product takes while it runs beside the FMM.
 """
 
 from __future__ import annotations
@@ -117,3 +120,16 @@ def tune(src_xy, w, tgt_xy, ndens: int = 1, geometry: str = "generic", root=None
         cache[key] = result
         _store_cache(path, cache)
     return dict(result, cached=False)
+
+
+def tune_overlap(plan, f, out, choices=(0, 1, 2, 4), steps: int = 5) -> dict:
+    """Time graph-replayed evaluations for each blocks-per-SM share of the
+    correction product run beside the FMM (0: after it), keep the fastest.
+    Returns {"blocks_per_sm", "table": [{"blocks_per_sm", "ms"}]}."""
+    table = []
+    for c in choices:
+        plan.set_overlap(c)
+        table.append({"blocks_per_sm": c, "ms": _time_eval(plan, f, out, steps)})
+    best = min(table, key=lambda r: r["ms"])
+    plan.set_overlap(best["blocks_per_sm"])
+    return {"blocks_per_sm": best["blocks_per_sm"], "table": table}

@@ -409,6 +409,8 @@ struct vp_plan_s {
     // the correction product runs beside the FMM on a low-priority stream
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int side_blocks = 0;  // grid of the product beside the FMM: a share of each SM (0: not beside)
+    int sms = 152;
     // staging for vp_eval_host
     double* stage = nullptr;
     size_t stage_cap = 0;
@@ -955,7 +957,14 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             in_pbox.insert(in_pbox.end(), rbox[(size_t)a].begin(), rbox[(size_t)a].end());
         }
     }
-    int32_t *d_sym_leaves = nullptr, *d_in_ptr = nullptr, *d_in_pptr = nullptr, *d_in_pbox = nullptr;
+    std::vector<int32_t> pt_leaf;
+    if (sym) {
+        pt_leaf.assign((size_t)n_tgt, 0);
+        for (int32_t b : B.leaves)
+            for (int32_t j = B.brt[2 * (size_t)b]; j < B.brt[2 * (size_t)b + 1]; ++j) pt_leaf[(size_t)j] = b;
+    }
+    int32_t *d_sym_leaves = nullptr, *d_in_ptr = nullptr, *d_in_pptr = nullptr, *d_in_pbox = nullptr,
+            *d_pt_leaf = nullptr;
     int64_t *d_sym_off = nullptr, *d_in_slot = nullptr;
     if (sym) {
         up(&d_sym_leaves, sym_leaves);
@@ -964,6 +973,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         up(&d_in_slot, in_slot);
         up(&d_in_pptr, in_pptr);
         up(&d_in_pbox, in_pbox);
+        up(&d_pt_leaf, pt_leaf);
     }
     up(&d_up, B.u_ptr);
     up(&d_ui, B.u_idx);
@@ -1035,6 +1045,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         int least = 0, greatest = 0;
         e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+        p->side_blocks = 2 * p->sms;
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     }
@@ -1078,6 +1090,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     dt.sym_in_slot = d_in_slot;
     dt.sym_in_pptr = d_in_pptr;
     dt.sym_in_pbox = d_in_pbox;
+    dt.sym_pt_leaf = d_pt_leaf;
     dt.sym_slots = nslots;
     DevTables& tb = p->tab;
     tb.H = d_tab + off[0];
@@ -1366,13 +1379,13 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         double* oc = out + (int64_t)d0 * ld_out;
         // Pi f does not depend on the FMM: outside phase timing it runs beside the
         // FMM on the plan's low-priority stream, and the smooth part is added after
-        const bool overlap = p->grouped && !p->timer.on;
+        const bool overlap = p->grouped && !p->timer.on && p->side_blocks > 0;
         if (overlap) {
             VP_CUDA(cudaEventRecord(p->ev_fork, s));
             VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
             VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, p->side));
             VP_CUDA(launch_out_grouped(nd, p->gfwd, nullptr, nullptr, nullptr, p->ws.xf, p->n_f, oc, ld_out,
-                                       kOutOverwrite, p->side));
+                                       kOutOverwrite, p->side_blocks, p->side));
             VP_CUDA(cudaEventRecord(p->ev_join, p->side));
             p->last_launches += 2;
         }
@@ -1391,7 +1404,7 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         } else if (p->grouped) {
             VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, s));
             VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f, oc, ld_out,
-                                       kOutWithPsi, s));
+                                       kOutWithPsi, 0, s));
             p->last_launches += 1;
         } else {
             VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc,
@@ -1492,13 +1505,13 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             const double* gc = g + (int64_t)d0 * ld_g;
             double* gfc0 = grad_f + (int64_t)d0 * ld_gf;
             // Pi^T g beside the transposed FMM (as in the forward evaluation)
-            const bool overlap = p->grouped && !p->ups;
+            const bool overlap = p->grouped && !p->ups && p->side_blocks > 0;
             if (overlap) {
                 VP_CUDA(cudaEventRecord(p->ev_fork, s));
                 VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
                 VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, p->side));
                 VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc0, ld_gf,
-                                           kOutOverwrite, p->side));
+                                           kOutOverwrite, p->side_blocks, p->side));
                 VP_CUDA(cudaEventRecord(p->ev_join, p->side));
             }
             VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
@@ -1513,7 +1526,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                 if (p->grouped) {
                     VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                     VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc, ld_gf,
-                                               kOutAccumulate, s));
+                                               kOutAccumulate, 0, s));
                 } else if (p->cptr) {
                     VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_f, nullptr, nullptr, nullptr, p->cptr, p->crow,
                                                p->cval, gc, ld_g, gfc, ld_gf, s));
@@ -1521,7 +1534,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             } else if (p->grouped) {
                 VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
                 VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
-                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, kOutWithPsi, s));
+                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, kOutWithPsi, 0, s));
             } else {
                 VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr,
                                            p->crow, p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
@@ -1639,6 +1652,17 @@ vp_status vp_plan_set_flags(vp_plan p, uint32_t flags)
         return fail(VP_ERR_ARG, "only VP_FLAG_TIMING and VP_FLAG_GRAPH can change after plan creation");
     p->flags = flags;
     p->timer.on = (flags & VP_FLAG_TIMING) != 0;
+    return VP_OK;
+}
+
+vp_status vp_plan_set_overlap(vp_plan p, int32_t blocks_per_sm)
+{
+    vp_status st = check_plan(p);
+    if (st != VP_OK) return st;
+    if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(VP_ERR_ARG, "blocks_per_sm outside 0..64");
+    p->side_blocks = p->side ? blocks_per_sm * p->sms : 0;
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old schedule
+    p->graphs.clear();
     return VP_OK;
 }
 

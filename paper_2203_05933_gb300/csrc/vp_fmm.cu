@@ -1440,12 +1440,24 @@ __global__ void k_sym_reduce(DevTree t, PassGeom g, const float2* __restrict__ s
                              double* __restrict__ psi)
 {
     constexpr int P1 = P + 1;
-    const int lane = threadIdx.x & 31;
-    for (int li = global_warp(); li < t.nleaf; li += num_warps()) {
-        const int A = t.leaves[li];
+    // one thread per evaluation point: neighbouring threads read neighbouring slots
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.n_eval; j += gridDim.x * blockDim.x) {
+        const int A = t.sym_pt_leaf[j];
         const int s0 = t.sym_in_ptr[A], s1 = t.sym_in_ptr[A + 1];
         if (s0 == s1) continue;
-        const int e0 = g.erng[2 * A], e1 = g.erng[2 * A + 1];
+        const int jl = j - g.erng[2 * A];
+        double acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+#pragma unroll 4
+        for (int k = s0; k < s1; ++k) {
+            const int64_t o = (t.sym_in_slot[k] + jl) * ND;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const float2 v = slots[o + d];
+                acc[d] += (double)v.x + (double)v.y;
+            }
+        }
         double cst[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) cst[d] = 0.0;
@@ -1458,22 +1470,8 @@ __global__ void k_sym_reduce(DevTree t, PassGeom g, const float2* __restrict__ s
                 cst[d] = fma(dl, (double)m0.x + (double)m0.y, cst[d]);
             }
         }
-        for (int j = lane; j < e1 - e0; j += 32) {
-            double acc[ND];
 #pragma unroll
-            for (int d = 0; d < ND; ++d) acc[d] = 0.0;
-#pragma unroll 4
-            for (int k = s0; k < s1; ++k) {
-                const int64_t o = (t.sym_in_slot[k] + j) * ND;
-#pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    const float2 v = slots[o + d];
-                    acc[d] += (double)v.x + (double)v.y;
-                }
-            }
-#pragma unroll
-            for (int d = 0; d < ND; ++d) psi[(int64_t)(e0 + j) * ND + d] += fma(0.5, acc[d], cst[d]);
-        }
+        for (int d = 0; d < ND; ++d) psi[(int64_t)j * ND + d] += fma(0.5, acc[d], cst[d]);
     }
 }
 
@@ -1544,7 +1542,8 @@ cudaError_t fmm_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, 
         if (sym) {
             k_leaf_ff<P, ND, true><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi,
                                                                    ws.work, ws.slots);
-            k_sym_reduce<P, ND><<<warp_blocks(t.nleaf), threads, 0, s>>>(t, g, ws.slots, ws.Mf, ws.psi);
+            const int rblocks = std::max(1, std::min((g.n_eval + 255) / 256, 152 * 32));
+            k_sym_reduce<P, ND><<<rblocks, 256, 0, s>>>(t, g, ws.slots, ws.Mf, ws.psi);
         } else {
             k_leaf_ff<P, ND, false><<<pblocks, kLeafThreads, 0, s>>>(t, g, ws.qf, ws.Mf, ws.Lf, tab.logtab, ws.psi,
                                                                     ws.work, nullptr);

@@ -52,6 +52,7 @@ struct DevTree {
     const int64_t* sym_in_slot = nullptr; // slot bases received by a leaf
     const int32_t* sym_in_pptr = nullptr; // per box: range of sym_in_pbox
     const int32_t* sym_in_pbox = nullptr; // leaves b that sent slots to a leaf
+    const int32_t* sym_pt_leaf = nullptr; // [points] the leaf of each point (tree order)
     int64_t sym_slots = 0;
 };
 
@@ -168,11 +169,12 @@ cudaError_t launch_grad_out(int nd, bool accumulate, int32_t n_tgt, const int32_
 // launch_out_adjoint accumulates when psi is NULL).
 cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, float2* xf, cudaStream_t s);
 // mode: kOutWithPsi (out = -(1/2pi) w psi + A x), kOutAccumulate (out += A x),
-// kOutOverwrite (out = A x).
+// kOutOverwrite (out = A x). max_blocks > 0 caps the grid (a product run beside other
+// kernels takes a share of each SM only).
 constexpr int kOutWithPsi = 0, kOutAccumulate = 1, kOutOverwrite = 2;
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
-                               int mode, cudaStream_t s);
+                               int mode, int max_blocks, cudaStream_t s);
 // out[d][r] += -(1/2pi) w psi[inv[r]][d] for r < n (w = w_sorted[inv[r]] or 1)
 cudaError_t launch_add_psi(int nd, int32_t n, const int32_t* inv, const double* w_sorted, const double* psi,
                            double* out, int64_t ld_out, cudaStream_t s);

@@ -146,7 +146,8 @@ __global__ void k_add_psi(int32_t n, const int32_t* __restrict__ inv, const doub
 
 template <int ND>
 cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
-                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, int mode, cudaStream_t s)
+                              const float2* xf, int64_t ld_xf, double* out, int64_t ld_out, int mode, int max_blocks,
+                              cudaStream_t s)
 {
     cudaError_t e = cudaFuncSetAttribute(k_out_grouped<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kGroupSmemBytes);
@@ -158,7 +159,8 @@ cudaError_t launch_grouped_nd(const DevGroupedCSR& A, const int32_t* inv, const 
     if (want < smem_m) smem_m = want;
     if (smem_m < 2) smem_m = 2;
     const size_t bytes = (size_t)smem_m * ND * sizeof(float2);
-    int blocks = A.ngroups < 152 * 16 ? A.ngroups : 152 * 16;
+    const int cap = max_blocks > 0 ? max_blocks : 152 * 16;
+    int blocks = A.ngroups < cap ? A.ngroups : cap;
     if (blocks < 1) blocks = 1;
     k_out_grouped<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, xf, ld_xf, out, ld_out,
                                                           mode);
@@ -179,13 +181,13 @@ cudaError_t launch_to_ff_rows(int nd, int32_t n, const double* x, int64_t ld_x, 
 
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
-                               int mode, cudaStream_t s)
+                               int mode, int max_blocks, cudaStream_t s)
 {
     switch (nd) {
-        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
-        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
-        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
-        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, s);
+        case 1: return launch_grouped_nd<1>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
+        case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
+        case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
+        case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -32,7 +32,8 @@ TREE_ARRAYS = {
 
 EXPORTED = [
     "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host",
-    "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_destroy", "vp_status_string", "vp_last_error", "vp_version",
+    "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_set_overlap", "vp_plan_destroy",
+    "vp_status_string", "vp_last_error", "vp_version",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
     "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
 ]
@@ -111,6 +112,7 @@ def _load():
                                 ctypes.POINTER(I32)],
         "vp_plan_destroy": [P],
         "vp_plan_set_flags": [P, ctypes.c_uint32],
+        "vp_plan_set_overlap": [P, I32],
         "vp_status_string": [I32],
         "vp_last_error": [],
         "vp_version": [],
@@ -460,6 +462,9 @@ class Plan:
 
     def set_flags(self, flags: int):
         vp_plan_set_flags(self.handle, flags)
+
+    def set_overlap(self, blocks_per_sm: int):
+        _check(_load().vp_plan_set_overlap(self.handle, blocks_per_sm), "vp_plan_set_overlap")
 
     def info(self) -> vp_plan_stats:
         return vp_plan_info(self.handle)

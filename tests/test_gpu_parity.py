@@ -384,3 +384,22 @@ def test_p16_float_float_matches_fp64(ndens):
     err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / inputs.normaliser(prob)[:, None]))
     print(f"P=16 float-float vs FP64, {ndens} densities: {err:.2e}")
     assert err <= 1e-12
+
+
+def test_correction_beside_fmm_matches_sequential():
+    # the correction product run beside the FMM (any share of the SMs) gives the
+    # same bits as the single fused kernel after the FMM, forward and adjoint
+    prob = inputs.disk_problem(base_level=4, fine_level=6, ndens=3)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=16, leaf=64, max_dens=2,
+                          flags=vp.VP_FLAG_GRAPH, root=prob.root)
+    f = torch.as_tensor(prob.f, device="cuda")
+    g = torch.as_tensor(np.random.default_rng(8).standard_normal((3, prob.n_tgt)), device="cuda")
+    res = []
+    for share in (0, 1, 2, 8):
+        plan.set_overlap(share)
+        res.append((plan.eval(f).cpu().numpy(), plan.adjoint(g)[0].cpu().numpy()))
+    for a in res[1:]:
+        assert np.array_equal(a[0], res[0][0]) and np.array_equal(a[1], res[0][1])
+    with pytest.raises(vp.VPError):
+        plan.set_overlap(-1)
+    plan.close()
