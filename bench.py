@@ -109,10 +109,33 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of the disk problem of one replica (each rank refines around its own bumps)."""
+    from paper_2203_05933_gb300 import inputs
+
+    return inputs.SEED_BASE + 2 + 1000 * rank
+
+
+def combine_ranks(t_dev: float, points: float, world: int, device) -> tuple[float, float]:
+    """Whole-job figures of a replica run: the slowest rank's device time (max) and
+    the points all ranks evaluated (sum). One process per GPU; any
+    torch.distributed backend (NCCL on the GPUs, gloo in the CPU tests)."""
+    if world <= 1:
+        return t_dev, points
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([t_dev], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([points], dtype=torch.float64, device=device)
+    dist.all_reduce(p)
+    return float(t.item()), float(p.item())
+
+
 def make_problem(args, rank):
     from paper_2203_05933_gb300 import inputs
 
-    seed = inputs.SEED_BASE + 2 + 1000 * rank
+    seed = rank_seed(rank)
     if args.size == "small":
         return inputs.disk_problem(base_level=5, fine_level=7, seed=seed, name="disk_small")
     if args.size == "medium":
@@ -317,15 +340,7 @@ def main():
     wall = time.perf_counter() - wall0
     t_dev = sum(step_s)
     launches_per_eval = plan.info().last_launches
-    if world > 1:
-        t = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_dev = float(t.item())
-        total_pts = torch.tensor([prob.n_tgt * prob.ndens * args.steps], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(total_pts)
-        pts = float(total_pts.item())
-    else:
-        pts = float(prob.n_tgt * prob.ndens * args.steps)
+    t_dev, pts = combine_ranks(t_dev, float(prob.n_tgt * prob.ndens * args.steps), world, dev)
     value = pts / t_dev / 1e6
 
     # per-phase CUDA-event times (same kernels launched one by one, timing events on the stream)
