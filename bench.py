@@ -404,13 +404,17 @@ def main():
                                     leaf=args.leaf, max_dens=1, flags=vp.VP_FLAG_GRAPH)
         mf = torch.as_tensor(np.concatenate([p.f for p in probs], axis=1), device=dev)
         mo = torch.empty((1, mplan.n_tgt), dtype=torch.float64, device=dev)
+        movl = None
+        if tuned is not None:
+            from paper_2203_05933_gb300 import autotune
+            movl = autotune.tune_overlap(mplan, mf, mo, choices=(0, 1, 2, 4, 8))
         mplan.eval(mf, out=mo)
         torch.cuda.synchronize()
         mt = timed(lambda: mplan.eval(mf, out=mo), max(3, args.steps // 3))
         mi = mplan.info()
         many = {"problems": len(probs), "n_tgt": int(mi.n_tgt), "nnz": int(mi.nnz), "levels": int(mi.n_levels),
                 "value": mi.n_tgt / float(np.mean(mt)) / 1e6, "unit": UNIT, "ms_per_step": float(np.mean(mt)) * 1e3,
-                "launches_per_eval": int(mi.last_launches), "graph": True}
+                "launches_per_eval": int(mi.last_launches), "graph": True, "overlap": movl}
         mplan.close()
         del mf, mo
 
@@ -525,6 +529,9 @@ def main():
         plan_s = time.perf_counter() - t0
         sf = torch.as_tensor(sprob.f, device=dev)
         so = torch.empty((1, sprob.n_tgt), dtype=torch.float64, device=dev)
+        sovl = None
+        if tuned is not None:
+            sovl = autotune.tune_overlap(splan, sf, so, choices=(0, 1, 2, 4, 8))
         for _ in range(max(3, args.warmup)):
             splan.eval(sf, out=so)
         torch.cuda.synchronize()
@@ -534,7 +541,7 @@ def main():
                 "triangles": sprob.meta["n_triangles"], "p_fmm": int(si.p_fmm), "leaf": int(si.leaf),
                 "p2p_pairs": int(si.p2p_pairs), "value": sprob.n_tgt / float(np.mean(st)) / 1e6, "unit": UNIT,
                 "ms_per_step": float(np.mean(st)) * 1e3, "input_gen_s": gen_s, "plan_s": plan_s,
-                "launches_per_eval": int(si.last_launches), "graph": True,
+                "launches_per_eval": int(si.last_launches), "graph": True, "overlap": sovl,
                 "autotune": None if stune is None else {
                     "table": [{k: r[k] for k in ("p_fmm", "leaf", "err", "ms")} for r in stune["table"]],
                     "tuning_s": stune["tuning_s"]}}

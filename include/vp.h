@@ -264,12 +264,13 @@ vp_status vp_plan_phase_times(vp_plan plan, int32_t cap, const char** names,
 /* Change the run-time flags of a plan (VP_FLAG_TIMING, VP_FLAG_GRAPH); the other
  * bits must equal those given at creation (VP_ERR_ARG otherwise). */
 vp_status vp_plan_set_flags(vp_plan plan, uint32_t flags);
-/* With a correction matrix, vp_eval and vp_eval_adjoint run the correction product
- * beside the FMM on a plan-owned low-priority stream (captured graphs: the FMM
- * stream has the highest priority), then add the smooth part. blocks_per_sm sets
- * the product's grid, a share of each SM (default 2); 0 runs the product after the
- * FMM in one kernel instead. Drops captured graphs. Phase timing always runs the
- * product after the FMM. */
+/* With a correction matrix and blocks_per_sm > 0, vp_eval and vp_eval_adjoint run
+ * the correction product beside the FMM on a plan-owned low-priority stream
+ * (captured graphs: the FMM stream has the highest priority), with a grid of
+ * blocks_per_sm blocks on every SM, then add the smooth part. 0 (the default) runs
+ * the product after the FMM in one kernel. The best share depends on the balance
+ * of the two (autotune.tune_overlap measures it). Drops captured graphs. Phase
+ * timing always runs the product after the FMM. */
 vp_status vp_plan_set_overlap(vp_plan plan, int32_t blocks_per_sm);
 
 vp_status vp_plan_destroy(vp_plan plan);

@@ -1046,7 +1046,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, least);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-        p->side_blocks = 2 * p->sms;
+        p->side_blocks = 0;  // the product after the FMM until vp_plan_set_overlap asks otherwise
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
     }
