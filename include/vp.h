@@ -71,11 +71,26 @@ typedef struct {
     int32_t max_level;  /* deepest tree level (0 -> 24; at most 27)                          */
     int32_t max_dens;   /* densities processed per pass; workspace is sized for it (0 -> 1)  */
     int32_t flags;      /* VP_FLAG_* bits                                                    */
-    int32_t reserved;
+    int32_t kernel;     /* VP_KERNEL_LAPLACE (0, default) or VP_KERNEL_MHELMHOLTZ           */
     double root[3];     /* enclosing square (x0, y0, side); side <= 0 -> smallest square
                            around all points. Every point must satisfy
                            x0 <= x < x0 + side and y0 <= y < y0 + side.                      */
+    double lambda;      /* modified-Helmholtz parameter (> 0; VP_KERNEL_MHELMHOLTZ only)     */
 } vp_options;
+
+/* Green functions (arXiv 2203.05933, Sec. 2):
+ *   VP_KERNEL_LAPLACE      G(r, r0) = -(1/2pi) log|r - r0|                (L = -Delta)
+ *   VP_KERNEL_MHELMHOLTZ   G(r, r0) = (lambda^2/2pi) K0(lambda |r - r0|)  (L = -Delta + lambda^2)
+ * The prefactor lambda^2/2pi is the one the paper states; V then solves
+ * (-Delta + lambda^2) V = lambda^2 f. Modified-Helmholtz plans come from
+ * vp_plan_create only, evaluate one density per pass in FP64 (expansions, near
+ * field; log r from the float-float table log), support vp_eval, vp_eval_host and
+ * the grad_f part of vp_eval_adjoint (the kernel is symmetric), and reject
+ * grad_tgt with VP_ERR_UNSUPPORTED. Plan creation fails with VP_ERR_ARG if
+ * lambda * (box half side) puts the expansion tables out of FP64 range (roughly
+ * below 1e-4 for p_fmm = 30, or above a few hundred). */
+#define VP_KERNEL_LAPLACE 0
+#define VP_KERNEL_MHELMHOLTZ 1
 
 /* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
 #define VP_FLAG_TIMING 1u
@@ -274,6 +289,14 @@ vp_status vp_plan_set_flags(vp_plan plan, uint32_t flags);
 vp_status vp_plan_set_overlap(vp_plan plan, int32_t blocks_per_sm);
 
 vp_status vp_plan_destroy(vp_plan plan);
+
+/* G(r) of `kernel` (lambda as in vp_options) at n distances r[i] > 0, on the
+ * host, with the Bessel routines the plans use for their operator tables
+ * (K0 by its ascending series for lambda r <= 2, by the trapezoidal rule on its
+ * integral representation above; relative error about 1e-15). r, g: host,
+ * [n]. Errors: VP_ERR_ARG (NULL pointer, n < 0, r[i] <= 0, bad kernel or
+ * lambda). */
+vp_status vp_green_eval_host(int32_t kernel, double lambda, int64_t n, const double* r, double* g);
 
 /* Static description of a status code; never NULL. */
 const char* vp_status_string(int32_t status);

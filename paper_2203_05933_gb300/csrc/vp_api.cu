@@ -417,6 +417,8 @@ struct vp_plan_s {
     int64_t p2p_pairs = 0;
     int64_t p2p_evals = 0;      // distances evaluated by the symmetric near field
     int64_t last_launches = 0;
+    int kernel = VP_KERNEL_LAPLACE;
+    DevMH mh;                   // modified-Helmholtz tables (kernel == VP_KERNEL_MHELMHOLTZ)
     bool alive = true;
 
     template <typename T>
@@ -902,7 +904,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_leaves, B.leaves);
     // symmetric near field when the charge points of both passes are the evaluation
     // points (same coordinates, same tree order) and the U lists are symmetric
-    bool sym = !(p->flags & VP_FLAG_FP64) && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
+    bool sym = p->kernel == VP_KERNEL_LAPLACE && !(p->flags & VP_FLAG_FP64) && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
     if (sym) {
         for (int32_t b : B.leaves) {
             for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1] && sym; ++e2) {
@@ -1131,6 +1133,64 @@ vp_status plan_options(const vp_options* opt_in, vp_options& opt, int& P, int& l
     max_dens = opt.max_dens <= 0 ? 1 : opt.max_dens;
     if (leaf < 1 || leaf > 4096) return fail(VP_ERR_ARG, "leaf outside [1, 4096]");
     if (max_level < 1 || max_level >= kCoordBits) return fail(VP_ERR_ARG, "max_level outside [1, 27]");
+    if (opt.kernel != VP_KERNEL_LAPLACE && opt.kernel != VP_KERNEL_MHELMHOLTZ)
+        return fail(VP_ERR_ARG, "unknown kernel");
+    if (opt.kernel == VP_KERNEL_MHELMHOLTZ && !(opt.lambda > 0.0 && std::isfinite(opt.lambda)))
+        return fail(VP_ERR_ARG, "the modified-Helmholtz kernel needs a finite lambda > 0");
+    if (opt.kernel == VP_KERNEL_MHELMHOLTZ && (opt.flags & VP_FLAG_FP64))
+        return fail(VP_ERR_ARG, "VP_FLAG_FP64 applies to the Laplace kernel only");
+    return VP_OK;
+}
+
+// Operator tables of the modified-Helmholtz kernel for the plan's tree: one
+// half side per level (a single tree: every box of a level has the same size)
+// and a bound on every near-field distance.
+vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
+{
+    const int nl = B.n_levels;
+    std::vector<double> R((size_t)std::max(nl, 1), 0.0);
+    for (size_t b = 0; b < B.level.size(); ++b) {
+        double& r = R[(size_t)B.level[b]];
+        if (r == 0.0) r = B.radius[b];
+        else if (r != B.radius[b]) return fail(VP_ERR_UNSUPPORTED, "modified-Helmholtz plans need one tree");
+    }
+    for (int l = 1; l < nl; ++l)
+        if (R[(size_t)l] == 0.0) R[(size_t)l] = 0.5 * R[(size_t)l - 1];
+    double dmax = 0.0;
+    for (int32_t b : B.leaves)
+        for (int32_t e = B.u_ptr[(size_t)b]; e < B.u_ptr[(size_t)b + 1]; ++e) {
+            const int32_t a = B.u_idx[(size_t)e];
+            const double dx = B.center[2 * (size_t)a] - B.center[2 * (size_t)b];
+            const double dy = B.center[2 * (size_t)a + 1] - B.center[2 * (size_t)b + 1];
+            dmax = std::max(dmax, std::sqrt(dx * dx + dy * dy) + std::sqrt(2.0) * (B.radius[(size_t)a] + B.radius[(size_t)b]));
+        }
+    MhTables T;
+    const std::string err = make_mh_tables(p->P, lambda, R, dmax, T);
+    if (!err.empty()) return fail(VP_ERR_ARG, err);
+    cudaError_t e = cudaSuccess;
+    double *d_spow = nullptr, *d_na = nullptr, *d_nb = nullptr;
+    double2 *d_tm = nullptr, *d_tl = nullptr, *d_tv = nullptr;
+    if (e == cudaSuccess) e = p->upload(&d_spow, T.spow, s);
+    if (e == cudaSuccess) e = p->upload(&d_na, T.near_a, s);
+    if (e == cudaSuccess) e = p->upload(&d_nb, T.near_b, s);
+    if (e == cudaSuccess) e = p->upload(&d_tm, T.Tm, s);
+    if (e == cudaSuccess) e = p->upload(&d_tl, T.Tl, s);
+    if (e == cudaSuccess) e = p->upload(&d_tv, T.Tv, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
+    DevMH& m = p->mh;
+    m.lambda = lambda;
+    m.lam2_4 = 0.25 * lambda * lambda;
+    m.c0 = std::log(0.5 * lambda) + 0.577215664901532860606512090082402431;
+    m.psi_scale = -lambda * lambda;
+    m.inv_fact_P = T.inv_fact_P;
+    m.near_deg = T.near_deg;
+    m.near_a = d_na;
+    m.near_b = d_nb;
+    m.spow = d_spow;
+    m.Tm = d_tm;
+    m.Tl = d_tl;
+    m.Tv = d_tv;
     return VP_OK;
 }
 
@@ -1142,7 +1202,8 @@ vp_plan new_plan(const vp_options& opt, int P, int leaf, int max_dens)
     p->P = P;
     p->leaf = leaf;
     p->max_dens = max_dens;
-    p->nd_cap = chunk_for(max_dens, 8);
+    p->kernel = opt.kernel;
+    p->nd_cap = opt.kernel == VP_KERNEL_MHELMHOLTZ ? 1 : chunk_for(max_dens, 8);
     p->flags = (uint32_t)opt.flags;
     p->timer.on = (p->flags & VP_FLAG_TIMING) != 0;
     return p;
@@ -1177,6 +1238,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     vp_plan p = new_plan(opt, P, leaf, max_dens);
     if (!p) return fail(VP_ERR_OOM, "host allocation");
     st = finalize(p, B, P, s);
+    if (st == VP_OK && p->kernel == VP_KERNEL_MHELMHOLTZ) st = setup_mh(p, B, opt.lambda, s);
     if (st != VP_OK) {
         delete p;
         return st;
@@ -1200,6 +1262,8 @@ vp_status vp_plan_create_many(vp_plan* out, int32_t nprob, const int64_t* n_src,
     int P, leaf, max_level, max_dens;
     vp_status st = plan_options(opt_in, opt, P, leaf, max_level, max_dens);
     if (st != VP_OK) return st;
+    if (opt.kernel != VP_KERNEL_LAPLACE)
+        return fail(VP_ERR_UNSUPPORTED, "the modified-Helmholtz kernel is available through vp_plan_create only");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<Built> parts((size_t)nprob);
     int64_t tot_s = 0, tot_t = 0;
@@ -1298,6 +1362,8 @@ vp_status vp_plan_create_upsampled(vp_plan* out, int64_t n_src, const double* sr
     int P, leaf, max_level, max_dens;
     vp_status st = plan_options(opt_in, opt, P, leaf, max_level, max_dens);
     if (st != VP_OK) return st;
+    if (opt.kernel != VP_KERNEL_LAPLACE)
+        return fail(VP_ERR_UNSUPPORTED, "the modified-Helmholtz kernel is available through vp_plan_create only");
     cudaStream_t s = (cudaStream_t)stream;
     ProblemIn in;
     st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s, n_f);
@@ -1359,6 +1425,13 @@ extern "C" {
 
 namespace {
 
+// The FMM of one density chunk for the plan's kernel (psi in tree order).
+cudaError_t run_fmm(vp_plan p, int nd, const PassGeom& g, bool gradient, PhaseTimer* tm, cudaStream_t s)
+{
+    if (p->kernel == VP_KERNEL_MHELMHOLTZ) return launch_fmm_mhelm(p->P, p->dt, p->mh, p->tab.logtab, g, p->ws, tm, s);
+    return launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, gradient, use_fp64(p), tm, s);
+}
+
 // The launch sequence of one evaluation, enqueued on s.
 vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, double* out, int64_t ld_out,
                        cudaStream_t s)
@@ -1373,8 +1446,11 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         // level from level 2 up), M2L, L2L per level from level 3 down, leaf (+ slot
         // reduction), output
         const bool ffp = !use_fp64(p);
-        p->last_launches += 5 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
-                            (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);
+        if (p->kernel == VP_KERNEL_MHELMHOLTZ)
+            p->last_launches += 2 + mhelm_launches(p->dt.nlevels);
+        else
+            p->last_launches += 5 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
+                                (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
         double* oc = out + (int64_t)d0 * ld_out;
         // Pi f does not depend on the FMM: outside phase timing it runs beside the
@@ -1395,8 +1471,7 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         else
             VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf, s));
         p->timer.end(id);
-        VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, false, use_fp64(p),
-                                     p->timer.on ? &p->timer : nullptr, s));
+        VP_CUDA(run_fmm(p, nd, g, false, p->timer.on ? &p->timer : nullptr, s));
         id = p->timer.begin("out");
         if (overlap) {
             VP_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
@@ -1495,6 +1570,8 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
         if ((p->n_tgt > 0 && !g) || ld_g < p->n_tgt || ld_gf < p->n_f)
             return fail(VP_ERR_ARG, "grad_f needs g with valid leading dimensions");
     }
+    if (grad_tgt && p->kernel != VP_KERNEL_LAPLACE)
+        return fail(VP_ERR_UNSUPPORTED, "target gradients are available for the Laplace kernel only");
     if (ndens == 0) return VP_OK;
     p->timer.stream = s;
     p->timer.used = 0;
@@ -1515,7 +1592,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                 VP_CUDA(cudaEventRecord(p->ev_join, p->side));
             }
             VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
-            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gg, p->ws, false, use_fp64(p), nullptr, s));
+            VP_CUDA(run_fmm(p, nd, gg, false, nullptr, s));
             if (overlap) {
                 VP_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
                 VP_CUDA(launch_add_psi(nd, (int32_t)p->n_f, p->src_inv, p->w_sorted, p->ws.psi, gfc0, ld_gf, s));
@@ -1552,7 +1629,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             else
                 VP_CUDA(launch_charges(nd, (int32_t)p->n_src, p->src_perm, p->w_sorted, fc, ld_f, p->ws.q, p->ws.qf,
                                        s));
-            VP_CUDA(launch_fmm_potential(p->P, nd, p->dt, p->tab, gf, p->ws, true, use_fp64(p), nullptr, s));
+            VP_CUDA(run_fmm(p, nd, gf, true, nullptr, s));
             VP_CUDA(launch_grad_out(nd, d0 > 0, (int32_t)p->n_tgt, p->tgt_perm, p->ws.psi, g + (int64_t)d0 * ld_g,
                                     ld_g, grad_tgt, s));
             d0 += nd;
@@ -1663,6 +1740,20 @@ vp_status vp_plan_set_overlap(vp_plan p, int32_t blocks_per_sm)
     p->side_blocks = p->side ? blocks_per_sm * p->sms : 0;
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);  // captured with the old schedule
     p->graphs.clear();
+    return VP_OK;
+}
+
+vp_status vp_green_eval_host(int32_t kernel, double lambda, int64_t n, const double* r, double* g)
+{
+    if (n < 0 || (n > 0 && (!r || !g))) return fail(VP_ERR_ARG, "NULL pointer or n < 0");
+    if (kernel != VP_KERNEL_LAPLACE && kernel != VP_KERNEL_MHELMHOLTZ) return fail(VP_ERR_ARG, "unknown kernel");
+    if (kernel == VP_KERNEL_MHELMHOLTZ && !(lambda > 0.0 && std::isfinite(lambda)))
+        return fail(VP_ERR_ARG, "the modified-Helmholtz kernel needs a finite lambda > 0");
+    for (int64_t i = 0; i < n; ++i)
+        if (!(r[i] > 0.0)) return fail(VP_ERR_ARG, "distances must be > 0");
+    for (int64_t i = 0; i < n; ++i)
+        g[i] = kernel == VP_KERNEL_LAPLACE ? -0.159154943091895335768883763372514362 * std::log(r[i])
+                                           : green_mhelm_host(lambda, r[i]);
     return VP_OK;
 }
 

@@ -119,6 +119,30 @@ struct DevUpsample {
     const double* mats = nullptr;
 };
 
+// Modified-Helmholtz kernel (vp_mhelm.cu): per-level operator tables and the
+// near-field series. sigma_l = lambda R_l, R_l the half side of level-l boxes.
+struct DevMH {
+    double lambda = 0.0;
+    double lam2_4 = 0.0;             // lambda^2 / 4
+    double c0 = 0.0;                 // log(lambda / 2) + Euler's gamma
+    double psi_scale = 0.0;          // -lambda^2 (psi = -lambda^2 sum q K0)
+    double inv_fact_P = 0.0;         // 1 / P!
+    int near_deg = 0;                // near-field series terms k = 0..near_deg
+    const double* near_a = nullptr;  // [near_deg + 1] 1/(k!)^2
+    const double* near_b = nullptr;  // [near_deg + 1] H_k/(k!)^2
+    const double* spow = nullptr;    // [nlevels][P1] sigma_l^k
+    const double2* Tm = nullptr;     // [nlevels][4][2P+1][P1] M2M into a parent of level l
+    const double2* Tl = nullptr;     // [nlevels][4][2P+1][P1] L2L into a child of level l
+    const double2* Tv = nullptr;     // [nlevels][49][3P+1] M2L, K_n(v) for n = -2P..P
+};
+
+struct MhTables {
+    std::vector<double> spow, near_a, near_b;
+    std::vector<double2> Tm, Tl, Tv;
+    double inv_fact_P = 0.0;
+    int near_deg = 0;
+};
+
 struct Workspace {
     double* q = nullptr;      // [max(n_src, n_tgt)][ND] charges, tree order
     float2* qf = nullptr;     // [max(n_src, n_tgt)][ND] the same charges as hi/lo float pairs
@@ -186,6 +210,15 @@ cudaError_t launch_ups_charges(int nd, const DevUpsample& u, const int32_t* inv,
                                const double* f, int64_t ld_f, double* q, float2* qf, cudaStream_t s);
 cudaError_t launch_ups_adjoint(int nd, const DevUpsample& u, const int32_t* inv, const double* w_sorted,
                                const double* psi, double* out, int64_t ld_out, cudaStream_t s);
+
+// Modified-Helmholtz FMM (vp_mhelm.cu): one density per pass; psi = -lambda^2 sum q K0.
+cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g,
+                             Workspace& ws, PhaseTimer* timer, cudaStream_t s);
+int64_t mhelm_launches(int nlevels);
+// Host tables for half sides R_level[l]; near_dmax bounds every near-field distance.
+// Returns an error message, or "" on success.
+std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level, double near_dmax, MhTables& T);
+double green_mhelm_host(double lambda, double r);
 
 bool p_supported(int P);
 

@@ -1,0 +1,583 @@
+// FMM for the modified-Helmholtz kernel G(r, r0) = (lambda^2/2pi) K0(lambda |r - r0|)
+// (arXiv 2203.05933, Sec. 2: the Green function of L = -Delta + lambda^2; the
+// experiment of Sec. 5 with lambda^2 = 100 on the unit disk), in FP64 on sm_103a.
+//
+// Complex notation: for w = rho e^{i theta}, I_n(w) = I_n(lambda rho) e^{i n theta}
+// and K_n(w) = K_n(lambda rho) e^{i n theta} (n of either sign; I_{-n}(w) and
+// K_{-n}(w) are the conjugates). Graf's addition theorem gives
+//   K0(lambda |z - z'|) = sum_n K_n(z - c) conj(I_n(z' - c))   |z - c| > |z' - c|
+//                       = sum_n I_n(z - c) conj(K_n(z' - c))   |z - c| < |z' - c|
+//   I_n(u + v) = sum_k I_{n-k}(u) I_k(v)
+//   K_n(u + v) = sum_k (-1)^k K_{n-k}(v) I_k(u)                |u| < |v|
+// so that, with real charges (coefficients of -n are the conjugates of those of n),
+//   multipole  M'_n = sum_j q_j conj(I_n(z_j - c))           phi = sum_n K_n(z - c) M'_n
+//   local      L'_m (P2L: sum_j q_j conj(K_m(z_j - c)))      phi = sum_m I_m(z - c) L'_m
+//   M2M        M'_p,n = sum_j M'_c,j conj(I_{n-j}(d))         d = c_child - c_parent
+//   M2L        L'_m = (-1)^m sum_k K_{k-m}(v) M'_k            v = c_target - c_source
+//   L2L        L'_c,k = sum_m L'_p,m I_{m-k}(d)
+// Stored coefficients are scaled by sigma = lambda R (R the box half side):
+// M_n = M'_n / sigma^n, L_m = L'_m sigma^m, n, m = 0..P, which keeps them O(1)
+// for every box size. Per level the operators are fixed (four child quadrants,
+// 49 source-box offsets), so M2M, L2L and M2L read plan-time tables.
+//
+// Near field (direct sum over the U list): with y = lambda^2 r^2 / 4,
+//   K0 = I0(y) (-log(r^2)/2 - log(lambda/2) - gamma) + sum_{k>=1} H_k y^k / (k!)^2,
+//   I0(y) = sum_k y^k / (k!)^2 (Abramowitz & Stegun 9.6.13), H_k the harmonic numbers,
+// both series summed to the degree the plan's largest near-field distance needs
+// (y <= 1); log r^2 comes from the float-float table log of the Laplace kernels
+// (about 1e-12 absolute), everything else is FP64. Pairs with y > 1 take the
+// integral representation of K0 (vp_bessel.cuh).
+//
+// psi convention: psi = -lambda^2 sum_j q_j K0(lambda |z - z_j|), so that the
+// output kernels' V = -(1/2pi) psi (+ Pi f) give the modified-Helmholtz potential.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "vp_bessel.cuh"
+#include "vp_ff.cuh"
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kMhChunk = 16;        // charges staged per step in P2M / P2L
+constexpr int kMhLeafThreads = 128; // one target per thread in the leaf kernel
+constexpr int kMaxNearTerms = 16;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// a * b + c
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
+
+__device__ __forceinline__ int gwarp() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int nwarps() { return (int)((gridDim.x * blockDim.x) >> 5); }
+
+int wblocks(int64_t nwork)
+{
+    int64_t b = (nwork + kWarps - 1) / kWarps;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+// ----------------------------------------------------------------------------
+// P2M, one warp per leaf: M_n = sum_j q_j conj(u_j)^n h_n(y_j), u = (z - c)/(2R),
+// y = sigma^2 |u|^2 (= lambda^2 rho^2 / 4); h_P, h_{P+1} by their series, the
+// others by the downward recurrence.
+template <int P>
+__global__ void __launch_bounds__(kWarps * 32)
+    k_p2m_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, double2* __restrict__ M)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 pw[kWarps][kMhChunk][P1];
+    __shared__ double qs[kWarps][kMhChunk];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
+        const int b = t.leaves[li];
+        const int s0 = g.crng[2 * b], s1 = g.crng[2 * b + 1];
+        const double2 c = t.center[b];
+        const double inv2R = 0.5 / t.radius[b];
+        const double sig = mh.spow[t.level[b] * P1 + 1];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int base = s0; base < s1; base += kMhChunk) {
+            const int n = min(kMhChunk, s1 - base);
+            if (lane < n) {
+                const double2 z = g.cxy[base + lane];
+                const double2 u = make_double2((z.x - c.x) * inv2R, -(z.y - c.y) * inv2R);  // conj(u)
+                const double y = sig * sig * (u.x * u.x + u.y * u.y);
+                double hm, hm1;
+                bessel::h_series2(P, y, mh.inv_fact_P, hm, hm1);
+                pw[wb][lane][P].x = hm;
+                for (int m = P; m >= 1; --m) {
+                    const double hp = fma((double)m, hm, y * hm1);
+                    hm1 = hm;
+                    hm = hp;
+                    pw[wb][lane][m - 1].x = hp;
+                }
+                double2 p = make_double2(1.0, 0.0);
+                for (int m = 0; m <= P; ++m) {
+                    const double h = pw[wb][lane][m].x;
+                    pw[wb][lane][m] = make_double2(p.x * h, p.y * h);
+                    p = cmul(p, u);
+                }
+                qs[wb][lane] = q[base + lane];
+            }
+            __syncwarp();
+            if (lane <= P) {
+                for (int j = 0; j < n; ++j) {
+                    const double2 v = pw[wb][j][lane];
+                    acc.x = fma(qs[wb][j], v.x, acc.x);
+                    acc.y = fma(qs[wb][j], v.y, acc.y);
+                }
+            }
+            __syncwarp();
+        }
+        if (lane <= P) M[(int64_t)b * P1 + lane] = acc;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// M2M into the non-leaf boxes of level l, one warp per parent; lane n owns M_n.
+template <int P>
+__global__ void __launch_bounds__(kWarps * 32)
+    k_m2m_mh(DevTree t, DevMH mh, int l, int b0, int b1, double2* __restrict__ M)
+{
+    constexpr int P1 = P + 1, NJ = 2 * P + 1;
+    __shared__ double2 Ms[kWarps][P1];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int b = b0 + gwarp(); b < b1; b += nwarps()) {
+        if (t.is_leaf[b]) continue;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = 0; c < 4; ++c) {
+            const int ch = t.child[4 * b + c];
+            if (ch < 0) continue;
+            if (lane <= P) Ms[wb][lane] = M[(int64_t)ch * P1 + lane];
+            __syncwarp();
+            const int cq = (t.ixy[2 * ch] & 1) | ((t.ixy[2 * ch + 1] & 1) << 1);
+            if (lane <= P) {
+                const double2* T = mh.Tm + ((int64_t)(l * 4 + cq) * NJ) * P1 + lane;
+                for (int j = -P; j <= P; ++j) {
+                    const double2 m = j >= 0 ? Ms[wb][j] : conj2(Ms[wb][-j]);
+                    acc = cfma(T[(j + P) * P1], m, acc);
+                }
+            }
+            __syncwarp();
+        }
+        if (lane <= P) M[(int64_t)b * P1 + lane] = acc;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// L2L from the parents into the boxes of level l, one warp per child; lane k owns L_k.
+template <int P>
+__global__ void __launch_bounds__(kWarps * 32)
+    k_l2l_mh(DevTree t, DevMH mh, int l, int b0, int b1, double2* __restrict__ L)
+{
+    constexpr int P1 = P + 1, NJ = 2 * P + 1;
+    __shared__ double2 Ls[kWarps][P1];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int b = b0 + gwarp(); b < b1; b += nwarps()) {
+        const int p = t.parent[b];
+        if (lane <= P) Ls[wb][lane] = L[(int64_t)p * P1 + lane];
+        __syncwarp();
+        const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
+        if (lane <= P) {
+            const double2* T = mh.Tl + ((int64_t)(l * 4 + cq) * NJ) * P1 + lane;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int m = -P; m <= P; ++m) {
+                const double2 v = m >= 0 ? Ls[wb][m] : conj2(Ls[wb][-m]);
+                acc = cfma(T[(m + P) * P1], v, acc);
+            }
+            const int64_t i = (int64_t)b * P1 + lane;
+            const double2 o = L[i];
+            L[i] = make_double2(o.x + acc.x, o.y + acc.y);
+        }
+        __syncwarp();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// M2L over the V list plus P2L over the X list, one warp per box; lane m owns
+// L_m. Every box's L is written (zeros when both lists are empty).
+template <int P>
+__global__ void __launch_bounds__(kWarps * 32)
+    k_m2l_mh(DevTree t, DevMH mh, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
+             const double* __restrict__ q)
+{
+    constexpr int P1 = P + 1, NT = 3 * P + 1;
+    __shared__ double2 Ms[kWarps][P1];
+    __shared__ double2 Ts[kWarps][NT];
+    __shared__ double2 pw[kWarps][kMhChunk][P1];
+    __shared__ double qs[kWarps][kMhChunk];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int b = gwarp(); b < t.nbox; b += nwarps()) {
+        const int lev = t.level[b];
+        const double* sp = mh.spow + lev * P1;
+        const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
+        double2 vacc = make_double2(0.0, 0.0);
+        const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
+        for (int e = v0; e < v1; ++e) {
+            const int C = t.v_idx[e];
+            const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+            if (lane <= P) {
+                const double2 m = M[(int64_t)C * P1 + lane];
+                Ms[wb][lane] = make_double2(m.x * sp[lane], m.y * sp[lane]);  // M'_k = sigma^k M_k
+            }
+            const double2* T = mh.Tv + ((int64_t)lev * 49 + o) * NT;
+            for (int i = lane; i < NT; i += 32) Ts[wb][i] = T[i];
+            __syncwarp();
+            if (lane <= P) {
+                double2 s = make_double2(0.0, 0.0);
+                for (int k = 0; k <= P; ++k) s = cfma(Ts[wb][k - lane + 2 * P], Ms[wb][k], s);
+                for (int k = 1; k <= P; ++k) s = cfma(Ts[wb][-k - lane + 2 * P], conj2(Ms[wb][k]), s);
+                if (lane & 1) s = make_double2(-s.x, -s.y);
+                vacc = make_double2(vacc.x + s.x, vacc.y + s.y);
+            }
+            __syncwarp();
+        }
+        double2 lacc = make_double2(0.0, 0.0);
+        if (lane <= P) lacc = make_double2(vacc.x * sp[lane], vacc.y * sp[lane]);
+        const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
+        if (x1 > x0) {
+            const double2 c = t.center[b];
+            const double sig = sp[1];
+            for (int e = x0; e < x1; ++e) {
+                const int C = t.x_idx[e];
+                const int s0 = g.crng[2 * C], s1 = g.crng[2 * C + 1];
+                for (int base = s0; base < s1; base += kMhChunk) {
+                    const int n = min(kMhChunk, s1 - base);
+                    if (lane < n) {
+                        // sigma^n K_n(lambda rho) e^{-i n theta} of this charge about c
+                        const double2 z = g.cxy[base + lane];
+                        const double dx = z.x - c.x, dy = z.y - c.y;
+                        const double rho = sqrt(dx * dx + dy * dy);
+                        const double x = mh.lambda * rho;
+                        double k0, k1;
+                        bessel::k01(x, k0, k1);
+                        const double2 ph = make_double2(dx / rho, -dy / rho);
+                        double ka = k0, kb = sig * k1;
+                        const double s2 = sig * sig, r = 2.0 * sig / x;
+                        pw[wb][lane][0] = make_double2(ka, 0.0);
+                        double2 p = ph;
+                        pw[wb][lane][1] = make_double2(kb * p.x, kb * p.y);
+                        for (int m = 1; m < P; ++m) {
+                            const double kc = fma(s2, ka, (double)m * r * kb);
+                            ka = kb;
+                            kb = kc;
+                            p = cmul(p, ph);
+                            pw[wb][lane][m + 1] = make_double2(kb * p.x, kb * p.y);
+                        }
+                        qs[wb][lane] = q[base + lane];
+                    }
+                    __syncwarp();
+                    if (lane <= P) {
+                        for (int j = 0; j < n; ++j) {
+                            const double2 v = pw[wb][j][lane];
+                            lacc.x = fma(qs[wb][j], v.x, lacc.x);
+                            lacc.y = fma(qs[wb][j], v.y, lacc.y);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (lane <= P) L[(int64_t)b * P1 + lane] = lacc;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Per leaf: L2P, M2P over the W list and the direct sum over the U list; one
+// block per leaf, one target per thread.
+template <int P>
+__global__ void __launch_bounds__(kMhLeafThreads)
+    k_leaf_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
+              const double2* __restrict__ L, const float4* __restrict__ logtab, double* __restrict__ psi)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 Cs[P1];
+    __shared__ double2 sxy[kMhLeafThreads];
+    __shared__ double sq[kMhLeafThreads];
+    __shared__ double na[kMaxNearTerms], nb[kMaxNearTerms];
+    const int tid = threadIdx.x;
+    const int deg = mh.near_deg;
+    if (tid <= deg) {
+        na[tid] = mh.near_a[tid];
+        nb[tid] = mh.near_b[tid];
+    }
+    for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
+        const int b = t.leaves[li];
+        const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
+        if (e0 == e1) continue;
+        const double2 cb = t.center[b];
+        const double Rb = t.radius[b];
+        const double sig = mh.spow[t.level[b] * P1 + 1];
+        const double side = 2.0 * Rb;
+        const double inv_side2 = 1.0 / (side * side);
+        const double log_side2 = 2.0 * log(side);
+        const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
+        const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
+        for (int tb = e0; tb < e1; tb += kMhLeafThreads) {
+            const int ti = tb + tid;
+            const bool valid = ti < e1;
+            const double2 z = valid ? g.exy[ti] : cb;
+            double acc = 0.0;
+
+            // L2P: phi = 2 Re sum_m u^m h_m L_m - h_0 L_0, by Horner in u while h_m
+            // runs down its recurrence
+            __syncthreads();
+            for (int i = tid; i < P1; i += kMhLeafThreads) Cs[i] = L[(int64_t)b * P1 + i];
+            __syncthreads();
+            if (valid) {
+                const double2 u = make_double2((z.x - cb.x) / side, (z.y - cb.y) / side);
+                const double y = sig * sig * (u.x * u.x + u.y * u.y);
+                double hm, hm1;
+                bessel::h_series2(P, y, mh.inv_fact_P, hm, hm1);
+                double2 S = make_double2(Cs[P].x * hm, Cs[P].y * hm);
+                for (int m = P; m >= 1; --m) {
+                    const double hp = fma((double)m, hm, y * hm1);
+                    hm1 = hm;
+                    hm = hp;
+                    const double2 c = Cs[m - 1];
+                    S = cfma(S, u, make_double2(c.x * hp, c.y * hp));
+                }
+                acc += 2.0 * S.x - hm * Cs[0].x;
+            }
+            // M2P over W: phi = K_0 M_0 + 2 Re sum_{n>=1} sigma_D^n K_n e^{i n theta} M_n
+            for (int e = w0; e < w1; ++e) {
+                const int D = t.w_idx[e];
+                __syncthreads();
+                for (int i = tid; i < P1; i += kMhLeafThreads) Cs[i] = M[(int64_t)D * P1 + i];
+                __syncthreads();
+                if (valid) {
+                    const double2 cD = t.center[D];
+                    const double sD = mh.spow[t.level[D] * P1 + 1];
+                    const double dx = z.x - cD.x, dy = z.y - cD.y;
+                    const double rho = sqrt(dx * dx + dy * dy);
+                    const double x = mh.lambda * rho;
+                    double k0, k1;
+                    bessel::k01(x, k0, k1);
+                    const double2 ph = make_double2(dx / rho, dy / rho);
+                    double ka = k0, kb = sD * k1;
+                    const double s2 = sD * sD, r = 2.0 * sD / x;
+                    double2 p = ph;
+                    double s = kb * (p.x * Cs[1].x - p.y * Cs[1].y);
+                    for (int n = 1; n < P; ++n) {
+                        const double kc = fma(s2, ka, (double)n * r * kb);
+                        ka = kb;
+                        kb = kc;
+                        p = cmul(p, ph);
+                        s = fma(kb, p.x * Cs[n + 1].x - p.y * Cs[n + 1].y, s);
+                    }
+                    acc += fma(2.0, s, k0 * Cs[0].x);
+                }
+            }
+            // P2P over U
+            double near = 0.0;
+            for (int e = u0; e < u1; ++e) {
+                const int A = t.u_idx[e];
+                const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                for (int sb = a0; sb < a1; sb += kMhLeafThreads) {
+                    const int n = min(kMhLeafThreads, a1 - sb);
+                    __syncthreads();
+                    if (tid < n) {
+                        sxy[tid] = g.cxy[sb + tid];
+                        sq[tid] = q[sb + tid];
+                    }
+                    __syncthreads();
+                    if (valid) {
+                        for (int j = 0; j < n; ++j) {
+                            const double dx = z.x - sxy[j].x, dy = z.y - sxy[j].y;
+                            const double r2 = fma(dx, dx, dy * dy);
+                            if (r2 == 0.0) continue;  // coincident pair: no smooth term
+                            const double y = mh.lam2_4 * r2;
+                            double k0;
+                            if (y <= 1.0) {
+                                const double rs = r2 * inv_side2;
+                                const float h = __double2float_rn(rs);
+                                const float l = __double2float_rn(rs - (double)h);
+                                float S, lo;
+                                ff::log_pair(h, l, logtab, S, lo);
+                                const double lg = (double)S + (double)lo + log_side2;  // log r^2
+                                double ia = na[deg], sb2 = nb[deg];
+                                for (int k = deg - 1; k >= 0; --k) {
+                                    ia = fma(ia, y, na[k]);
+                                    sb2 = fma(sb2, y, nb[k]);
+                                }
+                                k0 = fma(ia, fma(-0.5, lg, -mh.c0), sb2);
+                            } else {
+                                k0 = bessel::k0_large(mh.lambda * sqrt(r2));
+                            }
+                            near = fma(sq[j], k0, near);
+                        }
+                    }
+                }
+            }
+            if (valid) psi[ti] = mh.psi_scale * (acc + near);
+        }
+    }
+}
+
+template <int P>
+cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g, Workspace& ws,
+                   PhaseTimer* tm, cudaStream_t s)
+{
+    const int threads = kWarps * 32;
+    int id = tm ? tm->begin("upward") : -1;
+    k_p2m_mh<P><<<wblocks(t.nleaf), threads, 0, s>>>(t, mh, g, ws.q, ws.M);
+    for (int l = t.nlevels - 2; l >= 2; --l) {  // multipoles of levels 0 and 1 are never read
+        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
+        k_m2m_mh<P><<<wblocks(b1 - b0), threads, 0, s>>>(t, mh, l, b0, b1, ws.M);
+    }
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("m2l") : -1;
+    k_m2l_mh<P><<<wblocks(t.nbox), threads, 0, s>>>(t, mh, g, ws.M, ws.L, ws.q);
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("l2l") : -1;
+    for (int l = 3; l < t.nlevels; ++l) {  // locals of levels 0 to 2 receive nothing from above
+        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
+        k_l2l_mh<P><<<wblocks(b1 - b0), threads, 0, s>>>(t, mh, l, b0, b1, ws.L);
+    }
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("leaf") : -1;
+    const int blocks = std::max(1, std::min(t.nleaf, 152 * 16));
+    k_leaf_mh<P><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.M, ws.L, logtab, ws.psi);
+    if (tm) tm->end(id);
+    return cudaGetLastError();
+}
+
+double2 d2(double x, double y)
+{
+    double2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+}  // namespace
+
+cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g,
+                             Workspace& ws, PhaseTimer* timer, cudaStream_t s)
+{
+    switch (P) {
+        case 16: return fmm_mh<16>(t, mh, logtab, g, ws, timer, s);
+        case 24: return fmm_mh<24>(t, mh, logtab, g, ws, timer, s);
+        case 30: return fmm_mh<30>(t, mh, logtab, g, ws, timer, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int64_t mhelm_launches(int nlevels) { return 3 + 2 * (int64_t)std::max(0, nlevels - 3); }
+
+std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level, double near_dmax, MhTables& T)
+{
+    const int P1 = P + 1, NJ = 2 * P + 1, NT = 3 * P + 1;
+    const int nl = (int)R_level.size();
+    T.spow.assign((size_t)nl * P1, 0.0);
+    T.Tm.assign((size_t)nl * 4 * NJ * P1, d2(0.0, 0.0));
+    T.Tl.assign((size_t)nl * 4 * NJ * P1, d2(0.0, 0.0));
+    T.Tv.assign((size_t)nl * 49 * NT, d2(0.0, 0.0));
+    // 1/m! and h_m(y_d) for the child offset d (|d| = sqrt(2) R_child, y_d = sigma_child^2 / 2)
+    std::vector<double> inv_fact((size_t)3 * P + 2, 1.0);
+    for (size_t m = 1; m < inv_fact.size(); ++m) inv_fact[m] = inv_fact[m - 1] / (double)m;
+    T.inv_fact_P = inv_fact[(size_t)P];
+    for (int l = 0; l < nl; ++l) {
+        const double sig = lambda * R_level[(size_t)l];
+        double pw = 1.0;
+        for (int k = 0; k <= P; ++k) {
+            T.spow[(size_t)l * P1 + k] = pw;
+            pw *= sig;
+        }
+    }
+    // M2M into a parent of level l (children at level l + 1) and L2L into a child of
+    // level l (parent at level l - 1): both shift by d = child centre - parent centre
+    for (int l = 0; l < nl; ++l) {
+        for (int pass = 0; pass < 2; ++pass) {
+            const int lc = pass == 0 ? l + 1 : l;  // level of the child
+            if (lc >= nl || lc < 1) continue;
+            const double sc = lambda * R_level[(size_t)lc];
+            const double yd = 0.5 * sc * sc;
+            std::vector<double> h((size_t)NJ + 1);
+            for (int a = 0; a <= 2 * P; ++a) h[(size_t)a] = bessel::h_series(a, yd, inv_fact[(size_t)a]);
+            for (int cq = 0; cq < 4; ++cq) {
+                const double th = std::atan2((cq & 2) ? 1.0 : -1.0, (cq & 1) ? 1.0 : -1.0);
+                double2* dst = (pass == 0 ? T.Tm.data() : T.Tl.data()) + (size_t)(l * 4 + cq) * NJ * P1;
+                for (int j = -P; j <= P; ++j) {
+                    for (int n = 0; n <= P; ++n) {
+                        double mag, ang;
+                        if (pass == 0) {
+                            // sigma_c^|j| / sigma_p^n conj(I_{n-j}(d)), sigma_p = 2 sigma_c
+                            const int a = std::abs(n - j);
+                            mag = std::ldexp(1.0, -n) * std::pow(sc, std::abs(j) - n + a) *
+                                  std::pow(std::sqrt(0.5), a) * h[(size_t)a];
+                            ang = -(double)(n - j) * th;
+                        } else {
+                            // sigma_c^k sigma_p^-|m| I_{m-k}(d) with (m, k) = (j, n)
+                            const int a = std::abs(j - n);
+                            mag = std::ldexp(1.0, -std::abs(j)) * std::pow(sc, n - std::abs(j) + a) *
+                                  std::pow(std::sqrt(0.5), a) * h[(size_t)a];
+                            ang = (double)(j - n) * th;
+                        }
+                        dst[(size_t)(j + P) * P1 + n] = d2(mag * std::cos(ang), mag * std::sin(ang));
+                    }
+                }
+            }
+        }
+    }
+    // M2L: K_n(v), n = -2P..P, v = c_target - c_source = -2 R_l (ox + i oy)
+    std::vector<double> K((size_t)2 * P + 1);
+    for (int l = 2; l < nl; ++l) {
+        const double R = R_level[(size_t)l];
+        for (int oy = -3; oy <= 3; ++oy)
+            for (int ox = -3; ox <= 3; ++ox) {
+                if (std::abs(ox) <= 1 && std::abs(oy) <= 1) continue;
+                const double vx = -2.0 * R * ox, vy = -2.0 * R * oy;
+                const double x = lambda * std::sqrt(vx * vx + vy * vy);
+                const double th = std::atan2(vy, vx);
+                double k0, k1;
+                bessel::k01(x, k0, k1);
+                K[0] = k0;
+                K[1] = k1;
+                for (int n = 1; n < 2 * P; ++n) K[(size_t)n + 1] = K[(size_t)n - 1] + (2.0 * n / x) * K[(size_t)n];
+                double2* dst = T.Tv.data() + ((size_t)l * 49 + (size_t)((oy + 3) * 7 + ox + 3)) * NT;
+                for (int n = -2 * P; n <= P; ++n) {
+                    const double kn = K[(size_t)std::abs(n)];
+                    dst[(size_t)(n + 2 * P)] = d2(kn * std::cos(n * th), kn * std::sin(n * th));
+                }
+            }
+    }
+    // near-field series: terms until the first omitted one is below 1e-18 at the
+    // largest y of the series path (y <= 1)
+    const double ymax = std::min(1.0, 0.25 * lambda * lambda * near_dmax * near_dmax);
+    int deg = 1;
+    double term = ymax;  // y^k / (k!)^2 at k = deg
+    while (deg < kMaxNearTerms - 1) {
+        const double next = term * ymax / ((double)(deg + 1) * (double)(deg + 1));
+        if (next * (4.0 + std::log((double)deg + 2.0)) < 1e-18) break;
+        term = next;
+        ++deg;
+    }
+    T.near_deg = deg;
+    T.near_a.assign((size_t)deg + 1, 0.0);
+    T.near_b.assign((size_t)deg + 1, 0.0);
+    double a = 1.0, H = 0.0;
+    for (int k = 0; k <= deg; ++k) {
+        if (k > 0) {
+            a /= (double)k * (double)k;
+            H += 1.0 / (double)k;
+        }
+        T.near_a[(size_t)k] = a;
+        T.near_b[(size_t)k] = H * a;
+    }
+    auto finite = [](const std::vector<double2>& v) {
+        for (const double2& z : v)
+            if (!std::isfinite(z.x) || !std::isfinite(z.y)) return false;
+        return true;
+    };
+    for (double v : T.spow)
+        if (!std::isfinite(v)) return "lambda times the box size is outside the range of the expansions";
+    if (!finite(T.Tm) || !finite(T.Tl) || !finite(T.Tv))
+        return "lambda times the box size is outside the range of the expansions";
+    return "";
+}
+
+double green_mhelm_host(double lambda, double r)
+{
+    double k0, k1;
+    bessel::k01(lambda * r, k0, k1);
+    return lambda * lambda * 0.159154943091895335768883763372514362 * k0;
+}
+
+}  // namespace vp

@@ -23,6 +23,8 @@ VP_OK = 0
 VP_FLAG_TIMING = 1
 VP_FLAG_FP64 = 2
 VP_FLAG_GRAPH = 4
+VP_KERNEL_LAPLACE = 0
+VP_KERNEL_MHELMHOLTZ = 1
 
 TREE_ARRAYS = {
     "box_level": 0, "box_ixy": 1, "box_parent": 2, "box_leaf": 3, "box_src": 4, "box_tgt": 5,
@@ -33,6 +35,7 @@ TREE_ARRAYS = {
 EXPORTED = [
     "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host",
     "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_set_overlap", "vp_plan_destroy",
+    "vp_green_eval_host",
     "vp_status_string", "vp_last_error", "vp_version",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
     "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
@@ -50,8 +53,8 @@ class VPError(RuntimeError):
 
 class vp_options(ctypes.Structure):
     _fields_ = [("p_fmm", ctypes.c_int32), ("leaf", ctypes.c_int32), ("max_level", ctypes.c_int32),
-                ("max_dens", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("root", ctypes.c_double * 3)]
+                ("max_dens", ctypes.c_int32), ("flags", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("root", ctypes.c_double * 3), ("lam", ctypes.c_double)]
 
 
 class vp_plan_stats(ctypes.Structure):
@@ -113,6 +116,7 @@ def _load():
         "vp_plan_destroy": [P],
         "vp_plan_set_flags": [P, ctypes.c_uint32],
         "vp_plan_set_overlap": [P, I32],
+        "vp_green_eval_host": [I32, ctypes.c_double, I64, P, P],
         "vp_status_string": [I32],
         "vp_last_error": [],
         "vp_version": [],
@@ -139,12 +143,23 @@ def _check(status: int, where: str):
         raise VPError(status, where)
 
 
-def make_options(p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0, root=None) -> vp_options:
+def make_options(p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0, root=None, kernel=0, lam=0.0) -> vp_options:
     o = vp_options()
     o.p_fmm, o.leaf, o.max_level, o.max_dens, o.flags = p_fmm, leaf, max_level, max_dens, flags
+    o.kernel, o.lam = kernel, lam
     if root is not None:
         o.root[0], o.root[1], o.root[2] = root
     return o
+
+
+def green_eval_host(r, kernel=0, lam=0.0):
+    """G(r) of the kernel (VP_KERNEL_LAPLACE or VP_KERNEL_MHELMHOLTZ) at distances
+    r > 0, on the host, with the plans' Bessel routines."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    g = np.empty_like(r)
+    _check(_load().vp_green_eval_host(kernel, lam, r.size, r.ctypes.data_as(ctypes.c_void_p),
+                                      g.ctypes.data_as(ctypes.c_void_p)), "vp_green_eval_host")
+    return g
 
 
 def _ptr(t):
@@ -427,8 +442,9 @@ class Plan:
 
     @classmethod
     def create(cls, src_xy, w, tgt_xy, csr=None, p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0,
-               root=None, stream=None) -> "Plan":
-        opts = make_options(p_fmm, leaf, max_level, max_dens, flags, root)
+               root=None, stream=None, kernel=0, lam=0.0) -> "Plan":
+        """kernel: VP_KERNEL_LAPLACE (default) or VP_KERNEL_MHELMHOLTZ with parameter lam."""
+        opts = make_options(p_fmm, leaf, max_level, max_dens, flags, root, kernel, lam)
         h = vp_plan_create(src_xy, w, tgt_xy, csr, opts, stream)
         info = vp_plan_info(h)
         return cls(h, int(info.n_src), int(info.n_tgt))
