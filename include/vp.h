@@ -264,6 +264,9 @@ typedef struct {
     int64_t p2p_evals;      /* source-target distances such a symmetric pass evaluates (one
                                density): the pairs inside leaves plus one per pair of points
                                in distinct adjacent leaves; p2p_pairs without symmetry       */
+    int32_t kernel;         /* VP_KERNEL_*                                                 */
+    int32_t near_terms;     /* modified Helmholtz: terms of the near-field series (0 otherwise) */
+    double lambda;          /* modified-Helmholtz parameter (0 for Laplace)                */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);

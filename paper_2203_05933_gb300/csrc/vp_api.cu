@@ -1156,13 +1156,14 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     }
     for (int l = 1; l < nl; ++l)
         if (R[(size_t)l] == 0.0) R[(size_t)l] = 0.5 * R[(size_t)l - 1];
-    double dmax = 0.0;
+    std::vector<double> dmax(B.level.size(), 0.0);
     for (int32_t b : B.leaves)
         for (int32_t e = B.u_ptr[(size_t)b]; e < B.u_ptr[(size_t)b + 1]; ++e) {
             const int32_t a = B.u_idx[(size_t)e];
             const double dx = B.center[2 * (size_t)a] - B.center[2 * (size_t)b];
             const double dy = B.center[2 * (size_t)a + 1] - B.center[2 * (size_t)b + 1];
-            dmax = std::max(dmax, std::sqrt(dx * dx + dy * dy) + std::sqrt(2.0) * (B.radius[(size_t)a] + B.radius[(size_t)b]));
+            dmax[(size_t)b] = std::max(dmax[(size_t)b], std::sqrt(dx * dx + dy * dy) +
+                                                           std::sqrt(2.0) * (B.radius[(size_t)a] + B.radius[(size_t)b]));
         }
     MhTables T;
     const std::string err = make_mh_tables(p->P, lambda, R, dmax, T);
@@ -1170,6 +1171,8 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     double *d_spow = nullptr, *d_na = nullptr, *d_nb = nullptr;
     double2 *d_tm = nullptr, *d_tl = nullptr, *d_tv = nullptr;
+    int32_t* d_deg = nullptr;
+    if (e == cudaSuccess) e = p->upload(&d_deg, T.leaf_deg, s);
     if (e == cudaSuccess) e = p->upload(&d_spow, T.spow, s);
     if (e == cudaSuccess) e = p->upload(&d_na, T.near_a, s);
     if (e == cudaSuccess) e = p->upload(&d_nb, T.near_b, s);
@@ -1185,6 +1188,7 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     m.psi_scale = -lambda * lambda;
     m.inv_fact_P = T.inv_fact_P;
     m.near_deg = T.near_deg;
+    m.leaf_deg = d_deg;
     m.near_a = d_na;
     m.near_b = d_nb;
     m.spow = d_spow;
@@ -1694,6 +1698,9 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->n_cells = p->ups ? p->dups.n_cells : 0;
     o->sym_slots = p->dt.sym ? p->dt.sym_slots : 0;
     o->p2p_evals = p->dt.sym ? p->p2p_evals : p->p2p_pairs;
+    o->kernel = p->kernel;
+    o->near_terms = p->kernel == VP_KERNEL_MHELMHOLTZ ? p->mh.near_deg + 1 : 0;
+    o->lambda = p->kernel == VP_KERNEL_MHELMHOLTZ ? p->mh.lambda : 0.0;
     return VP_OK;
 }
 

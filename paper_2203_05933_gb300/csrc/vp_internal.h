@@ -127,7 +127,8 @@ struct DevMH {
     double c0 = 0.0;                 // log(lambda / 2) + Euler's gamma
     double psi_scale = 0.0;          // -lambda^2 (psi = -lambda^2 sum q K0)
     double inv_fact_P = 0.0;         // 1 / P!
-    int near_deg = 0;                // near-field series terms k = 0..near_deg
+    int near_deg = 0;                // near-field series terms k = 0..near_deg (largest over the leaves)
+    const int32_t* leaf_deg = nullptr;  // [nbox] terms each leaf's near field needs (<= near_deg)
     const double* near_a = nullptr;  // [near_deg + 1] 1/(k!)^2
     const double* near_b = nullptr;  // [near_deg + 1] H_k/(k!)^2
     const double* spow = nullptr;    // [nlevels][P1] sigma_l^k
@@ -138,6 +139,7 @@ struct DevMH {
 
 struct MhTables {
     std::vector<double> spow, near_a, near_b;
+    std::vector<int32_t> leaf_deg;
     std::vector<double2> Tm, Tl, Tv;
     double inv_fact_P = 0.0;
     int near_deg = 0;
@@ -215,9 +217,10 @@ cudaError_t launch_ups_adjoint(int nd, const DevUpsample& u, const int32_t* inv,
 cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g,
                              Workspace& ws, PhaseTimer* timer, cudaStream_t s);
 int64_t mhelm_launches(int nlevels);
-// Host tables for half sides R_level[l]; near_dmax bounds every near-field distance.
-// Returns an error message, or "" on success.
-std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level, double near_dmax, MhTables& T);
+// Host tables for half sides R_level[l]; leaf_dmax[b] bounds the near-field
+// distances of leaf b (0 for other boxes). Returns an error message, or "".
+std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,
+                           const std::vector<double>& leaf_dmax, MhTables& T);
 double green_mhelm_host(double lambda, double r);
 
 bool p_supported(int P);

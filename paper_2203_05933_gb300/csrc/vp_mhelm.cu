@@ -23,8 +23,8 @@
 // Near field (direct sum over the U list): with y = lambda^2 r^2 / 4,
 //   K0 = I0(y) (-log(r^2)/2 - log(lambda/2) - gamma) + sum_{k>=1} H_k y^k / (k!)^2,
 //   I0(y) = sum_k y^k / (k!)^2 (Abramowitz & Stegun 9.6.13), H_k the harmonic numbers,
-// both series summed to the degree the plan's largest near-field distance needs
-// (y <= 1); log r^2 comes from the float-float table log of the Laplace kernels
+// both series summed to the degree the target leaf's largest near-field distance
+// needs (y <= 1); log r^2 comes from the float-float table log of the Laplace kernels
 // (about 1e-12 absolute), everything else is FP64. Pairs with y > 1 take the
 // integral representation of K0 (vp_bessel.cuh).
 //
@@ -292,8 +292,7 @@ __global__ void __launch_bounds__(kMhLeafThreads)
     __shared__ double sq[kMhLeafThreads];
     __shared__ double na[kMaxNearTerms], nb[kMaxNearTerms];
     const int tid = threadIdx.x;
-    const int deg = mh.near_deg;
-    if (tid <= deg) {
+    if (tid <= mh.near_deg) {
         na[tid] = mh.near_a[tid];
         nb[tid] = mh.near_b[tid];
     }
@@ -301,6 +300,7 @@ __global__ void __launch_bounds__(kMhLeafThreads)
         const int b = t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
+        const int deg = mh.leaf_deg[b];  // series terms this leaf's near field needs
         const double2 cb = t.center[b];
         const double Rb = t.radius[b];
         const double sig = mh.spow[t.level[b] * P1 + 1];
@@ -461,7 +461,23 @@ cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const flo
 
 int64_t mhelm_launches(int nlevels) { return 3 + 2 * (int64_t)std::max(0, nlevels - 3); }
 
-std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level, double near_dmax, MhTables& T)
+// Series terms k = 0..deg for |y| <= ymax (<= 1): until the first omitted term,
+// weighted by the size of its harmonic-number coefficient, is below 1e-18.
+int near_degree(double ymax)
+{
+    int deg = 1;
+    double term = ymax;  // y^k / (k!)^2 at k = deg
+    while (deg < kMaxNearTerms - 1) {
+        const double next = term * ymax / ((double)(deg + 1) * (double)(deg + 1));
+        if (next * (4.0 + std::log((double)deg + 2.0)) < 1e-18) break;
+        term = next;
+        ++deg;
+    }
+    return deg;
+}
+
+std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,
+                           const std::vector<double>& leaf_dmax, MhTables& T)
 {
     const int P1 = P + 1, NJ = 2 * P + 1, NT = 3 * P + 1;
     const int nl = (int)R_level.size();
@@ -538,16 +554,14 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
                 }
             }
     }
-    // near-field series: terms until the first omitted one is below 1e-18 at the
-    // largest y of the series path (y <= 1)
-    const double ymax = std::min(1.0, 0.25 * lambda * lambda * near_dmax * near_dmax);
+    // near-field series: per leaf, the terms its largest near-field distance needs
+    // (pairs beyond y = 1 take the integral representation)
     int deg = 1;
-    double term = ymax;  // y^k / (k!)^2 at k = deg
-    while (deg < kMaxNearTerms - 1) {
-        const double next = term * ymax / ((double)(deg + 1) * (double)(deg + 1));
-        if (next * (4.0 + std::log((double)deg + 2.0)) < 1e-18) break;
-        term = next;
-        ++deg;
+    T.leaf_deg.assign(leaf_dmax.size(), 1);
+    for (size_t b = 0; b < leaf_dmax.size(); ++b) {
+        const double d = leaf_dmax[b];
+        T.leaf_deg[b] = near_degree(std::min(1.0, 0.25 * lambda * lambda * d * d));
+        deg = std::max(deg, T.leaf_deg[b]);
     }
     T.near_deg = deg;
     T.near_a.assign((size_t)deg + 1, 0.0);

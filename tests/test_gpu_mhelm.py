@@ -38,10 +38,11 @@ def make(prob, lam, **opts):
     return vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, root=prob.root, kernel=MH, lam=lam, **opts)
 
 
-@pytest.mark.parametrize("lam,P", [(1.0, 30), (10.0, 16), (10.0, 24), (60.0, 16)])
+@pytest.mark.parametrize("lam,P", [(1.0, 30), (3.0, 24), (10.0, 24), (10.0, 30), (60.0, 24)])
 def test_cloud_matches_oracle(lam, P):
     # adaptive cloud with V, W and X lists; 1500 targets coincide with sources;
-    # at lambda = 60 many near-field pairs have lambda r > 2 (integral path of K0)
+    # at lambda = 60 many near-field pairs have lambda r > 2 (integral path of K0).
+    # (P = 16 truncates at about 1e-9 on this clustered cloud for every lambda.)
     prob = inputs.cloud_problem(6000, 5000, ndens=1, shared=1500, seed=71)
     plan = make(prob, lam, p_fmm=P, leaf=32)
     info = plan.info()
@@ -60,11 +61,11 @@ def test_densities_graph_and_timing():
     prob = inputs.cloud_problem(3000, 2500, ndens=3, shared=500, seed=72)
     lam = 5.0
     f = torch.as_tensor(prob.f, device="cuda")
-    plain = make(prob, lam, p_fmm=16, leaf=48)
+    plain = make(prob, lam, p_fmm=24, leaf=48)
     a = plain.eval(f).cpu().numpy()
     ref = mhelm.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, lam, prob.csr)
     assert float(np.max(np.abs(a - ref) / norm(prob, lam)[:, None])) <= TOL
-    graph = make(prob, lam, p_fmm=16, leaf=48, flags=vp.VP_FLAG_GRAPH)
+    graph = make(prob, lam, p_fmm=24, leaf=48, flags=vp.VP_FLAG_GRAPH)
     b1 = graph.eval(f).cpu().numpy()
     b2 = graph.eval(f).cpu().numpy()
     assert np.array_equal(a, b1) and np.array_equal(b1, b2)
@@ -98,7 +99,7 @@ def test_disk_sampled_targets():
     # the paper's modified-Helmholtz experiment is on the unit disk with lambda^2 = 100
     prob = inputs.disk_problem(base_level=5, fine_level=7)
     lam = 10.0
-    plan = make(prob, lam, p_fmm=16, leaf=128)
+    plan = make(prob, lam, p_fmm=16, leaf=128)  # 4e-11 on this geometry
     out = plan.eval(torch.as_tensor(prob.f, device="cuda")).cpu().numpy()
     rows = np.random.default_rng(9).choice(prob.n_tgt, size=300, replace=False)
     ref = mhelm.evaluate_rows(prob.src_xy, prob.w, prob.f, prob.tgt_xy, rows, lam, prob.csr)
@@ -129,7 +130,7 @@ def test_edge_cases():
     plan.close()
     # ragged sizes, no correction
     prob = inputs.cloud_problem(37, 1, ndens=1, seed=74, csr_per_row=0)
-    plan = make(prob, lam, p_fmm=16, leaf=8)
+    plan = make(prob, lam, p_fmm=24, leaf=8)
     out = plan.eval(torch.as_tensor(prob.f, device="cuda")).cpu().numpy()
     ref = mhelm.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, lam)
     assert float(np.max(np.abs(out - ref) / norm(prob, lam)[:, None])) <= TOL
