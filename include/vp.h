@@ -83,8 +83,9 @@ typedef struct {
  *   VP_KERNEL_MHELMHOLTZ   G(r, r0) = (lambda^2/2pi) K0(lambda |r - r0|)  (L = -Delta + lambda^2)
  * The prefactor lambda^2/2pi is the one the paper states; V then solves
  * (-Delta + lambda^2) V = lambda^2 f. Modified-Helmholtz plans come from
- * vp_plan_create only, evaluate one density per pass in FP64 (expansions, near
- * field; log r from the float-float table log), support vp_eval, vp_eval_host and
+ * vp_plan_create only, evaluate one density per pass (expansions in FP64; near
+ * field in float-float on the FP32 pipes, or in FP64 with VP_FLAG_FP64; log r
+ * from the float-float table log), support vp_eval, vp_eval_host and
  * the grad_f part of vp_eval_adjoint (the kernel is symmetric), and reject
  * grad_tgt with VP_ERR_UNSUPPORTED. Plan creation fails with VP_ERR_ARG if
  * lambda * (box half side) puts the expansion tables out of FP64 range (roughly

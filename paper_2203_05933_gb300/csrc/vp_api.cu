@@ -1137,8 +1137,6 @@ vp_status plan_options(const vp_options* opt_in, vp_options& opt, int& P, int& l
         return fail(VP_ERR_ARG, "unknown kernel");
     if (opt.kernel == VP_KERNEL_MHELMHOLTZ && !(opt.lambda > 0.0 && std::isfinite(opt.lambda)))
         return fail(VP_ERR_ARG, "the modified-Helmholtz kernel needs a finite lambda > 0");
-    if (opt.kernel == VP_KERNEL_MHELMHOLTZ && (opt.flags & VP_FLAG_FP64))
-        return fail(VP_ERR_ARG, "VP_FLAG_FP64 applies to the Laplace kernel only");
     return VP_OK;
 }
 
@@ -1432,7 +1430,8 @@ namespace {
 // The FMM of one density chunk for the plan's kernel (psi in tree order).
 cudaError_t run_fmm(vp_plan p, int nd, const PassGeom& g, bool gradient, PhaseTimer* tm, cudaStream_t s)
 {
-    if (p->kernel == VP_KERNEL_MHELMHOLTZ) return launch_fmm_mhelm(p->P, p->dt, p->mh, p->tab.logtab, g, p->ws, tm, s);
+    if (p->kernel == VP_KERNEL_MHELMHOLTZ)
+        return launch_fmm_mhelm(p->P, p->dt, p->mh, p->tab.logtab, g, p->ws, use_fp64(p), tm, s);
     return launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, gradient, use_fp64(p), tm, s);
 }
 

@@ -128,7 +128,8 @@ struct DevMH {
     double psi_scale = 0.0;          // -lambda^2 (psi = -lambda^2 sum q K0)
     double inv_fact_P = 0.0;         // 1 / P!
     int near_deg = 0;                // near-field series terms k = 0..near_deg (largest over the leaves)
-    const int32_t* leaf_deg = nullptr;  // [nbox] terms each leaf's near field needs (<= near_deg)
+    const int32_t* leaf_deg = nullptr;  // [nbox] per leaf: series degree (bits 0-7, <= near_deg) and the
+                                        // first term summed in FP32 by the float-float near field (bits 8+)
     const double* near_a = nullptr;  // [near_deg + 1] 1/(k!)^2
     const double* near_b = nullptr;  // [near_deg + 1] H_k/(k!)^2
     const double* spow = nullptr;    // [nlevels][P1] sigma_l^k
@@ -214,8 +215,9 @@ cudaError_t launch_ups_adjoint(int nd, const DevUpsample& u, const int32_t* inv,
                                const double* psi, double* out, int64_t ld_out, cudaStream_t s);
 
 // Modified-Helmholtz FMM (vp_mhelm.cu): one density per pass; psi = -lambda^2 sum q K0.
+// fp64: the near field in FP64 instead of float-float on the FP32 pipes.
 cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g,
-                             Workspace& ws, PhaseTimer* timer, cudaStream_t s);
+                             Workspace& ws, bool fp64, PhaseTimer* timer, cudaStream_t s);
 int64_t mhelm_launches(int nlevels);
 // Host tables for half sides R_level[l]; leaf_dmax[b] bounds the near-field
 // distances of leaf b (0 for other boxes). Returns an error message, or "".

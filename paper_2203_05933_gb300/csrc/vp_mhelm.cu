@@ -279,34 +279,123 @@ __global__ void __launch_bounds__(kWarps * 32)
 }
 
 // ----------------------------------------------------------------------------
+// Near field of one target over a staged tile of charges, float-float on the
+// FP32 pipes. Per pair (units of the target leaf's side): r'^2 from exact
+// leaf-centre offsets, log r'^2 by the table log, y = (lambda^2 side^2/4) r'^2,
+// T = -log(r'^2)/2 - (log side + log(lambda/2) + gamma), and
+// K0 = T I0(y) + S(y) with both series by Horner: the terms k >= m in FP32 (their
+// share of K0 is below the leaf's bound, see near_split), the terms k < m in
+// float-float. Pairs with y > 1 take the integral representation in FP64.
+// EXACT: the hi parts of target and source differ exactly in float.
+template <bool EXACT>
+__device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restrict__ s_rho,
+                                        const float2* __restrict__ s_q, int n, const float4* __restrict__ s_tab,
+                                        const float2* __restrict__ a2, const float2* __restrict__ b2, int deg, int m,
+                                        ff::F cy, ff::F Tc, double lam_side, float& ah, float& al)
+{
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+        const float4 sr = s_rho[k];
+        float dxs, dxe, dys, dye;
+        if (EXACT) {
+            dxs = __fsub_rn(rt.x, sr.x);
+            dxe = __fsub_rn(rt.y, sr.y);
+            dys = __fsub_rn(rt.z, sr.z);
+            dye = __fsub_rn(rt.w, sr.w);
+        } else {
+            ff::two_sum(rt.x, -sr.x, dxs, dxe);
+            dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
+            ff::two_sum(rt.z, -sr.z, dys, dye);
+            dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
+        }
+        const float px = __fmul_rn(dxs, dxs);
+        float pxe = fmaf(dxs, dxs, -px);
+        pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
+        pxe = fmaf(dxe, dxe, pxe);
+        const float py = __fmul_rn(dys, dys);
+        float pye = fmaf(dys, dys, -py);
+        pye = fmaf(__fadd_rn(dys, dys), dye, pye);
+        pye = fmaf(dye, dye, pye);
+        const float rs = __fadd_rn(px, py);
+        float re = __fsub_rn(fminf(px, py), __fsub_rn(rs, fmaxf(px, py)));
+        re = __fadd_rn(re, __fadd_rn(pxe, pye));
+        if (rs == 0.0f && re == 0.0f) continue;  // coincident pair: no smooth term
+        const ff::F r2{rs, re};
+        const ff::F y = ff::mul(r2, cy);
+        ff::F K;
+        if (y.h > 1.0f) {
+            K = ff::from_double(bessel::k0_large(lam_side * sqrt((double)rs + (double)re)));
+        } else {
+            float S, lo;
+            ff::log_pair(rs, re, s_tab, S, lo);
+            const ff::F T = ff::add(ff::F{-0.5f * S, -0.5f * lo}, Tc);
+            float ta = 0.0f, tb = 0.0f;
+            for (int j = deg; j >= m; --j) {
+                ta = fmaf(ta, y.h, a2[j].x);
+                tb = fmaf(tb, y.h, b2[j].x);
+            }
+            ff::F A{ta, 0.0f}, B{tb, 0.0f};
+            for (int j = m - 1; j >= 0; --j) {
+                A = ff::add(ff::mul(A, y), ff::F{a2[j].x, a2[j].y});
+                B = ff::add(ff::mul(B, y), ff::F{b2[j].x, b2[j].y});
+            }
+            K = ff::add(ff::mul(A, T), B);
+        }
+        const float2 qq = s_q[k];
+        const float p = __fmul_rn(qq.x, K.h);
+        float pe = fmaf(qq.x, K.h, -p);
+        pe = fmaf(qq.x, K.l, pe);
+        pe = fmaf(qq.y, K.h, pe);
+        float sh, se;
+        ff::two_sum(ah, p, sh, se);
+        ah = sh;
+        al = __fadd_rn(al, __fadd_rn(se, pe));
+    }
+}
+
+// ----------------------------------------------------------------------------
 // Per leaf: L2P, M2P over the W list and the direct sum over the U list; one
-// block per leaf, one target per thread.
-template <int P>
+// block per leaf, one target per thread. FF: the near field in float-float on
+// the FP32 pipes (mh_tile); else in FP64.
+template <int P, bool FF>
 __global__ void __launch_bounds__(kMhLeafThreads)
-    k_leaf_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
-              const double2* __restrict__ L, const float4* __restrict__ logtab, double* __restrict__ psi)
+    k_leaf_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
+              const double2* __restrict__ M, const double2* __restrict__ L, const float4* __restrict__ logtab,
+              double* __restrict__ psi)
 {
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1];
-    __shared__ double2 sxy[kMhLeafThreads];
-    __shared__ double sq[kMhLeafThreads];
+    __shared__ double2 sxy[FF ? 1 : kMhLeafThreads];
+    __shared__ double sq[FF ? 1 : kMhLeafThreads];
+    __shared__ float4 s_rho[FF ? kMhLeafThreads : 1];
+    __shared__ float2 s_qf[FF ? kMhLeafThreads : 1];
+    __shared__ float4 s_tab[FF ? 128 : 1];
     __shared__ double na[kMaxNearTerms], nb[kMaxNearTerms];
+    __shared__ float2 a2[kMaxNearTerms], b2[kMaxNearTerms];
     const int tid = threadIdx.x;
     if (tid <= mh.near_deg) {
         na[tid] = mh.near_a[tid];
         nb[tid] = mh.near_b[tid];
+        const ff::F fa = ff::from_double(mh.near_a[tid]), fb = ff::from_double(mh.near_b[tid]);
+        a2[tid] = make_float2(fa.h, fa.l);
+        b2[tid] = make_float2(fb.h, fb.l);
     }
+    if (FF)
+        for (int i = tid; i < 128; i += kMhLeafThreads) s_tab[i] = logtab[i];
     for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
         const int b = t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
-        const int deg = mh.leaf_deg[b];  // series terms this leaf's near field needs
+        const int code = mh.leaf_deg[b];  // series terms this leaf's near field needs, and its split
+        const int deg = code & 0xff, msplit = code >> 8;
         const double2 cb = t.center[b];
         const double Rb = t.radius[b];
         const double sig = mh.spow[t.level[b] * P1 + 1];
         const double side = 2.0 * Rb;
         const double inv_side2 = 1.0 / (side * side);
         const double log_side2 = 2.0 * log(side);
+        const ff::F cy = ff::from_double(mh.lam2_4 * side * side);
+        const ff::F Tc = ff::from_double(-(0.5 * log_side2 + mh.c0));
         const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
         for (int tb = e0; tb < e1; tb += kMhLeafThreads) {
@@ -366,41 +455,81 @@ __global__ void __launch_bounds__(kMhLeafThreads)
             }
             // P2P over U
             double near = 0.0;
-            for (int e = u0; e < u1; ++e) {
-                const int A = t.u_idx[e];
-                const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
-                for (int sb = a0; sb < a1; sb += kMhLeafThreads) {
-                    const int n = min(kMhLeafThreads, a1 - sb);
-                    __syncthreads();
-                    if (tid < n) {
-                        sxy[tid] = g.cxy[sb + tid];
-                        sq[tid] = q[sb + tid];
-                    }
-                    __syncthreads();
-                    if (valid) {
-                        for (int j = 0; j < n; ++j) {
-                            const double dx = z.x - sxy[j].x, dy = z.y - sxy[j].y;
-                            const double r2 = fma(dx, dx, dy * dy);
-                            if (r2 == 0.0) continue;  // coincident pair: no smooth term
-                            const double y = mh.lam2_4 * r2;
-                            double k0;
-                            if (y <= 1.0) {
-                                const double rs = r2 * inv_side2;
-                                const float h = __double2float_rn(rs);
-                                const float l = __double2float_rn(rs - (double)h);
-                                float S, lo;
-                                ff::log_pair(h, l, logtab, S, lo);
-                                const double lg = (double)S + (double)lo + log_side2;  // log r^2
-                                double ia = na[deg], sb2 = nb[deg];
-                                for (int k = deg - 1; k >= 0; --k) {
-                                    ia = fma(ia, y, na[k]);
-                                    sb2 = fma(sb2, y, nb[k]);
-                                }
-                                k0 = fma(ia, fma(-0.5, lg, -mh.c0), sb2);
+            if (FF) {
+                const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float ah = 0.0f, al = 0.0f;
+                for (int e = u0; e < u1; ++e) {
+                    const int A = t.u_idx[e];
+                    const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                    if (a0 == a1) continue;
+                    const float4 uo = t.u_off[e];  // leaf A's centre offset and scale in b units
+                    const bool exact_hi = uo.z >= 0.5f && uo.z <= 2.0f;
+                    for (int sb = a0; sb < a1; sb += kMhLeafThreads) {
+                        const int n = min(kMhLeafThreads, a1 - sb);
+                        __syncthreads();
+                        if (tid < n) {
+                            const int j = sb + tid;
+                            const float4 r = g.crho[j];
+                            ff::F sx, sy;
+                            if (exact_hi) {
+                                sx = ff::F{__fadd_rn(uo.x, __fmul_rn(uo.z, r.x)), __fmul_rn(uo.z, r.y)};
+                                sy = ff::F{__fadd_rn(uo.y, __fmul_rn(uo.z, r.z)), __fmul_rn(uo.z, r.w)};
                             } else {
-                                k0 = bessel::k0_large(mh.lambda * sqrt(r2));
+                                sx = ff::shift_scale(uo.x, uo.z, r.x, r.y);
+                                sy = ff::shift_scale(uo.y, uo.z, r.z, r.w);
                             }
-                            near = fma(sq[j], k0, near);
+                            s_rho[tid] = make_float4(sx.h, sx.l, sy.h, sy.l);
+                            s_qf[tid] = qf[j];
+                        }
+                        __syncthreads();
+                        if (valid) {
+                            if (exact_hi)
+                                mh_tile<true>(rt, s_rho, s_qf, n, s_tab, a2, b2, deg, msplit, cy, Tc,
+                                              mh.lambda * side, ah, al);
+                            else
+                                mh_tile<false>(rt, s_rho, s_qf, n, s_tab, a2, b2, deg, msplit, cy, Tc,
+                                               mh.lambda * side, ah, al);
+                        }
+                    }
+                }
+                near = (double)ah + (double)al;
+            } else {
+                for (int e = u0; e < u1; ++e) {
+                    const int A = t.u_idx[e];
+                    const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                    for (int sb = a0; sb < a1; sb += kMhLeafThreads) {
+                        const int n = min(kMhLeafThreads, a1 - sb);
+                        __syncthreads();
+                        if (tid < n) {
+                            sxy[tid] = g.cxy[sb + tid];
+                            sq[tid] = q[sb + tid];
+                        }
+                        __syncthreads();
+                        if (valid) {
+                            for (int j = 0; j < n; ++j) {
+                                const double dx = z.x - sxy[j].x, dy = z.y - sxy[j].y;
+                                const double r2 = fma(dx, dx, dy * dy);
+                                if (r2 == 0.0) continue;  // coincident pair: no smooth term
+                                const double y = mh.lam2_4 * r2;
+                                double k0;
+                                if (y <= 1.0) {
+                                    const double rs = r2 * inv_side2;
+                                    const float h = __double2float_rn(rs);
+                                    const float l = __double2float_rn(rs - (double)h);
+                                    float S, lo;
+                                    ff::log_pair(h, l, logtab, S, lo);
+                                    const double lg = (double)S + (double)lo + log_side2;  // log r^2
+                                    double ia = na[deg], sb2 = nb[deg];
+                                    for (int k = deg - 1; k >= 0; --k) {
+                                        ia = fma(ia, y, na[k]);
+                                        sb2 = fma(sb2, y, nb[k]);
+                                    }
+                                    k0 = fma(ia, fma(-0.5, lg, -mh.c0), sb2);
+                                } else {
+                                    k0 = bessel::k0_large(mh.lambda * sqrt(r2));
+                                }
+                                near = fma(sq[j], k0, near);
+                            }
                         }
                     }
                 }
@@ -412,7 +541,7 @@ __global__ void __launch_bounds__(kMhLeafThreads)
 
 template <int P>
 cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g, Workspace& ws,
-                   PhaseTimer* tm, cudaStream_t s)
+                   bool fp64, PhaseTimer* tm, cudaStream_t s)
 {
     const int threads = kWarps * 32;
     int id = tm ? tm->begin("upward") : -1;
@@ -433,7 +562,10 @@ cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, cons
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
     const int blocks = std::max(1, std::min(t.nleaf, 152 * 16));
-    k_leaf_mh<P><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.M, ws.L, logtab, ws.psi);
+    if (fp64)
+        k_leaf_mh<P, false><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab, ws.psi);
+    else
+        k_leaf_mh<P, true><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab, ws.psi);
     if (tm) tm->end(id);
     return cudaGetLastError();
 }
@@ -449,12 +581,12 @@ double2 d2(double x, double y)
 }  // namespace
 
 cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g,
-                             Workspace& ws, PhaseTimer* timer, cudaStream_t s)
+                             Workspace& ws, bool fp64, PhaseTimer* timer, cudaStream_t s)
 {
     switch (P) {
-        case 16: return fmm_mh<16>(t, mh, logtab, g, ws, timer, s);
-        case 24: return fmm_mh<24>(t, mh, logtab, g, ws, timer, s);
-        case 30: return fmm_mh<30>(t, mh, logtab, g, ws, timer, s);
+        case 16: return fmm_mh<16>(t, mh, logtab, g, ws, fp64, timer, s);
+        case 24: return fmm_mh<24>(t, mh, logtab, g, ws, fp64, timer, s);
+        case 30: return fmm_mh<30>(t, mh, logtab, g, ws, fp64, timer, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -474,6 +606,30 @@ int near_degree(double ymax)
         ++deg;
     }
     return deg;
+}
+
+// Smallest m in [1, deg + 1] such that the terms k >= m of both series, summed in
+// FP32 (relative error below 2^-20 for at most 16 terms), change K0 = T I0 + S by
+// less than 2e-15 for every 0 < y <= ymax, with |T| <= |log(4y/lambda^2)|/2 + |c0|.
+int near_split(int deg, double ymax, double lambda, double c0, const std::vector<double>& ca,
+               const std::vector<double>& cb)
+{
+    for (int m = 1; m <= deg; ++m) {
+        double worst = 0.0;
+        for (int i = 0; i < 400; ++i) {
+            const double y = ymax * std::ldexp(1.0, -i / 4);
+            if (y <= 0.0) break;
+            double ta = 0.0, tb = 0.0, ym = std::pow(y, m);
+            for (int k = m; k <= deg; ++k) {
+                ta += ca[(size_t)k] * std::pow(y, k - m);
+                tb += cb[(size_t)k] * std::pow(y, k - m);
+            }
+            const double Tabs = 0.5 * std::fabs(std::log(4.0 * y / (lambda * lambda))) + std::fabs(c0);
+            worst = std::max(worst, ym * (ta * Tabs + tb));
+        }
+        if (worst * 0x1p-20 < 2e-15) return m;
+    }
+    return deg + 1;
 }
 
 std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,
@@ -555,26 +711,41 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
             }
     }
     // near-field series: per leaf, the terms its largest near-field distance needs
-    // (pairs beyond y = 1 take the integral representation)
+    // (pairs beyond y = 1 take the integral representation) and the split between
+    // the float-float head and the FP32 tail of the Horner sums
+    std::vector<double> ca(kMaxNearTerms), cb(kMaxNearTerms);
+    {
+        double a = 1.0, H = 0.0;
+        for (int k = 0; k < kMaxNearTerms; ++k) {
+            if (k > 0) {
+                a /= (double)k * (double)k;
+                H += 1.0 / (double)k;
+            }
+            ca[(size_t)k] = a;
+            cb[(size_t)k] = H * a;
+        }
+    }
+    const double c0 = std::log(0.5 * lambda) + bessel::kEulerGamma;
     int deg = 1;
-    T.leaf_deg.assign(leaf_dmax.size(), 1);
+    T.leaf_deg.assign(leaf_dmax.size(), 1 | (2 << 8));
+    // ymax rounded up to a power of 2^(1/4) (the bounds grow with ymax), one
+    // evaluation per distinct value
+    std::vector<int> memo(512, -1);
     for (size_t b = 0; b < leaf_dmax.size(); ++b) {
         const double d = leaf_dmax[b];
-        T.leaf_deg[b] = near_degree(std::min(1.0, 0.25 * lambda * lambda * d * d));
-        deg = std::max(deg, T.leaf_deg[b]);
+        const double y = std::min(1.0, 0.25 * lambda * lambda * d * d);
+        const int key = y > 0.0 ? std::max(0, std::min(511, (int)std::floor(-4.0 * std::log2(y)))) : 511;
+        if (memo[(size_t)key] < 0) {
+            const double yq = std::ldexp(1.0, -key / 4) * std::pow(2.0, -(key % 4) / 4.0);
+            const int db = near_degree(yq);
+            memo[(size_t)key] = db | (near_split(db, yq, lambda, c0, ca, cb) << 8);
+        }
+        T.leaf_deg[b] = memo[(size_t)key];
+        deg = std::max(deg, memo[(size_t)key] & 0xff);
     }
     T.near_deg = deg;
-    T.near_a.assign((size_t)deg + 1, 0.0);
-    T.near_b.assign((size_t)deg + 1, 0.0);
-    double a = 1.0, H = 0.0;
-    for (int k = 0; k <= deg; ++k) {
-        if (k > 0) {
-            a /= (double)k * (double)k;
-            H += 1.0 / (double)k;
-        }
-        T.near_a[(size_t)k] = a;
-        T.near_b[(size_t)k] = H * a;
-    }
+    T.near_a.assign(ca.begin(), ca.begin() + deg + 1);
+    T.near_b.assign(cb.begin(), cb.begin() + deg + 1);
     auto finite = [](const std::vector<double2>& v) {
         for (const double2& z : v)
             if (!std::isfinite(z.x) || !std::isfinite(z.y)) return false;

@@ -55,6 +55,22 @@ def test_cloud_matches_oracle(lam, P):
     plan.close()
 
 
+@pytest.mark.parametrize("lam", [2.0, 10.0, 60.0])
+def test_float_float_near_field_matches_fp64(lam):
+    # the default near field (float-float on the FP32 pipes, FP32 series tails)
+    # against the all-FP64 one (VP_FLAG_FP64), same P and tree
+    prob = inputs.cloud_problem(6000, 5000, ndens=1, shared=1500, seed=77)
+    f = torch.as_tensor(prob.f, device="cuda")
+    res = {}
+    for flags in (0, vp.VP_FLAG_FP64):
+        plan = make(prob, lam, p_fmm=24, leaf=64, flags=flags)
+        res[flags] = plan.eval(f).cpu().numpy()
+        plan.close()
+    err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / norm(prob, lam)[:, None]))
+    print(f"modified Helmholtz lambda={lam}: float-float vs FP64 near field {err:.2e}")
+    assert err <= 1e-12
+
+
 def test_densities_graph_and_timing():
     # several densities (one pass each), graph replay bitwise equal to the plain
     # launch sequence, phase timing names
@@ -148,5 +164,3 @@ def test_rejected_options():
         make(prob, 0.0)
     with pytest.raises(vp.VPError):  # expansion tables out of range
         make(prob, 1e-12, p_fmm=30, leaf=8)
-    with pytest.raises(vp.VPError):  # the FP64 switch is for the Laplace kernel
-        make(prob, 1.0, flags=vp.VP_FLAG_FP64)
