@@ -625,20 +625,22 @@ def main():
         mplan.eval(f1, out=mo)
         mph = mplan.phase_times()
         mplan.set_flags(vp.VP_FLAG_GRAPH)
-        # near field: per directed pair 15 + 4 * terms FP64 FLOP (distance, series
-        # Horner pair, log assembly, accumulate); measured against the FP64 peak
-        pair_flop = 15 + 4 * (int(mi.near_terms) - 1)
+        # near field in float-float on the FP32 pipes: the plan's modelled FP32
+        # operation count (per directed pair 92 + 2 (deg - m + 1) + 24 m) against the
+        # FP32 issue rate; L2P and M2P (FP64) run in the same kernel
         leaf_ms = mph.get("leaf", float("nan"))
+        near_ops = int(mi.near_ops)
         mh_leg = {"workload": prob.name + f"_modified_helmholtz_lambda2_{args.mhelm:g}", "lambda": lam,
                   "p_fmm": int(mi.p_fmm), "leaf": int(mi.leaf), "n_tgt": prob.n_tgt,
                   "value": prob.n_tgt / float(np.mean(mt)) / 1e6, "unit": UNIT,
                   "ms_per_step": float(np.mean(mt)) * 1e3, "phase_ms": mph, "overlap": movl,
                   "launches_per_eval": int(mi.last_launches), "near_terms": int(mi.near_terms),
                   "p2p_pairs": int(mi.p2p_pairs), "graph": True,
-                  "leaf_roofline": {"bound": "alu", "unit": "TFLOP/s (FP64)", "peak": FP64_PEAK_TFLOPS,
-                                    "achieved": mi.p2p_pairs * pair_flop / (leaf_ms * 1e-3) / 1e12,
-                                    "frac": mi.p2p_pairs * pair_flop / (leaf_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                                    "per_unit": f"{pair_flop} FP64 FLOP per directed source-target pair"},
+                  "leaf_roofline": {"bound": "alu", "unit": "T FP32-ops/s", "peak": FP32_OPS_PEAK,
+                                    "achieved": near_ops / (leaf_ms * 1e-3) / 1e12,
+                                    "frac": near_ops / (leaf_ms * 1e-3) / 1e12 / FP32_OPS_PEAK,
+                                    "per_unit": f"{near_ops / max(1, mi.p2p_pairs):.0f} FP32 ops per directed "
+                                                f"source-target pair (plan model)"},
                   "candidates": table}
         if not args.no_cpu:
             rec, err = cpu_baseline_mhelm(prob, lam, mo_host)

@@ -268,6 +268,9 @@ typedef struct {
     int32_t kernel;         /* VP_KERNEL_*                                                 */
     int32_t near_terms;     /* modified Helmholtz: terms of the near-field series (0 otherwise) */
     double lambda;          /* modified-Helmholtz parameter (0 for Laplace)                */
+    int64_t near_ops;       /* modified Helmholtz: modelled FP32 operations of the float-float
+                               near field per density (about 92 + 2 (deg - m + 1) + 24 m per
+                               directed pair, deg and m the leaf's series degree and split) */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);

@@ -419,6 +419,7 @@ struct vp_plan_s {
     int64_t last_launches = 0;
     int kernel = VP_KERNEL_LAPLACE;
     DevMH mh;                   // modified-Helmholtz tables (kernel == VP_KERNEL_MHELMHOLTZ)
+    int64_t mh_near_ops = 0;    // modelled FP32 operations of its float-float near field
     bool alive = true;
 
     template <typename T>
@@ -1166,6 +1167,20 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     MhTables T;
     const std::string err = make_mh_tables(p->P, lambda, R, dmax, T);
     if (!err.empty()) return fail(VP_ERR_ARG, err);
+    // FP32 operations of the float-float near field per evaluation (one density):
+    // per directed pair about 92 + 2 (deg - m + 1) + 24 m (distance, table log, T,
+    // FP32 tails, float-float heads, K0, accumulate) for the leaf's (deg, m)
+    p->mh_near_ops = 0;
+    for (int32_t b : B.leaves) {
+        int64_t srcs = 0;
+        for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
+            const int32_t a = B.u_idx[(size_t)e2];
+            srcs += B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
+        }
+        const int code = T.leaf_deg[(size_t)b], deg = code & 0xff, m = code >> 8;
+        p->mh_near_ops += (int64_t)(B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b]) * srcs *
+                          (92 + 2 * (deg - m + 1) + 24 * m);
+    }
     cudaError_t e = cudaSuccess;
     double *d_spow = nullptr, *d_na = nullptr, *d_nb = nullptr;
     double2 *d_tm = nullptr, *d_tl = nullptr, *d_tv = nullptr;
@@ -1700,6 +1715,7 @@ vp_status vp_plan_info(vp_plan p, vp_plan_stats* o)
     o->kernel = p->kernel;
     o->near_terms = p->kernel == VP_KERNEL_MHELMHOLTZ ? p->mh.near_deg + 1 : 0;
     o->lambda = p->kernel == VP_KERNEL_MHELMHOLTZ ? p->mh.lambda : 0.0;
+    o->near_ops = p->kernel == VP_KERNEL_MHELMHOLTZ ? p->mh_near_ops : 0;
     return VP_OK;
 }
 

@@ -66,7 +66,7 @@ class vp_plan_stats(ctypes.Structure):
                 ("n_problems", ctypes.c_int64), ("root", ctypes.c_double * 3), ("n_f", ctypes.c_int64),
                 ("n_cells", ctypes.c_int64), ("sym_slots", ctypes.c_int64),
                 ("p2p_evals", ctypes.c_int64), ("kernel", ctypes.c_int32), ("near_terms", ctypes.c_int32),
-                ("lam", ctypes.c_double)]
+                ("lam", ctypes.c_double), ("near_ops", ctypes.c_int64)]
 
 
 VP_UPS_DENSE = 0
