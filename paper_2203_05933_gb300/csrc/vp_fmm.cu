@@ -1010,13 +1010,6 @@ __global__ void __launch_bounds__(kLeafThreads)
 // Absolute error of one log r2 is below about 3e-12; the result is converted
 // to FP64 once per target and combined with the leaf-size term
 // log(side) * (sum of the U-list charges minus coincident ones).
-namespace fflog {
-
-constexpr float kLn2Hi = 363409.0f / 524288.0f;  // ln 2 rounded to 19 fractional bits
-constexpr float kLn2Lo = 1.0f * (float)(0.693147180559945309417232121458176568 - 363409.0 / 524288.0);
-
-}  // namespace fflog
-
 // Float-float direct sum of one target over a staged tile of charges:
 // ah + al += sum_k q_k log r_k'^2, coincident charges collected in qco.
 // EXACT: the hi parts of target and source differ exactly in float.

@@ -133,8 +133,8 @@ struct DevMH {
     const double* near_a = nullptr;  // [near_deg + 1] 1/(k!)^2
     const double* near_b = nullptr;  // [near_deg + 1] H_k/(k!)^2
     const double* spow = nullptr;    // [nlevels][P1] sigma_l^k
-    const double2* Tm = nullptr;     // [nlevels][4][2P+1][P1] M2M into a parent of level l
-    const double2* Tl = nullptr;     // [nlevels][4][2P+1][P1] L2L into a child of level l
+    const double2* Tm = nullptr;     // [nlevels][4][P1][2][P1] M2M into a parent of level l (terms j, -j folded)
+    const double2* Tl = nullptr;     // [nlevels][4][P1][2][P1] L2L into a child of level l (terms m, -m folded)
     const double2* Tv = nullptr;     // [nlevels][49][3P+1] M2L, K_n(v) for n = -2P..P
 };
 

@@ -135,7 +135,7 @@ template <int P>
 __global__ void __launch_bounds__(kWarps * 32)
     k_m2m_mh(DevTree t, DevMH mh, int l, int b0, int b1, double2* __restrict__ M)
 {
-    constexpr int P1 = P + 1, NJ = 2 * P + 1;
+    constexpr int P1 = P + 1;
     __shared__ double2 Ms[kWarps][P1];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     for (int b = b0 + gwarp(); b < b1; b += nwarps()) {
@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(kWarps * 32)
             __syncwarp();
             const int cq = (t.ixy[2 * ch] & 1) | ((t.ixy[2 * ch + 1] & 1) << 1);
             if (lane <= P) {
-                const double2* T = mh.Tm + ((int64_t)(l * 4 + cq) * NJ) * P1 + lane;
-                for (int j = -P; j <= P; ++j) {
-                    const double2 m = j >= 0 ? Ms[wb][j] : conj2(Ms[wb][-j]);
-                    acc = cfma(T[(j + P) * P1], m, acc);
+                const double2* T = mh.Tm + ((int64_t)(l * 4 + cq) * 2 * P1) * P1 + lane;
+                for (int j = 0; j <= P; ++j) {
+                    const double2 m = Ms[wb][j], u = T[2 * j * P1], v = T[(2 * j + 1) * P1];
+                    acc.x = fma(m.x, u.x, fma(m.y, u.y, acc.x));
+                    acc.y = fma(m.x, v.x, fma(m.y, v.y, acc.y));
                 }
             }
             __syncwarp();
@@ -166,7 +167,7 @@ template <int P>
 __global__ void __launch_bounds__(kWarps * 32)
     k_l2l_mh(DevTree t, DevMH mh, int l, int b0, int b1, double2* __restrict__ L)
 {
-    constexpr int P1 = P + 1, NJ = 2 * P + 1;
+    constexpr int P1 = P + 1;
     __shared__ double2 Ls[kWarps][P1];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     for (int b = b0 + gwarp(); b < b1; b += nwarps()) {
@@ -175,11 +176,12 @@ __global__ void __launch_bounds__(kWarps * 32)
         __syncwarp();
         const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
         if (lane <= P) {
-            const double2* T = mh.Tl + ((int64_t)(l * 4 + cq) * NJ) * P1 + lane;
+            const double2* T = mh.Tl + ((int64_t)(l * 4 + cq) * 2 * P1) * P1 + lane;
             double2 acc = make_double2(0.0, 0.0);
-            for (int m = -P; m <= P; ++m) {
-                const double2 v = m >= 0 ? Ls[wb][m] : conj2(Ls[wb][-m]);
-                acc = cfma(T[(m + P) * P1], v, acc);
+            for (int m = 0; m <= P; ++m) {
+                const double2 c = Ls[wb][m], u = T[2 * m * P1], v = T[(2 * m + 1) * P1];
+                acc.x = fma(c.x, u.x, fma(c.y, u.y, acc.x));
+                acc.y = fma(c.x, v.x, fma(c.y, v.y, acc.y));
             }
             const int64_t i = (int64_t)b * P1 + lane;
             const double2 o = L[i];
@@ -638,8 +640,7 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
     const int P1 = P + 1, NJ = 2 * P + 1, NT = 3 * P + 1;
     const int nl = (int)R_level.size();
     T.spow.assign((size_t)nl * P1, 0.0);
-    T.Tm.assign((size_t)nl * 4 * NJ * P1, d2(0.0, 0.0));
-    T.Tl.assign((size_t)nl * 4 * NJ * P1, d2(0.0, 0.0));
+    std::vector<double2> fullM((size_t)nl * 4 * NJ * P1, d2(0.0, 0.0)), fullL(fullM);
     T.Tv.assign((size_t)nl * 49 * NT, d2(0.0, 0.0));
     // 1/m! and h_m(y_d) for the child offset d (|d| = sqrt(2) R_child, y_d = sigma_child^2 / 2)
     std::vector<double> inv_fact((size_t)3 * P + 2, 1.0);
@@ -665,7 +666,7 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
             for (int a = 0; a <= 2 * P; ++a) h[(size_t)a] = bessel::h_series(a, yd, inv_fact[(size_t)a]);
             for (int cq = 0; cq < 4; ++cq) {
                 const double th = std::atan2((cq & 2) ? 1.0 : -1.0, (cq & 1) ? 1.0 : -1.0);
-                double2* dst = (pass == 0 ? T.Tm.data() : T.Tl.data()) + (size_t)(l * 4 + cq) * NJ * P1;
+                double2* dst = (pass == 0 ? fullM.data() : fullL.data()) + (size_t)(l * 4 + cq) * NJ * P1;
                 for (int j = -P; j <= P; ++j) {
                     for (int n = 0; n <= P; ++n) {
                         double mag, ang;
@@ -688,6 +689,30 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
             }
         }
     }
+    // With real charges the coefficient of index -j is the conjugate of that of j, so
+    // the terms j and -j fold into one real 2x2 product per j >= 0: for entries
+    // T_j = p + iq, T_-j = r + is and a coefficient a + ib,
+    //   T_j (a + ib) + T_-j (a - ib) = a (p + r) + b (s - q) + i (a (q + s) + b (p - r)),
+    // stored as (p + r, s - q), (q + s, p - r) per (j, n); j = 0 is the plain product.
+    auto fold = [&](const std::vector<double2>& full, std::vector<double2>& out) {
+        out.assign((size_t)nl * 4 * 2 * P1 * P1, d2(0.0, 0.0));
+        for (size_t lq = 0; lq < (size_t)nl * 4; ++lq)
+            for (int j = 0; j <= P; ++j)
+                for (int n = 0; n <= P; ++n) {
+                    const double2 a = full[(lq * NJ + (size_t)(j + P)) * P1 + n];
+                    const double2 b = j > 0 ? full[(lq * NJ + (size_t)(P - j)) * P1 + n] : d2(0.0, 0.0);
+                    double2* o = out.data() + (lq * 2 * P1 + 2 * (size_t)j) * P1 + n;
+                    if (j == 0) {
+                        o[0] = d2(a.x, -a.y);
+                        o[P1] = d2(a.y, a.x);
+                    } else {
+                        o[0] = d2(a.x + b.x, b.y - a.y);
+                        o[P1] = d2(a.y + b.y, a.x - b.x);
+                    }
+                }
+    };
+    fold(fullM, T.Tm);
+    fold(fullL, T.Tl);
     // M2L: K_n(v), n = -2P..P, v = c_target - c_source = -2 R_l (ox + i oy)
     std::vector<double> K((size_t)2 * P + 1);
     for (int l = 2; l < nl; ++l) {

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(kUpsThreads)
         }
         __syncthreads();
         if (kind == 1) {
-            const int qa = ti[3], pa = ti[4], qb = ti[5], pb = ti[6];
+            const int pa = ti[4], qb = ti[5], pb = ti[6];  // ti[3] = qa enters through nq = qa qb
             const double* A = u.mats + u.toff[2 * t];
             const double* B = u.mats + u.toff[2 * t + 1];
             // tmp[d][ia][rb] = sum_ib B[rb][ib] f[d][ia][ib]
