@@ -1439,16 +1439,18 @@ __global__ void k_sym_reduce(DevTree t, PassGeom g, const float2* __restrict__ s
         const int s0 = t.sym_in_ptr[A], s1 = t.sym_in_ptr[A + 1];
         if (s0 == s1) continue;
         const int jl = j - g.erng[2 * A];
-        double acc[ND];
+        // float-float sums on the FP32 pipes (conversions to FP64 would occupy the
+        // FP64 pipe once per slot), converted once per point
+        ff::F acc[ND];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+        for (int d = 0; d < ND; ++d) acc[d] = ff::F{0.f, 0.f};
 #pragma unroll 4
         for (int k = s0; k < s1; ++k) {
             const int64_t o = (t.sym_in_slot[k] + jl) * ND;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 const float2 v = slots[o + d];
-                acc[d] += (double)v.x + (double)v.y;
+                acc[d] = ff::add(acc[d], ff::F{v.x, v.y});
             }
         }
         double cst[ND];
@@ -1464,7 +1466,7 @@ __global__ void k_sym_reduce(DevTree t, PassGeom g, const float2* __restrict__ s
             }
         }
 #pragma unroll
-        for (int d = 0; d < ND; ++d) psi[(int64_t)j * ND + d] += fma(0.5, acc[d], cst[d]);
+        for (int d = 0; d < ND; ++d) psi[(int64_t)j * ND + d] += fma(0.5, ff::to_double(acc[d]), cst[d]);
     }
 }
 

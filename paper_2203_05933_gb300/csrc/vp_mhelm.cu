@@ -360,7 +360,7 @@ __device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restric
 // block per leaf, one target per thread. FF: the near field in float-float on
 // the FP32 pipes (mh_tile); else in FP64.
 template <int P, bool FF>
-__global__ void __launch_bounds__(kMhLeafThreads)
+__global__ void __launch_bounds__(kMhLeafThreads, 8)
     k_leaf_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
               const double2* __restrict__ M, const double2* __restrict__ L, const float4* __restrict__ logtab,
               double* __restrict__ psi)
