@@ -135,7 +135,7 @@ struct DevMH {
     const double* spow = nullptr;    // [nlevels][P1] sigma_l^k
     const double2* Tm = nullptr;     // [nlevels][4][P1][2][P1] M2M into a parent of level l (terms j, -j folded)
     const double2* Tl = nullptr;     // [nlevels][4][P1][2][P1] L2L into a child of level l (terms m, -m folded)
-    const double2* Tv = nullptr;     // [nlevels][49][3P+1] M2L, K_n(v) for n = -2P..P
+    const double2* Tv = nullptr;     // [nlevels][49][P1][2][P1] M2L on scaled coefficients (k, -k folded)
 };
 
 struct MhTables {

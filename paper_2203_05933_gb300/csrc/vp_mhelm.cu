@@ -18,7 +18,8 @@
 // Stored coefficients are scaled by sigma = lambda R (R the box half side):
 // M_n = M'_n / sigma^n, L_m = L'_m sigma^m, n, m = 0..P, which keeps them O(1)
 // for every box size. Per level the operators are fixed (four child quadrants,
-// 49 source-box offsets), so M2M, L2L and M2L read plan-time tables.
+// 49 source-box offsets), so M2M, L2L and M2L read plan-time tables, with the
+// orders n and -n folded into one real 2x2 product per n (real charges).
 //
 // Near field (direct sum over the U list): with y = lambda^2 r^2 / 4,
 //   K0 = I0(y) (-log(r^2)/2 - log(lambda/2) - gamma) + sum_{k>=1} H_k y^k / (k!)^2,
@@ -46,7 +47,7 @@ namespace {
 
 constexpr int kWarps = 4;
 constexpr int kMhChunk = 16;        // charges staged per step in P2M / P2L
-constexpr int kMhLeafThreads = 128; // one target per thread in the leaf kernel
+constexpr int kMhLeafThreads = 64;  // one target per thread in the leaf kernel (two warps: a leaf of 64 keeps all lanes busy)
 constexpr int kMaxNearTerms = 16;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
@@ -59,8 +60,6 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
 {
     return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
-
-__device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 
 __device__ __forceinline__ int gwarp() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 __device__ __forceinline__ int nwarps() { return (int)((gridDim.x * blockDim.x) >> 5); }
@@ -199,9 +198,8 @@ __global__ void __launch_bounds__(kWarps * 32)
     k_m2l_mh(DevTree t, DevMH mh, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
              const double* __restrict__ q)
 {
-    constexpr int P1 = P + 1, NT = 3 * P + 1;
+    constexpr int P1 = P + 1;
     __shared__ double2 Ms[kWarps][P1];
-    __shared__ double2 Ts[kWarps][NT];
     __shared__ double2 pw[kWarps][kMhChunk][P1];
     __shared__ double qs[kWarps][kMhChunk];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
@@ -209,29 +207,26 @@ __global__ void __launch_bounds__(kWarps * 32)
         const int lev = t.level[b];
         const double* sp = mh.spow + lev * P1;
         const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
-        double2 vacc = make_double2(0.0, 0.0);
+        double2 lacc = make_double2(0.0, 0.0);
         const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
         for (int e = v0; e < v1; ++e) {
             const int C = t.v_idx[e];
             const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
-            if (lane <= P) {
-                const double2 m = M[(int64_t)C * P1 + lane];
-                Ms[wb][lane] = make_double2(m.x * sp[lane], m.y * sp[lane]);  // M'_k = sigma^k M_k
-            }
-            const double2* T = mh.Tv + ((int64_t)lev * 49 + o) * NT;
-            for (int i = lane; i < NT; i += 32) Ts[wb][i] = T[i];
+            if (lane <= P) Ms[wb][lane] = M[(int64_t)C * P1 + lane];
             __syncwarp();
             if (lane <= P) {
-                double2 s = make_double2(0.0, 0.0);
-                for (int k = 0; k <= P; ++k) s = cfma(Ts[wb][k - lane + 2 * P], Ms[wb][k], s);
-                for (int k = 1; k <= P; ++k) s = cfma(Ts[wb][-k - lane + 2 * P], conj2(Ms[wb][k]), s);
-                if (lane & 1) s = make_double2(-s.x, -s.y);
-                vacc = make_double2(vacc.x + s.x, vacc.y + s.y);
+                // the level's operator for this offset, acting on the scaled M and giving
+                // the scaled L, with the orders k and -k folded (real 2x2 per k)
+                const double2* T = mh.Tv + ((int64_t)(lev * 49 + o) * P1) * 2 * P1 + lane;
+#pragma unroll 5
+                for (int k = 0; k <= P; ++k) {
+                    const double2 m = Ms[wb][k], u = T[2 * k * P1], v = T[(2 * k + 1) * P1];
+                    lacc.x = fma(m.x, u.x, fma(m.y, u.y, lacc.x));
+                    lacc.y = fma(m.x, v.x, fma(m.y, v.y, lacc.y));
+                }
             }
             __syncwarp();
         }
-        double2 lacc = make_double2(0.0, 0.0);
-        if (lane <= P) lacc = make_double2(vacc.x * sp[lane], vacc.y * sp[lane]);
         const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
         if (x1 > x0) {
             const double2 c = t.center[b];
@@ -360,7 +355,7 @@ __device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restric
 // block per leaf, one target per thread. FF: the near field in float-float on
 // the FP32 pipes (mh_tile); else in FP64.
 template <int P, bool FF>
-__global__ void __launch_bounds__(kMhLeafThreads, 8)
+__global__ void __launch_bounds__(kMhLeafThreads, 16)
     k_leaf_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
               const double2* __restrict__ M, const double2* __restrict__ L, const float4* __restrict__ logtab,
               double* __restrict__ psi)
@@ -563,7 +558,7 @@ cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, cons
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
-    const int blocks = std::max(1, std::min(t.nleaf, 152 * 16));
+    const int blocks = std::max(1, std::min(t.nleaf, 152 * 32));
     if (fp64)
         k_leaf_mh<P, false><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab, ws.psi);
     else
@@ -637,11 +632,11 @@ int near_split(int deg, double ymax, double lambda, double c0, const std::vector
 std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,
                            const std::vector<double>& leaf_dmax, MhTables& T)
 {
-    const int P1 = P + 1, NJ = 2 * P + 1, NT = 3 * P + 1;
+    const int P1 = P + 1, NJ = 2 * P + 1;
     const int nl = (int)R_level.size();
     T.spow.assign((size_t)nl * P1, 0.0);
     std::vector<double2> fullM((size_t)nl * 4 * NJ * P1, d2(0.0, 0.0)), fullL(fullM);
-    T.Tv.assign((size_t)nl * 49 * NT, d2(0.0, 0.0));
+    T.Tv.assign((size_t)nl * 49 * 2 * P1 * P1, d2(0.0, 0.0));
     // 1/m! and h_m(y_d) for the child offset d (|d| = sqrt(2) R_child, y_d = sigma_child^2 / 2)
     std::vector<double> inv_fact((size_t)3 * P + 2, 1.0);
     for (size_t m = 1; m < inv_fact.size(); ++m) inv_fact[m] = inv_fact[m - 1] / (double)m;
@@ -713,10 +708,13 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
     };
     fold(fullM, T.Tm);
     fold(fullL, T.Tl);
-    // M2L: K_n(v), n = -2P..P, v = c_target - c_source = -2 R_l (ox + i oy)
+    // M2L per level and source-box offset (ox, oy) = ixy_source - ixy_target, on the
+    // scaled coefficients: L_m = sum_k (-1)^m sigma^(m + |k|) K_{k-m}(v) M_k (k < 0:
+    // conj(M_|k|)), v = c_target - c_source = -2 R_l (ox + i oy), folded as above
     std::vector<double> K((size_t)2 * P + 1);
+    std::vector<double2> A((size_t)P1 * NJ);
     for (int l = 2; l < nl; ++l) {
-        const double R = R_level[(size_t)l];
+        const double R = R_level[(size_t)l], sig = lambda * R;
         for (int oy = -3; oy <= 3; ++oy)
             for (int ox = -3; ox <= 3; ++ox) {
                 if (std::abs(ox) <= 1 && std::abs(oy) <= 1) continue;
@@ -728,11 +726,26 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
                 K[0] = k0;
                 K[1] = k1;
                 for (int n = 1; n < 2 * P; ++n) K[(size_t)n + 1] = K[(size_t)n - 1] + (2.0 * n / x) * K[(size_t)n];
-                double2* dst = T.Tv.data() + ((size_t)l * 49 + (size_t)((oy + 3) * 7 + ox + 3)) * NT;
-                for (int n = -2 * P; n <= P; ++n) {
-                    const double kn = K[(size_t)std::abs(n)];
-                    dst[(size_t)(n + 2 * P)] = d2(kn * std::cos(n * th), kn * std::sin(n * th));
-                }
+                for (int m = 0; m <= P; ++m)
+                    for (int k = -P; k <= P; ++k) {
+                        const int n = k - m;
+                        const double mag = ((m & 1) ? -1.0 : 1.0) * std::pow(sig, m + std::abs(k)) * K[(size_t)std::abs(n)];
+                        A[(size_t)m * NJ + (size_t)(k + P)] = d2(mag * std::cos(n * th), mag * std::sin(n * th));
+                    }
+                double2* dst = T.Tv.data() + ((size_t)l * 49 + (size_t)((oy + 3) * 7 + ox + 3)) * 2 * P1 * P1;
+                for (int k = 0; k <= P; ++k)
+                    for (int m = 0; m <= P; ++m) {
+                        const double2 a = A[(size_t)m * NJ + (size_t)(k + P)];
+                        const double2 b = k > 0 ? A[(size_t)m * NJ + (size_t)(P - k)] : d2(0.0, 0.0);
+                        double2* o = dst + 2 * (size_t)k * P1 + m;
+                        if (k == 0) {
+                            o[0] = d2(a.x, -a.y);
+                            o[P1] = d2(a.y, a.x);
+                        } else {
+                            o[0] = d2(a.x + b.x, b.y - a.y);
+                            o[P1] = d2(a.y + b.y, a.x - b.x);
+                        }
+                    }
             }
     }
     // near-field series: per leaf, the terms its largest near-field distance needs
