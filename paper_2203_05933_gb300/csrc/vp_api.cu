@@ -270,13 +270,14 @@ struct HostGroups {
     std::vector<int32_t> g_r0;
     std::vector<int64_t> g_c0;
     std::vector<int32_t> cols;
-    std::vector<int64_t> rowptr;  // row starts in vf (rows padded to even lengths)
-    std::vector<float> vf;
+    std::vector<int64_t> rowptr;  // row starts in vf / vd (rows padded to even lengths)
+    std::vector<float> vf;        // values as hi/lo floats (passes of several densities)
+    std::vector<double> vd;       // values in FP64 (passes of one density)
     int32_t max_m = 0;
 };
 
 void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
-                  const std::vector<double>& val, HostGroups& G)
+                  const std::vector<double>& val, bool with_ff, HostGroups& G)
 {
     int64_t start = -1;
     for (int64_t i = 0; i < nrows; ++i) {
@@ -304,10 +305,13 @@ void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::
         const int64_t len = rowptr[(size_t)i + 1] - rowptr[(size_t)i];
         G.rowptr[(size_t)i + 1] = G.rowptr[(size_t)i] + len + (len & 1);
     }
-    G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
+    G.vd.assign((size_t)G.rowptr[(size_t)nrows], 0.0);
+    if (with_ff) G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
     for (int64_t i = 0; i < nrows; ++i)
         for (int64_t k = rowptr[(size_t)i]; k < rowptr[(size_t)i + 1]; ++k) {
             const size_t o = (size_t)(G.rowptr[(size_t)i] + (k - rowptr[(size_t)i]));
+            G.vd[o] = val[(size_t)k];
+            if (!with_ff) continue;
             const float h = (float)val[(size_t)k];
             G.vf[2 * o] = h;
             G.vf[2 * o + 1] = (float)(val[(size_t)k] - (double)h);
@@ -1013,16 +1017,20 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             HostGroups G;
             const bool fwd = pass == 0;
             const int64_t nrows = fwd ? n_tgt : n_cols;
-            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, G);
+            // FP64 values for passes of one density; hi/lo floats as well when the
+            // plan evaluates several densities per pass
+            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, p->nd_cap > 1, G);
             DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
             int32_t *d_r0 = nullptr, *d_cols = nullptr;
             int64_t *d_c0 = nullptr, *d_rp = nullptr;
             float* d_vf = nullptr;
+            double* d_vd = nullptr;
             up(&d_r0, G.g_r0);
             up(&d_c0, G.g_c0);
             up(&d_cols, G.cols);
             up(&d_rp, G.rowptr);
-            up(&d_vf, G.vf);
+            if (p->nd_cap > 1) up(&d_vf, G.vf);
+            up(&d_vd, G.vd);
             A.nrows = (int32_t)nrows;
             A.ngroups = (int32_t)G.g_r0.size() - 1;
             A.max_m = G.max_m;
@@ -1031,6 +1039,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             A.cols = d_cols;
             A.rowptr = d_rp;
             A.vf = (const float2*)d_vf;
+            A.vd = d_vd;
         }
     }
     const int P1 = P + 1;
@@ -1113,7 +1122,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.Blf = (const float2*)(d_fftab + offf[6]);
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
-                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off};
+                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
+                           p->gfwd.vd, p->gadj.vd};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
                           p->gfwd.vf, p->gadj.vf};
     bool ok = true;
@@ -1442,6 +1452,25 @@ extern "C" {
 
 namespace {
 
+// Grouped correction product of one density chunk: out = A x (mode as in
+// launch_out_grouped), x in caller order with leading dimension ld_x. One
+// density: the FP64 kernel straight on x; several: float-float after a
+// conversion pass. Counts its launches.
+vp_status grouped_apply(vp_plan p, int nd, const DevGroupedCSR& A, int64_t ncols, const int32_t* inv,
+                        const double* w, const double* psi, const double* x, int64_t ld_x, double* out,
+                        int64_t ld_out, int mode, int max_blocks, cudaStream_t s)
+{
+    if (nd == 1) {
+        VP_CUDA(launch_out_grouped64(A, inv, w, psi, x, out, mode, max_blocks, s));
+        p->last_launches += 1;
+        return VP_OK;
+    }
+    VP_CUDA(launch_to_ff_rows(nd, (int32_t)ncols, x, ld_x, p->ws.xf, s));
+    VP_CUDA(launch_out_grouped(nd, A, inv, w, psi, p->ws.xf, ncols, out, ld_out, mode, max_blocks, s));
+    p->last_launches += 2;
+    return VP_OK;
+}
+
 // The FMM of one density chunk for the plan's kernel (psi in tree order).
 cudaError_t run_fmm(vp_plan p, int nd, const PassGeom& g, bool gradient, PhaseTimer* tm, cudaStream_t s)
 {
@@ -1464,10 +1493,11 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         // level from level 2 up), M2L, L2L per level from level 3 down, leaf (+ slot
         // reduction), output
         const bool ffp = !use_fp64(p);
+        // (the output launches are counted where they are made)
         if (p->kernel == VP_KERNEL_MHELMHOLTZ)
-            p->last_launches += 2 + mhelm_launches(p->dt.nlevels);
+            p->last_launches += 1 + mhelm_launches(p->dt.nlevels);
         else
-            p->last_launches += 5 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
+            p->last_launches += 4 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
                                 (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);
         const double* fc = f + (int64_t)d0 * ld_f;
         double* oc = out + (int64_t)d0 * ld_out;
@@ -1477,11 +1507,10 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         if (overlap) {
             VP_CUDA(cudaEventRecord(p->ev_fork, s));
             VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-            VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, p->side));
-            VP_CUDA(launch_out_grouped(nd, p->gfwd, nullptr, nullptr, nullptr, p->ws.xf, p->n_f, oc, ld_out,
-                                       kOutOverwrite, p->side_blocks, p->side));
+            const vp_status st = grouped_apply(p, nd, p->gfwd, p->n_f, nullptr, nullptr, nullptr, fc, ld_f, oc,
+                                               ld_out, kOutOverwrite, p->side_blocks, p->side);
+            if (st != VP_OK) return st;
             VP_CUDA(cudaEventRecord(p->ev_join, p->side));
-            p->last_launches += 2;
         }
         int id = p->timer.begin("charges");
         if (p->ups)
@@ -1494,14 +1523,15 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         if (overlap) {
             VP_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
             VP_CUDA(launch_add_psi(nd, (int32_t)p->n_tgt, p->tgt_inv, nullptr, p->ws.psi, oc, ld_out, s));
-        } else if (p->grouped) {
-            VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_f, fc, ld_f, p->ws.xf, s));
-            VP_CUDA(launch_out_grouped(nd, p->gfwd, p->tgt_inv, nullptr, p->ws.psi, p->ws.xf, p->n_f, oc, ld_out,
-                                       kOutWithPsi, 0, s));
             p->last_launches += 1;
+        } else if (p->grouped) {
+            const vp_status st = grouped_apply(p, nd, p->gfwd, p->n_f, p->tgt_inv, nullptr, p->ws.psi, fc, ld_f, oc,
+                                               ld_out, kOutWithPsi, 0, s);
+            if (st != VP_OK) return st;
         } else {
             VP_CUDA(launch_out_forward(nd, (int32_t)p->n_tgt, p->tgt_inv, p->ws.psi, p->rowptr, p->col, p->val, fc,
                                        ld_f, out + (int64_t)d0 * ld_out, ld_out, s));
+            p->last_launches += 1;
         }
         p->timer.end(id);
         d0 += nd;
@@ -1593,6 +1623,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
     if (ndens == 0) return VP_OK;
     p->timer.stream = s;
     p->timer.used = 0;
+    const int64_t fwd_launches = p->last_launches;  // the stats report the last vp_eval
     if (grad_f && p->n_f > 0) {
         PassGeom gg = adjoint_geom(p);
         for (int d0 = 0; d0 < ndens;) {
@@ -1604,9 +1635,9 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             if (overlap) {
                 VP_CUDA(cudaEventRecord(p->ev_fork, s));
                 VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-                VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, p->side));
-                VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc0, ld_gf,
-                                           kOutOverwrite, p->side_blocks, p->side));
+                const vp_status st = grouped_apply(p, nd, p->gadj, p->n_tgt, nullptr, nullptr, nullptr, gc, ld_g,
+                                                   gfc0, ld_gf, kOutOverwrite, p->side_blocks, p->side);
+                if (st != VP_OK) return st;
                 VP_CUDA(cudaEventRecord(p->ev_join, p->side));
             }
             VP_CUDA(launch_charges(nd, (int32_t)p->n_tgt, p->tgt_perm, nullptr, gc, ld_g, p->ws.q, p->ws.qf, s));
@@ -1619,17 +1650,17 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                 double* gfc = grad_f + (int64_t)d0 * ld_gf;
                 VP_CUDA(launch_ups_adjoint(nd, p->dups, p->src_inv, p->w_sorted, p->ws.psi, gfc, ld_gf, s));
                 if (p->grouped) {
-                    VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
-                    VP_CUDA(launch_out_grouped(nd, p->gadj, nullptr, nullptr, nullptr, p->ws.xf, p->n_tgt, gfc, ld_gf,
-                                               kOutAccumulate, 0, s));
+                    const vp_status st = grouped_apply(p, nd, p->gadj, p->n_tgt, nullptr, nullptr, nullptr, gc, ld_g,
+                                                       gfc, ld_gf, kOutAccumulate, 0, s);
+                    if (st != VP_OK) return st;
                 } else if (p->cptr) {
                     VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_f, nullptr, nullptr, nullptr, p->cptr, p->crow,
                                                p->cval, gc, ld_g, gfc, ld_gf, s));
                 }
             } else if (p->grouped) {
-                VP_CUDA(launch_to_ff_rows(nd, (int32_t)p->n_tgt, gc, ld_g, p->ws.xf, s));
-                VP_CUDA(launch_out_grouped(nd, p->gadj, p->src_inv, p->w_sorted, p->ws.psi, p->ws.xf, p->n_tgt,
-                                           grad_f + (int64_t)d0 * ld_gf, ld_gf, kOutWithPsi, 0, s));
+                const vp_status st = grouped_apply(p, nd, p->gadj, p->n_tgt, p->src_inv, p->w_sorted, p->ws.psi, gc,
+                                                   ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, kOutWithPsi, 0, s);
+                if (st != VP_OK) return st;
             } else {
                 VP_CUDA(launch_out_adjoint(nd, (int32_t)p->n_src, p->src_inv, p->w_sorted, p->ws.psi, p->cptr,
                                            p->crow, p->cval, gc, ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, s));
@@ -1653,6 +1684,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             d0 += nd;
         }
     }
+    p->last_launches = fwd_launches;
     return VP_OK;
 }
 
