@@ -626,8 +626,9 @@ def main():
         mph = mplan.phase_times()
         mplan.set_flags(vp.VP_FLAG_GRAPH)
         # near field in float-float on the FP32 pipes: the plan's modelled FP32
-        # operation count (per directed pair 92 + 2 (deg - m + 1) + 24 m) against the
-        # FP32 issue rate; L2P and M2P (FP64) run in the same kernel
+        # operation count (per evaluated distance 92 + 2 (deg - m + 1) + 24 m, +14 when
+        # it serves both directions) against the FP32 issue rate; L2P and M2P (FP64)
+        # run in the same kernel
         leaf_ms = mph.get("leaf", float("nan"))
         near_ops = int(mi.near_ops)
         mh_leg = {"workload": prob.name + f"_modified_helmholtz_lambda2_{args.mhelm:g}", "lambda": lam,
@@ -639,8 +640,9 @@ def main():
                   "leaf_roofline": {"bound": "alu", "unit": "T FP32-ops/s", "peak": FP32_OPS_PEAK,
                                     "achieved": near_ops / (leaf_ms * 1e-3) / 1e12,
                                     "frac": near_ops / (leaf_ms * 1e-3) / 1e12 / FP32_OPS_PEAK,
-                                    "per_unit": f"{near_ops / max(1, mi.p2p_pairs):.0f} FP32 ops per directed "
-                                                f"source-target pair (plan model)"},
+                                    "per_unit": f"{near_ops / max(1, mi.p2p_evals):.0f} FP32 ops per evaluated "
+                                                f"distance (plan model; {int(mi.p2p_evals)} evaluations for "
+                                                f"{int(mi.p2p_pairs)} directed pairs)"},
                   "candidates": table}
         if not args.no_cpu:
             rec, err = cpu_baseline_mhelm(prob, lam, mo_host)

@@ -270,7 +270,8 @@ typedef struct {
     double lambda;          /* modified-Helmholtz parameter (0 for Laplace)                */
     int64_t near_ops;       /* modified Helmholtz: modelled FP32 operations of the float-float
                                near field per density (about 92 + 2 (deg - m + 1) + 24 m per
-                               directed pair, deg and m the leaf's series degree and split) */
+                               evaluated distance, deg and m the leaf's series degree and
+                               split, +14 where one evaluation serves both directions) */
 } vp_plan_stats;
 
 vp_status vp_plan_info(vp_plan plan, vp_plan_stats* out);

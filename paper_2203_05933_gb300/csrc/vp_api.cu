@@ -270,14 +270,13 @@ struct HostGroups {
     std::vector<int32_t> g_r0;
     std::vector<int64_t> g_c0;
     std::vector<int32_t> cols;
-    std::vector<int64_t> rowptr;  // row starts in vf / vd (rows padded to even lengths)
-    std::vector<float> vf;        // values as hi/lo floats (passes of several densities)
-    std::vector<double> vd;       // values in FP64 (passes of one density)
+    std::vector<int64_t> rowptr;  // row starts in vf (rows padded to even lengths)
+    std::vector<float> vf;
     int32_t max_m = 0;
 };
 
 void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
-                  const std::vector<double>& val, bool with_ff, HostGroups& G)
+                  const std::vector<double>& val, HostGroups& G)
 {
     int64_t start = -1;
     for (int64_t i = 0; i < nrows; ++i) {
@@ -305,13 +304,10 @@ void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::
         const int64_t len = rowptr[(size_t)i + 1] - rowptr[(size_t)i];
         G.rowptr[(size_t)i + 1] = G.rowptr[(size_t)i] + len + (len & 1);
     }
-    G.vd.assign((size_t)G.rowptr[(size_t)nrows], 0.0);
-    if (with_ff) G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
+    G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
     for (int64_t i = 0; i < nrows; ++i)
         for (int64_t k = rowptr[(size_t)i]; k < rowptr[(size_t)i + 1]; ++k) {
             const size_t o = (size_t)(G.rowptr[(size_t)i] + (k - rowptr[(size_t)i]));
-            G.vd[o] = val[(size_t)k];
-            if (!with_ff) continue;
             const float h = (float)val[(size_t)k];
             G.vf[2 * o] = h;
             G.vf[2 * o + 1] = (float)(val[(size_t)k] - (double)h);
@@ -909,7 +905,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_leaves, B.leaves);
     // symmetric near field when the charge points of both passes are the evaluation
     // points (same coordinates, same tree order) and the U lists are symmetric
-    bool sym = p->kernel == VP_KERNEL_LAPLACE && !(p->flags & VP_FLAG_FP64) && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
+    bool sym = !(p->flags & VP_FLAG_FP64) && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
     if (sym) {
         for (int32_t b : B.leaves) {
             for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1] && sym; ++e2) {
@@ -1017,20 +1013,16 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             HostGroups G;
             const bool fwd = pass == 0;
             const int64_t nrows = fwd ? n_tgt : n_cols;
-            // FP64 values for passes of one density; hi/lo floats as well when the
-            // plan evaluates several densities per pass
-            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, p->nd_cap > 1, G);
+            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, G);
             DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
             int32_t *d_r0 = nullptr, *d_cols = nullptr;
             int64_t *d_c0 = nullptr, *d_rp = nullptr;
             float* d_vf = nullptr;
-            double* d_vd = nullptr;
             up(&d_r0, G.g_r0);
             up(&d_c0, G.g_c0);
             up(&d_cols, G.cols);
             up(&d_rp, G.rowptr);
-            if (p->nd_cap > 1) up(&d_vf, G.vf);
-            up(&d_vd, G.vd);
+            up(&d_vf, G.vf);
             A.nrows = (int32_t)nrows;
             A.ngroups = (int32_t)G.g_r0.size() - 1;
             A.max_m = G.max_m;
@@ -1039,7 +1031,6 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             A.cols = d_cols;
             A.rowptr = d_rp;
             A.vf = (const float2*)d_vf;
-            A.vd = d_vd;
         }
     }
     const int P1 = P + 1;
@@ -1122,8 +1113,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.Blf = (const float2*)(d_fftab + offf[6]);
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
-                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
-                           p->gfwd.vd, p->gadj.vd};
+                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
                           p->gfwd.vf, p->gadj.vf};
     bool ok = true;
@@ -1178,18 +1168,21 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     const std::string err = make_mh_tables(p->P, lambda, R, dmax, T);
     if (!err.empty()) return fail(VP_ERR_ARG, err);
     // FP32 operations of the float-float near field per evaluation (one density):
-    // per directed pair about 92 + 2 (deg - m + 1) + 24 m (distance, table log, T,
-    // FP32 tails, float-float heads, K0, accumulate) for the leaf's (deg, m)
+    // per evaluated distance about 92 + 2 (deg - m + 1) + 24 m (distance, table log,
+    // T, FP32 tails, float-float heads, K0, accumulate) for the leaf's (deg, m), +14
+    // when the evaluation serves both directions (symmetric near field)
     p->mh_near_ops = 0;
     for (int32_t b : B.leaves) {
-        int64_t srcs = 0;
+        int64_t own = 0, both = 0;
         for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
             const int32_t a = B.u_idx[(size_t)e2];
-            srcs += B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
+            const int64_t na = B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
+            if (!p->dt.sym || a == b) own += na;
+            else if (a > b) both += na;
         }
         const int code = T.leaf_deg[(size_t)b], deg = code & 0xff, m = code >> 8;
-        p->mh_near_ops += (int64_t)(B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b]) * srcs *
-                          (92 + 2 * (deg - m + 1) + 24 * m);
+        const int64_t ops = 92 + 2 * (deg - m + 1) + 24 * m;
+        p->mh_near_ops += (int64_t)(B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b]) * (own * ops + both * (ops + 14));
     }
     cudaError_t e = cudaSuccess;
     double *d_spow = nullptr, *d_na = nullptr, *d_nb = nullptr;
@@ -1453,18 +1446,14 @@ extern "C" {
 namespace {
 
 // Grouped correction product of one density chunk: out = A x (mode as in
-// launch_out_grouped), x in caller order with leading dimension ld_x. One
-// density: the FP64 kernel straight on x; several: float-float after a
-// conversion pass. Counts its launches.
+// launch_out_grouped), x in caller order with leading dimension ld_x, converted
+// to hi/lo floats first. Counts its launches. (An FP64 form of the product, one
+// DFMA per nonzero, was measured at 1.74 ms against 0.93 ms on the 1.09 M disk,
+// and slowed the FMM beside it: the FP64 pipe is too narrow for it on GB300.)
 vp_status grouped_apply(vp_plan p, int nd, const DevGroupedCSR& A, int64_t ncols, const int32_t* inv,
                         const double* w, const double* psi, const double* x, int64_t ld_x, double* out,
                         int64_t ld_out, int mode, int max_blocks, cudaStream_t s)
 {
-    if (nd == 1) {
-        VP_CUDA(launch_out_grouped64(A, inv, w, psi, x, out, mode, max_blocks, s));
-        p->last_launches += 1;
-        return VP_OK;
-    }
     VP_CUDA(launch_to_ff_rows(nd, (int32_t)ncols, x, ld_x, p->ws.xf, s));
     VP_CUDA(launch_out_grouped(nd, A, inv, w, psi, p->ws.xf, ncols, out, ld_out, mode, max_blocks, s));
     p->last_launches += 2;
@@ -1495,7 +1484,7 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         const bool ffp = !use_fp64(p);
         // (the output launches are counted where they are made)
         if (p->kernel == VP_KERNEL_MHELMHOLTZ)
-            p->last_launches += 1 + mhelm_launches(p->dt.nlevels);
+            p->last_launches += 1 + mhelm_launches(p->dt.nlevels, p->dt.sym && ffp);
         else
             p->last_launches += 4 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
                                 (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);

@@ -100,8 +100,7 @@ struct DevGroupedCSR {
     const int64_t* g_c0 = nullptr;     // [ngroups + 1] offsets into cols
     const int32_t* cols = nullptr;     // column list of each group
     const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf
-    const float2* vf = nullptr;        // values as hi/lo floats (plans with passes of several densities)
-    const double* vd = nullptr;        // the same values in FP64 (passes of one density)
+    const float2* vf = nullptr;        // [nnz] values as hi/lo floats
 };
 
 // Per-cell interpolation from the density's p-nodes to the FMM's q-nodes
@@ -203,9 +202,6 @@ constexpr int kOutWithPsi = 0, kOutAccumulate = 1, kOutOverwrite = 2;
 cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
                                const double* psi, const float2* xf, int64_t ld_xf, double* out, int64_t ld_out,
                                int mode, int max_blocks, cudaStream_t s);
-// The same for one density in FP64, x in caller order and FP64 (no conversion pass).
-cudaError_t launch_out_grouped64(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
-                                 const double* x, double* out, int mode, int max_blocks, cudaStream_t s);
 // out[d][r] += -(1/2pi) w psi[inv[r]][d] for r < n (w = w_sorted[inv[r]] or 1)
 cudaError_t launch_add_psi(int nd, int32_t n, const int32_t* inv, const double* w_sorted, const double* psi,
                            double* out, int64_t ld_out, cudaStream_t s);
@@ -222,7 +218,7 @@ cudaError_t launch_ups_adjoint(int nd, const DevUpsample& u, const int32_t* inv,
 // fp64: the near field in FP64 instead of float-float on the FP32 pipes.
 cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g,
                              Workspace& ws, bool fp64, PhaseTimer* timer, cudaStream_t s);
-int64_t mhelm_launches(int nlevels);
+int64_t mhelm_launches(int nlevels, bool sym_reduce);
 // Host tables for half sides R_level[l]; leaf_dmax[b] bounds the near-field
 // distances of leaf b (0 for other boxes). Returns an error message, or "".
 std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,

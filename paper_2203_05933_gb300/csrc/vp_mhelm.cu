@@ -284,6 +284,80 @@ __global__ void __launch_bounds__(kWarps * 32)
 // share of K0 is below the leaf's bound, see near_split), the terms k < m in
 // float-float. Pairs with y > 1 take the integral representation in FP64.
 // EXACT: the hi parts of target and source differ exactly in float.
+// K0(lambda r) of one pair in float-float (see mh_tile); false for a coincident pair.
+template <bool EXACT>
+__device__ __forceinline__ bool mh_pair(const float4 rt, const float4 sr, const float4* __restrict__ s_tab,
+                                        const float2* __restrict__ a2, const float2* __restrict__ b2, int deg, int m,
+                                        ff::F cy, ff::F Tc, double lam_side, ff::F& K)
+{
+    float dxs, dxe, dys, dye;
+    if (EXACT) {
+        dxs = __fsub_rn(rt.x, sr.x);
+        dxe = __fsub_rn(rt.y, sr.y);
+        dys = __fsub_rn(rt.z, sr.z);
+        dye = __fsub_rn(rt.w, sr.w);
+    } else {
+        ff::two_sum(rt.x, -sr.x, dxs, dxe);
+        dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
+        ff::two_sum(rt.z, -sr.z, dys, dye);
+        dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
+    }
+    const float px = __fmul_rn(dxs, dxs);
+    float pxe = fmaf(dxs, dxs, -px);
+    pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
+    pxe = fmaf(dxe, dxe, pxe);
+    const float py = __fmul_rn(dys, dys);
+    float pye = fmaf(dys, dys, -py);
+    pye = fmaf(__fadd_rn(dys, dys), dye, pye);
+    pye = fmaf(dye, dye, pye);
+    const float rs = __fadd_rn(px, py);
+    float re = __fsub_rn(fminf(px, py), __fsub_rn(rs, fmaxf(px, py)));
+    re = __fadd_rn(re, __fadd_rn(pxe, pye));
+    if (rs == 0.0f && re == 0.0f) return false;  // coincident pair: no smooth term
+    const ff::F r2{rs, re};
+    const ff::F y = ff::mul(r2, cy);
+    if (y.h > 1.0f) {
+        K = ff::from_double(bessel::k0_large(lam_side * sqrt((double)rs + (double)re)));
+        return true;
+    }
+    float S, lo;
+    ff::log_pair(rs, re, s_tab, S, lo);
+    const ff::F T = ff::add(ff::F{-0.5f * S, -0.5f * lo}, Tc);
+    float ta = 0.0f, tb = 0.0f;
+    for (int j = deg; j >= m; --j) {
+        ta = fmaf(ta, y.h, a2[j].x);
+        tb = fmaf(tb, y.h, b2[j].x);
+    }
+    ff::F A{ta, 0.0f}, B{tb, 0.0f};
+    for (int j = m - 1; j >= 0; --j) {
+        A = ff::add(ff::mul(A, y), ff::F{a2[j].x, a2[j].y});
+        B = ff::add(ff::mul(B, y), ff::F{b2[j].x, b2[j].y});
+    }
+    K = ff::add(ff::mul(A, T), B);
+    return true;
+}
+
+// (ah, al) += q K in float-float
+__device__ __forceinline__ void ff_acc(float2 q, ff::F K, float& ah, float& al)
+{
+    const float p = __fmul_rn(q.x, K.h);
+    float pe = fmaf(q.x, K.h, -p);
+    pe = fmaf(q.x, K.l, pe);
+    pe = fmaf(q.y, K.h, pe);
+    float sh, se;
+    ff::two_sum(ah, p, sh, se);
+    ah = sh;
+    al = __fadd_rn(al, __fadd_rn(se, pe));
+}
+
+// Near field of one target over a staged tile of charges, float-float on the
+// FP32 pipes. Per pair (units of the target leaf's side): r'^2 from exact
+// leaf-centre offsets, log r'^2 by the table log, y = (lambda^2 side^2/4) r'^2,
+// T = -log(r'^2)/2 - (log side + log(lambda/2) + gamma), and
+// K0 = T I0(y) + S(y) with both series by Horner: the terms k >= m in FP32 (their
+// share of K0 is below the leaf's bound, see near_split), the terms k < m in
+// float-float. Pairs with y > 1 take the integral representation in FP64.
+// EXACT: the hi parts of target and source differ exactly in float.
 template <bool EXACT>
 __device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restrict__ s_rho,
                                         const float2* __restrict__ s_q, int n, const float4* __restrict__ s_tab,
@@ -292,61 +366,36 @@ __device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restric
 {
 #pragma unroll 2
     for (int k = 0; k < n; ++k) {
-        const float4 sr = s_rho[k];
-        float dxs, dxe, dys, dye;
-        if (EXACT) {
-            dxs = __fsub_rn(rt.x, sr.x);
-            dxe = __fsub_rn(rt.y, sr.y);
-            dys = __fsub_rn(rt.z, sr.z);
-            dye = __fsub_rn(rt.w, sr.w);
-        } else {
-            ff::two_sum(rt.x, -sr.x, dxs, dxe);
-            dxe = __fadd_rn(dxe, __fsub_rn(rt.y, sr.y));
-            ff::two_sum(rt.z, -sr.z, dys, dye);
-            dye = __fadd_rn(dye, __fsub_rn(rt.w, sr.w));
-        }
-        const float px = __fmul_rn(dxs, dxs);
-        float pxe = fmaf(dxs, dxs, -px);
-        pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
-        pxe = fmaf(dxe, dxe, pxe);
-        const float py = __fmul_rn(dys, dys);
-        float pye = fmaf(dys, dys, -py);
-        pye = fmaf(__fadd_rn(dys, dys), dye, pye);
-        pye = fmaf(dye, dye, pye);
-        const float rs = __fadd_rn(px, py);
-        float re = __fsub_rn(fminf(px, py), __fsub_rn(rs, fmaxf(px, py)));
-        re = __fadd_rn(re, __fadd_rn(pxe, pye));
-        if (rs == 0.0f && re == 0.0f) continue;  // coincident pair: no smooth term
-        const ff::F r2{rs, re};
-        const ff::F y = ff::mul(r2, cy);
         ff::F K;
-        if (y.h > 1.0f) {
-            K = ff::from_double(bessel::k0_large(lam_side * sqrt((double)rs + (double)re)));
-        } else {
-            float S, lo;
-            ff::log_pair(rs, re, s_tab, S, lo);
-            const ff::F T = ff::add(ff::F{-0.5f * S, -0.5f * lo}, Tc);
-            float ta = 0.0f, tb = 0.0f;
-            for (int j = deg; j >= m; --j) {
-                ta = fmaf(ta, y.h, a2[j].x);
-                tb = fmaf(tb, y.h, b2[j].x);
+        if (mh_pair<EXACT>(rt, s_rho[k], s_tab, a2, b2, deg, m, cy, Tc, lam_side, K)) ff_acc(s_q[k], K, ah, al);
+    }
+}
+
+// Symmetric pass over one chunk of at most 32 charges of a leaf A for the 32
+// targets of one warp (the targets are the charge points of the warp's own leaf
+// b, A != b): as in the Laplace kernel, lane l takes charge (l + t) mod 32 at
+// step t, adds q_j K to its target and q_i K to a float-float sum for that
+// charge, and the sums move one lane down after each step, so that lane l ends
+// with the warp's total for charge l. rh, rl must be zero on entry.
+template <bool EXACT>
+__device__ __forceinline__ void mh_chunk_sym(const float4 rt, float2 qi, bool valid_i, const float4* __restrict__ s_rho,
+                                             const float2* __restrict__ s_q, int n, int lane,
+                                             const float4* __restrict__ s_tab, const float2* __restrict__ a2,
+                                             const float2* __restrict__ b2, int deg, int m, ff::F cy, ff::F Tc,
+                                             double lam_side, float& ah, float& al, float& rh, float& rl)
+{
+    const int from = (lane + 1) & 31;
+    for (int t = 0; t < 32; ++t) {
+        const int j = (lane + t) & 31;
+        if (valid_i && j < n) {
+            ff::F K;
+            if (mh_pair<EXACT>(rt, s_rho[j], s_tab, a2, b2, deg, m, cy, Tc, lam_side, K)) {
+                ff_acc(s_q[j], K, ah, al);
+                ff_acc(qi, K, rh, rl);
             }
-            ff::F A{ta, 0.0f}, B{tb, 0.0f};
-            for (int j = m - 1; j >= 0; --j) {
-                A = ff::add(ff::mul(A, y), ff::F{a2[j].x, a2[j].y});
-                B = ff::add(ff::mul(B, y), ff::F{b2[j].x, b2[j].y});
-            }
-            K = ff::add(ff::mul(A, T), B);
         }
-        const float2 qq = s_q[k];
-        const float p = __fmul_rn(qq.x, K.h);
-        float pe = fmaf(qq.x, K.h, -p);
-        pe = fmaf(qq.x, K.l, pe);
-        pe = fmaf(qq.y, K.h, pe);
-        float sh, se;
-        ff::two_sum(ah, p, sh, se);
-        ah = sh;
-        al = __fadd_rn(al, __fadd_rn(se, pe));
+        rh = __shfl_sync(0xffffffffu, rh, from);
+        rl = __shfl_sync(0xffffffffu, rl, from);
     }
 }
 
@@ -354,12 +403,13 @@ __device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restric
 // Per leaf: L2P, M2P over the W list and the direct sum over the U list; one
 // block per leaf, one target per thread. FF: the near field in float-float on
 // the FP32 pipes (mh_tile); else in FP64.
-template <int P, bool FF>
-__global__ void __launch_bounds__(kMhLeafThreads, 16)
+template <int P, bool FF, bool SYM>
+__global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
     k_leaf_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
               const double2* __restrict__ M, const double2* __restrict__ L, const float4* __restrict__ logtab,
-              double* __restrict__ psi)
+              double* __restrict__ psi, float2* __restrict__ slots)
 {
+    static_assert(FF || !SYM, "the symmetric near field is float-float");
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1];
     __shared__ double2 sxy[FF ? 1 : kMhLeafThreads];
@@ -380,7 +430,7 @@ __global__ void __launch_bounds__(kMhLeafThreads, 16)
     if (FF)
         for (int i = tid; i < 128; i += kMhLeafThreads) s_tab[i] = logtab[i];
     for (int li = blockIdx.x; li < t.nleaf; li += gridDim.x) {
-        const int b = t.leaves[li];
+        const int b = SYM ? t.sym_leaves[li] : t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
         const int code = mh.leaf_deg[b];  // series terms this leaf's near field needs, and its split
@@ -455,10 +505,19 @@ __global__ void __launch_bounds__(kMhLeafThreads, 16)
             if (FF) {
                 const float4 rt = valid ? g.erho[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
                 float ah = 0.0f, al = 0.0f;
+                // SYM: leaves A < b are skipped (A's block hands their part over through
+                // the slots), leaves A > b are summed in both directions
+                const int warp = tid >> 5, lane = tid & 31;
+                const int grp = (tb - e0) / 32 + warp;  // this warp's group of 32 targets of b
+                const bool grp_live = tb + 32 * warp < e1;
+                const float2 qi = (SYM && valid) ? qf[ti] : make_float2(0.f, 0.f);
                 for (int e = u0; e < u1; ++e) {
                     const int A = t.u_idx[e];
                     const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
                     if (a0 == a1) continue;
+                    if (SYM && A < b) continue;
+                    const bool rev = SYM && A > b;
+                    const int64_t sbase = rev ? t.sym_off[e] + (int64_t)grp * (a1 - a0) : 0;
                     const float4 uo = t.u_off[e];  // leaf A's centre offset and scale in b units
                     const bool exact_hi = uo.z >= 0.5f && uo.z <= 2.0f;
                     for (int sb = a0; sb < a1; sb += kMhLeafThreads) {
@@ -479,7 +538,21 @@ __global__ void __launch_bounds__(kMhLeafThreads, 16)
                             s_qf[tid] = qf[j];
                         }
                         __syncthreads();
-                        if (valid) {
+                        if (rev) {
+                            if (grp_live) {  // warp-uniform
+                                for (int c = 0; c < n; c += 32) {
+                                    const int nc = min(32, n - c);
+                                    float rh = 0.0f, rl = 0.0f;
+                                    if (exact_hi)
+                                        mh_chunk_sym<true>(rt, qi, valid, s_rho + c, s_qf + c, nc, lane, s_tab, a2, b2,
+                                                           deg, msplit, cy, Tc, mh.lambda * side, ah, al, rh, rl);
+                                    else
+                                        mh_chunk_sym<false>(rt, qi, valid, s_rho + c, s_qf + c, nc, lane, s_tab, a2,
+                                                            b2, deg, msplit, cy, Tc, mh.lambda * side, ah, al, rh, rl);
+                                    if (lane < nc) slots[sbase + (sb - a0) + c + lane] = make_float2(rh, rl);
+                                }
+                            }
+                        } else if (valid) {
                             if (exact_hi)
                                 mh_tile<true>(rt, s_rho, s_qf, n, s_tab, a2, b2, deg, msplit, cy, Tc,
                                               mh.lambda * side, ah, al);
@@ -536,6 +609,26 @@ __global__ void __launch_bounds__(kMhLeafThreads, 16)
     }
 }
 
+// Symmetric near field: adds the slots handed over to each point by the
+// lower adjacent leaves, in a fixed order, times psi_scale.
+__global__ void k_sym_reduce_mh(DevTree t, DevMH mh, PassGeom g, const float2* __restrict__ slots,
+                                double* __restrict__ psi)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.n_eval; j += gridDim.x * blockDim.x) {
+        const int A = t.sym_pt_leaf[j];
+        const int s0 = t.sym_in_ptr[A], s1 = t.sym_in_ptr[A + 1];
+        if (s0 == s1) continue;
+        const int jl = j - g.erng[2 * A];
+        ff::F acc{0.f, 0.f};
+#pragma unroll 4
+        for (int k = s0; k < s1; ++k) {
+            const float2 v = slots[t.sym_in_slot[k] + jl];
+            acc = ff::add(acc, ff::F{v.x, v.y});
+        }
+        psi[j] = fma(mh.psi_scale, ff::to_double(acc), psi[j]);
+    }
+}
+
 template <int P>
 cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, const PassGeom& g, Workspace& ws,
                    bool fp64, PhaseTimer* tm, cudaStream_t s)
@@ -559,10 +652,18 @@ cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, cons
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
     const int blocks = std::max(1, std::min(t.nleaf, 152 * 32));
-    if (fp64)
-        k_leaf_mh<P, false><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab, ws.psi);
-    else
-        k_leaf_mh<P, true><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab, ws.psi);
+    if (fp64) {
+        k_leaf_mh<P, false, false><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab,
+                                                                    ws.psi, nullptr);
+    } else if (t.sym) {
+        k_leaf_mh<P, true, true><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab, ws.psi,
+                                                                  ws.slots);
+        const int rblocks = std::max(1, std::min((g.n_eval + 255) / 256, 152 * 32));
+        k_sym_reduce_mh<<<rblocks, 256, 0, s>>>(t, mh, g, ws.slots, ws.psi);
+    } else {
+        k_leaf_mh<P, true, false><<<blocks, kMhLeafThreads, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M, ws.L, logtab,
+                                                                   ws.psi, nullptr);
+    }
     if (tm) tm->end(id);
     return cudaGetLastError();
 }
@@ -588,7 +689,10 @@ cudaError_t launch_fmm_mhelm(int P, const DevTree& t, const DevMH& mh, const flo
     }
 }
 
-int64_t mhelm_launches(int nlevels) { return 3 + 2 * (int64_t)std::max(0, nlevels - 3); }
+int64_t mhelm_launches(int nlevels, bool sym_reduce)
+{
+    return 3 + 2 * (int64_t)std::max(0, nlevels - 3) + (sym_reduce ? 1 : 0);
+}
 
 // Series terms k = 0..deg for |y| <= ymax (<= 1): until the first omitted term,
 // weighted by the size of its harmonic-number coefficient, is below 1e-18.

@@ -1,7 +1,6 @@
 // Correction apply (a7): out = -(1/2pi) psi + Pi f, the sparse map of the
 // per-cell corrections "accurate minus smooth" (arXiv 2203.05933, Sec. 4,
-// paragraph after Eq. nsrcs): passes of several densities on the FP32 pipes in
-// float-float arithmetic, passes of one density in FP64 (k_out_grouped64).
+// paragraph after Eq. nsrcs), on the FP32 pipes in float-float arithmetic.
 //
 // The rows of one cell share their column list (every node of a cell couples
 // to the nodes of the same near cells), so the plan stores each distinct
@@ -129,74 +128,6 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
 }
 
-// One density in FP64: the same grouped layout with the values as doubles (8 B per
-// nonzero, as the hi/lo pairs) and x gathered straight from the caller's FP64
-// vector. One DFMA per nonzero keeps the kernel on the FP64 pipe and off the
-// issue slots that the FP32-bound FMM kernels need when it runs beside them.
-__global__ void __launch_bounds__(kGroupThreads)
-    k_out_grouped64(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
-                    const double* __restrict__ psi, const double* __restrict__ x, double* __restrict__ out, int mode)
-{
-    extern __shared__ __align__(16) double X[];  // [smem_m] (even): lanes read pairs of columns
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int gi = blockIdx.x; gi < A.ngroups; gi += gridDim.x) {
-        const int r0 = A.g_r0[gi], r1 = A.g_r0[gi + 1];
-        const int64_t c0 = A.g_c0[gi];
-        const int m = (int)(A.g_c0[gi + 1] - c0);
-        const bool staged = m + (m & 1) <= smem_m;
-        __syncthreads();
-        if (staged) {
-            for (int i = threadIdx.x; i < m; i += blockDim.x) X[i] = x[A.cols[c0 + i]];
-            if ((m & 1) && threadIdx.x == 0) X[m] = 0.0;
-        }
-        __syncthreads();
-        const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
-        for (int r = r0 + warp; r < r1; r += nw) {
-            const double2* vrow = reinterpret_cast<const double2*>(A.vd + A.rowptr[r]);  // rows start on 16 bytes
-            constexpr int U = 4;
-            double acc[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) acc[u] = 0.0;
-            for (int q0 = lane; q0 < np; q0 += 32 * U) {
-                double2 v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int q = q0 + 32 * u;
-                    v[u] = q < np ? vrow[q] : make_double2(0.0, 0.0);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int q = q0 + 32 * u;
-                    if (q < np) {
-                        const int k = 2 * q;
-                        double2 xx;
-                        if (staged) {
-                            xx = *reinterpret_cast<const double2*>(X + k);
-                        } else {
-                            xx.x = x[A.cols[c0 + k]];
-                            xx.y = k + 1 < m ? x[A.cols[c0 + k + 1]] : 0.0;
-                        }
-                        acc[u] = fma(v[u].x, xx.x, fma(v[u].y, xx.y, acc[u]));
-                    }
-                }
-            }
-            double t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) {
-                if (mode == kOutWithPsi) {
-                    const int32_t ri = inv[r];
-                    const double wv = w_sorted ? w_sorted[ri] : 1.0;
-                    out[r] = fma(-kInv2PiG * wv, psi[ri], t);
-                } else if (mode == kOutAccumulate) {
-                    out[r] += t;
-                } else {
-                    out[r] = t;
-                }
-            }
-        }
-    }
-}
-
 // out[d][r] += -(1/2pi) w psi[inv[r]][d], w = w_sorted[inv[r]] or 1 (the smooth part added
 // to a correction computed on its own)
 template <int ND>
@@ -259,24 +190,6 @@ cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* in
         case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_out_grouped64(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
-                                 const double* x, double* out, int mode, int max_blocks, cudaStream_t s)
-{
-    cudaError_t e = cudaFuncSetAttribute(k_out_grouped64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGroupSmemBytes);
-    if (e != cudaSuccess) return e;
-    int smem_m = kGroupSmemBytes / (int)sizeof(double);  // even
-    const int want = A.max_m + (A.max_m & 1);
-    if (want < smem_m) smem_m = want;
-    if (smem_m < 2) smem_m = 2;
-    const int cap = max_blocks > 0 ? max_blocks : 152 * 16;
-    int blocks = A.ngroups < cap ? A.ngroups : cap;
-    if (blocks < 1) blocks = 1;
-    k_out_grouped64<<<blocks, kGroupThreads, (size_t)smem_m * sizeof(double), s>>>(A, smem_m, inv, w_sorted, psi, x,
-                                                                                    out, mode);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_add_psi(int nd, int32_t n, const int32_t* inv, const double* w_sorted, const double* psi,

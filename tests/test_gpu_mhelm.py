@@ -71,6 +71,24 @@ def test_float_float_near_field_matches_fp64(lam):
     assert err <= 1e-12
 
 
+def test_symmetric_near_field_matches_fp64():
+    # targets = nodes: each distance between adjacent leaves is evaluated once for
+    # both directions (slots + reduction); against the all-FP64 directed near field
+    prob = inputs.disk_problem(base_level=5, fine_level=6)
+    lam = 10.0
+    f = torch.as_tensor(prob.f, device="cuda")
+    res = {}
+    for flags in (0, vp.VP_FLAG_FP64):
+        plan = make(prob, lam, p_fmm=24, leaf=64, flags=flags)
+        info = plan.info()
+        assert (info.sym_slots > 0) == (flags == 0)
+        res[flags] = plan.eval(f).cpu().numpy()
+        plan.close()
+    err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / norm(prob, lam)[:, None]))
+    print(f"modified Helmholtz symmetric vs FP64 near field {err:.2e}")
+    assert err <= 1e-12
+
+
 def test_densities_graph_and_timing():
     # several densities (one pass each), graph replay bitwise equal to the plain
     # launch sequence, phase timing names
