@@ -76,13 +76,18 @@ int wblocks(int64_t nwork)
 // P2M, one warp per leaf: M_n = sum_j q_j conj(u_j)^n h_n(y_j), u = (z - c)/(2R),
 // y = sigma^2 |u|^2 (= lambda^2 rho^2 / 4); h_P, h_{P+1} by their series, the
 // others by the downward recurrence.
+// Two warps per block and 32 charges per step, so that every lane prepares one
+// charge's terms.
+constexpr int kP2mWarps = 2;
+
 template <int P>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kP2mWarps * 32)
     k_p2m_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, double2* __restrict__ M)
 {
     constexpr int P1 = P + 1;
-    __shared__ double2 pw[kWarps][kMhChunk][P1];
-    __shared__ double qs[kWarps][kMhChunk];
+    constexpr int kMhChunk = 32;
+    __shared__ double2 pw[kP2mWarps][kMhChunk][P1];
+    __shared__ double qs[kP2mWarps][kMhChunk];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
         const int b = t.leaves[li];
@@ -635,7 +640,8 @@ cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, cons
 {
     const int threads = kWarps * 32;
     int id = tm ? tm->begin("upward") : -1;
-    k_p2m_mh<P><<<wblocks(t.nleaf), threads, 0, s>>>(t, mh, g, ws.q, ws.M);
+    k_p2m_mh<P><<<std::max(1, std::min((t.nleaf + kP2mWarps - 1) / kP2mWarps, 152 * 64)), kP2mWarps * 32, 0, s>>>(
+        t, mh, g, ws.q, ws.M);
     for (int l = t.nlevels - 2; l >= 2; --l) {  // multipoles of levels 0 and 1 are never read
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
         k_m2m_mh<P><<<wblocks(b1 - b0), threads, 0, s>>>(t, mh, l, b0, b1, ws.M);
