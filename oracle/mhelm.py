@@ -103,3 +103,15 @@ def evaluate_rows(src_xy, w, f, tgt_xy, rows, lam: float, csr=None) -> np.ndarra
             a, b = int(rowptr[i]), int(rowptr[i + 1])
             out[:, k] += fd[:, col[a:b]] @ val[a:b]
     return out
+
+
+def adjoint_cols(src_xy, w, g, tgt_xy, cols, lam: float, csr=None) -> np.ndarray:
+    """A^T g at the sources ``cols`` only ([ndens, len(cols)])."""
+    cols = np.asarray(cols, np.int64)
+    src = np.asarray(src_xy, np.float64).reshape(-1, 2)
+    out = adjoint(src[cols], np.asarray(w, np.float64)[cols], g, tgt_xy, lam)
+    if csr is not None:
+        gd = _dens(g, np.asarray(tgt_xy).reshape(-1, 2).shape[0])
+        A = _csr_matrix(csr, gd.shape[1], src.shape[0])
+        out += (A.T @ gd.T).T[:, cols]
+    return out

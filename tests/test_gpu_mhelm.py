@@ -129,6 +129,23 @@ def test_adjoint_matches_oracle():
     plan.close()
 
 
+def test_adjoint_symmetric_near_field():
+    # node targets: the transposed pass also takes the symmetric near field
+    prob = inputs.disk_problem(base_level=5, fine_level=6, ndens=2)
+    lam = 10.0
+    g = np.random.default_rng(6).standard_normal((2, prob.n_tgt))
+    plan = make(prob, lam, p_fmm=24, leaf=64)
+    assert plan.info().sym_slots > 0
+    gf = plan.adjoint(torch.as_tensor(g, device="cuda"))[0].cpu().numpy()
+    sub = np.random.default_rng(7).choice(prob.n_src, size=300, replace=False)
+    ref = mhelm.adjoint_cols(prob.src_xy, prob.w, g, prob.tgt_xy, sub, lam, prob.csr)
+    scale = lam * lam / (2 * math.pi) * prob.w.max() * np.abs(g).sum(axis=1)
+    err = float(np.max(np.abs(gf[:, sub] - ref) / scale[:, None]))
+    print(f"modified Helmholtz adjoint (symmetric near field) rel err {err:.2e}")
+    assert err <= TOL
+    plan.close()
+
+
 def test_disk_sampled_targets():
     # the paper's modified-Helmholtz experiment is on the unit disk with lambda^2 = 100
     prob = inputs.disk_problem(base_level=5, fine_level=7)

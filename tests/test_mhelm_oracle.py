@@ -86,6 +86,10 @@ def test_adjoint_identity_and_correction():
     for i in range(0, prob.n_tgt, 17):
         s = sum(val[k] * prob.f[0, col[k]] for k in range(rowptr[i], rowptr[i + 1]))
         assert abs(Af[0, i] - plain[0, i] - s) <= 1e-12 * (abs(s) + abs(plain[0, i]))
+    # sampled sources of the adjoint agree with the full one
+    cols = np.arange(0, prob.n_src, 29)
+    subc = mhelm.adjoint_cols(prob.src_xy, prob.w, g, prob.tgt_xy, cols, lam, prob.csr)
+    assert np.allclose(subc, ATg[:, cols], rtol=1e-13, atol=1e-13 * np.abs(ATg).max())
     # sampled rows agree with the full evaluation
     rows = np.arange(0, prob.n_tgt, 23)
     sub = mhelm.evaluate_rows(prob.src_xy, prob.w, prob.f, prob.tgt_xy, rows, lam, prob.csr)
