@@ -1165,7 +1165,7 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
                                                            std::sqrt(2.0) * (B.radius[(size_t)a] + B.radius[(size_t)b]));
         }
     MhTables T;
-    const std::string err = make_mh_tables(p->P, lambda, R, dmax, T);
+    const std::string err = make_mh_tables(p->P, lambda, R, dmax, !(p->flags & VP_FLAG_FP64), T);
     if (!err.empty()) return fail(VP_ERR_ARG, err);
     // FP32 operations of the float-float near field per evaluation (one density):
     // per evaluated distance about 92 + 2 (deg - m + 1) + 24 m (distance, table log,
@@ -1187,6 +1187,7 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     double *d_spow = nullptr, *d_na = nullptr, *d_nb = nullptr;
     double2 *d_tm = nullptr, *d_tl = nullptr, *d_tv = nullptr;
+    float4* d_tvf = nullptr;
     int32_t* d_deg = nullptr;
     if (e == cudaSuccess) e = p->upload(&d_deg, T.leaf_deg, s);
     if (e == cudaSuccess) e = p->upload(&d_spow, T.spow, s);
@@ -1194,7 +1195,8 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     if (e == cudaSuccess) e = p->upload(&d_nb, T.near_b, s);
     if (e == cudaSuccess) e = p->upload(&d_tm, T.Tm, s);
     if (e == cudaSuccess) e = p->upload(&d_tl, T.Tl, s);
-    if (e == cudaSuccess) e = p->upload(&d_tv, T.Tv, s);
+    if (e == cudaSuccess && !T.Tv.empty()) e = p->upload(&d_tv, T.Tv, s);
+    if (e == cudaSuccess && !T.Tvf.empty()) e = p->upload(&d_tvf, T.Tvf, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create upload");
     DevMH& m = p->mh;
@@ -1211,6 +1213,7 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     m.Tm = d_tm;
     m.Tl = d_tl;
     m.Tv = d_tv;
+    m.Tvf = d_tvf;
     return VP_OK;
 }
 

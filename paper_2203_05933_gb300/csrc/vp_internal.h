@@ -136,12 +136,14 @@ struct DevMH {
     const double2* Tm = nullptr;     // [nlevels][4][P1][2][P1] M2M into a parent of level l (terms j, -j folded)
     const double2* Tl = nullptr;     // [nlevels][4][P1][2][P1] L2L into a child of level l (terms m, -m folded)
     const double2* Tv = nullptr;     // [nlevels][49][P1][2][P1] M2L on scaled coefficients (k, -k folded)
+    const float4* Tvf = nullptr;     // the same divided by m! |k|!, float-float (re_h, re_l, im_h, im_l)
 };
 
 struct MhTables {
     std::vector<double> spow, near_a, near_b;
     std::vector<int32_t> leaf_deg;
     std::vector<double2> Tm, Tl, Tv;
+    std::vector<float4> Tvf;
     double inv_fact_P = 0.0;
     int near_deg = 0;
 };
@@ -222,7 +224,7 @@ int64_t mhelm_launches(int nlevels, bool sym_reduce);
 // Host tables for half sides R_level[l]; leaf_dmax[b] bounds the near-field
 // distances of leaf b (0 for other boxes). Returns an error message, or "".
 std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,
-                           const std::vector<double>& leaf_dmax, MhTables& T);
+                           const std::vector<double>& leaf_dmax, bool ff, MhTables& T);
 double green_mhelm_host(double lambda, double r);
 
 bool p_supported(int P);

@@ -198,39 +198,73 @@ __global__ void __launch_bounds__(kWarps * 32)
 // ----------------------------------------------------------------------------
 // M2L over the V list plus P2L over the X list, one warp per box; lane m owns
 // L_m. Every box's L is written (zeros when both lists are empty).
-template <int P>
+// FF: the V-list products in float-float on the FP32 pipes, on coefficients
+// normalised by factorials (M~_k = k! M_k, L~_m = L_m / m!, operator entries
+// divided by m! |k|!), which keeps every operand O(1) and inside the float range;
+// else in FP64 on the scaled coefficients.
+template <int P, bool FF>
 __global__ void __launch_bounds__(kWarps * 32)
     k_m2l_mh(DevTree t, DevMH mh, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
              const double* __restrict__ q)
 {
     constexpr int P1 = P + 1;
-    __shared__ double2 Ms[kWarps][P1];
+    __shared__ double2 Ms[kWarps][FF ? 1 : P1];
+    __shared__ float4 Mf[kWarps][FF ? P1 : 1];
     __shared__ double2 pw[kWarps][kMhChunk][P1];
     __shared__ double qs[kWarps][kMhChunk];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    double fact = 1.0;  // lane!
+    for (int i = 2; i <= lane; ++i) fact *= (double)i;
     for (int b = gwarp(); b < t.nbox; b += nwarps()) {
         const int lev = t.level[b];
         const double* sp = mh.spow + lev * P1;
         const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
         double2 lacc = make_double2(0.0, 0.0);
         const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
-        for (int e = v0; e < v1; ++e) {
-            const int C = t.v_idx[e];
-            const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
-            if (lane <= P) Ms[wb][lane] = M[(int64_t)C * P1 + lane];
-            __syncwarp();
-            if (lane <= P) {
-                // the level's operator for this offset, acting on the scaled M and giving
-                // the scaled L, with the orders k and -k folded (real 2x2 per k)
-                const double2* T = mh.Tv + ((int64_t)(lev * 49 + o) * P1) * 2 * P1 + lane;
-#pragma unroll 5
-                for (int k = 0; k <= P; ++k) {
-                    const double2 m = Ms[wb][k], u = T[2 * k * P1], v = T[(2 * k + 1) * P1];
-                    lacc.x = fma(m.x, u.x, fma(m.y, u.y, lacc.x));
-                    lacc.y = fma(m.x, v.x, fma(m.y, v.y, lacc.y));
+        if (FF) {
+            ff::F re{0.f, 0.f}, im{0.f, 0.f};
+            for (int e = v0; e < v1; ++e) {
+                const int C = t.v_idx[e];
+                const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+                if (lane <= P) {
+                    const double2 m = M[(int64_t)C * P1 + lane];
+                    const ff::F a = ff::from_double(m.x * fact), c = ff::from_double(m.y * fact);
+                    Mf[wb][lane] = make_float4(a.h, a.l, c.h, c.l);
                 }
+                __syncwarp();
+                if (lane <= P) {
+                    const float4* T = mh.Tvf + ((int64_t)(lev * 49 + o) * P1) * 2 * P1 + lane;
+#pragma unroll 5
+                    for (int k = 0; k <= P; ++k) {
+                        const float4 mk = Mf[wb][k], u = T[2 * k * P1], v = T[(2 * k + 1) * P1];
+                        const ff::F a{mk.x, mk.y}, c{mk.z, mk.w};
+                        re = ff::add(re, ff::add(ff::mul(a, ff::F{u.x, u.y}), ff::mul(c, ff::F{u.z, u.w})));
+                        im = ff::add(im, ff::add(ff::mul(a, ff::F{v.x, v.y}), ff::mul(c, ff::F{v.z, v.w})));
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
+            if (lane <= P) lacc = make_double2(ff::to_double(re) * fact, ff::to_double(im) * fact);
+        }
+        if (!FF) {
+            for (int e = v0; e < v1; ++e) {
+                const int C = t.v_idx[e];
+                const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+                if (lane <= P) Ms[wb][lane] = M[(int64_t)C * P1 + lane];
+                __syncwarp();
+                if (lane <= P) {
+                    // the level's operator for this offset, acting on the scaled M and giving
+                    // the scaled L, with the orders k and -k folded (real 2x2 per k)
+                    const double2* T = mh.Tv + ((int64_t)(lev * 49 + o) * P1) * 2 * P1 + lane;
+#pragma unroll 5
+                    for (int k = 0; k <= P; ++k) {
+                        const double2 m = Ms[wb][k], u = T[2 * k * P1], v = T[(2 * k + 1) * P1];
+                        lacc.x = fma(m.x, u.x, fma(m.y, u.y, lacc.x));
+                        lacc.y = fma(m.x, v.x, fma(m.y, v.y, lacc.y));
+                    }
+                }
+                __syncwarp();
+            }
         }
         const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
         if (x1 > x0) {
@@ -648,7 +682,10 @@ cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, cons
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("m2l") : -1;
-    k_m2l_mh<P><<<wblocks(t.nbox), threads, 0, s>>>(t, mh, g, ws.M, ws.L, ws.q);
+    if (fp64)
+        k_m2l_mh<P, false><<<wblocks(t.nbox), threads, 0, s>>>(t, mh, g, ws.M, ws.L, ws.q);
+    else
+        k_m2l_mh<P, true><<<wblocks(t.nbox), threads, 0, s>>>(t, mh, g, ws.M, ws.L, ws.q);
     if (tm) tm->end(id);
     id = tm ? tm->begin("l2l") : -1;
     for (int l = 3; l < t.nlevels; ++l) {  // locals of levels 0 to 2 receive nothing from above
@@ -740,7 +777,7 @@ int near_split(int deg, double ymax, double lambda, double c0, const std::vector
 }
 
 std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_level,
-                           const std::vector<double>& leaf_dmax, MhTables& T)
+                           const std::vector<double>& leaf_dmax, bool ff, MhTables& T)
 {
     const int P1 = P + 1, NJ = 2 * P + 1;
     const int nl = (int)R_level.size();
@@ -858,6 +895,27 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
                     }
             }
     }
+    // float-float copy of the M2L tables, entries divided by m! |k|! (the kernel
+    // multiplies M_k by k! and L~_m by m!)
+    if (ff) {
+        T.Tvf.assign(T.Tv.size(), make_float4(0.f, 0.f, 0.f, 0.f));
+        auto split = [](double v, float& h, float& l) {
+            h = (float)v;
+            l = (float)(v - (double)h);
+        };
+        for (size_t lo = 0; lo < (size_t)nl * 49; ++lo)
+            for (int k = 0; k <= P; ++k)
+                for (int m = 0; m <= P; ++m)
+                    for (int half = 0; half < 2; ++half) {
+                        const size_t i = (lo * P1 + (size_t)k) * 2 * P1 + (size_t)half * P1 + (size_t)m;
+                        const double sc = inv_fact[(size_t)m] * inv_fact[(size_t)k];
+                        float4 o;
+                        split(T.Tv[i].x * sc, o.x, o.y);
+                        split(T.Tv[i].y * sc, o.z, o.w);
+                        T.Tvf[i] = o;
+                    }
+        T.Tv.clear();
+    }
     // near-field series: per leaf, the terms its largest near-field distance needs
     // (pairs beyond y = 1 take the integral representation) and the split between
     // the float-float head and the FP32 tail of the Horner sums
@@ -903,6 +961,9 @@ std::string make_mh_tables(int P, double lambda, const std::vector<double>& R_le
         if (!std::isfinite(v)) return "lambda times the box size is outside the range of the expansions";
     if (!finite(T.Tm) || !finite(T.Tl) || !finite(T.Tv))
         return "lambda times the box size is outside the range of the expansions";
+    for (const float4& v : T.Tvf)
+        if (!std::isfinite(v.x) || !std::isfinite(v.y) || !std::isfinite(v.z) || !std::isfinite(v.w))
+            return "lambda times the box size is outside the range of the float-float M2L";
     return "";
 }
 
