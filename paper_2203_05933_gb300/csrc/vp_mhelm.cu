@@ -80,14 +80,18 @@ int wblocks(int64_t nwork)
 // charge's terms.
 constexpr int kP2mWarps = 2;
 
-template <int P>
+template <int P, bool FF>
 __global__ void __launch_bounds__(kP2mWarps * 32)
-    k_p2m_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, double2* __restrict__ M)
+    k_p2m_mh(DevTree t, DevMH mh, PassGeom g, const double* __restrict__ q, const float2* __restrict__ qf,
+             double2* __restrict__ M)
 {
     constexpr int P1 = P + 1;
     constexpr int kMhChunk = 32;
-    __shared__ double2 pw[kP2mWarps][kMhChunk][P1];
-    __shared__ double qs[kP2mWarps][kMhChunk];
+    // FF: the powers, the recurrence and the sums in float-float on the FP32 pipes
+    __shared__ double2 pw[kP2mWarps][FF ? 1 : kMhChunk][FF ? 1 : P1];
+    __shared__ double qs[kP2mWarps][FF ? 1 : kMhChunk];
+    __shared__ float4 pwf[kP2mWarps][FF ? kMhChunk : 1][FF ? P1 : 1];
+    __shared__ float2 qsf[kP2mWarps][FF ? kMhChunk : 1];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
         const int b = t.leaves[li];
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(kP2mWarps * 32)
         const double inv2R = 0.5 / t.radius[b];
         const double sig = mh.spow[t.level[b] * P1 + 1];
         double2 acc = make_double2(0.0, 0.0);
+        ff::C accf{{0.f, 0.f}, {0.f, 0.f}};
         for (int base = s0; base < s1; base += kMhChunk) {
             const int n = min(kMhChunk, s1 - base);
             if (lane < n) {
@@ -104,32 +109,62 @@ __global__ void __launch_bounds__(kP2mWarps * 32)
                 const double y = sig * sig * (u.x * u.x + u.y * u.y);
                 double hm, hm1;
                 bessel::h_series2(P, y, mh.inv_fact_P, hm, hm1);
-                pw[wb][lane][P].x = hm;
-                for (int m = P; m >= 1; --m) {
-                    const double hp = fma((double)m, hm, y * hm1);
-                    hm1 = hm;
-                    hm = hp;
-                    pw[wb][lane][m - 1].x = hp;
+                if (FF) {
+                    const ff::F yf = ff::from_double(y);
+                    ff::F h = ff::from_double(hm), h1 = ff::from_double(hm1);
+                    pwf[wb][lane][P] = make_float4(h.h, h.l, 0.f, 0.f);
+                    for (int m = P; m >= 1; --m) {
+                        const ff::F hp = ff::add(ff::mul(h, ff::F{(float)m, 0.f}), ff::mul(yf, h1));
+                        h1 = h;
+                        h = hp;
+                        pwf[wb][lane][m - 1] = make_float4(hp.h, hp.l, 0.f, 0.f);
+                    }
+                    const ff::C uf = ff::from_double2(u);
+                    ff::C pp{{1.f, 0.f}, {0.f, 0.f}};
+                    for (int m = 0; m <= P; ++m) {
+                        const float4 hv = pwf[wb][lane][m];
+                        const ff::F hh{hv.x, hv.y};
+                        pwf[wb][lane][m] = ff::to_float4(ff::C{ff::mul(pp.re, hh), ff::mul(pp.im, hh)});
+                        pp = ff::cnorm(ff::cmul(pp, uf));
+                    }
+                    qsf[wb][lane] = qf[base + lane];
+                } else {
+                    pw[wb][lane][P].x = hm;
+                    for (int m = P; m >= 1; --m) {
+                        const double hp = fma((double)m, hm, y * hm1);
+                        hm1 = hm;
+                        hm = hp;
+                        pw[wb][lane][m - 1].x = hp;
+                    }
+                    double2 p = make_double2(1.0, 0.0);
+                    for (int m = 0; m <= P; ++m) {
+                        const double h = pw[wb][lane][m].x;
+                        pw[wb][lane][m] = make_double2(p.x * h, p.y * h);
+                        p = cmul(p, u);
+                    }
+                    qs[wb][lane] = q[base + lane];
                 }
-                double2 p = make_double2(1.0, 0.0);
-                for (int m = 0; m <= P; ++m) {
-                    const double h = pw[wb][lane][m].x;
-                    pw[wb][lane][m] = make_double2(p.x * h, p.y * h);
-                    p = cmul(p, u);
-                }
-                qs[wb][lane] = q[base + lane];
             }
             __syncwarp();
             if (lane <= P) {
-                for (int j = 0; j < n; ++j) {
-                    const double2 v = pw[wb][j][lane];
-                    acc.x = fma(qs[wb][j], v.x, acc.x);
-                    acc.y = fma(qs[wb][j], v.y, acc.y);
+                if (FF) {
+                    for (int j = 0; j < n; ++j) {
+                        const ff::C v = ff::from_float4(pwf[wb][j][lane]);
+                        const ff::F qq{qsf[wb][j].x, qsf[wb][j].y};
+                        accf.re = ff::add(accf.re, ff::mul(qq, v.re));
+                        accf.im = ff::add(accf.im, ff::mul(qq, v.im));
+                    }
+                } else {
+                    for (int j = 0; j < n; ++j) {
+                        const double2 v = pw[wb][j][lane];
+                        acc.x = fma(qs[wb][j], v.x, acc.x);
+                        acc.y = fma(qs[wb][j], v.y, acc.y);
+                    }
                 }
             }
             __syncwarp();
         }
-        if (lane <= P) M[(int64_t)b * P1 + lane] = acc;
+        if (lane <= P) M[(int64_t)b * P1 + lane] = FF ? ff::to_double2(accf) : acc;
     }
 }
 
@@ -451,6 +486,7 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
     static_assert(FF || !SYM, "the symmetric near field is float-float");
     constexpr int P1 = P + 1;
     __shared__ double2 Cs[P1];
+    __shared__ float4 Csf[FF ? P1 : 1];
     __shared__ double2 sxy[FF ? 1 : kMhLeafThreads];
     __shared__ double sq[FF ? 1 : kMhLeafThreads];
     __shared__ float4 s_rho[FF ? kMhLeafThreads : 1];
@@ -491,11 +527,32 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
             double acc = 0.0;
 
             // L2P: phi = 2 Re sum_m u^m h_m L_m - h_0 L_0, by Horner in u while h_m
-            // runs down its recurrence
+            // runs down its recurrence (FF: in float-float)
             __syncthreads();
-            for (int i = tid; i < P1; i += kMhLeafThreads) Cs[i] = L[(int64_t)b * P1 + i];
+            for (int i = tid; i < P1; i += kMhLeafThreads) {
+                Cs[i] = L[(int64_t)b * P1 + i];
+                if (FF) Csf[i] = ff::to_float4(ff::from_double2(Cs[i]));
+            }
             __syncthreads();
-            if (valid) {
+            if (FF && valid) {
+                const double2 ud = make_double2((z.x - cb.x) / side, (z.y - cb.y) / side);
+                const double y = sig * sig * (ud.x * ud.x + ud.y * ud.y);
+                double hm, hm1;
+                bessel::h_series2(P, y, mh.inv_fact_P, hm, hm1);
+                const ff::C u = ff::from_double2(ud);
+                const ff::F yf = ff::from_double(y);
+                ff::F h = ff::from_double(hm), h1 = ff::from_double(hm1);
+                const ff::C cP = ff::from_float4(Csf[P]);
+                ff::C S{ff::mul(cP.re, h), ff::mul(cP.im, h)};
+                for (int m = P; m >= 1; --m) {
+                    const ff::F hp = ff::add(ff::mul(h, ff::F{(float)m, 0.f}), ff::mul(yf, h1));
+                    h1 = h;
+                    h = hp;
+                    const ff::C cm = ff::from_float4(Csf[m - 1]);
+                    S = ff::cnorm(ff::cadd(ff::cmul(S, u), ff::C{ff::mul(cm.re, hp), ff::mul(cm.im, hp)}));
+                }
+                acc += 2.0 * ff::to_double(S.re) - ff::to_double(h) * Cs[0].x;
+            } else if (valid) {
                 const double2 u = make_double2((z.x - cb.x) / side, (z.y - cb.y) / side);
                 const double y = sig * sig * (u.x * u.x + u.y * u.y);
                 double hm, hm1;
@@ -674,8 +731,11 @@ cudaError_t fmm_mh(const DevTree& t, const DevMH& mh, const float4* logtab, cons
 {
     const int threads = kWarps * 32;
     int id = tm ? tm->begin("upward") : -1;
-    k_p2m_mh<P><<<std::max(1, std::min((t.nleaf + kP2mWarps - 1) / kP2mWarps, 152 * 64)), kP2mWarps * 32, 0, s>>>(
-        t, mh, g, ws.q, ws.M);
+    const int pblocks = std::max(1, std::min((t.nleaf + kP2mWarps - 1) / kP2mWarps, 152 * 64));
+    if (fp64)
+        k_p2m_mh<P, false><<<pblocks, kP2mWarps * 32, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M);
+    else
+        k_p2m_mh<P, true><<<pblocks, kP2mWarps * 32, 0, s>>>(t, mh, g, ws.q, ws.qf, ws.M);
     for (int l = t.nlevels - 2; l >= 2; --l) {  // multipoles of levels 0 and 1 are never read
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
         k_m2m_mh<P><<<wblocks(b1 - b0), threads, 0, s>>>(t, mh, l, b0, b1, ws.M);
