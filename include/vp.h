@@ -9,7 +9,8 @@
  *
  *   out[d][i] = sum_{j : r_j != t_i} w_j f[d][j] G(r_j, t_i)  +  sum_k Pi_ik f[d][k]
  *
- *   G(r, r0) = -(1/2pi) log|r - r0|                       (Sec. 2.1)
+ *   G(r, r0) = -(1/2pi) log|r - r0|                       (Sec. 2.1), or the
+ *              modified-Helmholtz kernel (VP_KERNEL_MHELMHOLTZ, below)
  *   first sum: the target-independent smooth quadrature rule over all cells,
  *              Jacobians folded into the weights w_j       (Eq. Tk_smooth_quad
  *              and the remark after it; Eq. vio_rokh_quad_rule; Sec. 4.2)

@@ -1,5 +1,7 @@
 // C ABI of libvp (declared in include/vp.h): plan construction, evaluation,
-// adjoint, inspection. Host code only; kernels live in vp_fmm.cu.
+// adjoint, inspection. Host code only; kernels live in vp_fmm.cu (Laplace FMM),
+// vp_mhelm.cu (modified-Helmholtz FMM), vp_spmv.cu (correction apply),
+// vp_upsample.cu, vp_interp.cu, vp_tricorr.cu and vp_static.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

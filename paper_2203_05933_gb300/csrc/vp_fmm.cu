@@ -1,6 +1,8 @@
-// FMM kernels for the smooth-quadrature point sum of the volume potential and
-// the correction apply (arXiv 2203.05933, Eq. Tk_smooth_quad and the sparse
-// correction matrix of Sec. 4), all in IEEE float64 on sm_103a.
+// FMM kernels (Laplace kernel) for the smooth-quadrature point sum of the
+// volume potential (arXiv 2203.05933, Eq. Tk_smooth_quad): an all-FP64 set
+// (VP_FLAG_FP64, and the target gradient) and the default set in float-float
+// arithmetic on the FP32 pipes (k_*_ff), on sm_103a; plus the FP64 reference
+// forms of the output and correction steps.
 //
 // Potential convention inside this file: psi(z) = Re sum_j q_j log(z - z_j),
 // so that V = -(1/2pi) psi with G = -(1/2pi) log|r - r0| (Sec. 2.1). The
