@@ -244,6 +244,18 @@ vp_status vp_eval_adjoint(vp_plan plan, int32_t ndens,
 vp_status vp_eval_host(vp_plan plan, int32_t ndens, const double* f_host,
                        double* out_host, void* stream);
 
+/*
+ * vp_eval_batch — several independent plans evaluated on one stream, in order:
+ * plan k takes ndens[k] densities f[k] (leading dimension ld_f[k]) into out[k]
+ * (ld_out[k]), with the conventions of vp_eval (each plan replays its own graph
+ * with VP_FLAG_GRAPH). For many small problems the single-launch form is one
+ * forest plan (vp_plan_create_many): one launch per phase for all problems and
+ * one graph per evaluation. Stops at the first error (earlier plans' results
+ * stand). Host arrays of length nplans; device buffers as in vp_eval.
+ */
+vp_status vp_eval_batch(int32_t nplans, const vp_plan* plans, const int32_t* ndens, const double* const* f,
+                        const int64_t* ld_f, double* const* out, const int64_t* ld_out, void* stream);
+
 /* Plan summary (host struct filled by vp_plan_info). */
 typedef struct {
     int64_t n_src, n_tgt, nnz;

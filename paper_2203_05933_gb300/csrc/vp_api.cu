@@ -327,6 +327,7 @@ bool finite_all(const std::vector<double>& a)
 
 namespace vp {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+std::vector<float> log_table() { return make_log_table(); }
 }  // namespace vp
 
 // ---------------------------------------------------------------------------
@@ -1679,6 +1680,19 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
         }
     }
     p->last_launches = fwd_launches;
+    return VP_OK;
+}
+
+vp_status vp_eval_batch(int32_t nplans, const vp_plan* plans, const int32_t* ndens, const double* const* f,
+                        const int64_t* ld_f, double* const* out, const int64_t* ld_out, void* stream)
+{
+    if (nplans < 0) return fail(VP_ERR_ARG, "nplans < 0");
+    if (nplans == 0) return VP_OK;
+    if (!plans || !ndens || !f || !ld_f || !out || !ld_out) return fail(VP_ERR_ARG, "NULL batch array");
+    for (int32_t k = 0; k < nplans; ++k) {
+        const vp_status st = vp_eval(plans[k], ndens[k], f[k], ld_f[k], out[k], ld_out[k], stream);
+        if (st != VP_OK) return st;
+    }
     return VP_OK;
 }
 

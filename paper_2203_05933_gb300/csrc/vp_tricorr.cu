@@ -20,9 +20,11 @@
 #include <vector>
 
 #include "vp.h"
+#include "vp_ff.cuh"
 
 namespace vp {
 void set_last_error(const std::string& msg);  // defined with the rest of the ABI (vp_api.cu)
+std::vector<float> log_table();               // the table of the float-float log (vp_api.cu)
 }
 
 struct vp_tricorr_s {
@@ -33,7 +35,10 @@ struct vp_tricorr_s {
     double* coef = nullptr;      // [n_basis][n_nodes]
     double* chi = nullptr;       // [n_nodes][n_rule][2]
     double* tau = nullptr;       // [n_nodes][n_rule]
-    double* B = nullptr;         // [n_nodes][n_basis][n_rule]
+    double* B = nullptr;         // [n_nodes][n_basis][n_rule] (device copy unused; the kernel reads Bf)
+    float2* Bf = nullptr;        // B as hi/lo floats
+    double* logt2 = nullptr;     // [n_nodes][n_rule] 2 log|tau| (tau > 0 nodes)
+    float4* logtab = nullptr;    // [128] table of the float-float log
     std::vector<void*> allocs;
     bool alive = true;
     ~vp_tricorr_s()
@@ -43,6 +48,8 @@ struct vp_tricorr_s {
 };
 
 namespace {
+
+namespace ff = vp::ff;
 
 constexpr int kTcThreads = 128;
 constexpr int kTcMaxBasis = 36;
@@ -104,15 +111,23 @@ __device__ __forceinline__ void tri_map(const TriGeom& g, double xi, double eta,
     J = fabs(x_xi * y_eta - x_eta * y_xi);
 }
 
+// One block per (target node a, cell). The mapped Green function at each rule
+// node is assembled in float-float on the FP32 pipes from FP64 map values
+// (log r^2 by the float-float table log, in units of the cell's bounding size,
+// log tau^2 precomputed), and the contraction with B_a runs in float-float; the
+// cell map itself (blending map, trigonometry) stays FP64.
 __global__ void __launch_bounds__(kTcThreads)
     k_tricorr(int64_t n_cells, int32_t n_nodes, int32_t n_basis, int32_t n_rule, const double* __restrict__ geom,
               const double* __restrict__ node_ref, const double* __restrict__ node_w, const double* __restrict__ coef,
-              const double* __restrict__ chi, const double* __restrict__ tau, const double* __restrict__ B,
-              double* __restrict__ out)
+              const double* __restrict__ chi, const double* __restrict__ tau, const float2* __restrict__ Bf,
+              const double* __restrict__ logt2, const float4* __restrict__ logtab, double* __restrict__ out)
 {
     __shared__ double red[kTcThreads / 32][kTcMaxBasis];
     __shared__ double vhat[kTcMaxBasis];
+    __shared__ float4 s_tab[128];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 128; i += kTcThreads) s_tab[i] = logtab[i];
+    __syncthreads();
     for (int64_t blk = blockIdx.x; blk < n_cells * n_nodes; blk += gridDim.x) {
         const int a = (int)(blk / n_cells);  // target node major: blocks of one node share B_a
         const int64_t c = blk - (int64_t)a * n_cells;
@@ -132,32 +147,49 @@ __global__ void __launch_bounds__(kTcThreads)
         g.c4 = gp[11];
         double x0, y0, J0;
         tri_map(g, node_ref[2 * a], node_ref[2 * a + 1], x0, y0, J0);
-        double acc[kTcMaxBasis];
+        // length unit of the cell: its longest vertex-to-vertex distance squared
+        const double h2 = fmax(fmax((g.v1x - g.v0x) * (g.v1x - g.v0x) + (g.v1y - g.v0y) * (g.v1y - g.v0y),
+                                    (g.v2x - g.v0x) * (g.v2x - g.v0x) + (g.v2y - g.v0y) * (g.v2y - g.v0y)),
+                               (g.v2x - g.v1x) * (g.v2x - g.v1x) + (g.v2y - g.v1y) * (g.v2y - g.v1y));
+        const double inv_h2 = 1.0 / h2, log_h2 = log(h2);
+        ff::F acc[kTcMaxBasis];
 #pragma unroll
-        for (int b = 0; b < kTcMaxBasis; ++b) acc[b] = 0.0;
+        for (int b = 0; b < kTcMaxBasis; ++b) acc[b] = ff::F{0.f, 0.f};
         const double* ch = chi + (int64_t)a * n_rule * 2;
         const double* ta = tau + (int64_t)a * n_rule;
-        const double* Ba = B + (int64_t)a * n_basis * n_rule;
+        const double* lt = logt2 + (int64_t)a * n_rule;
+        const float2* Ba = Bf + (int64_t)a * n_basis * n_rule;
         for (int i = tid; i < n_rule; i += kTcThreads) {
             double x, y, J;
             tri_map(g, ch[2 * i], ch[2 * i + 1], x, y, J);
-            const double t = ta[i];
-            double gi;
-            if (t < 0.0) {
-                gi = kInv2PiT * J;  // the -log t part sits in the weights
+            ff::F gi;
+            if (ta[i] < 0.0) {
+                gi = ff::from_double(kInv2PiT * J);  // the -log t part sits in the weights
             } else {
-                const double L = log(hypot(x - x0, y - y0)) - log(t);
-                gi = -kInv2PiT * L * J;
+                // -(1/2pi) J log(r / t) = -(1/4pi) J (log(r^2/h^2) + log h^2 - log t^2)
+                const double dx = x - x0, dy = y - y0;
+                const double rs = (dx * dx + dy * dy) * inv_h2;
+                const ff::F r2 = ff::from_double(rs);
+                float S, lo;
+                ff::log_pair(r2.h, r2.l, s_tab, S, lo);
+                const ff::F L = ff::add(ff::F{S, lo}, ff::from_double(log_h2 - lt[i]));
+                gi = ff::mul(L, ff::from_double(-0.5 * kInv2PiT * J));
             }
 #pragma unroll
             for (int b = 0; b < kTcMaxBasis; ++b)
-                if (b < n_basis) acc[b] = fma(Ba[(int64_t)b * n_rule + i], gi, acc[b]);
+                if (b < n_basis) {
+                    const float2 bv = Ba[(int64_t)b * n_rule + i];
+                    acc[b] = ff::add(acc[b], ff::mul(ff::F{bv.x, bv.y}, gi));
+                }
         }
 #pragma unroll
         for (int b = 0; b < kTcMaxBasis; ++b) {
-            double v = acc[b];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][b] = v;
+            ff::F v = acc[b];
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h = __shfl_xor_sync(0xffffffffu, v.h, o), l = __shfl_xor_sync(0xffffffffu, v.l, o);
+                v = ff::add(v, ff::F{h, l});
+            }
+            if (lane == 0) red[warp][b] = ff::to_double(v);
         }
         __syncthreads();
         if (tid < n_basis) {
@@ -220,6 +252,28 @@ vp_status vp_tricorr_create(vp_tricorr* out, int32_t n_nodes, int32_t n_basis, i
         *dst[k] = (double*)q;
         e = cudaMemcpyAsync(q, src[k], sizes[k] * sizeof(double), cudaMemcpyHostToDevice, s);
     }
+    // B as hi/lo floats, 2 log|tau| per rule node, and the table of the float-float log
+    std::vector<float> hbf(2 * sizes[5]);
+    for (size_t i = 0; i < sizes[5]; ++i) {
+        const float h = (float)B[i];
+        hbf[2 * i] = h;
+        hbf[2 * i + 1] = (float)(B[i] - (double)h);
+    }
+    std::vector<double> hlt(sizes[4]);
+    for (size_t i = 0; i < sizes[4]; ++i) hlt[i] = tau[i] > 0.0 ? 2.0 * std::log(tau[i]) : 0.0;
+    const std::vector<float> hlog = vp::log_table();
+    auto up = [&](void** dstp, const void* srcp, size_t bytes) {
+        if (e != cudaSuccess) return;
+        void* q = nullptr;
+        e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return;
+        tc->allocs.push_back(q);
+        *dstp = q;
+        e = cudaMemcpyAsync(q, srcp, bytes, cudaMemcpyHostToDevice, s);
+    };
+    up((void**)&tc->Bf, hbf.data(), hbf.size() * sizeof(float));
+    up((void**)&tc->logt2, hlt.data(), hlt.size() * sizeof(double));
+    up((void**)&tc->logtab, hlog.data(), hlog.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         delete tc;
@@ -244,7 +298,7 @@ vp_status vp_tricorr_eval(vp_tricorr tc, int64_t n_cells, const double* geom, do
     const int blocks = (int)(work < 152 * 16 ? work : 152 * 16);
     k_tricorr<<<blocks, kTcThreads, 0, (cudaStream_t)stream>>>(n_cells, tc->n_nodes, tc->n_basis, tc->n_rule, geom,
                                                                 tc->node_ref, tc->node_w, tc->coef, tc->chi, tc->tau,
-                                                                tc->B, out);
+                                                                tc->Bf, tc->logt2, tc->logtab, out);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return tfail(VP_ERR_CUDA, std::string("vp_tricorr_eval: ") + cudaGetErrorString(e));
     return VP_OK;

@@ -33,7 +33,7 @@ TREE_ARRAYS = {
 }
 
 EXPORTED = [
-    "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host",
+    "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_eval_batch",
     "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_set_overlap", "vp_plan_destroy",
     "vp_green_eval_host",
     "vp_status_string", "vp_last_error", "vp_version",
@@ -111,6 +111,7 @@ def _load():
         "vp_eval": [P, I32, P, I64, P, I64, P],
         "vp_eval_adjoint": [P, I32, P, I64, P, I64, P, I64, P, P],
         "vp_eval_host": [P, I32, P, P, P],
+        "vp_eval_batch": [I32, P, P, P, P, P, P, P],
         "vp_plan_info": [P, ctypes.POINTER(vp_plan_stats)],
         "vp_plan_phase_times": [P, I32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(I32)],
@@ -151,6 +152,27 @@ def make_options(p_fmm=0, leaf=0, max_level=0, max_dens=0, flags=0, root=None, k
     if root is not None:
         o.root[0], o.root[1], o.root[2] = root
     return o
+
+
+def eval_batch(plans, fs, outs=None, stream=None):
+    """vp_eval_batch: plans[k] evaluates fs[k] (CUDA float64 [ndens, n_src]) into
+    outs[k] (allocated when None); returns the outputs."""
+    import torch
+    n = len(plans)
+    if len(fs) != n:
+        raise ValueError("one density block per plan")
+    fs = [f.reshape(1, -1) if f.dim() == 1 else f for f in fs]
+    fs = [f if f.stride(1) == 1 else f.contiguous() for f in fs]
+    if outs is None:
+        outs = [torch.empty((f.shape[0], p.n_tgt), dtype=torch.float64, device=f.device) for p, f in zip(plans, fs)]
+    P = ctypes.c_void_p
+    arr = lambda t, vals: (t * n)(*vals)
+    _check(_load().vp_eval_batch(
+        n, arr(P, [p.handle for p in plans]), arr(ctypes.c_int32, [f.shape[0] for f in fs]),
+        arr(P, [f.data_ptr() for f in fs]), arr(ctypes.c_int64, [max(f.stride(0), f.shape[1], 1) for f in fs]),
+        arr(P, [o.data_ptr() for o in outs]), arr(ctypes.c_int64, [max(o.stride(0), o.shape[1], 1) for o in outs]),
+        _stream(stream)), "vp_eval_batch")
+    return outs
 
 
 def green_eval_host(r, kernel=0, lam=0.0):

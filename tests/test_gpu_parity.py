@@ -403,3 +403,24 @@ def test_correction_beside_fmm_matches_sequential():
     with pytest.raises(vp.VPError):
         plan.set_overlap(-1)
     plan.close()
+
+
+def test_eval_batch_matches_single_evaluations():
+    # vp_eval_batch runs each plan's evaluation in order on one stream: the same
+    # bits as separate vp_eval calls (one plan with two densities, a modified-
+    # Helmholtz plan, a graph-replaying plan)
+    probs = [inputs.cloud_problem(2000, 1500, ndens=2, shared=300, seed=81),
+             inputs.cloud_problem(1200, 900, ndens=1, seed=82),
+             inputs.box_grid_problem(nbox=4, order=8)]
+    plans = [vp.Plan.create(probs[0].src_xy, probs[0].w, probs[0].tgt_xy, probs[0].csr, p_fmm=16, leaf=32, max_dens=2),
+             vp.Plan.create(probs[1].src_xy, probs[1].w, probs[1].tgt_xy, probs[1].csr, p_fmm=24, leaf=32,
+                            kernel=vp.VP_KERNEL_MHELMHOLTZ, lam=5.0),
+             vp.Plan.create(probs[2].src_xy, probs[2].w, probs[2].tgt_xy, probs[2].csr, p_fmm=30, leaf=64,
+                            flags=vp.VP_FLAG_GRAPH, root=probs[2].root)]
+    fs = [torch.as_tensor(p.f, device="cuda") for p in probs]
+    single = [pl.eval(f).cpu().numpy() for pl, f in zip(plans, fs)]
+    batch = [o.cpu().numpy() for o in vp.eval_batch(plans, fs)]
+    for a, b in zip(single, batch):
+        assert np.array_equal(a, b)
+    for pl in plans:
+        pl.close()
