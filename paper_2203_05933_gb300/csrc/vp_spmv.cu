@@ -34,6 +34,85 @@ __global__ void k_to_ff_rows(int64_t total, int32_t n, const double* __restrict_
     }
 }
 
+// The rows of one group, one warp per row: U independent accumulators per
+// density keep U 16-byte value loads in flight per lane (four for one or two
+// densities; two beyond, where each value is reused ND times and registers are
+// the scarcer resource). STAGED: x[:, cols] sits in shared memory (F, density
+// d at F + d * smem_m); else it is gathered from xf.
+template <int ND, bool STAGED>
+__device__ __forceinline__ void grouped_rows(const DevGroupedCSR& A, int r0, int r1, int64_t c0, int m, int smem_m,
+                                             const float2* __restrict__ F, const int32_t* __restrict__ inv,
+                                             const double* __restrict__ w_sorted, const double* __restrict__ psi,
+                                             const float2* __restrict__ xf, int64_t ld_xf, double* __restrict__ out,
+                                             int64_t ld_out, int mode, int lane, int warp, int nw)
+{
+    constexpr int U = ND >= 4 ? 2 : 4;
+    const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
+    for (int r = r0 + warp; r < r1; r += nw) {
+        const float4* vrow = reinterpret_cast<const float4*>(A.vf + A.rowptr[r]);  // rows start on 16 bytes
+        ff::F acc[U][ND];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[u][d] = ff::F{0.f, 0.f};
+        for (int q0 = lane; q0 < np; q0 += 32 * U) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + 32 * u;
+                v[u] = q < np ? vrow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = q0 + 32 * u;
+                if (q < np) {
+                    const int k = 2 * q;
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        float4 x;
+                        if (STAGED) {
+                            x = *reinterpret_cast<const float4*>(F + d * smem_m + k);
+                        } else {
+                            const float2 x0 = xf[d * ld_xf + A.cols[c0 + k]];
+                            const float2 x1 = k + 1 < m ? xf[d * ld_xf + A.cols[c0 + k + 1]] : make_float2(0.f, 0.f);
+                            x = make_float4(x0.x, x0.y, x1.x, x1.y);
+                        }
+                        acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].x, v[u].y}, ff::F{x.x, x.y}));
+                        acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].z, v[u].w}, ff::F{x.z, x.w}));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 1; u < U; ++u)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[0][d] = ff::add(acc[0][d], acc[u][d]);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h = __shfl_xor_sync(0xffffffffu, acc[0][d].h, o);
+                const float l = __shfl_xor_sync(0xffffffffu, acc[0][d].l, o);
+                acc[0][d] = ff::add(acc[0][d], ff::F{h, l});
+            }
+        }
+        if (lane == 0) {
+            if (mode == kOutWithPsi) {
+                const int32_t ri = inv[r];
+                const double wv = w_sorted ? w_sorted[ri] : 1.0;
+#pragma unroll
+                for (int d = 0; d < ND; ++d)
+                    out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
+            } else if (mode == kOutAccumulate) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) out[d * ld_out + r] += ff::to_double(acc[0][d]);
+            } else {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) out[d * ld_out + r] = ff::to_double(acc[0][d]);
+            }
+        }
+    }
+}
+
 template <int ND>
 __global__ void __launch_bounds__(kGroupThreads)
     k_out_grouped(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
@@ -57,74 +136,12 @@ __global__ void __launch_bounds__(kGroupThreads)
             if ((m & 1) && threadIdx.x < ND) F[threadIdx.x * smem_m + m] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
-        for (int r = r0 + warp; r < r1; r += nw) {
-            const float4* vrow = reinterpret_cast<const float4*>(A.vf + A.rowptr[r]);  // rows start on 16 bytes
-            // U independent accumulators per density keep U 16-byte loads in flight per
-            // lane (four for one or two densities; two beyond, where each value is
-            // reused ND times and registers are the scarcer resource)
-            constexpr int U = ND >= 4 ? 2 : 4;
-            ff::F acc[U][ND];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[u][d] = ff::F{0.f, 0.f};
-            for (int q0 = lane; q0 < np; q0 += 32 * U) {
-                float4 v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int q = q0 + 32 * u;
-                    v[u] = q < np ? vrow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int q = q0 + 32 * u;
-                    if (q < np) {
-                        const int k = 2 * q;
-#pragma unroll
-                        for (int d = 0; d < ND; ++d) {
-                            float4 x;
-                            if (staged) {
-                                x = *reinterpret_cast<const float4*>(F + d * smem_m + k);
-                            } else {
-                                const float2 x0 = xf[d * ld_xf + A.cols[c0 + k]];
-                                const float2 x1 = k + 1 < m ? xf[d * ld_xf + A.cols[c0 + k + 1]] : make_float2(0.f, 0.f);
-                                x = make_float4(x0.x, x0.y, x1.x, x1.y);
-                            }
-                            acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].x, v[u].y}, ff::F{x.x, x.y}));
-                            acc[u][d] = ff::add(acc[u][d], ff::mul(ff::F{v[u].z, v[u].w}, ff::F{x.z, x.w}));
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 1; u < U; ++u)
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[0][d] = ff::add(acc[0][d], acc[u][d]);
-#pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float h = __shfl_xor_sync(0xffffffffu, acc[0][d].h, o);
-                    const float l = __shfl_xor_sync(0xffffffffu, acc[0][d].l, o);
-                    acc[0][d] = ff::add(acc[0][d], ff::F{h, l});
-                }
-            }
-            if (lane == 0) {
-                if (mode == kOutWithPsi) {
-                    const int32_t ri = inv[r];
-                    const double wv = w_sorted ? w_sorted[ri] : 1.0;
-#pragma unroll
-                    for (int d = 0; d < ND; ++d)
-                        out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], ff::to_double(acc[0][d]));
-                } else if (mode == kOutAccumulate) {
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) out[d * ld_out + r] += ff::to_double(acc[0][d]);
-                } else {
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) out[d * ld_out + r] = ff::to_double(acc[0][d]);
-                }
-            }
-        }
+        if (staged)
+            grouped_rows<ND, true>(A, r0, r1, c0, m, smem_m, F, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, lane,
+                                   warp, nw);
+        else
+            grouped_rows<ND, false>(A, r0, r1, c0, m, smem_m, F, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode,
+                                    lane, warp, nw);
     }
 }
 
