@@ -36,7 +36,7 @@ struct vp_tricorr_s {
     double* chi = nullptr;       // [n_nodes][n_rule][2]
     double* tau = nullptr;       // [n_nodes][n_rule]
     double* B = nullptr;         // [n_nodes][n_basis][n_rule] (device copy unused; the kernel reads Bf)
-    float2* Bf = nullptr;        // B as hi/lo floats
+    float2* Bf = nullptr;        // B node-major [n_nodes][n_rule][n_basis] as hi/lo floats
     double* logt2 = nullptr;     // [n_nodes][n_rule] 2 log|tau| (tau > 0 nodes)
     float4* logtab = nullptr;    // [128] table of the float-float log
     std::vector<void*> allocs;
@@ -111,21 +111,25 @@ __device__ __forceinline__ void tri_map(const TriGeom& g, double xi, double eta,
     J = fabs(x_xi * y_eta - x_eta * y_xi);
 }
 
-// One block per (target node a, cell). The mapped Green function at each rule
-// node is assembled in float-float on the FP32 pipes from FP64 map values
-// (log r^2 by the float-float table log, in units of the cell's bounding size,
-// log tau^2 precomputed), and the contraction with B_a runs in float-float; the
-// cell map itself (blending map, trigonometry) stays FP64.
+// One block per (target node a, cell). Each warp takes 32 rule nodes at a time:
+// lane l assembles the mapped Green function at node l of the chunk (FP64 cell
+// map; log r^2 by the float-float table log in units of the cell's bounding
+// size, log tau^2 precomputed; the rest in float-float) and parks it in shared
+// memory; then lane b accumulates basis function b (and b + 32) over the chunk
+// from B_a stored node-major (coalesced). Few registers per thread, so that
+// enough warps hide the latency of the FP64 map.
 __global__ void __launch_bounds__(kTcThreads)
     k_tricorr(int64_t n_cells, int32_t n_nodes, int32_t n_basis, int32_t n_rule, const double* __restrict__ geom,
               const double* __restrict__ node_ref, const double* __restrict__ node_w, const double* __restrict__ coef,
-              const double* __restrict__ chi, const double* __restrict__ tau, const float2* __restrict__ Bf,
+              const double* __restrict__ chi, const double* __restrict__ tau, const float2* __restrict__ Bt,
               const double* __restrict__ logt2, const float4* __restrict__ logtab, double* __restrict__ out)
 {
     __shared__ double red[kTcThreads / 32][kTcMaxBasis];
     __shared__ double vhat[kTcMaxBasis];
     __shared__ float4 s_tab[128];
+    __shared__ float2 gs[kTcThreads / 32][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarp = kTcThreads / 32;
     for (int i = tid; i < 128; i += kTcThreads) s_tab[i] = logtab[i];
     __syncthreads();
     for (int64_t blk = blockIdx.x; blk < n_cells * n_nodes; blk += gridDim.x) {
@@ -152,49 +156,52 @@ __global__ void __launch_bounds__(kTcThreads)
                                     (g.v2x - g.v0x) * (g.v2x - g.v0x) + (g.v2y - g.v0y) * (g.v2y - g.v0y)),
                                (g.v2x - g.v1x) * (g.v2x - g.v1x) + (g.v2y - g.v1y) * (g.v2y - g.v1y));
         const double inv_h2 = 1.0 / h2, log_h2 = log(h2);
-        ff::F acc[kTcMaxBasis];
-#pragma unroll
-        for (int b = 0; b < kTcMaxBasis; ++b) acc[b] = ff::F{0.f, 0.f};
+        ff::F acc0{0.f, 0.f}, acc1{0.f, 0.f};  // basis functions lane and lane + 32
         const double* ch = chi + (int64_t)a * n_rule * 2;
         const double* ta = tau + (int64_t)a * n_rule;
         const double* lt = logt2 + (int64_t)a * n_rule;
-        const float2* Ba = Bf + (int64_t)a * n_basis * n_rule;
-        for (int i = tid; i < n_rule; i += kTcThreads) {
-            double x, y, J;
-            tri_map(g, ch[2 * i], ch[2 * i + 1], x, y, J);
-            ff::F gi;
-            if (ta[i] < 0.0) {
-                gi = ff::from_double(kInv2PiT * J);  // the -log t part sits in the weights
-            } else {
-                // -(1/2pi) J log(r / t) = -(1/4pi) J (log(r^2/h^2) + log h^2 - log t^2)
-                const double dx = x - x0, dy = y - y0;
-                const double rs = (dx * dx + dy * dy) * inv_h2;
-                const ff::F r2 = ff::from_double(rs);
-                float S, lo;
-                ff::log_pair(r2.h, r2.l, s_tab, S, lo);
-                const ff::F L = ff::add(ff::F{S, lo}, ff::from_double(log_h2 - lt[i]));
-                gi = ff::mul(L, ff::from_double(-0.5 * kInv2PiT * J));
-            }
-#pragma unroll
-            for (int b = 0; b < kTcMaxBasis; ++b)
-                if (b < n_basis) {
-                    const float2 bv = Ba[(int64_t)b * n_rule + i];
-                    acc[b] = ff::add(acc[b], ff::mul(ff::F{bv.x, bv.y}, gi));
+        const float2* Ba = Bt + (int64_t)a * n_rule * n_basis;
+        for (int base = warp * 32; base < n_rule; base += nwarp * 32) {
+            const int i = base + lane;
+            ff::F gi{0.f, 0.f};
+            if (i < n_rule) {
+                double x, y, J;
+                tri_map(g, ch[2 * i], ch[2 * i + 1], x, y, J);
+                if (ta[i] < 0.0) {
+                    gi = ff::from_double(kInv2PiT * J);  // the -log t part sits in the weights
+                } else {
+                    // -(1/2pi) J log(r / t) = -(1/4pi) J (log(r^2/h^2) + log h^2 - log t^2)
+                    const double dx = x - x0, dy = y - y0;
+                    const ff::F r2 = ff::from_double((dx * dx + dy * dy) * inv_h2);
+                    float S, lo;
+                    ff::log_pair(r2.h, r2.l, s_tab, S, lo);
+                    const ff::F L = ff::add(ff::F{S, lo}, ff::from_double(log_h2 - lt[i]));
+                    gi = ff::mul(L, ff::from_double(-0.5 * kInv2PiT * J));
                 }
-        }
-#pragma unroll
-        for (int b = 0; b < kTcMaxBasis; ++b) {
-            ff::F v = acc[b];
-            for (int o = 16; o > 0; o >>= 1) {
-                const float h = __shfl_xor_sync(0xffffffffu, v.h, o), l = __shfl_xor_sync(0xffffffffu, v.l, o);
-                v = ff::add(v, ff::F{h, l});
             }
-            if (lane == 0) red[warp][b] = ff::to_double(v);
+            gs[warp][lane] = make_float2(gi.h, gi.l);
+            __syncwarp();
+            const int n = min(32, n_rule - base);
+            const float2* Bc = Ba + (int64_t)base * n_basis;
+            for (int j = 0; j < n; ++j) {
+                const ff::F gj{gs[warp][j].x, gs[warp][j].y};
+                if (lane < n_basis) {
+                    const float2 bv = Bc[(int64_t)j * n_basis + lane];
+                    acc0 = ff::add(acc0, ff::mul(ff::F{bv.x, bv.y}, gj));
+                }
+                if (lane + 32 < n_basis) {
+                    const float2 bv = Bc[(int64_t)j * n_basis + lane + 32];
+                    acc1 = ff::add(acc1, ff::mul(ff::F{bv.x, bv.y}, gj));
+                }
+            }
+            __syncwarp();
         }
+        if (lane < n_basis) red[warp][lane] = ff::to_double(acc0);
+        if (lane + 32 < n_basis) red[warp][lane + 32] = ff::to_double(acc1);
         __syncthreads();
         if (tid < n_basis) {
             double v = 0.0;
-            for (int w = 0; w < kTcThreads / 32; ++w) v += red[w][tid];
+            for (int w = 0; w < nwarp; ++w) v += red[w][tid];
             vhat[tid] = v;
         }
         __syncthreads();
@@ -252,13 +259,18 @@ vp_status vp_tricorr_create(vp_tricorr* out, int32_t n_nodes, int32_t n_basis, i
         *dst[k] = (double*)q;
         e = cudaMemcpyAsync(q, src[k], sizes[k] * sizeof(double), cudaMemcpyHostToDevice, s);
     }
-    // B as hi/lo floats, 2 log|tau| per rule node, and the table of the float-float log
+    // B node-major ([n_nodes][n_rule][n_basis]) as hi/lo floats, 2 log|tau| per rule
+    // node, and the table of the float-float log
     std::vector<float> hbf(2 * sizes[5]);
-    for (size_t i = 0; i < sizes[5]; ++i) {
-        const float h = (float)B[i];
-        hbf[2 * i] = h;
-        hbf[2 * i + 1] = (float)(B[i] - (double)h);
-    }
+    for (size_t a = 0; a < (size_t)n_nodes; ++a)
+        for (size_t bb = 0; bb < (size_t)n_basis; ++bb)
+            for (size_t i = 0; i < (size_t)n_rule; ++i) {
+                const double v = B[(a * n_basis + bb) * n_rule + i];
+                const size_t o = (a * n_rule + i) * n_basis + bb;
+                const float h = (float)v;
+                hbf[2 * o] = h;
+                hbf[2 * o + 1] = (float)(v - (double)h);
+            }
     std::vector<double> hlt(sizes[4]);
     for (size_t i = 0; i < sizes[4]; ++i) hlt[i] = tau[i] > 0.0 ? 2.0 * std::log(tau[i]) : 0.0;
     const std::vector<float> hlog = vp::log_table();
