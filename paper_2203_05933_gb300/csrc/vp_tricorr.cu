@@ -183,17 +183,22 @@ __global__ void __launch_bounds__(kTcThreads)
             __syncwarp();
             const int n = min(32, n_rule - base);
             const float2* Bc = Ba + (int64_t)base * n_basis;
+            // the chunk's sum first, then into the running total: the terms cancel
+            // strongly, and short sequential sums keep the float-float rounding small
+            ff::F c0{0.f, 0.f}, c1{0.f, 0.f};
             for (int j = 0; j < n; ++j) {
                 const ff::F gj{gs[warp][j].x, gs[warp][j].y};
                 if (lane < n_basis) {
                     const float2 bv = Bc[(int64_t)j * n_basis + lane];
-                    acc0 = ff::add(acc0, ff::mul(ff::F{bv.x, bv.y}, gj));
+                    c0 = ff::add(c0, ff::mul(ff::F{bv.x, bv.y}, gj));
                 }
                 if (lane + 32 < n_basis) {
                     const float2 bv = Bc[(int64_t)j * n_basis + lane + 32];
-                    acc1 = ff::add(acc1, ff::mul(ff::F{bv.x, bv.y}, gj));
+                    c1 = ff::add(c1, ff::mul(ff::F{bv.x, bv.y}, gj));
                 }
             }
+            acc0 = ff::add(acc0, c0);
+            acc1 = ff::add(acc1, c1);
             __syncwarp();
         }
         if (lane < n_basis) red[warp][lane] = ff::to_double(acc0);
