@@ -65,7 +65,39 @@ struct TriGeom {
     double v0x, v0y, v1x, v1y, v2x, v2y;
     int kind;
     double c0, c1, c2, c3, c4;
+    // curved edge: sin and cos of the start angle (and of k times it for the polar
+    // arc), for the angle-addition form of the edge parametrisation
+    bool small;  // every angle increment along the edge below 0.3 in magnitude
+    double s0, cs0, sk0, ck0;
 };
+
+// sin and cos of a small angle d (|d| <= 0.3) by their Taylor series to d^13 and
+// d^14 (relative error below 1e-16)
+__device__ __forceinline__ void sincos_small(double d, double& sn, double& cs)
+{
+    const double d2 = d * d;
+    sn = d * (1.0 - d2 / 6.0 * (1.0 - d2 / 20.0 * (1.0 - d2 / 42.0 * (1.0 - d2 / 72.0 * (1.0 - d2 / 110.0 *
+                                                                                        (1.0 - d2 / 156.0))))));
+    cs = 1.0 - d2 / 2.0 * (1.0 - d2 / 12.0 * (1.0 - d2 / 30.0 * (1.0 - d2 / 56.0 * (1.0 - d2 / 90.0 *
+                                                                                     (1.0 - d2 / 132.0 *
+                                                                                      (1.0 - d2 / 182.0))))));
+}
+
+// the per-cell part of the curved-edge parametrisation
+__device__ __forceinline__ void tri_prepare(TriGeom& g)
+{
+    g.small = false;
+    g.s0 = g.cs0 = g.sk0 = g.ck0 = 0.0;
+    if (g.kind == 1) {
+        g.small = fabs(g.c4 - g.c3) <= 0.3;
+        sincos(g.c3, &g.s0, &g.cs0);
+    } else if (g.kind == 2) {
+        const double dth = g.c3 - g.c2;
+        g.small = fabs(dth) <= 0.3 && fabs(g.c1 * dth) <= 0.3;
+        sincos(g.c2, &g.s0, &g.cs0);
+        sincos(g.c1 * g.c2, &g.sk0, &g.ck0);
+    }
+}
 
 // Point and Jacobian of the cell map at (xi, eta)
 __device__ __forceinline__ void tri_map(const TriGeom& g, double xi, double eta, double& x, double& y, double& J)
@@ -79,7 +111,14 @@ __device__ __forceinline__ void tri_map(const TriGeom& g, double xi, double eta,
         if (g.kind == 1) {  // circle arc (cx, cy, r, th0, th1)
             const double dth = g.c4 - g.c3;
             double sn, cs;
-            sincos(g.c3 + xi * dth, &sn, &cs);
+            if (g.small) {  // sin and cos of th0 + xi dth by angle addition
+                double sd, cd;
+                sincos_small(xi * dth, sd, cd);
+                sn = fma(g.s0, cd, g.cs0 * sd);
+                cs = fma(g.cs0, cd, -g.s0 * sd);
+            } else {
+                sincos(g.c3 + xi * dth, &sn, &cs);
+            }
             lam = g.c0 + g.c2 * cs;
             mu = g.c1 + g.c2 * sn;
             dlam = -g.c2 * dth * sn;
@@ -88,8 +127,18 @@ __device__ __forceinline__ void tri_map(const TriGeom& g, double xi, double eta,
             const double dth = g.c3 - g.c2;
             const double th = g.c2 + xi * dth;
             double sn, cs, skt, ckt;
-            sincos(th, &sn, &cs);
-            sincos(g.c1 * th, &skt, &ckt);
+            if (g.small) {
+                double sd, cd, skd, ckd;
+                sincos_small(xi * dth, sd, cd);
+                sincos_small(g.c1 * xi * dth, skd, ckd);
+                sn = fma(g.s0, cd, g.cs0 * sd);
+                cs = fma(g.cs0, cd, -g.s0 * sd);
+                skt = fma(g.sk0, ckd, g.ck0 * skd);
+                ckt = fma(g.ck0, ckd, -g.sk0 * skd);
+            } else {
+                sincos(th, &sn, &cs);
+                sincos(g.c1 * th, &skt, &ckt);
+            }
             const double r = 1.0 + g.c0 * ckt, dr = -g.c0 * g.c1 * skt;
             lam = r * cs;
             mu = r * sn;
@@ -149,6 +198,7 @@ __global__ void __launch_bounds__(kTcThreads)
         g.c2 = gp[9];
         g.c3 = gp[10];
         g.c4 = gp[11];
+        tri_prepare(g);
         double x0, y0, J0;
         tri_map(g, node_ref[2 * a], node_ref[2 * a + 1], x0, y0, J0);
         // length unit of the cell: its longest vertex-to-vertex distance squared
