@@ -75,12 +75,26 @@ struct TriGeom {
 // d^14 (relative error below 1e-16)
 __device__ __forceinline__ void sincos_small(double d, double& sn, double& cs)
 {
+    // nested Horner form with the reciprocals as constants (no divisions)
+    constexpr double r6 = 1.0 / 6.0, r20 = 1.0 / 20.0, r42 = 1.0 / 42.0, r72 = 1.0 / 72.0, r110 = 1.0 / 110.0,
+                     r156 = 1.0 / 156.0;
+    constexpr double r2 = 0.5, r12 = 1.0 / 12.0, r30 = 1.0 / 30.0, r56 = 1.0 / 56.0, r90 = 1.0 / 90.0,
+                     r132 = 1.0 / 132.0, r182 = 1.0 / 182.0;
     const double d2 = d * d;
-    sn = d * (1.0 - d2 / 6.0 * (1.0 - d2 / 20.0 * (1.0 - d2 / 42.0 * (1.0 - d2 / 72.0 * (1.0 - d2 / 110.0 *
-                                                                                        (1.0 - d2 / 156.0))))));
-    cs = 1.0 - d2 / 2.0 * (1.0 - d2 / 12.0 * (1.0 - d2 / 30.0 * (1.0 - d2 / 56.0 * (1.0 - d2 / 90.0 *
-                                                                                     (1.0 - d2 / 132.0 *
-                                                                                      (1.0 - d2 / 182.0))))));
+    double t = fma(-d2 * r156, 1.0, 1.0);
+    t = fma(-d2 * r110, t, 1.0);
+    t = fma(-d2 * r72, t, 1.0);
+    t = fma(-d2 * r42, t, 1.0);
+    t = fma(-d2 * r20, t, 1.0);
+    t = fma(-d2 * r6, t, 1.0);
+    sn = d * t;
+    double u = fma(-d2 * r182, 1.0, 1.0);
+    u = fma(-d2 * r132, u, 1.0);
+    u = fma(-d2 * r90, u, 1.0);
+    u = fma(-d2 * r56, u, 1.0);
+    u = fma(-d2 * r30, u, 1.0);
+    u = fma(-d2 * r12, u, 1.0);
+    cs = fma(-d2 * r2, u, 1.0);
 }
 
 // the per-cell part of the curved-edge parametrisation
@@ -146,16 +160,17 @@ __device__ __forceinline__ void tri_map(const TriGeom& g, double xi, double eta,
             dmu = dth * (dr * sn + r * cs);
         }
         const double om = 1.0 - xi;
-        const double gg = l0 / om;
+        const double iom = 1.0 / om;  // one division per node
+        const double gg = l0 * iom;
         const double phx = lam - om * g.v0x - xi * g.v1x;
         const double phy = mu - om * g.v0y - xi * g.v1y;
         x += gg * phx;
         y += gg * phy;
-        const double dg = -eta / (om * om);
+        const double dg = -eta * iom * iom;
         x_xi += dg * phx + gg * (dlam + g.v0x - g.v1x);
         y_xi += dg * phy + gg * (dmu + g.v0y - g.v1y);
-        x_eta -= phx / om;
-        y_eta -= phy / om;
+        x_eta -= phx * iom;
+        y_eta -= phy * iom;
     }
     J = fabs(x_xi * y_eta - x_eta * y_xi);
 }
