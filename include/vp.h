@@ -84,9 +84,10 @@ typedef struct {
  *   VP_KERNEL_MHELMHOLTZ   G(r, r0) = (lambda^2/2pi) K0(lambda |r - r0|)  (L = -Delta + lambda^2)
  * The prefactor lambda^2/2pi is the one the paper states; V then solves
  * (-Delta + lambda^2) V = lambda^2 f. Modified-Helmholtz plans come from
- * vp_plan_create only, evaluate one density per pass (expansions in FP64; near
- * field in float-float on the FP32 pipes, or in FP64 with VP_FLAG_FP64; log r
- * from the float-float table log), support vp_eval, vp_eval_host and
+ * vp_plan_create only and evaluate one density per pass: P2M, M2L, L2P and the
+ * near field (symmetric when the targets are the nodes) in float-float on the
+ * FP32 pipes, M2M, L2L, P2L and M2P in FP64; VP_FLAG_FP64 runs every step in
+ * FP64. They support vp_eval, vp_eval_host, vp_eval_batch and
  * the grad_f part of vp_eval_adjoint (the kernel is symmetric), and reject
  * grad_tgt with VP_ERR_UNSUPPORTED. Plan creation fails with VP_ERR_ARG if
  * lambda * (box half side) puts the expansion tables out of FP64 range (roughly
@@ -96,9 +97,9 @@ typedef struct {
 
 /* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
 #define VP_FLAG_TIMING 1u
-/* Run the near field (direct sums over adjacent leaves) and M2L in FP64 instead of the
- * default float-float evaluation on the FP32 pipes (same result to about 1e-12 relative
- * to the total charge; several times slower on GB300). */
+/* Run the near field (direct sums over adjacent leaves), M2L and the other float-float
+ * steps in FP64 instead of on the FP32 pipes (same result to about 1e-12 relative to
+ * the total charge; several times slower on GB300). */
 #define VP_FLAG_FP64 2u
 /* Capture each distinct vp_eval call (same f, out, leading dimensions and ndens) once
  * into a CUDA graph and replay it afterwards. The first call with new arguments
