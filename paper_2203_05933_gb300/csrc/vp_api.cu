@@ -922,7 +922,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             if (!sym) break;
         }
     }
-    std::vector<int32_t> sym_leaves, in_ptr, in_pptr, in_pbox;
+    std::vector<int32_t> sym_leaves, in_ptr, in_pptr, in_pbox, own;
     std::vector<int64_t> sym_off, in_slot;
     int64_t nslots = 0;
     if (sym) {
@@ -932,23 +932,39 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         std::vector<int32_t> asc(B.leaves);
         std::sort(asc.begin(), asc.end());
         std::vector<int64_t> cost((size_t)nb, 0);
+        own.assign((size_t)nb, 0);
         for (int32_t b : asc) {
             const int64_t nt_b = B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b];
             if (nt_b == 0) continue;
             const int64_t ng = (nt_b + 31) / 32;
+            // own pairs once each when the leaf is small enough and no two of its
+            // points coincide (the coincident-pair bookkeeping stays directed)
+            bool own_ok = ng <= kOwnGroups && p->kernel == VP_KERNEL_LAPLACE;
+            if (own_ok) {
+                std::vector<std::pair<double, double>> pts;
+                for (int32_t j = B.brt[2 * (size_t)b]; j < B.brt[2 * (size_t)b + 1]; ++j)
+                    pts.emplace_back(B.txy[2 * (size_t)j], B.txy[2 * (size_t)j + 1]);
+                std::sort(pts.begin(), pts.end());
+                for (size_t k = 1; k < pts.size() && own_ok; ++k) own_ok = !(pts[k] == pts[k - 1]);
+            }
+            own[(size_t)b] = own_ok ? 1 : 0;
             int64_t work = 0;
             for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
                 const int32_t a = B.u_idx[(size_t)e2];
                 const int64_t na = B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
                 if (a < b || na == 0) continue;
+                if (a == b) {
+                    work += own_ok ? 0 : na;
+                    if (own_ok) p->p2p_evals += nt_b * (nt_b - 1) / 2;
+                    continue;
+                }
                 work += na;
-                if (a == b) continue;
                 sym_off[(size_t)e2] = nslots;
                 for (int64_t gi = 0; gi < ng; ++gi) rin[(size_t)a].push_back(nslots + gi * na);
                 rbox[(size_t)a].push_back(b);
                 nslots += ng * na;
             }
-            cost[(size_t)b] = nt_b * work;
+            cost[(size_t)b] = nt_b * work + (own_ok ? nt_b * (nt_b - 1) / 2 : 0);
             p->p2p_evals += nt_b * work;
         }
         sym_leaves = B.leaves;
@@ -970,7 +986,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             for (int32_t j = B.brt[2 * (size_t)b]; j < B.brt[2 * (size_t)b + 1]; ++j) pt_leaf[(size_t)j] = b;
     }
     int32_t *d_sym_leaves = nullptr, *d_in_ptr = nullptr, *d_in_pptr = nullptr, *d_in_pbox = nullptr,
-            *d_pt_leaf = nullptr;
+            *d_pt_leaf = nullptr, *d_own = nullptr;
     int64_t *d_sym_off = nullptr, *d_in_slot = nullptr;
     if (sym) {
         up(&d_sym_leaves, sym_leaves);
@@ -980,6 +996,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         up(&d_in_pptr, in_pptr);
         up(&d_in_pbox, in_pbox);
         up(&d_pt_leaf, pt_leaf);
+        up(&d_own, own);
     }
     up(&d_up, B.u_ptr);
     up(&d_ui, B.u_idx);
@@ -1097,6 +1114,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     dt.sym_in_pptr = d_in_pptr;
     dt.sym_in_pbox = d_in_pbox;
     dt.sym_pt_leaf = d_pt_leaf;
+    dt.sym_own = d_own;
     dt.sym_slots = nslots;
     DevTables& tb = p->tab;
     tb.H = d_tab + off[0];

@@ -1156,6 +1156,71 @@ __device__ __forceinline__ void p2p_chunk_sym(const float4 rt, const float2* qi,
     }
 }
 
+// Symmetric pass over the warp's own group of at most 32 points (targets and
+// charges are the same points of leaf b, no two coincident): at step t = 1..16
+// lane l takes point j = (l + t) mod 32 (at t = 16 only lanes l < 16, so that
+// each pair is taken once), adds q_j log r^2 to its own sum and sends
+// q_l log r^2 to lane j by a shuffle.
+template <int ND>
+__device__ __forceinline__ void p2p_diag_sym(const float4 rt, const float2* qi, bool valid_i,
+                                             const float4* __restrict__ s_rho,
+                                             const float2 (*__restrict__ s_q)[ND], int n, int lane,
+                                             const float4* __restrict__ s_tab, float* ah, float* al)
+{
+    for (int t = 1; t <= 16; ++t) {
+        const int j = (lane + t) & 31;
+        float vh[ND], vl[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) vh[d] = vl[d] = 0.f;
+        if (valid_i && j < n && (t < 16 || lane < 16)) {
+            const float4 sr = s_rho[j];
+            const float dxs = __fsub_rn(rt.x, sr.x), dxe = __fsub_rn(rt.y, sr.y);
+            const float dys = __fsub_rn(rt.z, sr.z), dye = __fsub_rn(rt.w, sr.w);
+            const float px = __fmul_rn(dxs, dxs);
+            float pxe = fmaf(dxs, dxs, -px);
+            pxe = fmaf(__fadd_rn(dxs, dxs), dxe, pxe);
+            pxe = fmaf(dxe, dxe, pxe);
+            const float py = __fmul_rn(dys, dys);
+            float pye = fmaf(dys, dys, -py);
+            pye = fmaf(__fadd_rn(dys, dys), dye, pye);
+            pye = fmaf(dye, dye, pye);
+            const float rs = __fadd_rn(px, py);
+            float re = __fsub_rn(fminf(px, py), __fsub_rn(rs, fmaxf(px, py)));
+            re = __fadd_rn(re, __fadd_rn(pxe, pye));
+            float S, lo;
+            ff::log_pair(rs, re, s_tab, S, lo);
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const float2 qq = s_q[j][d];
+                const float p = __fmul_rn(qq.x, S);
+                float pe = fmaf(qq.x, S, -p);
+                pe = fmaf(qq.x, lo, pe);
+                pe = fmaf(qq.y, S, pe);
+                float sh, se;
+                ff::two_sum(ah[d], p, sh, se);
+                ah[d] = sh;
+                al[d] = __fadd_rn(al[d], __fadd_rn(se, pe));
+                const float r = __fmul_rn(qi[d].x, S);
+                float re2 = fmaf(qi[d].x, S, -r);
+                re2 = fmaf(qi[d].x, lo, re2);
+                re2 = fmaf(qi[d].y, S, re2);
+                vh[d] = r;
+                vl[d] = re2;
+            }
+        }
+        const int from = (lane - t) & 31;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const float rh = __shfl_sync(0xffffffffu, vh[d], from);
+            const float rl = __shfl_sync(0xffffffffu, vl[d], from);
+            float sh, se;
+            ff::two_sum(ah[d], rh, sh, se);
+            ah[d] = sh;
+            al[d] = __fadd_rn(al[d], __fadd_rn(se, rl));
+        }
+    }
+}
+
 template <int P, int ND, bool SYM>
 __global__ void __launch_bounds__(kLeafThreads)
     k_leaf_ff(DevTree t, PassGeom g, const float2* __restrict__ qf, const float4* __restrict__ Mf,
@@ -1168,6 +1233,11 @@ __global__ void __launch_bounds__(kLeafThreads)
     __shared__ float4 s_rho[kLeafThreads];
     __shared__ float2 s_q[kLeafThreads][ND];
     __shared__ float4 s_tab[128];
+    // own-leaf pairs between groups g < c of 32 points: the sums for group c's
+    // points made by group g's warp, [pair (g, c)][lane][d]
+    constexpr bool kOwn = SYM && ND <= 2;
+    constexpr int kOwnPairs = kOwnGroups * (kOwnGroups - 1) / 2;
+    __shared__ float2 s_own[kOwn ? kOwnPairs : 1][32][kOwn ? ND : 1];
     const int tid = threadIdx.x;
     for (int i = tid; i < 128; i += kLeafThreads) s_tab[i] = logtab[i];
     // persistent blocks pull leaves from a queue (leaves are stored costliest first)
@@ -1182,6 +1252,7 @@ __global__ void __launch_bounds__(kLeafThreads)
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
         const double log_side = t.log_radius[b] + 0.693147180559945309417232121458176568;
+        const bool own_sym = kOwn && t.sym_own[b] != 0;  // block-uniform
         const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
         for (int tb = e0; tb < e1; tb += kLeafThreads) {
@@ -1263,6 +1334,11 @@ __global__ void __launch_bounds__(kLeafThreads)
                 }
                 if (SYM && A < b) continue;
                 const bool rev = SYM && A > b;
+                const bool own = own_sym && A == b;
+                if (own && valid) {  // the coincident self pair, for the leaf-size term
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) qco[d] = ff::add(qco[d], ff::F{qi[d].x, qi[d].y});
+                }
                 const int64_t sbase = rev ? t.sym_off[e] + (int64_t)grp * (a1 - a0) : 0;
                 // same level or one level apart: hi parts differ exactly (both on
                 // the 2^-22 grid after the exact shift/scale), so dx = (th - sh) + (tl - sl)
@@ -1306,11 +1382,53 @@ __global__ void __launch_bounds__(kLeafThreads)
                                 }
                             }
                         }
+                    } else if (own) {
+                        if constexpr (kOwn) {
+                            if (grp_live) {  // warp-uniform
+                                for (int c = 0; c < n; c += 32) {
+                                    const int cg = (sb - a0 + c) >> 5;  // the charges' group
+                                    const int nc = min(32, n - c);
+                                    if (cg < grp) continue;  // that warp handed these pairs over
+                                    if (cg == grp) {
+                                        p2p_diag_sym<ND>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab, ah, al);
+                                    } else {
+                                        float rh[ND], rl[ND];
+#pragma unroll
+                                        for (int d = 0; d < ND; ++d) rh[d] = rl[d] = 0.f;
+                                        p2p_chunk_sym<ND, true>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab,
+                                                                ah, al, rh, rl);
+                                        const int pr = cg * (cg - 1) / 2 + grp;
+#pragma unroll
+                                        for (int d = 0; d < ND; ++d) s_own[pr][lane][d] = make_float2(rh[d], rl[d]);
+                                    }
+                                }
+                            }
+                        }
                     } else if (valid) {
                         if (exact_hi)
                             p2p_tile<ND, true>(rt, s_rho, s_q, n, s_tab, ah, al, qco);
                         else
                             p2p_tile<ND, false>(rt, s_rho, s_q, n, s_tab, ah, al, qco);
+                    }
+                }
+            }
+            if constexpr (kOwn) {
+                if (own_sym) {
+                    // own-leaf sums handed over by the warps of lower groups (this pass's
+                    // other warp, or earlier passes), in a fixed order
+                    __syncthreads();
+                    if (valid) {
+                        for (int gp = 0; gp < grp; ++gp) {
+                            const int pr = grp * (grp - 1) / 2 + gp;
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) {
+                                const float2 v = s_own[pr][lane][d];
+                                float sh, se;
+                                ff::two_sum(ah[d], v.x, sh, se);
+                                ah[d] = sh;
+                                al[d] = __fadd_rn(al[d], __fadd_rn(se, v.y));
+                            }
+                        }
                     }
                 }
             }

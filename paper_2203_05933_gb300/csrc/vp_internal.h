@@ -53,8 +53,15 @@ struct DevTree {
     const int32_t* sym_in_pptr = nullptr; // per box: range of sym_in_pbox
     const int32_t* sym_in_pbox = nullptr; // leaves b that sent slots to a leaf
     const int32_t* sym_pt_leaf = nullptr; // [points] the leaf of each point (tree order)
+    // Within a leaf (at most kOwnGroups groups of 32 points, no two points at the
+    // same coordinates) each pair of its points is also evaluated once: in-warp for
+    // pairs inside a group of 32, and between groups with the partial sums handed
+    // over through shared memory.
+    const int32_t* sym_own = nullptr;     // [nbox] 1: the leaf's own pairs are symmetric
     int64_t sym_slots = 0;
 };
+
+constexpr int kOwnGroups = 4;  // leaves of at most 128 points take the symmetric own-leaf sum
 
 // Translation-operator tables for one expansion order P (P1 = P + 1 entries).
 struct DevTables {
