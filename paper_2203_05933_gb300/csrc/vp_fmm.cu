@@ -1236,6 +1236,7 @@ __global__ void __launch_bounds__(kLeafThreads)
     // own-leaf pairs between groups g < c of 32 points: the sums for group c's
     // points made by group g's warp, [pair (g, c)][lane][d]
     constexpr bool kOwn = SYM && ND <= 2;
+    static_assert(kLeafThreads == 64, "the own-leaf hand-over assumes passes of two groups of 32 targets");
     constexpr int kOwnPairs = kOwnGroups * (kOwnGroups - 1) / 2;
     __shared__ float2 s_own[kOwn ? kOwnPairs : 1][32][kOwn ? ND : 1];
     const int tid = threadIdx.x;
@@ -1388,6 +1389,15 @@ __global__ void __launch_bounds__(kLeafThreads)
                                 for (int c = 0; c < n; c += 32) {
                                     const int cg = (sb - a0 + c) >> 5;  // the charges' group
                                     const int nc = min(32, n - c);
+                                    // pairs with a group of the same pass of 64 targets are
+                                    // summed in both directions by both warps (no barrier
+                                    // inside the pass); pairs with groups of later passes
+                                    // are handed over through shared memory
+                                    const bool same_pass = (cg >> 1) == (grp >> 1) && cg != grp;
+                                    if (same_pass) {
+                                        if (valid) p2p_tile<ND, true>(rt, s_rho + c, s_q + c, nc, s_tab, ah, al, qco);
+                                        continue;
+                                    }
                                     if (cg < grp) continue;  // that warp handed these pairs over
                                     if (cg == grp) {
                                         p2p_diag_sym<ND>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab, ah, al);
@@ -1414,11 +1424,10 @@ __global__ void __launch_bounds__(kLeafThreads)
             }
             if constexpr (kOwn) {
                 if (own_sym) {
-                    // own-leaf sums handed over by the warps of lower groups (this pass's
-                    // other warp, or earlier passes), in a fixed order
-                    __syncthreads();
+                    // own-leaf sums handed over by the warps of earlier passes (written
+                    // before this pass's staging barriers), in a fixed order
                     if (valid) {
-                        for (int gp = 0; gp < grp; ++gp) {
+                        for (int gp = 0; gp < (grp & ~1); ++gp) {
                             const int pr = grp * (grp - 1) / 2 + gp;
 #pragma unroll
                             for (int d = 0; d < ND; ++d) {
