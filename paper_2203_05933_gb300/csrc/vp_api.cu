@@ -948,14 +948,29 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
                 for (size_t k = 1; k < pts.size() && own_ok; ++k) own_ok = !(pts[k] == pts[k - 1]);
             }
             own[(size_t)b] = own_ok ? 1 : 0;
-            int64_t work = 0;
+            int64_t work = 0, own_cost = 0;
             for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
                 const int32_t a = B.u_idx[(size_t)e2];
                 const int64_t na = B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
                 if (a < b || na == 0) continue;
                 if (a == b) {
                     work += own_ok ? 0 : na;
-                    if (own_ok) p->p2p_evals += nt_b * (nt_b - 1) / 2;
+                    if (own_ok) {
+                        // distances evaluated for the leaf's own pairs: each pair inside a
+                        // group of 32 and between groups of different passes of 64 targets
+                        // once, pairs between the two groups of one pass in both directions
+                        int64_t ev = 0;
+                        for (int64_t g1 = 0; g1 < ng; ++g1) {
+                            const int64_t s1 = std::min<int64_t>(32, nt_b - 32 * g1);
+                            ev += s1 * (s1 - 1) / 2;
+                            for (int64_t g2 = g1 + 1; g2 < ng; ++g2) {
+                                const int64_t s2 = std::min<int64_t>(32, nt_b - 32 * g2);
+                                ev += (g1 / 2 == g2 / 2) ? 2 * s1 * s2 : s1 * s2;
+                            }
+                        }
+                        p->p2p_evals += ev;
+                        own_cost = ev;
+                    }
                     continue;
                 }
                 work += na;
@@ -964,7 +979,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
                 rbox[(size_t)a].push_back(b);
                 nslots += ng * na;
             }
-            cost[(size_t)b] = nt_b * work + (own_ok ? nt_b * (nt_b - 1) / 2 : 0);
+            cost[(size_t)b] = nt_b * work + own_cost;
             p->p2p_evals += nt_b * work;
         }
         sym_leaves = B.leaves;
