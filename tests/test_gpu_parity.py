@@ -340,10 +340,13 @@ def test_box_grid_with_area_to_line_corrections():
 
 
 @pytest.mark.parametrize("which", ["boxgrid", "disk"])
-def test_symmetric_near_field_matches_fp64(which):
+@pytest.mark.parametrize("leaf", [32, 128])
+def test_symmetric_near_field_matches_fp64(which, leaf):
     # targets = nodes: the near field is summed once per pair of adjacent leaves
-    # (partial sums handed between leaves); the all-FP64 kernels sum every
-    # directed pair. Forward (three densities: chunks of 2 and 1) and adjoint.
+    # (partial sums handed between leaves) and, within a leaf, once per pair of
+    # its points (in-warp, and across groups of 32 through shared memory at leaf
+    # 128); the all-FP64 kernels sum every directed pair. Forward (three
+    # densities: chunks of 2 and 1) and adjoint.
     if which == "boxgrid":
         prob = inputs.box_grid_problem(nbox=8, order=8, ndens=3)
     else:
@@ -352,10 +355,12 @@ def test_symmetric_near_field_matches_fp64(which):
     g = torch.as_tensor(np.random.default_rng(6).standard_normal((3, prob.n_tgt)), device="cuda")
     res = {}
     for flags in (0, vp.VP_FLAG_FP64):
-        plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=32, max_dens=2, flags=flags,
-                              root=prob.root)
+        plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=leaf, max_dens=2,
+                              flags=flags, root=prob.root)
         info = plan.info()
         assert (info.sym_slots > 0) == (flags == 0)
+        if flags == 0:
+            assert info.p2p_evals < info.p2p_pairs // 2 + info.n_tgt * leaf  # own pairs counted once
         res[flags] = (plan.eval(f).cpu().numpy(), plan.adjoint(g)[0].cpu().numpy())
         plan.close()
     norm = inputs.normaliser(prob)[:, None]
@@ -424,3 +429,25 @@ def test_eval_batch_matches_single_evaluations():
         assert np.array_equal(a, b)
     for pl in plans:
         pl.close()
+
+
+def test_symmetric_near_field_with_coincident_points():
+    # nodes with repeated coordinates: leaves holding two points at the same place
+    # keep the directed own-leaf sum (coincident pairs skipped, the leaf-size term
+    # corrected); the others take the symmetric one. Against the oracle.
+    base = inputs.cloud_problem(3000, 10, ndens=2, seed=83, csr_per_row=0)
+    rng = np.random.default_rng(84)
+    dup = rng.choice(3000, size=300, replace=False)
+    src = np.vstack([base.src_xy, base.src_xy[dup]])
+    w = np.concatenate([base.w, base.w[dup] * 0.5])
+    f = np.hstack([base.f, base.f[:, dup]])
+    csr = inputs.random_csr(src.shape[0], src.shape[0], 8, seed=85)
+    plan = vp.Plan.create(src, w, src.copy(), csr, p_fmm=30, leaf=128, max_dens=2)
+    assert plan.info().sym_slots > 0
+    out = plan.eval(torch.as_tensor(f, device="cuda")).cpu().numpy()
+    ref = oracle.evaluate(src, w, f, src, csr)
+    norm = np.abs(w[None, :] * f).sum(axis=1)[:, None]
+    err = float(np.max(np.abs(out - ref) / norm))
+    print(f"symmetric near field with coincident nodes: rel err {err:.2e}")
+    assert err <= TOL
+    plan.close()
