@@ -34,10 +34,10 @@ __global__ void k_to_ff_rows(int64_t total, int32_t n, const double* __restrict_
     }
 }
 
-// The rows of one group, one warp per row: two independent accumulators per
-// density keep two 16-byte value loads in flight per lane (enough for HBM at this
-// occupancy; four left more lanes idle in the last pass over a row of a few
-// hundred values). STAGED: x[:, cols] sits in shared memory (F, density
+// The rows of one group, one warp per row: U independent accumulators per
+// density keep U 16-byte value loads in flight per lane (four for one or two
+// densities; two beyond, where each value is reused ND times and registers are
+// the scarcer resource). STAGED: x[:, cols] sits in shared memory (F, density
 // d at F + d * smem_m); else it is gathered from xf.
 template <int ND, bool STAGED>
 __device__ __forceinline__ void grouped_rows(const DevGroupedCSR& A, int r0, int r1, int64_t c0, int m, int smem_m,
@@ -46,7 +46,7 @@ __device__ __forceinline__ void grouped_rows(const DevGroupedCSR& A, int r0, int
                                              const float2* __restrict__ xf, int64_t ld_xf, double* __restrict__ out,
                                              int64_t ld_out, int mode, int lane, int warp, int nw)
 {
-    constexpr int U = 2;
+    constexpr int U = ND >= 4 ? 2 : 4;
     const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
     for (int r = r0 + warp; r < r1; r += nw) {
         const float4* vrow = reinterpret_cast<const float4*>(A.vf + A.rowptr[r]);  // rows start on 16 bytes
