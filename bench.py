@@ -44,7 +44,7 @@ P2P_FF_OPS_REVERSE = 14.0   # extra FP32 operations when one evaluation serves b
 PROFILED_TRAFFIC = {
     "leaf": ((15.190528e6 + 1024) / 84050308, "evaluated distances", "profiles/k_leaf_ff_sym_disk_medium.md"),
     "m2l": (3.043e6 / 145118, "V-list pairs", "profiles/k_m2l_ff_disk_medium.md"),
-    "out": ((1298.617e6 + 5.707e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
+    "out": ((1298.617e6 + 5.689e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
 }
 
 
