@@ -691,7 +691,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
         "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
                    "ndens": prob.ndens, "p_fmm": info.p_fmm, "leaf": info.leaf, "levels": info.n_levels,
                    "boxes": info.n_boxes, "p2p_pairs": info.p2p_pairs, "m2l_pairs": info.n_v_pairs,
