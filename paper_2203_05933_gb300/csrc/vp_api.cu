@@ -423,7 +423,6 @@ struct vp_plan_s {
     int kernel = VP_KERNEL_LAPLACE;
     DevMH mh;                   // modified-Helmholtz tables (kernel == VP_KERNEL_MHELMHOLTZ)
     int64_t mh_near_ops = 0;    // modelled FP32 operations of its float-float near field
-    std::vector<int32_t> own_host;  // per box: the leaf's own pairs are symmetric (host copy)
     bool alive = true;
 
     template <typename T>
@@ -940,7 +939,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             const int64_t ng = (nt_b + 31) / 32;
             // own pairs once each when the leaf is small enough and no two of its
             // points coincide (the coincident-pair bookkeeping stays directed)
-            bool own_ok = ng <= kOwnGroups;
+            bool own_ok = ng <= kOwnGroups && p->kernel == VP_KERNEL_LAPLACE;
             if (own_ok) {
                 std::vector<std::pair<double, double>> pts;
                 for (int32_t j = B.brt[2 * (size_t)b]; j < B.brt[2 * (size_t)b + 1]; ++j)
@@ -1013,7 +1012,6 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         up(&d_in_pbox, in_pbox);
         up(&d_pt_leaf, pt_leaf);
         up(&d_own, own);
-        p->own_host = own;
     }
     up(&d_up, B.u_ptr);
     up(&d_ui, B.u_idx);
@@ -1211,36 +1209,16 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
     // when the evaluation serves both directions (symmetric near field)
     p->mh_near_ops = 0;
     for (int32_t b : B.leaves) {
-        const int64_t nt_b = B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b];
-        const std::vector<int32_t>& own_host = p->own_host;
-        int64_t one_way = 0, two_way = 0;  // evaluated distances
+        int64_t own = 0, both = 0;
         for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1]; ++e2) {
             const int32_t a = B.u_idx[(size_t)e2];
             const int64_t na = B.brs[2 * (size_t)a + 1] - B.brs[2 * (size_t)a];
-            if (!p->dt.sym) {
-                one_way += nt_b * na;
-            } else if (a > b) {
-                two_way += nt_b * na;
-            } else if (a == b && !own_host.empty() && own_host[(size_t)b]) {
-                // as the kernel: pairs inside a group of 32 and between groups of
-                // different passes once, the two groups of one pass both ways
-                const int64_t ng = (nt_b + 31) / 32;
-                for (int64_t g1 = 0; g1 < ng; ++g1) {
-                    const int64_t s1 = std::min<int64_t>(32, nt_b - 32 * g1);
-                    two_way += s1 * (s1 - 1) / 2;
-                    for (int64_t g2 = g1 + 1; g2 < ng; ++g2) {
-                        const int64_t s2 = std::min<int64_t>(32, nt_b - 32 * g2);
-                        if (g1 / 2 == g2 / 2) one_way += 2 * s1 * s2;
-                        else two_way += s1 * s2;
-                    }
-                }
-            } else if (a == b) {
-                one_way += nt_b * na;
-            }
+            if (!p->dt.sym || a == b) own += na;
+            else if (a > b) both += na;
         }
         const int code = T.leaf_deg[(size_t)b], deg = code & 0xff, m = code >> 8;
         const int64_t ops = 92 + 2 * (deg - m + 1) + 24 * m;
-        p->mh_near_ops += one_way * ops + two_way * (ops + 14);
+        p->mh_near_ops += (int64_t)(B.brt[2 * (size_t)b + 1] - B.brt[2 * (size_t)b]) * (own * ops + both * (ops + 14));
     }
     cudaError_t e = cudaSuccess;
     double *d_spow = nullptr, *d_na = nullptr, *d_nb = nullptr;

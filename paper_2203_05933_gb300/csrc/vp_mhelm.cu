@@ -473,42 +473,6 @@ __device__ __forceinline__ void mh_chunk_sym(const float4 rt, float2 qi, bool va
     }
 }
 
-// Symmetric pass over the warp's own group of at most 32 points (targets and
-// charges are the same points of leaf b, no two coincident): at step t = 1..16
-// lane l takes point j = (l + t) mod 32 (at t = 16 only lanes l < 16, so that
-// each pair is taken once), adds q_j K to its own sum and sends q_l K to lane j
-// by a shuffle.
-__device__ __forceinline__ void mh_diag_sym(const float4 rt, float2 qi, bool valid_i, const float4* __restrict__ s_rho,
-                                            const float2* __restrict__ s_q, int n, int lane,
-                                            const float4* __restrict__ s_tab, const float2* __restrict__ a2,
-                                            const float2* __restrict__ b2, int deg, int m, ff::F cy, ff::F Tc,
-                                            double lam_side, float& ah, float& al)
-{
-    for (int t = 1; t <= 16; ++t) {
-        const int j = (lane + t) & 31;
-        float vh = 0.0f, vl = 0.0f;
-        if (valid_i && j < n && (t < 16 || lane < 16)) {
-            ff::F K;
-            if (mh_pair<true>(rt, s_rho[j], s_tab, a2, b2, deg, m, cy, Tc, lam_side, K)) {
-                ff_acc(s_q[j], K, ah, al);
-                const float p = __fmul_rn(qi.x, K.h);
-                float pe = fmaf(qi.x, K.h, -p);
-                pe = fmaf(qi.x, K.l, pe);
-                pe = fmaf(qi.y, K.h, pe);
-                vh = p;
-                vl = pe;
-            }
-        }
-        const int from = (lane - t) & 31;
-        const float rh = __shfl_sync(0xffffffffu, vh, from);
-        const float rl = __shfl_sync(0xffffffffu, vl, from);
-        float sh, se;
-        ff::two_sum(ah, rh, sh, se);
-        ah = sh;
-        al = __fadd_rn(al, __fadd_rn(se, rl));
-    }
-}
-
 // ----------------------------------------------------------------------------
 // Per leaf: L2P, M2P over the W list and the direct sum over the U list; one
 // block per leaf, one target per thread. FF: the near field in float-float on
@@ -530,11 +494,6 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
     __shared__ float4 s_tab[FF ? 128 : 1];
     __shared__ double na[kMaxNearTerms], nb[kMaxNearTerms];
     __shared__ float2 a2[kMaxNearTerms], b2[kMaxNearTerms];
-    // own-leaf pairs between groups g < c of 32 points in different passes of 64
-    // targets: group c's sums made by group g's warp, [pair (g, c)][lane]
-    constexpr int kOwnPairs = kOwnGroups * (kOwnGroups - 1) / 2;
-    __shared__ float2 s_own[SYM ? kOwnPairs : 1][32];
-    static_assert(kMhLeafThreads == 64, "the own-leaf hand-over assumes passes of two groups of 32 targets");
     const int tid = threadIdx.x;
     if (tid <= mh.near_deg) {
         na[tid] = mh.near_a[tid];
@@ -549,7 +508,6 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
         const int b = SYM ? t.sym_leaves[li] : t.leaves[li];
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
-        const bool own_sym = SYM && t.sym_own[b] != 0;  // block-uniform
         const int code = mh.leaf_deg[b];  // series terms this leaf's near field needs, and its split
         const int deg = code & 0xff, msplit = code >> 8;
         const double2 cb = t.center[b];
@@ -655,7 +613,6 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
                     if (a0 == a1) continue;
                     if (SYM && A < b) continue;
                     const bool rev = SYM && A > b;
-                    const bool own = own_sym && A == b;
                     const int64_t sbase = rev ? t.sym_off[e] + (int64_t)grp * (a1 - a0) : 0;
                     const float4 uo = t.u_off[e];  // leaf A's centre offset and scale in b units
                     const bool exact_hi = uo.z >= 0.5f && uo.z <= 2.0f;
@@ -691,31 +648,6 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
                                     if (lane < nc) slots[sbase + (sb - a0) + c + lane] = make_float2(rh, rl);
                                 }
                             }
-                        } else if (own) {
-                            if (grp_live) {  // warp-uniform
-                                for (int c = 0; c < n; c += 32) {
-                                    const int cg = (sb - a0 + c) >> 5;  // the charges' group
-                                    const int nc = min(32, n - c);
-                                    // pairs with the other group of this pass: both directions
-                                    // by both warps; with later passes: handed over
-                                    if ((cg >> 1) == (grp >> 1) && cg != grp) {
-                                        if (valid)
-                                            mh_tile<true>(rt, s_rho + c, s_qf + c, nc, s_tab, a2, b2, deg, msplit, cy,
-                                                          Tc, mh.lambda * side, ah, al);
-                                        continue;
-                                    }
-                                    if (cg < grp) continue;  // that warp handed these pairs over
-                                    if (cg == grp) {
-                                        mh_diag_sym(rt, qi, valid, s_rho + c, s_qf + c, nc, lane, s_tab, a2, b2, deg,
-                                                    msplit, cy, Tc, mh.lambda * side, ah, al);
-                                    } else {
-                                        float rh = 0.0f, rl = 0.0f;
-                                        mh_chunk_sym<true>(rt, qi, valid, s_rho + c, s_qf + c, nc, lane, s_tab, a2,
-                                                           b2, deg, msplit, cy, Tc, mh.lambda * side, ah, al, rh, rl);
-                                        s_own[cg * (cg - 1) / 2 + grp][lane] = make_float2(rh, rl);
-                                    }
-                                }
-                            }
                         } else if (valid) {
                             if (exact_hi)
                                 mh_tile<true>(rt, s_rho, s_qf, n, s_tab, a2, b2, deg, msplit, cy, Tc,
@@ -724,17 +656,6 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
                                 mh_tile<false>(rt, s_rho, s_qf, n, s_tab, a2, b2, deg, msplit, cy, Tc,
                                                mh.lambda * side, ah, al);
                         }
-                    }
-                }
-                if (own_sym && valid) {
-                    // own-leaf sums handed over by the warps of earlier passes (written
-                    // before this pass's staging barriers), in a fixed order
-                    for (int gp = 0; gp < (grp & ~1); ++gp) {
-                        const float2 v = s_own[grp * (grp - 1) / 2 + gp][lane];
-                        float sh, se;
-                        ff::two_sum(ah, v.x, sh, se);
-                        ah = sh;
-                        al = __fadd_rn(al, __fadd_rn(se, v.y));
                     }
                 }
                 near = (double)ah + (double)al;
