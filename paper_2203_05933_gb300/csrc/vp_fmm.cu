@@ -1081,8 +1081,9 @@ __device__ __forceinline__ void p2p_tile(const float4 rt, const float4* __restri
 // it adds q_j log r^2 to its own target and q_i log r^2 (q_i the charge at its
 // target) to a float-float accumulator for that source, and the accumulators
 // move one lane down after each step; after 32 steps lane l holds the sum over
-// the warp's targets for source l. rh, rl must be zero on entry.
-template <int ND, bool EXACT>
+// the warp's targets for source l. rh, rl must be zero on entry. FULL: 32
+// sources and 32 valid targets (no per-step test).
+template <int ND, bool EXACT, bool FULL = false>
 __device__ __forceinline__ void p2p_chunk_sym(const float4 rt, const float2* qi, bool valid_i,
                                               const float4* __restrict__ s_rho,
                                               const float2 (*__restrict__ s_q)[ND], int n, int lane,
@@ -1092,7 +1093,7 @@ __device__ __forceinline__ void p2p_chunk_sym(const float4 rt, const float2* qi,
 #pragma unroll 2
     for (int t = 0; t < 32; ++t) {
         const int j = (lane + t) & 31;
-        if (valid_i && j < n) {
+        if (FULL || (valid_i && j < n)) {
             const float4 sr = s_rho[j];
             float dxs, dxe, dys, dye;
             if (EXACT) {
@@ -1370,7 +1371,11 @@ __global__ void __launch_bounds__(kLeafThreads)
                                 float rh[ND], rl[ND];
 #pragma unroll
                                 for (int d = 0; d < ND; ++d) rh[d] = rl[d] = 0.f;
-                                if (exact_hi)
+                                const bool full = nc == 32 && __all_sync(0xffffffffu, valid);  // warp-uniform
+                                if (exact_hi && full)
+                                    p2p_chunk_sym<ND, true, true>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab,
+                                                                  ah, al, rh, rl);
+                                else if (exact_hi)
                                     p2p_chunk_sym<ND, true>(rt, qi, valid, s_rho + c, s_q + c, nc, lane, s_tab, ah,
                                                             al, rh, rl);
                                 else
