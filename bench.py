@@ -42,7 +42,7 @@ P2P_FF_OPS_REVERSE = 14.0   # extra FP32 operations when one evaluation serves b
 # kernels on the medium disk case (profiles/*_disk_medium.md), scaled to a
 # launch by the units it processes; None once a kernel changes until re-profiled.
 PROFILED_TRAFFIC = {
-    "leaf": None,  # full-chunk form of the symmetric pass since the last capture
+    "leaf": ((15.194368e6 + 1024) / 84050308, "evaluated distances", "profiles/k_leaf_ff_sym_disk_medium.md"),
     "m2l": (3.043e6 / 145118, "V-list pairs", "profiles/k_m2l_ff_disk_medium.md"),
     "out": ((1298.617e6 + 5.689e6) / 159866880, "nonzeros", "profiles/k_out_grouped_disk_medium.md"),
 }

@@ -450,9 +450,8 @@ __device__ __forceinline__ void mh_tile(const float4 rt, const float4* __restric
 // b, A != b): as in the Laplace kernel, lane l takes charge (l + t) mod 32 at
 // step t, adds q_j K to its target and q_i K to a float-float sum for that
 // charge, and the sums move one lane down after each step, so that lane l ends
-// with the warp's total for charge l. rh, rl must be zero on entry. FULL: 32
-// charges and 32 valid targets (no per-step test).
-template <bool EXACT, bool FULL = false>
+// with the warp's total for charge l. rh, rl must be zero on entry.
+template <bool EXACT>
 __device__ __forceinline__ void mh_chunk_sym(const float4 rt, float2 qi, bool valid_i, const float4* __restrict__ s_rho,
                                              const float2* __restrict__ s_q, int n, int lane,
                                              const float4* __restrict__ s_tab, const float2* __restrict__ a2,
@@ -462,7 +461,7 @@ __device__ __forceinline__ void mh_chunk_sym(const float4 rt, float2 qi, bool va
     const int from = (lane + 1) & 31;
     for (int t = 0; t < 32; ++t) {
         const int j = (lane + t) & 31;
-        if (FULL || (valid_i && j < n)) {
+        if (valid_i && j < n) {
             ff::F K;
             if (mh_pair<EXACT>(rt, s_rho[j], s_tab, a2, b2, deg, m, cy, Tc, lam_side, K)) {
                 ff_acc(s_q[j], K, ah, al);
@@ -640,12 +639,7 @@ __global__ void __launch_bounds__(kMhLeafThreads, SYM ? 10 : 16)
                                 for (int c = 0; c < n; c += 32) {
                                     const int nc = min(32, n - c);
                                     float rh = 0.0f, rl = 0.0f;
-                                    const bool full = nc == 32 && __all_sync(0xffffffffu, valid);  // warp-uniform
-                                    if (exact_hi && full)
-                                        mh_chunk_sym<true, true>(rt, qi, valid, s_rho + c, s_qf + c, nc, lane, s_tab,
-                                                                 a2, b2, deg, msplit, cy, Tc, mh.lambda * side, ah, al,
-                                                                 rh, rl);
-                                    else if (exact_hi)
+                                    if (exact_hi)
                                         mh_chunk_sym<true>(rt, qi, valid, s_rho + c, s_qf + c, nc, lane, s_tab, a2, b2,
                                                            deg, msplit, cy, Tc, mh.lambda * side, ah, al, rh, rl);
                                     else
