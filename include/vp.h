@@ -40,7 +40,13 @@
  *   - Every entry point returns a vp_status. No exception crosses the ABI. On
  *     error the output buffers hold unspecified values and the plan stays
  *     usable unless the status is VP_ERR_CUDA (sticky CUDA errors).
- *   - Arithmetic is IEEE float64 throughout.
+ *   - Arithmetic: by default every floating-point operation of an evaluation
+ *     (charges, FMM, near field with the library's own table-driven FP64 log,
+ *     correction product) is IEEE float64 on the FP64 pipes. VP_FLAG_FF moves
+ *     the heavy steps to the FP32 pipes in float-float arithmetic (an
+ *     unevaluated sum of two floats, about 48 significant bits, narrower than
+ *     float64 in significand and exponent range) with float64 inputs and
+ *     outputs; VP_FLAG_FP64 selects the plain float64 reference kernels.
  */
 #ifndef VP_H
 #define VP_H
@@ -57,7 +63,8 @@ typedef enum {
                                point outside a caller-given root box, ld < n            */
     VP_ERR_CUDA = 2,        /* a CUDA runtime call failed (message: vp_last_error)        */
     VP_ERR_OOM = 3,         /* device or host allocation failed                           */
-    VP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                         */
+    VP_ERR_TIMEOUT = 4,     /* reserved: no kernel of this library waits on the device, so
+                               no entry point returns it                                  */
     VP_ERR_UNSUPPORTED = 5, /* option outside the compiled set (e.g. p_fmm not built)     */
     VP_ERR_STATE = 6        /* plan used after destroy, or on another device              */
 } vp_status;
@@ -97,10 +104,21 @@ typedef struct {
 
 /* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
 #define VP_FLAG_TIMING 1u
-/* Run the near field (direct sums over adjacent leaves), M2L and the other float-float
- * steps in FP64 instead of on the FP32 pipes (same result to about 1e-12 relative to
- * the total charge; several times slower on GB300). */
+/* Arithmetic of a plan (fixed at creation; the two flags exclude each other).
+ * Default (neither flag): every step in float64 on the FP64 pipes, shaped for GB300's
+ * FP64 rate: near field with the library's own table-driven float64 logarithm (within
+ * about 1.5 ulp) and each distance between two adjacent leaves evaluated once for both
+ * directions when the targets are the nodes; M2L, P2M/M2M, L2L, L2P in float64 with all
+ * lanes busy; correction product with float64 values.
+ * VP_FLAG_FP64: the plain float64 reference kernels (directed near field with CUDA's
+ * log, one warp per box and coefficient lane for the expansions); the target gradient
+ * of vp_eval_adjoint always runs these.
+ * VP_FLAG_FF: the near field, M2L, P2M/M2M/L2L/L2P and the correction product on the
+ * FP32 pipes in float-float arithmetic (about 48 significant bits, narrower than
+ * float64; float64 inputs and outputs), several times faster on GB300; the results
+ * agree with the float64 ones to about 1e-12 of the total charge. */
 #define VP_FLAG_FP64 2u
+#define VP_FLAG_FF 8u
 /* Capture each distinct vp_eval call (same f, out, leading dimensions and ndens) once
  * into a CUDA graph and replay it afterwards. The first call with new arguments
  * synchronizes `stream` and captures on a plan-owned stream; later calls only launch
@@ -320,6 +338,15 @@ vp_status vp_plan_destroy(vp_plan plan);
  * lambda). */
 vp_status vp_green_eval_host(int32_t kernel, double lambda, int64_t n, const double* r, double* g);
 
+/* Roofline denominators measured on the current device at its present clocks:
+ * sustained FP64 and FP32 fused multiply-add throughput in TFLOP/s (2 flops per FMA),
+ * from chains of independent FMAs in every lane of a full grid (best of two timed
+ * launches after a warm-up launch, CUDA events on `stream`). The paper has no
+ * counterpart: this supports the measurement of the kernels against their roofline.
+ * Allocates and frees a small device buffer and synchronizes `stream`. Takes
+ * about 0.1 s. Errors: VP_ERR_ARG (NULL output), VP_ERR_OOM, VP_ERR_CUDA. */
+vp_status vp_measure_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
+
 /* Static description of a status code; never NULL. */
 const char* vp_status_string(int32_t status);
 
@@ -460,9 +487,19 @@ vp_status vp_tricorr_destroy(vp_tricorr tc);
  * exits. Limits: n_src + n_tgt <= VP_STATIC_SCRATCH_DOUBLES, else VP_ERR_ARG
  * ("problem too large for the static scratch"; see vp_last_error).
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture that should contain later calls. All calls share
+ * Argument checks: src_xy and tgt_xy must be 16-byte aligned (they are read
+ * as pairs of doubles), else VP_ERR_ARG; a correction matrix with n_src == 0
+ * is rejected with VP_ERR_ARG. The CSR itself is trusted, not validated:
+ * rowptr must be non-decreasing with rowptr[0] = 0 and every column index in
+ * [0, n_src). Validating it would need a pass with scratch of its own; a
+ * malformed CSR makes the kernel read outside f (undefined results or a device
+ * fault), so pass one built or validated by vp_plan_create's rules.
+ *
+ * Each call made outside a stream capture looks up the array's device address
+ * (cudaGetSymbolAddress, with the device current); a call made while `stream`
+ * is being captured reuses the address of the last uncaptured call on that
+ * device, so make one call before any stream capture that should contain
+ * later calls (else VP_ERR_STATE). All calls share
  * the one array and it keeps the last call's contents; every element a call
  * reads is written earlier in the same call, so nothing needs clearing. Calls
  * whose work overlaps on the GPU (different streams, or different host threads

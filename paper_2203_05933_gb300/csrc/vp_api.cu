@@ -272,13 +272,14 @@ struct HostGroups {
     std::vector<int32_t> g_r0;
     std::vector<int64_t> g_c0;
     std::vector<int32_t> cols;
-    std::vector<int64_t> rowptr;  // row starts in vf (rows padded to even lengths)
-    std::vector<float> vf;
+    std::vector<int64_t> rowptr;  // row starts in vf / vd (rows padded to even lengths)
+    std::vector<float> vf;        // hi/lo float pairs (float-float plans)
+    std::vector<double> vd;       // float64 values (float64 plans)
     int32_t max_m = 0;
 };
 
 void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
-                  const std::vector<double>& val, HostGroups& G)
+                  const std::vector<double>& val, bool as_f64, HostGroups& G)
 {
     int64_t start = -1;
     for (int64_t i = 0; i < nrows; ++i) {
@@ -305,6 +306,13 @@ void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::
     for (int64_t i = 0; i < nrows; ++i) {
         const int64_t len = rowptr[(size_t)i + 1] - rowptr[(size_t)i];
         G.rowptr[(size_t)i + 1] = G.rowptr[(size_t)i] + len + (len & 1);
+    }
+    if (as_f64) {
+        G.vd.assign((size_t)G.rowptr[(size_t)nrows], 0.0);
+        for (int64_t i = 0; i < nrows; ++i)
+            for (int64_t k = rowptr[(size_t)i]; k < rowptr[(size_t)i + 1]; ++k)
+                G.vd[(size_t)(G.rowptr[(size_t)i] + (k - rowptr[(size_t)i]))] = val[(size_t)k];
+        return;
     }
     G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
     for (int64_t i = 0; i < nrows; ++i)
@@ -368,6 +376,7 @@ struct vp_plan_s {
     int max_dens = 1;
     int nd_cap = 1;
     uint32_t flags = 0;
+    Arith arith = Arith::kF64;  // fixed at creation from VP_FLAG_FF / VP_FLAG_FP64
     int64_t n_src = 0, n_tgt = 0, nnz = 0;
     int64_t n_f = 0;            // density length: n_src, or the p-nodes of an upsampled plan
     bool ups = false;           // charges interpolated per cell from the p-nodes (oversampling)
@@ -394,7 +403,7 @@ struct vp_plan_s {
     int64_t* cptr = nullptr;
     int32_t* crow = nullptr;
     double* cval = nullptr;
-    bool grouped = false;       // correction applied by the grouped float-float kernel
+    bool grouped = false;       // correction applied by a grouped kernel (float64, or float-float with VP_FLAG_FF)
     DevGroupedCSR gfwd, gadj;   // Pi and Pi^T, rows grouped by shared column lists
     Workspace ws;
     PhaseTimer timer;
@@ -504,7 +513,10 @@ PassGeom adjoint_geom(vp_plan p)
     return g;
 }
 
-bool use_fp64(vp_plan p) { return (p->flags & VP_FLAG_FP64) != 0; }
+// plain float64 reference kernels (VP_FLAG_FP64)
+bool use_fp64(vp_plan p) { return p->arith == Arith::kPlain; }
+// float-float kernels on the FP32 pipes (VP_FLAG_FF)
+bool use_ff(vp_plan p) { return p->arith == Arith::kFF; }
 
 }  // namespace
 
@@ -526,7 +538,7 @@ const char* vp_status_string(int32_t status)
 
 const char* vp_last_error(void) { return g_last_error.c_str(); }
 
-const char* vp_version(void) { return "libvp 0.1 sm_103a fp64"; }
+const char* vp_version(void) { return "libvp 0.2 sm_103a fp64"; }
 
 }  // extern "C"
 
@@ -855,6 +867,9 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     size_t off[7];
     std::vector<double> tables = make_tables(P, off);
     std::vector<float> logtab = make_log_table();
+    std::vector<double2> log64;
+    std::vector<double> elog64;
+    make_log64_tables(log64, elog64);
     size_t offf[8];
     std::vector<float> fftab = make_ff_tables(P, offf);
 
@@ -908,7 +923,9 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_leaves, B.leaves);
     // symmetric near field when the charge points of both passes are the evaluation
     // points (same coordinates, same tree order) and the U lists are symmetric
-    bool sym = !(p->flags & VP_FLAG_FP64) && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
+    // (the modified-Helmholtz kernel has a symmetric form on its float-float path only)
+    const bool sym_kernel = p->kernel == VP_KERNEL_LAPLACE ? p->arith != Arith::kPlain : p->arith == Arith::kFF;
+    bool sym = sym_kernel && n_src == n_tgt && n_src > 0 && B.sxy == B.txy && B.brs == B.brt;
     if (sym) {
         for (int32_t b : B.leaves) {
             for (int32_t e2 = B.u_ptr[(size_t)b]; e2 < B.u_ptr[(size_t)b + 1] && sym; ++e2) {
@@ -939,7 +956,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             const int64_t ng = (nt_b + 31) / 32;
             // own pairs once each when the leaf is small enough and no two of its
             // points coincide (the coincident-pair bookkeeping stays directed)
-            bool own_ok = ng <= kOwnGroups && p->kernel == VP_KERNEL_LAPLACE;
+            // (float-float Laplace kernel only; the float64 kernel sums a leaf's own pairs directed)
+            bool own_ok = ng <= kOwnGroups && p->kernel == VP_KERNEL_LAPLACE && p->arith == Arith::kFF;
             if (own_ok) {
                 std::vector<std::pair<double, double>> pts;
                 for (int32_t j = B.brt[2 * (size_t)b]; j < B.brt[2 * (size_t)b + 1]; ++j)
@@ -1025,6 +1043,10 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     float *d_logtab = nullptr, *d_srho = nullptr, *d_trho = nullptr, *d_fftab = nullptr;
     int32_t* d_level = nullptr;
     up(&d_logtab, logtab);
+    double2* d_log64 = nullptr;
+    double* d_elog64 = nullptr;
+    up(&d_log64, log64);
+    up(&d_elog64, elog64);
     up(&d_fftab, fftab);
     up(&d_srho, B.srho);
     up(&d_trho, B.trho);
@@ -1034,7 +1056,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_xoff, B.xoff);
     p->src_rho = (float4*)d_srho;
     p->tgt_rho = (float4*)d_trho;
-    p->grouped = has_corr && !(p->flags & VP_FLAG_FP64);
+    p->grouped = has_corr && p->arith != Arith::kPlain;
     if (has_corr && !p->grouped) {
         up(&p->rowptr, B.hrow);
         up(&p->col, B.hcol);
@@ -1048,16 +1070,21 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             HostGroups G;
             const bool fwd = pass == 0;
             const int64_t nrows = fwd ? n_tgt : n_cols;
-            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval, G);
+            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval,
+                         p->arith == Arith::kF64, G);
             DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
             int32_t *d_r0 = nullptr, *d_cols = nullptr;
             int64_t *d_c0 = nullptr, *d_rp = nullptr;
             float* d_vf = nullptr;
+            double* d_vd = nullptr;
             up(&d_r0, G.g_r0);
             up(&d_c0, G.g_c0);
             up(&d_cols, G.cols);
             up(&d_rp, G.rowptr);
-            up(&d_vf, G.vf);
+            if (p->arith == Arith::kF64)
+                up(&d_vd, G.vd);
+            else
+                up(&d_vf, G.vf);
             A.nrows = (int32_t)nrows;
             A.ngroups = (int32_t)G.g_r0.size() - 1;
             A.max_m = G.max_m;
@@ -1066,6 +1093,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
             A.cols = d_cols;
             A.rowptr = d_rp;
             A.vf = (const float2*)d_vf;
+            A.vd = d_vd;
         }
     }
     const int P1 = P + 1;
@@ -1140,6 +1168,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.log2o = d_tab + off[5];
     tb.zpow = (const double2*)(d_tab + off[6]);
     tb.logtab = (const float4*)d_logtab;
+    tb.log64 = d_log64;
+    tb.elog64 = d_elog64;
     tb.Hf = (const float2*)(d_fftab + offf[0]);
     tb.tpowf = (const float4*)(d_fftab + offf[1]);
     tb.mtpowf = (const float4*)(d_fftab + offf[2]);
@@ -1149,7 +1179,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.Blf = (const float2*)(d_fftab + offf[6]);
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
-                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off};
+                           p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
+                           tb.log64, p->gfwd.vd, p->gadj.vd};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
                           p->gfwd.vf, p->gadj.vf};
     bool ok = true;
@@ -1174,6 +1205,8 @@ vp_status plan_options(const vp_options* opt_in, vp_options& opt, int& P, int& l
         return fail(VP_ERR_ARG, "unknown kernel");
     if (opt.kernel == VP_KERNEL_MHELMHOLTZ && !(opt.lambda > 0.0 && std::isfinite(opt.lambda)))
         return fail(VP_ERR_ARG, "the modified-Helmholtz kernel needs a finite lambda > 0");
+    if ((opt.flags & VP_FLAG_FF) && (opt.flags & VP_FLAG_FP64))
+        return fail(VP_ERR_ARG, "VP_FLAG_FF and VP_FLAG_FP64 exclude each other");
     return VP_OK;
 }
 
@@ -1201,7 +1234,7 @@ vp_status setup_mh(vp_plan p, const Built& B, double lambda, cudaStream_t s)
                                                            std::sqrt(2.0) * (B.radius[(size_t)a] + B.radius[(size_t)b]));
         }
     MhTables T;
-    const std::string err = make_mh_tables(p->P, lambda, R, dmax, !(p->flags & VP_FLAG_FP64), T);
+    const std::string err = make_mh_tables(p->P, lambda, R, dmax, use_ff(p), T);
     if (!err.empty()) return fail(VP_ERR_ARG, err);
     // FP32 operations of the float-float near field per evaluation (one density):
     // per evaluated distance about 92 + 2 (deg - m + 1) + 24 m (distance, table log,
@@ -1264,6 +1297,7 @@ vp_plan new_plan(const vp_options& opt, int P, int leaf, int max_dens)
     p->kernel = opt.kernel;
     p->nd_cap = opt.kernel == VP_KERNEL_MHELMHOLTZ ? 1 : chunk_for(max_dens, 8);
     p->flags = (uint32_t)opt.flags;
+    p->arith = (p->flags & VP_FLAG_FF) ? Arith::kFF : (p->flags & VP_FLAG_FP64) ? Arith::kPlain : Arith::kF64;
     p->timer.on = (p->flags & VP_FLAG_TIMING) != 0;
     return p;
 }
@@ -1493,6 +1527,11 @@ vp_status grouped_apply(vp_plan p, int nd, const DevGroupedCSR& A, int64_t ncols
                         const double* w, const double* psi, const double* x, int64_t ld_x, double* out,
                         int64_t ld_out, int mode, int max_blocks, cudaStream_t s)
 {
+    if (p->arith == Arith::kF64) {
+        VP_CUDA(launch_out_grouped64(nd, A, inv, w, psi, x, ld_x, out, ld_out, mode, max_blocks, s));
+        p->last_launches += 1;
+        return VP_OK;
+    }
     VP_CUDA(launch_to_ff_rows(nd, (int32_t)ncols, x, ld_x, p->ws.xf, s));
     VP_CUDA(launch_out_grouped(nd, A, inv, w, psi, p->ws.xf, ncols, out, ld_out, mode, max_blocks, s));
     p->last_launches += 2;
@@ -1503,7 +1542,8 @@ vp_status grouped_apply(vp_plan p, int nd, const DevGroupedCSR& A, int64_t ncols
 cudaError_t run_fmm(vp_plan p, int nd, const PassGeom& g, bool gradient, PhaseTimer* tm, cudaStream_t s)
 {
     if (p->kernel == VP_KERNEL_MHELMHOLTZ)
-        return launch_fmm_mhelm(p->P, p->dt, p->mh, p->tab.logtab, g, p->ws, use_fp64(p), tm, s);
+        return launch_fmm_mhelm(p->P, p->dt, p->mh, p->tab.logtab, g, p->ws, !use_ff(p), tm, s);
+    if (p->arith == Arith::kF64 && !gradient) return launch_fmm64(p->P, nd, p->dt, p->tab, g, p->ws, tm, s);
     return launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, gradient, use_fp64(p), tm, s);
 }
 
@@ -1520,13 +1560,17 @@ vp_status enqueue_eval(vp_plan p, int32_t ndens, const double* f, int64_t ld_f, 
         // charges, P2M (+ M2M in the same launch on the float-float path, else per
         // level from level 2 up), M2L, L2L per level from level 3 down, leaf (+ slot
         // reduction), output
-        const bool ffp = !use_fp64(p);
         // (the output launches are counted where they are made)
-        if (p->kernel == VP_KERNEL_MHELMHOLTZ)
-            p->last_launches += 1 + mhelm_launches(p->dt.nlevels, p->dt.sym && ffp);
-        else
+        if (p->kernel == VP_KERNEL_MHELMHOLTZ) {
+            p->last_launches += 1 + mhelm_launches(p->dt.nlevels, p->dt.sym && use_ff(p));
+        } else if (p->arith == Arith::kF64) {
+            // charges, upward (P2M + M2M), M2L, L2L per level from 3, leaf (+ slot reduction)
+            p->last_launches += 4 + (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym ? 1 : 0);
+        } else {
+            const bool ffp = use_ff(p);
             p->last_launches += 4 + (ffp ? 0 : (int64_t)std::max(0, p->dt.nlevels - 3)) +
-                                (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && nd <= 2 ? 1 : 0);
+                                (int64_t)std::max(0, p->dt.nlevels - 3) + (p->dt.sym && ffp && nd <= 2 ? 1 : 0);
+        }
         const double* fc = f + (int64_t)d0 * ld_f;
         double* oc = out + (int64_t)d0 * ld_out;
         // Pi f does not depend on the FMM: outside phase timing it runs beside the

@@ -1,0 +1,751 @@
+// FMM kernels (Laplace kernel) in IEEE float64 arithmetic, shaped for GB300's
+// narrow FP64 pipe (2 DFMA per clock per SM): every kernel keeps all 32 lanes
+// of its FP64 instructions busy and spends as few FP64 operations per unit of
+// work as the arithmetic allows; integer, shared-memory and shuffle work is
+// cheap beside them and is used freely. This is the default arithmetic of
+// libvp (arXiv 2203.05933: the smooth-quadrature point sum of
+// Eq. Tk_smooth_quad evaluated by a point FMM, Sec. 4).
+//
+// Conventions as in vp_fmm.cu: psi(z) = Re sum_j q_j log(z - z_j), expansions
+// scaled by the box half-side R (M_k = a_k / R^k, L_l = b_l R^l), the same
+// scaled translation operators.
+//
+// Near field. Coordinates are the absolute float64 node coordinates (as in the
+// direct sum), so dx, dy are the exact differences of the inputs for nearby
+// points. log r^2 comes from an own table-driven logarithm (the method of
+// P. T. P. Tang, "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 16(4), 1990): with r^2 = 2^e m and c_k
+// the table point nearest m (spacing 2^-12),
+//     log r^2 = e log 2 + T_k + log1p(u),   u = m s_k - 1,   T_k = -log s_k,
+// where s_k = RN(1/c_k) is a float64 and T_k is its exact logarithm rounded
+// once, so the split is exact whatever the rounding of s_k; |u| <= 2^-13 and
+// log1p(u) = u (1 - u/2 + u^2/3) has truncation error below 2^-54. u is one FMA
+// of r^2 with s_k 2^-e (the power of two is applied to s_k's exponent field by
+// an integer add, exactly); the sum e log 2 + T_k is one addition of two table
+// values, and the last multiplication of the series is fused with the final
+// addition: log r^2 = fma(u, 1 - u/2 + u^2/3, e log 2 + T_k). That is 5 FP64
+// operations per logarithm. Error: the roundings of e log 2, T_k and their sum
+// (each at most half an ulp of numbers below max(1, |e| log 2)) plus the final
+// rounding, so |error| <= 2^-52 max(1, |e| log 2) + half an ulp of the result:
+// about one ulp of log r^2 wherever |log r^2| >= 1, an absolute 2^-52 near
+// r^2 = 1 (tested against CUDA's log through the public API). With the squares
+// and differences, one directed pair costs 10 FP64 operations; a pair
+// evaluated once for both directions costs 11.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+constexpr int kW64 = 4;             // warps per block of the expansion kernels
+constexpr int kLeafWarps64 = 8;     // warps per block of the near-field kernel
+constexpr int kEBias = 64;          // exponent table covers e in [-64, 63]
+
+__device__ __forceinline__ double2 cmul64(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// a * b + c
+__device__ __forceinline__ double2 cfma64(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__device__ __forceinline__ int gwarp() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int nwarps() { return (int)((gridDim.x * blockDim.x) >> 5); }
+
+// CUDA's log for the pairs outside the table's exponent range (kept out of line:
+// it is not met on the hot path).
+__device__ __noinline__ double log_r2_slow(double r2) { return r2 == 0.0 ? 0.0 : log(r2); }
+
+// log(r2) by the table-driven method above. tab[k] = (s_k, T_k), etab[e + 64] =
+// e log 2. r2 == 0 (a bitwise-coincident pair) gives 0 (no smooth term);
+// r2 outside [2^-64, 2^63] takes CUDA's log (not met by nodes of a domain of
+// size O(1) unless two of them are within 2^-32 of each other).
+__device__ __forceinline__ double log_r2(double r2, const double2* __restrict__ tab, const double* __restrict__ etab)
+{
+    const int hi = __double2hiint(r2);
+    const int h = hi + (1 << (19 - kLog64Bits));       // round m to the nearest table point
+    const int e = (h >> 20) - 1023;                      // exponent of 2^e c_k
+    const int k = (h >> (20 - kLog64Bits)) & ((1 << kLog64Bits) - 1);
+    const double2 sk = tab[k];
+    const int ei = min(max(e + kEBias, 0), 2 * kEBias - 1);
+    const double s = __hiloint2double(__double2hiint(sk.x) - (e << 20), __double2loint(sk.x));  // s_k 2^-e
+    const double u = fma(r2, s, -1.0);
+    const double b = fma(u, fma(u, 0x1.5555555555555p-2, -0.5), 1.0);  // 1 - u/2 + u^2/3
+    double L = fma(u, b, etab[ei] + sk.y);
+    if ((unsigned)(e + kEBias) >= (unsigned)(2 * kEBias)) L = log_r2_slow(r2);
+    return L;
+}
+
+// ----------------------------------------------------------------------------
+// a5 + a6: near field, L2P and W-list M2P of one leaf per warp (persistent
+// warps pull leaves from a queue, costliest first). Lane i holds one
+// evaluation point of the current group of 32; the sources of each U-list leaf
+// are staged 32 at a time in the warp's shared buffer.
+// SYM (evaluation points are the charge points, same tree order): leaves
+// A < b are skipped, A == b is summed directed (coincident pairs give 0), and
+// for A > b each distance is evaluated once: at step t lane l takes source
+// (l + t) mod 32, adds q_j log r^2 to its own point and q_i log r^2 to an
+// accumulator for that source, which moves one lane down each step; after 32
+// steps lane l holds the group's sum for source l and writes it to the slot of
+// (b, A, group), added to A's points by k_sym_reduce64 in a fixed order.
+template <int ND>
+struct LeafStage64 {
+    double2 xy[32];
+    double q[32][ND];
+};
+
+template <int P, int ND, bool SYM>
+__global__ void __launch_bounds__(kLeafWarps64 * 32)
+    k_leaf64(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
+             const double2* __restrict__ L, const double2* __restrict__ logtab, const double* __restrict__ etab_g,
+             double* __restrict__ psi, int* __restrict__ work, double* __restrict__ slots)
+{
+    constexpr int P1 = P + 1;
+    extern __shared__ __align__(16) unsigned char smem64[];
+    double2* tab = reinterpret_cast<double2*>(smem64);                       // [1 << kLog64Bits]
+    double* etab = reinterpret_cast<double*>(tab + (1 << kLog64Bits));       // [2 * kEBias]
+    LeafStage64<ND>* stage = reinterpret_cast<LeafStage64<ND>*>(etab + 2 * kEBias);
+    for (int i = threadIdx.x; i < (1 << kLog64Bits); i += blockDim.x) tab[i] = logtab[i];
+    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) etab[i] = etab_g[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    LeafStage64<ND>& st = stage[threadIdx.x >> 5];
+
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(work, 1);
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= t.nleaf) break;
+        const int b = SYM ? t.sym_leaves[li] : t.leaves[li];
+        const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
+        if (e0 == e1) continue;
+        const double2 cb = t.center[b];
+        const double invRb = 1.0 / t.radius[b];
+        const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
+        const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
+        for (int gb = e0; gb < e1; gb += 32) {
+            const int grp = (gb - e0) >> 5;
+            const int ti = gb + lane;
+            const bool valid = ti < e1;
+            const double2 z = valid ? g.exy[ti] : cb;
+            double acc[ND], near[ND], qi[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                acc[d] = 0.0;
+                near[d] = 0.0;
+                qi[d] = (SYM && valid) ? q[(int64_t)ti * ND + d] : 0.0;
+            }
+            // L2P: Re sum_l L_l u^l by Horner, u = (z - c)/R
+            {
+                const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
+                const double2* Lb = L + (int64_t)b * P1 * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double2 s = Lb[P * ND + d];
+#pragma unroll 4
+                    for (int l = P - 1; l >= 0; --l) s = cfma64(s, u, Lb[l * ND + d]);
+                    acc[d] = s.x;
+                }
+            }
+            // M2P over W: M_0 log|z - c| + Re sum_k M_k v^k, v = R/(z - c)
+            for (int e = w0; e < w1; ++e) {
+                const int D = t.w_idx[e];
+                const double2 cD = t.center[D];
+                const double RD = t.radius[D];
+                const double dx = z.x - cD.x, dy = z.y - cD.y;
+                const double r2 = fma(dx, dx, dy * dy);
+                const double2 v = make_double2(dx / r2 * RD, -dy / r2 * RD);
+                const double lg = 0.5 * log_r2(r2, tab, etab);
+                const double2* MD = M + (int64_t)D * P1 * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double2 s = make_double2(0.0, 0.0);
+#pragma unroll 2
+                    for (int k = P; k >= 1; --k) {
+                        const double2 m = MD[k * ND + d];
+                        s = cmul64(make_double2(s.x + m.x, s.y + m.y), v);
+                    }
+                    acc[d] += fma(MD[d].x, lg, s.x);
+                }
+            }
+            // P2P over U
+            for (int e = u0; e < u1; ++e) {
+                const int A = t.u_idx[e];
+                if (SYM && A < b) continue;
+                const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                const bool rev = SYM && A > b;
+                const int64_t sbase = rev ? t.sym_off[e] + (int64_t)grp * (a1 - a0) : 0;
+                for (int c = a0; c < a1; c += 32) {
+                    const int n = min(32, a1 - c);
+                    __syncwarp();
+                    if (lane < n) {
+                        st.xy[lane] = g.cxy[c + lane];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) st.q[lane][d] = q[(int64_t)(c + lane) * ND + d];
+                    }
+                    __syncwarp();
+                    if (rev) {
+                        double rv[ND];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) rv[d] = 0.0;
+                        if (n == 32 && __all_sync(0xffffffffu, valid)) {
+#pragma unroll 2
+                            for (int s = 0; s < 32; ++s) {
+                                const int j = (lane + s) & 31;
+                                const double2 sp = st.xy[j];
+                                const double dx = z.x - sp.x, dy = z.y - sp.y;
+                                const double Lg = log_r2(fma(dx, dx, dy * dy), tab, etab);
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) {
+                                    near[d] = fma(st.q[j][d], Lg, near[d]);
+                                    rv[d] = fma(qi[d], Lg, rv[d]);
+                                    rv[d] = __shfl_sync(0xffffffffu, rv[d], (lane + 1) & 31);
+                                }
+                            }
+                        } else {
+                            for (int s = 0; s < 32; ++s) {
+                                const int j = (lane + s) & 31;
+                                if (valid && j < n) {
+                                    const double2 sp = st.xy[j];
+                                    const double dx = z.x - sp.x, dy = z.y - sp.y;
+                                    const double Lg = log_r2(fma(dx, dx, dy * dy), tab, etab);
+#pragma unroll
+                                    for (int d = 0; d < ND; ++d) {
+                                        near[d] = fma(st.q[j][d], Lg, near[d]);
+                                        rv[d] = fma(qi[d], Lg, rv[d]);
+                                    }
+                                }
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) rv[d] = __shfl_sync(0xffffffffu, rv[d], (lane + 1) & 31);
+                            }
+                        }
+                        if (lane < n) {
+                            const int64_t o = (sbase + (c - a0) + lane) * ND;
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) slots[o + d] = rv[d];
+                        }
+                    } else if (valid) {
+#pragma unroll 4
+                        for (int j = 0; j < n; ++j) {
+                            const double2 sp = st.xy[j];
+                            const double dx = z.x - sp.x, dy = z.y - sp.y;
+                            const double Lg = log_r2(fma(dx, dx, dy * dy), tab, etab);
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) near[d] = fma(st.q[j][d], Lg, near[d]);
+                        }
+                    }
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) psi[(int64_t)ti * ND + d] = fma(0.5, near[d], acc[d]);
+            }
+        }
+    }
+}
+
+// Adds the symmetric near field's slots to the receiving points, one thread per
+// point, slots in a fixed order (deterministic results).
+template <int ND>
+__global__ void k_sym_reduce64(DevTree t, PassGeom g, const double* __restrict__ slots, double* __restrict__ psi)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < g.n_eval; j += gridDim.x * blockDim.x) {
+        const int A = t.sym_pt_leaf[j];
+        const int s0 = t.sym_in_ptr[A], s1 = t.sym_in_ptr[A + 1];
+        if (s0 == s1) continue;
+        const int jl = j - g.erng[2 * A];
+        double acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = 0.0;
+#pragma unroll 4
+        for (int k = s0; k < s1; ++k) {
+            const int64_t o = (t.sym_in_slot[k] + jl) * ND;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] += slots[o + d];
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) psi[(int64_t)j * ND + d] = fma(0.5, acc[d], psi[(int64_t)j * ND + d]);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a3: P2M and the whole M2M pass in one launch, one warp per leaf. The charges
+// are taken 32 at a time: lane j forms the powers u_j^k (u = (z - c)/R) of its
+// point into the warp's buffer, then lane k sums q_j u_j^k over the 32 points.
+// With the arrival counters (one per box, zero on entry and left zero), a warp
+// that has finished a box counts itself in at the parent after a fence, and
+// the warp that completes the count computes the parent's M2M and carries on
+// upwards; nothing waits. Multipoles of levels 0 and 1 are never read.
+//   M2M (scaled): B_l = -M_0 zeta^l / l + sum_{k<=l} C(l-1,k-1) 2^-k M_k zeta^(l-k)
+template <int P, int ND>
+__device__ __forceinline__ void m2m_box64(const DevTree& t, const DevTables& tab, int b, double2* __restrict__ M,
+                                          double2* __restrict__ buf, int lane)
+{
+    constexpr int P1 = P + 1;
+    double2 acc[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+    const double minv_l = lane == 0 ? 0.0 : -1.0 / (double)lane;
+    for (int c = 0; c < 4; ++c) {
+        const int ch = t.child[4 * b + c];
+        if (ch < 0) continue;
+        __syncwarp();
+        for (int i = lane; i < P1 * ND; i += 32) buf[i] = __ldcg(M + (int64_t)ch * P1 * ND + i);
+        __syncwarp();
+        if (lane <= P) {
+            const double2* zp = tab.zpow + c * P1;
+            if (lane == 0) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d].x += buf[d].x, acc[d].y += buf[d].y;
+            } else {
+                const double2 zl = zp[lane];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double m0 = buf[d].x * minv_l;
+                    acc[d].x = fma(m0, zl.x, acc[d].x);
+                    acc[d].y = fma(m0, zl.y, acc[d].y);
+                }
+                for (int k = 1; k <= lane; ++k) {
+                    const double bm = tab.Bm[lane * P1 + k];
+                    const double2 z = zp[lane - k];
+                    const double2 zb = make_double2(z.x * bm, z.y * bm);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d] = cfma64(zb, buf[k * ND + d], acc[d]);
+                }
+            }
+        }
+    }
+    if (lane <= P) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) M[((int64_t)b * P1 + lane) * ND + d] = acc[d];
+    }
+    __syncwarp();
+}
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kW64 * 32)
+    k_p2m64(DevTree t, DevTables tab, PassGeom g, const double* __restrict__ q, double2* __restrict__ M,
+            int* __restrict__ counters)
+{
+    constexpr int P1 = P + 1;
+    extern __shared__ __align__(16) unsigned char smem_p2m[];
+    // per warp: [32][P1] powers, then [32][ND] charges; the M2M reuses the powers' space
+    constexpr int kPerWarp = 32 * P1 + (32 * ND + 1) / 2;
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    double2* pw = reinterpret_cast<double2*>(smem_p2m) + (size_t)wb * kPerWarp;
+    double* qs = reinterpret_cast<double*>(pw + 32 * P1);
+    const double sc = lane == 0 ? 1.0 : -1.0 / (double)lane;
+    for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
+        const int b = t.leaves[li];
+        const int s0 = g.crng[2 * b], s1 = g.crng[2 * b + 1];
+        double2 acc[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+        const double2 c = t.center[b];
+        const double invR = 1.0 / t.radius[b];
+        for (int base = s0; base < s1; base += 32) {
+            const int n = min(32, s1 - base);
+            __syncwarp();
+            if (lane < n) {
+                const double2 z = g.cxy[base + lane];
+                const double2 u = make_double2((z.x - c.x) * invR, (z.y - c.y) * invR);
+                double2 p = u;
+                pw[lane * P1 + 1] = p;
+#pragma unroll 4
+                for (int k = 2; k <= P; ++k) {
+                    p = cmul64(p, u);
+                    pw[lane * P1 + k] = p;
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) qs[lane * ND + d] = q[(int64_t)(base + lane) * ND + d];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int j = 0; j < n; ++j)
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) acc[d].x += qs[j * ND + d];
+            } else if (lane <= P) {
+                for (int j = 0; j < n; ++j) {
+                    const double2 pv = pw[j * P1 + lane];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        acc[d].x = fma(qs[j * ND + d], pv.x, acc[d].x);
+                        acc[d].y = fma(qs[j * ND + d], pv.y, acc[d].y);
+                    }
+                }
+            }
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d)
+                M[((int64_t)b * P1 + lane) * ND + d] = make_double2(acc[d].x * sc, acc[d].y * sc);
+        }
+        for (int cur = b;;) {
+            const int par = t.parent[cur];
+            if (par < 0 || t.level[par] < 2) break;
+            __threadfence();  // this warp's M(cur) before its arrival at the parent
+            __syncwarp();
+            int old = 0;
+            if (lane == 0) old = atomicAdd(&counters[par], 1);
+            old = __shfl_sync(0xffffffffu, old, 0);
+            int nch = 0;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) nch += t.child[4 * par + cc] >= 0 ? 1 : 0;
+            if (old != nch - 1) break;  // a sibling is still running; it will carry on
+            __threadfence();            // the siblings' M before reading them
+            if (lane == 0) counters[par] = 0;
+            m2m_box64<P, ND>(t, tab, par, M, pw, lane);
+            cur = par;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a4: M2L over the V list plus P2L over the X list, one warp per target box.
+// For P = 16 the two half-warps take alternate V entries (all 32 lanes busy);
+// for P = 24, 30 one entry per warp. Within an entry, lane i of the half
+// computes A_l = M_l (-t)^l for l = i + 1 into shared memory, then
+//   L_l += t^l (sum_k H[l][k] A_k - M_0 / l)          (lane i, l = i + 1)
+//   Re L_0 += M_0 log|z0| + sum_k Re A_k              (a reduction over the half)
+// Im L_0 is not needed (L2P takes the real part; it is left zero). Afterwards
+// the halves are added and lane l holds L_l; the X list adds
+//   L_0 += q log|z - c|,  L_l -= (q / l) v^l,  v = R/(z - c).
+template <int P>
+struct M2L64Shape {
+    static constexpr int P1 = P + 1;
+    static constexpr int kHalves = P <= 16 ? 2 : 1;
+    static constexpr int kLanes = 32 / kHalves;
+};
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kW64 * 32)
+    k_m2l64(DevTree t, DevTables tab, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
+            const double* __restrict__ q, const double2* __restrict__ logtab, const double* __restrict__ etab)
+{
+    using S = M2L64Shape<P>;
+    constexpr int P1 = S::P1;
+    constexpr int NH = S::kHalves, NL = S::kLanes;
+    static_assert(P <= NL, "one lane per coefficient l = 1..P");
+    __shared__ double Ht[P1 * P1];                     // Ht[k][l] = H[l][k]
+    __shared__ double2 As[kW64][NH][P1][ND];           // A_k per half (k = 1..P)
+    __shared__ double2 pws[kW64][8][P1];               // P2L powers, 8 charges at a time
+    __shared__ double qls[kW64][8][ND + 1];            // P2L charges and logs
+    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) Ht[(i % P1) * P1 + i / P1] = tab.H[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    const int half = lane / NL, li = lane % NL;
+    const int l = li + 1;  // coefficient of this lane
+    const bool active = l <= P;
+    const double inv_l = active ? 1.0 / (double)l : 0.0;
+
+    for (int b = gwarp(); b < t.nbox; b += nwarps()) {
+        double2 lacc[ND];
+        double l0[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            lacc[d] = make_double2(0.0, 0.0);
+            l0[d] = 0.0;
+        }
+        const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
+        const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
+        const double logR = t.log_radius[b];
+        for (int e0 = v0; e0 < v1; e0 += NH) {
+            const int e = e0 + half;
+            const bool live = e < v1;
+            int o = 0, C = 0;
+            if (live) {
+                C = t.v_idx[e];
+                o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+            }
+            double m0[ND];
+            __syncwarp();
+            if (live) {
+                const double2* MC = M + (int64_t)C * P1 * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) m0[d] = MC[d].x;
+                if (active) {
+                    const double2 mt = tab.mtpow[o * P1 + l];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) As[wb][half][l][d] = cmul64(MC[l * ND + d], mt);
+                }
+            }
+            __syncwarp();
+            if (live) {
+                double2 acc[ND];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+                const int lr = active ? l : P;  // idle lanes repeat row P (result unused)
+#pragma unroll 4
+                for (int k = 1; k <= P; ++k) {
+                    const double h = Ht[k * P1 + lr];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const double2 a = As[wb][half][k][d];
+                        acc[d].x = fma(h, a.x, acc[d].x);
+                        acc[d].y = fma(h, a.y, acc[d].y);
+                    }
+                }
+                const double2 tl = tab.tpow[o * P1 + lr];
+                const double lz = logR + tab.log2o[o];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double2 a = make_double2(fma(-m0[d], inv_l, acc[d].x), acc[d].y);
+                    if (active) lacc[d] = cfma64(tl, a, lacc[d]);
+                    // Re L_0: lane i contributes Re A_(i+1); lane 0 of the half adds M_0 log|z0|
+                    double r = active ? As[wb][half][l][d].x : 0.0;
+                    if (li == 0) r = fma(m0[d], lz, r);
+                    l0[d] += r;
+                }
+            }
+        }
+        // add the halves' partial locals, reduce Re L_0 over the warp, and move
+        // coefficient l to lane l (lane 0 takes L_0)
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            if (NH == 2) {
+                lacc[d].x += __shfl_down_sync(0xffffffffu, lacc[d].x, 16);
+                lacc[d].y += __shfl_down_sync(0xffffffffu, lacc[d].y, 16);
+            }
+            for (int off = 16; off > 0; off >>= 1) l0[d] += __shfl_xor_sync(0xffffffffu, l0[d], off);
+            double2 v = make_double2(__shfl_up_sync(0xffffffffu, lacc[d].x, 1), __shfl_up_sync(0xffffffffu, lacc[d].y, 1));
+            if (lane == 0) v = make_double2(l0[d], 0.0);
+            lacc[d] = v;
+        }
+        // X list (P2L), lane l <= P owns L_l
+        const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
+        if (x1 > x0) {
+            const double2 c = t.center[b];
+            const double R = t.radius[b];
+            const double inv_ll = (lane == 0 || lane > P) ? 0.0 : 1.0 / (double)lane;
+            for (int e = x0; e < x1; ++e) {
+                const int Cx = t.x_idx[e];
+                const int s0 = g.crng[2 * Cx], s1 = g.crng[2 * Cx + 1];
+                for (int base = s0; base < s1; base += 8) {
+                    const int n = min(8, s1 - base);
+                    __syncwarp();
+                    if (lane < n) {
+                        const double2 z = g.cxy[base + lane];
+                        const double dx = z.x - c.x, dy = z.y - c.y;
+                        const double r2 = fma(dx, dx, dy * dy);
+                        const double s = R / r2;
+                        const double2 v = make_double2(dx * s, -dy * s);
+                        double2 p = make_double2(1.0, 0.0);
+                        pws[wb][lane][0] = p;
+                        for (int k = 1; k <= P; ++k) {
+                            p = cmul64(p, v);
+                            pws[wb][lane][k] = p;
+                        }
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) qls[wb][lane][d] = q[(int64_t)(base + lane) * ND + d];
+                        qls[wb][lane][ND] = 0.5 * log_r2(r2, logtab, etab);
+                    }
+                    __syncwarp();
+                    if (lane <= P) {
+                        for (int j = 0; j < n; ++j) {
+                            if (lane == 0) {
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) lacc[d].x = fma(qls[wb][j][d], qls[wb][j][ND], lacc[d].x);
+                            } else {
+                                const double2 pv = pws[wb][j][lane];
+#pragma unroll
+                                for (int d = 0; d < ND; ++d) {
+                                    const double cq = -qls[wb][j][d] * inv_ll;
+                                    lacc[d].x = fma(cq, pv.x, lacc[d].x);
+                                    lacc[d].y = fma(cq, pv.y, lacc[d].y);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (lane <= P) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) L[((int64_t)b * P1 + lane) * ND + d] = lacc[d];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// a5: L2L into the boxes of one level, one warp per child box, lane l owns L'_l:
+//   L'_l += 2^-l sum_{k>=l} C(k, l) zeta^(k-l) L_k   (zeta = child offset / R_parent)
+template <int P, int ND>
+__global__ void __launch_bounds__(kW64 * 32)
+    k_l2l64(DevTree t, DevTables tab, int b0, int b1, double2* __restrict__ L)
+{
+    constexpr int P1 = P + 1;
+    __shared__ double2 Ls[kW64][P1][ND];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    for (int b = b0 + gwarp(); b < b1; b += nwarps()) {
+        const int p = t.parent[b];
+        const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
+        __syncwarp();
+        for (int i = lane; i < P1 * ND; i += 32) (&Ls[wb][0][0])[i] = L[(int64_t)p * P1 * ND + i];
+        __syncwarp();
+        if (lane <= P) {
+            const double2* zp = tab.zpow + cq * P1;
+            double2 acc[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
+            for (int k = lane; k <= P; ++k) {
+                const double bl = tab.Bl[lane * P1 + k];
+                const double2 z = zp[k - lane];
+                const double2 zb = make_double2(z.x * bl, z.y * bl);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) acc[d] = cfma64(zb, Ls[wb][k][d], acc[d]);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const int64_t i = ((int64_t)b * P1 + lane) * ND + d;
+                const double2 o = L[i];
+                L[i] = make_double2(o.x + acc[d].x, o.y + acc[d].y);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+int blocks_for_warps(int64_t nwork, int warps_per_block)
+{
+    int64_t b = (nwork + warps_per_block - 1) / warps_per_block;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+int device_sms()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, n = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            sms = n;
+        else
+            sms = 152;
+    }
+    return sms;
+}
+
+template <int P, int ND>
+size_t p2m_smem()
+{
+    return (size_t)kW64 * (32 * (P + 1) + (32 * ND + 1) / 2) * sizeof(double2);
+}
+
+template <int ND>
+size_t leaf_smem()
+{
+    return (size_t)(1 << kLog64Bits) * sizeof(double2) + 2 * kEBias * sizeof(double) +
+           (size_t)kLeafWarps64 * sizeof(LeafStage64<ND>);
+}
+
+template <int P, int ND>
+cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, PhaseTimer* tm,
+                       cudaStream_t s)
+{
+    const int threads = kW64 * 32;
+    // one-time opt-in to the dynamic shared memory of this instantiation
+    static bool attr_done = false;
+    static int leaf_resident[2] = {0, 0};
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_p2m64<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<P, ND>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_leaf64<P, ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_leaf64<P, ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
+        if (e != cudaSuccess) return e;
+        for (int si = 0; si < 2; ++si) {
+            int nb = 0;
+            e = si ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64<P, ND, true>, kLeafWarps64 * 32, leaf_smem<ND>())
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64<P, ND, false>, kLeafWarps64 * 32, leaf_smem<ND>());
+            if (e != cudaSuccess) return e;
+            leaf_resident[si] = std::max(1, nb);
+        }
+        attr_done = true;
+    }
+    int id = tm ? tm->begin("upward") : -1;
+    k_p2m64<P, ND><<<blocks_for_warps(t.nleaf, kW64), threads, p2m_smem<P, ND>(), s>>>(t, tab, g, ws.q, ws.M,
+                                                                                      ws.m2m_count);
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("m2l") : -1;
+    k_m2l64<P, ND><<<blocks_for_warps(t.nbox, kW64), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q, tab.log64,
+                                                                     tab.elog64);
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("l2l") : -1;
+    // boxes of levels 0 and 1 have empty V and X lists, so the first L2L that
+    // adds anything goes into level 3
+    for (int l = 3; l < t.nlevels; ++l) {
+        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
+        k_l2l64<P, ND><<<blocks_for_warps(b1 - b0, kW64), threads, 0, s>>>(t, tab, b0, b1, ws.L);
+    }
+    if (tm) tm->end(id);
+    id = tm ? tm->begin("leaf") : -1;
+    const bool sym = t.sym;
+    const int si = sym ? 1 : 0;
+    const int lblocks = std::max(1, std::min((t.nleaf + kLeafWarps64 - 1) / kLeafWarps64, device_sms() * leaf_resident[si]));
+    cudaMemsetAsync(ws.work, 0, sizeof(int), s);
+    double* slots = reinterpret_cast<double*>(ws.slots);  // the slot buffer holds 8 bytes per slot and density
+    if (sym) {
+        k_leaf64<P, ND, true><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
+                                                                                 tab.elog64, ws.psi, ws.work, slots);
+        const int rblocks = std::max(1, std::min((g.n_eval + 255) / 256, 152 * 32));
+        k_sym_reduce64<ND><<<rblocks, 256, 0, s>>>(t, g, slots, ws.psi);
+    } else {
+        k_leaf64<P, ND, false><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
+                                                                                  tab.elog64, ws.psi, ws.work, nullptr);
+    }
+    if (tm) tm->end(id);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t fmm64_p(int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, PhaseTimer* tm,
+                    cudaStream_t s)
+{
+    switch (nd) {
+        case 1: return fmm64_impl<P, 1>(t, tab, g, ws, tm, s);
+        case 2: return fmm64_impl<P, 2>(t, tab, g, ws, tm, s);
+        case 4: return fmm64_impl<P, 4>(t, tab, g, ws, tm, s);
+        case 8: return fmm64_impl<P, 8>(t, tab, g, ws, tm, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
+                         PhaseTimer* timer, cudaStream_t s)
+{
+    switch (P) {
+        case 16: return fmm64_p<16>(nd, t, tab, g, ws, timer, s);
+        case 24: return fmm64_p<24>(nd, t, tab, g, ws, timer, s);
+        case 30: return fmm64_p<30>(nd, t, tab, g, ws, timer, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Host tables of the FP64 logarithm: tab[k] = (s_k, T_k) with c_k = 1 + k 2^-B,
+// s_k = RN(1/c_k), T_k = -log(s_k) rounded once from extended precision
+// (long double: at least 64 significant bits on the targets this builds for);
+// etab[i] = (i - 64) log 2.
+void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab)
+{
+    const int n = 1 << kLog64Bits;
+    tab.resize((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const double c = 1.0 + std::ldexp((double)k, -kLog64Bits);  // exact
+        const double sk = 1.0 / c;
+        const long double T = -std::log((long double)sk);
+        tab[(size_t)k] = make_double2(sk, (double)T);
+    }
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    etab.resize(2 * kEBias);
+    for (int i = 0; i < 2 * kEBias; ++i) etab[(size_t)i] = (double)((long double)(i - kEBias) * ln2);
+}
+
+}  // namespace vp

@@ -63,6 +63,16 @@ struct DevTree {
 
 constexpr int kOwnGroups = 4;  // leaves of at most 128 points take the symmetric own-leaf sum
 
+// Table of the FP64 near-field logarithm (vp_fmm64.cu): 2^kLog64Bits entries.
+constexpr int kLog64Bits = 12;
+
+// Arithmetic of a plan's evaluation (fixed at plan creation).
+enum class Arith {
+    kF64,    // default: every step in float64 on the FP64 pipes (vp_fmm64.cu, k_out_grouped64)
+    kFF,     // VP_FLAG_FF: heavy steps in float-float on the FP32 pipes
+    kPlain   // VP_FLAG_FP64: the plain float64 reference kernels
+};
+
 // Translation-operator tables for one expansion order P (P1 = P + 1 entries).
 struct DevTables {
     const double* H = nullptr;      // [P1][P1] H[l][k] = C(l+k-1, k-1)            (M2L)
@@ -73,6 +83,8 @@ struct DevTables {
     const double* log2o = nullptr;  // [49] log(2 |o|)                             (M2L)
     const double2* zpow = nullptr;  // [4][P1] zeta_c^m, zeta_c = child offset / R_parent
     const float4* logtab = nullptr; // [128] {1/c_k, T_hi, T_lo, 0}, T = -log(1/c_k)  (P2P log)
+    const double2* log64 = nullptr; // [1 << kLog64Bits] {s_k, -log s_k}               (FP64 log)
+    const double* elog64 = nullptr; // [128] (i - 64) log 2                            (FP64 log)
     // float-float copies for the FP32-pipe M2L
     const float2* Hf = nullptr;     // [P1][P1]
     const float4* tpowf = nullptr;  // [49][P1] complex (re_h, re_l, im_h, im_l)
@@ -106,8 +118,9 @@ struct DevGroupedCSR {
     const int32_t* g_r0 = nullptr;     // [ngroups + 1] first row of each group
     const int64_t* g_c0 = nullptr;     // [ngroups + 1] offsets into cols
     const int32_t* cols = nullptr;     // column list of each group
-    const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf
-    const float2* vf = nullptr;        // [nnz] values as hi/lo floats
+    const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf / vd
+    const float2* vf = nullptr;        // [nnz] values as hi/lo floats (float-float plans)
+    const double* vd = nullptr;        // [nnz] values as float64 (float64 plans)
 };
 
 // Per-cell interpolation from the density's p-nodes to the FMM's q-nodes
@@ -180,6 +193,17 @@ struct PhaseTimer {
     int begin(const char* name);    // records a start event, returns interval id (-1 if off)
     void end(int id);
 };
+
+// The float64 FMM (vp_fmm64.cu): upward pass, M2L, L2L and the leaf kernel with the
+// symmetric near field when t.sym. Enqueues on `s`; nd is 1, 2, 4 or 8.
+cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
+                         PhaseTimer* timer, cudaStream_t s);
+void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);
+// Correction apply in float64 (vp_spmv.cu): the same modes as launch_out_grouped, values
+// A.vd, x read in caller order (x[d * ld_x + col]).
+cudaError_t launch_out_grouped64(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
+                                 const double* psi, const double* x, int64_t ld_x, double* out, int64_t ld_out,
+                                 int mode, int max_blocks, cudaStream_t s);
 
 // Launchers (vp_fmm.cu). All enqueue on `s`; nd is the density chunk (1, 2, 4 or 8).
 cudaError_t launch_charges(int nd, int32_t n, const int32_t* perm, const double* w_sorted,

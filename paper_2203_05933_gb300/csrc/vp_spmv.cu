@@ -1,6 +1,7 @@
 // Correction apply (a7): out = -(1/2pi) psi + Pi f, the sparse map of the
 // per-cell corrections "accurate minus smooth" (arXiv 2203.05933, Sec. 4,
-// paragraph after Eq. nsrcs), on the FP32 pipes in float-float arithmetic.
+// paragraph after Eq. nsrcs): in float64 (k_out_grouped64, the default) or on
+// the FP32 pipes in float-float arithmetic (k_out_grouped, VP_FLAG_FF).
 //
 // The rows of one cell share their column list (every node of a cell couples
 // to the nodes of the same near cells), so the plan stores each distinct
@@ -145,6 +146,127 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
 }
 
+// Float64 form (float64 plans): values A.vd (8 bytes per nonzero, rows padded to
+// even lengths, so each row starts on 16 bytes), one DFMA per nonzero and
+// density. Eight lanes share a row (four rows per warp at a time), so that the
+// closing reduction costs three shuffle-adds per row against a row length of a
+// few hundred; the rows of a group read the same staged columns (broadcast).
+constexpr int kRowLanes64 = 8;
+
+template <int ND, bool STAGED>
+__device__ __forceinline__ void grouped_rows64(const DevGroupedCSR& A, int r0, int r1, int64_t c0, int m, int smem_m,
+                                               const double* __restrict__ F, const int32_t* __restrict__ inv,
+                                               const double* __restrict__ w_sorted, const double* __restrict__ psi,
+                                               const double* __restrict__ x, int64_t ld_x, double* __restrict__ out,
+                                               int64_t ld_out, int mode, int lane, int warp, int nw)
+{
+    constexpr int RPW = 32 / kRowLanes64;  // rows per warp at a time
+    const int li = lane % kRowLanes64, sub = lane / kRowLanes64;
+    const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
+    for (int rb = r0 + warp * RPW; rb < r1; rb += nw * RPW) {
+        const int r = rb + sub;
+        const bool live = r < r1;
+        double acc0[ND], acc1[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc0[d] = acc1[d] = 0.0;
+        if (live) {
+            const double2* vrow = reinterpret_cast<const double2*>(A.vd + A.rowptr[r]);
+#pragma unroll 2
+            for (int qp = li; qp < np; qp += kRowLanes64) {
+                const double2 v = __ldcs(vrow + qp);  // streamed once: do not keep in L1/L2
+                const int k = 2 * qp;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double2 xv;
+                    if (STAGED) {
+                        xv = *reinterpret_cast<const double2*>(F + d * smem_m + k);
+                    } else {
+                        xv.x = x[d * ld_x + A.cols[c0 + k]];
+                        xv.y = k + 1 < m ? x[d * ld_x + A.cols[c0 + k + 1]] : 0.0;
+                    }
+                    acc0[d] = fma(v.x, xv.x, acc0[d]);
+                    acc1[d] = fma(v.y, xv.y, acc1[d]);
+                }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            double a = acc0[d] + acc1[d];
+#pragma unroll
+            for (int o = kRowLanes64 / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            acc0[d] = a;
+        }
+        if (live && li == 0) {
+            if (mode == kOutWithPsi) {
+                const int32_t ri = inv[r];
+                const double wv = w_sorted ? w_sorted[ri] : 1.0;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], acc0[d]);
+            } else if (mode == kOutAccumulate) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) out[d * ld_out + r] += acc0[d];
+            } else {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) out[d * ld_out + r] = acc0[d];
+            }
+        }
+    }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(kGroupThreads)
+    k_out_grouped64(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
+                    const double* __restrict__ psi, const double* __restrict__ x, int64_t ld_x,
+                    double* __restrict__ out, int64_t ld_out, int mode)
+{
+    // [ND][smem_m] (smem_m even): x at the group's columns, density-major
+    extern __shared__ __align__(16) double F64[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int gi = blockIdx.x; gi < A.ngroups; gi += gridDim.x) {
+        const int r0 = A.g_r0[gi], r1 = A.g_r0[gi + 1];
+        const int64_t c0 = A.g_c0[gi];
+        const int m = (int)(A.g_c0[gi + 1] - c0);
+        const bool staged = m + (m & 1) <= smem_m;
+        __syncthreads();
+        if (staged) {
+            for (int i = threadIdx.x; i < m * ND; i += blockDim.x) {
+                const int k = i % m, d = i / m;
+                F64[d * smem_m + k] = x[d * ld_x + A.cols[c0 + k]];
+            }
+            if ((m & 1) && threadIdx.x < ND) F64[threadIdx.x * smem_m + m] = 0.0;
+        }
+        __syncthreads();
+        if (staged)
+            grouped_rows64<ND, true>(A, r0, r1, c0, m, smem_m, F64, inv, w_sorted, psi, x, ld_x, out, ld_out, mode,
+                                     lane, warp, nw);
+        else
+            grouped_rows64<ND, false>(A, r0, r1, c0, m, smem_m, F64, inv, w_sorted, psi, x, ld_x, out, ld_out, mode,
+                                      lane, warp, nw);
+    }
+}
+
+template <int ND>
+cudaError_t launch_grouped64_nd(const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted, const double* psi,
+                                const double* x, int64_t ld_x, double* out, int64_t ld_out, int mode, int max_blocks,
+                                cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_out_grouped64<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGroupSmemBytes);
+    if (e != cudaSuccess) return e;
+    int smem_m = kGroupSmemBytes / (ND * (int)sizeof(double));
+    smem_m &= ~1;
+    const int want = A.max_m + (A.max_m & 1);
+    if (want < smem_m) smem_m = want;
+    if (smem_m < 2) smem_m = 2;
+    const size_t bytes = (size_t)smem_m * ND * sizeof(double);
+    const int cap = max_blocks > 0 ? max_blocks : 152 * 16;
+    int blocks = A.ngroups < cap ? A.ngroups : cap;
+    if (blocks < 1) blocks = 1;
+    k_out_grouped64<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, x, ld_x, out, ld_out,
+                                                            mode);
+    return cudaGetLastError();
+}
+
 // out[d][r] += -(1/2pi) w psi[inv[r]][d], w = w_sorted[inv[r]] or 1 (the smooth part added
 // to a correction computed on its own)
 template <int ND>
@@ -205,6 +327,19 @@ cudaError_t launch_out_grouped(int nd, const DevGroupedCSR& A, const int32_t* in
         case 2: return launch_grouped_nd<2>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
         case 4: return launch_grouped_nd<4>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
         case 8: return launch_grouped_nd<8>(A, inv, w_sorted, psi, xf, ld_xf, out, ld_out, mode, max_blocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_out_grouped64(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,
+                                 const double* psi, const double* x, int64_t ld_x, double* out, int64_t ld_out,
+                                 int mode, int max_blocks, cudaStream_t s)
+{
+    switch (nd) {
+        case 1: return launch_grouped64_nd<1>(A, inv, w_sorted, psi, x, ld_x, out, ld_out, mode, max_blocks, s);
+        case 2: return launch_grouped64_nd<2>(A, inv, w_sorted, psi, x, ld_x, out, ld_out, mode, max_blocks, s);
+        case 4: return launch_grouped64_nd<4>(A, inv, w_sorted, psi, x, ld_x, out, ld_out, mode, max_blocks, s);
+        case 8: return launch_grouped64_nd<8>(A, inv, w_sorted, psi, x, ld_x, out, ld_out, mode, max_blocks, s);
         default: return cudaErrorInvalidValue;
     }
 }

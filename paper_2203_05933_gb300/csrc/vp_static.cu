@@ -12,6 +12,7 @@
 // convenience variant of the direct (P2P) kernel for small problems.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -101,16 +102,25 @@ vp_status static_fail(vp_status st, const std::string& m)
     return st;
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device with that device current.
-vp_status static_scratch(double** out)
+// Device address of the scratch array for the current device. It is looked up
+// with that device current on every call made outside a stream capture (the
+// lookup allocates nothing, and a fresh lookup stays valid after the module was
+// reloaded, e.g. after cudaDeviceReset); a call made while `s` is being
+// captured reuses the address of the device's last uncaptured call.
+vp_status static_scratch(cudaStream_t s, double** out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return static_fail(VP_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return static_fail(VP_ERR_UNSUPPORTED, "device ordinal above 63");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return static_fail(VP_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_static_mutex);
-    if (!g_static_ptr[dev]) {
+    if (cs != cudaStreamCaptureStatusNone && !g_static_ptr[dev])
+        return static_fail(VP_ERR_STATE, "first call on this device made inside a stream capture: call once outside "
+                                         "the capture first");
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_vp_static_scratch);
         if (e != cudaSuccess || !p)
@@ -135,6 +145,11 @@ extern "C" vp_status vp_eval_direct_static(int64_t n_src, const double* src_xy, 
         return static_fail(VP_ERR_ARG, "NULL input or output");
     if (ld_f < n_src || ld_out < n_tgt) return static_fail(VP_ERR_ARG, "leading dimension too small");
     if (corr_rowptr && n_src > 0 && (!corr_col || !corr_val)) return static_fail(VP_ERR_ARG, "NULL CSR array");
+    // a correction needs source values to multiply (its rows are not read here, see below)
+    if (corr_rowptr && n_src == 0) return static_fail(VP_ERR_ARG, "correction matrix given with n_src == 0");
+    // the kernels read the points as 16-byte (double2) vectors
+    if ((((uintptr_t)src_xy) | ((uintptr_t)tgt_xy)) & 15u)
+        return static_fail(VP_ERR_ARG, "src_xy and tgt_xy must be 16-byte aligned");
     // scratch layout per density pass: q [n_src] then partial [nsplit][n_tgt]
     int64_t nsplit = (n_src + 4095) / 4096;
     if (nsplit < 1) nsplit = 1;
@@ -144,7 +159,7 @@ extern "C" vp_status vp_eval_direct_static(int64_t n_src, const double* src_xy, 
         return static_fail(VP_ERR_ARG, "problem too large for the static scratch: n_src + n_tgt must not exceed "
                                        "VP_STATIC_SCRATCH_DOUBLES");
     double* scratch = nullptr;
-    vp_status st = static_scratch(&scratch);
+    vp_status st = static_scratch((cudaStream_t)stream, &scratch);
     if (st != VP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     double* q = scratch;

@@ -23,6 +23,7 @@ VP_OK = 0
 VP_FLAG_TIMING = 1
 VP_FLAG_FP64 = 2
 VP_FLAG_GRAPH = 4
+VP_FLAG_FF = 8
 VP_KERNEL_LAPLACE = 0
 VP_KERNEL_MHELMHOLTZ = 1
 
@@ -36,7 +37,7 @@ EXPORTED = [
     "vp_plan_create", "vp_plan_create_many", "vp_plan_create_upsampled", "vp_eval", "vp_eval_adjoint", "vp_eval_host", "vp_eval_batch",
     "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_set_overlap", "vp_plan_destroy",
     "vp_green_eval_host",
-    "vp_status_string", "vp_last_error", "vp_version",
+    "vp_status_string", "vp_last_error", "vp_version", "vp_measure_peaks",
     "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
     "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
 ]
@@ -122,6 +123,7 @@ def _load():
         "vp_status_string": [I32],
         "vp_last_error": [],
         "vp_version": [],
+        "vp_measure_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P],
         "vp_tree_build": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options)],
         "vp_tree_get": [P, I32, P, ctypes.POINTER(I64)],
         "vp_tree_destroy": [P],
@@ -523,22 +525,56 @@ class Plan:
             pass
 
 
+def vp_measure_peaks(stream=None) -> tuple[float, float]:
+    """Binding of vp_measure_peaks: (FP64, FP32) FMA throughput of the current
+    device in TFLOP/s."""
+    lib = _load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.vp_measure_peaks(ctypes.byref(a), ctypes.byref(b), _stream(stream)), "vp_measure_peaks")
+    return a.value, b.value
+
+
 def vp_eval_direct_static(src_xy, w, f, tgt_xy, out, csr=None, stream=None):
     """Binding of the allocation-free entry point (direct sum, scratch in a fixed
     device array). Every argument must already be a CUDA float64 tensor (CSR:
     int64 rowptr, int32 col, float64 val) because the call itself allocates
     nothing; `out` [ndens, n_tgt] receives the result."""
+    import torch
+
     lib = _load()
     fn = lib.vp_eval_direct_static
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     fn.argtypes = [I64, P, P, I32, P, I64, I64, P, P, P, P, P, I64, P]
     fn.restype = ctypes.c_int
+    rowptr, col, val = csr if csr is not None else (None, None, None)
+
+    def need(t, name, dtype, shape_ok):
+        # the call allocates nothing, so nothing is copied or converted here
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if t.numel() > 0 and t.stride(-1) != 1:
+            raise ValueError(f"{name} must have unit stride in its last dimension")
+        if not shape_ok(t):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}")
+
+    need(src_xy, "src_xy", torch.float64, lambda t: t.dim() == 2 and t.shape[1] == 2 and t.is_contiguous())
+    need(tgt_xy, "tgt_xy", torch.float64, lambda t: t.dim() == 2 and t.shape[1] == 2 and t.is_contiguous())
+    n_src, n_tgt = src_xy.shape[0], tgt_xy.shape[0]
+    need(w, "w", torch.float64, lambda t: t.dim() == 1 and t.shape[0] == n_src)
     f2 = f.reshape(1, -1) if f.dim() == 1 else f
     out2 = out.reshape(1, -1) if out.dim() == 1 else out
-    n_src, n_tgt = src_xy.shape[0], tgt_xy.shape[0]
-    rowptr, col, val = csr if csr is not None else (None, None, None)
-    st = fn(n_src, _ptr(src_xy), _ptr(w), f2.shape[0], _ptr(f2), max(f2.stride(0), n_src, 1), n_tgt, _ptr(tgt_xy),
-            _ptr(rowptr), _ptr(col), _ptr(val), _ptr(out2), max(out2.stride(0), n_tgt, 1), _stream(stream))
+    need(f2, "f", torch.float64, lambda t: t.dim() == 2 and t.shape[1] == n_src)
+    need(out2, "out", torch.float64, lambda t: t.dim() == 2 and t.shape[1] == n_tgt and t.shape[0] == f2.shape[0])
+    if csr is not None:
+        need(rowptr, "csr rowptr", torch.int64, lambda t: t.dim() == 1 and t.shape[0] == n_tgt + 1)
+        need(col, "csr col", torch.int32, lambda t: t.dim() == 1)
+        need(val, "csr val", torch.float64, lambda t: t.dim() == 1 and t.shape[0] == col.shape[0])
+    ld_f = f2.stride(0) if f2.shape[0] > 1 else max(n_src, 1)
+    ld_out = out2.stride(0) if out2.shape[0] > 1 else max(n_tgt, 1)
+    st = fn(n_src, _ptr(src_xy), _ptr(w), f2.shape[0], _ptr(f2), ld_f, n_tgt, _ptr(tgt_xy),
+            _ptr(rowptr), _ptr(col), _ptr(val), _ptr(out2), ld_out, _stream(stream))
     _check(st, "vp_eval_direct_static")
     return out
 

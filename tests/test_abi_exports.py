@@ -36,3 +36,28 @@ def test_status_strings_without_gpu():
     assert lib.vp_status_string(0) == b"ok"
     assert lib.vp_status_string(1) == b"invalid argument"
     assert b"sm_103a" in lib.vp_version()
+
+
+def _static_fn(lib):
+    fn = lib.vp_eval_direct_static
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    fn.argtypes = [I64, P, P, I32, P, I64, I64, P, P, P, P, P, I64, P]
+    fn.restype = ctypes.c_int
+    return fn
+
+
+def test_static_entry_rejects_misaligned_points_without_gpu():
+    # The pointers are never dereferenced: the argument checks run before any
+    # CUDA call, so this needs no device. 0x1008 is 8-byte but not 16-byte aligned.
+    lib = ctypes.CDLL(build.build())
+    fn = _static_fn(lib)
+    good, bad = 0x1000, 0x1008
+    assert fn(10, bad, good, 1, good, 10, 10, good, None, None, None, good, 10, None) == 1
+    assert fn(10, good, good, 1, good, 10, 10, bad, None, None, None, good, 10, None) == 1
+
+
+def test_static_entry_rejects_correction_without_sources_without_gpu():
+    lib = ctypes.CDLL(build.build())
+    fn = _static_fn(lib)
+    p = 0x1000
+    assert fn(0, None, None, 1, None, 0, 10, p, p, p, p, p, 10, None) == 1

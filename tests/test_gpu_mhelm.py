@@ -57,16 +57,16 @@ def test_cloud_matches_oracle(lam, P):
 
 @pytest.mark.parametrize("lam", [2.0, 10.0, 60.0])
 def test_float_float_near_field_matches_fp64(lam):
-    # the default near field (float-float on the FP32 pipes, FP32 series tails)
-    # against the all-FP64 one (VP_FLAG_FP64), same P and tree
+    # the float-float near field (VP_FLAG_FF: FP32 pipes, FP32 series tails)
+    # against the all-FP64 one (the default), same P and tree
     prob = inputs.cloud_problem(6000, 5000, ndens=1, shared=1500, seed=77)
     f = torch.as_tensor(prob.f, device="cuda")
     res = {}
-    for flags in (0, vp.VP_FLAG_FP64):
+    for flags in (vp.VP_FLAG_FF, 0):
         plan = make(prob, lam, p_fmm=24, leaf=64, flags=flags)
         res[flags] = plan.eval(f).cpu().numpy()
         plan.close()
-    err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / norm(prob, lam)[:, None]))
+    err = float(np.max(np.abs(res[vp.VP_FLAG_FF] - res[0]) / norm(prob, lam)[:, None]))
     print(f"modified Helmholtz lambda={lam}: float-float vs FP64 near field {err:.2e}")
     assert err <= 1e-12
 
@@ -78,13 +78,13 @@ def test_symmetric_near_field_matches_fp64():
     lam = 10.0
     f = torch.as_tensor(prob.f, device="cuda")
     res = {}
-    for flags in (0, vp.VP_FLAG_FP64):
+    for flags in (vp.VP_FLAG_FF, 0):
         plan = make(prob, lam, p_fmm=24, leaf=64, flags=flags)
         info = plan.info()
-        assert (info.sym_slots > 0) == (flags == 0)
+        assert (info.sym_slots > 0) == (flags == vp.VP_FLAG_FF)
         res[flags] = plan.eval(f).cpu().numpy()
         plan.close()
-    err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / norm(prob, lam)[:, None]))
+    err = float(np.max(np.abs(res[vp.VP_FLAG_FF] - res[0]) / norm(prob, lam)[:, None]))
     print(f"modified Helmholtz symmetric vs FP64 near field {err:.2e}")
     assert err <= 1e-12
 
@@ -130,11 +130,12 @@ def test_adjoint_matches_oracle():
 
 
 def test_adjoint_symmetric_near_field():
-    # node targets: the transposed pass also takes the symmetric near field
+    # node targets: the transposed pass of the float-float kernels also takes the
+    # symmetric near field
     prob = inputs.disk_problem(base_level=5, fine_level=6, ndens=2)
     lam = 10.0
     g = np.random.default_rng(6).standard_normal((2, prob.n_tgt))
-    plan = make(prob, lam, p_fmm=24, leaf=64)
+    plan = make(prob, lam, p_fmm=24, leaf=64, flags=vp.VP_FLAG_FF)
     assert plan.info().sym_slots > 0
     gf = plan.adjoint(torch.as_tensor(g, device="cuda"))[0].cpu().numpy()
     sub = np.random.default_rng(7).choice(prob.n_src, size=300, replace=False)

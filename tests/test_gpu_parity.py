@@ -233,22 +233,29 @@ def test_disk_1M_sampled_targets(P):
     plan.close()
 
 
+# agreement of a plan's arithmetic with the plain float64 kernels on the same
+# tree: the default float64 kernels differ from them only in rounding (own log
+# within about 1.5 ulp, summation order); float-float keeps about 48 bits
+MODE_TOL = {0: 1e-14, vp.VP_FLAG_FF: 1e-12}
+MODE_NAME = {0: "float64", vp.VP_FLAG_FF: "float-float"}
+
+
+@pytest.mark.parametrize("mode", [0, vp.VP_FLAG_FF])
 @pytest.mark.parametrize("leaf,seed", [(8, 41), (32, 42), (64, 43)])
-def test_float_float_paths_match_fp64(leaf, seed):
-    # the default float-float near field and M2L against the all-FP64 kernels on
-    # the same tree: agreement far below the 1e-10 gate shows the float-float
-    # evaluation keeps FP64-level accuracy
+def test_arith_paths_match_plain_fp64(mode, leaf, seed):
     prob = inputs.cloud_problem(4000, 3000, ndens=3, shared=800, seed=seed)
     f = torch.as_tensor(prob.f, device="cuda")
     outs = []
-    for flags in (0, vp.VP_FLAG_FP64):
+    for flags in (mode, vp.VP_FLAG_FP64):
         plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=leaf, max_dens=4,
                               flags=flags)
         outs.append(plan.eval(f).cpu().numpy())
         plan.close()
     diff = rel_err(prob, outs[0], outs[1])
-    print(f"float-float vs FP64 kernels, leaf={leaf}: {diff:.3e}")
-    assert diff <= 1e-12
+    print(f"{MODE_NAME[mode]} vs plain FP64 kernels, leaf={leaf}: {diff:.3e}")
+    assert diff <= MODE_TOL[mode]
+    ref = oracle.evaluate(prob.src_xy, prob.w, prob.f, prob.tgt_xy, prob.csr)
+    assert rel_err(prob, outs[0], ref) <= TOL
 
 
 def test_many_problems_one_plan():
@@ -303,6 +310,8 @@ def test_graph_replay_matches_direct_launches():
     assert torch.allclose(out2, 2.0 * ref, rtol=1e-14, atol=1e-14 * float(ref.abs().max()))
     with pytest.raises(vp.VPError):
         plan.set_flags(vp.VP_FLAG_FP64)
+    with pytest.raises(vp.VPError):
+        plan.set_flags(vp.VP_FLAG_FF)
     plan.close()
 
 
@@ -339,9 +348,10 @@ def test_box_grid_with_area_to_line_corrections():
     plan.close()
 
 
+@pytest.mark.parametrize("mode", [0, vp.VP_FLAG_FF])
 @pytest.mark.parametrize("which", ["boxgrid", "disk"])
 @pytest.mark.parametrize("leaf", [32, 128])
-def test_symmetric_near_field_matches_fp64(which, leaf):
+def test_symmetric_near_field_matches_fp64(mode, which, leaf):
     # targets = nodes: the near field is summed once per pair of adjacent leaves
     # (partial sums handed between leaves) and, within a leaf, once per pair of
     # its points (in-warp, and across groups of 32 through shared memory at leaf
@@ -354,49 +364,53 @@ def test_symmetric_near_field_matches_fp64(which, leaf):
     f = torch.as_tensor(prob.f, device="cuda")
     g = torch.as_tensor(np.random.default_rng(6).standard_normal((3, prob.n_tgt)), device="cuda")
     res = {}
-    for flags in (0, vp.VP_FLAG_FP64):
+    for flags in (mode, vp.VP_FLAG_FP64):
         plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=leaf, max_dens=2,
                               flags=flags, root=prob.root)
         info = plan.info()
-        assert (info.sym_slots > 0) == (flags == 0)
-        if flags == 0:
+        assert (info.sym_slots > 0) == (flags == mode)
+        if flags == vp.VP_FLAG_FF:
             assert info.p2p_evals < info.p2p_pairs // 2 + info.n_tgt * leaf  # own pairs counted once
+        elif flags == 0:
+            assert info.p2p_evals < info.p2p_pairs // 2 + info.n_tgt * leaf * 2  # own leaves directed
         res[flags] = (plan.eval(f).cpu().numpy(), plan.adjoint(g)[0].cpu().numpy())
         plan.close()
     norm = inputs.normaliser(prob)[:, None]
-    err = float(np.max(np.abs(res[0][0] - res[vp.VP_FLAG_FP64][0]) / norm))
+    err = float(np.max(np.abs(res[mode][0] - res[vp.VP_FLAG_FP64][0]) / norm))
     scale = np.abs(g.cpu().numpy()).sum(axis=1)[:, None] * prob.w.max()
-    err_a = float(np.max(np.abs(res[0][1] - res[vp.VP_FLAG_FP64][1]) / scale))
-    print(f"{which}: symmetric float-float vs FP64 forward {err:.2e} adjoint {err_a:.2e}")
-    assert err <= 1e-12 and err_a <= 1e-12
+    err_a = float(np.max(np.abs(res[mode][1] - res[vp.VP_FLAG_FP64][1]) / scale))
+    print(f"{which}: symmetric {MODE_NAME[mode]} vs plain FP64 forward {err:.2e} adjoint {err_a:.2e}")
+    assert err <= MODE_TOL[mode] and err_a <= MODE_TOL[mode]
 
 
+@pytest.mark.parametrize("mode", [0, vp.VP_FLAG_FF])
 @pytest.mark.parametrize("ndens", [1, 3, 8])
-def test_p16_float_float_matches_fp64(ndens):
+def test_p16_paths_match_fp64(mode, ndens):
     # P = 16 has its own M2L schedule (half-warps over alternate V-list entries);
     # check it, with every density chunk width, against the all-FP64 kernels on
     # an adaptive cloud (V, W and X lists all present)
     prob = inputs.cloud_problem(6000, 5000, ndens=ndens, shared=1500, seed=61)
     f = torch.as_tensor(prob.f, device="cuda")
     res = {}
-    for flags in (0, vp.VP_FLAG_FP64):
+    for flags in (mode, vp.VP_FLAG_FP64):
         plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=16, leaf=32, max_dens=8,
                               flags=flags)
         info = plan.info()
         assert info.n_x_pairs > 0 and info.n_w_pairs > 0
         res[flags] = plan.eval(f).cpu().numpy()
         plan.close()
-    err = float(np.max(np.abs(res[0] - res[vp.VP_FLAG_FP64]) / inputs.normaliser(prob)[:, None]))
-    print(f"P=16 float-float vs FP64, {ndens} densities: {err:.2e}")
-    assert err <= 1e-12
+    err = float(np.max(np.abs(res[mode] - res[vp.VP_FLAG_FP64]) / inputs.normaliser(prob)[:, None]))
+    print(f"P=16 {MODE_NAME[mode]} vs plain FP64, {ndens} densities: {err:.2e}")
+    assert err <= MODE_TOL[mode]
 
 
-def test_correction_beside_fmm_matches_sequential():
+@pytest.mark.parametrize("mode", [0, vp.VP_FLAG_FF])
+def test_correction_beside_fmm_matches_sequential(mode):
     # the correction product run beside the FMM (any share of the SMs) gives the
     # same bits as the single fused kernel after the FMM, forward and adjoint
     prob = inputs.disk_problem(base_level=4, fine_level=6, ndens=3)
     plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=16, leaf=64, max_dens=2,
-                          flags=vp.VP_FLAG_GRAPH, root=prob.root)
+                          flags=vp.VP_FLAG_GRAPH | mode, root=prob.root)
     f = torch.as_tensor(prob.f, device="cuda")
     g = torch.as_tensor(np.random.default_rng(8).standard_normal((3, prob.n_tgt)), device="cuda")
     res = []
@@ -431,7 +445,8 @@ def test_eval_batch_matches_single_evaluations():
         pl.close()
 
 
-def test_symmetric_near_field_with_coincident_points():
+@pytest.mark.parametrize("mode", [0, vp.VP_FLAG_FF])
+def test_symmetric_near_field_with_coincident_points(mode):
     # nodes with repeated coordinates: leaves holding two points at the same place
     # keep the directed own-leaf sum (coincident pairs skipped, the leaf-size term
     # corrected); the others take the symmetric one. Against the oracle.
@@ -442,7 +457,7 @@ def test_symmetric_near_field_with_coincident_points():
     w = np.concatenate([base.w, base.w[dup] * 0.5])
     f = np.hstack([base.f, base.f[:, dup]])
     csr = inputs.random_csr(src.shape[0], src.shape[0], 8, seed=85)
-    plan = vp.Plan.create(src, w, src.copy(), csr, p_fmm=30, leaf=128, max_dens=2)
+    plan = vp.Plan.create(src, w, src.copy(), csr, p_fmm=30, leaf=128, max_dens=2, flags=mode)
     assert plan.info().sym_slots > 0
     out = plan.eval(torch.as_tensor(f, device="cuda")).cpu().numpy()
     ref = oracle.evaluate(src, w, f, src, csr)

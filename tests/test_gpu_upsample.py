@@ -65,7 +65,7 @@ def _disk_upsampled(base=4, fine=6, ndens=3, seed=77):
     return mp, mq, ups, csr, f
 
 
-@pytest.mark.parametrize("flags", [0, vp.VP_FLAG_FP64])
+@pytest.mark.parametrize("flags", [0, vp.VP_FLAG_FF, vp.VP_FLAG_FP64])
 def test_box_grid_upsampled_constant_density_is_exact(flags):
     nbox = 6
     p = inputs.box_grid_problem(nbox=nbox, order=8, csr="none")
@@ -88,7 +88,7 @@ def test_box_grid_upsampled_constant_density_is_exact(flags):
     plan.close()
 
 
-@pytest.mark.parametrize("flags", [0, vp.VP_FLAG_FP64])
+@pytest.mark.parametrize("flags", [0, vp.VP_FLAG_FF, vp.VP_FLAG_FP64])
 def test_disk_upsampled_forward_adjoint_gradient(flags):
     mp, mq, ups, csr, f = _disk_upsampled()
     tgt = mp.xy  # the p-nodes are the targets

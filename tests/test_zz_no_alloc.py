@@ -57,6 +57,50 @@ def test_static_matches_planned_eval_twice(case):
     plan.close()
 
 
+def test_static_exact_fill_and_split():
+    # n_src + n_tgt equal to the scratch capacity: the source split must shrink
+    # to one slice so that the charges and one row of partial sums fill it exactly
+    n_src = 4097
+    n_tgt = (1 << 21) - n_src
+    rng = np.random.default_rng(11)
+    src_np = rng.uniform(-1.0, 1.0, (n_src, 2))
+    tgt_np = rng.uniform(-1.0, 1.0, (n_tgt, 2))
+    tgt_np[:100] = src_np[:100]  # some coincident pairs
+    w_np = rng.uniform(0.5, 1.5, n_src)
+    f_np = rng.standard_normal((1, n_src))
+    plan = vp.Plan.create(src_np, w_np, tgt_np, None, p_fmm=30, leaf=64, max_dens=1)
+    src, tgt, w, f = _dev(src_np), _dev(tgt_np), _dev(w_np), _dev(f_np)
+    nrm = float(np.abs(w_np * f_np[0]).sum())
+    for call in range(2):
+        ref = plan.eval(f).cpu().numpy()
+        out = torch.full((1, n_tgt), np.nan, dtype=torch.float64, device="cuda")
+        vp.vp_eval_direct_static(src, w, f, tgt, out)
+        err = float(np.max(np.abs(out.cpu().numpy() - ref)) / nrm)
+        assert err <= TOL, (call, err)
+    plan.close()
+
+
+def test_static_padded_leading_dimensions():
+    # strided rows (ld = n + 7) and a source count that leaves a ragged last slice
+    n_src, n_tgt, nd = 4096 * 3 + 1, 5000, 2
+    rng = np.random.default_rng(12)
+    src_np = rng.uniform(-1.0, 1.0, (n_src, 2))
+    tgt_np = rng.uniform(-1.0, 1.0, (n_tgt, 2))
+    w_np = rng.uniform(0.5, 1.5, n_src)
+    f_np = rng.standard_normal((nd, n_src))
+    fbuf = torch.full((nd, n_src + 7), np.nan, dtype=torch.float64, device="cuda")
+    fbuf[:, :n_src] = _dev(f_np)
+    obuf = torch.full((nd, n_tgt + 7), 123.0, dtype=torch.float64, device="cuda")
+    plan = vp.Plan.create(src_np, w_np, tgt_np, None, p_fmm=30, leaf=64, max_dens=2)
+    ref = plan.eval(_dev(f_np)).cpu().numpy()
+    vp.vp_eval_direct_static(_dev(src_np), _dev(w_np), fbuf[:, :n_src], _dev(tgt_np), obuf[:, :n_tgt])
+    got = obuf.cpu().numpy()
+    nrm = np.abs(w_np[None, :] * f_np).sum(axis=1)[:, None]
+    assert float(np.max(np.abs(got[:, :n_tgt] - ref) / nrm)) <= TOL
+    assert np.all(got[:, n_tgt:] == 123.0)  # the padding is not written
+    plan.close()
+
+
 def test_static_rejects_oversize():
     n = (1 << 21) // 2 + 1  # n_src + n_tgt above the scratch capacity
     src = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
