@@ -266,64 +266,6 @@ std::vector<float> make_rho(const Tree& T, const std::vector<double>& xy_sorted,
     return r;
 }
 
-// Groups of consecutive rows with identical column lists, and the values as
-// hi/lo float pairs, for the grouped correction apply.
-struct HostGroups {
-    std::vector<int32_t> g_r0;
-    std::vector<int64_t> g_c0;
-    std::vector<int32_t> cols;
-    std::vector<int64_t> rowptr;  // row starts in vf / vd (rows padded to even lengths)
-    std::vector<float> vf;        // hi/lo float pairs (float-float plans)
-    std::vector<double> vd;       // float64 values (float64 plans)
-    int32_t max_m = 0;
-};
-
-void build_groups(int64_t nrows, const std::vector<int64_t>& rowptr, const std::vector<int32_t>& col,
-                  const std::vector<double>& val, bool as_f64, HostGroups& G)
-{
-    int64_t start = -1;
-    for (int64_t i = 0; i < nrows; ++i) {
-        const int64_t a = rowptr[(size_t)i], b = rowptr[(size_t)i + 1];
-        bool same = start >= 0;
-        if (same) {
-            const int64_t sa = rowptr[(size_t)start], sb = rowptr[(size_t)start + 1];
-            same = (b - a) == (sb - sa) &&
-                   std::memcmp(col.data() + a, col.data() + sa, (size_t)(b - a) * sizeof(int32_t)) == 0;
-        }
-        if (!same) {
-            G.g_r0.push_back((int32_t)i);
-            G.g_c0.push_back((int64_t)G.cols.size());
-            G.cols.insert(G.cols.end(), col.begin() + a, col.begin() + b);
-            G.max_m = std::max<int32_t>(G.max_m, (int32_t)(b - a));
-            start = i;
-        }
-    }
-    G.g_r0.push_back((int32_t)nrows);
-    G.g_c0.push_back((int64_t)G.cols.size());
-    // values as hi/lo floats, every row padded to an even length (zeros), so that
-    // each row starts on a 16-byte boundary and is read as pairs of values
-    G.rowptr.assign((size_t)nrows + 1, 0);
-    for (int64_t i = 0; i < nrows; ++i) {
-        const int64_t len = rowptr[(size_t)i + 1] - rowptr[(size_t)i];
-        G.rowptr[(size_t)i + 1] = G.rowptr[(size_t)i] + len + (len & 1);
-    }
-    if (as_f64) {
-        G.vd.assign((size_t)G.rowptr[(size_t)nrows], 0.0);
-        for (int64_t i = 0; i < nrows; ++i)
-            for (int64_t k = rowptr[(size_t)i]; k < rowptr[(size_t)i + 1]; ++k)
-                G.vd[(size_t)(G.rowptr[(size_t)i] + (k - rowptr[(size_t)i]))] = val[(size_t)k];
-        return;
-    }
-    G.vf.assign((size_t)G.rowptr[(size_t)nrows] * 2, 0.0f);
-    for (int64_t i = 0; i < nrows; ++i)
-        for (int64_t k = rowptr[(size_t)i]; k < rowptr[(size_t)i + 1]; ++k) {
-            const size_t o = (size_t)(G.rowptr[(size_t)i] + (k - rowptr[(size_t)i]));
-            const float h = (float)val[(size_t)k];
-            G.vf[2 * o] = h;
-            G.vf[2 * o + 1] = (float)(val[(size_t)k] - (double)h);
-        }
-}
-
 bool finite_all(const std::vector<double>& a)
 {
     for (double x : a)
@@ -404,7 +346,7 @@ struct vp_plan_s {
     int32_t* crow = nullptr;
     double* cval = nullptr;
     bool grouped = false;       // correction applied by a grouped kernel (float64, or float-float with VP_FLAG_FF)
-    DevGroupedCSR gfwd, gadj;   // Pi and Pi^T, rows grouped by shared column lists
+    DevGroupedCSR gfwd;         // Pi, rows grouped by shared column lists (Pi^T g from the same layout)
     Workspace ws;
     PhaseTimer timer;
     struct GraphEntry {
@@ -553,6 +495,11 @@ struct ProblemIn {
     std::vector<int64_t> hrow;
     std::vector<int32_t> hcol;
     std::vector<double> hval;
+    // the caller's device CSR when its columns and values stay on the device
+    const int64_t* d_row = nullptr;
+    const int32_t* d_col = nullptr;
+    const double* d_val = nullptr;
+    bool dev_csr = false;
     double root[3] = {0.0, 0.0, 0.0};
 };
 
@@ -572,13 +519,21 @@ struct Built {
     std::vector<int64_t> hrow;
     std::vector<int32_t> hcol;
     std::vector<double> hval;
+    const int64_t* d_row = nullptr;  // caller's device CSR (dev_csr), else hrow/hcol/hval hold it
+    const int32_t* d_col = nullptr;
+    const double* d_val = nullptr;
+    bool dev_csr = false;
     int64_t p2p_pairs = 0;
     double root[3] = {0.0, 0.0, 0.0};
 };
 
+// copy_vals: bring the correction's columns and values to the host (plain float64
+// plans and forests); otherwise only rowptr is copied and checked here, and the
+// columns and values are checked on the device when the plan builds its layout.
 vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const double* w, int64_t n_tgt,
                        const double* tgt_xy, const int64_t* corr_rowptr, const int32_t* corr_col,
-                       const double* corr_val, int64_t nnz, cudaStream_t s, int64_t n_cols = -1)
+                       const double* corr_val, int64_t nnz, cudaStream_t s, int64_t n_cols = -1,
+                       bool copy_vals = true)
 {
     if (n_cols < 0) n_cols = n_src;
     P.n_cols = n_cols;
@@ -602,9 +557,15 @@ vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const 
     if (P.has_corr) {
         P.hrow.resize((size_t)n_tgt + 1);
         VP_CUDA(cudaMemcpyAsync(P.hrow.data(), corr_rowptr, P.hrow.size() * sizeof(int64_t), cudaMemcpyDefault, s));
-        P.hcol.resize((size_t)nnz);
-        P.hval.resize((size_t)nnz);
-        if (nnz) {
+        P.dev_csr = !copy_vals;
+        P.d_row = corr_rowptr;
+        P.d_col = corr_col;
+        P.d_val = corr_val;
+        if (copy_vals) {
+            P.hcol.resize((size_t)nnz);
+            P.hval.resize((size_t)nnz);
+        }
+        if (nnz && copy_vals) {
             VP_CUDA(cudaMemcpyAsync(P.hcol.data(), corr_col, P.hcol.size() * sizeof(int32_t), cudaMemcpyDefault, s));
             VP_CUDA(cudaMemcpyAsync(P.hval.data(), corr_val, P.hval.size() * sizeof(double), cudaMemcpyDefault, s));
         }
@@ -615,6 +576,7 @@ vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const 
         if (P.hrow[0] != 0 || P.hrow[(size_t)n_tgt] != nnz) return fail(VP_ERR_ARG, "CSR rowptr does not span [0, nnz]");
         for (int64_t i = 0; i < n_tgt; ++i)
             if (P.hrow[(size_t)i + 1] < P.hrow[(size_t)i]) return fail(VP_ERR_ARG, "CSR rowptr not monotone");
+        if (!copy_vals) return VP_OK;
         for (int64_t k = 0; k < nnz; ++k)
             if (P.hcol[(size_t)k] < 0 || P.hcol[(size_t)k] >= n_cols) return fail(VP_ERR_ARG, "CSR column out of range");
         if (!finite_all(P.hval)) return fail(VP_ERR_ARG, "non-finite CSR value");
@@ -703,6 +665,10 @@ std::string build_one(ProblemIn& P, const TreeOptions& to, Built& B)
     B.hrow = std::move(P.hrow);
     B.hcol = std::move(P.hcol);
     B.hval = std::move(P.hval);
+    B.d_row = P.d_row;
+    B.d_col = P.d_col;
+    B.d_val = P.d_val;
+    B.dev_csr = P.dev_csr;
     return "";
 }
 
@@ -823,6 +789,127 @@ Built merge(std::vector<Built>& parts)
     return M;
 }
 
+// The grouped correction on the device (vp_csr.cu), from the caller's device CSR or
+// (forests) from the host arrays uploaded to temporaries: the columns and values
+// are checked on the device, consecutive rows with identical column lists become
+// groups (one stored column list each), the values are copied into rows padded to
+// even lengths (float64, or hi/lo floats for float-float plans), and for the
+// transposed product each column gets the ascending list of the positions where
+// it appears among the groups' column lists. Only rowptr, the row flags and the
+// groups' column lists pass through the host.
+vp_status build_grouped(vp_plan p, Built& B, cudaStream_t s)
+{
+    const int64_t nrows = B.n_tgt, ncols = B.n_cols, nnz = B.nnz;
+    struct Temps {
+        std::vector<void*> v;
+        ~Temps()
+        {
+            for (void* q : v) cudaFree(q);
+        }
+    } tmp;
+    auto talloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes ? bytes : 1) != cudaSuccess) return nullptr;
+        tmp.v.push_back(q);
+        return q;
+    };
+    const int64_t* d_row = B.d_row;
+    const int32_t* d_col = B.d_col;
+    const double* d_val = B.d_val;
+    if (!B.dev_csr) {
+        int64_t* r = (int64_t*)talloc(B.hrow.size() * sizeof(int64_t));
+        int32_t* c = (int32_t*)talloc(B.hcol.size() * sizeof(int32_t));
+        double* v = (double*)talloc(B.hval.size() * sizeof(double));
+        if (!r || !c || !v) return fail(VP_ERR_OOM, "device temporaries of the correction");
+        VP_CUDA(cudaMemcpyAsync(r, B.hrow.data(), B.hrow.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        if (nnz) {
+            VP_CUDA(cudaMemcpyAsync(c, B.hcol.data(), B.hcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            VP_CUDA(cudaMemcpyAsync(v, B.hval.data(), B.hval.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        }
+        d_row = r;
+        d_col = c;
+        d_val = v;
+    }
+    int* d_err = (int*)talloc(sizeof(int));
+    uint8_t* d_same = (uint8_t*)talloc((size_t)std::max<int64_t>(nrows, 1));
+    if (!d_err || !d_same) return fail(VP_ERR_OOM, "device temporaries of the correction");
+    VP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+    VP_CUDA(launch_csr_check(nnz, d_col, d_val, ncols, d_err, s));
+    VP_CUDA(launch_row_same(nrows, d_row, d_col, d_same, s));
+    int herr = 0;
+    std::vector<uint8_t> same((size_t)nrows);
+    VP_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (nrows) VP_CUDA(cudaMemcpyAsync(same.data(), d_same, (size_t)nrows, cudaMemcpyDeviceToHost, s));
+    VP_CUDA(cudaStreamSynchronize(s));
+    if (herr & 1) return fail(VP_ERR_ARG, "CSR column out of range");
+    if (herr & 2) return fail(VP_ERR_ARG, "non-finite CSR value");
+    // groups of consecutive equal rows, their column offsets, padded value offsets
+    std::vector<int32_t> g_r0;
+    std::vector<int64_t> g_c0, prow((size_t)nrows + 1, 0);
+    int64_t pos = 0;
+    int32_t max_m = 0;
+    for (int64_t i = 0; i < nrows; ++i) {
+        const int64_t len = B.hrow[(size_t)i + 1] - B.hrow[(size_t)i];
+        if (i == 0 || !same[(size_t)i]) {
+            g_r0.push_back((int32_t)i);
+            g_c0.push_back(pos);
+            pos += len;
+            max_m = std::max<int32_t>(max_m, (int32_t)len);
+        }
+        prow[(size_t)i + 1] = prow[(size_t)i] + len + (len & 1);
+    }
+    g_r0.push_back((int32_t)nrows);
+    g_c0.push_back(pos);
+    DevGroupedCSR& A = p->gfwd;
+    int32_t *d_r0 = nullptr, *d_cols = nullptr;
+    int64_t *d_c0 = nullptr, *d_prow = nullptr;
+    cudaError_t e = p->upload(&d_r0, g_r0, s);
+    if (e == cudaSuccess) e = p->upload(&d_c0, g_c0, s);
+    if (e == cudaSuccess) e = p->upload(&d_prow, prow, s);
+    if (e == cudaSuccess) e = p->alloc(&d_cols, (size_t)pos);
+    if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create correction layout");
+    A.nrows = (int32_t)nrows;
+    A.ngroups = (int32_t)g_r0.size() - 1;
+    A.max_m = max_m;
+    A.g_r0 = d_r0;
+    A.g_c0 = d_c0;
+    A.rowptr = d_prow;
+    A.cols = d_cols;
+    VP_CUDA(launch_group_cols(A.ngroups, d_r0, d_c0, d_row, d_col, d_cols, s));
+    if (p->arith == Arith::kF64) {
+        double* vd = nullptr;
+        VP_CUDA(p->alloc(&vd, (size_t)prow[(size_t)nrows]));
+        VP_CUDA(launch_pad_values(nrows, d_row, d_prow, d_val, vd, nullptr, s));
+        A.vd = vd;
+    } else {
+        float2* vf = nullptr;
+        VP_CUDA(p->alloc(&vf, (size_t)prow[(size_t)nrows]));
+        VP_CUDA(launch_pad_values(nrows, d_row, d_prow, d_val, nullptr, vf, s));
+        A.vf = vf;
+    }
+    // positions of every column among the groups' column lists, ascending
+    std::vector<int32_t> hcols((size_t)pos);
+    if (pos) VP_CUDA(cudaMemcpyAsync(hcols.data(), d_cols, (size_t)pos * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    VP_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> inc_ptr((size_t)ncols + 1, 0), inc_pos((size_t)pos);
+    for (int64_t q = 0; q < pos; ++q) inc_ptr[(size_t)hcols[(size_t)q] + 1]++;
+    for (int64_t c = 0; c < ncols; ++c) inc_ptr[(size_t)c + 1] += inc_ptr[(size_t)c];
+    {
+        std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+        for (int64_t q = 0; q < pos; ++q) inc_pos[(size_t)fill[(size_t)hcols[(size_t)q]]++] = q;
+    }
+    int64_t *d_iptr = nullptr, *d_ipos = nullptr;
+    e = p->upload(&d_iptr, inc_ptr, s);
+    if (e == cudaSuccess) e = p->upload(&d_ipos, inc_pos, s);
+    if (e == cudaSuccess) e = p->alloc(&p->ws.adj_partial, (size_t)pos * p->nd_cap);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // before the temporaries are freed
+    if (e != cudaSuccess) return cuda_fail(e, "vp_plan_create correction layout");
+    A.adj_ncols = ncols;
+    A.inc_ptr = d_iptr;
+    A.inc_pos = d_ipos;
+    return VP_OK;
+}
+
 vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
 {
     const int64_t n_src = B.n_src, n_tgt = B.n_tgt, nnz = B.nnz, n_cols = B.n_cols;
@@ -846,11 +933,12 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     p->stat_x = (int64_t)B.x_idx.size();
     std::memcpy(p->stat_root, B.root, sizeof(p->stat_root));
 
-    // transposed correction (columns = sources), for the adjoint
+    // transposed correction (columns = sources), for the adjoint of plain float64 plans
+    // (the grouped plans compute Pi^T g from the forward layout, see vp_csr.cu)
     std::vector<int64_t> hcptr;
     std::vector<int32_t> hcrow;
     std::vector<double> hcval;
-    if (has_corr) {
+    if (has_corr && p->arith == Arith::kPlain) {
         hcptr.assign((size_t)n_cols + 1, 0);
         for (int64_t k = 0; k < nnz; ++k) hcptr[(size_t)B.hcol[(size_t)k] + 1]++;
         for (int64_t j = 0; j < n_cols; ++j) hcptr[(size_t)j + 1] += hcptr[(size_t)j];
@@ -1065,36 +1153,9 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
         up(&p->crow, hcrow);
         up(&p->cval, hcval);
     }
-    if (p->grouped) {
-        for (int pass = 0; pass < 2; ++pass) {
-            HostGroups G;
-            const bool fwd = pass == 0;
-            const int64_t nrows = fwd ? n_tgt : n_cols;
-            build_groups(nrows, fwd ? B.hrow : hcptr, fwd ? B.hcol : hcrow, fwd ? B.hval : hcval,
-                         p->arith == Arith::kF64, G);
-            DevGroupedCSR& A = fwd ? p->gfwd : p->gadj;
-            int32_t *d_r0 = nullptr, *d_cols = nullptr;
-            int64_t *d_c0 = nullptr, *d_rp = nullptr;
-            float* d_vf = nullptr;
-            double* d_vd = nullptr;
-            up(&d_r0, G.g_r0);
-            up(&d_c0, G.g_c0);
-            up(&d_cols, G.cols);
-            up(&d_rp, G.rowptr);
-            if (p->arith == Arith::kF64)
-                up(&d_vd, G.vd);
-            else
-                up(&d_vf, G.vf);
-            A.nrows = (int32_t)nrows;
-            A.ngroups = (int32_t)G.g_r0.size() - 1;
-            A.max_m = G.max_m;
-            A.g_r0 = d_r0;
-            A.g_c0 = d_c0;
-            A.cols = d_cols;
-            A.rowptr = d_rp;
-            A.vf = (const float2*)d_vf;
-            A.vd = d_vd;
-        }
+    if (p->grouped && e == cudaSuccess) {
+        const vp_status gst = build_grouped(p, B, s);
+        if (gst != VP_OK) return gst;
     }
     const int P1 = P + 1;
     const int64_t npts = std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(n_src, n_tgt), n_cols), 1);
@@ -1180,9 +1241,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
                            p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
-                           tb.log64, p->gfwd.vd, p->gadj.vd};
-    const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf,
-                          p->gfwd.vf, p->gadj.vf};
+                           tb.log64, p->gfwd.vd};
+    const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf, p->gfwd.vf};
     bool ok = true;
     for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);
     for (const void* q : vec8) ok = ok && ((uintptr_t)q % 8 == 0);
@@ -1319,7 +1379,8 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     if (st != VP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     ProblemIn in;
-    st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s);
+    st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s, -1,
+                      (opt.flags & VP_FLAG_FP64) != 0);
     if (st != VP_OK) return st;
     TreeOptions to;
     to.leaf = leaf;
@@ -1459,7 +1520,8 @@ vp_status vp_plan_create_upsampled(vp_plan* out, int64_t n_src, const double* sr
         return fail(VP_ERR_UNSUPPORTED, "the modified-Helmholtz kernel is available through vp_plan_create only");
     cudaStream_t s = (cudaStream_t)stream;
     ProblemIn in;
-    st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s, n_f);
+    st = copy_problem(in, n_src, src_xy, w, n_tgt, tgt_xy, corr_rowptr, corr_col, corr_val, nnz, s, n_f,
+                      (opt.flags & VP_FLAG_FP64) != 0);
     if (st != VP_OK) return st;
     TreeOptions to;
     to.leaf = leaf;
@@ -1534,6 +1596,17 @@ vp_status grouped_apply(vp_plan p, int nd, const DevGroupedCSR& A, int64_t ncols
     }
     VP_CUDA(launch_to_ff_rows(nd, (int32_t)ncols, x, ld_x, p->ws.xf, s));
     VP_CUDA(launch_out_grouped(nd, A, inv, w, psi, p->ws.xf, ncols, out, ld_out, mode, max_blocks, s));
+    p->last_launches += 2;
+    return VP_OK;
+}
+
+// Pi^T x of one density chunk from the forward grouped layout (modes as in
+// launch_out_grouped; the columns are the density's points). Counts its launches.
+vp_status adj_apply(vp_plan p, int nd, const int32_t* inv, const double* w, const double* psi, const double* x,
+                    int64_t ld_x, double* out, int64_t ld_out, int mode, int max_blocks, cudaStream_t s)
+{
+    VP_CUDA(launch_adj_grouped(nd, p->gfwd, p->arith == Arith::kF64, x, ld_x, p->ws.adj_partial, inv, w, psi, out,
+                               ld_out, mode, max_blocks, s));
     p->last_launches += 2;
     return VP_OK;
 }
@@ -1707,7 +1780,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
             if (overlap) {
                 VP_CUDA(cudaEventRecord(p->ev_fork, s));
                 VP_CUDA(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-                const vp_status st = grouped_apply(p, nd, p->gadj, p->n_tgt, nullptr, nullptr, nullptr, gc, ld_g,
+                const vp_status st = adj_apply(p, nd, nullptr, nullptr, nullptr, gc, ld_g,
                                                    gfc0, ld_gf, kOutOverwrite, p->side_blocks, p->side);
                 if (st != VP_OK) return st;
                 VP_CUDA(cudaEventRecord(p->ev_join, p->side));
@@ -1722,7 +1795,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                 double* gfc = grad_f + (int64_t)d0 * ld_gf;
                 VP_CUDA(launch_ups_adjoint(nd, p->dups, p->src_inv, p->w_sorted, p->ws.psi, gfc, ld_gf, s));
                 if (p->grouped) {
-                    const vp_status st = grouped_apply(p, nd, p->gadj, p->n_tgt, nullptr, nullptr, nullptr, gc, ld_g,
+                    const vp_status st = adj_apply(p, nd, nullptr, nullptr, nullptr, gc, ld_g,
                                                        gfc, ld_gf, kOutAccumulate, 0, s);
                     if (st != VP_OK) return st;
                 } else if (p->cptr) {
@@ -1730,7 +1803,7 @@ vp_status vp_eval_adjoint(vp_plan p, int32_t ndens, const double* g, int64_t ld_
                                                p->cval, gc, ld_g, gfc, ld_gf, s));
                 }
             } else if (p->grouped) {
-                const vp_status st = grouped_apply(p, nd, p->gadj, p->n_tgt, p->src_inv, p->w_sorted, p->ws.psi, gc,
+                const vp_status st = adj_apply(p, nd, p->src_inv, p->w_sorted, p->ws.psi, gc,
                                                    ld_g, grad_f + (int64_t)d0 * ld_gf, ld_gf, kOutWithPsi, 0, s);
                 if (st != VP_OK) return st;
             } else {

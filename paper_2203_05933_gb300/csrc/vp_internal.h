@@ -121,6 +121,11 @@ struct DevGroupedCSR {
     const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf / vd
     const float2* vf = nullptr;        // [nnz] values as hi/lo floats (float-float plans)
     const double* vd = nullptr;        // [nnz] values as float64 (float64 plans)
+    // transposed product: the positions p (into cols) where column c appears,
+    // ascending, for c < adj_ncols
+    int64_t adj_ncols = 0;
+    const int64_t* inc_ptr = nullptr;  // [adj_ncols + 1]
+    const int64_t* inc_pos = nullptr;  // [g_c0[ngroups]]
 };
 
 // Per-cell interpolation from the density's p-nodes to the FMM's q-nodes
@@ -180,6 +185,7 @@ struct Workspace {
     int* work = nullptr;      // work-queue counter of the persistent near-field kernel
     float2* slots = nullptr;  // [sym_slots][ND] symmetric near-field partial sums
     int* m2m_count = nullptr; // [nbox] arrivals of finished children (zero between launches)
+    double* adj_partial = nullptr;  // [positions of the grouped correction][ND] transposed partial sums
     int32_t nd_cap = 0;
 };
 
@@ -199,6 +205,22 @@ struct PhaseTimer {
 cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
                          PhaseTimer* timer, cudaStream_t s);
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);
+// Device-side construction of the grouped correction (vp_csr.cu). err: device int,
+// bit 1 = column out of range, bit 2 = non-finite value. same[i] = row i repeats row i - 1.
+cudaError_t launch_csr_check(int64_t nnz, const int32_t* col, const double* val, int64_t ncols, int* err,
+                             cudaStream_t s);
+cudaError_t launch_row_same(int64_t nrows, const int64_t* rowptr, const int32_t* col, uint8_t* same, cudaStream_t s);
+cudaError_t launch_group_cols(int32_t ngroups, const int32_t* g_r0, const int64_t* g_c0, const int64_t* rowptr,
+                              const int32_t* col, int32_t* cols, cudaStream_t s);
+// exactly one of vd (float64) and vf (hi/lo floats) is non-NULL
+cudaError_t launch_pad_values(int64_t nrows, const int64_t* rowptr, const int64_t* prow, const double* val,
+                              double* vd, float2* vf, cudaStream_t s);
+// out (columns, caller order) = Pi^T x in the modes of launch_out_grouped (inv, w_sorted,
+// psi index the columns' tree positions); partial: [g_c0[ngroups]][nd] scratch.
+cudaError_t launch_adj_grouped(int nd, const DevGroupedCSR& A, bool f64, const double* x, int64_t ld_x,
+                               double* partial, const int32_t* inv, const double* w_sorted, const double* psi,
+                               double* out, int64_t ld_out, int mode, int max_blocks, cudaStream_t s);
+
 // Correction apply in float64 (vp_spmv.cu): the same modes as launch_out_grouped, values
 // A.vd, x read in caller order (x[d * ld_x + col]).
 cudaError_t launch_out_grouped64(int nd, const DevGroupedCSR& A, const int32_t* inv, const double* w_sorted,

@@ -114,7 +114,14 @@ def synthetic_csr_values(rowptr, col, w, seed: int, scale: float = 1.0):
     """Seeded stand-in values for a correction pattern, sized like real ones
     (a few times the node weight of the column). For parity and timing only."""
     rng = np.random.default_rng(seed)
-    return scale * rng.standard_normal(col.size) * np.asarray(w)[col]
+    v = rng.standard_normal(col.size)
+    w = np.asarray(w)
+    step = 1 << 26  # in place, a slice at a time (the matrices reach billions of entries)
+    for a in range(0, col.size, step):
+        v[a:a + step] *= w[col[a:a + step]]
+    if scale != 1.0:
+        v *= scale
+    return v
 
 
 def box_grid_problem(nbox: int = 16, order: int = 8, ndens: int = 1, seed: int = SEED_BASE + 1,
@@ -452,6 +459,10 @@ def star_problem(size: str = "4M", ndens: int = 1, seed: int = SEED_BASE + 3, ta
         bb = mesh.cell_bbox
         cc = np.stack([(bb[:, 0] + bb[:, 1]) / 2, (bb[:, 2] + bb[:, 3]) / 2], axis=1)
         _, near = cKDTree(cc).query(rnd)
+        # the random points are stored cell by cell (stable order within a cell),
+        # so that the correction rows of one cell are consecutive
+        order = np.argsort(near, kind="stable")
+        rnd, near = rnd[order], near[order]
         tgt = np.ascontiguousarray(np.vstack([xy[sub], rnd]))
         tgt_cell = np.concatenate([node_cell[sub], near])
     mat = None

@@ -197,6 +197,19 @@ def test_bad_arguments_raise():
     w[2] = np.nan
     with pytest.raises(vp.VPError):
         vp.Plan.create(np.zeros((4, 2)), w, np.zeros((4, 2)))
+    # the correction's columns and values are checked on the device (float64 and
+    # float-float plans) or on the host (plain float64 plans)
+    for flags in (0, vp.VP_FLAG_FF, vp.VP_FLAG_FP64):
+        with pytest.raises(vp.VPError):
+            vp.Plan.create(np.zeros((4, 2)), np.ones(4), np.zeros((4, 2)),
+                           (np.array([0, 1, 1, 1, 1]), np.array([9], np.int32), np.ones(1)), flags=flags)
+        with pytest.raises(vp.VPError):
+            vp.Plan.create(np.zeros((4, 2)), np.ones(4), np.zeros((4, 2)),
+                           (np.array([0, 1, 2, 2, 2]), np.array([0, -1], np.int32), np.ones(2)), flags=flags)
+        with pytest.raises(vp.VPError):
+            vp.Plan.create(np.zeros((4, 2)), np.ones(4), np.zeros((4, 2)),
+                           (np.array([0, 1, 2, 2, 2]), np.array([0, 3], np.int32), np.array([1.0, np.inf])),
+                           flags=flags)
 
 
 def test_phase_timing_flag():
