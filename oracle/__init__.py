@@ -59,8 +59,9 @@ def _load():
         lib.vpo_adjoint.argtypes = lib.vpo_eval.argtypes
         lib.vpo_grad_targets.argtypes = [_i64, _ptr, _ptr, _i32, _ptr, _i64, _ptr, _i64,
                                          _i64, _ptr, _ptr, ctypes.c_int]
+        lib.vpo_grad_scale.argtypes = lib.vpo_grad_targets.argtypes
         lib.vpo_max_threads.argtypes = []
-        for fn in (lib.vpo_eval, lib.vpo_adjoint, lib.vpo_grad_targets, lib.vpo_max_threads):
+        for fn in (lib.vpo_eval, lib.vpo_adjoint, lib.vpo_grad_targets, lib.vpo_grad_scale, lib.vpo_max_threads):
             fn.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -148,6 +149,24 @@ def grad_targets(src_xy, w, f, g, tgt_xy, nthreads: int = 0) -> np.ndarray:
                                   int(nthreads))
     if rc != 0:
         raise RuntimeError(f"vpo_grad_targets failed ({rc})")
+    return out
+
+
+def grad_scale(src_xy, w, f, g, tgt_xy, nthreads: int = 0) -> np.ndarray:
+    """Per-target normaliser of dL/dt errors: sum_d |g[d, i]| sum_j |w_j f[d, j]| / (2 pi |t_i - r_j|)
+    (coincident pairs skipped), the sum of the absolute values of the gradient's terms."""
+    src_xy = _c(src_xy, np.float64).reshape(-1, 2)
+    tgt_xy = _c(tgt_xy, np.float64).reshape(-1, 2)
+    w = _c(w, np.float64)
+    f = _dens(f, src_xy.shape[0])
+    g = _dens(g, tgt_xy.shape[0])
+    if g.shape[0] != f.shape[0]:
+        raise ValueError("f and g must hold the same number of densities")
+    out = np.empty(tgt_xy.shape[0], np.float64)
+    rc = _load().vpo_grad_scale(src_xy.shape[0], _p(src_xy), _p(w), f.shape[0], _p(f), f.shape[1],
+                                _p(g), g.shape[1], tgt_xy.shape[0], _p(tgt_xy), _p(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"vpo_grad_scale failed ({rc})")
     return out
 
 

@@ -239,3 +239,35 @@ int vpo_grad_targets(int64_t n_src, const double* src_xy, const double* w,
     }
     return 0;
 }
+
+/*
+ * Normaliser of the target gradient's error, the analogue of sum_j |w_j f_j| for
+ * the potential: the sum of the absolute values of the terms of dL/dt_i,
+ * out[i] = sum_d |g[d][i]| sum_{j: r_j != t_i} |w_j f[d][j]| / (2 pi |t_i - r_j|).
+ * It bounds |dL/dt_i| (triangle inequality) and equals it when every term points
+ * the same way.
+ */
+int vpo_grad_scale(int64_t n_src, const double* src_xy, const double* w,
+                   int32_t ndens, const double* f, int64_t ld_f,
+                   const double* g, int64_t ld_g,
+                   int64_t n_tgt, const double* tgt_xy,
+                   double* out, int nthreads)
+{
+    if (n_src < 0 || n_tgt < 0 || ndens < 0) return 1;
+    vpo_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n_tgt; ++i) {
+        const double x0 = tgt_xy[2 * i], y0 = tgt_xy[2 * i + 1];
+        vpo_sum acc = {0.0, 0.0};
+        for (int64_t j = 0; j < n_src; ++j) {
+            const double x = src_xy[2 * j], y = src_xy[2 * j + 1];
+            if (x == x0 && y == y0) continue;
+            const double dx = x0 - x, dy = y0 - y;
+            double q = 0.0;
+            for (int32_t d = 0; d < ndens; ++d) q += fabs(g[d * ld_g + i] * f[d * ld_f + j]);
+            vpo_add(&acc, VPO_INV_2PI * fabs(w[j]) * q / sqrt(dx * dx + dy * dy));
+        }
+        out[i] = vpo_val(&acc);
+    }
+    return 0;
+}

@@ -77,18 +77,32 @@ def _time_eval(plan, f, out, steps):
 
 def tune(src_xy, w, tgt_xy, ndens: int = 1, geometry: str = "generic", root=None, tol: float = 1e-10,
          safety: float = 0.1, steps: int = 5, p_choices=P_CHOICES, leaf_choices=LEAF_CHOICES,
-         use_cache: bool = True, seed: int = 7) -> dict:
-    """Returns {"p_fmm", "leaf", "max_dens", "ms", "err", "table", "key", "cached"}."""
+         use_cache: bool = True, seed: int = 7, flags: int = 0, f_check=None) -> dict:
+    """Returns {"p_fmm", "leaf", "max_dens", "ms", "err", "table", "key", "cached"}.
+    flags: the arithmetic of the plans tuned (0: float64, vp.VP_FLAG_FF: float-float).
+    f_check: optional [k, n] densities of the workload itself, checked beside the
+    random ones (the error is the larger of the two). Smooth densities have large
+    multipole moments relative to sum |w f| and so show larger truncation errors
+    than random ones; a choice made on random densities alone can miss the gate."""
     import torch
 
     n = int(np.asarray(src_xy).reshape(-1, 2).shape[0])
-    key = cache_key(geometry, n, ndens)
+    key = cache_key(geometry, n, ndens) + f"|f{flags}"
     path = _cache_path()
     cache = _load_cache(path) if use_cache else {}
     if use_cache and key in cache:
         return dict(cache[key], cached=True)
     rng = np.random.default_rng(seed)
-    f = torch.as_tensor(rng.standard_normal((ndens, n)), device="cuda")
+    fr = rng.standard_normal((ndens, n))
+    if f_check is not None:
+        fc = np.asarray(f_check, np.float64).reshape(-1, n)[:max(1, min(ndens, 8))]
+        k = min(fc.shape[0], ndens)
+        fr[:k] = fc[:k] if ndens > 1 else fc[:1]
+        if ndens == 1:
+            fr = np.vstack([fr, rng.standard_normal((1, n))])  # one random density beside it
+    nd_time = ndens  # timing uses the requested number of densities
+    f = torch.as_tensor(fr, device="cuda")
+    ndens = f.shape[0]
     wt = np.asarray(w, dtype=np.float64)
     norm = torch.as_tensor(np.abs(wt[None, :] * f.cpu().numpy()).sum(axis=1), device="cuda")
     chunk = 1
@@ -99,15 +113,16 @@ def tune(src_xy, w, tgt_xy, ndens: int = 1, geometry: str = "generic", root=None
     ref = ref_plan.eval(f)
     ref_plan.close()
     out = torch.empty_like(ref)
+    ft, outt = f[:nd_time], out[:nd_time]
     table = []
     t0 = time.perf_counter()
     for P in p_choices:
         for leaf in leaf_choices:
-            plan = vp.Plan.create(src_xy, w, tgt_xy, None, p_fmm=P, leaf=leaf, max_dens=chunk, flags=vp.VP_FLAG_GRAPH,
-                                  root=root)
+            plan = vp.Plan.create(src_xy, w, tgt_xy, None, p_fmm=P, leaf=leaf, max_dens=chunk,
+                                  flags=vp.VP_FLAG_GRAPH | flags, root=root)
             plan.eval(f, out=out)
             err = float(((out - ref).abs().max(dim=1).values / norm).max())
-            ms = _time_eval(plan, f, out, steps)
+            ms = _time_eval(plan, ft, outt, steps)
             plan.close()
             table.append({"p_fmm": P, "leaf": leaf, "max_dens": chunk, "err": err, "ms": ms,
                           "ok": err <= tol * safety})

@@ -1616,7 +1616,7 @@ cudaError_t run_fmm(vp_plan p, int nd, const PassGeom& g, bool gradient, PhaseTi
 {
     if (p->kernel == VP_KERNEL_MHELMHOLTZ)
         return launch_fmm_mhelm(p->P, p->dt, p->mh, p->tab.logtab, g, p->ws, !use_ff(p), tm, s);
-    if (p->arith == Arith::kF64 && !gradient) return launch_fmm64(p->P, nd, p->dt, p->tab, g, p->ws, tm, s);
+    if (p->arith == Arith::kF64) return launch_fmm64(p->P, nd, p->dt, p->tab, g, p->ws, gradient, tm, s);
     return launch_fmm_potential(p->P, nd, p->dt, p->tab, g, p->ws, gradient, use_fp64(p), tm, s);
 }
 

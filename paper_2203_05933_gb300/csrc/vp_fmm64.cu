@@ -251,6 +251,134 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
     }
 }
 
+// 1/r2 by two Newton-Raphson steps (y <- y + y (1 - r2 y)) from the hardware's
+// approximate float64 reciprocal (rcp.approx.ftz.f64, relative error about
+// 2^-22): after two steps the relative error is at the rounding level. Four
+// FP64 operations. r2 > 0 and normal.
+__device__ __forceinline__ double recip_r2(double r2)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r2));
+    double e = fma(-r2, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-r2, y, 1.0);
+    return fma(y, e, y);
+}
+
+// a8 (target gradient): grad Re phi at the evaluation points, psi[(e * 2 + c) * ND + d]
+// (c = 0: d/dx, 1: d/dy), one leaf per warp as in k_leaf64 (directed):
+//   L2P  d/dz sum_l L_l u^l = (1/R) sum_l l L_l u^(l-1)  -> (Re, -Im)
+//   M2P  d/dz [M_0 log(z - c) + sum_k M_k v^k] = (M_0 - sum_k k M_k v^k) / (z - c)
+//   P2P  sum_j q_j (z - z_j) / |z - z_j|^2   (coincident pairs skipped)
+// One directed pair costs 11 FP64 operations (differences, r^2, the reciprocal,
+// q / r^2 and two accumulations).
+template <int P, int ND>
+__global__ void __launch_bounds__(kLeafWarps64 * 32)
+    k_leaf_grad64(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
+                  const double2* __restrict__ L, double* __restrict__ psi, int* __restrict__ work)
+{
+    constexpr int P1 = P + 1;
+    __shared__ LeafStage64<ND> stage[kLeafWarps64];
+    const int lane = threadIdx.x & 31;
+    LeafStage64<ND>& st = stage[threadIdx.x >> 5];
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(work, 1);
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= t.nleaf) break;
+        const int b = t.leaves[li];
+        const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
+        if (e0 == e1) continue;
+        const double2 cb = t.center[b];
+        const double invRb = 1.0 / t.radius[b];
+        const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
+        const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
+        for (int gb = e0; gb < e1; gb += 32) {
+            const int ti = gb + lane;
+            const bool valid = ti < e1;
+            const double2 z = valid ? g.exy[ti] : cb;
+            double gx[ND], gy[ND];
+            {
+                const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
+                const double2* Lb = L + (int64_t)b * P1 * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double2 lp = Lb[P * ND + d];
+                    double2 s = make_double2(lp.x * P, lp.y * P);
+#pragma unroll 4
+                    for (int l = P - 1; l >= 1; --l) {
+                        const double2 c = Lb[l * ND + d];
+                        s = cfma64(s, u, make_double2(c.x * l, c.y * l));
+                    }
+                    gx[d] = s.x * invRb;
+                    gy[d] = -s.y * invRb;
+                }
+            }
+            for (int e = w0; e < w1; ++e) {
+                const int D = t.w_idx[e];
+                const double2 cD = t.center[D];
+                const double RD = t.radius[D];
+                const double dx = z.x - cD.x, dy = z.y - cD.y;
+                const double ir = recip_r2(fma(dx, dx, dy * dy));
+                const double2 inv = make_double2(dx * ir, -dy * ir);  // 1/(z - c)
+                const double2 v = make_double2(inv.x * RD, inv.y * RD);
+                const double2* MD = M + (int64_t)D * P1 * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double2 s = make_double2(0.0, 0.0);
+#pragma unroll 2
+                    for (int k = P; k >= 1; --k) {
+                        const double2 m = MD[k * ND + d];
+                        s = cmul64(make_double2(fma(m.x, (double)k, s.x), fma(m.y, (double)k, s.y)), v);
+                    }
+                    const double2 dphi = cmul64(inv, make_double2(MD[d].x - s.x, MD[d].y - s.y));
+                    gx[d] += dphi.x;
+                    gy[d] -= dphi.y;
+                }
+            }
+            double nx[ND], ny[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) nx[d] = ny[d] = 0.0;
+            for (int e = u0; e < u1; ++e) {
+                const int A = t.u_idx[e];
+                const int a0 = g.crng[2 * A], a1 = g.crng[2 * A + 1];
+                for (int c = a0; c < a1; c += 32) {
+                    const int n = min(32, a1 - c);
+                    __syncwarp();
+                    if (lane < n) {
+                        st.xy[lane] = g.cxy[c + lane];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) st.q[lane][d] = q[(int64_t)(c + lane) * ND + d];
+                    }
+                    __syncwarp();
+                    if (valid) {
+#pragma unroll 4
+                        for (int j = 0; j < n; ++j) {
+                            const double2 sp = st.xy[j];
+                            const double dx = z.x - sp.x, dy = z.y - sp.y;
+                            const double r2 = fma(dx, dx, dy * dy);
+                            const double ir = r2 == 0.0 ? 0.0 : recip_r2(r2);  // coincident: no term
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) {
+                                const double qr = st.q[j][d] * ir;
+                                nx[d] = fma(qr, dx, nx[d]);
+                                ny[d] = fma(qr, dy, ny[d]);
+                            }
+                        }
+                    }
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    psi[((int64_t)ti * 2 + 0) * ND + d] = gx[d] + nx[d];
+                    psi[((int64_t)ti * 2 + 1) * ND + d] = gy[d] + ny[d];
+                }
+            }
+        }
+    }
+}
+
 // Adds the symmetric near field's slots to the receiving points, one thread per
 // point, slots in a fixed order (deterministic results).
 template <int ND>
@@ -645,8 +773,8 @@ size_t leaf_smem()
 }
 
 template <int P, int ND>
-cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, PhaseTimer* tm,
-                       cudaStream_t s)
+cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool gradient,
+                       PhaseTimer* tm, cudaStream_t s)
 {
     const int threads = kW64 * 32;
     // one-time opt-in to the dynamic shared memory of this instantiation
@@ -685,6 +813,13 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
+    if (gradient) {
+        const int gblocks = std::max(1, std::min((t.nleaf + kLeafWarps64 - 1) / kLeafWarps64, device_sms() * 4));
+        cudaMemsetAsync(ws.work, 0, sizeof(int), s);
+        k_leaf_grad64<P, ND><<<gblocks, kLeafWarps64 * 32, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi, ws.work);
+        if (tm) tm->end(id);
+        return cudaGetLastError();
+    }
     const bool sym = t.sym;
     const int si = sym ? 1 : 0;
     const int lblocks = std::max(1, std::min((t.nleaf + kLeafWarps64 - 1) / kLeafWarps64, device_sms() * leaf_resident[si]));
@@ -704,14 +839,14 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
 }
 
 template <int P>
-cudaError_t fmm64_p(int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, PhaseTimer* tm,
-                    cudaStream_t s)
+cudaError_t fmm64_p(int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws, bool gradient,
+                    PhaseTimer* tm, cudaStream_t s)
 {
     switch (nd) {
-        case 1: return fmm64_impl<P, 1>(t, tab, g, ws, tm, s);
-        case 2: return fmm64_impl<P, 2>(t, tab, g, ws, tm, s);
-        case 4: return fmm64_impl<P, 4>(t, tab, g, ws, tm, s);
-        case 8: return fmm64_impl<P, 8>(t, tab, g, ws, tm, s);
+        case 1: return fmm64_impl<P, 1>(t, tab, g, ws, gradient, tm, s);
+        case 2: return fmm64_impl<P, 2>(t, tab, g, ws, gradient, tm, s);
+        case 4: return fmm64_impl<P, 4>(t, tab, g, ws, gradient, tm, s);
+        case 8: return fmm64_impl<P, 8>(t, tab, g, ws, gradient, tm, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -719,12 +854,12 @@ cudaError_t fmm64_p(int nd, const DevTree& t, const DevTables& tab, const PassGe
 }  // namespace
 
 cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
-                         PhaseTimer* timer, cudaStream_t s)
+                         bool gradient, PhaseTimer* timer, cudaStream_t s)
 {
     switch (P) {
-        case 16: return fmm64_p<16>(nd, t, tab, g, ws, timer, s);
-        case 24: return fmm64_p<24>(nd, t, tab, g, ws, timer, s);
-        case 30: return fmm64_p<30>(nd, t, tab, g, ws, timer, s);
+        case 16: return fmm64_p<16>(nd, t, tab, g, ws, gradient, timer, s);
+        case 24: return fmm64_p<24>(nd, t, tab, g, ws, gradient, timer, s);
+        case 30: return fmm64_p<30>(nd, t, tab, g, ws, gradient, timer, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -202,8 +202,9 @@ struct PhaseTimer {
 
 // The float64 FMM (vp_fmm64.cu): upward pass, M2L, L2L and the leaf kernel with the
 // symmetric near field when t.sym. Enqueues on `s`; nd is 1, 2, 4 or 8.
+// gradient: the leaf kernel writes grad Re phi (psi[(e * 2 + c) * ND + d]) instead of the potential.
 cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
-                         PhaseTimer* timer, cudaStream_t s);
+                         bool gradient, PhaseTimer* timer, cudaStream_t s);
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);
 // Device-side construction of the grouped correction (vp_csr.cu). err: device int,
 // bit 1 = column out of range, bit 2 = non-finite value. same[i] = row i repeats row i - 1.

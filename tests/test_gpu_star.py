@@ -107,9 +107,12 @@ def test_star_1M_differentiation():
     rows = np.unique(np.concatenate([rng.choice(prob.n_tgt - n_ex, 16384 - n_ex, replace=False),
                                      np.arange(prob.n_tgt - n_ex, prob.n_tgt)]))
     ref_t = oracle.grad_targets(prob.src_xy, prob.w, prob.f, resid[:, rows], prob.tgt_xy[rows])
-    err_t = float(np.max(np.abs(gt[rows] - ref_t)) / np.max(np.abs(ref_t)))
-    print(f"star 1M dL/dt rel err {err_t:.3e} on {rows.size} targets")
-    assert err_t <= 1e-8
+    scale_t = oracle.grad_scale(prob.src_xy, prob.w, prob.f, resid[:, rows], prob.tgt_xy[rows])
+    err_t = float(np.max(np.abs(gt[rows] - ref_t) / scale_t[:, None]))
+    err_m = float(np.max(np.abs(gt[rows] - ref_t)) / np.max(np.abs(ref_t)))
+    print(f"star 1M dL/dt rel err {err_t:.3e} per target (sum of |terms|), {err_m:.3e} of max |ref|, "
+          f"on {rows.size} targets")
+    assert err_t <= TOL
 
     # central differences of V at the hole centres, h = 1e-6 (one plan holds every shifted point)
     h = 1e-6

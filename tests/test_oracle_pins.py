@@ -186,3 +186,36 @@ def test_oracle_threads_do_not_change_result():
     a = oracle.evaluate(p.src_xy, p.w, p.f, p.tgt_xy, p.csr, nthreads=1)
     b = oracle.evaluate(p.src_xy, p.w, p.f, p.tgt_xy, p.csr, nthreads=4)
     assert np.array_equal(a, b)
+
+
+def test_oracle_grad_scale_bounds_and_closed_forms():
+    # one source: the normaliser is |g q| / (2 pi r) = |dL/dt|; sources on a ray on
+    # one side with charges of one sign: every term points the same way, so the
+    # normaliser equals |dL/dt|; random clouds: it bounds |dL/dt| from above
+    t = np.array([[0.3, -0.2]])
+    s = np.array([[1.1, 0.4]])
+    r = np.hypot(0.8, 0.6)
+    sc = oracle.grad_scale(s, np.array([0.7]), np.array([[2.0]]), np.array([[-1.5]]), t)
+    assert abs(sc[0] - 1.5 * 0.7 * 2.0 / (2 * np.pi * r)) <= 1e-15
+    ray = np.array([[0.3 + a, -0.2] for a in (0.1, 0.25, 0.7, 1.3)])
+    w = np.array([0.5, 1.0, 2.0, 0.25])
+    f = np.array([[1.0, 3.0, 0.5, 2.0]])
+    g = np.array([[0.8]])
+    sc = oracle.grad_scale(ray, w, f, g, t)
+    gr = oracle.grad_targets(ray, w, f, g, t)
+    assert abs(sc[0] - np.hypot(*gr[0])) <= 1e-14 * sc[0]
+    rng = np.random.default_rng(9)
+    src = rng.uniform(-1, 1, (300, 2))
+    tgt = np.vstack([rng.uniform(-1, 1, (40, 2)), src[:5]])  # some coincident targets
+    w = rng.uniform(0.1, 1.0, 300)
+    f = rng.standard_normal((2, 300))
+    g = rng.standard_normal((2, 45))
+    sc = oracle.grad_scale(src, w, f, g, tgt)
+    gr = oracle.grad_targets(src, w, f, g, tgt)
+    assert np.all(np.hypot(gr[:, 0], gr[:, 1]) <= sc * (1 + 1e-13))
+    # the brute-force definition written out with numpy
+    d = np.hypot(tgt[:, None, 0] - src[None, :, 0], tgt[:, None, 1] - src[None, :, 1])
+    with np.errstate(divide="ignore"):
+        inv = np.where(d > 0, 1.0 / d, 0.0)
+    want = np.einsum("di,dj,ij->i", np.abs(g), np.abs(w[None, :] * f), inv) / (2 * np.pi)
+    assert np.max(np.abs(sc - want) / want) <= 1e-13
