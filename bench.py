@@ -716,7 +716,8 @@ def leg_diff(args, dev, flush, stream):
     t0 = time.perf_counter()
     prob = inputs.star_problem("1M" if args.size == "full" else "small", targets="nodes", csr="near")
     gen_s = time.perf_counter() - t0
-    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=24, leaf=64, max_dens=1,
+    # P = 30: the target gradient (1/r kernel) meets the 1e-10 gate at P = 30 (1.5e-10 at P = 24)
+    plan = vp.Plan.create(prob.src_xy, prob.w, prob.tgt_xy, prob.csr, p_fmm=30, leaf=64, max_dens=1,
                           flags=vp.VP_FLAG_GRAPH, root=prob.root)
     ustar = torch.as_tensor(np.random.default_rng(12).standard_normal((1, prob.n_tgt)), device=dev)
     f0 = torch.as_tensor(prob.f, device=dev)
@@ -741,7 +742,7 @@ def leg_diff(args, dev, flush, stream):
     tg = float(np.mean(time_calls(lambda: step(False), reps, flush, stream))) * 1e3
     tt = float(np.mean(time_calls(lambda: step(True), reps, flush, stream))) * 1e3
     rec = {"workload": "star_1M_nodes_near", "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
-           "dtype": "f64", "p_fmm": 24, "leaf": 64, "input_gen_s": gen_s,
+           "dtype": "f64", "p_fmm": 30, "leaf": 64, "input_gen_s": gen_s,
            "forward_ms": tf, "loss_and_grad_f_ms": tg, "loss_grad_f_and_grad_t_ms": tt,
            "ratio_grad_f_vs_forward": tg / tf, "ratio_grad_f_t_vs_forward": tt / tf,
            "value": prob.n_tgt / (tt * 1e-3) / 1e6, "unit": "Mpoints/s (forward + dL/df + dL/dt)"}

@@ -132,8 +132,15 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
         for (int gb = e0; gb < e1; gb += 32) {
             const int grp = (gb - e0) >> 5;
-            const int ti = gb + lane;
-            const bool valid = ti < e1;
+            // directed sums: a group of fewer than 32 points is shared by ksplit
+            // sub-groups of lanes that divide the sources among them (masked lanes
+            // would cost FP64 issue slots all the same); their partial sums are
+            // added by shuffles at the end
+            const int gcount = min(32, e1 - gb);
+            const int ksplit = SYM ? 1 : 32 / gcount;
+            const int sub = SYM ? 0 : lane / gcount;
+            const int ti = SYM ? gb + lane : gb + lane % gcount;
+            const bool valid = SYM ? ti < e1 : sub < ksplit;
             const double2 z = valid ? g.exy[ti] : cb;
             double acc[ND], near[ND], qi[ND];
 #pragma unroll
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                         }
                     } else if (valid) {
 #pragma unroll 4
-                        for (int j = 0; j < n; ++j) {
+                        for (int j = sub; j < n; j += ksplit) {
                             const double2 sp = st.xy[j];
                             const double dx = z.x - sp.x, dy = z.y - sp.y;
                             const double Lg = log_r2(fma(dx, dx, dy * dy), tab, etab);
@@ -243,7 +250,14 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                     }
                 }
             }
-            if (valid) {
+            for (int sg = 1; sg < ksplit; ++sg) {  // warp-uniform
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double v = __shfl_down_sync(0xffffffffu, near[d], sg * gcount);
+                    if (sub == 0) near[d] += v;
+                }
+            }
+            if (valid && sub == 0) {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) psi[(int64_t)ti * ND + d] = fma(0.5, near[d], acc[d]);
             }
@@ -294,8 +308,13 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
         const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
         for (int gb = e0; gb < e1; gb += 32) {
-            const int ti = gb + lane;
-            const bool valid = ti < e1;
+            // a group of fewer than 32 points is shared by ksplit sub-groups of lanes
+            // that divide the sources among them (as in k_leaf64)
+            const int gcount = min(32, e1 - gb);
+            const int ksplit = 32 / gcount;
+            const int sub = lane / gcount;
+            const int ti = gb + lane % gcount;
+            const bool valid = sub < ksplit;
             const double2 z = valid ? g.exy[ti] : cb;
             double gx[ND], gy[ND];
             {
@@ -353,7 +372,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                     __syncwarp();
                     if (valid) {
 #pragma unroll 4
-                        for (int j = 0; j < n; ++j) {
+                        for (int j = sub; j < n; j += ksplit) {
                             const double2 sp = st.xy[j];
                             const double dx = z.x - sp.x, dy = z.y - sp.y;
                             const double r2 = fma(dx, dx, dy * dy);
@@ -368,7 +387,18 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                     }
                 }
             }
-            if (valid) {
+            for (int sg = 1; sg < ksplit; ++sg) {  // warp-uniform
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double vx = __shfl_down_sync(0xffffffffu, nx[d], sg * gcount);
+                    const double vy = __shfl_down_sync(0xffffffffu, ny[d], sg * gcount);
+                    if (sub == 0) {
+                        nx[d] += vx;
+                        ny[d] += vy;
+                    }
+                }
+            }
+            if (valid && sub == 0) {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
                     psi[((int64_t)ti * 2 + 0) * ND + d] = gx[d] + nx[d];
