@@ -1133,8 +1133,12 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_logtab, logtab);
     double2* d_log64 = nullptr;
     double* d_elog64 = nullptr;
+    double2* d_m2m64 = nullptr;
     up(&d_log64, log64);
     up(&d_elog64, elog64);
+    up(&d_m2m64, make_m2m64_table(P));
+    double2* d_l2l64 = nullptr;
+    up(&d_l2l64, make_l2l64_table(P));
     up(&d_fftab, fftab);
     up(&d_srho, B.srho);
     up(&d_trho, B.trho);
@@ -1231,6 +1235,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.logtab = (const float4*)d_logtab;
     tb.log64 = d_log64;
     tb.elog64 = d_elog64;
+    tb.m2m64 = d_m2m64;
+    tb.l2l64 = d_l2l64;
     tb.Hf = (const float2*)(d_fftab + offf[0]);
     tb.tpowf = (const float4*)(d_fftab + offf[1]);
     tb.mtpowf = (const float4*)(d_fftab + offf[2]);

@@ -442,47 +442,85 @@ __global__ void k_sym_reduce64(DevTree t, PassGeom g, const double* __restrict__
 // the warp that completes the count computes the parent's M2M and carries on
 // upwards; nothing waits. Multipoles of levels 0 and 1 are never read.
 //   M2M (scaled): B_l = -M_0 zeta^l / l + sum_{k<=l} C(l-1,k-1) 2^-k M_k zeta^(l-k)
+// M2M of box b into M(b), balanced over the lanes: with the table
+// m2m[c][l][k] = C(l-1, k-1) 2^-k zeta_c^(l-k) (k >= 1) and -zeta_c^l / l (k = 0),
+// B_l = sum_c sum_{k=0..l} m2m[c][l][k] M_k(child c) (M_0 real). Lane i of a child
+// slot owns the rows l1 = i + 1 and l2 = P - i, whose l1 + l2 + 2 = P + 3 terms it
+// walks in one loop, so every lane does the same work; floor(32 / H) children
+// (H = ceil(P / 2) lanes each) are done at once and their partial rows added by
+// shuffles. Lane 0 also forms B_0 = sum_c M_0(child c).
 template <int P, int ND>
-__device__ __forceinline__ void m2m_box64(const DevTree& t, const DevTables& tab, int b, double2* __restrict__ M,
-                                          double2* __restrict__ buf, int lane)
+__device__ __forceinline__ void m2m_box64(const DevTree& t, const double2* __restrict__ m2m, int b,
+                                          double2* __restrict__ M, double2* __restrict__ buf, int lane)
 {
     constexpr int P1 = P + 1;
-    double2 acc[ND];
+    constexpr int H = (P + 1) / 2;   // lanes per child slot
+    constexpr int CS = 32 / H;       // child slots per round
+    const int slot = lane / H, i = lane % H;
+    const int l1 = i + 1, l2 = P - i;
+    // the four children's multipoles (zeros for missing children), [c][k][d]
+    int chs[4];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
-    const double minv_l = lane == 0 ? 0.0 : -1.0 / (double)lane;
-    for (int c = 0; c < 4; ++c) {
-        const int ch = t.child[4 * b + c];
-        if (ch < 0) continue;
-        __syncwarp();
-        for (int i = lane; i < P1 * ND; i += 32) buf[i] = __ldcg(M + (int64_t)ch * P1 * ND + i);
-        __syncwarp();
-        if (lane <= P) {
-            const double2* zp = tab.zpow + c * P1;
-            if (lane == 0) {
+    for (int c = 0; c < 4; ++c) chs[c] = t.child[4 * b + c];
+    __syncwarp();
+    for (int idx = lane; idx < 4 * P1 * ND; idx += 32) {
+        const int c = idx / (P1 * ND), r = idx % (P1 * ND);
+        buf[idx] = chs[c] >= 0 ? __ldcg(M + (int64_t)chs[c] * P1 * ND + r) : make_double2(0.0, 0.0);
+    }
+    __syncwarp();
+    double2 a1[ND], a2[ND];
 #pragma unroll
-                for (int d = 0; d < ND; ++d) acc[d].x += buf[d].x, acc[d].y += buf[d].y;
-            } else {
-                const double2 zl = zp[lane];
+    for (int d = 0; d < ND; ++d) a1[d] = a2[d] = make_double2(0.0, 0.0);
+    if (slot < CS) {
+        for (int c = slot; c < 4; c += CS) {
+            const double2* mc = m2m + (size_t)c * P1 * P1;
+            const double2* bc = buf + (size_t)c * P1 * ND;
+            for (int j = 0; j < P + 3; ++j) {
+                const bool first = j <= l1;
+                const int l = first ? l1 : l2;
+                const int k = first ? j : j - l1 - 1;
+                const double2 zb = mc[l * P1 + k];
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    const double m0 = buf[d].x * minv_l;
-                    acc[d].x = fma(m0, zl.x, acc[d].x);
-                    acc[d].y = fma(m0, zl.y, acc[d].y);
-                }
-                for (int k = 1; k <= lane; ++k) {
-                    const double bm = tab.Bm[lane * P1 + k];
-                    const double2 z = zp[lane - k];
-                    const double2 zb = make_double2(z.x * bm, z.y * bm);
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) acc[d] = cfma64(zb, buf[k * ND + d], acc[d]);
+                    const double2 v = bc[k * ND + d];
+                    if (first)
+                        a1[d] = cfma64(zb, v, a1[d]);
+                    else
+                        a2[d] = cfma64(zb, v, a2[d]);
                 }
             }
         }
     }
-    if (lane <= P) {
+    // add the child slots' partial rows into the lanes of slot 0
 #pragma unroll
-        for (int d = 0; d < ND; ++d) M[((int64_t)b * P1 + lane) * ND + d] = acc[d];
+    for (int sl = 1; sl < CS; ++sl) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const double2 v1 = make_double2(__shfl_down_sync(0xffffffffu, a1[d].x, sl * H),
+                                            __shfl_down_sync(0xffffffffu, a1[d].y, sl * H));
+            const double2 v2 = make_double2(__shfl_down_sync(0xffffffffu, a2[d].x, sl * H),
+                                            __shfl_down_sync(0xffffffffu, a2[d].y, sl * H));
+            if (slot == 0) {
+                a1[d].x += v1.x, a1[d].y += v1.y;
+                a2[d].x += v2.x, a2[d].y += v2.y;
+            }
+        }
+    }
+    if (slot == 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            M[((int64_t)b * P1 + l1) * ND + d] = a1[d];
+            if (l2 != l1) M[((int64_t)b * P1 + l2) * ND + d] = a2[d];
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            double2 m0 = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) m0.x += buf[(size_t)c * P1 * ND + d].x, m0.y += buf[(size_t)c * P1 * ND + d].y;
+            M[((int64_t)b * P1) * ND + d] = m0;
+        }
     }
     __syncwarp();
 }
@@ -495,7 +533,7 @@ __global__ void __launch_bounds__(kW64 * 32)
     constexpr int P1 = P + 1;
     extern __shared__ __align__(16) unsigned char smem_p2m[];
     // per warp: [32][P1] powers, then [32][ND] charges; the M2M reuses the powers' space
-    constexpr int kPerWarp = 32 * P1 + (32 * ND + 1) / 2;
+    constexpr int kPerWarp = (32 > 4 * ND ? 32 : 4 * ND) * P1 + (32 * ND + 1) / 2;  // M2M stages [4][P1][ND]
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
     double2* pw = reinterpret_cast<double2*>(smem_p2m) + (size_t)wb * kPerWarp;
     double* qs = reinterpret_cast<double*>(pw + 32 * P1);
@@ -559,7 +597,7 @@ __global__ void __launch_bounds__(kW64 * 32)
             if (old != nch - 1) break;  // a sibling is still running; it will carry on
             __threadfence();            // the siblings' M before reading them
             if (lane == 0) counters[par] = 0;
-            m2m_box64<P, ND>(t, tab, par, M, pw, lane);
+            m2m_box64<P, ND>(t, tab.m2m64, par, M, pw, lane);
             cur = par;
         }
     }
@@ -567,20 +605,35 @@ __global__ void __launch_bounds__(kW64 * 32)
 
 // ----------------------------------------------------------------------------
 // a4: M2L over the V list plus P2L over the X list, one warp per target box.
-// For P = 16 the two half-warps take alternate V entries (all 32 lanes busy);
-// for P = 24, 30 one entry per warp. Within an entry, lane i of the half
-// computes A_l = M_l (-t)^l for l = i + 1 into shared memory, then
-//   L_l += t^l (sum_k H[l][k] A_k - M_0 / l)          (lane i, l = i + 1)
-//   Re L_0 += M_0 log|z0| + sum_k Re A_k              (a reduction over the half)
+// The warp takes G V-list entries of its box at a time and walks the G * P
+// items (entry s, coefficient l = 1..P) in R = G P / 32 rounds of 32 lanes, so
+// that every lane of every FP64 instruction works (G = 2 at P = 16, 4 at P = 24,
+// 1 at P = 30, where 30 of 32 lanes do). For an entry with source box C and
+// offset o (t = R/z0 from the offset table):
+//   A_k = M_k (-t)^k                                  (item (s, k), into shared memory)
+//   L_l += t^l (sum_k H[l][k] A_k - M_0 / l)          (item (s, l), accumulated per lane)
+//   Re L_0 += M_0 log|z0| + sum_k Re A_k              (per lane, reduced over the warp)
 // Im L_0 is not needed (L2P takes the real part; it is left zero). Afterwards
-// the halves are added and lane l holds L_l; the X list adds
+// the entries' partial locals are added through shared memory so that lane l
+// holds L_l, and the X list adds
 //   L_0 += q log|z - c|,  L_l -= (q / l) v^l,  v = R/(z - c).
 template <int P>
 struct M2L64Shape {
     static constexpr int P1 = P + 1;
-    static constexpr int kHalves = P <= 16 ? 2 : 1;
-    static constexpr int kLanes = 32 / kHalves;
+    static constexpr int G = P == 16 ? 2 : (P == 24 ? 4 : 1);  // V entries per warp at a time
+    static constexpr int R = (G * P + 31) / 32;                 // rounds of 32 items
 };
+
+template <int P, int ND>
+size_t m2l64_smem()
+{
+    using S = M2L64Shape<P>;
+    // per warp: A [G][P1][ND] double2, then the X list's powers [8][P1] double2 and
+    // charges and logs [8][ND + 1] double (the A space is reused for the partial locals)
+    const size_t a = (size_t)S::G * S::P1 * ND * sizeof(double2);
+    const size_t x = (size_t)8 * S::P1 * sizeof(double2) + (size_t)8 * (ND + 1) * sizeof(double);
+    return (size_t)kW64 * (a + x) + (((size_t)S::P1 * S::P1 * sizeof(double) + 15) & ~(size_t)15);
+}
 
 template <int P, int ND>
 __global__ void __launch_bounds__(kW64 * 32)
@@ -588,99 +641,140 @@ __global__ void __launch_bounds__(kW64 * 32)
             const double* __restrict__ q, const double2* __restrict__ logtab, const double* __restrict__ etab)
 {
     using S = M2L64Shape<P>;
-    constexpr int P1 = S::P1;
-    constexpr int NH = S::kHalves, NL = S::kLanes;
-    static_assert(P <= NL, "one lane per coefficient l = 1..P");
-    __shared__ double Ht[P1 * P1];                     // Ht[k][l] = H[l][k]
-    __shared__ double2 As[kW64][NH][P1][ND];           // A_k per half (k = 1..P)
-    __shared__ double2 pws[kW64][8][P1];               // P2L powers, 8 charges at a time
-    __shared__ double qls[kW64][8][ND + 1];            // P2L charges and logs
+    constexpr int P1 = S::P1, G = S::G, R = S::R;
+    extern __shared__ __align__(16) unsigned char smem_m2l[];
+    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+    constexpr size_t kA = (size_t)G * P1 * ND;                 // double2 per warp
+    constexpr size_t kPw = (size_t)8 * P1;                      // double2 per warp
+    double* Ht = reinterpret_cast<double*>(smem_m2l);           // Ht[k][l] = H[l][k]
+    double2* wbase = reinterpret_cast<double2*>(smem_m2l + ((P1 * P1 * sizeof(double) + 15) & ~(size_t)15)) +
+                     (size_t)wb * (kA + kPw + (8 * (ND + 1) + 1) / 2);
+    double2* As = wbase;                                        // [G][P1][ND]
+    double2* pws = wbase + kA;                                  // [8][P1]
+    double* qls = reinterpret_cast<double*>(pws + kPw);         // [8][ND + 1]
     for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) Ht[(i % P1) * P1 + i / P1] = tab.H[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    const int half = lane / NL, li = lane % NL;
-    const int l = li + 1;  // coefficient of this lane
-    const bool active = l <= P;
-    const double inv_l = active ? 1.0 / (double)l : 0.0;
+
+    // the items of this lane in each round: entry slot and coefficient (1..P), or idle
+    int it_s[R], it_l[R];
+    double inv_l[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int f = r * 32 + lane;
+        const bool on = f < G * P;
+        it_s[r] = on ? f / P : -1;
+        it_l[r] = on ? f % P + 1 : P;  // idle lanes repeat row P (result unused)
+        inv_l[r] = 1.0 / (double)it_l[r];
+    }
 
     for (int b = gwarp(); b < t.nbox; b += nwarps()) {
-        double2 lacc[ND];
-        double l0[ND];
+        double2 lacc[R][ND];
+        double l0d[ND];
 #pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            lacc[d] = make_double2(0.0, 0.0);
-            l0[d] = 0.0;
-        }
+        for (int d = 0; d < ND; ++d) l0d[d] = 0.0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int d = 0; d < ND; ++d) lacc[r][d] = make_double2(0.0, 0.0);
         const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
         const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
         const double logR = t.log_radius[b];
-        for (int e0 = v0; e0 < v1; e0 += NH) {
-            const int e = e0 + half;
-            const bool live = e < v1;
-            int o = 0, C = 0;
-            if (live) {
-                C = t.v_idx[e];
-                o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
-            }
-            double m0[ND];
+        for (int e0 = v0; e0 < v1; e0 += G) {
             __syncwarp();
-            if (live) {
-                const double2* MC = M + (int64_t)C * P1 * ND;
+            // A_k of the G entries (item (s, k) per lane and round); Re A_k and
+            // M_0 log|z0| go into this lane's share of Re L_0
 #pragma unroll
-                for (int d = 0; d < ND; ++d) m0[d] = MC[d].x;
-                if (active) {
-                    const double2 mt = tab.mtpow[o * P1 + l];
+            for (int r = 0; r < R; ++r) {
+                const int s = it_s[r], k = it_l[r];
+                if (s < 0) continue;
+                const int e = e0 + s;
+                if (e < v1) {
+                    const int C = t.v_idx[e];
+                    const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+                    const double2 mt = tab.mtpow[o * P1 + k];
+                    const double2* MC = M + (int64_t)C * P1 * ND;
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) As[wb][half][l][d] = cmul64(MC[l * ND + d], mt);
+                    for (int d = 0; d < ND; ++d) {
+                        const double2 a = cmul64(MC[k * ND + d], mt);
+                        As[(s * P1 + k) * ND + d] = a;
+                        l0d[d] += a.x;
+                        if (k == 1) {
+                            As[(s * P1) * ND + d] = MC[d];  // M_0 of the entry
+                            l0d[d] = fma(MC[d].x, logR + tab.log2o[o], l0d[d]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        As[(s * P1 + k) * ND + d] = make_double2(0.0, 0.0);
+                        if (k == 1) As[(s * P1) * ND + d] = make_double2(0.0, 0.0);
+                    }
                 }
             }
             __syncwarp();
-            if (live) {
+            // L_l of item (s, l): t^l (sum_k H[l][k] A_k - M_0 / l)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int s = it_s[r] < 0 ? 0 : it_s[r], l = it_l[r];
+                const int e = e0 + s;
+                const bool live = it_s[r] >= 0 && e < v1;
                 double2 acc[ND];
 #pragma unroll
                 for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
-                const int lr = active ? l : P;  // idle lanes repeat row P (result unused)
+                const double2* Aw = As + (size_t)s * P1 * ND;
 #pragma unroll 4
                 for (int k = 1; k <= P; ++k) {
-                    const double h = Ht[k * P1 + lr];
+                    const double h = Ht[k * P1 + l];
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
-                        const double2 a = As[wb][half][k][d];
+                        const double2 a = Aw[k * ND + d];
                         acc[d].x = fma(h, a.x, acc[d].x);
                         acc[d].y = fma(h, a.y, acc[d].y);
                     }
                 }
-                const double2 tl = tab.tpow[o * P1 + lr];
-                const double lz = logR + tab.log2o[o];
+                int o = 0;
+                if (live) {
+                    const int C = t.v_idx[e];
+                    o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
+                }
+                const double2 tl = tab.tpow[o * P1 + l];
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    const double2 a = make_double2(fma(-m0[d], inv_l, acc[d].x), acc[d].y);
-                    if (active) lacc[d] = cfma64(tl, a, lacc[d]);
-                    // Re L_0: lane i contributes Re A_(i+1); lane 0 of the half adds M_0 log|z0|
-                    double r = active ? As[wb][half][l][d].x : 0.0;
-                    if (li == 0) r = fma(m0[d], lz, r);
-                    l0[d] += r;
+                    const double2 a = make_double2(fma(-Aw[d].x, inv_l[r], acc[d].x), acc[d].y);
+                    if (live) lacc[r][d] = cfma64(tl, a, lacc[r][d]);
                 }
             }
         }
-        // add the halves' partial locals, reduce Re L_0 over the warp, and move
-        // coefficient l to lane l (lane 0 takes L_0)
+        // add the entries' partial locals: item (s, l) -> shared [s][l], then lane l sums over s
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (it_s[r] < 0) continue;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) As[(it_s[r] * P1 + it_l[r]) * ND + d] = lacc[r][d];
+        }
+        __syncwarp();
+        double2 lo[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
-            if (NH == 2) {
-                lacc[d].x += __shfl_down_sync(0xffffffffu, lacc[d].x, 16);
-                lacc[d].y += __shfl_down_sync(0xffffffffu, lacc[d].y, 16);
+            double s0 = l0d[d];
+            for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+            lo[d] = make_double2(0.0, 0.0);
+            if (lane == 0) {
+                lo[d].x = s0;
+            } else if (lane <= P) {
+                for (int s = 0; s < G; ++s) {
+                    const double2 v = As[(s * P1 + lane) * ND + d];
+                    lo[d].x += v.x;
+                    lo[d].y += v.y;
+                }
             }
-            for (int off = 16; off > 0; off >>= 1) l0[d] += __shfl_xor_sync(0xffffffffu, l0[d], off);
-            double2 v = make_double2(__shfl_up_sync(0xffffffffu, lacc[d].x, 1), __shfl_up_sync(0xffffffffu, lacc[d].y, 1));
-            if (lane == 0) v = make_double2(l0[d], 0.0);
-            lacc[d] = v;
         }
         // X list (P2L), lane l <= P owns L_l
         const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
         if (x1 > x0) {
             const double2 c = t.center[b];
-            const double R = t.radius[b];
+            const double Rb = t.radius[b];
             const double inv_ll = (lane == 0 || lane > P) ? 0.0 : 1.0 / (double)lane;
             for (int e = x0; e < x1; ++e) {
                 const int Cx = t.x_idx[e];
@@ -692,31 +786,32 @@ __global__ void __launch_bounds__(kW64 * 32)
                         const double2 z = g.cxy[base + lane];
                         const double dx = z.x - c.x, dy = z.y - c.y;
                         const double r2 = fma(dx, dx, dy * dy);
-                        const double s = R / r2;
-                        const double2 v = make_double2(dx * s, -dy * s);
-                        double2 p = make_double2(1.0, 0.0);
-                        pws[wb][lane][0] = p;
+                        const double sc = Rb / r2;
+                        const double2 v = make_double2(dx * sc, -dy * sc);
+                        double2 pw = make_double2(1.0, 0.0);
+                        pws[lane * P1] = pw;
                         for (int k = 1; k <= P; ++k) {
-                            p = cmul64(p, v);
-                            pws[wb][lane][k] = p;
+                            pw = cmul64(pw, v);
+                            pws[lane * P1 + k] = pw;
                         }
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) qls[wb][lane][d] = q[(int64_t)(base + lane) * ND + d];
-                        qls[wb][lane][ND] = 0.5 * log_r2(r2, logtab, etab);
+                        for (int d = 0; d < ND; ++d) qls[lane * (ND + 1) + d] = q[(int64_t)(base + lane) * ND + d];
+                        qls[lane * (ND + 1) + ND] = 0.5 * log_r2(r2, logtab, etab);
                     }
                     __syncwarp();
                     if (lane <= P) {
                         for (int j = 0; j < n; ++j) {
                             if (lane == 0) {
 #pragma unroll
-                                for (int d = 0; d < ND; ++d) lacc[d].x = fma(qls[wb][j][d], qls[wb][j][ND], lacc[d].x);
+                                for (int d = 0; d < ND; ++d)
+                                    lo[d].x = fma(qls[j * (ND + 1) + d], qls[j * (ND + 1) + ND], lo[d].x);
                             } else {
-                                const double2 pv = pws[wb][j][lane];
+                                const double2 pv = pws[j * P1 + lane];
 #pragma unroll
                                 for (int d = 0; d < ND; ++d) {
-                                    const double cq = -qls[wb][j][d] * inv_ll;
-                                    lacc[d].x = fma(cq, pv.x, lacc[d].x);
-                                    lacc[d].y = fma(cq, pv.y, lacc[d].y);
+                                    const double cq = -qls[j * (ND + 1) + d] * inv_ll;
+                                    lo[d].x = fma(cq, pv.x, lo[d].x);
+                                    lo[d].y = fma(cq, pv.y, lo[d].y);
                                 }
                             }
                         }
@@ -726,44 +821,62 @@ __global__ void __launch_bounds__(kW64 * 32)
         }
         if (lane <= P) {
 #pragma unroll
-            for (int d = 0; d < ND; ++d) L[((int64_t)b * P1 + lane) * ND + d] = lacc[d];
+            for (int d = 0; d < ND; ++d) L[((int64_t)b * P1 + lane) * ND + d] = lo[d];
         }
     }
 }
 
 // ----------------------------------------------------------------------------
-// a5: L2L into the boxes of one level, one warp per child box, lane l owns L'_l:
-//   L'_l += 2^-l sum_{k>=l} C(k, l) zeta^(k-l) L_k   (zeta = child offset / R_parent)
+// a5: L2L into the boxes of one level, balanced over the lanes: with the table
+// l2l[c][l][k] = C(k, l) 2^-l zeta_c^(k-l) (k >= l, zeta_c the child offset over
+// the parent half-side), L'_l += sum_{k=l..P} l2l[c][l][k] L_k(parent). Lane i of
+// a box slot owns the rows l1 = i and l2 = P - i (P + 2 terms together, so every
+// lane does the same work; the middle row of even P once); floor(32 / (P/2 + 1))
+// child boxes per warp at a time.
 template <int P, int ND>
 __global__ void __launch_bounds__(kW64 * 32)
     k_l2l64(DevTree t, DevTables tab, int b0, int b1, double2* __restrict__ L)
 {
     constexpr int P1 = P + 1;
-    __shared__ double2 Ls[kW64][P1][ND];
-    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    for (int b = b0 + gwarp(); b < b1; b += nwarps()) {
+    constexpr int H = P / 2 + 1;    // lanes per box slot
+    constexpr int BS = 32 / H;      // boxes per warp at a time
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / H, i = lane % H;
+    const int l1 = i, l2 = P - i;
+    for (int bb = b0 + gwarp() * BS; bb < b1; bb += nwarps() * BS) {
+        const int b = bb + slot;
+        if (slot >= BS || b >= b1) continue;
         const int p = t.parent[b];
         const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
-        __syncwarp();
-        for (int i = lane; i < P1 * ND; i += 32) (&Ls[wb][0][0])[i] = L[(int64_t)p * P1 * ND + i];
-        __syncwarp();
-        if (lane <= P) {
-            const double2* zp = tab.zpow + cq * P1;
-            double2 acc[ND];
+        const double2* tc = tab.l2l64 + (size_t)cq * P1 * P1;
+        const double2* Lp = L + (int64_t)p * P1 * ND;
+        double2 a1[ND], a2[ND];
 #pragma unroll
-            for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
-            for (int k = lane; k <= P; ++k) {
-                const double bl = tab.Bl[lane * P1 + k];
-                const double2 z = zp[k - lane];
-                const double2 zb = make_double2(z.x * bl, z.y * bl);
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[d] = cfma64(zb, Ls[wb][k][d], acc[d]);
-            }
+        for (int d = 0; d < ND; ++d) a1[d] = a2[d] = make_double2(0.0, 0.0);
+        const int n1 = P - l1 + 1;  // terms of row l1; row l2 has P - l2 + 1 = l1 + 1
+        for (int j = 0; j < P + 2; ++j) {
+            const bool first = j < n1;
+            const int l = first ? l1 : l2;
+            const int k = first ? l1 + j : l2 + (j - n1);
+            const double2 zb = tc[l * P1 + k];
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
-                const int64_t i = ((int64_t)b * P1 + lane) * ND + d;
-                const double2 o = L[i];
-                L[i] = make_double2(o.x + acc[d].x, o.y + acc[d].y);
+                const double2 v = Lp[k * ND + d];
+                if (first)
+                    a1[d] = cfma64(zb, v, a1[d]);
+                else
+                    a2[d] = cfma64(zb, v, a2[d]);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            int64_t o = ((int64_t)b * P1 + l1) * ND + d;
+            double2 x = L[o];
+            L[o] = make_double2(x.x + a1[d].x, x.y + a1[d].y);
+            if (l2 != l1) {
+                o = ((int64_t)b * P1 + l2) * ND + d;
+                x = L[o];
+                L[o] = make_double2(x.x + a2[d].x, x.y + a2[d].y);
             }
         }
     }
@@ -792,7 +905,7 @@ int device_sms()
 template <int P, int ND>
 size_t p2m_smem()
 {
-    return (size_t)kW64 * (32 * (P + 1) + (32 * ND + 1) / 2) * sizeof(double2);
+    return (size_t)kW64 * ((32 > 4 * ND ? 32 : 4 * ND) * (P + 1) + (32 * ND + 1) / 2) * sizeof(double2);
 }
 
 template <int ND>
@@ -813,6 +926,9 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_p2m64<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<P, ND>());
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_m2l64<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)m2l64_smem<P, ND>());
+        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_leaf64<P, ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_leaf64<P, ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
@@ -831,15 +947,16 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
                                                                                       ws.m2m_count);
     if (tm) tm->end(id);
     id = tm ? tm->begin("m2l") : -1;
-    k_m2l64<P, ND><<<blocks_for_warps(t.nbox, kW64), threads, 0, s>>>(t, tab, g, ws.M, ws.L, ws.q, tab.log64,
-                                                                     tab.elog64);
+    k_m2l64<P, ND><<<blocks_for_warps(t.nbox, kW64), threads, m2l64_smem<P, ND>(), s>>>(t, tab, g, ws.M, ws.L, ws.q,
+                                                                                       tab.log64, tab.elog64);
     if (tm) tm->end(id);
     id = tm ? tm->begin("l2l") : -1;
     // boxes of levels 0 and 1 have empty V and X lists, so the first L2L that
     // adds anything goes into level 3
     for (int l = 3; l < t.nlevels; ++l) {
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
-        k_l2l64<P, ND><<<blocks_for_warps(b1 - b0, kW64), threads, 0, s>>>(t, tab, b0, b1, ws.L);
+        k_l2l64<P, ND><<<blocks_for_warps((b1 - b0 + 32 / (P / 2 + 1) - 1) / (32 / (P / 2 + 1)), kW64), threads, 0,
+                         s>>>(t, tab, b0, b1, ws.L);
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
@@ -892,6 +1009,60 @@ cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, 
         case 30: return fmm64_p<30>(nd, t, tab, g, ws, gradient, timer, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// M2M table of order P: m2m[c][l][k] = C(l-1, k-1) 2^-k zeta_c^(l-k) for 1 <= k <= l,
+// m2m[c][l][0] = -zeta_c^l / l (l >= 1), zero elsewhere; zeta_c = ((c & 1 ? 1 : -1) +
+// i (c & 2 ? 1 : -1)) / 2 is the child-centre offset over the parent half-side. The
+// binomial products are exact in float64 (dyadic zeta powers), the 1/l terms rounded once.
+std::vector<double2> make_m2m64_table(int P)
+{
+    const int P1 = P + 1;
+    std::vector<double2> tab((size_t)4 * P1 * P1, make_double2(0.0, 0.0));
+    for (int c = 0; c < 4; ++c) {
+        const double zx = (c & 1) ? 0.5 : -0.5, zy = (c & 2) ? 0.5 : -0.5;
+        std::vector<double2> zp((size_t)P1);
+        zp[0] = make_double2(1.0, 0.0);
+        for (int m = 1; m <= P; ++m)
+            zp[(size_t)m] = make_double2(zp[(size_t)m - 1].x * zx - zp[(size_t)m - 1].y * zy,
+                                         zp[(size_t)m - 1].x * zy + zp[(size_t)m - 1].y * zx);
+        for (int l = 1; l <= P; ++l) {
+            double2* row = tab.data() + ((size_t)c * P1 + l) * P1;
+            row[0] = make_double2(-zp[(size_t)l].x / l, -zp[(size_t)l].y / l);
+            double binom = 1.0;  // C(l-1, k-1), k = 1
+            for (int k = 1; k <= l; ++k) {
+                const double w = std::ldexp(binom, -k);
+                row[k] = make_double2(w * zp[(size_t)(l - k)].x, w * zp[(size_t)(l - k)].y);
+                binom = binom * (double)(l - k) / (double)k;  // C(l-1, k) (exact: integers below 2^53)
+            }
+        }
+    }
+    return tab;
+}
+
+// L2L table of order P: l2l[c][l][k] = C(k, l) 2^-l zeta_c^(k-l) for k >= l (exact in
+// float64: dyadic zeta powers, integer binomials below 2^53), zero elsewhere.
+std::vector<double2> make_l2l64_table(int P)
+{
+    const int P1 = P + 1;
+    std::vector<double2> tab((size_t)4 * P1 * P1, make_double2(0.0, 0.0));
+    for (int c = 0; c < 4; ++c) {
+        const double zx = (c & 1) ? 0.5 : -0.5, zy = (c & 2) ? 0.5 : -0.5;
+        std::vector<double2> zp((size_t)P1);
+        zp[0] = make_double2(1.0, 0.0);
+        for (int m = 1; m <= P; ++m)
+            zp[(size_t)m] = make_double2(zp[(size_t)m - 1].x * zx - zp[(size_t)m - 1].y * zy,
+                                         zp[(size_t)m - 1].x * zy + zp[(size_t)m - 1].y * zx);
+        for (int l = 0; l <= P; ++l) {
+            double binom = 1.0;  // C(k, l), k = l
+            for (int k = l; k <= P; ++k) {
+                const double w = std::ldexp(binom, -l);
+                tab[((size_t)c * P1 + l) * P1 + k] = make_double2(w * zp[(size_t)(k - l)].x, w * zp[(size_t)(k - l)].y);
+                binom = binom * (double)(k + 1) / (double)(k + 1 - l);  // C(k + 1, l)
+            }
+        }
+    }
+    return tab;
 }
 
 // Host tables of the FP64 logarithm: tab[k] = (s_k, T_k) with c_k = 1 + k 2^-B,

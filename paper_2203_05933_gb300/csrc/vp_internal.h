@@ -85,6 +85,8 @@ struct DevTables {
     const float4* logtab = nullptr; // [128] {1/c_k, T_hi, T_lo, 0}, T = -log(1/c_k)  (P2P log)
     const double2* log64 = nullptr; // [1 << kLog64Bits] {s_k, -log s_k}               (FP64 log)
     const double* elog64 = nullptr; // [128] (i - 64) log 2                            (FP64 log)
+    const double2* m2m64 = nullptr; // [4][P1][P1] M2M coefficients per child quadrant   (float64 M2M)
+    const double2* l2l64 = nullptr; // [4][P1][P1] L2L coefficients per child quadrant   (float64 L2L)
     // float-float copies for the FP32-pipe M2L
     const float2* Hf = nullptr;     // [P1][P1]
     const float4* tpowf = nullptr;  // [49][P1] complex (re_h, re_l, im_h, im_l)
@@ -206,6 +208,8 @@ struct PhaseTimer {
 cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
                          bool gradient, PhaseTimer* timer, cudaStream_t s);
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);
+std::vector<double2> make_m2m64_table(int P);
+std::vector<double2> make_l2l64_table(int P);
 // Device-side construction of the grouped correction (vp_csr.cu). err: device int,
 // bit 1 = column out of range, bit 2 = non-finite value. same[i] = row i repeats row i - 1.
 cudaError_t launch_csr_check(int64_t nnz, const int32_t* col, const double* val, int64_t ncols, int* err,
