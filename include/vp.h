@@ -358,8 +358,8 @@ const char* vp_version(void);
 
 /*
  * Host-side inspection of the tree and interaction lists (no GPU needed).
- * vp_tree_build builds exactly the tree vp_plan_create would build for the same
- * points and options, on the host, from host arrays.
+ * vp_tree_build builds exactly the tree vp_plan_create builds (on the GPU) for
+ * the same points and options, on the host, from host arrays.
  * vp_tree_get copies one array out (which = VP_TREE_*); pass dst = NULL to get
  * the element count in *count first. Arrays:
  *   VP_TREE_BOX_LEVEL   int32 [n_boxes]
@@ -382,6 +382,16 @@ enum {
 };
 vp_status vp_tree_build(vp_tree* out, int64_t n_src, const double* src_xy_host,
                         int64_t n_tgt, const double* tgt_xy_host, const vp_options* opt);
+/*
+ * vp_tree_build_device — the same tree and lists, bit for bit, built on the GPU
+ * from device point arrays (what vp_plan_create uses): Morton keys on the 28-bit
+ * grid of the root square, an LSD radix sort that keeps equal keys in caller
+ * order, splitting level by level and the U/V/W/X lists, as kernels; the result
+ * is copied into a host-side vp_tree for vp_tree_get. src_xy, tgt_xy: device.
+ * Synchronizes `stream`. Errors: VP_ERR_ARG (as vp_tree_build), VP_ERR_CUDA.
+ */
+vp_status vp_tree_build_device(vp_tree* out, int64_t n_src, const double* src_xy, int64_t n_tgt,
+                               const double* tgt_xy, const vp_options* opt, void* stream);
 vp_status vp_tree_get(vp_tree tree, int32_t which, int32_t* dst, int64_t* count);
 vp_status vp_tree_destroy(vp_tree tree);
 

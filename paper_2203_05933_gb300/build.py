@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libvp.so")
 OBJ_DIR = os.path.join(PKG, "_build")
 
-SOURCES = ["vp_tree.cpp", "vp_api.cu", "vp_fmm.cu", "vp_fmm64.cu", "vp_spmv.cu", "vp_csr.cu", "vp_static.cu", "vp_upsample.cu", "vp_interp.cu", "vp_tricorr.cu", "vp_mhelm.cu", "vp_calib.cu"]
+SOURCES = ["vp_tree.cpp", "vp_api.cu", "vp_fmm.cu", "vp_fmm64.cu", "vp_spmv.cu", "vp_csr.cu", "vp_static.cu", "vp_upsample.cu", "vp_interp.cu", "vp_tricorr.cu", "vp_mhelm.cu", "vp_calib.cu", "vp_tree_gpu.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

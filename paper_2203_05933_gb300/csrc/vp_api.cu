@@ -495,6 +495,9 @@ struct ProblemIn {
     std::vector<int64_t> hrow;
     std::vector<int32_t> hcol;
     std::vector<double> hval;
+    // the caller's device coordinates (the tree is built from them on the device)
+    const double* d_src = nullptr;
+    const double* d_tgt = nullptr;
     // the caller's device CSR when its columns and values stay on the device
     const int64_t* d_row = nullptr;
     const int32_t* d_col = nullptr;
@@ -546,6 +549,8 @@ vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const 
     P.n_src = n_src;
     P.n_tgt = n_tgt;
     P.nnz = P.has_corr ? nnz : 0;
+    P.d_src = src_xy;
+    P.d_tgt = tgt_xy;
     P.hs.resize((size_t)n_src * 2);
     P.hw.resize((size_t)n_src);
     P.ht.resize((size_t)n_tgt * 2);
@@ -584,10 +589,12 @@ vp_status copy_problem(ProblemIn& P, int64_t n_src, const double* src_xy, const 
     return VP_OK;
 }
 
-std::string build_one(ProblemIn& P, const TreeOptions& to, Built& B)
+// The tree is built on the device from the caller's coordinates (build_tree_gpu,
+// the same tree as the host build_tree).
+std::string build_one(ProblemIn& P, const TreeOptions& to, Built& B, cudaStream_t s)
 {
     Tree T;
-    std::string err = build_tree(P.n_src, P.hs.data(), P.n_tgt, P.ht.data(), to, T);
+    std::string err = build_tree_gpu(P.n_src, P.d_src, P.n_tgt, P.d_tgt, to, T, s);
     if (!err.empty()) return err;
     const int64_t n_src = P.n_src, n_tgt = P.n_tgt;
     const int32_t nb = (int32_t)T.n_boxes();
@@ -1393,7 +1400,7 @@ vp_status vp_plan_create(vp_plan* out, int64_t n_src, const double* src_xy, cons
     to.max_level = max_level;
     std::memcpy(to.root, opt.root, sizeof(to.root));
     Built B;
-    std::string err = build_one(in, to, B);
+    std::string err = build_one(in, to, B, s);
     if (!err.empty()) return fail(VP_ERR_ARG, err);
     vp_plan p = new_plan(opt, P, leaf, max_dens);
     if (!p) return fail(VP_ERR_OOM, "host allocation");
@@ -1439,7 +1446,7 @@ vp_status vp_plan_create_many(vp_plan* out, int32_t nprob, const int64_t* n_src,
         to.leaf = leaf;
         to.max_level = max_level;
         if (roots) std::memcpy(to.root, roots + 3 * (size_t)k, sizeof(to.root));
-        std::string err = build_one(in, to, parts[(size_t)k]);
+        std::string err = build_one(in, to, parts[(size_t)k], s);
         if (!err.empty()) return fail(VP_ERR_ARG, "problem " + std::to_string(k) + ": " + err);
     }
     Built B = merge(parts);
@@ -1534,7 +1541,7 @@ vp_status vp_plan_create_upsampled(vp_plan* out, int64_t n_src, const double* sr
     to.max_level = max_level;
     std::memcpy(to.root, opt.root, sizeof(to.root));
     Built B;
-    std::string err = build_one(in, to, B);
+    std::string err = build_one(in, to, B, s);
     if (!err.empty()) return fail(VP_ERR_ARG, err);
     vp_plan p = new_plan(opt, P, leaf, max_dens);
     if (!p) return fail(VP_ERR_OOM, "host allocation");
@@ -2011,6 +2018,33 @@ vp_status vp_tree_build(vp_tree* out, int64_t n_src, const double* src_xy, int64
     if (!err.empty()) {
         delete t;
         return fail(VP_ERR_ARG, err);
+    }
+    *out = t;
+    return VP_OK;
+}
+
+vp_status vp_tree_build_device(vp_tree* out, int64_t n_src, const double* src_xy, int64_t n_tgt,
+                               const double* tgt_xy, const vp_options* opt_in, void* stream)
+{
+    if (!out) return fail(VP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_src < 0 || n_tgt < 0) return fail(VP_ERR_ARG, "negative size");
+    if ((n_src > 0 && !src_xy) || (n_tgt > 0 && !tgt_xy)) return fail(VP_ERR_ARG, "NULL point array");
+    vp_options opt;
+    std::memset(&opt, 0, sizeof(opt));
+    if (opt_in) opt = *opt_in;
+    TreeOptions to;
+    to.leaf = opt.leaf == 0 ? 64 : opt.leaf;
+    to.max_level = opt.max_level == 0 ? 24 : opt.max_level;
+    to.root[0] = opt.root[0];
+    to.root[1] = opt.root[1];
+    to.root[2] = opt.root[2];
+    vp_tree t = new (std::nothrow) vp_tree_s();
+    if (!t) return fail(VP_ERR_OOM, "host allocation");
+    std::string err = build_tree_gpu(n_src, src_xy, n_tgt, tgt_xy, to, t->t, (cudaStream_t)stream);
+    if (!err.empty()) {
+        delete t;
+        return fail(err.rfind("CUDA:", 0) == 0 ? VP_ERR_CUDA : VP_ERR_ARG, err);
     }
     *out = t;
     return VP_OK;

@@ -287,4 +287,10 @@ double green_mhelm_host(double lambda, double r);
 
 bool p_supported(int P);
 
+// The adaptive tree and its lists built on the device from device coordinates
+// (vp_tree_gpu.cu): the same Tree, bit for bit, as build_tree on the host.
+// Returns "" or a message ("CUDA: ..." for runtime failures). Synchronizes s.
+std::string build_tree_gpu(int64_t n_src, const double* src_xy, int64_t n_tgt, const double* tgt_xy,
+                           const TreeOptions& opt, Tree& t, cudaStream_t s);
+
 }  // namespace vp

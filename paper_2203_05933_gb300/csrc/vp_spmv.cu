@@ -166,26 +166,37 @@ __device__ __forceinline__ void grouped_rows64(const DevGroupedCSR& A, int r0, i
     for (int rb = r0 + warp * RPW; rb < r1; rb += nw * RPW) {
         const int r = rb + sub;
         const bool live = r < r1;
+        // U value pairs per lane in flight (loads issued before the arithmetic)
+        constexpr int U = ND <= 2 ? 4 : 2;
         double acc0[ND], acc1[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc0[d] = acc1[d] = 0.0;
         if (live) {
             const double2* vrow = reinterpret_cast<const double2*>(A.vd + A.rowptr[r]);
-#pragma unroll 2
-            for (int qp = li; qp < np; qp += kRowLanes64) {
-                const double2 v = __ldcs(vrow + qp);  // streamed once: do not keep in L1/L2
-                const int k = 2 * qp;
+            for (int q0 = li; q0 < np; q0 += U * kRowLanes64) {
+                double2 v[U];
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    double2 xv;
-                    if (STAGED) {
-                        xv = *reinterpret_cast<const double2*>(F + d * smem_m + k);
-                    } else {
-                        xv.x = x[d * ld_x + A.cols[c0 + k]];
-                        xv.y = k + 1 < m ? x[d * ld_x + A.cols[c0 + k + 1]] : 0.0;
+                for (int u = 0; u < U; ++u) {
+                    const int qp = q0 + u * kRowLanes64;
+                    v[u] = qp < np ? __ldcs(vrow + qp) : make_double2(0.0, 0.0);  // streamed once
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int qp = q0 + u * kRowLanes64;
+                    if (qp >= np) continue;
+                    const int k = 2 * qp;
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        double2 xv;
+                        if (STAGED) {
+                            xv = *reinterpret_cast<const double2*>(F + d * smem_m + k);
+                        } else {
+                            xv.x = x[d * ld_x + A.cols[c0 + k]];
+                            xv.y = k + 1 < m ? x[d * ld_x + A.cols[c0 + k + 1]] : 0.0;
+                        }
+                        acc0[d] = fma(v[u].x, xv.x, acc0[d]);
+                        acc1[d] = fma(v[u].y, xv.y, acc1[d]);
                     }
-                    acc0[d] = fma(v.x, xv.x, acc0[d]);
-                    acc1[d] = fma(v.y, xv.y, acc1[d]);
                 }
             }
         }

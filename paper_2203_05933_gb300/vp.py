@@ -38,7 +38,7 @@ EXPORTED = [
     "vp_plan_info", "vp_plan_phase_times", "vp_plan_set_flags", "vp_plan_set_overlap", "vp_plan_destroy",
     "vp_green_eval_host",
     "vp_status_string", "vp_last_error", "vp_version", "vp_measure_peaks",
-    "vp_tree_build", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
+    "vp_tree_build", "vp_tree_build_device", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
     "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
 ]
 
@@ -125,6 +125,7 @@ def _load():
         "vp_version": [],
         "vp_measure_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P],
         "vp_tree_build": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options)],
+        "vp_tree_build_device": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options), P],
         "vp_tree_get": [P, I32, P, ctypes.POINTER(I64)],
         "vp_tree_destroy": [P],
         "vp_interp_create": [ctypes.POINTER(P), I32, ctypes.POINTER(vp_interp_type), I64, P, P, I64, P, P, P],
@@ -437,6 +438,24 @@ def vp_tree_build(src_xy: np.ndarray, tgt_xy: np.ndarray, options: vp_options | 
                            tgt.ctypes.data_as(ctypes.c_void_p),
                            ctypes.byref(options) if options is not None else None)
     _check(st, "vp_tree_build")
+    return _tree_arrays(h)
+
+
+def vp_tree_build_device(src_xy, tgt_xy, options: vp_options | None = None, stream=None) -> dict:
+    """The same tree and lists built on the GPU (vp_tree_build_device) from device
+    copies of the points; returns the same dict of int32 arrays."""
+    lib = _load()
+    src = _dev_f64(src_xy).reshape(-1, 2)
+    tgt = _dev_f64(tgt_xy).reshape(-1, 2)
+    h = ctypes.c_void_p()
+    st = lib.vp_tree_build_device(ctypes.byref(h), src.shape[0], _ptr(src), tgt.shape[0], _ptr(tgt),
+                                  ctypes.byref(options) if options is not None else None, _stream(stream))
+    _check(st, "vp_tree_build_device")
+    return _tree_arrays(h)
+
+
+def _tree_arrays(h) -> dict:
+    lib = _load()
     out = {}
     try:
         for name, which in TREE_ARRAYS.items():
