@@ -55,10 +55,16 @@ F64_OPS_L2P_PER_COEF = 4.0
 P2P_FF_OPS_PER_PAIR = 77.0
 P2P_FF_OPS_REVERSE = 14.0
 FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12  # FP32/INT32 lane-operations per second (T ops/s)
-# DRAM bytes (read + write) per work unit from one ncu capture of the float64
-# leaf kernel on a small case, scaled to a launch by the units it processes;
-# None until a capture of the current kernel exists.
-PROFILED_TRAFFIC = {}
+# DRAM bytes (read + write) per work unit from one ncu capture (--set full) of
+# each float64 kernel on the 1 M star (own-cell pattern, P = 24, one density),
+# scaled to a launch by the units it processes: (bytes per unit, unit attribute
+# of the plan info, unit name, P, densities, kernel). Only a phase whose kernel
+# has not changed since its capture is listed; others report traffic null.
+PROFILED_TRAFFIC = {
+    "leaf": (60.52, "n_tgt", "target", 24, 1, "k_leaf64<24, 1, 0>"),
+    "m2l": (22.41, "n_v_pairs", "V-list pair", 24, 1, "k_m2l64<24, 1>"),
+    "upward": (26.52, "n_src", "source", 24, 1, "k_p2m64<24, 1>"),
+}
 
 
 def hbm_peak():
@@ -91,7 +97,7 @@ def roofline_models(info, ndens, fp64_tflops):
                              f"target for L2P; the kernel issues {F64_OPS_PAIR:.0f} FP64 ops per directed pair, "
                              f"{F64_OPS_SYM:.0f} per distance serving both directions ({evals} evaluations for "
                              f"{pairs} directed pairs)"},
-        "m2l": {"kernel": "k_m2l64 (float64 scaled-Hankel M2L, half-warps for P = 16)",
+        "m2l": {"kernel": "k_m2l64 (float64 scaled-Hankel M2L + P2L, G V-list entries per warp)",
                 "flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens,
                 "ops": info.n_v_pairs * (2.0 * P * P + 10.0 * P) * ndens, "units": info.n_v_pairs,
                 "ops_peak": ops_peak, "per_unit": f"8(P+1)^2 flops per V-list pair, P={P}"},
@@ -390,10 +396,12 @@ def roofline_of(phase_ms, info, ndens, fp64_tflops, fp64_src):
             gbs = m["bytes"] / t / 1e9
             r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": m["hbm_peak"], "frac": gbs / m["hbm_peak"],
                         "peak_source": m["hbm_src"]}
-        if PROFILED_TRAFFIC.get(name) and m.get("units"):
-            per, what, src = PROFILED_TRAFFIC[name]
-            r["traffic"] = per * m["units"]
-            r["traffic_source"] = f"ncu dram__bytes_read.sum + dram__bytes_write.sum per {what}, {src}, scaled"
+        tr = PROFILED_TRAFFIC.get(name)
+        if tr and tr[3] == info.p_fmm and tr[4] == ndens and not getattr(info, "sym_slots", 0):
+            per, attr, what, _, _, kern = tr
+            r["traffic"] = per * float(getattr(info, attr))
+            r["traffic_source"] = (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of {kern}: {per} B per {what} "
+                                   f"on the 1 M star (own-cell pattern), scaled to this launch")
         out[name] = r
     return out
 
@@ -772,7 +780,7 @@ def main():
     vp._load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    fp64_tflops, fp32_tflops = vp.vp_measure_peaks()
+    fp64_tflops, fp32_tflops, dmma_tflops, bf16mma_tflops = vp.vp_measure_peaks(tensor=True)
     fp64_src = ("vp_measure_peaks in this run: chains of independent FP64 FMAs in every lane of a full grid "
                 "(measured)")
     t0 = time.perf_counter()
@@ -899,7 +907,8 @@ def main():
         "phase_ms": phase_ms,
         "roofline": roofline,
         "roofline_phases": rl_all,
-        "peaks": {"fp64_tflops": fp64_tflops, "fp32_tflops": fp32_tflops, "source": fp64_src},
+        "peaks": {"fp64_tflops": fp64_tflops, "fp32_tflops": fp32_tflops, "f64_mma_tflops": dmma_tflops,
+                  "bf16_mma_sync_tflops": bf16mma_tflops, "source": fp64_src},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(prob.n_src * 8),
                 "d2h_bytes_per_step": int(prob.n_tgt * 8)},
