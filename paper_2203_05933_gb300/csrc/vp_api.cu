@@ -1146,6 +1146,19 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_m2m64, make_m2m64_table(P));
     double2* d_l2l64 = nullptr;
     up(&d_l2l64, make_l2l64_table(P));
+    std::vector<uint16_t> m2lh;
+    std::vector<int32_t> m2le;
+    std::vector<double2> mtpow_s;
+    std::vector<double> tau_pow;
+    make_m2l_tensor_tables(P, m2lh, m2le, mtpow_s, tau_pow);
+    uint16_t* d_m2lh = nullptr;
+    int32_t* d_m2le = nullptr;
+    double2* d_mtpow_s = nullptr;
+    double* d_tau_pow = nullptr;
+    up(&d_m2lh, m2lh);
+    up(&d_m2le, m2le);
+    up(&d_mtpow_s, mtpow_s);
+    up(&d_tau_pow, tau_pow);
     up(&d_fftab, fftab);
     up(&d_srho, B.srho);
     up(&d_trho, B.trho);
@@ -1244,6 +1257,10 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.elog64 = d_elog64;
     tb.m2m64 = d_m2m64;
     tb.l2l64 = d_l2l64;
+    tb.m2lh = reinterpret_cast<const uint32_t*>(d_m2lh);
+    tb.m2le = d_m2le;
+    tb.mtpow_s = d_mtpow_s;
+    tb.tau_pow = d_tau_pow;
     tb.Hf = (const float2*)(d_fftab + offf[0]);
     tb.tpowf = (const float4*)(d_fftab + offf[1]);
     tb.mtpowf = (const float4*)(d_fftab + offf[2]);
@@ -1254,7 +1271,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
                            p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
-                           tb.log64, p->gfwd.vd};
+                           tb.log64, p->gfwd.vd, tb.m2lh, tb.mtpow_s};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf, p->gfwd.vf};
     bool ok = true;
     for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);

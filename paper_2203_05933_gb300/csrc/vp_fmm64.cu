@@ -35,6 +35,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "vp_internal.h"
 
@@ -260,6 +262,165 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
             if (valid && sub == 0) {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) psi[(int64_t)ti * ND + d] = fma(0.5, near[d], acc[d]);
+            }
+        }
+    }
+}
+
+// a5 + a6, directed (evaluation points are not the charge points of a
+// symmetric plan): one leaf per warp from the persistent queue. First the far
+// part of each evaluation point of the leaf (L2P + W-list M2P, one point per
+// lane) is written to psi. Then the near field: the charge points of all U-list
+// leaves form one stream, staged 32 at a time; the leaf's T points and K
+// interleaved subsets of each 32-point chunk share the lanes (lane = a K + kap
+// takes point a of the pass and chunk positions kap, kap + K, ...), in
+// ceil(T K / 32) passes over the stream, K in {1, 2, 4, 8, 16} chosen per leaf
+// for the fewest lane-steps (every lane of an FP64 instruction costs an issue
+// slot, busy or not). The K partial sums of a point are added by shuffles and
+// psi += near / 2 (the log is of r^2).
+template <int P, int ND>
+__global__ void __launch_bounds__(kLeafWarps64 * 32)
+    k_leaf64d(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
+              const double2* __restrict__ L, const double2* __restrict__ logtab, const double* __restrict__ etab_g,
+              double* __restrict__ psi, int* __restrict__ work)
+{
+    constexpr int P1 = P + 1;
+    extern __shared__ __align__(16) unsigned char smem64d[];
+    double2* tab = reinterpret_cast<double2*>(smem64d);                      // [1 << kLog64Bits]
+    double* etab = reinterpret_cast<double*>(tab + (1 << kLog64Bits));       // [2 * kEBias]
+    LeafStage64<ND>* stage = reinterpret_cast<LeafStage64<ND>*>(etab + 2 * kEBias);
+    for (int i = threadIdx.x; i < (1 << kLog64Bits); i += blockDim.x) tab[i] = logtab[i];
+    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) etab[i] = etab_g[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    LeafStage64<ND>& st = stage[threadIdx.x >> 5];
+
+    for (;;) {
+        int li = 0;
+        if (lane == 0) li = atomicAdd(work, 1);
+        li = __shfl_sync(0xffffffffu, li, 0);
+        if (li >= t.nleaf) break;
+        const int b = t.leaves[li];
+        const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
+        if (e0 == e1) continue;
+        const int T = e1 - e0;
+        const double2 cb = t.center[b];
+        const double invRb = 1.0 / t.radius[b];
+        const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
+        const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
+        // far part: L2P (Re sum_l L_l u^l, u = (z - c)/R, Horner) and M2P over W
+        // (M_0 log|z - c| + Re sum_k M_k v^k, v = R/(z - c))
+        for (int i = lane; i < T; i += 32) {
+            const double2 z = g.exy[e0 + i];
+            double acc[ND];
+            const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
+            const double2* Lb = L + (int64_t)b * P1 * ND;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                double2 sl = Lb[P * ND + d];
+#pragma unroll 4
+                for (int l = P - 1; l >= 0; --l) sl = cfma64(sl, u, Lb[l * ND + d]);
+                acc[d] = sl.x;
+            }
+            for (int e = w0; e < w1; ++e) {
+                const int D = t.w_idx[e];
+                const double2 cD = t.center[D];
+                const double RD = t.radius[D];
+                const double dx = z.x - cD.x, dy = z.y - cD.y;
+                const double r2 = fma(dx, dx, dy * dy);
+                const double2 v = make_double2(dx / r2 * RD, -dy / r2 * RD);
+                const double lg = 0.5 * log_r2(r2, tab, etab);
+                const double2* MD = M + (int64_t)D * P1 * ND;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double2 sm = make_double2(0.0, 0.0);
+#pragma unroll 2
+                    for (int k = P; k >= 1; --k) {
+                        const double2 m = MD[k * ND + d];
+                        sm = cmul64(make_double2(sm.x + m.x, sm.y + m.y), v);
+                    }
+                    acc[d] += fma(MD[d].x, lg, sm.x);
+                }
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) psi[(int64_t)(e0 + i) * ND + d] = acc[d];
+        }
+        __syncwarp();  // the far parts before other lanes add to them
+        // the U-list stream and the split with the fewest lane-steps
+        int S = 0;
+        for (int e = u0; e < u1; ++e) {
+            const int A = t.u_idx[e];
+            S += g.crng[2 * A + 1] - g.crng[2 * A];
+        }
+        if (S == 0) continue;
+        const int full = S >> 5, rem = S & 31;
+        int K = 1;
+        long long best = -1;
+        for (int kk = 1; kk <= 16; kk <<= 1) {
+            const long long steps = (long long)((T * kk + 31) / 32) * (full * (32 / kk) + (rem + kk - 1) / kk);
+            if (best < 0 || steps < best) {
+                best = steps;
+                K = kk;
+            }
+        }
+        const int per = 32 / K;  // points per pass
+        const int a = lane / K, kap = lane % K;
+        for (int p0 = 0; p0 < T; p0 += per) {
+            const int ti = p0 + a;
+            const bool valid = ti < T;
+            const double2 z = valid ? g.exy[e0 + ti] : cb;
+            double near[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) near[d] = 0.0;
+            int ecur = u0, ebase = 0;  // U entry holding stream position c0, and its first position
+            for (int c0 = 0; c0 < S; c0 += 32) {
+                const int n = min(32, S - c0);
+                __syncwarp();
+                if (lane < n) {
+                    int e = ecur, pos = c0 + lane - ebase;
+                    int A = t.u_idx[e];
+                    int a0 = g.crng[2 * A], len = g.crng[2 * A + 1] - a0;
+                    while (pos >= len) {
+                        pos -= len;
+                        A = t.u_idx[++e];
+                        a0 = g.crng[2 * A];
+                        len = g.crng[2 * A + 1] - a0;
+                    }
+                    const int j = a0 + pos;
+                    st.xy[lane] = g.cxy[j];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) st.q[lane][d] = q[(int64_t)j * ND + d];
+                }
+                // move the cursor to the entry holding position c0 + 32
+                for (;;) {
+                    const int A = t.u_idx[ecur];
+                    const int len = g.crng[2 * A + 1] - g.crng[2 * A];
+                    if (ebase + len > c0 + 32 || ecur + 1 >= u1) break;
+                    ebase += len;
+                    ++ecur;
+                }
+                __syncwarp();
+                if (valid) {
+#pragma unroll 4
+                    for (int j = kap; j < n; j += K) {
+                        const double2 sp = st.xy[j];
+                        const double dx = z.x - sp.x, dy = z.y - sp.y;
+                        const double Lg = log_r2(fma(dx, dx, dy * dy), tab, etab);
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) near[d] = fma(st.q[j][d], Lg, near[d]);
+                    }
+                }
+            }
+            for (int off = 1; off < K; off <<= 1) {  // warp-uniform
+#pragma unroll
+                for (int d = 0; d < ND; ++d) near[d] += __shfl_xor_sync(0xffffffffu, near[d], off);
+            }
+            if (valid && kap == 0) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double* o = psi + (int64_t)(e0 + ti) * ND + d;
+                    *o = fma(0.5, near[d], *o);
+                }
             }
         }
     }
@@ -605,34 +766,134 @@ __global__ void __launch_bounds__(kW64 * 32)
 
 // ----------------------------------------------------------------------------
 // a4: M2L over the V list plus P2L over the X list, one warp per target box.
-// The warp takes G V-list entries of its box at a time and walks the G * P
-// items (entry s, coefficient l = 1..P) in R = G P / 32 rounds of 32 lanes, so
-// that every lane of every FP64 instruction works (G = 2 at P = 16, 4 at P = 24,
-// 1 at P = 30, where 30 of 32 lanes do). For an entry with source box C and
-// offset o (t = R/z0 from the offset table):
-//   A_k = M_k (-t)^k                                  (item (s, k), into shared memory)
-//   L_l += t^l (sum_k H[l][k] A_k - M_0 / l)          (item (s, l), accumulated per lane)
-//   Re L_0 += M_0 log|z0| + sum_k Re A_k              (per lane, reduced over the warp)
-// Im L_0 is not needed (L2P takes the real part; it is left zero). Afterwards
-// the entries' partial locals are added through shared memory so that lane l
-// holds L_l, and the X list adds
-//   L_0 += q log|z - c|,  L_l -= (q / l) v^l,  v = R/(z - c).
-template <int P>
-struct M2L64Shape {
+//
+// For a V-list entry with source box C and offset o (t = R/z0 from the offset
+// table) the local coefficients of the target box receive
+//   L_l += t^l Y_l,   Y_l = sum_{k=0..P} H[l][k] A_k,   l = 1..P,
+//   A_k = M_k (-t)^k (k >= 1), A_0 = M_0, H[l][k] = C(l+k-1, k-1), H[l][0] = -1/l,
+//   Re L_0 += M_0 log|z0| + sum_{k>=1} Re A_k.
+// With tau = 2^-1.5 and the scaled operands H'[l][k] = H[l][k] tau^k, A'_k =
+// M_k (-t/tau)^k (so that H' A' = H A term by term), both operands are bounded:
+// |A'_k| <= sum |q| / k because |t| <= 1/4 and the scaled multipole satisfies
+// |M_k| <= sum |q| 2^(k/2) / k, and every H'[l][k] t^l u^l (|u| <= sqrt 2 at an
+// evaluation point) is at most 2^-1.5.
+//
+// The products Y = H' A' run on the tensor cores, exactly: each operand is
+// rounded to 62-bit fixed point (H' per row, A' per column, with a power-of-two
+// scale) and split into eight signed 8-bit digits, x = sum_j d_j 2^(8 (7 - j));
+// a digit is an integer of at most 8 significant bits and so exact in bf16.
+// mma.sync m16n8k16 (bf16 inputs, f32 accumulation) forms for each level n the
+// sum S_n = sum_{i+j=n} Hd_i Ad_j over k: products of two digits are at most
+// 2^14 and |S_n| < 2^22, so every partial sum is an integer below 2^24 and the
+// f32 accumulation is exact. Levels n <= 7 are kept (36 digit products; the rest
+// lie below 2^-62 of the operands' scales per term) and combined in 64-bit
+// integers, Y = sum_n S_n 2^(40 - 8n) (S_6, S_7 rounded down by 8 and 16 bits),
+// converted once to float64 and scaled by a power of two folded into t^l. The
+// result differs from the exact product of the float64 operands by about 2^-55
+// of (row maximum x column maximum), the size of float64 rounding in the same
+// (P + 1)-term sum; with the bounds above that is below 2^-55 * 2^-1.5 * sum |q|
+// in the potential per V-list pair. The float64 work left per pair is A' (one
+// complex multiply per k), the conversions and t^l Y_l: about 11 P operations
+// against 2 P^2 + 10 P for the sum itself.
+//
+// A warp takes G entries at a time (8 tensor columns per n-tile: real and
+// imaginary parts of G entries x ND densities), forms A' (item (entry, k) per
+// lane), the column exponents (shared-memory maximum), the digits of A' into
+// its shared tile, then per 16-row m-tile the 28 digit products of levels 0-6
+// (two k-steps each), and adds t^l Y_l into the lane's rows (fragment row
+// groups) and column pair. The X list (P2L) then adds
+//   L_0 += q log|z - c|,  L_l -= (q / l) v^l,  v = R/(z - c),
+// with lane l owning L_l; 32 sources at a time (lane j forms the powers of v_j).
+constexpr int kSl = 8;   // 8-bit digits per operand
+constexpr int kHs = 40;  // row stride (bf16 elements) of the digit tiles: conflict-free fragment loads
+constexpr size_t kHdBytes = (size_t)kSl * 32 * kHs * sizeof(uint16_t);
+
+template <int P, int ND>
+struct M2LTShape {
     static constexpr int P1 = P + 1;
-    static constexpr int G = P == 16 ? 2 : (P == 24 ? 4 : 1);  // V entries per warp at a time
-    static constexpr int R = (G * P + 31) / 32;                 // rounds of 32 items
+    static constexpr int MT = (P + 15) / 16;           // m-tiles of 16 rows (l = 1..P)
+    static constexpr int NT = ND <= 4 ? 1 : ND / 4;    // n-tiles of 8 columns
+    static constexpr int NCOL = 8 * NT;
+    static constexpr int G = NCOL / (2 * ND);          // V-list entries per group
+    static constexpr int RA = (G * P + 31) / 32;       // rounds of the A' items (entry, k = 1..P)
+    static constexpr int RS = (NCOL * P1 + 31) / 32;   // rounds of the digit items (column, k = 0..P)
+    // per-warp shared memory: A' [G][P1][ND] double2 and the digits [kSl][NCOL][kHs]
+    // bf16 for the V list, the same space for the X list's powers [32][P1] double2;
+    // charges and logs [32][ND + 1] double; column exponents [G ND], entry offsets [G]
+    static constexpr size_t kAs = (size_t)G * P1 * ND * 16;
+    static constexpr size_t kBt = (size_t)kSl * NCOL * kHs * 2;
+    static constexpr size_t kPw = (size_t)32 * P1 * 16;
+    static constexpr size_t kR1 = kAs + kBt > kPw ? kAs + kBt : kPw;
+    static constexpr size_t kQl = (((size_t)32 * (ND + 1) * 8) + 15) & ~(size_t)15;
+    static constexpr size_t kEx = (((size_t)(G * ND + G) * 4) + 15) & ~(size_t)15;
+    static constexpr size_t kWarp = kR1 + kQl + kEx;
 };
 
 template <int P, int ND>
 size_t m2l64_smem()
 {
-    using S = M2L64Shape<P>;
-    // per warp: A [G][P1][ND] double2, then the X list's powers [8][P1] double2 and
-    // charges and logs [8][ND + 1] double (the A space is reused for the partial locals)
-    const size_t a = (size_t)S::G * S::P1 * ND * sizeof(double2);
-    const size_t x = (size_t)8 * S::P1 * sizeof(double2) + (size_t)8 * (ND + 1) * sizeof(double);
-    return (size_t)kW64 * (a + x) + (((size_t)S::P1 * S::P1 * sizeof(double) + 15) & ~(size_t)15);
+    return kHdBytes + 128 + (size_t)kW64 * M2LTShape<P, ND>::kWarp;
+}
+
+// unbiased binary exponent of |x| (a large negative sentinel for zero)
+__device__ __forceinline__ int expo64(double x)
+{
+    const int E = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+    return E == 0 ? -4000 : E - 1023;
+}
+
+// round(x 2^(62 - e)) for |x| < 2^(e - 1), by integer operations on the bits of
+// x: |result| < 2^61 (zero and subnormal x give 0)
+__device__ __forceinline__ long long fixed62(double x, int e)
+{
+    const long long bits = __double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    if (E == 0) return 0;
+    const long long mant = (bits & 0xfffffffffffffLL) | 0x10000000000000LL;
+    const int sh = E - 1075 + 62 - e;  // x 2^(62 - e) = mant 2^sh, sh <= 8
+    long long X;
+    if (sh >= 0)
+        X = mant << sh;
+    else if (sh < -62)
+        X = 0;
+    else
+        X = (mant + (1LL << (-sh - 1))) >> (-sh);
+    return bits < 0 ? -X : X;
+}
+
+// bf16 bit pattern of an integer |d| <= 2^8 (exact): through the f32 value
+// 1.5 2^23 + d, whose unit in the last place is 1
+__device__ __forceinline__ uint16_t bf16_digit(int d)
+{
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return (uint16_t)(__float_as_uint(f) >> 16);
+}
+
+// integer value of an f32 holding an integer |v| < 2^22 (same device as above)
+__device__ __forceinline__ long long int_of_f32(float v)
+{
+    return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+}
+
+// v 2^sc by the exponent field (0 below the normal range)
+__device__ __forceinline__ double scale_pow2(double v, int sc)
+{
+    const long long bits = __double_as_longlong(v);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    const int En = E + sc;
+    if (E == 0 || En <= 0) return 0.0;
+    if (En >= 2047) return ldexp(v, sc);
+    return __longlong_as_double(bits + (long long)sc * (1LL << 52));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 template <int P, int ND>
@@ -640,118 +901,205 @@ __global__ void __launch_bounds__(kW64 * 32)
     k_m2l64(DevTree t, DevTables tab, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
             const double* __restrict__ q, const double2* __restrict__ logtab, const double* __restrict__ etab)
 {
-    using S = M2L64Shape<P>;
-    constexpr int P1 = S::P1, G = S::G, R = S::R;
+    using S = M2LTShape<P, ND>;
+    constexpr int P1 = S::P1, MT = S::MT, NT = S::NT, NCOL = S::NCOL, G = S::G, RA = S::RA, RS = S::RS;
     extern __shared__ __align__(16) unsigned char smem_m2l[];
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    constexpr size_t kA = (size_t)G * P1 * ND;                 // double2 per warp
-    constexpr size_t kPw = (size_t)8 * P1;                      // double2 per warp
-    double* Ht = reinterpret_cast<double*>(smem_m2l);           // Ht[k][l] = H[l][k]
-    double2* wbase = reinterpret_cast<double2*>(smem_m2l + ((P1 * P1 * sizeof(double) + 15) & ~(size_t)15)) +
-                     (size_t)wb * (kA + kPw + (8 * (ND + 1) + 1) / 2);
-    double2* As = wbase;                                        // [G][P1][ND]
-    double2* pws = wbase + kA;                                  // [8][P1]
-    double* qls = reinterpret_cast<double*>(pws + kPw);         // [8][ND + 1]
-    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) Ht[(i % P1) * P1 + i / P1] = tab.H[i];
+    const int gq = lane >> 2, tq = lane & 3;  // fragment row group, column pair
+    uint16_t* Hd = reinterpret_cast<uint16_t*>(smem_m2l);           // [kSl][32][kHs]
+    int* eHs = reinterpret_cast<int*>(smem_m2l + kHdBytes);         // [32]
+    unsigned char* wbase = smem_m2l + kHdBytes + 128 + (size_t)wb * S::kWarp;
+    double2* As = reinterpret_cast<double2*>(wbase);                // [G][P1][ND]
+    uint16_t* Bt = reinterpret_cast<uint16_t*>(wbase + S::kAs);     // [kSl][NCOL][kHs]
+    double2* pws = reinterpret_cast<double2*>(wbase);                               // [32][P1] (X list)
+    double* qls = reinterpret_cast<double*>(wbase + S::kR1);                         // [32][ND + 1]
+    int* em = reinterpret_cast<int*>(wbase + S::kR1 + S::kQl);                       // [G ND]
+    int* eo = em + G * ND;                                                                // [G]
+    for (int i = threadIdx.x; i < (int)(kHdBytes / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t*>(Hd)[i] = tab.m2lh[i];
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) eHs[i] = tab.m2le[i];
+    for (int i = lane; i < (int)(S::kBt / 4); i += 32) reinterpret_cast<uint32_t*>(Bt)[i] = 0u;  // k padding stays 0
     __syncthreads();
 
-    // the items of this lane in each round: entry slot and coefficient (1..P), or idle
-    int it_s[R], it_l[R];
-    double inv_l[R];
+    // this lane's A' items: entry slot and coefficient k = 1..P per round, and tau^k
+    int it_s[RA], it_k[RA];
+    double tauk[RA];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < RA; ++r) {
         const int f = r * 32 + lane;
         const bool on = f < G * P;
         it_s[r] = on ? f / P : -1;
-        it_l[r] = on ? f % P + 1 : P;  // idle lanes repeat row P (result unused)
-        inv_l[r] = 1.0 / (double)it_l[r];
+        it_k[r] = on ? f % P + 1 : 1;
+        tauk[r] = tab.tau_pow[it_k[r]];
     }
 
     for (int b = gwarp(); b < t.nbox; b += nwarps()) {
-        double2 lacc[R][ND];
+        double2 lacc[2 * MT][NT];
+#pragma unroll
+        for (int i = 0; i < 2 * MT; ++i)
+#pragma unroll
+            for (int n = 0; n < NT; ++n) lacc[i][n] = make_double2(0.0, 0.0);
         double l0d[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) l0d[d] = 0.0;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int d = 0; d < ND; ++d) lacc[r][d] = make_double2(0.0, 0.0);
         const int v0 = t.v_ptr[b], v1 = t.v_ptr[b + 1];
         const int bx = t.ixy[2 * b], by = t.ixy[2 * b + 1];
         const double logR = t.log_radius[b];
         for (int e0 = v0; e0 < v1; e0 += G) {
             __syncwarp();
-            // A_k of the G entries (item (s, k) per lane and round); Re A_k and
-            // M_0 log|z0| go into this lane's share of Re L_0
+            if (lane < G * ND) em[lane] = -4000;
+            if (lane < G) eo[lane] = -1;
+            __syncwarp();
+            // A'_k of the G entries (item (s, k) per lane and round), the column
+            // exponents, and this lane's share of Re L_0
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int s = it_s[r], k = it_l[r];
-                if (s < 0) continue;
+            for (int r = 0; r < RA; ++r) {
+                const int s = it_s[r], k = it_k[r];
+                int exd[ND];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) exd[d] = -4000;
                 const int e = e0 + s;
-                if (e < v1) {
+                if (s >= 0 && e < v1) {
                     const int C = t.v_idx[e];
                     const int o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
-                    const double2 mt = tab.mtpow[o * P1 + k];
+                    const double2 mt = tab.mtpow_s[o * P1 + k];
                     const double2* MC = M + (int64_t)C * P1 * ND;
+                    if (k == 1) eo[s] = o;
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
                         const double2 a = cmul64(MC[k * ND + d], mt);
                         As[(s * P1 + k) * ND + d] = a;
-                        l0d[d] += a.x;
+                        l0d[d] = fma(a.x, tauk[r], l0d[d]);
+                        exd[d] = max(expo64(a.x), expo64(a.y));
                         if (k == 1) {
-                            As[(s * P1) * ND + d] = MC[d];  // M_0 of the entry
-                            l0d[d] = fma(MC[d].x, logR + tab.log2o[o], l0d[d]);
+                            const double2 m0 = MC[d];
+                            As[(s * P1) * ND + d] = m0;
+                            l0d[d] = fma(m0.x, logR + tab.log2o[o], l0d[d]);
+                            exd[d] = max(exd[d], max(expo64(m0.x), expo64(m0.y)));
                         }
                     }
-                } else {
+                } else if (s >= 0) {
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
                         As[(s * P1 + k) * ND + d] = make_double2(0.0, 0.0);
                         if (k == 1) As[(s * P1) * ND + d] = make_double2(0.0, 0.0);
                     }
                 }
-            }
-            __syncwarp();
-            // L_l of item (s, l): t^l (sum_k H[l][k] A_k - M_0 / l)
+                // maximum over the lanes of one entry (consecutive lanes of the round):
+                // a segmented reduction downwards, the segment's first lane publishes
+                bool same[5];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int s = it_s[r] < 0 ? 0 : it_s[r], l = it_l[r];
-                const int e = e0 + s;
-                const bool live = it_s[r] >= 0 && e < v1;
-                double2 acc[ND];
-#pragma unroll
-                for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
-                const double2* Aw = As + (size_t)s * P1 * ND;
-#pragma unroll 4
-                for (int k = 1; k <= P; ++k) {
-                    const double h = Ht[k * P1 + l];
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        const double2 a = Aw[k * ND + d];
-                        acc[d].x = fma(h, a.x, acc[d].x);
-                        acc[d].y = fma(h, a.y, acc[d].y);
-                    }
+                for (int i = 0; i < 5; ++i) {
+                    const int s2 = __shfl_down_sync(0xffffffffu, s, 1 << i);
+                    same[i] = lane + (1 << i) < 32 && s2 == s;
                 }
-                int o = 0;
-                if (live) {
-                    const int C = t.v_idx[e];
-                    o = (t.ixy[2 * C + 1] - by + 3) * 7 + (t.ixy[2 * C] - bx + 3);
-                }
-                const double2 tl = tab.tpow[o * P1 + l];
+                const int sp = __shfl_up_sync(0xffffffffu, s, 1);
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    const double2 a = make_double2(fma(-Aw[d].x, inv_l[r], acc[d].x), acc[d].y);
-                    if (live) lacc[r][d] = cfma64(tl, a, lacc[r][d]);
+                    int m = exd[d];
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const int v = __shfl_down_sync(0xffffffffu, m, 1 << i);
+                        if (same[i]) m = max(m, v);
+                    }
+                    if (s >= 0 && (lane == 0 || sp != s)) atomicMax(&em[s * ND + d], m);
+                }
+            }
+            __syncwarp();
+            // digits of A': item (column c, k), column c = (s ND + d) 2 + (0: real, 1: imaginary)
+#pragma unroll
+            for (int r = 0; r < RS; ++r) {
+                const int f = r * 32 + lane;
+                if (f >= NCOL * P1) continue;
+                const int c = f / P1, k = f % P1, sd = c >> 1;
+                const double2 a = As[((sd / ND) * P1 + k) * ND + sd % ND];
+                long long X = fixed62((c & 1) ? a.y : a.x, em[sd] + 2);
+                uint16_t* dst = Bt + (size_t)c * kHs + k;
+#pragma unroll
+                for (int j = kSl - 1; j >= 1; --j) {
+                    const int dj = (int)(signed char)(X & 0xff);
+                    dst[(size_t)j * NCOL * kHs] = bf16_digit(dj);
+                    X = (X - dj) >> 8;
+                }
+                dst[0] = bf16_digit((int)X);
+            }
+            __syncwarp();
+            // Y = H' A' on the tensor cores, level by level, then L_l += t^l Y_l
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                uint32_t bfr[kSl][2][2];
+#pragma unroll
+                for (int j = 0; j < kSl; ++j)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint16_t* col = Bt + ((size_t)j * NCOL + 8 * nt + gq) * kHs + 16 * ks + 2 * tq;
+                        bfr[j][ks][0] = *reinterpret_cast<const uint32_t*>(col);
+                        bfr[j][ks][1] = *reinterpret_cast<const uint32_t*>(col + 8);
+                    }
+                const int sd = 4 * nt + tq;  // this lane's column pair
+                const int o = eo[sd / ND];
+                const int eA = em[sd] + 2;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    float acc[kSl][4];
+#pragma unroll
+                    for (int n = 0; n < kSl; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                        for (int i = 0; i < kSl; ++i) {
+                            const uint16_t* hr = Hd + ((size_t)i * 32 + 16 * mt + gq) * kHs + 16 * ks + 2 * tq;
+                            const uint32_t a0 = *reinterpret_cast<const uint32_t*>(hr);
+                            const uint32_t a1 = *reinterpret_cast<const uint32_t*>(hr + 8 * kHs);
+                            const uint32_t a2 = *reinterpret_cast<const uint32_t*>(hr + 8);
+                            const uint32_t a3 = *reinterpret_cast<const uint32_t*>(hr + 8 * kHs + 8);
+#pragma unroll
+                            for (int j = 0; j + i < kSl; ++j)
+                                mma_bf16_16816(acc[i + j], a0, a1, a2, a3, bfr[j][ks][0], bfr[j][ks][1]);
+                        }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int row = 16 * mt + 8 * h + gq, l = row + 1;
+                        if (l > P || o < 0) continue;
+                        long long yr = 0, yi = 0;
+#pragma unroll
+#pragma unroll
+                        for (int n = 0; n < 6; ++n) {
+                            yr += int_of_f32(acc[n][2 * h]) * (1LL << (40 - 8 * n));
+                            yi += int_of_f32(acc[n][2 * h + 1]) * (1LL << (40 - 8 * n));
+                        }
+                        yr += (int_of_f32(acc[6][2 * h]) >> 8) + (int_of_f32(acc[7][2 * h]) >> 16);
+                        yi += (int_of_f32(acc[6][2 * h + 1]) >> 8) + (int_of_f32(acc[7][2 * h + 1]) >> 16);
+                        const int sc = eHs[row] + eA - 52;
+                        const double2 tl = tab.tpow[o * P1 + l];
+                        const double2 ts = make_double2(scale_pow2(tl.x, sc), scale_pow2(tl.y, sc));
+                        lacc[2 * mt + h][nt] = cfma64(ts, make_double2((double)yr, (double)yi), lacc[2 * mt + h][nt]);
+                    }
                 }
             }
         }
-        // add the entries' partial locals: item (s, l) -> shared [s][l], then lane l sums over s
+        // the column pairs of one density are summed over the lanes that hold
+        // them (tq with the same (4 nt + tq) mod ND), then lane l takes L_l
+#pragma unroll
+        for (int i = 0; i < 2 * MT; ++i)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int off = ND; off < 4; off <<= 1) {
+                    lacc[i][n].x += __shfl_xor_sync(0xffffffffu, lacc[i][n].x, off);
+                    lacc[i][n].y += __shfl_xor_sync(0xffffffffu, lacc[i][n].y, off);
+                }
         __syncwarp();
+        if (tq < ND) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (it_s[r] < 0) continue;
+            for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-            for (int d = 0; d < ND; ++d) As[(it_s[r] * P1 + it_l[r]) * ND + d] = lacc[r][d];
+                for (int h = 0; h < 2; ++h) {
+                    const int l = 16 * mt + 8 * h + gq + 1;
+                    if (l > P) continue;
+#pragma unroll
+                    for (int n = 0; n < NT; ++n) As[l * ND + (4 * n + tq) % ND] = lacc[2 * mt + h][n];
+                }
         }
         __syncwarp();
         double2 lo[ND];
@@ -760,15 +1108,10 @@ __global__ void __launch_bounds__(kW64 * 32)
             double s0 = l0d[d];
             for (int off = 16; off > 0; off >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, off);
             lo[d] = make_double2(0.0, 0.0);
-            if (lane == 0) {
+            if (lane == 0)
                 lo[d].x = s0;
-            } else if (lane <= P) {
-                for (int s = 0; s < G; ++s) {
-                    const double2 v = As[(s * P1 + lane) * ND + d];
-                    lo[d].x += v.x;
-                    lo[d].y += v.y;
-                }
-            }
+            else if (lane <= P)
+                lo[d] = As[lane * ND + d];
         }
         // X list (P2L), lane l <= P owns L_l
         const int x0 = t.x_ptr[b], x1 = t.x_ptr[b + 1];
@@ -779,8 +1122,8 @@ __global__ void __launch_bounds__(kW64 * 32)
             for (int e = x0; e < x1; ++e) {
                 const int Cx = t.x_idx[e];
                 const int s0 = g.crng[2 * Cx], s1 = g.crng[2 * Cx + 1];
-                for (int base = s0; base < s1; base += 8) {
-                    const int n = min(8, s1 - base);
+                for (int base = s0; base < s1; base += 32) {
+                    const int n = min(32, s1 - base);
                     __syncwarp();
                     if (lane < n) {
                         const double2 z = g.cxy[base + lane];
@@ -818,6 +1161,10 @@ __global__ void __launch_bounds__(kW64 * 32)
                     }
                 }
             }
+            // the powers shared the digit tile's space: zero its k padding again
+            __syncwarp();
+            for (int i = lane; i < kSl * NCOL * (32 - P1); i += 32)
+                Bt[(i / (32 - P1)) * kHs + P1 + i % (32 - P1)] = 0;
         }
         if (lane <= P) {
 #pragma unroll
@@ -931,12 +1278,12 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_leaf64<P, ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_leaf64<P, ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
+            e = cudaFuncSetAttribute(k_leaf64d<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
         if (e != cudaSuccess) return e;
         for (int si = 0; si < 2; ++si) {
             int nb = 0;
             e = si ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64<P, ND, true>, kLeafWarps64 * 32, leaf_smem<ND>())
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64<P, ND, false>, kLeafWarps64 * 32, leaf_smem<ND>());
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64d<P, ND>, kLeafWarps64 * 32, leaf_smem<ND>());
             if (e != cudaSuccess) return e;
             leaf_resident[si] = std::max(1, nb);
         }
@@ -978,8 +1325,8 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         const int rblocks = std::max(1, std::min((g.n_eval + 255) / 256, 152 * 32));
         k_sym_reduce64<ND><<<rblocks, 256, 0, s>>>(t, g, slots, ws.psi);
     } else {
-        k_leaf64<P, ND, false><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
-                                                                                  tab.elog64, ws.psi, ws.work, nullptr);
+        k_leaf64d<P, ND><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
+                                                                            tab.elog64, ws.psi, ws.work);
     }
     if (tm) tm->end(id);
     return cudaGetLastError();
@@ -1038,6 +1385,79 @@ std::vector<double2> make_m2m64_table(int P)
         }
     }
     return tab;
+}
+
+// Tables of the tensor-core M2L of order P (see k_m2l64), tau = 2^-1.5:
+//   hd [8][32][40] bf16 digits of H'[l][k] (row l - 1, column k = 0..P; zero
+//      padding), H'[l][0] = -1/l, H'[l][k] = C(l+k-1, k-1) tau^k;
+//   eh [32] row exponents e with |H'[l][k]| < 2^(e - 1), H' ~ X 2^(e - 62);
+//   mts [49][P1] (-t_o / tau)^k, t_o = 1/(2 (ox + i oy)) (zero for near offsets);
+//   taup [P1] tau^k.
+// Computed in long double; the digits are the balanced base-256 digits of the
+// 62-bit fixed-point value, most significant first.
+static uint64_t binom_u64_host(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;  // exact at every step
+    return r;
+}
+
+void make_m2l_tensor_tables(int P, std::vector<uint16_t>& hd, std::vector<int32_t>& eh, std::vector<double2>& mts,
+                            std::vector<double>& taup)
+{
+    const int P1 = P + 1;
+    const long double tau = 0.353553390593273762200422181052424519642L;  // 2^-1.5
+    std::vector<long double> tp((size_t)P1);
+    tp[0] = 1.0L;
+    for (int k = 1; k <= P; ++k) tp[(size_t)k] = tp[(size_t)k - 1] * tau;
+    taup.assign((size_t)P1, 0.0);
+    for (int k = 0; k <= P; ++k) taup[(size_t)k] = (double)tp[(size_t)k];
+    hd.assign((size_t)kSl * 32 * kHs, 0);
+    eh.assign(32, 0);
+    auto bf16_bits = [](int d) -> uint16_t {  // exact: |d| <= 256
+        const float f = (float)d;
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return (uint16_t)(u >> 16);
+    };
+    for (int l = 1; l <= P; ++l) {
+        std::vector<long double> row((size_t)P1);
+        long double mx = 0.0L;
+        for (int k = 0; k <= P; ++k) {
+            row[(size_t)k] = k == 0 ? -1.0L / (long double)l : (long double)binom_u64_host(l + k - 1, k - 1) * tp[(size_t)k];
+            mx = std::max(mx, std::fabs(row[(size_t)k]));
+        }
+        const int e = std::ilogb(mx) + 2;
+        eh[(size_t)l - 1] = e;
+        for (int k = 0; k <= P; ++k) {
+            long long X = std::llround(std::ldexp(row[(size_t)k], 62 - e));
+            int dg[kSl];
+            for (int j = kSl - 1; j >= 1; --j) {
+                const int dj = (int)(signed char)(X & 0xff);
+                dg[j] = dj;
+                X = (X - dj) / 256;
+            }
+            dg[0] = (int)X;
+            for (int j = 0; j < kSl; ++j) hd[((size_t)j * 32 + (l - 1)) * kHs + k] = bf16_bits(dg[j]);
+        }
+    }
+    mts.assign((size_t)49 * P1, make_double2(0.0, 0.0));
+    for (int oy = -3; oy <= 3; ++oy)
+        for (int ox = -3; ox <= 3; ++ox) {
+            if (std::max(std::abs(ox), std::abs(oy)) < 2) continue;
+            const long double den = 2.0L * (long double)(ox * ox + oy * oy);
+            // -t / tau, t = (ox - i oy) / den
+            const long double ur = -(long double)ox / den / tau, ui = (long double)oy / den / tau;
+            long double pr = 1.0L, pi = 0.0L;
+            const int o = (oy + 3) * 7 + (ox + 3);
+            for (int k = 0; k <= P; ++k) {
+                mts[(size_t)o * P1 + k] = make_double2((double)pr, (double)pi);
+                const long double nr = pr * ur - pi * ui, ni = pr * ui + pi * ur;
+                pr = nr;
+                pi = ni;
+            }
+        }
 }
 
 // L2L table of order P: l2l[c][l][k] = C(k, l) 2^-l zeta_c^(k-l) for k >= l (exact in

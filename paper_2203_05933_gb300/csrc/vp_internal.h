@@ -87,6 +87,10 @@ struct DevTables {
     const double* elog64 = nullptr; // [128] (i - 64) log 2                            (FP64 log)
     const double2* m2m64 = nullptr; // [4][P1][P1] M2M coefficients per child quadrant   (float64 M2M)
     const double2* l2l64 = nullptr; // [4][P1][P1] L2L coefficients per child quadrant   (float64 L2L)
+    const uint32_t* m2lh = nullptr; // [8][32][40] bf16 digits of the scaled M2L matrix, as 32-bit words
+    const int32_t* m2le = nullptr;  // [32] row exponents of those digits
+    const double2* mtpow_s = nullptr; // [49][P1] (-t_o / tau)^k, tau = 2^-1.5            (float64 M2L)
+    const double* tau_pow = nullptr;  // [P1] tau^k
     // float-float copies for the FP32-pipe M2L
     const float2* Hf = nullptr;     // [P1][P1]
     const float4* tpowf = nullptr;  // [49][P1] complex (re_h, re_l, im_h, im_l)
@@ -210,6 +214,8 @@ cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, 
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);
 std::vector<double2> make_m2m64_table(int P);
 std::vector<double2> make_l2l64_table(int P);
+void make_m2l_tensor_tables(int P, std::vector<uint16_t>& hd, std::vector<int32_t>& eh, std::vector<double2>& mts,
+                            std::vector<double>& taup);
 // Device-side construction of the grouped correction (vp_csr.cu). err: device int,
 // bit 1 = column out of range, bit 2 = non-finite value. same[i] = row i repeats row i - 1.
 cudaError_t launch_csr_check(int64_t nnz, const int32_t* col, const double* val, int64_t ncols, int* err,
