@@ -333,6 +333,9 @@ struct vp_plan_s {
     // points and weights in tree order
     double2* src_xy = nullptr;
     double2* tgt_xy = nullptr;
+    longlong2* src_fix = nullptr;  // the same points on the integer grid 2^-fix_sigma
+    longlong2* tgt_fix = nullptr;
+    int fix_sigma = 60;
     float4* src_rho = nullptr;
     float4* tgt_rho = nullptr;
     double* w_sorted = nullptr;
@@ -427,6 +430,33 @@ int chunk_for(int remaining, int cap)
     return nd;
 }
 
+// Integer coordinates of points on the grid 2^-sigma: x 2^sigma is exact in
+// float64 (a power of two), rounded to the nearest integer (exact unless
+// |x| < 2^(61 - sigma - 53)).
+__global__ void k_fix_coords(int64_t n, const double* __restrict__ xy, double scale, long long* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2ll_rn(xy[i] * scale);
+}
+
+// sigma with max |coordinate| 2^sigma < 2^61, so that differences stay below 2^62
+int fix_sigma(const std::vector<double>& a, const std::vector<double>& b)
+{
+    double mx = 0.0;
+    for (double v : a) mx = std::max(mx, std::fabs(v));
+    for (double v : b) mx = std::max(mx, std::fabs(v));
+    return mx > 0.0 ? 60 - std::ilogb(mx) : 60;
+}
+
+// (E - 2 sigma) log 2, E = 0..127, in long double
+std::vector<double> make_elogfix(int sigma)
+{
+    std::vector<double> t(128);
+    const long double ln2 = 0.693147180559945309417232121458176568L;
+    for (int E = 0; E < 128; ++E) t[(size_t)E] = (double)((long double)(E - 2 * sigma) * ln2);
+    return t;
+}
+
 PassGeom forward_geom(vp_plan p)
 {
     PassGeom g;
@@ -438,6 +468,8 @@ PassGeom forward_geom(vp_plan p)
     g.erng = p->box_tgt;
     g.erho = p->tgt_rho;
     g.n_eval = (int32_t)p->n_tgt;
+    g.cfix = p->src_fix;
+    g.efix = p->tgt_fix;
     return g;
 }
 
@@ -452,6 +484,8 @@ PassGeom adjoint_geom(vp_plan p)
     g.erng = p->box_src;
     g.erho = p->src_rho;
     g.n_eval = (int32_t)p->n_src;
+    g.cfix = p->tgt_fix;
+    g.efix = p->src_fix;
     return g;
 }
 
@@ -978,6 +1012,22 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_xy_t, B.txy);
     p->src_xy = (double2*)d_xy_s;
     p->tgt_xy = (double2*)d_xy_t;
+    p->fix_sigma = fix_sigma(B.sxy, B.txy);
+    {
+        long long *fs = nullptr, *ft = nullptr;
+        if (e == cudaSuccess) e = p->alloc(&fs, B.sxy.size());
+        if (e == cudaSuccess) e = p->alloc(&ft, B.txy.size());
+        const double scale = std::ldexp(1.0, p->fix_sigma);
+        if (e == cudaSuccess && !B.sxy.empty())
+            k_fix_coords<<<(int)std::min<size_t>((B.sxy.size() + 255) / 256, 4096), 256, 0, s>>>(
+                (int64_t)B.sxy.size(), d_xy_s, scale, fs);
+        if (e == cudaSuccess && !B.txy.empty())
+            k_fix_coords<<<(int)std::min<size_t>((B.txy.size() + 255) / 256, 4096), 256, 0, s>>>(
+                (int64_t)B.txy.size(), d_xy_t, scale, ft);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        p->src_fix = (longlong2*)fs;
+        p->tgt_fix = (longlong2*)ft;
+    }
     up(&p->w_sorted, B.ws);
     up(&p->src_perm, B.src_perm);
     up(&p->tgt_perm, B.tgt_perm);
@@ -1159,6 +1209,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_m2le, m2le);
     up(&d_mtpow_s, mtpow_s);
     up(&d_tau_pow, tau_pow);
+    double* d_elogfix = nullptr;
+    up(&d_elogfix, make_elogfix(p->fix_sigma));
     up(&d_fftab, fftab);
     up(&d_srho, B.srho);
     up(&d_trho, B.trho);
@@ -1261,6 +1313,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.m2le = d_m2le;
     tb.mtpow_s = d_mtpow_s;
     tb.tau_pow = d_tau_pow;
+    tb.elogfix = d_elogfix;
     tb.Hf = (const float2*)(d_fftab + offf[0]);
     tb.tpowf = (const float4*)(d_fftab + offf[1]);
     tb.mtpowf = (const float4*)(d_fftab + offf[2]);
@@ -1271,7 +1324,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
                            p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
-                           tb.log64, p->gfwd.vd, tb.m2lh, tb.mtpow_s};
+                           tb.log64, p->gfwd.vd, tb.m2lh, tb.mtpow_s, p->src_fix, p->tgt_fix};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf, p->gfwd.vf};
     bool ok = true;
     for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);

@@ -85,6 +85,53 @@ __device__ __forceinline__ double log_r2(double r2, const double2* __restrict__ 
     return L;
 }
 
+// log(r^2) of two points given as integers on the grid 2^-sigma (dx, dy below
+// 2^62 in magnitude). r^2 2^(2 sigma) = dx^2 + dy^2 is formed exactly in 128-bit
+// integers and rounded to 53 bits, m 2^(n - 52) with m in [2^52, 2^53); rounding
+// m to the nearest table point c_k = 1 + k 2^-12 gives E = n or n + 1 and
+// y = r^2 2^(2 sigma - E) in [1 - 2^-13, 2), built from the bits; then, as in
+// log_r2, log r^2 = (E - 2 sigma) log 2 + T_k + log1p(u), u = y s_k - 1, with
+// elog[E] = (E - 2 sigma) log 2. Five FP64 operations; the square and its
+// normalisation run on the integer pipes. r^2 = 0 (coincident points) gives 0.
+__device__ __forceinline__ double log_r2_fix(long long dx, long long dy, const double2* __restrict__ tab,
+                                             const double* __restrict__ elog)
+{
+    const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
+    const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
+    const unsigned long long l1 = ax * ax, l2 = ay * ay;
+    unsigned long long lo = l1 + l2;
+    unsigned long long hi = __umul64hi(ax, ax) + __umul64hi(ay, ay) + (lo < l1 ? 1ULL : 0ULL);
+    if ((hi | lo) == 0ULL) return 0.0;
+    int n = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
+    const int sh = n - 52;
+    unsigned long long m;
+    int rb = 0;  // the first bit below the 53 kept
+    if (sh <= 0) {
+        m = lo << (-sh);
+    } else if (sh < 64) {
+        m = (lo >> sh) | (sh == 0 ? 0ULL : hi << (64 - sh));
+        rb = (int)((lo >> (sh - 1)) & 1ULL);
+    } else {
+        m = hi >> (sh - 64);
+        rb = (int)(sh == 64 ? (lo >> 63) : ((hi >> (sh - 65)) & 1ULL));
+    }
+    m += (unsigned long long)rb;
+    if (m >> 53) {  // rounded up to 2^53
+        m >>= 1;
+        ++n;
+    }
+    const unsigned long long h = m + (1ULL << (51 - kLog64Bits));  // to the nearest table point
+    const int carry = (int)(h >> 53);
+    const int E = n + carry;
+    const int k = (int)((h >> (52 - kLog64Bits)) & ((1ULL << kLog64Bits) - 1));
+    const double y = __longlong_as_double(
+        (long long)(((unsigned long long)(1023 - carry) << 52) | (m & 0xfffffffffffffULL)));
+    const double2 sk = tab[k];
+    const double u = fma(y, sk.x, -1.0);
+    const double b = fma(u, fma(u, 0x1.5555555555555p-2, -0.5), 1.0);  // 1 - u/2 + u^2/3
+    return fma(u, b, elog[E] + sk.y);
+}
+
 // ----------------------------------------------------------------------------
 // a5 + a6: near field, L2P and W-list M2P of one leaf per warp (persistent
 // warps pull leaves from a queue, costliest first). Lane i holds one
@@ -100,6 +147,12 @@ __device__ __forceinline__ double log_r2(double r2, const double2* __restrict__ 
 template <int ND>
 struct LeafStage64 {
     double2 xy[32];
+    double q[32][ND];
+};
+
+template <int ND>
+struct LeafStageFix {
+    longlong2 xy[32];  // integer coordinates (PassGeom::cfix)
     double q[32][ND];
 };
 
@@ -276,24 +329,29 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
 // takes point a of the pass and chunk positions kap, kap + K, ...), in
 // ceil(T K / 32) passes over the stream, K in {1, 2, 4, 8, 16} chosen per leaf
 // for the fewest lane-steps (every lane of an FP64 instruction costs an issue
-// slot, busy or not). The K partial sums of a point are added by shuffles and
-// psi += near / 2 (the log is of r^2).
+// slot, busy or not). The pairs take the points' integer coordinates and
+// log_r2_fix (six FP64 operations a pair with the accumulation). The K partial
+// sums of a point are added by shuffles and psi += near / 2 (the log is of r^2).
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafWarps64 * 32)
     k_leaf64d(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
               const double2* __restrict__ L, const double2* __restrict__ logtab, const double* __restrict__ etab_g,
-              double* __restrict__ psi, int* __restrict__ work)
+              const double* __restrict__ elogfix_g, double* __restrict__ psi, int* __restrict__ work)
 {
     constexpr int P1 = P + 1;
     extern __shared__ __align__(16) unsigned char smem64d[];
     double2* tab = reinterpret_cast<double2*>(smem64d);                      // [1 << kLog64Bits]
     double* etab = reinterpret_cast<double*>(tab + (1 << kLog64Bits));       // [2 * kEBias]
-    LeafStage64<ND>* stage = reinterpret_cast<LeafStage64<ND>*>(etab + 2 * kEBias);
+    double* elogfix = etab + 2 * kEBias;                                     // [128]
+    LeafStageFix<ND>* stage = reinterpret_cast<LeafStageFix<ND>*>(elogfix + 2 * kEBias);
     for (int i = threadIdx.x; i < (1 << kLog64Bits); i += blockDim.x) tab[i] = logtab[i];
-    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) etab[i] = etab_g[i];
+    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) {
+        etab[i] = etab_g[i];
+        elogfix[i] = elogfix_g[i];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    LeafStage64<ND>& st = stage[threadIdx.x >> 5];
+    LeafStageFix<ND>& st = stage[threadIdx.x >> 5];
 
     for (;;) {
         int li = 0;
@@ -368,7 +426,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
         for (int p0 = 0; p0 < T; p0 += per) {
             const int ti = p0 + a;
             const bool valid = ti < T;
-            const double2 z = valid ? g.exy[e0 + ti] : cb;
+            const longlong2 z = valid ? g.efix[e0 + ti] : make_longlong2(0, 0);
             double near[ND];
 #pragma unroll
             for (int d = 0; d < ND; ++d) near[d] = 0.0;
@@ -387,7 +445,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                         len = g.crng[2 * A + 1] - a0;
                     }
                     const int j = a0 + pos;
-                    st.xy[lane] = g.cxy[j];
+                    st.xy[lane] = g.cfix[j];
 #pragma unroll
                     for (int d = 0; d < ND; ++d) st.q[lane][d] = q[(int64_t)j * ND + d];
                 }
@@ -403,9 +461,8 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                 if (valid) {
 #pragma unroll 4
                     for (int j = kap; j < n; j += K) {
-                        const double2 sp = st.xy[j];
-                        const double dx = z.x - sp.x, dy = z.y - sp.y;
-                        const double Lg = log_r2(fma(dx, dx, dy * dy), tab, etab);
+                        const longlong2 sp = st.xy[j];
+                        const double Lg = log_r2_fix(z.x - sp.x, z.y - sp.y, tab, elogfix);
 #pragma unroll
                         for (int d = 0; d < ND; ++d) near[d] = fma(st.q[j][d], Lg, near[d]);
                     }
@@ -1258,7 +1315,7 @@ size_t p2m_smem()
 template <int ND>
 size_t leaf_smem()
 {
-    return (size_t)(1 << kLog64Bits) * sizeof(double2) + 2 * kEBias * sizeof(double) +
+    return (size_t)(1 << kLog64Bits) * sizeof(double2) + 4 * kEBias * sizeof(double) +
            (size_t)kLeafWarps64 * sizeof(LeafStage64<ND>);
 }
 
@@ -1326,7 +1383,7 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         k_sym_reduce64<ND><<<rblocks, 256, 0, s>>>(t, g, slots, ws.psi);
     } else {
         k_leaf64d<P, ND><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
-                                                                            tab.elog64, ws.psi, ws.work);
+                                                                            tab.elog64, tab.elogfix, ws.psi, ws.work);
     }
     if (tm) tm->end(id);
     return cudaGetLastError();

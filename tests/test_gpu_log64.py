@@ -1,16 +1,16 @@
 """The float64 near field's own logarithm, measured through the public API.
 
 One source at the origin with unit weight and density and targets on the x axis
-(dy = 0, so r^2 = RN(dx^2) is formed identically on both sides): with a single
-leaf every pair is summed directly, the local expansion is zero, and
-out_i = -(1/2pi) * (1/2) log(r_i^2) up to the final multiplication, which both
-sides round the same way. So |out - ref| measures the logarithm's own error.
-The table-driven method (Tang 1990: table spacing 2^-12, cubic log1p, e log 2
-and the table logarithm added in float64) has absolute error below
+at multiples of 2^-50 (so that their coordinates are exact on the integer grid
+the directed near field uses, and r^2 = dx^2 is formed exactly there, then
+rounded once to 53 bits): with a single leaf every pair is summed directly, the
+local expansion is zero, and out_i = -(1/2pi) * (1/2) log(r_i^2) up to the
+final multiplication. So |out - ref| measures the logarithm's own error. The
+table-driven method (Tang 1990: table spacing 2^-12, cubic log1p, e log 2 and
+the table logarithm added in float64) has absolute error below
 2^-52 max(1, |e| log 2) plus half an ulp of the result (e the binary exponent
-of r^2): about one ulp of log r^2 where |log r^2| >= 1, an absolute 2^-52 near
-r^2 = 1. Distances below 2^-32 and above 2^31.5 take CUDA's log (outside the
-table's exponent range); they are covered too, as is the coincident pair.
+of r^2), plus 2^-53 for the rounding of r^2 (the reference rounds r^2 too):
+about one ulp of log r^2 where |log r^2| >= 1. The coincident pair gives 0.
 """
 
 import numpy as np
@@ -32,13 +32,14 @@ def _built():
 
 def test_log64_within_three_ulp():
     rng = np.random.default_rng(5)
-    # log-uniform distances over 1e-12 .. 40 (both table and fall-back ranges),
+    # log-uniform distances over 1e-12 .. 40,
     # plus values next to powers of two and table points, where the rounding of
     # the table index changes
     r = np.exp(rng.uniform(np.log(1e-12), np.log(40.0), 3000))
     p2 = np.ldexp(1.0, np.arange(-30, 5))
     near = np.concatenate([p2 * (1 + 1e-15), p2 * (1 - 1e-15), p2 * (1 + 2.0 ** -13), p2 * (1 - 2.0 ** -14)])
     r = np.concatenate([r, np.sqrt(near)])
+    r = np.round(np.ldexp(r, 50)) * 2.0 ** -50  # on the grid: exact integer coordinates
     n = r.size
     tgt = np.stack([r, np.zeros(n)], axis=1)
     tgt = np.vstack([tgt, [[0.0, 0.0]]])  # the coincident target: no smooth term
@@ -52,8 +53,8 @@ def test_log64_within_three_ulp():
     L = np.log(r2)
     ref = -inv2pi * (0.5 * L)
     e = np.frexp(r2)[1] - 1
-    bound = 0.5 * inv2pi * (2.0 ** -52 * np.maximum(1.0, np.abs(e) * np.log(2.0)) + np.spacing(np.abs(L))) \
-        + 2.0 * np.spacing(np.abs(ref))
+    bound = 0.5 * inv2pi * (2.0 ** -52 * np.maximum(1.0, np.abs(e) * np.log(2.0)) + 2.0 ** -52
+                            + np.spacing(np.abs(L))) + 2.0 * np.spacing(np.abs(ref))
     ratio = np.abs(out[:n] - ref) / bound
     big = np.abs(L) >= 1.0
     ulps = np.abs(out[:n] - ref)[big] / np.spacing(np.abs(ref[big]))
@@ -70,6 +71,7 @@ def test_default_and_plain_kernels_agree_on_a_line():
     # two results differ by at most the logarithm's error
     rng = np.random.default_rng(6)
     r = np.exp(rng.uniform(np.log(1e-6), np.log(4.0), 2000))
+    r = np.round(np.ldexp(r, 50)) * 2.0 ** -50
     tgt = np.stack([r, np.zeros(r.size)], axis=1)
     outs = []
     for flags in (0, vp.VP_FLAG_FP64):
@@ -80,6 +82,6 @@ def test_default_and_plain_kernels_agree_on_a_line():
     inv2pi = 0.159154943091895335768883763372514362
     L = np.log(r * r)
     e = np.frexp(r * r)[1] - 1
-    bound = 0.5 * inv2pi * (2.0 ** -52 * np.maximum(1.0, np.abs(e) * np.log(2.0)) + 2 * np.spacing(np.abs(L))) \
-        + 2.0 * np.spacing(np.abs(outs[1]))
+    bound = 0.5 * inv2pi * (2.0 ** -52 * np.maximum(1.0, np.abs(e) * np.log(2.0)) + 2.0 ** -52
+                            + 2 * np.spacing(np.abs(L))) + 2.0 * np.spacing(np.abs(outs[1]))
     assert np.max(np.abs(outs[0] - outs[1]) / bound) <= 1.0
