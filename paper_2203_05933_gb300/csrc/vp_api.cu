@@ -448,15 +448,6 @@ int fix_sigma(const std::vector<double>& a, const std::vector<double>& b)
     return mx > 0.0 ? 60 - std::ilogb(mx) : 60;
 }
 
-// (E - 2 sigma) log 2, E = 0..127, in long double
-std::vector<double> make_elogfix(int sigma)
-{
-    std::vector<double> t(128);
-    const long double ln2 = 0.693147180559945309417232121458176568L;
-    for (int E = 0; E < 128; ++E) t[(size_t)E] = (double)((long double)(E - 2 * sigma) * ln2);
-    return t;
-}
-
 PassGeom forward_geom(vp_plan p)
 {
     PassGeom g;
@@ -470,6 +461,7 @@ PassGeom forward_geom(vp_plan p)
     g.n_eval = (int32_t)p->n_tgt;
     g.cfix = p->src_fix;
     g.efix = p->tgt_fix;
+    g.fix_sigma = p->fix_sigma;
     return g;
 }
 
@@ -486,6 +478,7 @@ PassGeom adjoint_geom(vp_plan p)
     g.n_eval = (int32_t)p->n_src;
     g.cfix = p->tgt_fix;
     g.efix = p->src_fix;
+    g.fix_sigma = p->fix_sigma;
     return g;
 }
 
@@ -1209,8 +1202,6 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_m2le, m2le);
     up(&d_mtpow_s, mtpow_s);
     up(&d_tau_pow, tau_pow);
-    double* d_elogfix = nullptr;
-    up(&d_elogfix, make_elogfix(p->fix_sigma));
     up(&d_fftab, fftab);
     up(&d_srho, B.srho);
     up(&d_trho, B.trho);
@@ -1313,7 +1304,6 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.m2le = d_m2le;
     tb.mtpow_s = d_mtpow_s;
     tb.tau_pow = d_tau_pow;
-    tb.elogfix = d_elogfix;
     tb.Hf = (const float2*)(d_fftab + offf[0]);
     tb.tpowf = (const float4*)(d_fftab + offf[1]);
     tb.mtpowf = (const float4*)(d_fftab + offf[2]);

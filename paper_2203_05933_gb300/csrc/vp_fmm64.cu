@@ -86,22 +86,26 @@ __device__ __forceinline__ double log_r2(double r2, const double2* __restrict__ 
 }
 
 // log(r^2) of two points given as integers on the grid 2^-sigma (dx, dy below
-// 2^62 in magnitude). r^2 2^(2 sigma) = dx^2 + dy^2 is formed exactly in 128-bit
-// integers and rounded to 53 bits, m 2^(n - 52) with m in [2^52, 2^53); rounding
-// m to the nearest table point c_k = 1 + k 2^-12 gives E = n or n + 1 and
-// y = r^2 2^(2 sigma - E) in [1 - 2^-13, 2), built from the bits; then, as in
-// log_r2, log r^2 = (E - 2 sigma) log 2 + T_k + log1p(u), u = y s_k - 1, with
-// elog[E] = (E - 2 sigma) log 2. Five FP64 operations; the square and its
-// normalisation run on the integer pipes. r^2 = 0 (coincident points) gives 0.
+// 2^62 in magnitude), in two parts: log r^2 = Lp + Ep log 2. r^2 2^(2 sigma) =
+// dx^2 + dy^2 is formed exactly in 128-bit integers and rounded to 53 bits,
+// m 2^(n - 52) with m in [2^52, 2^53); rounding m to the nearest table point
+// c_k = 1 + k 2^-12 gives E = n or n + 1 and y = r^2 2^(2 sigma - E) in
+// [1 - 2^-13, 2), built from the bits; then as in log_r2, Lp = T_k + log1p(u),
+// u = y s_k - 1 (four FP64 operations), and the integer Ep = E - 2 sigma. The
+// square and its normalisation run on the integer pipes. r^2 = 0 (coincident
+// points) gives Lp = 0, Ep = 0.
 __device__ __forceinline__ double log_r2_fix(long long dx, long long dy, const double2* __restrict__ tab,
-                                             const double* __restrict__ elog)
+                                             int two_sigma, int& Ep)
 {
     const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
     const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
     const unsigned long long l1 = ax * ax, l2 = ay * ay;
     unsigned long long lo = l1 + l2;
     unsigned long long hi = __umul64hi(ax, ax) + __umul64hi(ay, ay) + (lo < l1 ? 1ULL : 0ULL);
-    if ((hi | lo) == 0ULL) return 0.0;
+    if ((hi | lo) == 0ULL) {
+        Ep = 0;
+        return 0.0;
+    }
     int n = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
     const int sh = n - 52;
     unsigned long long m;
@@ -109,7 +113,7 @@ __device__ __forceinline__ double log_r2_fix(long long dx, long long dy, const d
     if (sh <= 0) {
         m = lo << (-sh);
     } else if (sh < 64) {
-        m = (lo >> sh) | (sh == 0 ? 0ULL : hi << (64 - sh));
+        m = (lo >> sh) | (hi << (64 - sh));
         rb = (int)((lo >> (sh - 1)) & 1ULL);
     } else {
         m = hi >> (sh - 64);
@@ -122,14 +126,33 @@ __device__ __forceinline__ double log_r2_fix(long long dx, long long dy, const d
     }
     const unsigned long long h = m + (1ULL << (51 - kLog64Bits));  // to the nearest table point
     const int carry = (int)(h >> 53);
-    const int E = n + carry;
+    Ep = n + carry - two_sigma;
     const int k = (int)((h >> (52 - kLog64Bits)) & ((1ULL << kLog64Bits) - 1));
     const double y = __longlong_as_double(
         (long long)(((unsigned long long)(1023 - carry) << 52) | (m & 0xfffffffffffffULL)));
     const double2 sk = tab[k];
     const double u = fma(y, sk.x, -1.0);
     const double b = fma(u, fma(u, 0x1.5555555555555p-2, -0.5), 1.0);  // 1 - u/2 + u^2/3
-    return fma(u, b, elog[E] + sk.y);
+    return fma(u, b, sk.y);
+}
+
+// round(x 2^t) by integer operations on the bits of x, for |x 2^t| < 2^62
+// (zero and subnormal x give 0)
+__device__ __forceinline__ long long round_pow2(double x, int t)
+{
+    const long long bits = __double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7ff);
+    if (E == 0) return 0;
+    const long long mant = (bits & 0xfffffffffffffLL) | 0x10000000000000LL;
+    const int sh = E - 1075 + t;  // x 2^t = mant 2^sh
+    long long X;
+    if (sh >= 0)
+        X = mant << sh;
+    else if (sh < -62)
+        X = 0;
+    else
+        X = (mant + (1LL << (-sh - 1))) >> (-sh);
+    return bits < 0 ? -X : X;
 }
 
 // ----------------------------------------------------------------------------
@@ -154,6 +177,7 @@ template <int ND>
 struct LeafStageFix {
     longlong2 xy[32];  // integer coordinates (PassGeom::cfix)
     double q[32][ND];
+    long long Q[32][ND];  // round(q 2^tq): the charges in fixed point for the exponent part
 };
 
 template <int P, int ND, bool SYM>
@@ -329,26 +353,26 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
 // takes point a of the pass and chunk positions kap, kap + K, ...), in
 // ceil(T K / 32) passes over the stream, K in {1, 2, 4, 8, 16} chosen per leaf
 // for the fewest lane-steps (every lane of an FP64 instruction costs an issue
-// slot, busy or not). The pairs take the points' integer coordinates and
-// log_r2_fix (six FP64 operations a pair with the accumulation). The K partial
-// sums of a point are added by shuffles and psi += near / 2 (the log is of r^2).
+// slot, busy or not). A pair takes the points' integer coordinates and
+// log_r2_fix: sum_j q_j log r_j^2 = sum_j q_j Lp_j + log 2 * sum_j q_j Ep_j, the
+// first in float64 (five FP64 operations a pair with the accumulation), the
+// second exactly in 128-bit integers from the charges in fixed point,
+// Q_j = round(q_j 2^tq) with tq set per leaf by the largest |q| of its stream
+// (|Q| < 2^55, |Q Ep| < 2^62). The K partial sums of a point are added by
+// shuffles and psi += near / 2 (the log is of r^2).
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafWarps64 * 32)
     k_leaf64d(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
               const double2* __restrict__ L, const double2* __restrict__ logtab, const double* __restrict__ etab_g,
-              const double* __restrict__ elogfix_g, double* __restrict__ psi, int* __restrict__ work)
+              int two_sigma, double* __restrict__ psi, int* __restrict__ work)
 {
     constexpr int P1 = P + 1;
     extern __shared__ __align__(16) unsigned char smem64d[];
     double2* tab = reinterpret_cast<double2*>(smem64d);                      // [1 << kLog64Bits]
     double* etab = reinterpret_cast<double*>(tab + (1 << kLog64Bits));       // [2 * kEBias]
-    double* elogfix = etab + 2 * kEBias;                                     // [128]
-    LeafStageFix<ND>* stage = reinterpret_cast<LeafStageFix<ND>*>(elogfix + 2 * kEBias);
+    LeafStageFix<ND>* stage = reinterpret_cast<LeafStageFix<ND>*>(etab + 2 * kEBias);
     for (int i = threadIdx.x; i < (1 << kLog64Bits); i += blockDim.x) tab[i] = logtab[i];
-    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) {
-        etab[i] = etab_g[i];
-        elogfix[i] = elogfix_g[i];
-    }
+    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) etab[i] = etab_g[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     LeafStageFix<ND>& st = stage[threadIdx.x >> 5];
@@ -404,13 +428,58 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
             for (int d = 0; d < ND; ++d) psi[(int64_t)(e0 + i) * ND + d] = acc[d];
         }
         __syncwarp();  // the far parts before other lanes add to them
-        // the U-list stream and the split with the fewest lane-steps
         int S = 0;
         for (int e = u0; e < u1; ++e) {
             const int A = t.u_idx[e];
             S += g.crng[2 * A + 1] - g.crng[2 * A];
         }
         if (S == 0) continue;
+        // position p of the U-list stream -> charge index, from the cursor (entry
+        // ecur whose first position is ebase <= p)
+        auto charge_at = [&](int ecur, int ebase, int p) -> int {
+            int e = ecur, pos = p - ebase;
+            int A = t.u_idx[e];
+            int a0 = g.crng[2 * A], len = g.crng[2 * A + 1] - a0;
+            while (pos >= len) {
+                pos -= len;
+                A = t.u_idx[++e];
+                a0 = g.crng[2 * A];
+                len = g.crng[2 * A + 1] - a0;
+            }
+            return a0 + pos;
+        };
+        auto advance = [&](int& ecur, int& ebase, int p) {  // cursor to the entry holding position p
+            for (;;) {
+                const int A = t.u_idx[ecur];
+                const int len = g.crng[2 * A + 1] - g.crng[2 * A];
+                if (ebase + len > p || ecur + 1 >= u1) break;
+                ebase += len;
+                ++ecur;
+            }
+        };
+        // the scale of the fixed-point charges: the largest |q| of the stream
+        int tq[ND];
+        {
+            unsigned int mx[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) mx[d] = 0u;
+            int ecur = u0, ebase = 0;
+            for (int c0 = 0; c0 < S; c0 += 32) {
+                if (c0 + lane < S) {
+                    const int j = charge_at(ecur, ebase, c0 + lane);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d)
+                        mx[d] = max(mx[d], (unsigned int)__double2hiint(q[(int64_t)j * ND + d]) & 0x7fffffffu);
+                }
+                advance(ecur, ebase, c0 + 32);
+            }
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const unsigned int m = __reduce_max_sync(0xffffffffu, mx[d]);
+                tq[d] = 54 - ((int)(m >> 20) - 1023);  // |q| < 2^(ex + 1), ex = (m >> 20) - 1023: |Q| < 2^55
+            }
+        }
+        // the split with the fewest lane-steps
         const int full = S >> 5, rem = S & 31;
         int K = 1;
         long long best = -1;
@@ -428,55 +497,62 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
             const bool valid = ti < T;
             const longlong2 z = valid ? g.efix[e0 + ti] : make_longlong2(0, 0);
             double near[ND];
+            __int128 ne[ND];
 #pragma unroll
-            for (int d = 0; d < ND; ++d) near[d] = 0.0;
-            int ecur = u0, ebase = 0;  // U entry holding stream position c0, and its first position
+            for (int d = 0; d < ND; ++d) {
+                near[d] = 0.0;
+                ne[d] = 0;
+            }
+            int ecur = u0, ebase = 0;
             for (int c0 = 0; c0 < S; c0 += 32) {
                 const int n = min(32, S - c0);
                 __syncwarp();
                 if (lane < n) {
-                    int e = ecur, pos = c0 + lane - ebase;
-                    int A = t.u_idx[e];
-                    int a0 = g.crng[2 * A], len = g.crng[2 * A + 1] - a0;
-                    while (pos >= len) {
-                        pos -= len;
-                        A = t.u_idx[++e];
-                        a0 = g.crng[2 * A];
-                        len = g.crng[2 * A + 1] - a0;
-                    }
-                    const int j = a0 + pos;
+                    const int j = charge_at(ecur, ebase, c0 + lane);
                     st.xy[lane] = g.cfix[j];
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) st.q[lane][d] = q[(int64_t)j * ND + d];
+                    for (int d = 0; d < ND; ++d) {
+                        const double qj = q[(int64_t)j * ND + d];
+                        st.q[lane][d] = qj;
+                        st.Q[lane][d] = round_pow2(qj, tq[d]);
+                    }
                 }
-                // move the cursor to the entry holding position c0 + 32
-                for (;;) {
-                    const int A = t.u_idx[ecur];
-                    const int len = g.crng[2 * A + 1] - g.crng[2 * A];
-                    if (ebase + len > c0 + 32 || ecur + 1 >= u1) break;
-                    ebase += len;
-                    ++ecur;
-                }
+                advance(ecur, ebase, c0 + 32);
                 __syncwarp();
                 if (valid) {
 #pragma unroll 4
                     for (int j = kap; j < n; j += K) {
                         const longlong2 sp = st.xy[j];
-                        const double Lg = log_r2_fix(z.x - sp.x, z.y - sp.y, tab, elogfix);
+                        int Ep;
+                        const double Lp = log_r2_fix(z.x - sp.x, z.y - sp.y, tab, two_sigma, Ep);
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) near[d] = fma(st.q[j][d], Lg, near[d]);
+                        for (int d = 0; d < ND; ++d) {
+                            near[d] = fma(st.q[j][d], Lp, near[d]);
+                            ne[d] += (__int128)(st.Q[j][d] * (long long)Ep);
+                        }
                     }
                 }
             }
             for (int off = 1; off < K; off <<= 1) {  // warp-uniform
 #pragma unroll
-                for (int d = 0; d < ND; ++d) near[d] += __shfl_xor_sync(0xffffffffu, near[d], off);
+                for (int d = 0; d < ND; ++d) {
+                    near[d] += __shfl_xor_sync(0xffffffffu, near[d], off);
+                    const unsigned long long lo = (unsigned long long)ne[d];
+                    const long long hi = (long long)(ne[d] >> 64);
+                    const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, off);
+                    const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                    ne[d] += ((__int128)hi2 << 64) + (__int128)lo2;
+                }
             }
             if (valid && kap == 0) {
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
+                    // log 2 * sum Q Ep 2^-tq, the 128-bit sum converted once
+                    const double es = fma((double)(long long)(ne[d] >> 64), 0x1p64,
+                                          (double)(unsigned long long)ne[d]);
+                    const double tot = fma(es, ldexp(0.693147180559945309417232121458, -tq[d]), near[d]);
                     double* o = psi + (int64_t)(e0 + ti) * ND + d;
-                    *o = fma(0.5, near[d], *o);
+                    *o = fma(0.5, tot, *o);
                 }
             }
         }
@@ -1315,8 +1391,8 @@ size_t p2m_smem()
 template <int ND>
 size_t leaf_smem()
 {
-    return (size_t)(1 << kLog64Bits) * sizeof(double2) + 4 * kEBias * sizeof(double) +
-           (size_t)kLeafWarps64 * sizeof(LeafStage64<ND>);
+    return (size_t)(1 << kLog64Bits) * sizeof(double2) + 2 * kEBias * sizeof(double) +
+           (size_t)kLeafWarps64 * std::max(sizeof(LeafStage64<ND>), sizeof(LeafStageFix<ND>));
 }
 
 template <int P, int ND>
@@ -1383,7 +1459,8 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         k_sym_reduce64<ND><<<rblocks, 256, 0, s>>>(t, g, slots, ws.psi);
     } else {
         k_leaf64d<P, ND><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
-                                                                            tab.elog64, tab.elogfix, ws.psi, ws.work);
+                                                                            tab.elog64, 2 * g.fix_sigma, ws.psi,
+                                                                            ws.work);
     }
     if (tm) tm->end(id);
     return cudaGetLastError();

@@ -91,7 +91,6 @@ struct DevTables {
     const int32_t* m2le = nullptr;  // [32] row exponents of those digits
     const double2* mtpow_s = nullptr; // [49][P1] (-t_o / tau)^k, tau = 2^-1.5            (float64 M2L)
     const double* tau_pow = nullptr;  // [P1] tau^k
-    const double* elogfix = nullptr;  // [128] (E - 2 sigma) log 2: the log of r^2 from integer coordinates
     // float-float copies for the FP32-pipe M2L
     const float2* Hf = nullptr;     // [P1][P1]
     const float4* tpowf = nullptr;  // [49][P1] complex (re_h, re_l, im_h, im_l)
@@ -117,6 +116,7 @@ struct PassGeom {
     // only where |x| < 2^(61 - sigma - 53)), |value| < 2^61
     const longlong2* cfix = nullptr;
     const longlong2* efix = nullptr;
+    int32_t fix_sigma = 60;
 };
 
 // Correction matrix with consecutive rows that share one column list grouped
