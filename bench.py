@@ -780,7 +780,7 @@ def main():
     vp._load()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    fp64_tflops, fp32_tflops, dmma_tflops, bf16mma_tflops = vp.vp_measure_peaks(tensor=True)
+    fp64_tflops, fp32_tflops, dmma_tflops, bf16mma_tflops, s8mma_tops = vp.vp_measure_peaks(tensor=True)
     fp64_src = ("vp_measure_peaks in this run: chains of independent FP64 FMAs in every lane of a full grid "
                 "(measured)")
     t0 = time.perf_counter()
@@ -908,7 +908,7 @@ def main():
         "roofline": roofline,
         "roofline_phases": rl_all,
         "peaks": {"fp64_tflops": fp64_tflops, "fp32_tflops": fp32_tflops, "f64_mma_tflops": dmma_tflops,
-                  "bf16_mma_sync_tflops": bf16mma_tflops, "source": fp64_src},
+                  "bf16_mma_sync_tflops": bf16mma_tflops, "s8_mma_sync_tops": s8mma_tops, "source": fp64_src},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(prob.n_src * 8),
                 "d2h_bytes_per_step": int(prob.n_tgt * 8)},

@@ -341,15 +341,16 @@ vp_status vp_green_eval_host(int32_t kernel, double lambda, int64_t n, const dou
 /* Roofline denominators measured on the current device at its present clocks:
  * sustained FP64 and FP32 fused multiply-add throughput in TFLOP/s (2 flops per FMA),
  * from chains of independent FMAs in every lane of a full grid (best of two timed
- * launches after a warm-up launch, CUDA events on `stream`); if `dmma_tflops` /
- * `bf16_mma_tflops` are not NULL, also the FP64 tensor instruction (mma.sync
- * m8n8k4 f64) and the bf16 warp-level tensor instruction (mma.sync m16n8k16,
- * f32 accumulation) measured the same way. The paper has no counterpart: this
+ * launches after a warm-up launch, CUDA events on `stream`); if `dmma_tflops`,
+ * `bf16_mma_tflops` / `s8_mma_tops` are not NULL, also the FP64 tensor
+ * instruction (mma.sync m8n8k4 f64), the bf16 warp-level tensor instruction
+ * (mma.sync m16n8k16, f32 accumulation) and the int8 one (mma.sync m16n8k32,
+ * s32 accumulation, in T operations/s) measured the same way. The paper has no counterpart: this
  * supports the measurement of the kernels against their roofline. Allocates and
  * frees a small device buffer and synchronizes `stream`. Takes about 0.2 s.
  * Errors: VP_ERR_ARG (NULL fp64/fp32 output), VP_ERR_OOM, VP_ERR_CUDA. */
 vp_status vp_measure_peaks(double* fp64_tflops, double* fp32_tflops, double* dmma_tflops, double* bf16_mma_tflops,
-                           void* stream);
+                           double* s8_mma_tops, void* stream);
 
 /* Static description of a status code; never NULL. */
 const char* vp_status_string(int32_t status);

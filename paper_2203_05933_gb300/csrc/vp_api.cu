@@ -336,6 +336,8 @@ struct vp_plan_s {
     longlong2* src_fix = nullptr;  // the same points on the integer grid 2^-fix_sigma
     longlong2* tgt_fix = nullptr;
     int fix_sigma = 60;
+    double2* src_pow = nullptr;    // powers of the points relative to their leaves, [n][P] (float64 plans)
+    double2* tgt_pow = nullptr;
     float4* src_rho = nullptr;
     float4* tgt_rho = nullptr;
     double* w_sorted = nullptr;
@@ -462,6 +464,8 @@ PassGeom forward_geom(vp_plan p)
     g.cfix = p->src_fix;
     g.efix = p->tgt_fix;
     g.fix_sigma = p->fix_sigma;
+    g.cpow = p->src_pow;
+    g.epow = p->tgt_pow;
     return g;
 }
 
@@ -479,6 +483,8 @@ PassGeom adjoint_geom(vp_plan p)
     g.cfix = p->tgt_fix;
     g.efix = p->src_fix;
     g.fix_sigma = p->fix_sigma;
+    g.cpow = p->tgt_pow;
+    g.epow = p->src_pow;
     return g;
 }
 
@@ -1287,6 +1293,14 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     dt.sym_pt_leaf = d_pt_leaf;
     dt.sym_own = d_own;
     dt.sym_slots = nslots;
+    if (p->arith == Arith::kF64) {
+        // the points' powers in their leaves (P2M and L2P inputs of the float64 kernels)
+        cudaError_t ep = p->alloc(&p->src_pow, (size_t)n_src * P);
+        if (ep == cudaSuccess) ep = p->alloc(&p->tgt_pow, (size_t)n_tgt * P);
+        if (ep == cudaSuccess && n_src > 0) ep = launch_point_powers(P, dt, p->box_src, p->src_xy, p->src_pow, s);
+        if (ep == cudaSuccess && n_tgt > 0) ep = launch_point_powers(P, dt, p->box_tgt, p->tgt_xy, p->tgt_pow, s);
+        if (ep != cudaSuccess) return cuda_fail(ep, "vp_plan_create point powers");
+    }
     DevTables& tb = p->tab;
     tb.H = d_tab + off[0];
     tb.Bm = d_tab + off[1];

@@ -206,7 +206,6 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
         const double2 cb = t.center[b];
-        const double invRb = 1.0 / t.radius[b];
         const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
         for (int gb = e0; gb < e1; gb += 32) {
@@ -228,16 +227,20 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                 near[d] = 0.0;
                 qi[d] = (SYM && valid) ? q[(int64_t)ti * ND + d] : 0.0;
             }
-            // L2P: Re sum_l L_l u^l by Horner, u = (z - c)/R
+            // L2P: Re sum_l L_l u^l, u = (z - c)/R, from the point's stored powers
             {
-                const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
                 const double2* Lb = L + (int64_t)b * P1 * ND;
+                const double2* up = g.epow + (int64_t)(valid ? ti : e0) * P;
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    double2 s = Lb[P * ND + d];
+                for (int d = 0; d < ND; ++d) acc[d] = Lb[d].x;
 #pragma unroll 4
-                    for (int l = P - 1; l >= 0; --l) s = cfma64(s, u, Lb[l * ND + d]);
-                    acc[d] = s.x;
+                for (int l = 1; l <= P; ++l) {
+                    const double2 ul = up[l - 1];
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const double2 Ll = Lb[l * ND + d];
+                        acc[d] = fma(Ll.x, ul.x, fma(-Ll.y, ul.y, acc[d]));
+                    }
                 }
             }
             // M2P over W: M_0 log|z - c| + Re sum_k M_k v^k, v = R/(z - c)
@@ -386,23 +389,25 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
         const int e0 = g.erng[2 * b], e1 = g.erng[2 * b + 1];
         if (e0 == e1) continue;
         const int T = e1 - e0;
-        const double2 cb = t.center[b];
-        const double invRb = 1.0 / t.radius[b];
         const int u0 = t.u_ptr[b], u1 = t.u_ptr[b + 1];
         const int w0 = t.w_ptr[b], w1 = t.w_ptr[b + 1];
-        // far part: L2P (Re sum_l L_l u^l, u = (z - c)/R, Horner) and M2P over W
-        // (M_0 log|z - c| + Re sum_k M_k v^k, v = R/(z - c))
+        // far part: L2P (Re sum_l L_l u^l, u = (z - c)/R, from the point's stored
+        // powers) and M2P over W (M_0 log|z - c| + Re sum_k M_k v^k, v = R/(z - c))
         for (int i = lane; i < T; i += 32) {
             const double2 z = g.exy[e0 + i];
             double acc[ND];
-            const double2 u = make_double2((z.x - cb.x) * invRb, (z.y - cb.y) * invRb);
             const double2* Lb = L + (int64_t)b * P1 * ND;
+            const double2* up = g.epow + (int64_t)(e0 + i) * P;  // u^l, u = (z - c)/R
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                double2 sl = Lb[P * ND + d];
+            for (int d = 0; d < ND; ++d) acc[d] = Lb[d].x;
 #pragma unroll 4
-                for (int l = P - 1; l >= 0; --l) sl = cfma64(sl, u, Lb[l * ND + d]);
-                acc[d] = sl.x;
+            for (int l = 1; l <= P; ++l) {
+                const double2 ul = up[l - 1];
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const double2 Ll = Lb[l * ND + d];
+                    acc[d] = fma(Ll.x, ul.x, fma(-Ll.y, ul.y, acc[d]));
+                }
             }
             for (int e = w0; e < w1; ++e) {
                 const int D = t.w_idx[e];
@@ -728,9 +733,9 @@ __global__ void k_sym_reduce64(DevTree t, PassGeom g, const double* __restrict__
 }
 
 // ----------------------------------------------------------------------------
-// a3: P2M and the whole M2M pass in one launch, one warp per leaf. The charges
-// are taken 32 at a time: lane j forms the powers u_j^k (u = (z - c)/R) of its
-// point into the warp's buffer, then lane k sums q_j u_j^k over the 32 points.
+// a3: P2M and the whole M2M pass in one launch, one warp per leaf: lane k sums
+// q_j u_j^k over the leaf's points (u = (z - c)/R), the powers read from the
+// plan's per-point table (formed once, the geometry being static).
 // With the arrival counters (one per box, zero on entry and left zero), a warp
 // that has finished a box counts itself in at the parent after a fence, and
 // the warp that completes the count computes the parent's M2M and carries on
@@ -826,11 +831,9 @@ __global__ void __launch_bounds__(kW64 * 32)
 {
     constexpr int P1 = P + 1;
     extern __shared__ __align__(16) unsigned char smem_p2m[];
-    // per warp: [32][P1] powers, then [32][ND] charges; the M2M reuses the powers' space
-    constexpr int kPerWarp = (32 > 4 * ND ? 32 : 4 * ND) * P1 + (32 * ND + 1) / 2;  // M2M stages [4][P1][ND]
+    // per warp: the M2M's stage of the four children's multipoles [4][P1][ND]
     const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    double2* pw = reinterpret_cast<double2*>(smem_p2m) + (size_t)wb * kPerWarp;
-    double* qs = reinterpret_cast<double*>(pw + 32 * P1);
+    double2* pw = reinterpret_cast<double2*>(smem_p2m) + (size_t)wb * 4 * P1 * ND;
     const double sc = lane == 0 ? 1.0 : -1.0 / (double)lane;
     for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
         const int b = t.leaves[li];
@@ -838,37 +841,16 @@ __global__ void __launch_bounds__(kW64 * 32)
         double2 acc[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
-        const double2 c = t.center[b];
-        const double invR = 1.0 / t.radius[b];
-        for (int base = s0; base < s1; base += 32) {
-            const int n = min(32, s1 - base);
-            __syncwarp();
-            if (lane < n) {
-                const double2 z = g.cxy[base + lane];
-                const double2 u = make_double2((z.x - c.x) * invR, (z.y - c.y) * invR);
-                double2 p = u;
-                pw[lane * P1 + 1] = p;
+        // lane k sums q_j u_j^k over the leaf's points (u_j^k stored per point); lane 0 sums q_j
+        if (lane <= P) {
 #pragma unroll 4
-                for (int k = 2; k <= P; ++k) {
-                    p = cmul64(p, u);
-                    pw[lane * P1 + k] = p;
-                }
+            for (int j = s0; j < s1; ++j) {
+                const double2 pv = lane == 0 ? make_double2(1.0, 0.0) : g.cpow[(int64_t)j * P + lane - 1];
 #pragma unroll
-                for (int d = 0; d < ND; ++d) qs[lane * ND + d] = q[(int64_t)(base + lane) * ND + d];
-            }
-            __syncwarp();
-            if (lane == 0) {
-                for (int j = 0; j < n; ++j)
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) acc[d].x += qs[j * ND + d];
-            } else if (lane <= P) {
-                for (int j = 0; j < n; ++j) {
-                    const double2 pv = pw[j * P1 + lane];
-#pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        acc[d].x = fma(qs[j * ND + d], pv.x, acc[d].x);
-                        acc[d].y = fma(qs[j * ND + d], pv.y, acc[d].y);
-                    }
+                for (int d = 0; d < ND; ++d) {
+                    const double qv = q[(int64_t)j * ND + d];
+                    acc[d].x = fma(qv, pv.x, acc[d].x);
+                    acc[d].y = fma(qv, pv.y, acc[d].y);
                 }
             }
         }
@@ -936,9 +918,10 @@ __global__ void __launch_bounds__(kW64 * 32)
 // (two k-steps each), and adds t^l Y_l into the lane's rows (fragment row
 // groups) and column pair. The X list (P2L) then adds
 //   L_0 += q log|z - c|,  L_l -= (q / l) v^l,  v = R/(z - c),
-// with lane l owning L_l; 32 sources at a time (lane j forms the powers of v_j).
+// with lane l owning L_l; kXB sources at a time (lane j forms the powers of v_j).
 constexpr int kSl = 8;   // 8-bit digits per operand
 constexpr int kHs = 40;  // row stride (bf16 elements) of the digit tiles: conflict-free fragment loads
+constexpr int kXB = 16;  // X-list sources per batch
 constexpr size_t kHdBytes = (size_t)kSl * 32 * kHs * sizeof(uint16_t);
 
 template <int P, int ND>
@@ -951,13 +934,13 @@ struct M2LTShape {
     static constexpr int RA = (G * P + 31) / 32;       // rounds of the A' items (entry, k = 1..P)
     static constexpr int RS = (NCOL * P1 + 31) / 32;   // rounds of the digit items (column, k = 0..P)
     // per-warp shared memory: A' [G][P1][ND] double2 and the digits [kSl][NCOL][kHs]
-    // bf16 for the V list, the same space for the X list's powers [32][P1] double2;
-    // charges and logs [32][ND + 1] double; column exponents [G ND], entry offsets [G]
+    // bf16 for the V list, the same space for the X list's powers [kXB][P1] double2;
+    // charges and logs [kXB][ND + 1] double; column exponents [G ND], entry offsets [G]
     static constexpr size_t kAs = (size_t)G * P1 * ND * 16;
     static constexpr size_t kBt = (size_t)kSl * NCOL * kHs * 2;
-    static constexpr size_t kPw = (size_t)32 * P1 * 16;
+    static constexpr size_t kPw = (size_t)kXB * P1 * 16;
     static constexpr size_t kR1 = kAs + kBt > kPw ? kAs + kBt : kPw;
-    static constexpr size_t kQl = (((size_t)32 * (ND + 1) * 8) + 15) & ~(size_t)15;
+    static constexpr size_t kQl = (((size_t)kXB * (ND + 1) * 8) + 15) & ~(size_t)15;
     static constexpr size_t kEx = (((size_t)(G * ND + G) * 4) + 15) & ~(size_t)15;
     static constexpr size_t kWarp = kR1 + kQl + kEx;
 };
@@ -1030,7 +1013,7 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint3
 }
 
 template <int P, int ND>
-__global__ void __launch_bounds__(kW64 * 32)
+__global__ void __launch_bounds__(kW64 * 32, ND <= 2 ? 4 : 2)
     k_m2l64(DevTree t, DevTables tab, PassGeom g, const double2* __restrict__ M, double2* __restrict__ L,
             const double* __restrict__ q, const double2* __restrict__ logtab, const double* __restrict__ etab)
 {
@@ -1044,8 +1027,8 @@ __global__ void __launch_bounds__(kW64 * 32)
     unsigned char* wbase = smem_m2l + kHdBytes + 128 + (size_t)wb * S::kWarp;
     double2* As = reinterpret_cast<double2*>(wbase);                // [G][P1][ND]
     uint16_t* Bt = reinterpret_cast<uint16_t*>(wbase + S::kAs);     // [kSl][NCOL][kHs]
-    double2* pws = reinterpret_cast<double2*>(wbase);                               // [32][P1] (X list)
-    double* qls = reinterpret_cast<double*>(wbase + S::kR1);                         // [32][ND + 1]
+    double2* pws = reinterpret_cast<double2*>(wbase);                               // [kXB][P1] (X list)
+    double* qls = reinterpret_cast<double*>(wbase + S::kR1);                         // [kXB][ND + 1]
     int* em = reinterpret_cast<int*>(wbase + S::kR1 + S::kQl);                       // [G ND]
     int* eo = em + G * ND;                                                                // [G]
     for (int i = threadIdx.x; i < (int)(kHdBytes / 4); i += blockDim.x)
@@ -1255,8 +1238,8 @@ __global__ void __launch_bounds__(kW64 * 32)
             for (int e = x0; e < x1; ++e) {
                 const int Cx = t.x_idx[e];
                 const int s0 = g.crng[2 * Cx], s1 = g.crng[2 * Cx + 1];
-                for (int base = s0; base < s1; base += 32) {
-                    const int n = min(32, s1 - base);
+                for (int base = s0; base < s1; base += kXB) {
+                    const int n = min(kXB, s1 - base);
                     __syncwarp();
                     if (lane < n) {
                         const double2 z = g.cxy[base + lane];
@@ -1385,7 +1368,7 @@ int device_sms()
 template <int P, int ND>
 size_t p2m_smem()
 {
-    return (size_t)kW64 * ((32 > 4 * ND ? 32 : 4 * ND) * (P + 1) + (32 * ND + 1) / 2) * sizeof(double2);
+    return (size_t)kW64 * 4 * (P + 1) * ND * sizeof(double2);
 }
 
 template <int ND>
@@ -1490,6 +1473,52 @@ cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, 
         case 30: return fmm64_p<30>(nd, t, tab, g, ws, gradient, timer, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+
+namespace {
+// Powers u^k, k = 1..P, of each point relative to its leaf, u = (z - c)/R (c
+// the leaf's center, R its half side), [n][P] in tree order: the geometry is
+// static, so they are formed once per plan and serve as the P2M input where
+// the points carry charges and as the L2P input where they are evaluated. The
+// same products as P2M formed on the fly (u, then p <- p u). One warp per leaf.
+template <int P>
+__global__ void k_point_powers(DevTree t, const int32_t* __restrict__ rng, const double2* __restrict__ xy,
+                               double2* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
+        const int b = t.leaves[li];
+        const int s0 = rng[2 * b], s1 = rng[2 * b + 1];
+        const double2 c = t.center[b];
+        const double invR = 1.0 / t.radius[b];
+        for (int j = s0 + lane; j < s1; j += 32) {
+            const double2 z = xy[j];
+            const double2 u = make_double2((z.x - c.x) * invR, (z.y - c.y) * invR);
+            double2 pk = u;
+            double2* o = out + (int64_t)j * P;
+            o[0] = pk;
+            for (int k = 2; k <= P; ++k) {
+                pk = cmul64(pk, u);
+                o[k - 1] = pk;
+            }
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_point_powers(int P, const DevTree& t, const int32_t* rng, const double2* xy, double2* out,
+                                cudaStream_t s)
+{
+    if (t.nleaf == 0) return cudaSuccess;
+    const int blocks = blocks_for_warps(t.nleaf, kW64);
+    switch (P) {
+        case 16: k_point_powers<16><<<blocks, kW64 * 32, 0, s>>>(t, rng, xy, out); break;
+        case 24: k_point_powers<24><<<blocks, kW64 * 32, 0, s>>>(t, rng, xy, out); break;
+        case 30: k_point_powers<30><<<blocks, kW64 * 32, 0, s>>>(t, rng, xy, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // M2M table of order P: m2m[c][l][k] = C(l-1, k-1) 2^-k zeta_c^(l-k) for 1 <= k <= l,

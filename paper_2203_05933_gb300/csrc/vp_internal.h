@@ -117,6 +117,9 @@ struct PassGeom {
     const longlong2* cfix = nullptr;
     const longlong2* efix = nullptr;
     int32_t fix_sigma = 60;
+    // powers u^k (k = 1..P) of each point relative to its leaf, [n][P] (float64 plans)
+    const double2* cpow = nullptr;
+    const double2* epow = nullptr;
 };
 
 // Correction matrix with consecutive rows that share one column list grouped
@@ -214,6 +217,8 @@ struct PhaseTimer {
 // The float64 FMM (vp_fmm64.cu): upward pass, M2L, L2L and the leaf kernel with the
 // symmetric near field when t.sym. Enqueues on `s`; nd is 1, 2, 4 or 8.
 // gradient: the leaf kernel writes grad Re phi (psi[(e * 2 + c) * ND + d]) instead of the potential.
+cudaError_t launch_point_powers(int P, const DevTree& t, const int32_t* rng, const double2* xy, double2* out,
+                                cudaStream_t s);
 cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
                          bool gradient, PhaseTimer* timer, cudaStream_t s);
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);

@@ -124,7 +124,8 @@ def _load():
         "vp_last_error": [],
         "vp_version": [],
         "vp_measure_peaks": [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P],
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), P],
         "vp_tree_build": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options)],
         "vp_tree_build_device": [ctypes.POINTER(P), I64, P, I64, P, ctypes.POINTER(vp_options), P],
         "vp_tree_get": [P, I32, P, ctypes.POINTER(I64)],
@@ -547,13 +548,14 @@ class Plan:
 
 def vp_measure_peaks(stream=None, tensor=False):
     """Binding of vp_measure_peaks: (FP64, FP32) FMA throughput of the current
-    device in TFLOP/s; with tensor=True also (f64 mma, bf16 mma) throughput,
-    returned as a 4-tuple."""
+    device in TFLOP/s; with tensor=True also (f64 mma, bf16 mma) throughput in
+    TFLOP/s and int8 mma throughput in T ops/s, returned as a 5-tuple."""
     lib = _load()
-    a, b, c, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    a, b, c, d, e = (ctypes.c_double() for _ in range(5))
     _check(lib.vp_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c) if tensor else None,
-                                ctypes.byref(d) if tensor else None, _stream(stream)), "vp_measure_peaks")
-    return (a.value, b.value, c.value, d.value) if tensor else (a.value, b.value)
+                                ctypes.byref(d) if tensor else None, ctypes.byref(e) if tensor else None,
+                                _stream(stream)), "vp_measure_peaks")
+    return (a.value, b.value, c.value, d.value, e.value) if tensor else (a.value, b.value)
 
 
 def vp_eval_direct_static(src_xy, w, f, tgt_xy, out, csr=None, stream=None):
