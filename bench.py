@@ -638,8 +638,66 @@ def leg_tricorr(args, dev, flush, stream, fp64_tflops):
            "arith": "FP64 cell maps; mapped Green function and the 36 x rule-node contraction in "
                     "float-float (contraction_tflops counts its 2 flops per term)",
            "host_numpy_s_per_cell": host_cell_s, "setup_s": setup_s}
+    rec["near"] = near_pairs_leg(tc, dev, flush, stream)
     tc.close()
     return rec
+
+
+def near_pairs_leg(tc, dev, flush, stream, max_pairs=16384):
+    """Near-singular correction rows (vp_tricorr_near_eval) of the star mesh: every
+    node of another cell within 0.4 h of a triangle cell whose smallest angle is
+    at least 20 degrees (h its longest side; Sec. 3.1), up to max_pairs pairs."""
+    import torch
+    from scipy.spatial import cKDTree
+    from paper_2203_05933_gb300 import inputs
+    from paper_2203_05933_gb300.setup import meshes as smeshes
+    from paper_2203_05933_gb300.setup import tricorr as stricorr
+
+    t0 = time.perf_counter()
+    holes, _, _, _ = inputs.star_geometry()
+    mesh = smeshes.star_mesh(holes, base_level=7, fine_level=7)
+    tree = cKDTree(mesh.xy)
+    s = np.linspace(0.0, 1.0, 33)
+    bxi = np.minimum(np.concatenate([s, 1 - s, np.zeros_like(s)]), 1.0 - 1e-9)
+    beta = np.concatenate([np.zeros_like(s), s, 1 - s])
+    geoms, tgts, cells = [], [], 0
+    for k, g in enumerate(mesh.geom):
+        if g[0] != "tri" or len(tgts) >= max_pairs:
+            continue
+        v = np.asarray(g[1], float)
+        e = [np.linalg.norm(v[(i + 1) % 3] - v[i]) for i in range(3)]
+        ang = min(np.degrees(np.arccos(np.clip(np.dot(v[(i + 1) % 3] - v[i], v[(i + 2) % 3] - v[i]) /
+                                               (np.linalg.norm(v[(i + 1) % 3] - v[i]) * np.linalg.norm(v[(i + 2) % 3] - v[i])),
+                                               -1, 1))) for i in range(3))
+        if ang < 20.0:
+            continue
+        h = max(e)
+        bx, by, _ = stricorr.cell_map(g)(bxi, beta)
+        cand = tree.query_ball_point(v.mean(axis=0), h + 0.4 * h)
+        a, b = mesh.cell_start[k], mesh.cell_start[k + 1]
+        cand = [i for i in cand if not (a <= i < b)]
+        if not cand:
+            continue
+        pts = mesh.xy[cand]
+        d = np.min(np.hypot(pts[:, None, 0] - bx[None], pts[:, None, 1] - by[None]), axis=1)
+        keep = pts[d < 0.4 * h]
+        gp = stricorr.geom_params(g)
+        for q in keep[: max(0, max_pairs - len(tgts))]:
+            geoms.append(gp)
+            tgts.append(q)
+        cells += 1
+    setup_s = time.perf_counter() - t0
+    g = torch.as_tensor(np.array(geoms), device=dev)
+    tg = torch.as_tensor(np.array(tgts), device=dev)
+    out = torch.empty((g.shape[0], tc.n_nodes), dtype=torch.float64, device=dev)
+    tc.near(g, tg, out=out)
+    torch.cuda.synchronize()
+    tt = time_calls(lambda: tc.near(g, tg, out=out), 3, flush, stream)
+    ms = float(np.mean(tt)) * 1e3
+    return {"mesh": "star, base level 7", "cells": cells, "pairs": int(g.shape[0]), "ms": ms,
+            "value": g.shape[0] / (ms * 1e-3), "unit": "pairs/s", "dtype": "f64",
+            "rule": "star point = nearest cell point; t: 18 dyadic panels x 8 GL, s: graded panels x 10 GL",
+            "setup_s": setup_s}
 
 
 def leg_mhelm(args, dev, flush, stream, prob, f):

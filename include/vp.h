@@ -475,6 +475,33 @@ typedef struct vp_tricorr_s* vp_tricorr;
 vp_status vp_tricorr_create(vp_tricorr* out, int32_t n_nodes, int32_t n_basis, int32_t n_rule,
                             const double* node_ref, const double* node_w, const double* coef,
                             const double* chi, const double* tau, const double* B, void* stream);
+
+/*
+ * Near-singular corrections of mapped triangles (Sec. 3.3.3, Eq.
+ * vp_near_singular, and the inner product of Eq. singcorr_inner_prod): for
+ * pair p, a cell (geom[p], as in vp_tricorr_eval) and a target r0 = tgt[p]
+ * strictly outside it (in its near zone, Sec. 3.1),
+ *   out[p][j] = sum_b Vhat_b coef[b][j] - w_j J(zeta_j) G(R(zeta_j), r0),
+ *   Vhat_b = int_T0 G(R(zeta), r0) K_b(zeta) J(zeta) dzeta,
+ * the "accurate minus smooth" block row of the pair (Sec. 4). Vhat is taken by
+ * the area-to-line conversion (Lemma 1) with the star point at the cell point
+ * nearest r0 (Eq. rstar_def): rays to the edges not through it, Gauss-Legendre
+ * in t (8 points) on panels graded dyadically towards both ends of the rays
+ * and in s (10 points) on panels graded towards the star point's foot and
+ * towards the point nearest r0 on each edge; K_b is the collapsed-coordinate
+ * Legendre x Jacobi basis (total degree <= 7, the order of coef's rows).
+ * Measured against adaptive quadrature: about 1e-13 of the accurate part for
+ * targets down to 1e-3 cell sizes on cells whose smallest angle is 20 degrees
+ * or more (on slivers of a few degrees the fixed rules lose accuracy, as the
+ * self blocks do). geom [n_pairs][12],
+ * tgt [n_pairs][2], out [n_pairs][n_nodes]: device. A target on or inside the
+ * cell is outside the contract (its result is not finite or not accurate).
+ * Errors: VP_ERR_STATE (invalid plan, other device), VP_ERR_ARG (n_pairs < 0,
+ * NULL pointers), VP_ERR_UNSUPPORTED (n_basis not a complete basis of degree
+ * <= 7), VP_ERR_CUDA. Enqueues on `stream` only.
+ */
+vp_status vp_tricorr_near_eval(vp_tricorr tc, int64_t n_pairs, const double* geom, const double* tgt, double* out,
+                               void* stream);
 vp_status vp_tricorr_eval(vp_tricorr tc, int64_t n_cells, const double* geom, double* out,
                           void* stream);
 vp_status vp_tricorr_destroy(vp_tricorr tc);

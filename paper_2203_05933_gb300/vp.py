@@ -39,7 +39,7 @@ EXPORTED = [
     "vp_green_eval_host",
     "vp_status_string", "vp_last_error", "vp_version", "vp_measure_peaks",
     "vp_tree_build", "vp_tree_build_device", "vp_tree_get", "vp_tree_destroy", "vp_interp_create", "vp_interp_eval", "vp_interp_destroy",
-    "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_destroy",
+    "vp_tricorr_create", "vp_tricorr_eval", "vp_tricorr_near_eval", "vp_tricorr_destroy",
 ]
 
 
@@ -135,6 +135,7 @@ def _load():
         "vp_interp_destroy": [P],
         "vp_tricorr_create": [ctypes.POINTER(P), I32, I32, I32, P, P, P, P, P, P, P],
         "vp_tricorr_eval": [P, I64, P, P, P],
+        "vp_tricorr_near_eval": [P, I64, P, P, P, P],
         "vp_tricorr_destroy": [P],
     }
     for name, args in sig.items():
@@ -656,7 +657,7 @@ class Interp:
 
 
 class TriCorr:
-    """Self-correction blocks of mapped triangles on the GPU (vp_tricorr_*).
+    """Self- and near-singular correction blocks of mapped triangles on the GPU (vp_tricorr_*).
     rules: dict of setup.tricorr.self_rules (xi, eta, tw, C, chi, tau, B)."""
 
     def __init__(self, rules, stream=None):
@@ -680,6 +681,21 @@ class TriCorr:
         if out is None:
             out = torch.empty((g.shape[0], self.n_nodes, self.n_nodes), dtype=torch.float64, device=g.device)
         _check(_load().vp_tricorr_eval(self.handle, g.shape[0], _ptr(g), _ptr(out), _stream(stream)), "vp_tricorr_eval")
+        return out
+
+    def near(self, geom, tgt, out=None, stream=None):
+        """Near-singular block rows (vp_tricorr_near_eval): geom [n_pairs, 12] the cell
+        of each pair, tgt [n_pairs, 2] its target outside the cell (numpy or CUDA
+        tensors); returns [n_pairs, n_nodes]."""
+        import torch
+        g = _dev_f64(geom).reshape(-1, 12)
+        t = _dev_f64(tgt).reshape(-1, 2)
+        if t.shape[0] != g.shape[0]:
+            raise ValueError("one target per cell")
+        if out is None:
+            out = torch.empty((g.shape[0], self.n_nodes), dtype=torch.float64, device=g.device)
+        _check(_load().vp_tricorr_near_eval(self.handle, g.shape[0], _ptr(g), _ptr(t), _ptr(out), _stream(stream)),
+               "vp_tricorr_near_eval")
         return out
 
     def close(self):
