@@ -1208,6 +1208,8 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     up(&d_m2le, m2le);
     up(&d_mtpow_s, mtpow_s);
     up(&d_tau_pow, tau_pow);
+    longlong2* d_logint = nullptr;
+    up(&d_logint, make_logint_table());
     up(&d_fftab, fftab);
     up(&d_srho, B.srho);
     up(&d_trho, B.trho);
@@ -1318,6 +1320,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.m2le = d_m2le;
     tb.mtpow_s = d_mtpow_s;
     tb.tau_pow = d_tau_pow;
+    tb.logint = d_logint;
     tb.Hf = (const float2*)(d_fftab + offf[0]);
     tb.tpowf = (const float4*)(d_fftab + offf[1]);
     tb.mtpowf = (const float4*)(d_fftab + offf[2]);
@@ -1328,7 +1331,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
                            p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
-                           tb.log64, p->gfwd.vd, tb.m2lh, tb.mtpow_s, p->src_fix, p->tgt_fix};
+                           tb.log64, p->gfwd.vd, tb.m2lh, tb.mtpow_s, p->src_fix, p->tgt_fix, tb.logint};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf, p->gfwd.vf};
     bool ok = true;
     for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);

@@ -85,74 +85,78 @@ __device__ __forceinline__ double log_r2(double r2, const double2* __restrict__ 
     return L;
 }
 
-// log(r^2) of two points given as integers on the grid 2^-sigma (dx, dy below
-// 2^62 in magnitude), in two parts: log r^2 = Lp + Ep log 2. r^2 2^(2 sigma) =
-// dx^2 + dy^2 is formed exactly in 128-bit integers and rounded to 53 bits,
-// m 2^(n - 52) with m in [2^52, 2^53); rounding m to the nearest table point
-// c_k = 1 + k 2^-12 gives E = n or n + 1 and y = r^2 2^(2 sigma - E) in
-// [1 - 2^-13, 2), built from the bits; then as in log_r2, Lp = T_k + log1p(u),
-// u = y s_k - 1 (four FP64 operations), and the integer Ep = E - 2 sigma. The
-// square and its normalisation run on the integer pipes. r^2 = 0 (coincident
-// points) gives Lp = 0, Ep = 0.
-__device__ __forceinline__ double log_r2_fix(long long dx, long long dy, const double2* __restrict__ tab,
-                                             int two_sigma, int& Ep)
+// Logarithm in fixed point on the integer pipes (the table method of log_r2,
+// P. T. P. Tang 1990, with integer arithmetic): for x = X 2^(e - 62), X in
+// [2^62, 2^63), returns Lp with log x = Lp 2^-60 + E log 2 (E = e, or e + 1
+// when X rounds up to the next power of two). The table point c_k = 1 + k
+// 2^-12 nearest x's mantissa is chosen from X's bits; tab[k] = (S_k, T_k) with
+// S_k = round(2^62 / c_k) and T_k = round(-log(S_k 2^-62) 2^60), so that
+// log x = E log 2 + T_k 2^-60 + log1p(u) exactly for u = (X S_k) 2^-124 - 1,
+// |u| <= 2^-13, whatever the rounding of S_k. X S_k is a 125-bit product;
+// u is kept as U = u 2^75 and log1p(u) = u (1 - u (1/2 - u (1/3 - u/4))) is
+// evaluated by four high-half 64-bit products (truncation below 2^-65, each
+// product's rounding below 2^-59). No floating-point operation.
+__device__ __forceinline__ long long log_fix(unsigned long long X, int e, const longlong2* __restrict__ tab, int& E)
+{
+    unsigned long long kr = ((X >> (61 - kLog64Bits)) + 1ULL) >> 1;  // 2^12 + k, rounded; 2^13 on a carry
+    const int carry = (int)(kr >> (kLog64Bits + 1));
+    if (carry) {
+        X >>= 1;
+        kr = 1ULL << kLog64Bits;
+    }
+    E = e + carry;
+    const longlong2 st = tab[kr - (1ULL << kLog64Bits)];
+    // U = X S_k - 2^124 (|U| < 2^112) and u75 = U >> 49, from the product's halves
+    const unsigned long long plo = X * (unsigned long long)st.x;
+    const long long phi = (long long)(__umul64hi(X, (unsigned long long)st.x) - (1ULL << 60));
+    const long long u75 = (long long)(((unsigned long long)phi << 15) | (plo >> 49));
+    const long long t0 = 0x1555555555555555LL - (u75 >> 15);              // (1/3 - u/4) 2^62
+    const long long t1 = (1LL << 61) - (__mul64hi(u75, t0) >> 11);        // (1/2 - u t0) 2^62
+    const long long t2 = (1LL << 62) - (__mul64hi(u75, t1) >> 11);        // (1 - u t1) 2^62
+    return st.y + (__mul64hi(u75, t2) >> 13);                              // (T_k + u t2) 2^60
+}
+
+// log of a positive float64 through log_fix (two conversions and an FMA)
+__device__ __forceinline__ double log_via_fix(double r2, const longlong2* __restrict__ tab)
+{
+    const long long bits = __double_as_longlong(r2);
+    const int eb = (int)((bits >> 52) & 0x7ff);
+    if (r2 <= 0.0 || eb == 0 || eb == 0x7ff) return r2 == 0.0 ? 0.0 : log(r2);
+    const unsigned long long X = (((unsigned long long)bits & 0xfffffffffffffULL) | 0x10000000000000ULL) << 10;
+    int E;
+    const long long Lp = log_fix(X, eb - 1023, tab, E);
+    return fma((double)E, 0.693147180559945309417232121458, (double)Lp * 0x1p-60);
+}
+
+// log r^2 of two points on the integer grid 2^-sigma (|dx|, |dy| < 2^62), in
+// fixed point: log r^2 = Lp 2^-60 + Ep log 2. dx^2 + dy^2 is formed exactly in
+// 128-bit integers and its leading 63 bits go to log_fix (truncation below
+// 2^-62 relative); Ep = E - 2 sigma. r^2 = 0 (coincident points) gives 0, 0.
+__device__ __forceinline__ long long log_r2_int(long long dx, long long dy, const longlong2* __restrict__ tab,
+                                                int two_sigma, int& Ep)
 {
     const unsigned long long ax = (unsigned long long)(dx < 0 ? -dx : dx);
     const unsigned long long ay = (unsigned long long)(dy < 0 ? -dy : dy);
     const unsigned long long l1 = ax * ax, l2 = ay * ay;
-    unsigned long long lo = l1 + l2;
-    unsigned long long hi = __umul64hi(ax, ax) + __umul64hi(ay, ay) + (lo < l1 ? 1ULL : 0ULL);
+    const unsigned long long lo = l1 + l2;
+    const unsigned long long hi = __umul64hi(ax, ax) + __umul64hi(ay, ay) + (lo < l1 ? 1ULL : 0ULL);
     if ((hi | lo) == 0ULL) {
         Ep = 0;
-        return 0.0;
+        return 0;
     }
-    int n = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
-    const int sh = n - 52;
-    unsigned long long m;
-    int rb = 0;  // the first bit below the 53 kept
-    if (sh <= 0) {
-        m = lo << (-sh);
-    } else if (sh < 64) {
-        m = (lo >> sh) | (hi << (64 - sh));
-        rb = (int)((lo >> (sh - 1)) & 1ULL);
-    } else {
-        m = hi >> (sh - 64);
-        rb = (int)(sh == 64 ? (lo >> 63) : ((hi >> (sh - 65)) & 1ULL));
-    }
-    m += (unsigned long long)rb;
-    if (m >> 53) {  // rounded up to 2^53
-        m >>= 1;
-        ++n;
-    }
-    const unsigned long long h = m + (1ULL << (51 - kLog64Bits));  // to the nearest table point
-    const int carry = (int)(h >> 53);
-    Ep = n + carry - two_sigma;
-    const int k = (int)((h >> (52 - kLog64Bits)) & ((1ULL << kLog64Bits) - 1));
-    const double y = __longlong_as_double(
-        (long long)(((unsigned long long)(1023 - carry) << 52) | (m & 0xfffffffffffffULL)));
-    const double2 sk = tab[k];
-    const double u = fma(y, sk.x, -1.0);
-    const double b = fma(u, fma(u, 0x1.5555555555555p-2, -0.5), 1.0);  // 1 - u/2 + u^2/3
-    return fma(u, b, sk.y);
-}
-
-// round(x 2^t) by integer operations on the bits of x, for |x 2^t| < 2^62
-// (zero and subnormal x give 0)
-__device__ __forceinline__ long long round_pow2(double x, int t)
-{
-    const long long bits = __double_as_longlong(x);
-    const int E = (int)((bits >> 52) & 0x7ff);
-    if (E == 0) return 0;
-    const long long mant = (bits & 0xfffffffffffffLL) | 0x10000000000000LL;
-    const int sh = E - 1075 + t;  // x 2^t = mant 2^sh
-    long long X;
-    if (sh >= 0)
-        X = mant << sh;
-    else if (sh < -62)
-        X = 0;
+    const int n = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
+    const int sh = n - 62;
+    unsigned long long X;
+    if (sh <= 0)
+        X = lo << (-sh);
+    else if (sh < 64)
+        X = (lo >> sh) | (hi << (64 - sh));
     else
-        X = (mant + (1LL << (-sh - 1))) >> (-sh);
-    return bits < 0 ? -X : X;
+        X = hi >> (sh - 64);
+    int E;
+    const long long Lp = log_fix(X, n, tab, E);
+    Ep = E - two_sigma;
+    return Lp;
 }
 
 // ----------------------------------------------------------------------------
@@ -177,7 +181,6 @@ template <int ND>
 struct LeafStageFix {
     longlong2 xy[32];  // integer coordinates (PassGeom::cfix)
     double q[32][ND];
-    long long Q[32][ND];  // round(q 2^tq): the charges in fixed point for the exponent part
 };
 
 template <int P, int ND, bool SYM>
@@ -356,26 +359,26 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
 // takes point a of the pass and chunk positions kap, kap + K, ...), in
 // ceil(T K / 32) passes over the stream, K in {1, 2, 4, 8, 16} chosen per leaf
 // for the fewest lane-steps (every lane of an FP64 instruction costs an issue
-// slot, busy or not). A pair takes the points' integer coordinates and
-// log_r2_fix: sum_j q_j log r_j^2 = sum_j q_j Lp_j + log 2 * sum_j q_j Ep_j, the
-// first in float64 (five FP64 operations a pair with the accumulation), the
-// second exactly in 128-bit integers from the charges in fixed point,
-// Q_j = round(q_j 2^tq) with tq set per leaf by the largest |q| of its stream
-// (|Q| < 2^55, |Q Ep| < 2^62). The K partial sums of a point are added by
+// slot, busy or not). A pair: r^2 from the points' integer coordinates in
+// 128-bit integers, its logarithm in fixed point (log_r2_int: log r^2 = Lp
+// 2^-60 + Ep log 2), both parts joined in one 64-bit fixed-point value L =
+// Lp 2^(sL - 60) + Ep round(log 2 2^sL) (sL chosen per plan so that |L| <
+// 2^63), converted once and accumulated in float64: q_j L_j with one FMA, the
+// factor 2^-sL applied per point. The K partial sums of a point are added by
 // shuffles and psi += near / 2 (the log is of r^2).
 template <int P, int ND>
 __global__ void __launch_bounds__(kLeafWarps64 * 32)
     k_leaf64d(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
-              const double2* __restrict__ L, const double2* __restrict__ logtab, const double* __restrict__ etab_g,
-              int two_sigma, double* __restrict__ psi, int* __restrict__ work)
+              const double2* __restrict__ L, const longlong2* __restrict__ logtab, int two_sigma, int sL,
+              long long ln2_sL, double* __restrict__ psi, int* __restrict__ work)
 {
     constexpr int P1 = P + 1;
     extern __shared__ __align__(16) unsigned char smem64d[];
-    double2* tab = reinterpret_cast<double2*>(smem64d);                      // [1 << kLog64Bits]
-    double* etab = reinterpret_cast<double*>(tab + (1 << kLog64Bits));       // [2 * kEBias]
-    LeafStageFix<ND>* stage = reinterpret_cast<LeafStageFix<ND>*>(etab + 2 * kEBias);
+    longlong2* tab = reinterpret_cast<longlong2*>(smem64d);                  // [1 << kLog64Bits] (S_k, T_k)
+    LeafStageFix<ND>* stage =
+        reinterpret_cast<LeafStageFix<ND>*>(smem64d + (size_t)(1 << kLog64Bits) * sizeof(longlong2) +
+                                            2 * kEBias * sizeof(double));
     for (int i = threadIdx.x; i < (1 << kLog64Bits); i += blockDim.x) tab[i] = logtab[i];
-    for (int i = threadIdx.x; i < 2 * kEBias; i += blockDim.x) etab[i] = etab_g[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     LeafStageFix<ND>& st = stage[threadIdx.x >> 5];
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                 const double dx = z.x - cD.x, dy = z.y - cD.y;
                 const double r2 = fma(dx, dx, dy * dy);
                 const double2 v = make_double2(dx / r2 * RD, -dy / r2 * RD);
-                const double lg = 0.5 * log_r2(r2, tab, etab);
+                const double lg = 0.5 * log_via_fix(r2, tab);
                 const double2* MD = M + (int64_t)D * P1 * ND;
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
@@ -462,28 +465,6 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                 ++ecur;
             }
         };
-        // the scale of the fixed-point charges: the largest |q| of the stream
-        int tq[ND];
-        {
-            unsigned int mx[ND];
-#pragma unroll
-            for (int d = 0; d < ND; ++d) mx[d] = 0u;
-            int ecur = u0, ebase = 0;
-            for (int c0 = 0; c0 < S; c0 += 32) {
-                if (c0 + lane < S) {
-                    const int j = charge_at(ecur, ebase, c0 + lane);
-#pragma unroll
-                    for (int d = 0; d < ND; ++d)
-                        mx[d] = max(mx[d], (unsigned int)__double2hiint(q[(int64_t)j * ND + d]) & 0x7fffffffu);
-                }
-                advance(ecur, ebase, c0 + 32);
-            }
-#pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                const unsigned int m = __reduce_max_sync(0xffffffffu, mx[d]);
-                tq[d] = 54 - ((int)(m >> 20) - 1023);  // |q| < 2^(ex + 1), ex = (m >> 20) - 1023: |Q| < 2^55
-            }
-        }
         // the split with the fewest lane-steps
         const int full = S >> 5, rem = S & 31;
         int K = 1;
@@ -501,13 +482,9 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
             const int ti = p0 + a;
             const bool valid = ti < T;
             const longlong2 z = valid ? g.efix[e0 + ti] : make_longlong2(0, 0);
-            double near[ND];
-            __int128 ne[ND];
+            double near[ND];  // sum q L, L in units of 2^-sL
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                near[d] = 0.0;
-                ne[d] = 0;
-            }
+            for (int d = 0; d < ND; ++d) near[d] = 0.0;
             int ecur = u0, ebase = 0;
             for (int c0 = 0; c0 < S; c0 += 32) {
                 const int n = min(32, S - c0);
@@ -516,11 +493,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                     const int j = charge_at(ecur, ebase, c0 + lane);
                     st.xy[lane] = g.cfix[j];
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        const double qj = q[(int64_t)j * ND + d];
-                        st.q[lane][d] = qj;
-                        st.Q[lane][d] = round_pow2(qj, tq[d]);
-                    }
+                    for (int d = 0; d < ND; ++d) st.q[lane][d] = q[(int64_t)j * ND + d];
                 }
                 advance(ecur, ebase, c0 + 32);
                 __syncwarp();
@@ -529,35 +502,23 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
                     for (int j = kap; j < n; j += K) {
                         const longlong2 sp = st.xy[j];
                         int Ep;
-                        const double Lp = log_r2_fix(z.x - sp.x, z.y - sp.y, tab, two_sigma, Ep);
+                        const long long Lp = log_r2_int(z.x - sp.x, z.y - sp.y, tab, two_sigma, Ep);
+                        const double Lv = (double)((Lp >> (60 - sL)) + (long long)Ep * ln2_sL);
 #pragma unroll
-                        for (int d = 0; d < ND; ++d) {
-                            near[d] = fma(st.q[j][d], Lp, near[d]);
-                            ne[d] += (__int128)(st.Q[j][d] * (long long)Ep);
-                        }
+                        for (int d = 0; d < ND; ++d) near[d] = fma(st.q[j][d], Lv, near[d]);
                     }
                 }
             }
             for (int off = 1; off < K; off <<= 1) {  // warp-uniform
 #pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    near[d] += __shfl_xor_sync(0xffffffffu, near[d], off);
-                    const unsigned long long lo = (unsigned long long)ne[d];
-                    const long long hi = (long long)(ne[d] >> 64);
-                    const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, off);
-                    const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, off);
-                    ne[d] += ((__int128)hi2 << 64) + (__int128)lo2;
-                }
+                for (int d = 0; d < ND; ++d) near[d] += __shfl_xor_sync(0xffffffffu, near[d], off);
             }
             if (valid && kap == 0) {
+                const double half = ldexp(0.5, -sL);
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
-                    // log 2 * sum Q Ep 2^-tq, the 128-bit sum converted once
-                    const double es = fma((double)(long long)(ne[d] >> 64), 0x1p64,
-                                          (double)(unsigned long long)ne[d]);
-                    const double tot = fma(es, ldexp(0.693147180559945309417232121458, -tq[d]), near[d]);
                     double* o = psi + (int64_t)(e0 + ti) * ND + d;
-                    *o = fma(0.5, tot, *o);
+                    *o = fma(half, near[d], *o);
                 }
             }
         }
@@ -1441,8 +1402,13 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         const int rblocks = std::max(1, std::min((g.n_eval + 255) / 256, 152 * 32));
         k_sym_reduce64<ND><<<rblocks, 256, 0, s>>>(t, g, slots, ws.psi);
     } else {
-        k_leaf64d<P, ND><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
-                                                                            tab.elog64, 2 * g.fix_sigma, ws.psi,
+        // the fixed-point log's scale: |Lp 2^(sL-60) + Ep log 2 2^sL| < 2^63 for |Ep| <= max(2 sigma, 127)
+        const int maxE = std::max(2 * g.fix_sigma, 127);
+        int sL = 60;
+        while (sL > 40 && std::ldexp((double)maxE * 0.6931471805599453 + 1.0, sL) >= 0x1p62) --sL;
+        const long long ln2_sL = std::llround(std::ldexp(0.693147180559945309417232121458176568L, sL));
+        k_leaf64d<P, ND><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.logint,
+                                                                            2 * g.fix_sigma, sL, ln2_sL, ws.psi,
                                                                             ws.work);
     }
     if (tm) tm->end(id);
@@ -1652,6 +1618,21 @@ std::vector<double2> make_l2l64_table(int P)
 // s_k = RN(1/c_k), T_k = -log(s_k) rounded once from extended precision
 // (long double: at least 64 significant bits on the targets this builds for);
 // etab[i] = (i - 64) log 2.
+// The fixed-point logarithm's table (log_fix): S_k = round(2^62 / c_k), c_k = 1 +
+// k 2^-12, and T_k = round(-log(S_k 2^-62) 2^60), in long double.
+std::vector<longlong2> make_logint_table()
+{
+    const int n = 1 << kLog64Bits;
+    std::vector<longlong2> tab((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        const long double c = 1.0L + std::ldexp((long double)k, -kLog64Bits);
+        const long double S = std::nearbyint(std::ldexp(1.0L, 62) / c);
+        const long double T = -std::log(std::ldexp(S, -62));
+        tab[(size_t)k] = make_longlong2((long long)S, (long long)std::llround(std::ldexp(T, 60)));
+    }
+    return tab;
+}
+
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab)
 {
     const int n = 1 << kLog64Bits;

@@ -91,6 +91,7 @@ struct DevTables {
     const int32_t* m2le = nullptr;  // [32] row exponents of those digits
     const double2* mtpow_s = nullptr; // [49][P1] (-t_o / tau)^k, tau = 2^-1.5            (float64 M2L)
     const double* tau_pow = nullptr;  // [P1] tau^k
+    const longlong2* logint = nullptr; // [1 << kLog64Bits] (S_k, T_k) of the fixed-point logarithm
     // float-float copies for the FP32-pipe M2L
     const float2* Hf = nullptr;     // [P1][P1]
     const float4* tpowf = nullptr;  // [49][P1] complex (re_h, re_l, im_h, im_l)
@@ -222,6 +223,7 @@ cudaError_t launch_point_powers(int P, const DevTree& t, const int32_t* rng, con
 cudaError_t launch_fmm64(int P, int nd, const DevTree& t, const DevTables& tab, const PassGeom& g, Workspace& ws,
                          bool gradient, PhaseTimer* timer, cudaStream_t s);
 void make_log64_tables(std::vector<double2>& tab, std::vector<double>& etab);
+std::vector<longlong2> make_logint_table();
 std::vector<double2> make_m2m64_table(int P);
 std::vector<double2> make_l2l64_table(int P);
 void make_m2l_tensor_tables(int P, std::vector<uint16_t>& hd, std::vector<int32_t>& eh, std::vector<double2>& mts,
