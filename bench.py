@@ -43,14 +43,15 @@ UNIT = "Mpoints/s"
 # costs 7 flops + 20 flop-equivalents for one FP64 log; P2M and L2P 8P flops per
 # point each; an M2L translation 8 (P+1)^2 flops; a correction nonzero 2 flops.
 P2P_FLOP_PER_PAIR = 27.0
-# FP64 pipe operations (DFMA, DADD, DMUL: one issue slot each) the float64
-# kernels spend: per directed pair of the near field (differences, r^2, the
-# table logarithm of 5 operations, one accumulation) and per distance evaluated
-# once for both directions (one more accumulation); L2P per point and
-# coefficient (one complex multiply-add).
-F64_OPS_PAIR = 10.0
+# FP64 pipe operations (DFMA, DADD, DMUL, conversions: one issue slot each) the
+# float64 kernels spend: per directed pair of the near field (one conversion of
+# the fixed-point logarithm, one FMA per density: r^2 and the logarithm run on
+# the integer pipes) and per distance evaluated once for both directions
+# (differences, r^2, the table logarithm of 5 operations, two accumulations);
+# L2P per point and coefficient (two FMAs from the stored powers).
+F64_OPS_PAIR = 2.0
 F64_OPS_SYM = 11.0
-F64_OPS_L2P_PER_COEF = 4.0
+F64_OPS_L2P_PER_COEF = 2.0
 # float-float: FP32 operations per evaluated distance (the kernel's model)
 P2P_FF_OPS_PER_PAIR = 77.0
 P2P_FF_OPS_REVERSE = 14.0
@@ -61,7 +62,7 @@ FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12  # FP32/INT32 lane-operations per sec
 # of the plan info, unit name, P, densities, kernel). Only a phase whose kernel
 # has not changed since its capture is listed; others report traffic null.
 PROFILED_TRAFFIC = {
-    "leaf": (485.7, "n_tgt", "target", 24, 1, "k_leaf64d<24, 1>"),
+    "leaf": (486.0, "n_tgt", "target", 24, 1, "k_leaf64d<24, 1>"),
     "m2l": (22.54, "n_v_pairs", "V-list pair", 24, 1, "k_m2l64<24, 1>"),
     "upward": (413.4, "n_src", "source", 24, 1, "k_p2m64<24, 1>"),
     "out": (8.63, "nnz", "nonzero", 24, 1, "k_out_grouped64<1>"),
@@ -89,15 +90,16 @@ def roofline_models(info, ndens, fp64_tflops):
     ops_peak = fp64_tflops / 2.0  # T FP64 pipe operations per second
     hbm, hbm_src = hbm_peak()
     return {
-        "leaf": {"kernel": "k_leaf64 (float64 P2P with the table logarithm + L2P + M2P) and k_sym_reduce64",
+        "leaf": {"kernel": "k_leaf64d (P2P with integer r^2 and the fixed-point logarithm, one FP64 FMA a pair; "
+                           "L2P + M2P) or, for targets at the nodes, k_leaf64 + k_sym_reduce64",
                  "flop": (pairs * P2P_FLOP_PER_PAIR + info.n_tgt * 8.0 * P) * ndens,
                  "ops": (one * (F64_OPS_PAIR + ndens - 1) + both * (F64_OPS_SYM + 2 * (ndens - 1))
                          + info.n_tgt * F64_OPS_L2P_PER_COEF * P * ndens),
                  "units": pairs, "ops_peak": ops_peak,
                  "per_unit": f"{P2P_FLOP_PER_PAIR:.0f} flop-eq per directed pair (7 + 20 for the log) + 8P per "
-                             f"target for L2P; the kernel issues {F64_OPS_PAIR:.0f} FP64 ops per directed pair, "
-                             f"{F64_OPS_SYM:.0f} per distance serving both directions ({evals} evaluations for "
-                             f"{pairs} directed pairs)"},
+                             f"target for L2P; the kernels issue {F64_OPS_PAIR:.0f} FP64 ops per directed pair "
+                             f"(plus about 100 integer instructions), {F64_OPS_SYM:.0f} per distance serving both "
+                             f"directions ({evals} evaluations for {pairs} directed pairs)"},
         "m2l": {"kernel": "k_m2l64 (float64 scaled-Hankel M2L + P2L, G V-list entries per warp)",
                 "flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens,
                 "ops": info.n_v_pairs * (2.0 * P * P + 10.0 * P) * ndens, "units": info.n_v_pairs,
@@ -950,12 +952,16 @@ def main():
     dom = max(rl_all, key=lambda k: rl_all[k]["ms"]) if rl_all else None
     roofline = dict(rl_all.get(dom, {}), phase=dom)
     roofline["note"] = ("frac counts the survey's 27 flop-equivalents per directed near-field pair (20 for a log) "
-                        "against the measured FP64 FMA peak; the kernel spends 5 FP64 operations per log, so frac "
-                        "can exceed 1. pipe_frac is the kernel's own FP64 operation count against the same peak.")
+                        "against the measured FP64 FMA peak; the kernel forms r^2 and the logarithm on the integer "
+                        "pipes (exact r^2, fixed-point log) and spends one conversion and one FP64 FMA per pair, so "
+                        "frac exceeds 1. pipe_frac is the kernel's own FP64 operation count against the same peak.")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "arith": ("float64 inputs and results; near-field r^2 exact in 128-bit integers and its logarithm in "
+                  "fixed point (2^-55) on the integer pipes, accumulated in float64; the M2L contraction as exact "
+                  "integer digit products on the bf16 tensor cores (62-bit operands); every other step IEEE float64"),
         "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
                    "correction": "own + near cells" if args.csr == "near" or args.workload == "disk" else "own cell",
                    "ndens": 1, "p_fmm": info.p_fmm, "leaf": info.leaf, "levels": info.n_levels,
