@@ -917,14 +917,17 @@ vp_status build_grouped(vp_plan p, Built& B, cudaStream_t s)
     A.cols = d_cols;
     VP_CUDA(launch_group_cols(A.ngroups, d_r0, d_c0, d_row, d_col, d_cols, s));
     if (p->arith == Arith::kF64) {
-        double* vd = nullptr;
-        VP_CUDA(p->alloc(&vd, (size_t)prow[(size_t)nrows]));
-        VP_CUDA(launch_pad_values(nrows, d_row, d_prow, d_val, vd, nullptr, s));
-        A.vd = vd;
+        int2* vi = nullptr;
+        int32_t* vexp = nullptr;
+        VP_CUDA(p->alloc(&vi, (size_t)prow[(size_t)nrows]));
+        VP_CUDA(p->alloc(&vexp, (size_t)std::max<int64_t>(nrows, 1)));
+        VP_CUDA(launch_fix_values(nrows, d_row, d_prow, d_val, vi, vexp, s));
+        A.vi = vi;
+        A.vexp = vexp;
     } else {
         float2* vf = nullptr;
         VP_CUDA(p->alloc(&vf, (size_t)prow[(size_t)nrows]));
-        VP_CUDA(launch_pad_values(nrows, d_row, d_prow, d_val, nullptr, vf, s));
+        VP_CUDA(launch_pad_values(nrows, d_row, d_prow, d_val, vf, s));
         A.vf = vf;
     }
     // positions of every column among the groups' column lists, ascending
@@ -1331,7 +1334,7 @@ vp_status finalize(vp_plan p, Built& B, int P, cudaStream_t s)
     tb.zpowf = (const float2*)(d_fftab + offf[7]);
     const void* vec16[] = {tb.tpow, tb.mtpow, tb.zpow, tb.logtab, tb.tpowf, tb.mtpowf, p->src_xy, p->tgt_xy,
                            p->src_rho, p->tgt_rho, p->ws.M, p->ws.Mf, p->ws.L, p->ws.Lf, p->dt.u_off, p->dt.x_off,
-                           tb.log64, p->gfwd.vd, tb.m2lh, tb.mtpow_s, p->src_fix, p->tgt_fix, tb.logint};
+                           tb.log64, p->gfwd.vi, tb.m2lh, tb.mtpow_s, p->src_fix, p->tgt_fix, tb.logint};
     const void* vec8[] = {tb.Hf, tb.log2of, tb.invlf, tb.Bmf, tb.Blf, tb.zpowf, p->ws.qf, p->ws.xf, p->gfwd.vf};
     bool ok = true;
     for (const void* q : vec16) ok = ok && ((uintptr_t)q % 16 == 0);
@@ -1671,10 +1674,9 @@ extern "C" {
 namespace {
 
 // Grouped correction product of one density chunk: out = A x (mode as in
-// launch_out_grouped), x in caller order with leading dimension ld_x, converted
-// to hi/lo floats first. Counts its launches. (An FP64 form of the product, one
-// DFMA per nonzero, was measured at 1.74 ms against 0.93 ms on the 1.09 M disk,
-// and slowed the FMM beside it: the FP64 pipe is too narrow for it on GB300.)
+// launch_out_grouped), x in caller order with leading dimension ld_x: exact
+// fixed-point sums for float64 plans; float-float plans convert x to hi/lo
+// floats first. Counts its launches.
 vp_status grouped_apply(vp_plan p, int nd, const DevGroupedCSR& A, int64_t ncols, const int32_t* inv,
                         const double* w, const double* psi, const double* x, int64_t ld_x, double* out,
                         int64_t ld_out, int mode, int max_blocks, cudaStream_t s)

@@ -9,8 +9,8 @@
 // the device straight from the caller's CSR: a check kernel (columns in range,
 // finite values), a row-equality flag per row (the host turns the flags into
 // group boundaries), a gather of each group's column list, and a copy of the
-// values into the padded layout (float64, or hi/lo floats for float-float
-// plans). No transposed copy of the values is made: Pi^T g is computed per
+// values into the padded layout (per-row fixed point for float64 plans, hi/lo
+// floats for float-float plans). No transposed copy of the values is made: Pi^T g is computed per
 // group as the transposed block product into a buffer of partial sums (one
 // entry per stored column position), then gathered per column over the
 // positions where it appears, in ascending order (deterministic).
@@ -80,24 +80,44 @@ __global__ void k_group_cols(int32_t ngroups, const int32_t* __restrict__ g_r0, 
     }
 }
 
-// values into the padded layout (row r at prow[r], length padded to even with a zero)
-template <bool F64>
+// values into the padded layout (row r at prow[r], length padded to even with a
+// zero) as hi/lo floats
 __global__ void k_pad_values(int64_t nrows, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ prow,
-                             const double* __restrict__ val, double* __restrict__ vd, float2* __restrict__ vf)
+                             const double* __restrict__ val, float2* __restrict__ vf)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
         const int64_t a = rowptr[r], len = rowptr[r + 1] - a, o = prow[r], plen = prow[r + 1] - o;
         for (int64_t k = lane; k < plen; k += 32) {
-            const double v = k < len ? val[a + k] : 0.0;
-            if (F64) {
-                vd[o + k] = v;
-            } else {
-                const ff::F f = ff::from_double(v);
-                vf[o + k] = make_float2(f.h, f.l);
-            }
+            const ff::F f = ff::from_double(k < len ? val[a + k] : 0.0);
+            vf[o + k] = make_float2(f.h, f.l);
         }
+    }
+}
+
+// The same layout in per-row fixed point (one warp per row): with 2^(e-1) <=
+// max_k |v_rk| < 2^e, V = rint(v 2^(52-e)), so |V| <= 2^52 and the rounding error
+// is at most 2^-52 of the row's largest value (the row's own float64 rounding is
+// 2^-53 of it); vexp[r] = e - 52. Stored as {V mod 2^26, V >> 26}: the product
+// kernel multiplies 26-bit pieces (exact 64-bit products) and keeps its sums
+// exact. A zero row stores zeros with vexp = 0.
+__global__ void k_fix_values(int64_t nrows, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ prow,
+                             const double* __restrict__ val, int2* __restrict__ vi, int32_t* __restrict__ vexp)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
+        const int64_t a = rowptr[r], len = rowptr[r + 1] - a, o = prow[r], plen = prow[r + 1] - o;
+        double mx = 0.0;
+        for (int64_t k = lane; k < len; k += 32) mx = fmax(mx, fabs(val[a + k]));
+        for (int s = 16; s > 0; s >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+        const int e = mx > 0.0 ? ilogb(mx) + 1 : 52;
+        for (int64_t k = lane; k < plen; k += 32) {
+            const long long V = k < len ? __double2ll_rn(ldexp(val[a + k], 52 - e)) : 0LL;
+            vi[o + k] = make_int2((int)(V & 0x3ffffff), (int)(V >> 26));
+        }
+        if (lane == 0) vexp[r] = e - 52;
     }
 }
 
@@ -111,8 +131,9 @@ template <int ND, bool F64>
 __global__ void __launch_bounds__(kAdjThreads)
     k_adj_partial(DevGroupedCSR A, const double* __restrict__ x, int64_t ld_x, double* __restrict__ partial)
 {
-    // x of the staged rows: float64, or as hi/lo floats for the float-float values
-    // (converted once per row here, not once per nonzero)
+    // x of the staged rows: float64 times the row's fixed-point scale (the values
+    // are then the exact integers V), or as hi/lo floats for the float-float
+    // values (converted once per row here, not once per nonzero)
     __shared__ double xs[kAdjRows][ND];
     float2(*xf)[ND] = reinterpret_cast<float2(*)[ND]>(&xs[0][0]);
     for (int g = blockIdx.x; g < A.ngroups; g += gridDim.x) {
@@ -135,7 +156,7 @@ __global__ void __launch_bounds__(kAdjThreads)
                     const int rr = i / ND, d = i % ND;
                     const double xv = x[d * ld_x + rb + rr];
                     if (F64) {
-                        xs[rr][d] = xv;
+                        xs[rr][d] = ldexp(xv, A.vexp[rb + rr]);  // the row's scale, exact
                     } else {
                         const ff::F f = ff::from_double(xv);
                         xf[rr][d] = make_float2(f.h, f.l);
@@ -146,7 +167,8 @@ __global__ void __launch_bounds__(kAdjThreads)
                     for (int rr = 0; rr < nr; ++rr) {
                         const int64_t o = A.rowptr[rb + rr] + k;
                         if (F64) {
-                            const double v = A.vd[o];
+                            const int2 vv = A.vi[o];
+                            const double v = (double)(((long long)vv.y << 26) + vv.x);  // |V| <= 2^52: exact
 #pragma unroll
                             for (int d = 0; d < ND; ++d) acc[d] = fma(v, xs[rr][d], acc[d]);
                         } else {
@@ -244,13 +266,18 @@ cudaError_t launch_group_cols(int32_t ngroups, const int32_t* g_r0, const int64_
 }
 
 cudaError_t launch_pad_values(int64_t nrows, const int64_t* rowptr, const int64_t* prow, const double* val,
-                              double* vd, float2* vf, cudaStream_t s)
+                              float2* vf, cudaStream_t s)
 {
     if (nrows == 0) return cudaSuccess;
-    if (vd)
-        k_pad_values<true><<<grid_for(nrows, 8), 256, 0, s>>>(nrows, rowptr, prow, val, vd, nullptr);
-    else
-        k_pad_values<false><<<grid_for(nrows, 8), 256, 0, s>>>(nrows, rowptr, prow, val, nullptr, vf);
+    k_pad_values<<<grid_for(nrows, 8), 256, 0, s>>>(nrows, rowptr, prow, val, vf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix_values(int64_t nrows, const int64_t* rowptr, const int64_t* prow, const double* val, int2* vi,
+                              int32_t* vexp, cudaStream_t s)
+{
+    if (nrows == 0) return cudaSuccess;
+    k_fix_values<<<grid_for(nrows, 8), 256, 0, s>>>(nrows, rowptr, prow, val, vi, vexp);
     return cudaGetLastError();
 }
 

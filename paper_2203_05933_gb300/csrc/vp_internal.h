@@ -133,9 +133,12 @@ struct DevGroupedCSR {
     const int32_t* g_r0 = nullptr;     // [ngroups + 1] first row of each group
     const int64_t* g_c0 = nullptr;     // [ngroups + 1] offsets into cols
     const int32_t* cols = nullptr;     // column list of each group
-    const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf / vd
+    const int64_t* rowptr = nullptr;   // [nrows + 1] offsets into vf / vi
     const float2* vf = nullptr;        // [nnz] values as hi/lo floats (float-float plans)
-    const double* vd = nullptr;        // [nnz] values as float64 (float64 plans)
+    // float64 plans: the values of row r in fixed point, v = V 2^vexp[r] with
+    // |V| <= 2^52, stored as {V mod 2^26, V >> 26} (both int32)
+    const int2* vi = nullptr;          // [nnz]
+    const int32_t* vexp = nullptr;     // [nrows]
     // transposed product: the positions p (into cols) where column c appears,
     // ascending, for c < adj_ncols
     int64_t adj_ncols = 0;
@@ -235,9 +238,13 @@ cudaError_t launch_csr_check(int64_t nnz, const int32_t* col, const double* val,
 cudaError_t launch_row_same(int64_t nrows, const int64_t* rowptr, const int32_t* col, uint8_t* same, cudaStream_t s);
 cudaError_t launch_group_cols(int32_t ngroups, const int32_t* g_r0, const int64_t* g_c0, const int64_t* rowptr,
                               const int32_t* col, int32_t* cols, cudaStream_t s);
-// exactly one of vd (float64) and vf (hi/lo floats) is non-NULL
+// the values into the padded layout as hi/lo floats (float-float plans)
 cudaError_t launch_pad_values(int64_t nrows, const int64_t* rowptr, const int64_t* prow, const double* val,
-                              double* vd, float2* vf, cudaStream_t s);
+                              float2* vf, cudaStream_t s);
+// the values into the padded layout in per-row fixed point (float64 plans: vi, vexp
+// of DevGroupedCSR)
+cudaError_t launch_fix_values(int64_t nrows, const int64_t* rowptr, const int64_t* prow, const double* val, int2* vi,
+                              int32_t* vexp, cudaStream_t s);
 // out (columns, caller order) = Pi^T x in the modes of launch_out_grouped (inv, w_sorted,
 // psi index the columns' tree positions); partial: [g_c0[ngroups]][nd] scratch.
 cudaError_t launch_adj_grouped(int nd, const DevGroupedCSR& A, bool f64, const double* x, int64_t ld_x,

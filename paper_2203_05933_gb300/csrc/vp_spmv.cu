@@ -1,14 +1,15 @@
 // Correction apply (a7): out = -(1/2pi) psi + Pi f, the sparse map of the
 // per-cell corrections "accurate minus smooth" (arXiv 2203.05933, Sec. 4,
-// paragraph after Eq. nsrcs): in float64 (k_out_grouped64, the default) or on
-// the FP32 pipes in float-float arithmetic (k_out_grouped, VP_FLAG_FF).
+// paragraph after Eq. nsrcs): float64 plans as exact fixed-point sums on the
+// integer pipes (k_out_grouped64, the default), float-float plans on the FP32
+// pipes (k_out_grouped, VP_FLAG_FF).
 //
 // The rows of one cell share their column list (every node of a cell couples
 // to the nodes of the same near cells), so the plan stores each distinct
 // column list once per group of consecutive rows. One block per group gathers
-// x[:, cols] once into shared memory as hi/lo floats; each warp then streams
-// its rows' values (8 bytes per nonzero, coalesced) and accumulates with
-// TwoProd/TwoSum. HBM traffic is one read of the values plus the outputs.
+// x[:, cols] once into shared memory; each warp then streams its rows' values
+// (8 bytes per nonzero, coalesced). HBM traffic is one read of the values plus
+// the outputs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -146,13 +147,143 @@ __global__ void __launch_bounds__(kGroupThreads)
     }
 }
 
-// Float64 form (float64 plans): values A.vd (8 bytes per nonzero, rows padded to
-// even lengths, so each row starts on 16 bytes), one DFMA per nonzero and
-// density. Eight lanes share a row (four rows per warp at a time), so that the
-// closing reduction costs three shuffle-adds per row against a row length of a
-// few hundred; the rows of a group read the same staged columns (broadcast).
+// Float64 plans. The values are stored in per-row fixed point (A.vi, A.vexp:
+// v = V 2^vexp[r], |V| <= 2^52, as the 26-bit pieces {V mod 2^26, V >> 26}); one
+// block per group stages x at the group's columns and puts each density in
+// fixed point too (X = x 2^(52-e), e from the largest staged |x|, so |X| <=
+// 2^52 and the rounding is at most 2^-53 of that largest value). A nonzero then
+// costs four 32x32-bit multiply-adds into three 64-bit sums (the products of the
+// high pieces, the cross products, the low pieces), each exact; per row the lane
+// sums combine into one exact 128-bit integer, which is rounded to float64 once.
+// So the row's result is the correctly rounded sum of the stored products (up
+// to the last conversion), and the integer pipes carry the work that would
+// otherwise take one DFMA per nonzero (the FP64 unit, 2 per clock per SM on
+// GB300, is slower than the values stream from HBM). Eight lanes share a row
+// (four rows per warp at a time); the rows of a group read the same staged
+// columns (broadcast).
+//
+// Groups whose columns do not fit the staging buffer, longer than kFixMaxM, or
+// whose x holds a non-finite value take the float64 loop instead: the same
+// stored values, each converted back to float64 exactly, one DFMA per nonzero.
 constexpr int kRowLanes64 = 8;
+// Block size: one group per block at a time, so small blocks (many resident per
+// SM, each with its own staging buffer) keep more value loads in flight than
+// large ones waiting at their barriers; with more densities the rows do more
+// work per value and larger blocks share one staging.
+template <int ND>
+constexpr int group64_threads()
+{
+    return ND == 1 ? 64 : ND == 2 ? 128 : 256;
+}
+// the longest column list staged (longer groups take the float64 loop from global memory)
+constexpr int kStage64MaxM = 3072;
+// the longest column list of the fixed-point loop: a lane then sums at most 512
+// products, which keeps every 64-bit partial sum below 2^63
+constexpr int kFixMaxM = 4096;
 
+// c + a b, 32 x 32 -> 64-bit signed
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c)
+{
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// A 128-bit two's-complement integer (hi, lo) as float64: correctly rounded when
+// it fits 64 bits; else |value| >= 2^63 and the two roundings stay within two
+// units in the last place.
+__device__ __forceinline__ double int128_to_double(long long hi, unsigned long long lo)
+{
+    if (hi == ((long long)lo >> 63)) return (double)(long long)lo;
+    return fma((double)hi, 0x1p64, (double)lo);  // |hi| < 2^53: exact
+}
+
+template <int ND>
+__device__ __forceinline__ void store_row64(int r, const double* v, const int32_t* __restrict__ inv,
+                                            const double* __restrict__ w_sorted, const double* __restrict__ psi,
+                                            double* __restrict__ out, int64_t ld_out, int mode)
+{
+    if (mode == kOutWithPsi) {
+        const int32_t ri = inv[r];
+        const double wv = w_sorted ? w_sorted[ri] : 1.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], v[d]);
+    } else if (mode == kOutAccumulate) {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) out[d * ld_out + r] += v[d];
+    } else {
+#pragma unroll
+        for (int d = 0; d < ND; ++d) out[d * ld_out + r] = v[d];
+    }
+}
+
+// The fixed-point loop: X[d * smem_m + k] = {X mod 2^26, X >> 26} of density d at
+// column k (even smem_m, a zero after odd m), x = X 2^xsc[d].
+template <int ND>
+__device__ __forceinline__ void grouped_rows_fix(const DevGroupedCSR& A, int r0, int r1, int m, int smem_m,
+                                                 const int2* __restrict__ X, const int* __restrict__ xsc,
+                                                 const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
+                                                 const double* __restrict__ psi, double* __restrict__ out,
+                                                 int64_t ld_out, int mode, int lane, int warp, int nw)
+{
+    constexpr int RPW = 32 / kRowLanes64;  // rows per warp at a time
+    constexpr int U = ND <= 2 ? 8 : 2;     // value pairs per lane in flight
+    const int li = lane % kRowLanes64, sub = lane / kRowLanes64;
+    const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
+    for (int rb = r0 + warp * RPW; rb < r1; rb += nw * RPW) {
+        const int r = rb + sub;
+        const bool live = r < r1;
+        long long hh[ND], md[ND], ll[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) hh[d] = md[d] = ll[d] = 0;
+        if (live) {
+            const int4* vrow = reinterpret_cast<const int4*>(A.vi + A.rowptr[r]);  // rows start on 16 bytes
+            for (int q0 = li; q0 < np; q0 += U * kRowLanes64) {
+                int4 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int qp = q0 + u * kRowLanes64;
+                    v[u] = qp < np ? __ldcs(vrow + qp) : make_int4(0, 0, 0, 0);  // streamed once
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int qp = q0 + u * kRowLanes64;
+                    if (qp >= np) continue;
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const int4 xv = *reinterpret_cast<const int4*>(X + d * smem_m + 2 * qp);
+                        ll[d] = mad_wide(v[u].x, xv.x, ll[d]);
+                        ll[d] = mad_wide(v[u].z, xv.z, ll[d]);
+                        md[d] = mad_wide(v[u].x, xv.y, md[d]);
+                        md[d] = mad_wide(v[u].y, xv.x, md[d]);
+                        md[d] = mad_wide(v[u].z, xv.w, md[d]);
+                        md[d] = mad_wide(v[u].w, xv.z, md[d]);
+                        hh[d] = mad_wide(v[u].y, xv.y, hh[d]);
+                        hh[d] = mad_wide(v[u].w, xv.w, hh[d]);
+                    }
+                }
+            }
+        }
+        double res[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            // the lane's sum hh 2^52 + md 2^26 + ll, then the row's eight lanes, in 128 bits
+            __int128 t = ((__int128)hh[d] << 52) + ((__int128)md[d] << 26) + (__int128)ll[d];
+#pragma unroll
+            for (int o = kRowLanes64 / 2; o > 0; o >>= 1) {
+                const long long th = __shfl_xor_sync(0xffffffffu, (long long)(t >> 64), o);
+                const unsigned long long tl = __shfl_xor_sync(0xffffffffu, (unsigned long long)t, o);
+                t += ((__int128)th << 64) | (__int128)tl;
+            }
+            res[d] = live ? ldexp(int128_to_double((long long)(t >> 64), (unsigned long long)t), A.vexp[r] + xsc[d])
+                          : 0.0;
+        }
+        if (live && li == 0) store_row64<ND>(r, res, inv, w_sorted, psi, out, ld_out, mode);
+    }
+}
+
+// The float64 loop over the same values (V converted exactly, the row's scale
+// applied to the sum). STAGED: x[:, cols] as float64 in F; else gathered from x.
 template <int ND, bool STAGED>
 __device__ __forceinline__ void grouped_rows64(const DevGroupedCSR& A, int r0, int r1, int64_t c0, int m, int smem_m,
                                                const double* __restrict__ F, const int32_t* __restrict__ inv,
@@ -160,31 +291,32 @@ __device__ __forceinline__ void grouped_rows64(const DevGroupedCSR& A, int r0, i
                                                const double* __restrict__ x, int64_t ld_x, double* __restrict__ out,
                                                int64_t ld_out, int mode, int lane, int warp, int nw)
 {
-    constexpr int RPW = 32 / kRowLanes64;  // rows per warp at a time
+    constexpr int RPW = 32 / kRowLanes64;
+    constexpr int U = ND <= 2 ? 4 : 2;
     const int li = lane % kRowLanes64, sub = lane / kRowLanes64;
-    const int np = (m + 1) >> 1;  // value pairs per row (the padding value is zero)
+    const int np = (m + 1) >> 1;
     for (int rb = r0 + warp * RPW; rb < r1; rb += nw * RPW) {
         const int r = rb + sub;
         const bool live = r < r1;
-        // U value pairs per lane in flight (loads issued before the arithmetic)
-        constexpr int U = ND <= 2 ? 4 : 2;
         double acc0[ND], acc1[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc0[d] = acc1[d] = 0.0;
         if (live) {
-            const double2* vrow = reinterpret_cast<const double2*>(A.vd + A.rowptr[r]);
+            const int4* vrow = reinterpret_cast<const int4*>(A.vi + A.rowptr[r]);
             for (int q0 = li; q0 < np; q0 += U * kRowLanes64) {
-                double2 v[U];
+                int4 v[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int qp = q0 + u * kRowLanes64;
-                    v[u] = qp < np ? __ldcs(vrow + qp) : make_double2(0.0, 0.0);  // streamed once
+                    v[u] = qp < np ? __ldcs(vrow + qp) : make_int4(0, 0, 0, 0);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int qp = q0 + u * kRowLanes64;
                     if (qp >= np) continue;
                     const int k = 2 * qp;
+                    const double v0 = (double)(((long long)v[u].y << 26) + v[u].x);  // |V| <= 2^52: exact
+                    const double v1 = (double)(((long long)v[u].w << 26) + v[u].z);
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
                         double2 xv;
@@ -194,8 +326,8 @@ __device__ __forceinline__ void grouped_rows64(const DevGroupedCSR& A, int r0, i
                             xv.x = x[d * ld_x + A.cols[c0 + k]];
                             xv.y = k + 1 < m ? x[d * ld_x + A.cols[c0 + k + 1]] : 0.0;
                         }
-                        acc0[d] = fma(v[u].x, xv.x, acc0[d]);
-                        acc1[d] = fma(v[u].y, xv.y, acc1[d]);
+                        acc0[d] = fma(v0, xv.x, acc0[d]);
+                        acc1[d] = fma(v1, xv.y, acc1[d]);
                     }
                 }
             }
@@ -205,54 +337,93 @@ __device__ __forceinline__ void grouped_rows64(const DevGroupedCSR& A, int r0, i
             double a = acc0[d] + acc1[d];
 #pragma unroll
             for (int o = kRowLanes64 / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            acc0[d] = a;
+            acc0[d] = live ? ldexp(a, A.vexp[r]) : 0.0;
         }
-        if (live && li == 0) {
-            if (mode == kOutWithPsi) {
-                const int32_t ri = inv[r];
-                const double wv = w_sorted ? w_sorted[ri] : 1.0;
-#pragma unroll
-                for (int d = 0; d < ND; ++d) out[d * ld_out + r] = fma(-kInv2PiG * wv, psi[(int64_t)ri * ND + d], acc0[d]);
-            } else if (mode == kOutAccumulate) {
-#pragma unroll
-                for (int d = 0; d < ND; ++d) out[d * ld_out + r] += acc0[d];
-            } else {
-#pragma unroll
-                for (int d = 0; d < ND; ++d) out[d * ld_out + r] = acc0[d];
-            }
-        }
+        if (live && li == 0) store_row64<ND>(r, acc0, inv, w_sorted, psi, out, ld_out, mode);
     }
 }
 
 template <int ND>
-__global__ void __launch_bounds__(kGroupThreads)
+__global__ void __launch_bounds__(group64_threads<ND>())
     k_out_grouped64(DevGroupedCSR A, int smem_m, const int32_t* __restrict__ inv, const double* __restrict__ w_sorted,
                     const double* __restrict__ psi, const double* __restrict__ x, int64_t ld_x,
                     double* __restrict__ out, int64_t ld_out, int mode)
 {
-    // [ND][smem_m] (smem_m even): x at the group's columns, density-major
+    // [ND][smem_m] (smem_m even): x at the group's columns, density-major, as
+    // float64 and then (same 8 bytes) in fixed point
     extern __shared__ __align__(16) double F64[];
+    __shared__ unsigned xe[ND];  // the largest biased exponent of the staged x, per density
+    __shared__ int xsc[ND];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int gi = blockIdx.x; gi < A.ngroups; gi += gridDim.x) {
         const int r0 = A.g_r0[gi], r1 = A.g_r0[gi + 1];
         const int64_t c0 = A.g_c0[gi];
         const int m = (int)(A.g_c0[gi + 1] - c0);
         const bool staged = m + (m & 1) <= smem_m;
+        __syncthreads();  // the previous group's rows are done with F64, xe, xsc
+        if (threadIdx.x < ND) xe[threadIdx.x] = 0u;
         __syncthreads();
         if (staged) {
-            for (int i = threadIdx.x; i < m * ND; i += blockDim.x) {
-                const int k = i % m, d = i / m;
-                F64[d * smem_m + k] = x[d * ld_x + A.cols[c0 + k]];
+            // four columns per thread at a time: their indices, then their x values
+            constexpr int G = 4;
+            unsigned em[ND];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) em[d] = 0u;
+            for (int k0 = threadIdx.x; k0 < m; k0 += G * blockDim.x) {
+                int c[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const int k = k0 + j * blockDim.x;
+                    c[j] = k < m ? A.cols[c0 + k] : -1;
+                }
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    double v[G];
+#pragma unroll
+                    for (int j = 0; j < G; ++j) v[j] = c[j] >= 0 ? x[d * ld_x + c[j]] : 0.0;
+#pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        if (c[j] < 0) continue;
+                        F64[d * smem_m + k0 + j * blockDim.x] = v[j];
+                        em[d] = max(em[d], (unsigned)(__double_as_longlong(v[j]) >> 52) & 0x7ffu);
+                    }
+                }
             }
-            if ((m & 1) && threadIdx.x < ND) F64[threadIdx.x * smem_m + m] = 0.0;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                em[d] = __reduce_max_sync(0xffffffffu, em[d]);
+                if (lane == 0) atomicMax(&xe[d], em[d]);
+            }
+            if ((m & 1) && threadIdx.x < ND) F64[threadIdx.x * smem_m + m] = 0.0;  // also the fixed-point zero
         }
         __syncthreads();
-        if (staged)
-            grouped_rows64<ND, true>(A, r0, r1, c0, m, smem_m, F64, inv, w_sorted, psi, x, ld_x, out, ld_out, mode,
-                                     lane, warp, nw);
-        else
+        if (!staged) {
             grouped_rows64<ND, false>(A, r0, r1, c0, m, smem_m, F64, inv, w_sorted, psi, x, ld_x, out, ld_out, mode,
                                       lane, warp, nw);
+            continue;
+        }
+        bool fix = m <= kFixMaxM;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) fix = fix && xe[d] < 0x7ffu;  // no infinity or NaN staged
+        if (!fix) {
+            grouped_rows64<ND, true>(A, r0, r1, c0, m, smem_m, F64, inv, w_sorted, psi, x, ld_x, out, ld_out, mode,
+                                     lane, warp, nw);
+            continue;
+        }
+        // in place, each element by the thread that staged it: |x| < 2^e, e = E - 1022
+        // for the largest biased exponent E (E = 0: zeros and subnormals, e = -1021)
+        int2* X = reinterpret_cast<int2*>(F64);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const int e = (int)max(xe[d], 1u) - 1022;
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                const long long q = __double2ll_rn(ldexp(F64[d * smem_m + k], 52 - e));
+                X[d * smem_m + k] = make_int2((int)(q & 0x3ffffff), (int)(q >> 26));
+            }
+            if (threadIdx.x == 0) xsc[d] = e - 52;
+        }
+        __syncthreads();
+        grouped_rows_fix<ND>(A, r0, r1, m, smem_m, X, xsc, inv, w_sorted, psi, out, ld_out, mode, lane, warp, nw);
     }
 }
 
@@ -261,20 +432,18 @@ cudaError_t launch_grouped64_nd(const DevGroupedCSR& A, const int32_t* inv, cons
                                 const double* x, int64_t ld_x, double* out, int64_t ld_out, int mode, int max_blocks,
                                 cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_out_grouped64<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGroupSmemBytes);
-    if (e != cudaSuccess) return e;
-    int smem_m = kGroupSmemBytes / (ND * (int)sizeof(double));
-    smem_m &= ~1;
-    const int want = A.max_m + (A.max_m & 1);
-    if (want < smem_m) smem_m = want;
+    // staging sized to the longest column list (even), at most kStage64MaxM columns
+    int smem_m = A.max_m + (A.max_m & 1);
+    if (smem_m > kStage64MaxM) smem_m = kStage64MaxM;
     if (smem_m < 2) smem_m = 2;
     const size_t bytes = (size_t)smem_m * ND * sizeof(double);
-    const int cap = max_blocks > 0 ? max_blocks : 152 * 16;
+    cudaError_t e = cudaFuncSetAttribute(k_out_grouped64<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    constexpr int threads = group64_threads<ND>();
+    const int cap = max_blocks > 0 ? max_blocks : 152 * (2048 / threads);
     int blocks = A.ngroups < cap ? A.ngroups : cap;
     if (blocks < 1) blocks = 1;
-    k_out_grouped64<ND><<<blocks, kGroupThreads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, x, ld_x, out, ld_out,
-                                                            mode);
+    k_out_grouped64<ND><<<blocks, threads, bytes, s>>>(A, smem_m, inv, w_sorted, psi, x, ld_x, out, ld_out, mode);
     return cudaGetLastError();
 }
 
