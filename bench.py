@@ -65,7 +65,7 @@ PROFILED_TRAFFIC = {
     "leaf": (486.0, "n_tgt", "target", 24, 1, "k_leaf64d<24, 1>"),
     "m2l": (22.54, "n_v_pairs", "V-list pair", 24, 1, "k_m2l64<24, 1>"),
     "upward": (413.4, "n_src", "source", 24, 1, "k_p2m64<24, 1>"),
-    "out": (8.63, "nnz", "nonzero", 24, 1, "k_out_grouped64<1>"),
+    "out": (8.70, "nnz", "nonzero", 24, 1, "k_out_grouped64<1>"),
 }
 
 
@@ -104,11 +104,14 @@ def roofline_models(info, ndens, fp64_tflops):
                 "flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens,
                 "ops": info.n_v_pairs * (2.0 * P * P + 10.0 * P) * ndens, "units": info.n_v_pairs,
                 "ops_peak": ops_peak, "per_unit": f"8(P+1)^2 flops per V-list pair, P={P}"},
-        "out": {"kernel": "k_out_grouped64 (float64 correction apply, rows grouped by shared column lists)",
-                "flop": info.nnz * 2.0 * ndens, "ops": info.nnz * 1.0 * ndens, "units": info.nnz,
+        "out": {"kernel": "k_out_grouped64 (correction apply in exact fixed point, rows grouped by shared "
+                          "column lists)", "bound": "hbm",
+                "flop": info.nnz * 2.0 * ndens, "ops": 0.0, "units": info.nnz,
                 "ops_peak": ops_peak, "bytes": info.nnz * 8.0 + info.n_tgt * 8.0 * (2 * ndens + 1),
                 "hbm_peak": hbm, "hbm_src": hbm_src,
-                "per_unit": "2 flops (one DFMA) and 8 B (one float64 value) per nonzero"},
+                "per_unit": "8 B per nonzero (one stored value) plus 8 B per target and density for x, psi and "
+                            "the result; the arithmetic is four 32x32-bit integer multiply-adds per nonzero (no "
+                            "FP64 operations)"},
         "upward": {"kernel": "k_p2m64 (float64 P2M + the M2M chain)",
                    "flop": info.n_src * 8.0 * P * ndens, "ops": info.n_src * 6.0 * P * ndens,
                    "units": info.n_src, "ops_peak": ops_peak, "per_unit": f"8P flops per source, P={P}"},
@@ -399,6 +402,11 @@ def roofline_of(phase_ms, info, ndens, fp64_tflops, fp64_src):
             gbs = m["bytes"] / t / 1e9
             r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": m["hbm_peak"], "frac": gbs / m["hbm_peak"],
                         "peak_source": m["hbm_src"]}
+        if m.get("bound") == "hbm":
+            # an HBM-bound phase: algorithmic bytes against the measured copy bandwidth
+            r.update({"bound": "hbm", "achieved": gbs, "peak": m["hbm_peak"], "unit": "GB/s",
+                      "frac": gbs / m["hbm_peak"], "peak_source": m["hbm_src"], "flop_tflops": achieved})
+            del r["pipe_ops_tops"], r["pipe_frac"]
         tr = PROFILED_TRAFFIC.get(name)
         if tr and tr[3] == info.p_fmm and tr[4] == ndens and not getattr(info, "sym_slots", 0):
             per, attr, what, _, _, kern = tr
@@ -961,7 +969,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "arith": ("float64 inputs and results; near-field r^2 exact in 128-bit integers and its logarithm in "
                   "fixed point (2^-55) on the integer pipes, accumulated in float64; the M2L contraction as exact "
-                  "integer digit products on the bf16 tensor cores (62-bit operands); every other step IEEE float64"),
+                  "integer digit products on the bf16 tensor cores (62-bit operands); the correction apply as exact "
+                  "128-bit sums of 52-bit fixed-point values and densities on the integer pipes, rounded once per "
+                  "row; every other step IEEE float64"),
         "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
                    "correction": "own + near cells" if args.csr == "near" or args.workload == "disk" else "own cell",
                    "ndens": 1, "p_fmm": info.p_fmm, "leaf": info.leaf, "levels": info.n_levels,

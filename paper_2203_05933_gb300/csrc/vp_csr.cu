@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "vp_ff.cuh"
+#include "vp_fixed.cuh"
 #include "vp_internal.h"
 
 namespace vp {
@@ -96,12 +97,14 @@ __global__ void k_pad_values(int64_t nrows, const int64_t* __restrict__ rowptr, 
     }
 }
 
-// The same layout in per-row fixed point (one warp per row): with 2^(e-1) <=
-// max_k |v_rk| < 2^e, V = rint(v 2^(52-e)), so |V| <= 2^52 and the rounding error
-// is at most 2^-52 of the row's largest value (the row's own float64 rounding is
-// 2^-53 of it); vexp[r] = e - 52. Stored as {V mod 2^26, V >> 26}: the product
-// kernel multiplies 26-bit pieces (exact 64-bit products) and keeps its sums
-// exact. A zero row stores zeros with vexp = 0.
+// The same layout in per-row fixed point (one warp per row): with E the largest
+// biased exponent among the row's values and e = max(E, 1) - 1022 (so every
+// |v| < 2^e, and 2^(e-1) <= max |v| for a normal maximum), V = v 2^(52-e)
+// rounded to the nearest integer: |V| <= 2^52 and the rounding error is at most
+// 2^-53 of 2^e, i.e. 2^-52 of the row's largest value (the row's own float64
+// rounding is 2^-53 of it); vexp[r] = e - 52. Stored as {V mod 2^26, V >> 26}:
+// the product kernel multiplies 26-bit pieces (exact 64-bit products) and keeps
+// its sums exact.
 __global__ void k_fix_values(int64_t nrows, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ prow,
                              const double* __restrict__ val, int2* __restrict__ vi, int32_t* __restrict__ vexp)
 {
@@ -109,12 +112,12 @@ __global__ void k_fix_values(int64_t nrows, const int64_t* __restrict__ rowptr, 
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < nrows; r += warps) {
         const int64_t a = rowptr[r], len = rowptr[r + 1] - a, o = prow[r], plen = prow[r + 1] - o;
-        double mx = 0.0;
-        for (int64_t k = lane; k < len; k += 32) mx = fmax(mx, fabs(val[a + k]));
-        for (int s = 16; s > 0; s >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, s));
-        const int e = mx > 0.0 ? ilogb(mx) + 1 : 52;
+        unsigned em = 0u;
+        for (int64_t k = lane; k < len; k += 32) em = max(em, exponent_field(val[a + k]));
+        em = __reduce_max_sync(0xffffffffu, em);
+        const int e = (int)max(em, 1u) - 1022;
         for (int64_t k = lane; k < plen; k += 32) {
-            const long long V = k < len ? __double2ll_rn(ldexp(val[a + k], 52 - e)) : 0LL;
+            const long long V = k < len ? fixed52(val[a + k], e) : 0LL;
             vi[o + k] = make_int2((int)(V & 0x3ffffff), (int)(V >> 26));
         }
         if (lane == 0) vexp[r] = e - 52;

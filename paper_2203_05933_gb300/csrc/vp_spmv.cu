@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "vp_ff.cuh"
+#include "vp_fixed.cuh"
 #include "vp_internal.h"
 
 namespace vp {
@@ -154,11 +155,12 @@ __global__ void __launch_bounds__(kGroupThreads)
 // 2^52 and the rounding is at most 2^-53 of that largest value). A nonzero then
 // costs four 32x32-bit multiply-adds into three 64-bit sums (the products of the
 // high pieces, the cross products, the low pieces), each exact; per row the lane
-// sums combine into one exact 128-bit integer, which is rounded to float64 once.
-// So the row's result is the correctly rounded sum of the stored products (up
-// to the last conversion), and the integer pipes carry the work that would
-// otherwise take one DFMA per nonzero (the FP64 unit, 2 per clock per SM on
-// GB300, is slower than the values stream from HBM). Eight lanes share a row
+// sums combine into one exact 128-bit integer, which is rounded to float64 once
+// (to nearest). So the row's result is the rounded exact sum of the stored
+// products, and the integer pipes carry the work that would otherwise take one
+// DFMA per nonzero (the FP64 unit, 2 per clock per SM on GB300, is slower than
+// the values stream from HBM); the conversions in and out of fixed point are
+// integer operations on the bits too (vp_fixed.cuh). Eight lanes share a row
 // (four rows per warp at a time); the rows of a group read the same staged
 // columns (broadcast).
 //
@@ -175,7 +177,8 @@ constexpr int group64_threads()
 {
     return ND == 1 ? 64 : ND == 2 ? 128 : 256;
 }
-// the longest column list staged (longer groups take the float64 loop from global memory)
+// the longest column list staged (longer groups, and for eight densities those
+// beyond kGroupSmemBytes, take the float64 loop from global memory)
 constexpr int kStage64MaxM = 3072;
 // the longest column list of the fixed-point loop: a lane then sums at most 512
 // products, which keeps every 64-bit partial sum below 2^63
@@ -187,15 +190,6 @@ __device__ __forceinline__ long long mad_wide(int a, int b, long long c)
     long long d;
     asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
     return d;
-}
-
-// A 128-bit two's-complement integer (hi, lo) as float64: correctly rounded when
-// it fits 64 bits; else |value| >= 2^63 and the two roundings stay within two
-// units in the last place.
-__device__ __forceinline__ double int128_to_double(long long hi, unsigned long long lo)
-{
-    if (hi == ((long long)lo >> 63)) return (double)(long long)lo;
-    return fma((double)hi, 0x1p64, (double)lo);  // |hi| < 2^53: exact
 }
 
 template <int ND>
@@ -275,8 +269,7 @@ __device__ __forceinline__ void grouped_rows_fix(const DevGroupedCSR& A, int r0,
                 const unsigned long long tl = __shfl_xor_sync(0xffffffffu, (unsigned long long)t, o);
                 t += ((__int128)th << 64) | (__int128)tl;
             }
-            res[d] = live ? ldexp(int128_to_double((long long)(t >> 64), (unsigned long long)t), A.vexp[r] + xsc[d])
-                          : 0.0;
+            res[d] = live ? int128_ldexp(t, A.vexp[r] + xsc[d]) : 0.0;
         }
         if (live && li == 0) store_row64<ND>(r, res, inv, w_sorted, psi, out, ld_out, mode);
     }
@@ -385,7 +378,7 @@ __global__ void __launch_bounds__(group64_threads<ND>())
                     for (int j = 0; j < G; ++j) {
                         if (c[j] < 0) continue;
                         F64[d * smem_m + k0 + j * blockDim.x] = v[j];
-                        em[d] = max(em[d], (unsigned)(__double_as_longlong(v[j]) >> 52) & 0x7ffu);
+                        em[d] = max(em[d], exponent_field(v[j]));
                     }
                 }
             }
@@ -417,7 +410,7 @@ __global__ void __launch_bounds__(group64_threads<ND>())
         for (int d = 0; d < ND; ++d) {
             const int e = (int)max(xe[d], 1u) - 1022;
             for (int k = threadIdx.x; k < m; k += blockDim.x) {
-                const long long q = __double2ll_rn(ldexp(F64[d * smem_m + k], 52 - e));
+                const long long q = fixed52(F64[d * smem_m + k], e);
                 X[d * smem_m + k] = make_int2((int)(q & 0x3ffffff), (int)(q >> 26));
             }
             if (threadIdx.x == 0) xsc[d] = e - 52;
@@ -433,8 +426,10 @@ cudaError_t launch_grouped64_nd(const DevGroupedCSR& A, const int32_t* inv, cons
                                 cudaStream_t s)
 {
     // staging sized to the longest column list (even), at most kStage64MaxM columns
+    // and kGroupSmemBytes
     int smem_m = A.max_m + (A.max_m & 1);
     if (smem_m > kStage64MaxM) smem_m = kStage64MaxM;
+    if (smem_m > (kGroupSmemBytes / (ND * (int)sizeof(double)) & ~1)) smem_m = kGroupSmemBytes / (ND * (int)sizeof(double)) & ~1;
     if (smem_m < 2) smem_m = 2;
     const size_t bytes = (size_t)smem_m * ND * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_out_grouped64<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
