@@ -31,6 +31,25 @@ __device__ __forceinline__ unsigned exponent_field(double x)
     return (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu;
 }
 
+// x 2^sh rounded to the nearest 128-bit integer (ties away from zero), for
+// |x 2^sh| < 2^125: the significand shifted left, or right with rounding.
+__device__ __forceinline__ __int128 fixed128(double x, int sh)
+{
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7ff);
+    unsigned long long M = (unsigned long long)b & 0xfffffffffffffULL;
+    if (E) M |= 1ULL << 52;
+    const int t = (E > 1 ? E : 1) - 1075 + sh;  // x 2^sh = M 2^t, t <= 72 by the bound
+    unsigned __int128 q;
+    if (t >= 0) {
+        q = (unsigned __int128)M << t;
+    } else {
+        const int r = -t;
+        q = r >= 64 ? 0 : (unsigned __int128)((M + (1ULL << (r - 1))) >> r);
+    }
+    return b < 0 ? -(__int128)q : (__int128)q;
+}
+
 // t 2^s as float64 for a 128-bit two's-complement integer t, rounded to the
 // nearest (ties away from zero): the magnitude's leading 53 bits, rounded, become
 // the significand and s plus the shift the exponent field; results outside the

@@ -38,6 +38,7 @@
 #include <cstring>
 #include <vector>
 
+#include "vp_fixed.cuh"
 #include "vp_internal.h"
 
 namespace vp {
@@ -1251,57 +1252,121 @@ __global__ void __launch_bounds__(kW64 * 32, ND <= 2 ? 4 : 2)
 }
 
 // ----------------------------------------------------------------------------
-// a5: L2L into the boxes of one level, balanced over the lanes: with the table
-// l2l[c][l][k] = C(k, l) 2^-l zeta_c^(k-l) (k >= l, zeta_c the child offset over
-// the parent half-side), L'_l += sum_{k=l..P} l2l[c][l][k] L_k(parent). Lane i of
-// a box slot owns the rows l1 = i and l2 = P - i (P + 2 terms together, so every
-// lane does the same work; the middle row of even P once); floor(32 / (P/2 + 1))
-// child boxes per warp at a time.
+// a5: L2L into the boxes of one level, exactly, on the integer pipes. With
+// zeta = s/2 the child's centre offset over the parent half-side, s = sx + i sy
+// (sx, sy = +-1 by quadrant), the scaled translation
+//   L'_l = sum_{k>=l} C(k, l) 2^-l zeta^(k-l) L_k
+// factors as a_k = s^k 2^-k L_k, b_l = sum_{k>=l} C(k, l) a_k, L'_l = conj(s)^l 2^-l b_l
+// (2^-l zeta^-l = s^-l and s^-1 = conj(s)/2). Since s^2 = 2 i sx sy, s^k 2^-k is
+// (i sx sy)^m 2^-m for k = 2m and (i sx sy)^m s 2^-(m+1) for k = 2m + 1: a_k and
+// L'_l take sign changes, swaps, one addition and power-of-two scales; b is the
+// Taylor shift of a by 1 (P(P+1)/2 additions, real and imaginary parts apart).
+// In 128-bit fixed point with one scale 2^F per parent and density, chosen from
+// the exponents of L so that every partial sum stays below 2^125 (a partial sum
+// of the shift is at most sum_k 2^k |a_k| = sum_k 2^(k/2) |L_k|), all of it is
+// exact and only the conversions round: L'_l is the correctly rounded value of
+// the translation of the parent's coefficients, with no FP64 instruction but
+// the final addition. Two lanes per child box: lane c of the pair carries the
+// real (c = 0) or imaginary (c = 1) sums and the pair swaps them by one shuffle
+// per coefficient at the end. A parent holding an infinity or NaN takes the
+// float64 table (l2l[c][l][k] = C(k, l) 2^-l zeta_c^(k-l)) instead.
+constexpr int kL2LThreads = 128;
+
+// component c of (sgn i)^m (X + i Y)
+__device__ __forceinline__ __int128 quarter_turn(__int128 X, __int128 Y, int m, int sgn, int c)
+{
+    __int128 re, im;
+    switch (m & 3) {
+        case 0: re = X, im = Y; break;
+        case 1: re = -Y, im = X; break;
+        case 2: re = -X, im = -Y; break;
+        default: re = Y, im = -X; break;
+    }
+    __int128 v = c ? im : re;
+    return (sgn < 0 && (m & 1)) ? -v : v;
+}
+
 template <int P, int ND>
-__global__ void __launch_bounds__(kW64 * 32)
+__global__ void __launch_bounds__(kL2LThreads)
     k_l2l64(DevTree t, DevTables tab, int b0, int b1, double2* __restrict__ L)
 {
     constexpr int P1 = P + 1;
-    constexpr int H = P / 2 + 1;    // lanes per box slot
-    constexpr int BS = 32 / H;      // boxes per warp at a time
-    const int lane = threadIdx.x & 31;
-    const int slot = lane / H, i = lane % H;
-    const int l1 = i, l2 = P - i;
-    for (int bb = b0 + gwarp() * BS; bb < b1; bb += nwarps() * BS) {
-        const int b = bb + slot;
-        if (slot >= BS || b >= b1) continue;
-        const int p = t.parent[b];
-        const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
-        const double2* tc = tab.l2l64 + (size_t)cq * P1 * P1;
-        const double2* Lp = L + (int64_t)p * P1 * ND;
-        double2 a1[ND], a2[ND];
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = (int)(gid & 1);
+    const int64_t bi = b0 + (gid >> 1);
+    // a pair past the level's end repeats its last box and stores nothing
+    const bool live = bi < b1;
+    const int b = live ? (int)bi : b1 - 1;
+    const unsigned pair = 3u << ((threadIdx.x & 31) & ~1);
+    const int p = t.parent[b];
+    const int cq = (t.ixy[2 * b] & 1) | ((t.ixy[2 * b + 1] & 1) << 1);
+    const int sx = (cq & 1) ? 1 : -1, sy = (cq & 2) ? 1 : -1, sg = sx * sy;
+    const double2* Lp = L + (int64_t)p * P1 * ND;
+    double* Lc = reinterpret_cast<double*>(L + (int64_t)b * P1 * ND);
+#pragma unroll 1
+    for (int d = 0; d < ND; ++d) {
+        // G = max_k (ceil(k/2) + e_k), |Re L_k|, |Im L_k| < 2^e_k
+        int G = -(1 << 20);
+        bool finite = true;
 #pragma unroll
-        for (int d = 0; d < ND; ++d) a1[d] = a2[d] = make_double2(0.0, 0.0);
-        const int n1 = P - l1 + 1;  // terms of row l1; row l2 has P - l2 + 1 = l1 + 1
-        for (int j = 0; j < P + 2; ++j) {
-            const bool first = j < n1;
-            const int l = first ? l1 : l2;
-            const int k = first ? l1 + j : l2 + (j - n1);
-            const double2 zb = tc[l * P1 + k];
-#pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                const double2 v = Lp[k * ND + d];
-                if (first)
-                    a1[d] = cfma64(zb, v, a1[d]);
-                else
-                    a2[d] = cfma64(zb, v, a2[d]);
-            }
+        for (int k = 0; k <= P; ++k) {
+            const double2 v = Lp[k * ND + d];
+            const unsigned e = max(max(exponent_field(v.x), exponent_field(v.y)), 1u);
+            finite = finite && e < 0x7ffu;
+            G = max(G, (k + 1) / 2 + (int)e - 1022);
         }
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            int64_t o = ((int64_t)b * P1 + l1) * ND + d;
-            double2 x = L[o];
-            L[o] = make_double2(x.x + a1[d].x, x.y + a1[d].y);
-            if (l2 != l1) {
-                o = ((int64_t)b * P1 + l2) * ND + d;
-                x = L[o];
-                L[o] = make_double2(x.x + a2[d].x, x.y + a2[d].y);
+        if (!finite) {
+            const double2* tc = tab.l2l64 + (size_t)cq * P1 * P1;
+            for (int l = 0; l <= P; ++l) {
+                double acc = 0.0;
+                for (int k = l; k <= P; ++k) {
+                    const double2 z = tc[l * P1 + k], v = Lp[k * ND + d];
+                    acc += c ? z.x * v.y + z.y * v.x : z.x * v.x - z.y * v.y;
+                }
+                if (live) Lc[(l * ND + d) * 2 + c] += acc;
             }
+            continue;
+        }
+        // sum_k 2^(k/2) |L_k| < (P + 1) 2^(G + 1) <= 2^(G + 6), so F = 119 - G keeps
+        // every partial sum below 2^125
+        const int F = 119 - G;
+        __int128 a[P1];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+            const double2 v = Lp[k * ND + d];
+            const int m = k >> 1;
+            __int128 X, Y;
+            if ((k & 1) == 0) {
+                X = fixed128(v.x, F - m);
+                Y = fixed128(v.y, F - m);
+            } else {  // times s
+                const __int128 x = fixed128(v.x, F - m - 1), y = fixed128(v.y, F - m - 1);
+                X = (sx > 0 ? x : -x) - (sy > 0 ? y : -y);
+                Y = (sy > 0 ? x : -x) + (sx > 0 ? y : -y);
+            }
+            a[k] = quarter_turn(X, Y, m, sg, c);
+        }
+        // Taylor shift by 1: b_l = sum_{k>=l} C(k, l) a_k
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+#pragma unroll
+            for (int j = P - 1; j >= i; --j) a[j] += a[j + 1];
+#pragma unroll
+        for (int l = 0; l <= P; ++l) {
+            const long long oh = __shfl_xor_sync(pair, (long long)(a[l] >> 64), 1);
+            const unsigned long long ol = __shfl_xor_sync(pair, (unsigned long long)a[l], 1);
+            const __int128 other = (__int128)(((unsigned __int128)(unsigned long long)oh << 64) | ol);
+            const __int128 Bx = c ? other : a[l], By = c ? a[l] : other;
+            const int m = l >> 1;
+            __int128 X = Bx, Y = By;
+            int sc = -F - m;
+            if (l & 1) {  // times conj(s)
+                X = (sx > 0 ? Bx : -Bx) + (sy > 0 ? By : -By);
+                Y = (sx > 0 ? By : -By) - (sy > 0 ? Bx : -Bx);
+                sc -= 1;
+            }
+            const __int128 v = quarter_turn(X, Y, m, -sg, c);
+            if (live) Lc[(l * ND + d) * 2 + c] += int128_ldexp(v, sc);
         }
     }
 }
@@ -1379,8 +1444,9 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
     // adds anything goes into level 3
     for (int l = 3; l < t.nlevels; ++l) {
         const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
-        k_l2l64<P, ND><<<blocks_for_warps((b1 - b0 + 32 / (P / 2 + 1) - 1) / (32 / (P / 2 + 1)), kW64), threads, 0,
-                         s>>>(t, tab, b0, b1, ws.L);
+        if (b1 <= b0) continue;
+        const int64_t lanes = 2 * (int64_t)(b1 - b0);
+        k_l2l64<P, ND><<<(int)((lanes + kL2LThreads - 1) / kL2LThreads), kL2LThreads, 0, s>>>(t, tab, b0, b1, ws.L);
     }
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
