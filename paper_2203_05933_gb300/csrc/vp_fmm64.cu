@@ -45,7 +45,17 @@ namespace vp {
 namespace {
 
 constexpr int kW64 = 4;             // warps per block of the expansion kernels
-constexpr int kLeafWarps64 = 8;     // warps per block of the near-field kernel
+// Warps per block of the near-field kernels. Each block holds one 64 KB copy of
+// the logarithm's table, so shared memory caps the resident blocks: at one or
+// two densities (64 registers) 16-warp blocks give 2 blocks, 32 warps per SM,
+// against 3 blocks of 8 warps; more densities need more registers than a
+// 512-thread block allows and keep 8 warps.
+template <int ND>
+constexpr int leaf_warps64()
+{
+    return ND <= 2 ? 16 : 8;
+}
+constexpr int kGradWarps64 = 8;  // warps per block of the near-field gradient kernel
 constexpr int kEBias = 64;          // exponent table covers e in [-64, 63]
 
 __device__ __forceinline__ double2 cmul64(double2 a, double2 b)
@@ -185,7 +195,7 @@ struct LeafStageFix {
 };
 
 template <int P, int ND, bool SYM>
-__global__ void __launch_bounds__(kLeafWarps64 * 32)
+__global__ void __launch_bounds__(leaf_warps64<ND>() * 32)
     k_leaf64(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
              const double2* __restrict__ L, const double2* __restrict__ logtab, const double* __restrict__ etab_g,
              double* __restrict__ psi, int* __restrict__ work, double* __restrict__ slots)
@@ -368,7 +378,7 @@ __global__ void __launch_bounds__(kLeafWarps64 * 32)
 // factor 2^-sL applied per point. The K partial sums of a point are added by
 // shuffles and psi += near / 2 (the log is of r^2).
 template <int P, int ND>
-__global__ void __launch_bounds__(kLeafWarps64 * 32)
+__global__ void __launch_bounds__(leaf_warps64<ND>() * 32)
     k_leaf64d(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
               const double2* __restrict__ L, const longlong2* __restrict__ logtab, int two_sigma, int sL,
               long long ln2_sL, double* __restrict__ psi, int* __restrict__ work)
@@ -548,12 +558,12 @@ __device__ __forceinline__ double recip_r2(double r2)
 // One directed pair costs 11 FP64 operations (differences, r^2, the reciprocal,
 // q / r^2 and two accumulations).
 template <int P, int ND>
-__global__ void __launch_bounds__(kLeafWarps64 * 32)
+__global__ void __launch_bounds__(kGradWarps64 * 32)
     k_leaf_grad64(DevTree t, PassGeom g, const double* __restrict__ q, const double2* __restrict__ M,
                   const double2* __restrict__ L, double* __restrict__ psi, int* __restrict__ work)
 {
     constexpr int P1 = P + 1;
-    __shared__ LeafStage64<ND> stage[kLeafWarps64];
+    __shared__ LeafStage64<ND> stage[kGradWarps64];
     const int lane = threadIdx.x & 31;
     LeafStage64<ND>& st = stage[threadIdx.x >> 5];
     for (;;) {
@@ -1401,7 +1411,7 @@ template <int ND>
 size_t leaf_smem()
 {
     return (size_t)(1 << kLog64Bits) * sizeof(double2) + 2 * kEBias * sizeof(double) +
-           (size_t)kLeafWarps64 * std::max(sizeof(LeafStage64<ND>), sizeof(LeafStageFix<ND>));
+           (size_t)leaf_warps64<ND>() * std::max(sizeof(LeafStage64<ND>), sizeof(LeafStageFix<ND>));
 }
 
 template <int P, int ND>
@@ -1424,8 +1434,8 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         if (e != cudaSuccess) return e;
         for (int si = 0; si < 2; ++si) {
             int nb = 0;
-            e = si ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64<P, ND, true>, kLeafWarps64 * 32, leaf_smem<ND>())
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64d<P, ND>, kLeafWarps64 * 32, leaf_smem<ND>());
+            e = si ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64<P, ND, true>, leaf_warps64<ND>() * 32, leaf_smem<ND>())
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_leaf64d<P, ND>, leaf_warps64<ND>() * 32, leaf_smem<ND>());
             if (e != cudaSuccess) return e;
             leaf_resident[si] = std::max(1, nb);
         }
@@ -1451,19 +1461,20 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
     if (tm) tm->end(id);
     id = tm ? tm->begin("leaf") : -1;
     if (gradient) {
-        const int gblocks = std::max(1, std::min((t.nleaf + kLeafWarps64 - 1) / kLeafWarps64, device_sms() * 4));
+        const int gblocks = std::max(1, std::min((t.nleaf + kGradWarps64 - 1) / kGradWarps64, device_sms() * 4));
         cudaMemsetAsync(ws.work, 0, sizeof(int), s);
-        k_leaf_grad64<P, ND><<<gblocks, kLeafWarps64 * 32, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi, ws.work);
+        k_leaf_grad64<P, ND><<<gblocks, kGradWarps64 * 32, 0, s>>>(t, g, ws.q, ws.M, ws.L, ws.psi, ws.work);
         if (tm) tm->end(id);
         return cudaGetLastError();
     }
     const bool sym = t.sym;
     const int si = sym ? 1 : 0;
-    const int lblocks = std::max(1, std::min((t.nleaf + kLeafWarps64 - 1) / kLeafWarps64, device_sms() * leaf_resident[si]));
+    constexpr int lw = leaf_warps64<ND>();
+    const int lblocks = std::max(1, std::min((t.nleaf + lw - 1) / lw, device_sms() * leaf_resident[si]));
     cudaMemsetAsync(ws.work, 0, sizeof(int), s);
     double* slots = reinterpret_cast<double*>(ws.slots);  // the slot buffer holds 8 bytes per slot and density
     if (sym) {
-        k_leaf64<P, ND, true><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
+        k_leaf64<P, ND, true><<<lblocks, lw * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.log64,
                                                                                  tab.elog64, ws.psi, ws.work, slots);
         const int rblocks = std::max(1, std::min((g.n_eval + 255) / 256, 152 * 32));
         k_sym_reduce64<ND><<<rblocks, 256, 0, s>>>(t, g, slots, ws.psi);
@@ -1473,7 +1484,7 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         int sL = 60;
         while (sL > 40 && std::ldexp((double)maxE * 0.6931471805599453 + 1.0, sL) >= 0x1p62) --sL;
         const long long ln2_sL = std::llround(std::ldexp(0.693147180559945309417232121458176568L, sL));
-        k_leaf64d<P, ND><<<lblocks, kLeafWarps64 * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.logint,
+        k_leaf64d<P, ND><<<lblocks, lw * 32, leaf_smem<ND>(), s>>>(t, g, ws.q, ws.M, ws.L, tab.logint,
                                                                             2 * g.fix_sigma, sL, ln2_sL, ws.psi,
                                                                             ws.work);
     }
