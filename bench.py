@@ -64,7 +64,7 @@ FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12  # FP32/INT32 lane-operations per sec
 PROFILED_TRAFFIC = {
     "leaf": (486.0, "n_tgt", "target", 24, 1, "k_leaf64d<24, 1>"),
     "m2l": (22.54, "n_v_pairs", "V-list pair", 24, 1, "k_m2l64<24, 1>"),
-    "upward": (413.4, "n_src", "source", 24, 1, "k_p2m64<24, 1>"),
+    "upward": (407.0, "n_src", "source", 24, 1, "k_p2m64<24, 1>"),
     "out": (8.70, "nnz", "nonzero", 24, 1, "k_out_grouped64<1>"),
 }
 
@@ -112,7 +112,7 @@ def roofline_models(info, ndens, fp64_tflops):
                 "per_unit": "8 B per nonzero (one stored value) plus 8 B per target and density for x, psi and "
                             "the result; the arithmetic is four 32x32-bit integer multiply-adds per nonzero (no "
                             "FP64 operations)"},
-        "upward": {"kernel": "k_p2m64 (float64 P2M + the M2M chain)",
+        "upward": {"kernel": "k_p2m64 (float64 P2M) + k_m2m64 (M2M per level, exact in 128-bit fixed point)",
                    "flop": info.n_src * 8.0 * P * ndens, "ops": info.n_src * 6.0 * P * ndens,
                    "units": info.n_src, "ops_peak": ops_peak, "per_unit": f"8P flops per source, P={P}"},
     }

@@ -704,108 +704,38 @@ __global__ void k_sym_reduce64(DevTree t, PassGeom g, const double* __restrict__
     }
 }
 
-// ----------------------------------------------------------------------------
-// a3: P2M and the whole M2M pass in one launch, one warp per leaf: lane k sums
-// q_j u_j^k over the leaf's points (u = (z - c)/R), the powers read from the
-// plan's per-point table (formed once, the geometry being static).
-// With the arrival counters (one per box, zero on entry and left zero), a warp
-// that has finished a box counts itself in at the parent after a fence, and
-// the warp that completes the count computes the parent's M2M and carries on
-// upwards; nothing waits. Multipoles of levels 0 and 1 are never read.
-//   M2M (scaled): B_l = -M_0 zeta^l / l + sum_{k<=l} C(l-1,k-1) 2^-k M_k zeta^(l-k)
-// M2M of box b into M(b), balanced over the lanes: with the table
-// m2m[c][l][k] = C(l-1, k-1) 2^-k zeta_c^(l-k) (k >= 1) and -zeta_c^l / l (k = 0),
-// B_l = sum_c sum_{k=0..l} m2m[c][l][k] M_k(child c) (M_0 real). Lane i of a child
-// slot owns the rows l1 = i + 1 and l2 = P - i, whose l1 + l2 + 2 = P + 3 terms it
-// walks in one loop, so every lane does the same work; floor(32 / H) children
-// (H = ceil(P / 2) lanes each) are done at once and their partial rows added by
-// shuffles. Lane 0 also forms B_0 = sum_c M_0(child c).
-template <int P, int ND>
-__device__ __forceinline__ void m2m_box64(const DevTree& t, const double2* __restrict__ m2m, int b,
-                                          double2* __restrict__ M, double2* __restrict__ buf, int lane)
+// component c of (sgn i)^m (X + i Y)
+__device__ __forceinline__ __int128 quarter_turn(__int128 X, __int128 Y, int m, int sgn, int c)
 {
-    constexpr int P1 = P + 1;
-    constexpr int H = (P + 1) / 2;   // lanes per child slot
-    constexpr int CS = 32 / H;       // child slots per round
-    const int slot = lane / H, i = lane % H;
-    const int l1 = i + 1, l2 = P - i;
-    // the four children's multipoles (zeros for missing children), [c][k][d]
-    int chs[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) chs[c] = t.child[4 * b + c];
-    __syncwarp();
-    for (int idx = lane; idx < 4 * P1 * ND; idx += 32) {
-        const int c = idx / (P1 * ND), r = idx % (P1 * ND);
-        buf[idx] = chs[c] >= 0 ? __ldcg(M + (int64_t)chs[c] * P1 * ND + r) : make_double2(0.0, 0.0);
+    __int128 re, im;
+    switch (m & 3) {
+        case 0: re = X, im = Y; break;
+        case 1: re = -Y, im = X; break;
+        case 2: re = -X, im = -Y; break;
+        default: re = Y, im = -X; break;
     }
-    __syncwarp();
-    double2 a1[ND], a2[ND];
-#pragma unroll
-    for (int d = 0; d < ND; ++d) a1[d] = a2[d] = make_double2(0.0, 0.0);
-    if (slot < CS) {
-        for (int c = slot; c < 4; c += CS) {
-            const double2* mc = m2m + (size_t)c * P1 * P1;
-            const double2* bc = buf + (size_t)c * P1 * ND;
-            for (int j = 0; j < P + 3; ++j) {
-                const bool first = j <= l1;
-                const int l = first ? l1 : l2;
-                const int k = first ? j : j - l1 - 1;
-                const double2 zb = mc[l * P1 + k];
-#pragma unroll
-                for (int d = 0; d < ND; ++d) {
-                    const double2 v = bc[k * ND + d];
-                    if (first)
-                        a1[d] = cfma64(zb, v, a1[d]);
-                    else
-                        a2[d] = cfma64(zb, v, a2[d]);
-                }
-            }
-        }
-    }
-    // add the child slots' partial rows into the lanes of slot 0
-#pragma unroll
-    for (int sl = 1; sl < CS; ++sl) {
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            const double2 v1 = make_double2(__shfl_down_sync(0xffffffffu, a1[d].x, sl * H),
-                                            __shfl_down_sync(0xffffffffu, a1[d].y, sl * H));
-            const double2 v2 = make_double2(__shfl_down_sync(0xffffffffu, a2[d].x, sl * H),
-                                            __shfl_down_sync(0xffffffffu, a2[d].y, sl * H));
-            if (slot == 0) {
-                a1[d].x += v1.x, a1[d].y += v1.y;
-                a2[d].x += v2.x, a2[d].y += v2.y;
-            }
-        }
-    }
-    if (slot == 0) {
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            M[((int64_t)b * P1 + l1) * ND + d] = a1[d];
-            if (l2 != l1) M[((int64_t)b * P1 + l2) * ND + d] = a2[d];
-        }
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            double2 m0 = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) m0.x += buf[(size_t)c * P1 * ND + d].x, m0.y += buf[(size_t)c * P1 * ND + d].y;
-            M[((int64_t)b * P1) * ND + d] = m0;
-        }
-    }
-    __syncwarp();
+    __int128 v = c ? im : re;
+    return (sgn < 0 && (m & 1)) ? -v : v;
 }
 
+// a 128-bit integer from the lane `lane ^ o` of `mask`
+__device__ __forceinline__ __int128 shfl_xor_i128(unsigned mask, __int128 v, int o)
+{
+    const long long hi = __shfl_xor_sync(mask, (long long)(v >> 64), o);
+    const unsigned long long lo = __shfl_xor_sync(mask, (unsigned long long)v, o);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+}
+
+// ----------------------------------------------------------------------------
+// a3: P2M, one warp per leaf: lane k sums q_j u_j^k over the leaf's points (u =
+// (z - c)/R), the powers read from the plan's per-point table (formed once, the
+// geometry being static); lane 0 sums q_j. Scaled: M_k = -(1/k) sum_j q_j u_j^k.
 template <int P, int ND>
 __global__ void __launch_bounds__(kW64 * 32)
-    k_p2m64(DevTree t, DevTables tab, PassGeom g, const double* __restrict__ q, double2* __restrict__ M,
-            int* __restrict__ counters)
+    k_p2m64(DevTree t, PassGeom g, const double* __restrict__ q, double2* __restrict__ M)
 {
     constexpr int P1 = P + 1;
-    extern __shared__ __align__(16) unsigned char smem_p2m[];
-    // per warp: the M2M's stage of the four children's multipoles [4][P1][ND]
-    const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
-    double2* pw = reinterpret_cast<double2*>(smem_p2m) + (size_t)wb * 4 * P1 * ND;
+    const int lane = threadIdx.x & 31;
     const double sc = lane == 0 ? 1.0 : -1.0 / (double)lane;
     for (int li = gwarp(); li < t.nleaf; li += nwarps()) {
         const int b = t.leaves[li];
@@ -813,7 +743,6 @@ __global__ void __launch_bounds__(kW64 * 32)
         double2 acc[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) acc[d] = make_double2(0.0, 0.0);
-        // lane k sums q_j u_j^k over the leaf's points (u_j^k stored per point); lane 0 sums q_j
         if (lane <= P) {
 #pragma unroll 4
             for (int j = s0; j < s1; ++j) {
@@ -825,28 +754,139 @@ __global__ void __launch_bounds__(kW64 * 32)
                     acc[d].y = fma(qv, pv.y, acc[d].y);
                 }
             }
-        }
-        if (lane <= P) {
 #pragma unroll
             for (int d = 0; d < ND; ++d)
                 M[((int64_t)b * P1 + lane) * ND + d] = make_double2(acc[d].x * sc, acc[d].y * sc);
         }
-        for (int cur = b;;) {
-            const int par = t.parent[cur];
-            if (par < 0 || t.level[par] < 2) break;
-            __threadfence();  // this warp's M(cur) before its arrival at the parent
-            __syncwarp();
-            int old = 0;
-            if (lane == 0) old = atomicAdd(&counters[par], 1);
-            old = __shfl_sync(0xffffffffu, old, 0);
-            int nch = 0;
+    }
+}
+
+// a3: M2M into the non-leaf boxes of one level (levels from the deepest up),
+// exactly, on the integer pipes. With zeta = s/2 the offset of child c from the
+// parent's centre over the parent half-side, s = sx + i sy (sx, sy = +-1 by
+// quadrant), the scaled M2M of the child's multipole M is
+//   B_l = -M_0 zeta^l / l + sum_{k=1..l} C(l-1, k-1) 2^-k M_k zeta^(l-k)   (l >= 1),
+//   B_0 = M_0,
+// which factors (2^-k zeta^(l-k) = 2^-l s^l s^-k, s^-1 = conj(s)/2) as
+//   a_k = conj(s)^k 2^-k M_k,  beta_n = sum_{j<=n} C(n, j) a_{j+1},
+//   B_l = 2^-l s^l (beta_{l-1} - M_0 / l).
+// conj(s)^k 2^-k and 2^-l s^l are quarter turns times powers of two (times
+// conj(s) or s for odd powers, one addition), beta is the binomial transform of
+// a (P(P-1)/2 additions, real and imaginary parts apart). In 128-bit fixed point
+// with one scale 2^F per parent and density, from the exponents of the four
+// children's coefficients so that every partial sum stays below 2^125, all of it
+// is exact (M_0 / l by an integer division, to one unit of 2^-F): the parent's
+// coefficients are the correctly rounded sums of the four translations. Eight
+// lanes per parent: lane 2c + r of the group carries the real (r = 0) or
+// imaginary (r = 1) sums of child c; partners swap by shuffles, the children's
+// sums are added by shuffles, and the lanes of child 0 store. A parent with an
+// infinity or NaN among its children's coefficients takes the float64 table
+// m2m[c][l][k] = C(l-1, k-1) 2^-k zeta_c^(l-k) (k >= 1), -zeta_c^l / l (k = 0).
+constexpr int kM2MThreads = 128;
+
+template <int P, int ND>
+__global__ void __launch_bounds__(kM2MThreads)
+    k_m2m64(DevTree t, DevTables tab, int b0, int b1, double2* __restrict__ M)
+{
+    constexpr int P1 = P + 1;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int g8 = (int)(gid & 7), c = g8 >> 1, r = g8 & 1;
+    const int64_t bi = b0 + (gid >> 3);
+    if (bi >= b1) return;  // the whole group of eight leaves together
+    const int b = (int)bi;
+    if (t.is_leaf[b]) return;
+    const unsigned grp = 0xffu << ((threadIdx.x & 31) & ~7);
+    const int ch = t.child[4 * b + c];
+    const int sx = (c & 1) ? 1 : -1, sy = (c & 2) ? 1 : -1, sg = sx * sy;
+    const double2* Mc = M + (int64_t)(ch >= 0 ? ch : 0) * P1 * ND;
+    double* Mb = reinterpret_cast<double*>(M + (int64_t)b * P1 * ND);
+#pragma unroll 1
+    for (int d = 0; d < ND; ++d) {
+        // H = max(e_0, max_{k>=1} (e_k - floor(k/2))) over the four children,
+        // |Re M_k|, |Im M_k| < 2^e_k (a missing child: zeros)
+        int H = -1021;
+        bool finite = true;
+        if (ch >= 0) {
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) nch += t.child[4 * par + cc] >= 0 ? 1 : 0;
-            if (old != nch - 1) break;  // a sibling is still running; it will carry on
-            __threadfence();            // the siblings' M before reading them
-            if (lane == 0) counters[par] = 0;
-            m2m_box64<P, ND>(t, tab.m2m64, par, M, pw, lane);
-            cur = par;
+            for (int k = 0; k <= P; ++k) {
+                const double2 v = Mc[k * ND + d];
+                const unsigned e = max(max(exponent_field(v.x), exponent_field(v.y)), 1u);
+                finite = finite && e < 0x7ffu;
+                H = max(H, (int)e - 1022 - k / 2);
+            }
+        }
+        H = max(H, __shfl_xor_sync(grp, H, 2));
+        H = max(H, __shfl_xor_sync(grp, H, 4));
+        finite = __all_sync(grp, finite);
+        if (!finite) {
+            const double2* tc = tab.m2m64 + (size_t)c * P1 * P1;
+            for (int l = 0; l <= P; ++l) {
+                double acc = 0.0;
+                if (ch >= 0) {
+                    if (l == 0) {
+                        acc = r ? Mc[d].y : Mc[d].x;
+                    } else {
+                        for (int k = 0; k <= l; ++k) {
+                            const double2 z = tc[l * P1 + k], v = Mc[k * ND + d];
+                            acc += r ? z.x * v.y + z.y * v.x : z.x * v.x - z.y * v.y;
+                        }
+                    }
+                }
+                acc += __shfl_xor_sync(grp, acc, 2);
+                acc += __shfl_xor_sync(grp, acc, 4);
+                if (c == 0) Mb[(l * ND + d) * 2 + r] = acc;
+            }
+            continue;
+        }
+        // every partial sum and the four children's total: below
+        // 4 sqrt2 (2^(P-1) P + 1) 2^(H + 1/2) <= 2^(H + P + 7) for P <= 30
+        const int F = 118 - P - H;
+        __int128 a[P];  // a[j] = a_{j+1}, then beta_j
+#pragma unroll
+        for (int k = 1; k <= P; ++k) {
+            const double2 v = ch >= 0 ? Mc[k * ND + d] : make_double2(0.0, 0.0);
+            const int m = k >> 1;
+            __int128 X, Y;
+            if ((k & 1) == 0) {
+                X = fixed128(v.x, F - m);
+                Y = fixed128(v.y, F - m);
+            } else {  // times conj(s)
+                const __int128 x = fixed128(v.x, F - m - 1), y = fixed128(v.y, F - m - 1);
+                X = (sx > 0 ? x : -x) + (sy > 0 ? y : -y);
+                Y = (sx > 0 ? y : -y) - (sy > 0 ? x : -x);
+            }
+            a[k - 1] = quarter_turn(X, Y, m, -sg, r);
+        }
+        // binomial transform: beta_n = sum_{j<=n} C(n, j) a_{j+1}
+#pragma unroll
+        for (int i = 1; i < P; ++i)
+#pragma unroll
+            for (int j = P - 1; j >= i; --j) a[j] += a[j - 1];
+        const double2 m0 = ch >= 0 ? Mc[d] : make_double2(0.0, 0.0);
+        const __int128 q0 = fixed128(r ? m0.y : m0.x, F);
+        {  // B_0 = sum of the children's M_0
+            __int128 v = q0;
+            v += shfl_xor_i128(grp, v, 2);
+            v += shfl_xor_i128(grp, v, 4);
+            if (c == 0) Mb[d * 2 + r] = int128_ldexp(v, -F);
+        }
+#pragma unroll
+        for (int l = 1; l <= P; ++l) {
+            const __int128 mine = a[l - 1] - q0 / (__int128)l;
+            const __int128 other = shfl_xor_i128(grp, mine, 1);
+            const __int128 Cx = r ? other : mine, Cy = r ? mine : other;
+            const int m = l >> 1;
+            __int128 X = Cx, Y = Cy;
+            int sc = -F - m;
+            if (l & 1) {  // times s
+                X = (sx > 0 ? Cx : -Cx) - (sy > 0 ? Cy : -Cy);
+                Y = (sy > 0 ? Cx : -Cx) + (sx > 0 ? Cy : -Cy);
+                sc -= 1;
+            }
+            __int128 v = quarter_turn(X, Y, m, sg, r);
+            v += shfl_xor_i128(grp, v, 2);
+            v += shfl_xor_i128(grp, v, 4);
+            if (c == 0) Mb[(l * ND + d) * 2 + r] = int128_ldexp(v, sc);
         }
     }
 }
@@ -1282,19 +1322,6 @@ __global__ void __launch_bounds__(kW64 * 32, ND <= 2 ? 4 : 2)
 // float64 table (l2l[c][l][k] = C(k, l) 2^-l zeta_c^(k-l)) instead.
 constexpr int kL2LThreads = 128;
 
-// component c of (sgn i)^m (X + i Y)
-__device__ __forceinline__ __int128 quarter_turn(__int128 X, __int128 Y, int m, int sgn, int c)
-{
-    __int128 re, im;
-    switch (m & 3) {
-        case 0: re = X, im = Y; break;
-        case 1: re = -Y, im = X; break;
-        case 2: re = -X, im = -Y; break;
-        default: re = Y, im = -X; break;
-    }
-    __int128 v = c ? im : re;
-    return (sgn < 0 && (m & 1)) ? -v : v;
-}
 
 template <int P, int ND>
 __global__ void __launch_bounds__(kL2LThreads)
@@ -1363,9 +1390,7 @@ __global__ void __launch_bounds__(kL2LThreads)
             for (int j = P - 1; j >= i; --j) a[j] += a[j + 1];
 #pragma unroll
         for (int l = 0; l <= P; ++l) {
-            const long long oh = __shfl_xor_sync(pair, (long long)(a[l] >> 64), 1);
-            const unsigned long long ol = __shfl_xor_sync(pair, (unsigned long long)a[l], 1);
-            const __int128 other = (__int128)(((unsigned __int128)(unsigned long long)oh << 64) | ol);
+            const __int128 other = shfl_xor_i128(pair, a[l], 1);
             const __int128 Bx = c ? other : a[l], By = c ? a[l] : other;
             const int m = l >> 1;
             __int128 X = Bx, Y = By;
@@ -1401,12 +1426,6 @@ int device_sms()
     return sms;
 }
 
-template <int P, int ND>
-size_t p2m_smem()
-{
-    return (size_t)kW64 * 4 * (P + 1) * ND * sizeof(double2);
-}
-
 template <int ND>
 size_t leaf_smem()
 {
@@ -1423,10 +1442,8 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
     static bool attr_done = false;
     static int leaf_resident[2] = {0, 0};
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2m64<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p2m_smem<P, ND>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_m2l64<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)m2l64_smem<P, ND>());
+        cudaError_t e = cudaFuncSetAttribute(k_m2l64<P, ND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)m2l64_smem<P, ND>());
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_leaf64<P, ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem<ND>());
         if (e == cudaSuccess)
@@ -1442,8 +1459,15 @@ cudaError_t fmm64_impl(const DevTree& t, const DevTables& tab, const PassGeom& g
         attr_done = true;
     }
     int id = tm ? tm->begin("upward") : -1;
-    k_p2m64<P, ND><<<blocks_for_warps(t.nleaf, kW64), threads, p2m_smem<P, ND>(), s>>>(t, tab, g, ws.q, ws.M,
-                                                                                      ws.m2m_count);
+    k_p2m64<P, ND><<<blocks_for_warps(t.nleaf, kW64), threads, 0, s>>>(t, g, ws.q, ws.M);
+    // M2M level by level from the deepest parents up; multipoles of levels 0 and 1
+    // are never read
+    for (int l = t.nlevels - 2; l >= 2; --l) {
+        const int b0 = t.level_start[l], b1 = t.level_start[l + 1];
+        if (b1 <= b0) continue;
+        const int64_t lanes = 8 * (int64_t)(b1 - b0);
+        k_m2m64<P, ND><<<(int)((lanes + kM2MThreads - 1) / kM2MThreads), kM2MThreads, 0, s>>>(t, tab, b0, b1, ws.M);
+    }
     if (tm) tm->end(id);
     id = tm ? tm->begin("m2l") : -1;
     k_m2l64<P, ND><<<blocks_for_warps(t.nbox, kW64), threads, m2l64_smem<P, ND>(), s>>>(t, tab, g, ws.M, ws.L, ws.q,
