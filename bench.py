@@ -62,7 +62,7 @@ FP32_OPS_PEAK = 152 * 128 * 2.070e9 / 1e12  # FP32/INT32 lane-operations per sec
 # of the plan info, unit name, P, densities, kernel). Only a phase whose kernel
 # has not changed since its capture is listed; others report traffic null.
 PROFILED_TRAFFIC = {
-    "leaf": (486.0, "n_tgt", "target", 24, 1, "k_leaf64d<24, 1>"),
+    "leaf": (485.3, "n_tgt", "target", 24, 1, "k_leaf64d<24, 1>"),
     "m2l": (22.54, "n_v_pairs", "V-list pair", 24, 1, "k_m2l64<24, 1>"),
     "upward": (407.0, "n_src", "source", 24, 1, "k_p2m64<24, 1>"),
     "out": (8.70, "nnz", "nonzero", 24, 1, "k_out_grouped64<1>"),

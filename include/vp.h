@@ -40,9 +40,9 @@
  *   - Every entry point returns a vp_status. No exception crosses the ABI. On
  *     error the output buffers hold unspecified values and the plan stays
  *     usable unless the status is VP_ERR_CUDA (sticky CUDA errors).
- *   - Arithmetic: by default every floating-point operation of an evaluation
- *     (charges, FMM, near field with the library's own table-driven FP64 log,
- *     correction product) is IEEE float64 on the FP64 pipes. VP_FLAG_FF moves
+ *   - Arithmetic: by default inputs, expansions and results are IEEE float64;
+ *     where exact integer arithmetic can replace float64 operations it does
+ *     (details at the flags below), rounding no worse than float64. VP_FLAG_FF moves
  *     the heavy steps to the FP32 pipes in float-float arithmetic (an
  *     unevaluated sum of two floats, about 48 significant bits, narrower than
  *     float64 in significand and exponent range) with float64 inputs and
@@ -105,11 +105,18 @@ typedef struct {
 /* Record CUDA events around every phase of vp_eval (read with vp_plan_phase_times). */
 #define VP_FLAG_TIMING 1u
 /* Arithmetic of a plan (fixed at creation; the two flags exclude each other).
- * Default (neither flag): every step in float64 on the FP64 pipes, shaped for GB300's
- * FP64 rate: near field with the library's own table-driven float64 logarithm (within
- * about 1.5 ulp) and each distance between two adjacent leaves evaluated once for both
- * directions when the targets are the nodes; M2L, P2M/M2M, L2L, L2P in float64 with all
- * lanes busy; correction product with float64 values.
+ * Default (neither flag): float64 results, shaped for GB300's narrow FP64 unit. The
+ * directed near field forms r^2 exactly from integer coordinates and its logarithm in
+ * fixed point (error about 2^-59), summing with float64 FMAs; when the targets are
+ * the nodes each distance between two adjacent leaves is evaluated once for both
+ * directions with the library's own table-driven float64 logarithm (within about 1.5
+ * ulp). M2L: the contraction as exact integer digit products on the tensor cores (62-bit
+ * operands), the rest in float64. M2M and L2L: exact in 128-bit fixed point, each
+ * coefficient correctly rounded. P2M, L2P: float64. Correction product: the values are
+ * stored per row in 52-bit fixed point (rounded to at most 2^-52 of the row's largest
+ * value) and the densities staged per row group the same way, summed exactly in 128
+ * bits and rounded once per row; the adjoint converts the stored values back exactly
+ * and sums in float64.
  * VP_FLAG_FP64: the plain float64 reference kernels (directed near field with CUDA's
  * log, one warp per box and coefficient lane for the expansions); the target gradient
  * of vp_eval_adjoint always runs these.
