@@ -8,8 +8,10 @@ nodes of every cell touching its cell; about 2.4e9 nonzeros): charges, the
 whole FMM (P2M, M2M, M2L, L2L, L2P, M2P, P2L, P2P) and the correction apply.
 
 Metric: volume-potential Mpoints/s = n_targets * ndens / t_eval, float64
-arithmetic, with the relative l-infinity error against the CPU oracle (sampled
-targets) reported beside it (the gate is 1e-10, normalised by sum_j |w_j f_j|).
+results (the steps done exactly in integers instead are listed under "arith"
+in the output line), with the relative l-infinity error against the CPU oracle
+(sampled targets) reported beside it (the gate is 1e-10, normalised by
+sum_j |w_j f_j|).
 Legs report the same path in float-float arithmetic (FP32 pipes), the unit-disk
 workload, 64 densities, the adjoint, 256 uneven problems, the differentiable
 form, oversampling, interpolation, triangle corrections and the
@@ -971,7 +973,8 @@ def main():
                   "fixed point (2^-55) on the integer pipes, accumulated in float64; the M2L contraction as exact "
                   "integer digit products on the bf16 tensor cores (62-bit operands); the correction apply as exact "
                   "128-bit sums of 52-bit fixed-point values and densities on the integer pipes, rounded once per "
-                  "row; every other step IEEE float64"),
+                  "row; M2M and L2L exact in 128-bit fixed point, each coefficient rounded once; every other step "
+                  "IEEE float64"),
         "config": {"workload": prob.name, "n_src": prob.n_src, "n_tgt": prob.n_tgt, "nnz": prob.nnz,
                    "correction": "own + near cells" if args.csr == "near" or args.workload == "disk" else "own cell",
                    "ndens": 1, "p_fmm": info.p_fmm, "leaf": info.leaf, "levels": info.n_levels,
