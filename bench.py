@@ -54,6 +54,7 @@ P2P_FLOP_PER_PAIR = 27.0
 F64_OPS_PAIR = 2.0
 F64_OPS_SYM = 11.0
 F64_OPS_L2P_PER_COEF = 2.0
+F64_OPS_M2L_PER_P = 11.0  # FP64 operations per V-list pair, in units of P (tensor-core M2L)
 # float-float: FP32 operations per evaluated distance (the kernel's model)
 P2P_FF_OPS_PER_PAIR = 77.0
 P2P_FF_OPS_REVERSE = 14.0
@@ -102,10 +103,13 @@ def roofline_models(info, ndens, fp64_tflops):
                              f"target for L2P; the kernels issue {F64_OPS_PAIR:.0f} FP64 ops per directed pair "
                              f"(plus about 100 integer instructions), {F64_OPS_SYM:.0f} per distance serving both "
                              f"directions ({evals} evaluations for {pairs} directed pairs)"},
-        "m2l": {"kernel": "k_m2l64 (float64 scaled-Hankel M2L + P2L, G V-list entries per warp)",
+        "m2l": {"kernel": "k_m2l64 (scaled-Hankel M2L, the contraction as exact integer digit products on the "
+                          "bf16 tensor cores; + P2L)",
                 "flop": info.n_v_pairs * 8.0 * (P + 1) ** 2 * ndens,
-                "ops": info.n_v_pairs * (2.0 * P * P + 10.0 * P) * ndens, "units": info.n_v_pairs,
-                "ops_peak": ops_peak, "per_unit": f"8(P+1)^2 flops per V-list pair, P={P}"},
+                "ops": info.n_v_pairs * F64_OPS_M2L_PER_P * P * ndens, "units": info.n_v_pairs,
+                "ops_peak": ops_peak,
+                "per_unit": f"8(P+1)^2 flops per V-list pair, P={P}; the kernel issues about "
+                            f"{F64_OPS_M2L_PER_P:.0f}P FP64 ops per pair (operand scaling and output accumulation)"},
         "out": {"kernel": "k_out_grouped64 (correction apply in exact fixed point, rows grouped by shared "
                           "column lists)", "bound": "hbm",
                 "flop": info.nnz * 2.0 * ndens, "ops": 0.0, "units": info.nnz,
@@ -115,8 +119,9 @@ def roofline_models(info, ndens, fp64_tflops):
                             "the result; the arithmetic is four 32x32-bit integer multiply-adds per nonzero (no "
                             "FP64 operations)"},
         "upward": {"kernel": "k_p2m64 (float64 P2M) + k_m2m64 (M2M per level, exact in 128-bit fixed point)",
-                   "flop": info.n_src * 8.0 * P * ndens, "ops": info.n_src * 6.0 * P * ndens,
-                   "units": info.n_src, "ops_peak": ops_peak, "per_unit": f"8P flops per source, P={P}"},
+                   "flop": info.n_src * 8.0 * P * ndens, "ops": info.n_src * 2.0 * (P + 1) * ndens,
+                   "units": info.n_src, "ops_peak": ops_peak,
+                   "per_unit": f"8P flops per source, P={P}; P2M issues 2(P+1) FP64 FMAs per source, M2M none"},
     }
 
 
